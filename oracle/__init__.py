@@ -1,0 +1,30 @@
+"""FP64 CPU oracle for the per-tile sCOLA particle-mesh evolution.
+
+TEST INFRASTRUCTURE, NOT PRODUCT CODE.  Only the test suite (``tests/``),
+``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may import
+anything from this package.  The CUDA library never calls into it and shares
+no code, tables or constants with it; the only thing both sides consume is the
+seeded synthetic input produced by ``synth_inputs``.
+
+The oracle is a plain, slow, double-precision restatement of the method of
+Leclercq et al., "Perfectly parallel cosmological simulations using spatial
+comoving Lagrangian acceleration" (arXiv:2003.04925).  Each function cites the
+section, equation or table of the paper it follows.  Equation numbers follow
+the paper's numbering of displayed equations (Eq. 1 is x = q + Psi).
+
+Modules
+-------
+cosmology   background, growth factors D1/D2, COLA time coefficients (App. A, B)
+ics         white-noise colouring with a BBKS power spectrum (Sec. 3.1, A.1)
+lpt         Lagrangian potentials phi1, phi2 and displacements Psi1, Psi2 (Sec. 2.1, A.2, C.2)
+tiling      tiles, buffers, sCOLA boxes, r and p (Sec. 3.2, B.1, B.2; Eqs. 20-21)
+boundary    Dirichlet boundary potential on the padded PM grid (Sec. 3.3 C.3, Eq. 23)
+pm          B^sCOLA deposit, Dirichlet DST-I Poisson solve, FDA gradient and
+            interpolation (Sec. 3.4, App. C)
+scola       the KDK driver for sCOLA boxes and the untiling (App. B, Sec. 3.2)
+tcola       periodic full-box tCOLA reference, used only to pin the sCOLA box
+            machinery (Sec. 2.2, Sec. 4.3)
+stats       final periodic CIC density and the P(k) estimator (Sec. 4.1-4.2, Eq. 24)
+
+Parity status of each part (what pins it) is listed in each module header.
+"""

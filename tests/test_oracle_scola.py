@@ -1,0 +1,111 @@
+"""Pins of the oracle's sCOLA driver (Sec. 3, App. A-B) against exact and limiting cases."""
+import numpy as np
+import pytest
+
+import synth_inputs
+from oracle import scola, tcola, tiling
+
+
+def _cfg(**kw):
+    base = dict(L=64.0, Np=16, Ntiles=2, Nbuf=3, mesh_ratio=1, nsteps=4, a_i=0.05, a_f=1.0)
+    base.update(kw)
+    return scola.ScolaConfig(**base)
+
+
+def test_zero_amplitude_is_exactly_zero():
+    cfg = _cfg()
+    out = scola.run_scola(np.zeros((16,) * 3, np.float32), cfg)
+    assert np.all(out["s"] == 0.0) and np.all(out["p"] == 0.0)
+
+
+def test_lpt_force_mode_follows_2lpt_exactly():
+    # Replacing the PM force by D1 Psi1 - (D2 - D1^2) Psi2 makes every kick vanish
+    # (Eq. 54), so p_res stays 0 and the drift telescopes onto x_LPT(a_f) (Eq. 39).
+    cfg = _cfg(nsteps=5)
+    w = synth_inputs.white_noise(16, 5)
+    out = scola.run_scola(w, cfg, force_mode="lpt")
+    f, sch = out["fields"], out["sched"]
+    s_lpt = (-sch["D1_f"] * f.psi1 + sch["D2_f"] * f.psi2).reshape(3, -1).T
+    np.testing.assert_allclose(out["s"], s_lpt, atol=1e-12 * np.abs(s_lpt).max())
+    for b in out["boxes"]:
+        assert np.abs(b["p_res"]).max() < 1e-14 * np.abs(f.psi1).max()
+
+
+def test_small_amplitude_residual_scales_linearly():
+    # At vanishing amplitude the dynamics is linear: Psi_res / Psi_LPT is eps-independent
+    # and small at large scales (the residual is the PM discretisation error).
+    cfg = _cfg(nsteps=4)
+    w = synth_inputs.white_noise(16, 6).astype(np.float64)
+    ratios = []
+    for eps in (1e-3, 1e-4):
+        out = scola.run_scola(eps * w, cfg)
+        f, sch = out["fields"], out["sched"]
+        s_lpt = (-sch["D1_f"] * f.psi1 + sch["D2_f"] * f.psi2).reshape(3, -1).T
+        ratios.append(np.sqrt(np.mean((out["s"] - s_lpt) ** 2) / np.mean(s_lpt**2)))
+    assert abs(ratios[0] / ratios[1] - 1) < 1e-3
+    assert ratios[0] < 0.5
+
+
+def _true_density_true_potential_run(cfg, w):
+    f = scola.initial_fields(w, cfg)
+    sch = scola.schedule(cfg)
+    ref = tcola.run_tcola(cfg, f, sch, record=True)
+    res = []
+    for b in range(cfg.nboxes):
+        g = scola.box_geometry(cfg, b)
+        idx = tcola.box_cell_to_full(cfg, g)
+        Ng = g.Ng
+
+        def dfn(k, idx=idx, Ng=Ng):
+            return tcola.restrict_padded(ref["deltas"][k], idx)[2:Ng + 2, 2:Ng + 2, 2:Ng + 2]
+
+        def pfn(k, idx=idx, Ng=Ng):
+            p = tcola.restrict_padded(ref["phis"][k], idx).copy()
+            p[2:Ng + 2, 2:Ng + 2, 2:Ng + 2] = 0.0
+            return p
+
+        res.append(scola.evolve_box(cfg, b, f, sch, delta_fn=dfn, phi_bc_fn=pfn))
+    return ref, res
+
+
+@pytest.mark.parametrize("ratio", [1, 2])
+def test_true_density_and_potential_reproduce_tcola(ratio):
+    # Sec. 4.3: with delta_int = delta and Phi_BCs = Phi (both from the monolithic run),
+    # the sCOLA boxes reproduce tCOLA.  With aligned PM grids this is exact up to rounding:
+    # the Dirichlet solve restricted to the box is unique (pins deposit-free box machinery,
+    # the DST solve, the ghost padding, gradient, interpolation and the kick/drift path).
+    cfg = _cfg(Np=16, Ntiles=2, Nbuf=3, mesh_ratio=ratio, nsteps=3)
+    w = synth_inputs.white_noise(16, 9).astype(np.float64) * 0.6
+    ref, res = _true_density_true_potential_run(cfg, w)
+    keep = tiling.tile_interior_mask(cfg.Np, cfg.Ntiles, 3)
+    for r in res:
+        ids = r["ids"][keep]
+        scale = np.abs(ref["s"]).max()
+        np.testing.assert_allclose(r["s"][keep], ref["s"][ids], atol=1e-9 * scale)
+        np.testing.assert_allclose(r["p"][keep], ref["p"][ids], atol=1e-9 * np.abs(ref["p"]).max())
+
+
+@pytest.mark.slow
+def test_buffer_convergence_towards_tcola():
+    # Larger buffers push the boundary approximations away from the tiles (Sec. 4.1-4.2).
+    w = synth_inputs.white_noise(32, 1)
+    errs = []
+    ref = None
+    for nbuf in (2, 4, 8):
+        cfg = scola.ScolaConfig(L=100.0, Np=32, Ntiles=2, Nbuf=nbuf, mesh_ratio=1, nsteps=6)
+        out = scola.run_scola(w, cfg)
+        if ref is None:
+            ref = tcola.run_tcola(cfg, out["fields"], out["sched"])
+        d = out["s"] - ref["s"]
+        errs.append(np.sqrt(np.mean(d**2)))
+    assert errs[0] > errs[1] > errs[2]
+
+
+def test_mass_drop_grows_from_a_small_initial_value():
+    # B^sCOLA discards CIC weight outside the box (Sec. 3.4.1): nothing is ever gained, the
+    # loss is small at a_i (displacements are small) and grows as particles leave the box.
+    cfg = _cfg(Np=16, Ntiles=2, Nbuf=3, nsteps=4)
+    out = scola.run_scola(synth_inputs.white_noise(16, 2), cfg)
+    for b in out["boxes"]:
+        lost = 1.0 - np.array(b["deposited"]) / b["geometry"].Nsc ** 3
+        assert np.all(lost >= -1e-12) and lost[0] < 0.02 and lost[-1] > lost[0]
