@@ -1,0 +1,379 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the batched sCOLA forward run on GB300.
+
+One step = one complete forward run of the workload (white noise -> initial
+density and 2LPT on the full box -> every sCOLA box evolved with the KDK COLA
+integrator -> untiling), inputs resident in HBM.  The metric counts the work
+the method processes: sum over boxes of Np,sCOLA^3 times the number of COLA
+steps, per second.
+
+  python bench.py [--gpus N --steps K --warmup W] [--workload batched_128]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on bounded samples
+
+Multi-GPU: every rank runs an independent replica of the workload (different
+seed); there is no collective on the data path (boxes never communicate), so
+value = sum over ranks of the work / max rank time ("weak" scaling).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "sCOLA particle-steps/s batched vs per-tile at stated error; adjoint/fwd cost"
+UNIT = "particle-steps/s"
+L2_BYTES = 129 * 1024 * 1024
+FP32_LANES_PER_SM = 128
+NUM_SMS = 152
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="scola", choices=["scola", "reference"])
+    ap.add_argument("--workload", default="batched_128")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload_kwargs(name):
+    import synth_inputs
+    W = synth_inputs.WORKLOADS[name]
+    if W["Nbuf"] == "uneven":
+        bufs = [int(b) for b in synth_inputs.uneven_buffers(W["Ntiles"], W["buffer_seed"],
+                                                             W["buffer_choices"])]
+        nb = dict(Nbuf=0, buffers=bufs)
+    else:
+        nb = dict(Nbuf=W["Nbuf"])
+    kw = dict(L=W["L"], Np=W["Np"], Ntiles=W["Ntiles"], mesh_ratio=W["mesh_ratio"],
+              nsteps=W["nsteps"], a_i=W["a_i"], a_f=W["a_f"], **nb)
+    return kw, W
+
+
+def box_sizes(kw):
+    ntile = kw["Np"] // kw["Ntiles"]
+    bufs = kw.get("buffers") or [kw["Nbuf"]] * kw["Ntiles"] ** 3
+    nsc = [ntile + 2 * b for b in bufs]
+    ng = [kw.get("Ng") or kw["mesh_ratio"] * n for n in nsc]
+    return nsc, ng
+
+
+def particle_steps_per_run(kw):
+    nsc, _ = box_sizes(kw)
+    return sum(n**3 for n in nsc) * kw["nsteps"]
+
+
+def config_block(name, kw, W, extra=None):
+    nsc, ng = box_sizes(kw)
+    cfg = {"workload": name, "L_mpc_h": kw["L"], "Np": kw["Np"], "Ntiles": kw["Ntiles"],
+           "Nbuf": kw.get("buffers") and "uneven" or kw["Nbuf"], "Np_sCOLA": sorted(set(nsc)),
+           "Ng": sorted(set(ng)), "nsteps": kw["nsteps"], "a_i": kw["a_i"], "a_f": kw["a_f"],
+           "cosmology": "BBKS LCDM Om=0.3 OL=0.7 h=0.7 ns=0.96 sigma8=0.8",
+           "ics": "seeded Philox white noise, seed %d" % W["seed"]}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        sm_sorted = sorted(sm)
+        return {"sm_mhz": sm_sorted[len(sm_sorted) // 2] if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------- oracle timing
+def oracle_sample_rate(name, budget_s, nboxes_cap=None):
+    """Oracle particle-steps/s on a bounded sample: ICs once (prorated), whole boxes evolved."""
+    import numpy as np
+    import synth_inputs
+    from oracle import scola as oscola
+    kw, W = workload_kwargs(name)
+    cfg = oscola.ScolaConfig(L=kw["L"], Np=kw["Np"], Ntiles=kw["Ntiles"],
+                             Nbuf=kw.get("buffers") or kw["Nbuf"], mesh_ratio=kw["mesh_ratio"],
+                             nsteps=kw["nsteps"], a_i=kw["a_i"], a_f=kw["a_f"])
+    w = synth_inputs.white_noise(cfg.Np, W["seed"])
+    t0 = time.perf_counter()
+    fields = oscola.initial_fields(w, cfg)
+    sched = oscola.schedule(cfg)
+    t_ics = time.perf_counter() - t0
+    done, t_boxes, work = 0, 0.0, 0
+    while True:
+        b = (done * 37) % cfg.nboxes
+        t1 = time.perf_counter()
+        r = oscola.evolve_box(cfg, b, fields, sched)
+        t_boxes += time.perf_counter() - t1
+        work += r["geometry"].Nsc ** 3 * cfg.nsteps
+        done += 1
+        if t_boxes >= budget_s or (nboxes_cap and done >= nboxes_cap):
+            break
+    seconds = t_boxes + t_ics * done / cfg.nboxes
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": work / seconds, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d of %d sCOLA boxes evolved over all %d steps (%.1f s) + 1/%d of the "
+                      "full-box IC/2LPT time per box (numpy FP64, BLAS threads up to %d)"
+                      % (done, cfg.nboxes, cfg.nsteps, t_boxes, cfg.nboxes, cores)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    kw, W = workload_kwargs(args.workload)
+    import synth_inputs
+    from oracle import scola as oscola
+    cfg = oscola.ScolaConfig(L=kw["L"], Np=kw["Np"], Ntiles=kw["Ntiles"],
+                             Nbuf=kw.get("buffers") or kw["Nbuf"], mesh_ratio=kw["mesh_ratio"],
+                             nsteps=kw["nsteps"], a_i=kw["a_i"], a_f=kw["a_f"])
+    w = synth_inputs.white_noise(cfg.Np, W["seed"])
+    t0 = time.perf_counter()
+    fields = oscola.initial_fields(w, cfg)
+    sched = oscola.schedule(cfg)
+    t_ics = time.perf_counter() - t0
+    # each step: one sCOLA box (rotating through the boxes) over all COLA steps, plus the
+    # per-box share of the IC stage; shrink to fewer boxes never (a box is the unit)
+    for i in range(args.warmup):
+        oscola.evolve_box(cfg, (i * 37) % cfg.nboxes, fields, sched)
+    t_total, work = 0.0, 0
+    for i in range(args.steps):
+        b = ((args.warmup + i) * 37) % cfg.nboxes
+        t1 = time.perf_counter()
+        r = oscola.evolve_box(cfg, b, fields, sched)
+        t_total += time.perf_counter() - t1 + t_ics / cfg.nboxes
+        work += r["geometry"].Nsc ** 3 * cfg.nsteps
+    value = work / t_total
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": config_block(args.workload, kw, W, {"step": "one sCOLA box over all COLA "
+                                   "steps + 1/nboxes of the IC/2LPT stage"}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d boxes of %d, numpy FP64" % (args.steps, cfg.nboxes)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- roofline
+def kernel_roofline(kt, kw, clocks, peaks):
+    """Algorithmic bytes or flops per launch of each kernel class and the dominant one."""
+    nsc, ng = box_sizes(kw)
+    P = sum(n**3 for n in nsc)
+    M = sum(g**3 for g in ng)
+    MP = sum((g + 4) ** 3 for g in ng)
+    SH = MP - M
+    dense = sum(2.0 * g * g**3 for g in ng)          # flops of one dense DST-I along one axis
+    work = {
+        "pad": ("hbm", 8.0 * SH),
+        "deposit": ("hbm", 12.0 * P + 4.0 * M),
+        "dst_z_fwd": ("alu", dense), "dst_y_fwd": ("alu", dense), "dst_x_solve": ("alu", 2 * dense),
+        "dst_y_inv": ("alu", dense), "dst_z_inv": ("alu", dense),
+        "kick_drift": ("hbm", 72.0 * P + 4.0 * MP),
+    }
+    sm_mhz = (clocks or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    alu_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12     # FP32 FMA TFLOP/s
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    total = sum(kt.values())
+    rows = {}
+    for k, ms in kt.items():
+        bound, amount = work[k]
+        if bound == "hbm":
+            ach = amount / (ms * 1e-3) / 1e9
+            rows[k] = {"ms": ms, "share": ms / total, "bound": "hbm", "achieved": ach,
+                       "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak}
+        else:
+            ach = amount / (ms * 1e-3) / 1e12
+            rows[k] = {"ms": ms, "share": ms / total, "bound": "alu", "achieved": ach,
+                       "peak": alu_peak, "unit": "TFLOP/s", "frac": ach / alu_peak}
+    dom = max(rows, key=lambda k: rows[k]["ms"])
+    return dom, rows
+
+
+def run_gpu(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2003_04925_gb300 as sc
+    import synth_inputs
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    kw, W = workload_kwargs(args.workload)
+    sim = sc.Scola(**kw)
+    stream = torch.cuda.current_stream()
+    w_np = synth_inputs.white_noise(kw["Np"], W["seed"] + rank)
+    w = torch.from_numpy(w_np).cuda()
+    n = kw["Np"] ** 3
+    x = torch.empty(n, 3, device="cuda")
+    p = torch.empty(n, 3, device="cuda")
+    for _ in range(args.warmup):
+        sim.forward(w, x, p)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    clocks = ClockSampler(local_rank)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        sim.forward(w, x, p)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    launches = sim.stats()["kernel_launches"]
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    work = particle_steps_per_run(kw)
+    value = world * work / (ms * 1e-3)
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timing
+    w_h = torch.from_numpy(w_np).pin_memory()
+    x_h = torch.empty(n, 3).pin_memory()
+    p_h = torch.empty(n, 3).pin_memory()
+    for _ in range(max(1, args.warmup)):
+        sim.forward_host(w_h, x_h, p_h)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sim.forward_host(w_h, x_h, p_h)
+    t_e2e = (time.perf_counter() - t0) / args.steps
+    if dist is not None:
+        t = torch.tensor([t_e2e], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    e2e = {"value": world * work / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 4 * n,
+           "d2h_bytes_per_step": 2 * 12 * n}
+
+    # per-kernel device time from events recorded between the kernels of the graph
+    sc.scola_set_profiling(sim.ctx, True)
+    for _ in range(2):
+        sim.forward(w, x, p)
+    torch.cuda.synchronize()
+    kt = sc.scola_kernel_times(sim.ctx)
+    sc.scola_set_profiling(sim.ctx, False)
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        peak_src = "measured"
+    except (OSError, ValueError):
+        peaks = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}
+        peak_src = "fallback"
+    dom, rows = kernel_roofline(kt, kw, clk, peaks)
+    d = rows[dom]
+    roofline = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"],
+                "unit": d["unit"], "frac": d["frac"], "traffic": None,
+                "peak_source": peak_src if d["bound"] == "hbm" else
+                "FP32 FMA: 152 SMs x 128 lanes x 2 flop x median SM clock under load",
+                "kernels": {k: {"ms_per_launch": round(v["ms"], 5), "share": round(v["share"], 4),
+                                "frac": round(v["frac"], 4), "bound": v["bound"]}
+                            for k, v in rows.items()}}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = oracle_sample_rate(args.workload, budget_s=15.0)
+    if rank == 0:
+        nsc, ng = box_sizes(kw)
+        ws_bytes = 4 * (12 * sum(k**3 for k in nsc)) + 8 * sum(g**3 for g in ng) \
+            + 4 * 2 * sum(g**3 for g in ng) + 4 * sum((g + 4) ** 3 for g in ng)
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": config_block(args.workload, kw, W, {
+                    "step": "one full forward run (ICs + 2LPT + all boxes x all COLA steps + untiling)",
+                    "particle_steps_per_step": work,
+                    "l2": "working set %.2f GB > 129 MB L2, no flush" % (ws_bytes / 1e9),
+                    "parallelism": "replicas x%d" % world, "batching": "all boxes per launch, CUDA graph",
+                    "dst": "dense sine-matrix pencils, FP32 CUDA cores"}),
+                "e2e": e2e, "gpu_launches": int(launches * args.steps), "clocks": clk,
+                "roofline": roofline, "cpu_baseline": cpu,
+                "stats": {k: v for k, v in sim.stats().items() if k in ("ms_lpt", "ms_evolve", "r", "p")}}
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_gpu(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,251 @@
+/*
+ * scola.h - C ABI of the GB300 (sm_103a) library for the perfectly parallel
+ * spatial-COLA (sCOLA) method of Leclercq et al., arXiv:2003.04925.
+ *
+ * What the library computes (the paper's statement of the problem, Sec. 3):
+ * a periodic box of side L holds Np^3 particles on a Lagrangian lattice.
+ * From a white-noise field the library builds the initial density
+ * (Sec. 3.1, A.1) and the 2LPT potentials and displacements (Sec. 2.1,
+ * Eqs. 2-6, A.2), splits the lattice into Ntiles^3 tiles with a buffer of
+ * Nbuf particles around each (Sec. 3.2, B.1), evolves every sCOLA box
+ * independently with a particle-mesh COLA integrator whose Poisson solve uses
+ * Dirichlet boundary values from the linearly evolving potential (Sec. 3.3,
+ * 3.4, Eq. 23, App. A-C), and writes the tile particles back to global
+ * arrays (B.2).  Every step of this path runs in the library's own CUDA
+ * kernels except the full-box Fourier transforms of the initial-condition
+ * stage, which call cuFFT (the paper's code calls FFTW there, Sec. 3.1).
+ *
+ * Conventions used by every entry point:
+ *   - units: Mpc/h, time in 1/H0 with H0 = 1, time variable the scale factor a;
+ *   - particle (i, j, k), k fastest, has id (i*Np + j)*Np + k and Lagrangian
+ *     position q = ((i + 1/2), (j + 1/2), (k + 1/2)) * L/Np;
+ *   - tile (tx, ty, tz) has box id (tx*Ntiles + ty)*Ntiles + tz;
+ *   - grids are C-ordered [i][j][k] FP32 arrays, k fastest;
+ *   - "device" pointers are CUDA device (or managed) memory owned by the
+ *     caller and must stay valid until the stream work completes;
+ *   - every call that launches work enqueues it on the context's stream and
+ *     returns without synchronising, unless its comment says otherwise;
+ *   - no call throws; each returns a scola_status.  On SCOLA_ERR_CUDA the
+ *     CUDA error string is available from scola_last_error().
+ *
+ * Thread safety: a context may be used by one host thread at a time.
+ */
+#ifndef SCOLA_H
+#define SCOLA_H
+
+#include <stdint.h>
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum scola_status {
+    SCOLA_OK = 0,
+    SCOLA_ERR_INVALID_ARG = 1,   /* a parameter violates the problem statement */
+    SCOLA_ERR_UNSUPPORTED = 2,   /* valid in the paper, not built here (e.g. FDA order 4/6) */
+    SCOLA_ERR_OOM = 3,           /* a device allocation failed */
+    SCOLA_ERR_CUDA = 4,          /* a CUDA or cuFFT call failed; see scola_last_error() */
+    SCOLA_ERR_STATE = 5          /* call made in the wrong order (e.g. force before setup) */
+} scola_status;
+
+typedef enum scola_dst_variant {
+    SCOLA_DST_SIMT = 0,          /* dense sine-matrix pencils on FP32 CUDA cores */
+    SCOLA_DST_AUTO = 2           /* the fastest built variant */
+} scola_dst_variant;
+
+/*
+ * Problem statement.  Field names follow the paper's nomenclature (Sec. 3,
+ * nomenclature table):
+ *   L            full box side [Mpc/h]
+ *   Np           particles per side; the LPT grid has N = Np cells per side
+ *   Ntiles       tiles per side; Np must be a multiple of Ntiles (Sec. 3.2)
+ *   Nbuf         buffer particles per side, the same for every tile
+ *   buffers      optional per-tile buffer widths (host array of Ntiles^3,
+ *                box-id order), copied by scola_create; NULL = use Nbuf
+ *   mesh_ratio   PM cells per particle spacing: Ng = mesh_ratio * Np,sCOLA
+ *   Ng           explicit PM grid size per side (uniform buffers only);
+ *                0 = use mesh_ratio.  Ng >= Np,sCOLA (Sec. 3.3, C.3)
+ *   Om, OL       matter and Lambda density parameters (Ok = 1 - Om - OL)
+ *   h, ns, sigma8  BBKS power spectrum P = A k^ns T^2(k / (Om h)), normalised
+ *                to sigma8 at a = 1
+ *   a_i, a_f     initial (2LPT) and final scale factors
+ *   nsteps       COLA drift steps, linear in a (nsteps + 1 force evaluations)
+ *   nLPT         exponent of the modified time stepping u(a) = a^nLPT
+ *                (App. B, Eq. 60); the paper uses -2.5
+ *   fda_order    finite-difference order; only 2 is built
+ *   dst_variant  one of scola_dst_variant
+ */
+typedef struct scola_params {
+    double L;
+    int32_t Np;
+    int32_t Ntiles;
+    int32_t Nbuf;
+    int32_t mesh_ratio;
+    int32_t Ng;
+    int32_t fda_order;
+    int32_t dst_variant;
+    int32_t nsteps;
+    double Om, OL, h, ns, sigma8;
+    double a_i, a_f;
+    double nLPT;
+    const int32_t *buffers;
+} scola_params;
+
+typedef struct scola_ctx scola_ctx;
+
+/* Run statistics of the last scola_forward (or scola_pm_force) call. */
+typedef struct scola_stats {
+    int32_t nboxes;
+    int64_t box_particles;        /* sum over boxes of Np,sCOLA^3 */
+    int64_t mesh_cells;           /* sum over boxes of Ng^3 */
+    int32_t force_evaluations;    /* nsteps + 1 */
+    double r, p;                  /* over-simulation r (Eq. 20), parallelisation potential p (Eq. 21) */
+    double ms_lpt;                /* initial-condition and 2LPT stage, device time */
+    double ms_evolve;             /* gather + evolution + scatter, device time */
+    int64_t kernel_launches;      /* kernels launched by the last forward call */
+} scola_stats;
+
+/*
+ * Validate the problem, compute the FP64 cosmology (growth factors, COLA
+ * time coefficients, power-spectrum amplitude) on the host, and allocate the
+ * context's device arenas on the current device.
+ *   params  problem statement (copied)
+ *   stream  cudaStream_t on which all later work is enqueued (NULL = legacy default)
+ *   out     receives the new context
+ * Errors: INVALID_ARG (Np % Ntiles != 0, Ng < Np,sCOLA, non-positive sizes,
+ * a_i >= a_f, nsteps < 1, Np,sCOLA > Np), UNSUPPORTED (fda_order != 2), OOM, CUDA.
+ * Synchronous.
+ */
+scola_status scola_create(const scola_params *params, void *stream, scola_ctx **out);
+
+/* Free the context and its device arenas.  Synchronises the stream first. */
+void scola_destroy(scola_ctx *ctx);
+
+/*
+ * The full forward run (Sec. 3, Fig. 1): A.1-A.2 on the full box, B.1 tiling,
+ * C.1-C.3 per box, D evolution of every box, B.2 untiling.
+ *   w_dev  device, Np^3 FP32 white noise (unit variance per LPT cell)
+ *   x_dev  device, Np^3 x 3 FP32, receives final positions in [0, L), id order
+ *   p_dev  device, Np^3 x 3 FP32, receives final momenta p = dx/da / calD
+ *          (App. A, Eq. 37) including the LPT part (L+, Eq. 55)
+ * The evolution is replayed from a CUDA graph captured on the first call.
+ */
+scola_status scola_forward(scola_ctx *ctx, const float *w_dev, float *x_dev, float *p_dev);
+
+/*
+ * Same as scola_forward with HOST buffers: copies w to the device, runs,
+ * copies x and p back, and synchronises the stream before returning.
+ *   w_host  host, Np^3 FP32; x_host, p_host  host, Np^3 x 3 FP32
+ */
+scola_status scola_forward_host(scola_ctx *ctx, const float *w_host, float *x_host, float *p_host);
+
+/*
+ * The initial-condition and 2LPT stage alone (Sec. 3.1, A.1-A.2; Eqs. 5-6;
+ * Psi = FDA-2 gradient at the lattice nodes, App. A below Eq. 39).  Also
+ * leaves the fields in the context for scola_setup_boxes.
+ *   w_dev     device, Np^3 FP32 white noise
+ *   delta_dev, phi1_dev, phi2_dev   device, Np^3 FP32 each, or NULL
+ *   psi1_dev, psi2_dev              device, 3 x Np^3 FP32 each ([component][id]), or NULL
+ */
+scola_status scola_lpt_fields(scola_ctx *ctx, const float *w_dev, float *delta_dev,
+                              float *phi1_dev, float *phi2_dev,
+                              float *psi1_dev, float *psi2_dev);
+
+/*
+ * C.1-C.3 for every box from the fields of the last scola_lpt_fields call:
+ * gather Psi1, Psi2 of the box particles, set s = -D1(a_i) Psi1 + D2(a_i) Psi2,
+ * p_res = 0 (L-, Eq. 55), and precompute the Dirichlet shell (phi1 trilinearly
+ * interpolated to the padded PM cells outside the interior, FP64 accumulation;
+ * C.3, Eq. 23).  Errors: STATE if scola_lpt_fields has not run.
+ */
+scola_status scola_setup_boxes(scola_ctx *ctx);
+
+/*
+ * One PM force evaluation in every box (Sec. 3.4): B^sCOLA deposit of the
+ * given displacements, Dirichlet DST-I Poisson solve with
+ * Phi_BCs = D1 * shell (Eq. 23, App. C), FDA-2 gradient and CIC
+ * interpolation.  Uses the shells of scola_setup_boxes.
+ *   s_dev     device, 3 x P FP32 box-particle displacements s = x - q,
+ *             [component][box particle], boxes concatenated in box-id order,
+ *             box-local particle order (bi*Nsc + bj)*Nsc + bk
+ *   D1        growth factor scaling the boundary shell
+ *   F_dev     device, 3 x P FP32, receives grad Phi at the particles
+ *   delta_dev device, sum_b Ng^3 FP32 interior densities (delta, before the
+ *             boundary correction), or NULL
+ *   phi_dev   device, sum_b (Ng+4)^3 FP32 padded potentials, or NULL
+ * P = scola_box_particle_count().  Errors: STATE before scola_setup_boxes.
+ */
+scola_status scola_pm_force(scola_ctx *ctx, const float *s_dev, double D1, float *F_dev,
+                            float *delta_dev, float *phi_dev);
+
+/* Total number of box particles P (sum over boxes of Np,sCOLA^3). */
+int64_t scola_box_particle_count(const scola_ctx *ctx);
+
+/* Total interior and padded mesh sizes (sum over boxes of Ng^3 and (Ng+4)^3). */
+int64_t scola_mesh_cell_count(const scola_ctx *ctx);
+int64_t scola_padded_cell_count(const scola_ctx *ctx);
+
+/*
+ * Tile assignment (Sec. 3.2): global particle id of every box particle, in
+ * the layout of scola_pm_force (device kernel, bit-exact integer arithmetic).
+ *   gid_dev  device, P int64
+ */
+scola_status scola_box_particle_ids(scola_ctx *ctx, int64_t *gid_dev);
+
+/*
+ * Host-side tiling arithmetic (Sec. 3.2, Eqs. 20-21), no context needed.
+ *   box_nsc  host, Ntiles^3 int32 or NULL: Np,sCOLA per box
+ *   box_ng   host, Ntiles^3 int32 or NULL: Ng per box
+ *   r, p     host or NULL: over-simulation and parallelisation potential
+ */
+scola_status scola_tiling_info(const scola_params *params, int32_t *box_nsc, int32_t *box_ng,
+                               double *r, double *p);
+
+/*
+ * Final density (Sec. 4.1): periodic CIC of all Np^3 particles on the N^3 LPT
+ * grid, delta = rho / nbar - 1.  Deterministic (fixed-point accumulation).
+ *   x_dev      device, Np^3 x 3 FP32 positions
+ *   delta_dev  device, Np^3 FP32
+ */
+scola_status scola_final_density(scola_ctx *ctx, const float *x_dev, float *delta_dev);
+
+/*
+ * FP64 time-stepping table the kernels use (App. B, Eqs. 52-60), computed on
+ * the host without a context or a GPU: growth factors by an adaptive
+ * Dormand-Prince integration of the growth equations (Eqs. 44-45), alpha~ by
+ * Gauss-Legendre quadrature, beta~ in closed form.
+ * For force evaluation k = 0..nsteps (host arrays of nsteps + 1, any may be NULL):
+ *   a_force, D1, D2, beta (coefficient of the kick that uses that force);
+ * for drift k = 0..nsteps-1 (host arrays of nsteps): alpha, dD1, dD2.
+ * Errors: as scola_create's validation.
+ */
+scola_status scola_time_table(const scola_params *params, double *a_force, double *D1, double *D2,
+                              double *beta, double *alpha, double *dD1, double *dD2);
+
+/*
+ * Profiling mode: when enabled, the evolution graph is re-captured with an
+ * external CUDA event recorded between consecutive kernels of every force
+ * evaluation, so that scola_kernel_times can report device time per kernel.
+ * Synchronises the stream.  Costs a few microseconds per force evaluation.
+ */
+scola_status scola_set_profiling(scola_ctx *ctx, int32_t enable);
+
+/*
+ * Average device time per launch [ms] of each kernel class in the last
+ * forward run made in profiling mode (synchronises on it).  ms_per_launch
+ * (host, n >= 8 doubles) receives, in order: pad (ghost layers of Phi),
+ * deposit (with the clearing of the accumulator), DST z forward, DST y
+ * forward, DST x forward + sine-space division + x inverse, DST y inverse,
+ * DST z inverse, interpolate + kick + drift.  Errors: STATE when profiling is off.
+ */
+scola_status scola_kernel_times(const scola_ctx *ctx, double *ms_per_launch, int32_t n);
+
+scola_status scola_get_stats(const scola_ctx *ctx, scola_stats *out);
+const char *scola_status_string(scola_status status);
+const char *scola_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SCOLA_H */

@@ -1,0 +1,18 @@
+"""GB300 (sm_103a) implementation of the perfectly parallel sCOLA method
+(Leclercq et al., arXiv:2003.04925): per-tile particle-mesh COLA evolution of
+independent sCOLA boxes with Dirichlet boundary conditions.
+
+The compute path is the CUDA library ``libscola.so`` (C ABI in
+``include/scola.h``); ``binding`` marshals arguments to it, and ``Scola``
+below adds device-memory management with PyTorch tensors.  Importing the
+package fails loudly if the library has not been built.
+"""
+from .binding import (  # noqa: F401
+    EXPORTED, KERNEL_CLASSES, SCOLA_DST_AUTO, SCOLA_DST_SIMT, ScolaError, ScolaParams, make_params,
+    scola_box_particle_count, scola_box_particle_ids, scola_create, scola_destroy,
+    scola_final_density, scola_forward, scola_forward_host, scola_get_stats, scola_last_error,
+    scola_lpt_fields, scola_mesh_cell_count, scola_padded_cell_count, scola_pm_force,
+    scola_kernel_times, scola_set_profiling, scola_setup_boxes, scola_status_string,
+    scola_tiling_info, scola_time_table,
+)
+from .simulation import Scola  # noqa: F401

@@ -1,0 +1,145 @@
+// Internal declarations shared by the translation units of libscola.
+// Device data layout (all FP32 unless noted; boxes concatenated in box-id order):
+//   particle arena  12 x P   rows s_x s_y s_z | p_x p_y p_z | psi1_x.. | psi2_x..
+//                            (SoA rows, P = sum_b Nsc_b^3, box-local order)
+//   acc             sum_b Ng_b^3 uint64 fixed-point CIC counts (2^-32 units)
+//   work, work2     sum_b Ng_b^3 interior meshes (transform ping-pong)
+//   phi             sum_b (Ng_b+4)^3 padded potential (interior + 2 ghost layers)
+//   shell           sum_b S_b compact Dirichlet shell values, S_b = (Ng+4)^3 - Ng^3
+//   dst tables      per distinct Ng: the sine matrix (transposed, padded rows)
+//                   and the Dirichlet eigenvalues
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "scola.h"
+
+namespace scola {
+
+constexpr int kChunk = 256;       // particles per CTA in particle kernels
+constexpr int kTC = 32;           // transform columns per tile in the DST passes
+constexpr int kXS = kTC + 4;      // shared-memory row stride of a column tile
+constexpr double kFix = 4294967296.0;  // 2^32: fixed-point scale of CIC weights
+
+struct BoxDesc {
+    int Nsc, Ng, Nbuf, tbl;       // tbl: index of the DST table for this Ng
+    int tx, ty, tz, pad0;
+    long long p_off;              // first particle in the arena
+    long long m_off;              // first interior mesh cell
+    long long pp_off;             // first padded mesh cell
+    long long sh_off;             // first compact shell value
+    float dq, dg, inv_dg, q2u;    // q2u = dq / dg
+    float nbar_inv;               // (Ng / Nsc)^3
+    float pad1[3];
+    double dg_d, origin_d[3];     // FP64 geometry for the shell interpolation
+};
+
+struct Chunk {                    // one CTA of a particle- or cell-parallel kernel
+    int box;
+    int start;
+};
+
+struct DstTable {                 // offsets into the device table arena (floats)
+    int Ng;
+    int LS;                       // padded row length of the transposed sine matrix (32 R)
+    long long st_off;             // ST[i * LS + l] = sin(pi (l+1)(i+1) / (Ng+1))
+    long long lam_off;            // lambda[l], l = 0..Ng-1
+};
+
+struct KickDrift {                // FP32 copies of FP64 host coefficients for one force time
+    float kF, k1, k2;             // p += kF F + k1 psi1 + k2 psi2
+    float alpha, d1, d2;          // s += alpha p + d1 psi1 + d2 psi2
+    int drift;                    // 0 on the last force evaluation
+};
+
+struct TimeTable {                // FP64 App. B coefficients
+    std::vector<double> a, a_half, D1, D2, beta, kick_from, kick_to, alpha, dD1, dD2;
+    double D1_i, D2_i, D1_f, D2_f, dD1da_f, dD2da_f, Hconf_f;
+};
+
+// ---- host mathematics (host_math.cpp) ----
+double conformal_hubble(double a, double Om, double OL);
+void growth_factors(double Om, double OL, const std::vector<double> &a, std::vector<double> &D1,
+                    std::vector<double> &D2, std::vector<double> &dD1da, std::vector<double> &dD2da);
+double alpha_tilde(double ai, double af, double aK, double Om, double OL, double nLPT);
+double beta_tilde(double ai, double af, double aD, double Om, double OL, double nLPT);
+TimeTable build_time_table(const scola_params &p);
+double bbks_amplitude(double Om, double h, double ns, double sigma8);
+
+// ---- context ----
+struct Ctx {
+    scola_params prm;
+    std::vector<int32_t> buffers;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int Np = 0, Ntiles = 0, nboxes = 0;
+    long long N3 = 0;
+    double L = 0, dq = 0, r = 0, p = 0, pk_amp = 0;
+    TimeTable tt;
+
+    std::vector<BoxDesc> boxes_h;
+    std::vector<DstTable> tables_h;
+    long long P = 0, M = 0, MP = 0, SH = 0;
+    int max_ng = 0, max_R = 0;
+
+    // device
+    BoxDesc *boxes = nullptr;
+    DstTable *tables = nullptr;
+    float *table_arena = nullptr;
+    Chunk *pchunks = nullptr;  int n_pchunks = 0;     // box particles
+    Chunk *tchunks = nullptr;  int n_tchunks = 0;     // tile particles (scatter)
+    Chunk *shchunks = nullptr; int n_shchunks = 0;    // shell cells
+    Chunk *zitems = nullptr;   int n_zitems = 0;      // z-pencil tiles
+    Chunk *citems = nullptr;   int n_citems = 0;      // (plane, column-tile) items
+    Chunk *mchunks = nullptr;  int n_mchunks = 0;     // interior mesh cells
+    long long sin_half_off = 0, sin_full_off = 0;     // LPT-grid sine tables in table_arena
+    int num_sms = 1, dst_ctas_per_sm = 1;
+    float *part = nullptr;
+    unsigned long long *acc = nullptr;
+    float *work = nullptr, *work2 = nullptr, *phi = nullptr, *shell = nullptr;
+
+    // full-box LPT stage
+    float *g[4] = {nullptr, nullptr, nullptr, nullptr};
+    float *phi1 = nullptr, *phi2 = nullptr, *psi1 = nullptr, *psi2 = nullptr;
+    cufftComplex *ck = nullptr, *cp = nullptr, *ct = nullptr;
+    cufftHandle plan_r2c = 0, plan_c2r = 0;
+    bool have_plans = false;
+    unsigned long long *dens_acc = nullptr;
+
+    cudaGraphExec_t evolve_exec = nullptr;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool lpt_done = false, setup_done = false;
+    scola_stats stats{};
+    long long launches = 0;
+};
+
+// ---- kernel launchers (k_*.cu); all enqueue on ctx.stream ----
+cudaError_t launch_colour(Ctx &c, cufftComplex *ck);
+cudaError_t launch_inv_laplacian(Ctx &c, const cufftComplex *in, cufftComplex *out, float scale);
+cudaError_t launch_second_derivative(Ctx &c, const cufftComplex *in, cufftComplex *out, int i, int j);
+cudaError_t launch_source_init(Ctx &c, const float *xx, const float *yy, const float *zz, float *S);
+cudaError_t launch_source_sub(Ctx &c, const float *t, float *S);
+cudaError_t launch_gradient(Ctx &c, const float *phi, float *psi);
+
+cudaError_t launch_box_init(Ctx &c);
+cudaError_t launch_shell(Ctx &c);
+cudaError_t launch_pad(Ctx &c, float D1);
+cudaError_t launch_deposit(Ctx &c, const float *s, long long stride);
+cudaError_t init_pm_kernels(Ctx &c);
+cudaError_t launch_poisson(Ctx &c);
+cudaError_t launch_poisson_pass(Ctx &c, int pass);
+cudaError_t launch_acc_to_delta(Ctx &c, float *out);
+cudaError_t launch_interp(Ctx &c, const float *s, long long stride, float *F);
+cudaError_t launch_kick_drift(Ctx &c, const KickDrift &kd);
+cudaError_t launch_scatter(Ctx &c, float *x, float *p);
+cudaError_t launch_box_ids(Ctx &c, int64_t *gid);
+cudaError_t launch_final_density(Ctx &c, const float *x, float *delta);
+
+void set_error(const std::string &msg);
+
+}  // namespace scola

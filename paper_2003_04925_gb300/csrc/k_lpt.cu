@@ -1,0 +1,190 @@
+// Full-box initial conditions and 2LPT (Sec. 3.1, steps A.1-A.2; Sec. 2.1, Eqs. 5-6).
+//
+// The Fourier transforms are cuFFT calls issued by the host (capi.cu); the
+// spectral multiplications and the configuration-space operations are here.
+// FDA order 2 throughout, spacing d = L/N:
+//   colouring    delta^(k) = w^(k) sqrt(P(|k|) / d^3) / N^3, delta^(0) = 0
+//   inverse Lap  phi^ = f^ / Lambda(k), Lambda = -(4/d^2) sum sin^2(pi n_i / N)
+//   phi_,ij      = IFFT[-D_i D_j phi1^],  D_i = sin(2 pi n_i / N) / d
+//                  (the central difference applied twice)
+//   source       sum_{i>j} phi_,ii phi_,jj - phi_,ij^2
+//   Psi          central-difference gradient at the grid nodes (periodic)
+// The sine tables sin(pi n/N) and sin(2 pi n/N)/d are FP64 host values stored in FP32.
+#include <cmath>
+
+#include "device_util.cuh"
+
+namespace scola {
+
+namespace {
+
+__device__ __forceinline__ int wavenumber(int i, int N) { return i < N / 2 ? i : i - N; }
+
+__device__ double bbks_T_dev(double k, double Omh) {
+    const double q = k / Omh;
+    const double poly = 1.0 + 3.89 * q + (16.1 * q) * (16.1 * q) + pow(5.46 * q, 3.0) +
+                        pow(6.71 * q, 4.0);
+    return log1p(2.34 * q) / (2.34 * q) * pow(poly, -0.25);
+}
+
+__global__ void k_colour(cufftComplex *ck, int N, double kf, double A, double ns, double Omh,
+                         double inv_d3, double norm) {
+    const int Nz = N / 2 + 1;
+    const long long n = (long long)N * N * Nz;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int kz = (int)(idx % Nz);
+        const long long t = idx / Nz;
+        const int ky = (int)(t % N);
+        const int kx = (int)(t / N);
+        const double nx = wavenumber(kx, N), ny = wavenumber(ky, N), nz = kz;
+        const double k = kf * sqrt(nx * nx + ny * ny + nz * nz);
+        float amp = 0.0f;
+        if (k > 0) {
+            const double T = bbks_T_dev(k, Omh);
+            amp = (float)(sqrt(A * pow(k, ns) * T * T * inv_d3) * norm);
+        }
+        cufftComplex v = ck[idx];
+        v.x *= amp;
+        v.y *= amp;
+        ck[idx] = v;
+    }
+}
+
+__global__ void k_inv_lap(const cufftComplex *in, cufftComplex *out, int N, const float *s_half,
+                          float inv_d2, float scale) {
+    const int Nz = N / 2 + 1;
+    const long long n = (long long)N * N * Nz;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int kz = (int)(idx % Nz);
+        const long long t = idx / Nz;
+        const int ky = (int)(t % N);
+        const int kx = (int)(t / N);
+        const float sx = s_half[kx], sy = s_half[ky], sz = s_half[kz];
+        const float lam = -4.0f * inv_d2 * (sx * sx + sy * sy + sz * sz);
+        cufftComplex v = in[idx];
+        const float m = (lam != 0.0f) ? scale / lam : 0.0f;
+        v.x *= m;
+        v.y *= m;
+        out[idx] = v;
+    }
+}
+
+__global__ void k_second_derivative(const cufftComplex *in, cufftComplex *out, int N,
+                                    const float *s_full, int ai, int aj) {
+    const int Nz = N / 2 + 1;
+    const long long n = (long long)N * N * Nz;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+         idx += (long long)gridDim.x * blockDim.x) {
+        int c[3];
+        c[2] = (int)(idx % Nz);
+        const long long t = idx / Nz;
+        c[1] = (int)(t % N);
+        c[0] = (int)(t / N);
+        const float m = -s_full[c[ai]] * s_full[c[aj]];
+        cufftComplex v = in[idx];
+        v.x *= m;
+        v.y *= m;
+        out[idx] = v;
+    }
+}
+
+__global__ void k_source_init(const float *xx, const float *yy, const float *zz, float *S,
+                              long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float a = xx[i], b = yy[i], c = zz[i];
+        S[i] = a * b + a * c + b * c;
+    }
+}
+
+__global__ void k_source_sub(const float *t, float *S, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float v = t[i];
+        S[i] -= v * v;
+    }
+}
+
+__global__ void k_gradient(const float *phi, float *psi, int N, float inv_2d) {
+    const long long N3 = (long long)N * N * N;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < N3;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(idx % N);
+        const long long t = idx / N;
+        const int j = (int)(t % N);
+        const int i = (int)(t / N);
+        const long long NN = (long long)N * N;
+        const int ip = i + 1 == N ? 0 : i + 1, im = i == 0 ? N - 1 : i - 1;
+        const int jp = j + 1 == N ? 0 : j + 1, jm = j == 0 ? N - 1 : j - 1;
+        const int kp = k + 1 == N ? 0 : k + 1, km = k == 0 ? N - 1 : k - 1;
+        const long long row = (long long)i * NN + (long long)j * N;
+        psi[idx] = (phi[(long long)ip * NN + (long long)j * N + k] -
+                    phi[(long long)im * NN + (long long)j * N + k]) * inv_2d;
+        psi[N3 + idx] = (phi[(long long)i * NN + (long long)jp * N + k] -
+                         phi[(long long)i * NN + (long long)jm * N + k]) * inv_2d;
+        psi[2 * N3 + idx] = (phi[row + kp] - phi[row + km]) * inv_2d;
+    }
+}
+
+int grid_for(long long n, int block) {
+    long long g = (n + block - 1) / block;
+    return (int)(g < 8192 ? (g > 0 ? g : 1) : 8192);
+}
+
+}  // namespace
+
+cudaError_t launch_colour(Ctx &c, cufftComplex *ck) {
+    const int N = c.Np;
+    const long long n = (long long)N * N * (N / 2 + 1);
+    const double d = c.L / N;
+    const double N3 = (double)N * N * N;
+    k_colour<<<grid_for(n, 256), 256, 0, c.stream>>>(ck, N, 2.0 * M_PI / c.L, c.pk_amp,
+                                                      c.prm.ns, c.prm.Om * c.prm.h,
+                                                      1.0 / (d * d * d), 1.0 / N3);
+    ++c.launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_inv_laplacian(Ctx &c, const cufftComplex *in, cufftComplex *out, float scale) {
+    const int N = c.Np;
+    const long long n = (long long)N * N * (N / 2 + 1);
+    const double d = c.L / N;
+    k_inv_lap<<<grid_for(n, 256), 256, 0, c.stream>>>(in, out, N, c.table_arena + c.sin_half_off,
+                                                       (float)(1.0 / (d * d)), scale);
+    ++c.launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_second_derivative(Ctx &c, const cufftComplex *in, cufftComplex *out, int i,
+                                     int j) {
+    const int N = c.Np;
+    const long long n = (long long)N * N * (N / 2 + 1);
+    k_second_derivative<<<grid_for(n, 256), 256, 0, c.stream>>>(
+        in, out, N, c.table_arena + c.sin_full_off, i, j);
+    ++c.launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_source_init(Ctx &c, const float *xx, const float *yy, const float *zz,
+                               float *S) {
+    k_source_init<<<grid_for(c.N3, 256), 256, 0, c.stream>>>(xx, yy, zz, S, c.N3);
+    ++c.launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_source_sub(Ctx &c, const float *t, float *S) {
+    k_source_sub<<<grid_for(c.N3, 256), 256, 0, c.stream>>>(t, S, c.N3);
+    ++c.launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gradient(Ctx &c, const float *phi, float *psi) {
+    const double d = c.L / c.Np;
+    k_gradient<<<grid_for(c.N3, 256), 256, 0, c.stream>>>(phi, psi, c.Np, (float)(0.5 / d));
+    ++c.launches;
+    return cudaGetLastError();
+}
+
+}  // namespace scola

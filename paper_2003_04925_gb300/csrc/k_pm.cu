@@ -1,0 +1,515 @@
+// Per-box particle-mesh step of sCOLA (Sec. 3.4, App. C), all boxes per launch.
+//
+// Mesh convention: cell c of a box has its centre at (c + 1/2) dg in the
+// box-local frame; a particle at x_loc has mesh coordinate u = x_loc/dg - 1/2.
+// The padded potential holds the 2 ghost layers of FDA order 2 (indices -2..Ng+1
+// stored at 0..Ng+3).
+//
+//  deposit       B^sCOLA (Sec. 3.4.1): CIC weights of every box particle onto
+//                the Ng^3 interior; weight that lands outside is discarded.
+//                Accumulated as 2^-32 fixed-point integers, so the result does
+//                not depend on the order of the atomic additions.
+//  pad           ghost layers of the potential <- D1(a_K) * shell (LEP, Eq. 23).
+//  poisson       the zero-boundary solve of App. C on delta' = delta - Lap Phi_BCs
+//                (Eq. 62): dense DST-I along z (with the density conversion and
+//                the boundary source), along y, then along x with the division
+//                by lambda_l + lambda_m + lambda_n (Eq. 71) and the inverse x
+//                transform, then inverse y, then inverse z with the 8/(Ng+1)^3
+//                scale (Eqs. 66-67), written into the padded potential.
+//                Each pass is a pencil matrix product Y = S X with the sine
+//                matrix S_li = sin(pi (l+1)(i+1)/(Ng+1)) held in shared memory.
+//  interp        FDA-2 central gradient at the 8 CIC corners, CIC-weighted
+//                (Sec. 3.4.2); u is clamped to [-1, Ng] with i0 <= Ng - 1.
+//  kick_drift    the sCOLA kick (Eqs. 48, 54) and COLA drift (Eq. 53) fused
+//                with the interpolation.
+#include <algorithm>
+
+#include "device_util.cuh"
+
+namespace scola {
+
+namespace {
+
+// ------------------------------------------------------------------ deposit
+__global__ void __launch_bounds__(kChunk)
+k_deposit(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
+          const float *__restrict__ s, long long stride, unsigned long long *__restrict__ acc) {
+    const Chunk ch = chunks[blockIdx.x];
+    const BoxDesc &B = boxes[ch.box];
+    const int Nsc = B.Nsc, Ng = B.Ng;
+    const int local = ch.start + threadIdx.x;
+    if (local >= Nsc * Nsc * Nsc) return;
+    const long long gi = B.p_off + local;
+    int b[3];
+    decode_local(local, Nsc, b[0], b[1], b[2]);
+    int i0[3];
+    float f[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float u = fmaf(__ldg(s + a * stride + gi), B.inv_dg, fmaf((float)b[a], B.q2u, 0.5f * B.q2u - 0.5f));
+        u = fminf(fmaxf(u, -2.0f), (float)Ng + 1.0f);
+        const float fl = floorf(u);
+        i0[a] = (int)fl;
+        f[a] = u - fl;
+    }
+    unsigned long long *base = acc + B.m_off;
+#pragma unroll
+    for (int dx = 0; dx < 2; ++dx) {
+        const int cx = i0[0] + dx;
+        if ((unsigned)cx >= (unsigned)Ng) continue;
+        const float wx = dx ? f[0] : 1.0f - f[0];
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy) {
+            const int cy = i0[1] + dy;
+            if ((unsigned)cy >= (unsigned)Ng) continue;
+            const float wxy = wx * (dy ? f[1] : 1.0f - f[1]);
+#pragma unroll
+            for (int dz = 0; dz < 2; ++dz) {
+                const int cz = i0[2] + dz;
+                if ((unsigned)cz >= (unsigned)Ng) continue;
+                const float w = wxy * (dz ? f[2] : 1.0f - f[2]);
+                atomicAdd(base + ((long long)cx * Ng + cy) * Ng + cz,
+                          __float2ull_rn(w * 4294967296.0f));
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ pad
+__global__ void __launch_bounds__(kChunk)
+k_pad(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
+      const float *__restrict__ shell, float *__restrict__ phi, float D1) {
+    const Chunk ch = chunks[blockIdx.x];
+    const BoxDesc &B = boxes[ch.box];
+    const long long idx = (long long)ch.start + threadIdx.x;
+    if (idx >= shell_count(B.Ng)) return;
+    int pi, pj, pk;
+    shell_coord(idx, B.Ng, pi, pj, pk);
+    const long long S = B.Ng + 4;
+    phi[B.pp_off + ((long long)pi * S + pj) * S + pk] = D1 * shell[B.sh_off + idx];
+}
+
+// ------------------------------------------------------------------ DST passes
+enum Pass { kZFwd = 0, kYFwd = 1, kXSolve = 2, kYInv = 3, kZInv = 4 };
+
+// acc[r][j] = sum_i ST[i][tl + 32 r] X[i][c0 + j]   (Y = S X on a column tile)
+template <int R>
+__device__ __forceinline__ void tile_product(const float *__restrict__ ST, int LS,
+                                             const float *__restrict__ X, int Ng, int tl, int c0,
+                                             float (&acc)[R][4]) {
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[r][j] = 0.0f;
+#pragma unroll 4
+    for (int i = 0; i < Ng; ++i) {
+        const float4 xv = *reinterpret_cast<const float4 *>(X + i * kXS + c0);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float sv = ST[i * LS + tl + 32 * r];
+            acc[r][0] = fmaf(sv, xv.x, acc[r][0]);
+            acc[r][1] = fmaf(sv, xv.y, acc[r][1]);
+            acc[r][2] = fmaf(sv, xv.z, acc[r][2]);
+            acc[r][3] = fmaf(sv, xv.w, acc[r][3]);
+        }
+    }
+}
+
+template <int R, int PASS>
+__global__ void __launch_bounds__(256)
+k_dst(const BoxDesc *__restrict__ boxes, const DstTable *__restrict__ tables,
+      const float *__restrict__ tab, const Chunk *__restrict__ items, int nitems,
+      const void *__restrict__ in_v, float *__restrict__ out, const float *__restrict__ phi_pad,
+      int ngmax) {
+    // shared layout, sized for the largest Ng of the launch:
+    //   ST[ngmax][32 R] | X[ngmax][kXS] | lambda[ngmax]
+    extern __shared__ __align__(16) float smem[];
+    const int LS = 32 * R;
+    const int tid = threadIdx.x;
+    const int tl = tid >> 3, c0 = (tid & 7) * 4;
+    int cur_tbl = -1, Ng = 0;
+    float *ST = smem;
+    float *X = smem + (long long)ngmax * LS;
+    float *lam = X + ngmax * kXS;
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const Chunk item = items[it];
+        const BoxDesc &B = boxes[item.box];
+        if (B.tbl != cur_tbl) {
+            __syncthreads();
+            const DstTable T = tables[B.tbl];
+            Ng = T.Ng;
+            for (int q = tid; q < Ng * LS; q += blockDim.x) ST[q] = tab[T.st_off + q];
+            for (int q = tid; q < Ng; q += blockDim.x) lam[q] = tab[T.lam_off + q];
+            cur_tbl = B.tbl;
+            __syncthreads();
+        }
+        const long long Ng2 = (long long)Ng * Ng;
+        // ---- load the column tile X[t][c]
+        int ncols;
+        long long zp0 = 0;     // first pencil (z passes)
+        int plane = 0, k0 = 0; // (plane, column offset) for y/x passes
+        if (PASS == kZFwd || PASS == kZInv) {
+            zp0 = (long long)item.start * kTC;
+            ncols = (int)min((long long)kTC, Ng2 - zp0);
+            for (int q = tid; q < Ng * kTC; q += blockDim.x) {
+                const int t = q % Ng, c = q / Ng;
+                float v = 0.0f;
+                if (c < ncols) {
+                    const long long p = zp0 + c;
+                    if (PASS == kZFwd) {
+                        const unsigned long long *acc =
+                            reinterpret_cast<const unsigned long long *>(in_v);
+                        const long long cell = B.m_off + p * Ng + t;
+                        v = (float)acc[cell] * (B.nbar_inv * 2.3283064365386963e-10f) - 1.0f;
+                        const int i = (int)(p / Ng), j = (int)(p % Ng), k = t;
+                        if (i == 0 || j == 0 || k == 0 || i == Ng - 1 || j == Ng - 1 || k == Ng - 1) {
+                            const long long S = Ng + 4;
+                            const float *P = phi_pad + B.pp_off;
+                            const long long ctr = ((long long)(i + 2) * S + (j + 2)) * S + (k + 2);
+                            float bc = 0.0f;
+                            if (i == 0) bc += P[ctr - S * S];
+                            if (i == Ng - 1) bc += P[ctr + S * S];
+                            if (j == 0) bc += P[ctr - S];
+                            if (j == Ng - 1) bc += P[ctr + S];
+                            if (k == 0) bc += P[ctr - 1];
+                            if (k == Ng - 1) bc += P[ctr + 1];
+                            v -= bc * (B.inv_dg * B.inv_dg);
+                        }
+                    } else {
+                        const float *in = reinterpret_cast<const float *>(in_v);
+                        v = in[B.m_off + p * Ng + t];
+                    }
+                }
+                X[t * kXS + c] = v;
+            }
+        } else {
+            const int nct = (Ng + kTC - 1) / kTC;
+            plane = item.start / nct;
+            k0 = (item.start % nct) * kTC;
+            ncols = min(kTC, Ng - k0);
+            const float *in = reinterpret_cast<const float *>(in_v);
+            // y passes: element (t = j, k) of plane i; x pass: element (t = i, k) of plane j
+            const long long base = B.m_off + (PASS == kXSolve ? (long long)plane * Ng : (long long)plane * Ng2) + k0;
+            const long long tstride = (PASS == kXSolve) ? Ng2 : Ng;
+            for (int q = tid; q < Ng * kTC; q += blockDim.x) {
+                const int c = q % kTC, t = q / kTC;
+                X[t * kXS + c] = (c < ncols) ? in[base + t * tstride + c] : 0.0f;
+            }
+        }
+        __syncthreads();
+
+        float acc[R][4];
+        tile_product<R>(ST, LS, X, Ng, tl, c0, acc);
+
+        if (PASS == kXSolve) {
+            // divide by the sum of eigenvalues (Eq. 71), then inverse x transform
+            __syncthreads();
+            const float lm = lam[plane];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int l = tl + 32 * r;
+                if (l < Ng) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int c = c0 + j;
+                        const float ln = (c < ncols) ? lam[k0 + c] : -1.0f;
+                        X[l * kXS + c] = acc[r][j] / (lam[l] + lm + ln);
+                    }
+                }
+            }
+            __syncthreads();
+            tile_product<R>(ST, LS, X, Ng, tl, c0, acc);
+        }
+
+        // ---- store
+        if (PASS == kYFwd || PASS == kYInv || PASS == kXSolve) {
+            const long long base = B.m_off + (PASS == kXSolve ? (long long)plane * Ng : (long long)plane * Ng2) + k0;
+            const long long tstride = (PASS == kXSolve) ? Ng2 : Ng;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int l = tl + 32 * r;
+                if (l < Ng) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (c0 + j < ncols) out[base + l * tstride + c0 + j] = acc[r][j];
+                }
+            }
+        } else {
+            // z passes: transpose through shared memory so that pencils are written contiguously
+            __syncthreads();
+            const float scale = (PASS == kZInv) ? 8.0f / ((float)(Ng + 1) * (Ng + 1) * (Ng + 1)) : 1.0f;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int l = tl + 32 * r;
+                if (l < Ng) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) X[l * kXS + c0 + j] = acc[r][j] * scale;
+                }
+            }
+            __syncthreads();
+            for (int q = tid; q < Ng * kTC; q += blockDim.x) {
+                const int t = q % Ng, c = q / Ng;
+                if (c < ncols) {
+                    const long long p = zp0 + c;
+                    if (PASS == kZFwd) {
+                        out[B.m_off + p * Ng + t] = X[t * kXS + c];
+                    } else {
+                        const long long S = Ng + 4;
+                        const int i = (int)(p / Ng), j = (int)(p % Ng);
+                        out[B.pp_off + ((long long)(i + 2) * S + (j + 2)) * S + 2 + t] = X[t * kXS + c];
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ interpolation
+__device__ __forceinline__ void interpolate_force(const BoxDesc &B, const float *__restrict__ phi,
+                                                  const int b[3], const float s[3], float F[3]) {
+    const int Ng = B.Ng;
+    int i0[3];
+    float w[3][2];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float u = fmaf(s[a], B.inv_dg, fmaf((float)b[a], B.q2u, 0.5f * B.q2u - 0.5f));
+        u = fminf(fmaxf(u, -1.0f), (float)Ng);
+        int fl = (int)floorf(u);
+        fl = min(fl, Ng - 1);
+        i0[a] = fl;
+        const float f = u - (float)fl;
+        w[a][0] = 1.0f - f;
+        w[a][1] = f;
+    }
+    const long long S1 = Ng + 4, S2 = S1 * S1;
+    const float *P = phi + B.pp_off + ((long long)(i0[0] + 2) * S1 + (i0[1] + 2)) * S1 + (i0[2] + 2);
+    float core[2][2][2], xm[2][2], xp[2][2], ym[2][2], yp[2][2], zm[2][2], zp[2][2];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+            for (int c = 0; c < 2; ++c) core[a][bb][c] = __ldg(P + a * S2 + bb * S1 + c);
+#pragma unroll
+    for (int p = 0; p < 2; ++p)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            xm[p][q] = __ldg(P - S2 + p * S1 + q);
+            xp[p][q] = __ldg(P + 2 * S2 + p * S1 + q);
+            ym[p][q] = __ldg(P + p * S2 - S1 + q);
+            yp[p][q] = __ldg(P + p * S2 + 2 * S1 + q);
+            zm[p][q] = __ldg(P + p * S2 + q * S1 - 1);
+            zp[p][q] = __ldg(P + p * S2 + q * S1 + 2);
+        }
+    float fx = 0.0f, fy = 0.0f, fz = 0.0f;
+#pragma unroll
+    for (int p = 0; p < 2; ++p)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            // x gradient at corners (0|1, p, q)
+            fx += w[1][p] * w[2][q] *
+                  (w[0][0] * (core[1][p][q] - xm[p][q]) + w[0][1] * (xp[p][q] - core[0][p][q]));
+            // y gradient at corners (p, 0|1, q)
+            fy += w[0][p] * w[2][q] *
+                  (w[1][0] * (core[p][1][q] - ym[p][q]) + w[1][1] * (yp[p][q] - core[p][0][q]));
+            // z gradient at corners (p, q, 0|1)
+            fz += w[0][p] * w[1][q] *
+                  (w[2][0] * (core[p][q][1] - zm[p][q]) + w[2][1] * (zp[p][q] - core[p][q][0]));
+        }
+    const float h = 0.5f * B.inv_dg;
+    F[0] = fx * h;
+    F[1] = fy * h;
+    F[2] = fz * h;
+}
+
+__global__ void __launch_bounds__(kChunk)
+k_interp(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
+         const float *__restrict__ s, long long stride, const float *__restrict__ phi,
+         float *__restrict__ F) {
+    const Chunk ch = chunks[blockIdx.x];
+    const BoxDesc &B = boxes[ch.box];
+    const int Nsc = B.Nsc;
+    const int local = ch.start + threadIdx.x;
+    if (local >= Nsc * Nsc * Nsc) return;
+    const long long gi = B.p_off + local;
+    int b[3];
+    decode_local(local, Nsc, b[0], b[1], b[2]);
+    float sv[3] = {s[gi], s[stride + gi], s[2 * stride + gi]};
+    float f[3];
+    interpolate_force(B, phi, b, sv, f);
+    F[gi] = f[0];
+    F[stride + gi] = f[1];
+    F[2 * stride + gi] = f[2];
+}
+
+__global__ void __launch_bounds__(kChunk)
+k_kick_drift(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
+             float *__restrict__ part, long long P, const float *__restrict__ phi, KickDrift kd) {
+    const Chunk ch = chunks[blockIdx.x];
+    const BoxDesc &B = boxes[ch.box];
+    const int Nsc = B.Nsc;
+    const int local = ch.start + threadIdx.x;
+    if (local >= Nsc * Nsc * Nsc) return;
+    const long long gi = B.p_off + local;
+    int b[3];
+    decode_local(local, Nsc, b[0], b[1], b[2]);
+    float s[3], p[3], p1[3], p2[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        s[a] = part[a * P + gi];
+        p[a] = part[(3 + a) * P + gi];
+        p1[a] = __ldg(part + (6 + a) * P + gi);
+        p2[a] = __ldg(part + (9 + a) * P + gi);
+    }
+    float F[3];
+    interpolate_force(B, phi, b, s, F);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        p[a] = fmaf(kd.kF, F[a], fmaf(kd.k1, p1[a], fmaf(kd.k2, p2[a], p[a])));
+        part[(3 + a) * P + gi] = p[a];
+        if (kd.drift) {
+            s[a] = fmaf(kd.alpha, p[a], fmaf(kd.d1, p1[a], fmaf(kd.d2, p2[a], s[a])));
+            part[a * P + gi] = s[a];
+        }
+    }
+}
+
+__global__ void k_acc_to_delta(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
+                               const unsigned long long *__restrict__ acc, float *__restrict__ out) {
+    const Chunk ch = chunks[blockIdx.x];
+    const BoxDesc &B = boxes[ch.box];
+    const long long n = (long long)B.Ng * B.Ng * B.Ng;
+    const long long idx = (long long)ch.start + threadIdx.x;
+    if (idx >= n) return;
+    out[B.m_off + idx] = (float)acc[B.m_off + idx] * (B.nbar_inv * 2.3283064365386963e-10f) - 1.0f;
+}
+
+size_t dst_smem_bytes(int R, int ngmax) {
+    return ((size_t)ngmax * 32 * R + (size_t)ngmax * kXS + ngmax) * sizeof(float);
+}
+
+template <int R, int PASS>
+cudaError_t run_pass(Ctx &c, const Chunk *items, int nitems, const void *in, float *out) {
+    const size_t smem = dst_smem_bytes(R, c.max_ng);
+    int grid = std::min(nitems, c.num_sms * c.dst_ctas_per_sm);
+    if (grid < 1) grid = 1;
+    k_dst<R, PASS><<<grid, 256, smem, c.stream>>>(c.boxes, c.tables, c.table_arena, items, nitems, in,
+                                                   out, c.phi, c.max_ng);
+    ++c.launches;
+    return cudaGetLastError();
+}
+
+template <int R>
+cudaError_t set_attrs_R() {
+    const int lim = 227 * 1024;
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_dst<R, kZFwd>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+    if ((e = cudaFuncSetAttribute(k_dst<R, kYFwd>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+    if ((e = cudaFuncSetAttribute(k_dst<R, kXSolve>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+    if ((e = cudaFuncSetAttribute(k_dst<R, kYInv>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+    return cudaFuncSetAttribute(k_dst<R, kZInv>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+}
+
+template <int R>
+int ctas_per_sm_R(int ngmax) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_dst<R, kYFwd>, 256, dst_smem_bytes(R, ngmax)) !=
+        cudaSuccess)
+        return 1;
+    return n > 0 ? n : 1;
+}
+
+template <int R>
+cudaError_t poisson_R(Ctx &c) {
+    cudaError_t e;
+    if ((e = run_pass<R, kZFwd>(c, c.zitems, c.n_zitems, c.acc, c.work)) != cudaSuccess) return e;
+    if ((e = run_pass<R, kYFwd>(c, c.citems, c.n_citems, c.work, c.work2)) != cudaSuccess) return e;
+    if ((e = run_pass<R, kXSolve>(c, c.citems, c.n_citems, c.work2, c.work)) != cudaSuccess) return e;
+    if ((e = run_pass<R, kYInv>(c, c.citems, c.n_citems, c.work, c.work2)) != cudaSuccess) return e;
+    return run_pass<R, kZInv>(c, c.zitems, c.n_zitems, c.work2, c.phi);
+}
+
+}  // namespace
+
+cudaError_t launch_deposit(Ctx &c, const float *s, long long stride) {
+    cudaError_t e = cudaMemsetAsync(c.acc, 0, sizeof(unsigned long long) * c.M, c.stream);
+    if (e != cudaSuccess) return e;
+    k_deposit<<<c.n_pchunks, kChunk, 0, c.stream>>>(c.boxes, c.pchunks, s, stride, c.acc);
+    ++c.launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pad(Ctx &c, float D1) {
+    k_pad<<<c.n_shchunks, kChunk, 0, c.stream>>>(c.boxes, c.shchunks, c.shell, c.phi, D1);
+    ++c.launches;
+    return cudaGetLastError();
+}
+
+cudaError_t init_pm_kernels(Ctx &c) {
+    cudaError_t e;
+    switch (c.max_R) {
+        case 1: e = set_attrs_R<1>(); c.dst_ctas_per_sm = ctas_per_sm_R<1>(c.max_ng); break;
+        case 2: e = set_attrs_R<2>(); c.dst_ctas_per_sm = ctas_per_sm_R<2>(c.max_ng); break;
+        case 3: e = set_attrs_R<3>(); c.dst_ctas_per_sm = ctas_per_sm_R<3>(c.max_ng); break;
+        case 4: e = set_attrs_R<4>(); c.dst_ctas_per_sm = ctas_per_sm_R<4>(c.max_ng); break;
+        case 5: e = set_attrs_R<5>(); c.dst_ctas_per_sm = ctas_per_sm_R<5>(c.max_ng); break;
+        case 6: e = set_attrs_R<6>(); c.dst_ctas_per_sm = ctas_per_sm_R<6>(c.max_ng); break;
+        default: return cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return e;
+    if (dst_smem_bytes(c.max_R, c.max_ng) > 227 * 1024) return cudaErrorInvalidValue;
+    return cudaSuccess;
+}
+
+cudaError_t launch_poisson(Ctx &c) {
+    switch (c.max_R) {
+        case 1: return poisson_R<1>(c);
+        case 2: return poisson_R<2>(c);
+        case 3: return poisson_R<3>(c);
+        case 4: return poisson_R<4>(c);
+        case 5: return poisson_R<5>(c);
+        case 6: return poisson_R<6>(c);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_poisson_pass(Ctx &c, int pass) {
+    // the five passes of launch_poisson, one at a time (for per-kernel timing)
+    switch (c.max_R * 8 + pass) {
+#define SCOLA_PASS_CASES(R)                                                                     \
+    case R * 8 + 0: return run_pass<R, kZFwd>(c, c.zitems, c.n_zitems, c.acc, c.work);          \
+    case R * 8 + 1: return run_pass<R, kYFwd>(c, c.citems, c.n_citems, c.work, c.work2);        \
+    case R * 8 + 2: return run_pass<R, kXSolve>(c, c.citems, c.n_citems, c.work2, c.work);      \
+    case R * 8 + 3: return run_pass<R, kYInv>(c, c.citems, c.n_citems, c.work, c.work2);        \
+    case R * 8 + 4: return run_pass<R, kZInv>(c, c.zitems, c.n_zitems, c.work2, c.phi);
+        SCOLA_PASS_CASES(1)
+        SCOLA_PASS_CASES(2)
+        SCOLA_PASS_CASES(3)
+        SCOLA_PASS_CASES(4)
+        SCOLA_PASS_CASES(5)
+        SCOLA_PASS_CASES(6)
+#undef SCOLA_PASS_CASES
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_interp(Ctx &c, const float *s, long long stride, float *F) {
+    k_interp<<<c.n_pchunks, kChunk, 0, c.stream>>>(c.boxes, c.pchunks, s, stride, c.phi, F);
+    ++c.launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_kick_drift(Ctx &c, const KickDrift &kd) {
+    k_kick_drift<<<c.n_pchunks, kChunk, 0, c.stream>>>(c.boxes, c.pchunks, c.part, c.P, c.phi, kd);
+    ++c.launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_acc_to_delta(Ctx &c, float *out) {
+    k_acc_to_delta<<<c.n_mchunks, kChunk, 0, c.stream>>>(c.boxes, c.mchunks, c.acc, out);
+    ++c.launches;
+    return cudaGetLastError();
+}
+
+}  // namespace scola

@@ -1,0 +1,82 @@
+"""Torch-facing wrapper around one libscola context.
+
+PyTorch provides device memory and the stream; every computation happens in
+libscola's kernels.  Tensors are FP32 CUDA tensors in the layouts documented
+in include/scola.h.
+"""
+import torch
+
+from . import binding as B
+
+
+class Scola:
+    """One sCOLA problem on one GPU (the current CUDA device)."""
+
+    def __init__(self, params=None, stream=None, **kw):
+        if not torch.cuda.is_available():
+            raise RuntimeError("libscola needs a CUDA device")
+        self.params = params if params is not None else B.make_params(**kw)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.ctx = B.scola_create(self.params, self.stream.cuda_stream)
+        self.P = B.scola_box_particle_count(self.ctx)
+        self.M = B.scola_mesh_cell_count(self.ctx)
+        self.MP = B.scola_padded_cell_count(self.ctx)
+        self.Np = self.params.Np
+
+    def close(self):
+        if self.ctx:
+            B.scola_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _empty(self, *shape, dtype=torch.float32):
+        return torch.empty(*shape, dtype=dtype, device="cuda")
+
+    def forward(self, w, x=None, p=None):
+        """Full run from white noise w (Np^3 FP32 CUDA tensor) -> (x, p), each (Np^3, 3)."""
+        n = self.Np ** 3
+        x = self._empty(n, 3) if x is None else x
+        p = self._empty(n, 3) if p is None else p
+        B.scola_forward(self.ctx, w.contiguous(), x, p)
+        return x, p
+
+    def forward_host(self, w_host, x_host, p_host):
+        B.scola_forward_host(self.ctx, w_host, x_host, p_host)
+
+    def lpt_fields(self, w):
+        N = self.Np
+        out = {k: self._empty(N, N, N) for k in ("delta", "phi1", "phi2")}
+        out.update({k: self._empty(3, N, N, N) for k in ("psi1", "psi2")})
+        B.scola_lpt_fields(self.ctx, w.contiguous(), out["delta"], out["phi1"], out["phi2"],
+                           out["psi1"], out["psi2"])
+        return out
+
+    def setup_boxes(self):
+        B.scola_setup_boxes(self.ctx)
+
+    def pm_force(self, s, D1, want_delta=False, want_phi=False):
+        """grad Phi at box particles from displacements s (3, P)."""
+        F = self._empty(3, self.P)
+        delta = self._empty(self.M) if want_delta else None
+        phi = self._empty(self.MP) if want_phi else None
+        B.scola_pm_force(self.ctx, s.contiguous(), D1, F, delta, phi)
+        return F, delta, phi
+
+    def box_particle_ids(self):
+        gid = self._empty(self.P, dtype=torch.int64)
+        B.scola_box_particle_ids(self.ctx, gid)
+        return gid
+
+    def final_density(self, x):
+        N = self.Np
+        d = self._empty(N, N, N)
+        B.scola_final_density(self.ctx, x.contiguous(), d)
+        return d
+
+    def stats(self):
+        return B.scola_get_stats(self.ctx)

@@ -1,0 +1,83 @@
+"""The C ABI library loads without a GPU and exports every symbol include/scola.h declares;
+its host-side FP64 arithmetic agrees with the oracle (no kernel is launched here)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2003_04925_gb300 as sc
+    return sc
+
+
+def _declared_functions():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names += re.findall(r"\b(scola_\w+)\s*\(", txt)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    so = ctypes.CDLL(os.path.join(ROOT, "paper_2003_04925_gb300", "libscola.so"))
+    declared = _declared_functions()
+    assert len(declared) >= 15
+    for name in declared:
+        assert hasattr(so, name), name
+    assert set(declared) <= set(lib.EXPORTED) | {n for n in declared if hasattr(so, n)}
+    missing_in_binding = set(declared) - set(lib.EXPORTED)
+    assert not missing_in_binding, missing_in_binding
+
+
+def test_validation_errors_without_gpu(lib):
+    bad = lib.make_params(L=100.0, Np=30, Ntiles=4, Nbuf=2)          # Np % Ntiles != 0
+    with pytest.raises(lib.ScolaError) as e:
+        lib.scola_tiling_info(bad)
+    assert e.value.status == 1
+    bad = lib.make_params(L=100.0, Np=32, Ntiles=2, Nbuf=4, Ng=20)    # Ng < Np,sCOLA
+    with pytest.raises(lib.ScolaError):
+        lib.scola_tiling_info(bad)
+    bad = lib.make_params(L=100.0, Np=32, Ntiles=2, Nbuf=4, fda_order=4)
+    with pytest.raises(lib.ScolaError) as e:
+        lib.scola_tiling_info(bad)
+    assert e.value.status == 2
+    bad = lib.make_params(L=100.0, Np=32, Ntiles=2, Nbuf=10)          # box larger than the lattice
+    with pytest.raises(lib.ScolaError):
+        lib.scola_tiling_info(bad)
+
+
+def test_tiling_info_matches_oracle_and_table1(lib):
+    from oracle import tiling
+    for (Np, Nt, Nb) in [(512, 4, 32), (1024, 8, 30), (128, 4, 8)]:
+        nsc, ng, r, p = lib.scola_tiling_info(lib.make_params(L=100.0, Np=Np, Ntiles=Nt, Nbuf=Nb,
+                                                              Ng=Np // Nt + 2 * Nb + 1))
+        r0, p0 = tiling.oversimulation(Np, Nt, Nb)
+        assert nsc == [Np // Nt + 2 * Nb] * Nt**3 and ng == [Np // Nt + 2 * Nb + 1] * Nt**3
+        assert abs(r - r0) < 1e-12 * r0 and abs(p - p0) < 1e-12 * p0
+    bufs = [4, 8, 16, 4, 8, 16, 4, 8]
+    nsc, ng, r, p = lib.scola_tiling_info(lib.make_params(L=500.0, Np=64, Ntiles=2, buffers=bufs))
+    assert nsc == [32 + 2 * b for b in bufs] and ng == nsc
+    assert abs(r - tiling.oversimulation(64, 2, bufs)[0]) < 1e-12
+
+
+@pytest.mark.parametrize("Om,OL,nsteps", [(0.3, 0.7, 20), (1.0, 0.0, 10), (0.25, 0.6, 7)])
+def test_time_table_matches_oracle(lib, Om, OL, nsteps):
+    # Two independent FP64 routes (Dormand-Prince + Gauss-Legendre here, RK4 + adaptive
+    # Simpson in the oracle) to the App. B coefficients must agree to ~1e-10.
+    from oracle import cosmology
+    prm = lib.make_params(L=100.0, Np=32, Ntiles=2, Nbuf=4, nsteps=nsteps, Om=Om, OL=OL)
+    t = lib.scola_time_table(prm)
+    o = cosmology.kdk_schedule(0.02, 1.0, nsteps, Om, OL)
+    for k_lib, k_or in [("a_force", "a"), ("D1", "D1"), ("D2", "D2"), ("beta", "beta"),
+                        ("alpha", "alpha"), ("dD1", "dD1"), ("dD2", "dD2")]:
+        np.testing.assert_allclose(t[k_lib], o[k_or], rtol=1e-9, atol=1e-13, err_msg=k_lib)

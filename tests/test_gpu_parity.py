@@ -1,0 +1,220 @@
+"""GPU parity: every stage of the CUDA path against the FP64 oracle on the same seeded inputs.
+
+Tolerances (FP32 path vs FP64 oracle; the derivation is in the design notes):
+  * integer work (tile assignment, particle ids): bit-exact;
+  * full-box fields (FP32 FFTs of size N^3): max error <= 2e-5 of the field's max;
+  * one PM force evaluation (FP32 dense DST-I of length Ng, then a central
+    difference): max error <= 2e-4 and RMS error <= 2e-5 of max |F|;
+  * the whole run (acceptance tolerance of the method's FP32 form): final-position
+    RMS <= 1e-3 PM cell, P(k) within 1e-3 relative for k <= k_Nyq / 2.
+"""
+import numpy as np
+import pytest
+import torch
+
+import synth_inputs
+from gpu_common import (box_initial_displacements, lib_kwargs, oracle_cfg, oracle_fields,
+                        oracle_shell, periodic_diff, workload_cfg)
+from oracle import pm, scola as oscola, stats, tiling
+
+pytestmark = pytest.mark.gpu
+
+
+class _Lazy:
+    """The package is imported on first use so that CPU-only collection never loads it."""
+
+    def __getattr__(self, name):
+        import paper_2003_04925_gb300 as pkg
+        return getattr(pkg, name)
+
+
+sc = _Lazy()
+
+SMALL = workload_cfg("plain_32")
+CASES_PM = {
+    "plain_32": SMALL,                                           # Ng = 24 (ragged tiles), 1:1
+    "ratio2": dict(SMALL, mesh_ratio=2, nsteps=4),               # Ng = 48, 2:1
+    "table1_like": dict(SMALL, Ng=25, nsteps=4),                 # Ng = Np,sCOLA + 1, 1:1 + 1
+    "uneven": dict(L=200.0, Np=64, Ntiles=2, buffers=[4, 8, 16, 4, 8, 4, 16, 8], mesh_ratio=1,
+                   nsteps=4, a_i=0.02, a_f=1.0),                 # Ng = 40, 48, 64 in one launch
+    "single_box": dict(L=80.0, Np=16, Ntiles=1, Nbuf=0, mesh_ratio=2, nsteps=3, a_i=0.02, a_f=1.0),
+}
+
+
+def _sim(kw):
+    return sc.Scola(**lib_kwargs(kw))
+
+
+def _to_dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+@pytest.mark.parametrize("name", ["plain_32", "single_box"])
+def test_lpt_fields_match_oracle(name):
+    kw = CASES_PM[name]
+    w, f, _ = oracle_fields(kw)
+    sim = _sim(kw)
+    out = sim.lpt_fields(_to_dev(w))
+    torch.cuda.synchronize()
+    for key, ref in [("delta", f.delta), ("phi1", f.phi1), ("phi2", f.phi2), ("psi1", f.psi1),
+                     ("psi2", f.psi2)]:
+        got = out[key].cpu().numpy().astype(np.float64)
+        err = np.abs(got - ref).max() / np.abs(ref).max()
+        assert err < 2e-5, (key, err)
+    sim.close()
+
+
+@pytest.mark.parametrize("name", list(CASES_PM))
+def test_box_particle_ids_are_bit_exact(name):
+    kw = CASES_PM[name]
+    cfg = oracle_cfg(kw)
+    sim = _sim(kw)
+    gid = sim.box_particle_ids().cpu().numpy()
+    ref = np.concatenate([tiling.box_global_ids(cfg.Np, cfg.Ntiles, oscola.box_geometry(cfg, b).t,
+                                                cfg.buffer_of(b)) for b in range(cfg.nboxes)])
+    assert gid.dtype == np.int64 and np.array_equal(gid, ref)
+    sim.close()
+
+
+@pytest.mark.parametrize("name", list(CASES_PM))
+def test_pm_force_matches_oracle(name):
+    # One force evaluation (deposit, Dirichlet DST-I solve, gradient, interpolation) on
+    # displacements 20x the initial 2LPT ones, so that particles leave their boxes
+    # (mass drop in the deposit, clamping in the interpolation).
+    kw = CASES_PM[name]
+    cfg = oracle_cfg(kw)
+    w, f, sched = oracle_fields(kw)
+    sim = _sim(kw)
+    sim.lpt_fields(_to_dev(w))
+    sim.setup_boxes()
+    D1 = 0.73
+    s_all, refs = [], []
+    for b in range(cfg.nboxes):
+        g, ids, s0 = box_initial_displacements(cfg, f, sched, b)
+        s = 20.0 * s0
+        s_all.append(s)
+        qloc = (tiling.box_local_lattice(g.Nsc) + 0.5) * (cfg.L / cfg.Np)
+        refs.append((g, pm.box_force(qloc + s, g.dg, g.Ng, g.Nsc, D1 * oracle_shell(cfg, f, g))))
+    s_cat = np.concatenate(s_all).T.copy()
+    F, delta, phi = sim.pm_force(_to_dev(s_cat), D1, want_delta=True, want_phi=True)
+    torch.cuda.synchronize()
+    F = F.cpu().numpy().astype(np.float64)
+    delta = delta.cpu().numpy().astype(np.float64)
+    phi = phi.cpu().numpy().astype(np.float64)
+    p_off = m_off = pp_off = 0
+    for g, r in refs:
+        n, ng3, np3 = g.Nsc**3, g.Ng**3, (g.Ng + 4) ** 3
+        Fb = F[:, p_off:p_off + n].T
+        scale = np.abs(r["F"]).max()
+        err = np.abs(Fb - r["F"])
+        assert err.max() <= 2e-4 * scale, (g.b, err.max() / scale)
+        assert np.sqrt(np.mean(err**2)) <= 2e-5 * scale
+        np.testing.assert_allclose(delta[m_off:m_off + ng3].reshape((g.Ng,) * 3), r["delta"],
+                                   atol=2e-6 * max(1.0, np.abs(r["delta"]).max()))
+        phib = phi[pp_off:pp_off + np3].reshape((g.Ng + 4,) * 3)
+        assert np.abs(phib - r["phi"]).max() <= 2e-5 * np.abs(r["phi"]).max()
+        p_off, m_off, pp_off = p_off + n, m_off + ng3, pp_off + np3
+    sim.close()
+
+
+def _forward(kw, w):
+    sim = _sim(kw)
+    x, p = sim.forward(_to_dev(w))
+    torch.cuda.synchronize()
+    out = x.cpu().numpy().astype(np.float64), p.cpu().numpy().astype(np.float64), sim
+    return out
+
+
+def _pk_rel_err(delta_a, delta_b, L, N):
+    kny = np.pi * N / L
+    edges = np.linspace(2 * np.pi / L * 0.999, kny / 2, 12)
+    _, pa, _ = stats.power_spectrum(delta_a, L, edges)
+    _, pb, _ = stats.power_spectrum(delta_b, L, edges)
+    ok = np.isfinite(pa) & np.isfinite(pb)
+    return np.abs(pa[ok] / pb[ok] - 1).max()
+
+
+@pytest.mark.parametrize("name", ["plain_32", "uneven", "table1_like"])
+def test_forward_matches_oracle(name):
+    kw = CASES_PM[name]
+    cfg = oracle_cfg(kw)
+    w = synth_inputs.white_noise(cfg.Np, 1)
+    x, p, sim = _forward(kw, w)
+    ref = oscola.run_scola(w, cfg)
+    dg = min(oscola.box_geometry(cfg, b).dg for b in range(cfg.nboxes))
+    dx = periodic_diff(x, ref["x"], cfg.L)
+    rms = np.sqrt(np.mean(np.sum(dx**2, axis=1))) / dg
+    assert rms <= 1e-3, rms
+    prel = np.sqrt(np.mean(np.sum((p - ref["p"]) ** 2, 1)) / np.mean(np.sum(ref["p"] ** 2, 1)))
+    assert prel <= 1e-3, prel
+    # final density (Sec. 4.1) and its power spectrum
+    dens = sim.final_density(torch.from_numpy(x.astype(np.float32)).cuda())
+    torch.cuda.synchronize()
+    dens = dens.cpu().numpy().astype(np.float64)
+    dens_same_x = stats.cic_density_periodic(x.astype(np.float32).astype(np.float64), cfg.L, cfg.Np, cfg.Np)
+    assert np.abs(dens - dens_same_x).max() < 1e-5 * max(1, np.abs(dens_same_x).max())
+    dens_ref = stats.cic_density_periodic(ref["x"], cfg.L, cfg.Np, cfg.Np)
+    assert _pk_rel_err(dens, dens_ref, cfg.L, cfg.Np) <= 1e-3
+    sim.close()
+
+
+def test_forward_is_deterministic_and_host_variant_agrees():
+    kw = CASES_PM["plain_32"]
+    w = synth_inputs.white_noise(32, 3)
+    sim = _sim(kw)
+    wd = _to_dev(w)
+    x1, p1 = sim.forward(wd)
+    x1, p1 = x1.clone(), p1.clone()
+    x2, p2 = sim.forward(wd)
+    torch.cuda.synchronize()
+    assert torch.equal(x1, x2) and torch.equal(p1, p2)
+    xh = torch.empty(32**3, 3).pin_memory()
+    ph = torch.empty(32**3, 3).pin_memory()
+    sim.forward_host(torch.from_numpy(w).pin_memory(), xh, ph)
+    assert torch.equal(xh, x1.cpu()) and torch.equal(ph, p1.cpu())
+    st = sim.stats()
+    assert st["kernel_launches"] > 100 and st["force_evaluations"] == kw["nsteps"] + 1
+    sim.close()
+
+
+def test_zero_amplitude_keeps_the_lattice():
+    kw = CASES_PM["plain_32"]
+    x, p, sim = _forward(kw, np.zeros((32,) * 3, np.float32))
+    q = oscola.lattice_positions(32, kw["L"])
+    assert np.abs(periodic_diff(x, q, kw["L"])).max() < 1e-5
+    assert np.abs(p).max() == 0.0
+    sim.close()
+
+
+def test_state_and_argument_errors():
+    kw = CASES_PM["plain_32"]
+    sim = _sim(kw)
+    s = torch.zeros(3, sim.P, device="cuda")
+    with pytest.raises(sc.ScolaError) as e:
+        sim.pm_force(s, 1.0)
+    assert e.value.status == 5
+    sim.close()
+    with pytest.raises(sc.ScolaError) as e:
+        sc.Scola(**dict(kw, Np=30))
+    assert e.value.status == 1
+
+
+@pytest.mark.slow
+def test_batched_128_sampled_boxes_match_oracle():
+    # Full-size batched workload in the benchmark's launch configuration; the oracle
+    # evolves two sampled boxes (boxes are independent, so each is exact on its own).
+    kw = workload_cfg("batched_128")
+    cfg = oracle_cfg(kw)
+    w = synth_inputs.white_noise(cfg.Np, 1)
+    x, p, sim = _forward(kw, w)
+    sim.close()
+    fields = oscola.initial_fields(w, cfg)
+    sched = oscola.schedule(cfg)
+    for b in (0, 37):
+        r = oscola.evolve_box(cfg, b, fields, sched)
+        keep = tiling.tile_interior_mask(cfg.Np, cfg.Ntiles, cfg.Nbuf)
+        ids = r["ids"][keep]
+        xr = np.mod(oscola.lattice_positions(cfg.Np, cfg.L)[ids] + r["s"][keep], cfg.L)
+        dx = periodic_diff(x[ids], xr, cfg.L)
+        rms = np.sqrt(np.mean(np.sum(dx**2, 1))) / r["geometry"].dg
+        assert rms <= 1e-3, (b, rms)
