@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--impl", default="scola", choices=["scola", "reference"])
     ap.add_argument("--workload", default="batched_128")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--forward-only", action="store_true",
+                    help="only W + K forward runs of the batched form (for ncu launch lists)")
     return ap.parse_args()
 
 
@@ -271,6 +273,16 @@ def run_gpu(args, rank, world, local_rank):
     for _ in range(args.warmup):
         sim.forward(w, x, p)
     torch.cuda.synchronize()
+    if args.forward_only:
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            sim.forward(w, x, p)
+        torch.cuda.synchronize()
+        if rank == 0:
+            print(json.dumps({"forward_only": True, "workload": args.workload, "steps": args.steps,
+                              "ms_per_step": 1e3 * (time.perf_counter() - t0) / max(1, args.steps)}))
+        sim.close()
+        return
 
     def barrier():
         if dist is not None:
@@ -315,6 +327,24 @@ def run_gpu(args, rank, world, local_rank):
     e2e = {"value": world * work / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 4 * n,
            "d2h_bytes_per_step": 2 * 12 * n}
 
+    # the plain per-tile form (one box per launch, boxes in turn) on the same input
+    pt = sc.Scola(**dict(kw, batch_mode=sc.SCOLA_BATCH_PER_TILE))
+    xp, pp = torch.empty_like(x), torch.empty_like(p)
+    pt.forward(w, xp, pp)
+    torch.cuda.synchronize()
+    same = bool(torch.equal(xp, x) and torch.equal(pp, p))
+    k_pt = max(1, args.steps // 2)
+    e0.record(stream)
+    for _ in range(k_pt):
+        pt.forward(w, xp, pp)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_pt = e0.elapsed_time(e1) / k_pt
+    pt.close()
+    per_tile = {"value": world * work / (ms_pt * 1e-3), "ms_per_step": ms_pt, "steps": k_pt,
+                "bit_identical_to_batched": same,
+                "speedup_batched_over_per_tile": ms_pt / ms}
+
     # per-kernel device time from events recorded between the kernels of the graph
     sc.scola_set_profiling(sim.ctx, True)
     for _ in range(2):
@@ -355,7 +385,8 @@ def run_gpu(args, rank, world, local_rank):
                     "l2": "working set %.2f GB > 129 MB L2, no flush" % (ws_bytes / 1e9),
                     "parallelism": "replicas x%d" % world, "batching": "all boxes per launch, CUDA graph",
                     "dst": "dense sine-matrix pencils, FP32 CUDA cores"}),
-                "e2e": e2e, "gpu_launches": int(launches * args.steps), "clocks": clk,
+                "e2e": e2e, "per_tile": per_tile, "gpu_launches": int(launches * args.steps),
+                "clocks": clk,
                 "roofline": roofline, "cpu_baseline": cpu,
                 "stats": {k: v for k, v in sim.stats().items() if k in ("ms_lpt", "ms_evolve", "r", "p")}}
         print(json.dumps(line), flush=True)

@@ -54,6 +54,11 @@ typedef enum scola_dst_variant {
     SCOLA_DST_AUTO = 2           /* the fastest built variant */
 } scola_dst_variant;
 
+typedef enum scola_batch_mode {
+    SCOLA_BATCH_ALL = 0,         /* every box in each launch (batched form) */
+    SCOLA_BATCH_PER_TILE = 1     /* one box per launch, boxes in turn (plain per-tile form) */
+} scola_batch_mode;
+
 /*
  * Problem statement.  Field names follow the paper's nomenclature (Sec. 3,
  * nomenclature table):
@@ -75,6 +80,7 @@ typedef enum scola_dst_variant {
  *                (App. B, Eq. 60); the paper uses -2.5
  *   fda_order    finite-difference order; only 2 is built
  *   dst_variant  one of scola_dst_variant
+ *   batch_mode   one of scola_batch_mode (same results, different launch shapes)
  */
 typedef struct scola_params {
     double L;
@@ -86,6 +92,8 @@ typedef struct scola_params {
     int32_t fda_order;
     int32_t dst_variant;
     int32_t nsteps;
+    int32_t batch_mode;
+    int32_t reserved;            /* must be 0 */
     double Om, OL, h, ns, sigma8;
     double a_i, a_f;
     double nLPT;

@@ -17,6 +17,8 @@ c_double, c_int32, c_int64, c_void_p, c_char_p = (ctypes.c_double, ctypes.c_int3
 SCOLA_OK = 0
 SCOLA_DST_SIMT = 0
 SCOLA_DST_AUTO = 2
+SCOLA_BATCH_ALL = 0
+SCOLA_BATCH_PER_TILE = 1
 
 
 class ScolaError(RuntimeError):
@@ -29,7 +31,8 @@ class ScolaParams(ctypes.Structure):
     _fields_ = [
         ("L", c_double), ("Np", c_int32), ("Ntiles", c_int32), ("Nbuf", c_int32),
         ("mesh_ratio", c_int32), ("Ng", c_int32), ("fda_order", c_int32),
-        ("dst_variant", c_int32), ("nsteps", c_int32),
+        ("dst_variant", c_int32), ("nsteps", c_int32), ("batch_mode", c_int32),
+        ("reserved", c_int32),
         ("Om", c_double), ("OL", c_double), ("h", c_double), ("ns", c_double),
         ("sigma8", c_double), ("a_i", c_double), ("a_f", c_double), ("nLPT", c_double),
         ("buffers", ctypes.POINTER(c_int32)),
@@ -102,10 +105,11 @@ def _ptr(x):
 
 def make_params(L, Np, Ntiles, Nbuf=0, mesh_ratio=1, Ng=0, nsteps=10, Om=0.3, OL=0.7, h=0.7,
                 ns=0.96, sigma8=0.8, a_i=0.02, a_f=1.0, nLPT=-2.5, fda_order=2,
-                dst_variant=SCOLA_DST_AUTO, buffers=None):
+                dst_variant=SCOLA_DST_AUTO, batch_mode=SCOLA_BATCH_ALL, buffers=None):
     """Build a ScolaParams; ``buffers`` (per-tile widths) is kept alive on the struct."""
     p = ScolaParams(L=L, Np=Np, Ntiles=Ntiles, Nbuf=Nbuf, mesh_ratio=mesh_ratio, Ng=Ng,
-                    fda_order=fda_order, dst_variant=dst_variant, nsteps=nsteps, Om=Om, OL=OL,
+                    fda_order=fda_order, dst_variant=dst_variant, nsteps=nsteps,
+                    batch_mode=batch_mode, reserved=0, Om=Om, OL=OL,
                     h=h, ns=ns, sigma8=sigma8, a_i=a_i, a_f=a_f, nLPT=nLPT)
     if buffers is not None:
         arr = (c_int32 * len(buffers))(*[int(b) for b in buffers])

@@ -85,6 +85,8 @@ scola_status validate(const scola_params *p, std::vector<int32_t> &bufs, std::ve
     }
     if (p->dst_variant != SCOLA_DST_SIMT && p->dst_variant != SCOLA_DST_AUTO)
         return invalid("unknown dst_variant");
+    if (p->batch_mode != SCOLA_BATCH_ALL && p->batch_mode != SCOLA_BATCH_PER_TILE)
+        return invalid("unknown batch_mode");
     if (p->nsteps < 1) return invalid("nsteps must be >= 1");
     if (!(p->a_i > 0 && p->a_f > p->a_i)) return invalid("need 0 < a_i < a_f");
     if (!(p->Om > 0)) return invalid("Om must be positive");
@@ -191,6 +193,10 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &geo) {
     long long P = 0, M = 0, MP = 0, SH = 0;
     std::map<int, double> dg_of_ng;
     for (int b = 0; b < c->nboxes; ++b) {
+        c->pbeg.push_back((int)pch.size());
+        c->shbeg.push_back((int)shch.size());
+        c->zbeg.push_back((int)zit.size());
+        c->cbeg.push_back((int)cit.size());
         const BoxGeom &g = geo[b];
         BoxDesc B;
         std::memset(&B, 0, sizeof(B));
@@ -241,6 +247,10 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &geo) {
             return SCOLA_ERR_UNSUPPORTED;
         }
     }
+    c->pbeg.push_back((int)pch.size());
+    c->shbeg.push_back((int)shch.size());
+    c->zbeg.push_back((int)zit.size());
+    c->cbeg.push_back((int)cit.size());
     for (auto &T : c->tables_h) {
         const double dg = dg_of_ng[T.Ng];
         for (int l = 0; l < T.Ng; ++l) {
@@ -250,6 +260,8 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &geo) {
     }
     c->P = P;
     c->M = M;
+    c->acc_clear_off = 0;
+    c->acc_clear_len = M;
     c->MP = MP;
     c->SH = SH;
     if (pch.size() > 0x7fffffff || zit.size() > 0x7fffffff || cit.size() > 0x7fffffff)
@@ -363,9 +375,58 @@ KickDrift kick_drift_coefficients(const TimeTable &t, int k) {
     return kd;
 }
 
-// C.1-C.3 and the whole KDK sequence on the context stream.  In profiling mode an
-// external event is recorded between consecutive kernels of every force evaluation.
+// Restricts every work list (and the accumulator clear) to one box; restores on destruction.
+struct BoxView {
+    scola_ctx *c;
+    Chunk *pch, *sh, *z, *cl;
+    int npch, nsh, nz, ncl;
+    long long off, len;
+    BoxView(scola_ctx *cc, int b) : c(cc) {
+        pch = c->pchunks; sh = c->shchunks; z = c->zitems; cl = c->citems;
+        npch = c->n_pchunks; nsh = c->n_shchunks; nz = c->n_zitems; ncl = c->n_citems;
+        off = c->acc_clear_off; len = c->acc_clear_len;
+        c->pchunks = pch + c->pbeg[b];
+        c->n_pchunks = c->pbeg[b + 1] - c->pbeg[b];
+        c->shchunks = sh + c->shbeg[b];
+        c->n_shchunks = c->shbeg[b + 1] - c->shbeg[b];
+        c->zitems = z + c->zbeg[b];
+        c->n_zitems = c->zbeg[b + 1] - c->zbeg[b];
+        c->citems = cl + c->cbeg[b];
+        c->n_citems = c->cbeg[b + 1] - c->cbeg[b];
+        const BoxDesc &B = c->boxes_h[b];
+        c->acc_clear_off = B.m_off;
+        c->acc_clear_len = (long long)B.Ng * B.Ng * B.Ng;
+    }
+    ~BoxView() {
+        c->pchunks = pch; c->shchunks = sh; c->zitems = z; c->citems = cl;
+        c->n_pchunks = npch; c->n_shchunks = nsh; c->n_zitems = nz; c->n_citems = ncl;
+        c->acc_clear_off = off; c->acc_clear_len = len;
+    }
+};
+
+// The plain per-tile form: every box evolved on its own, one box per launch, boxes in turn
+// (the paper's one-process-per-box organisation mapped onto one GPU).
+scola_status enqueue_evolution_per_tile(scola_ctx *c) {
+    const int n = (int)c->tt.alpha.size();
+    for (int b = 0; b < c->nboxes; ++b) {
+        BoxView v(c, b);
+        CK(launch_box_init(*c));
+        CK(launch_shell(*c));
+        for (int k = 0; k <= n; ++k) {
+            CK(launch_pad(*c, (float)c->tt.D1[k]));
+            CK(launch_deposit(*c, c->part, c->P));
+            CK(launch_poisson(*c));
+            CK(launch_kick_drift(*c, kick_drift_coefficients(c->tt, k)));
+        }
+    }
+    return SCOLA_OK;
+}
+
+// C.1-C.3 and the whole KDK sequence on the context stream, all boxes per launch.  In
+// profiling mode an external event is recorded between consecutive kernels of every
+// force evaluation.
 scola_status enqueue_evolution(scola_ctx *c) {
+    if (c->prm.batch_mode == SCOLA_BATCH_PER_TILE) return enqueue_evolution_per_tile(c);
     CK(launch_box_init(*c));
     CK(launch_shell(*c));
     const int n = (int)c->tt.alpha.size();
@@ -624,6 +685,11 @@ scola_status scola_set_profiling(scola_ctx *c, int enable) {
         c->evolve_exec = nullptr;
     }
     c->profiling = on;
+    if (on && c->prm.batch_mode == SCOLA_BATCH_PER_TILE) {
+        c->profiling = false;
+        set_error("profiling mode times the batched form only");
+        return SCOLA_ERR_UNSUPPORTED;
+    }
     if (on && c->prof_ev.empty()) {
         const size_t n = (size_t)(c->prm.nsteps + 1) * (KC_COUNT + 1);
         c->prof_ev.resize(n, nullptr);

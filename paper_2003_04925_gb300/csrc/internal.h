@@ -98,6 +98,9 @@ struct Ctx {
     Chunk *citems = nullptr;   int n_citems = 0;      // (plane, column-tile) items
     Chunk *mchunks = nullptr;  int n_mchunks = 0;     // interior mesh cells
     long long sin_half_off = 0, sin_full_off = 0;     // LPT-grid sine tables in table_arena
+    long long acc_clear_off = 0, acc_clear_len = 0;   // accumulator range the deposit clears
+    // first entry of each box in every work list (size nboxes + 1), for per-tile launches
+    std::vector<int> pbeg, shbeg, zbeg, cbeg;
     int num_sms = 1, dst_ctas_per_sm = 1;
     float *part = nullptr;
     unsigned long long *acc = nullptr;

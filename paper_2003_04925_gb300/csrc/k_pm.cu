@@ -433,7 +433,8 @@ cudaError_t poisson_R(Ctx &c) {
 }  // namespace
 
 cudaError_t launch_deposit(Ctx &c, const float *s, long long stride) {
-    cudaError_t e = cudaMemsetAsync(c.acc, 0, sizeof(unsigned long long) * c.M, c.stream);
+    cudaError_t e = cudaMemsetAsync(c.acc + c.acc_clear_off, 0,
+                                    sizeof(unsigned long long) * c.acc_clear_len, c.stream);
     if (e != cudaSuccess) return e;
     k_deposit<<<c.n_pchunks, kChunk, 0, c.stream>>>(c.boxes, c.pchunks, s, stride, c.acc);
     ++c.launches;

@@ -177,6 +177,22 @@ def test_forward_is_deterministic_and_host_variant_agrees():
     sim.close()
 
 
+@pytest.mark.parametrize("name", ["plain_32", "uneven"])
+def test_per_tile_form_matches_batched_form(name):
+    # One box per launch (the plain per-tile form) gives bit-identical results: every kernel
+    # computes each box independently and the deposit is order-independent.
+    kw = CASES_PM[name]
+    w = _to_dev(synth_inputs.white_noise(kw["Np"], 4))
+    a = _sim(kw)
+    b = _sim(dict(kw, batch_mode=sc.SCOLA_BATCH_PER_TILE))
+    xa, pa = a.forward(w)
+    xb, pb = b.forward(w)
+    torch.cuda.synchronize()
+    assert torch.equal(xa, xb) and torch.equal(pa, pb)
+    a.close()
+    b.close()
+
+
 def test_zero_amplitude_keeps_the_lattice():
     kw = CASES_PM["plain_32"]
     x, p, sim = _forward(kw, np.zeros((32,) * 3, np.float32))
@@ -195,7 +211,10 @@ def test_state_and_argument_errors():
     assert e.value.status == 5
     sim.close()
     with pytest.raises(sc.ScolaError) as e:
-        sc.Scola(**dict(kw, Np=30))
+        sc.Scola(**dict(kw, Np=31))            # Np not a multiple of Ntiles (Sec. 3.2)
+    assert e.value.status == 1
+    with pytest.raises(sc.ScolaError) as e:
+        sc.Scola(**dict(kw, Nbuf=9))           # Np,sCOLA = 34 > Np
     assert e.value.status == 1
 
 
