@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--impl", default="scola", choices=["scola", "reference"])
     ap.add_argument("--workload", default="batched_128")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--dst", default="tc", choices=["tc", "simt"],
+                    help="Poisson-solve form: tensor-core 3xTF32 (tc) or FP32 CUDA cores (simt)")
     ap.add_argument("--forward-only", action="store_true",
                     help="only W + K forward runs of the batched form (for ncu launch lists)")
     return ap.parse_args()
@@ -60,6 +62,7 @@ def workload_kwargs(name):
 
 
 def box_sizes(kw):
+    kw = {k: v for k, v in kw.items() if k != "dst_variant"}
     ntile = kw["Np"] // kw["Ntiles"]
     bufs = kw.get("buffers") or [kw["Nbuf"]] * kw["Ntiles"] ** 3
     nsc = [ntile + 2 * b for b in bufs]
@@ -215,21 +218,37 @@ def run_reference(args, rank, world):
 
 
 # ----------------------------------------------------------------------------- roofline
-def kernel_roofline(kt, kw, clocks, peaks):
-    """Algorithmic bytes or flops per launch of each kernel class and the dominant one."""
+def kernel_roofline(kt, kw, clocks, peaks, tc):
+    """Algorithmic bytes or flops per launch of each kernel class and the dominant one.
+
+    FP32 form: the five DST passes are dense products on CUDA cores (ALU bound,
+    2 Ng flops per cell per transform; pass 3 does two transforms).  Tensor-core
+    form: six passes, each streaming its mesh once (HBM bound: 4 B read + 4 B
+    written per cell, pass 1 reads the 8-byte fixed-point density).
+    """
     nsc, ng = box_sizes(kw)
     P = sum(n**3 for n in nsc)
     M = sum(g**3 for g in ng)
     MP = sum((g + 4) ** 3 for g in ng)
     SH = MP - M
     dense = sum(2.0 * g * g**3 for g in ng)          # flops of one dense DST-I along one axis
-    work = {
-        "pad": ("hbm", 8.0 * SH),
-        "deposit": ("hbm", 12.0 * P + 4.0 * M),
-        "dst_z_fwd": ("alu", dense), "dst_y_fwd": ("alu", dense), "dst_x_solve": ("alu", 2 * dense),
-        "dst_y_inv": ("alu", dense), "dst_z_inv": ("alu", dense),
-        "kick_drift": ("hbm", 72.0 * P + 4.0 * MP),
-    }
+    work = {"pad": ("hbm", 8.0 * SH), "deposit": ("hbm", 12.0 * P + 4.0 * M),
+            "kick_drift": ("hbm", 72.0 * P + 4.0 * MP)}
+    if tc:
+        names = ["dst_1_z_fwd", "dst_2_y_fwd", "dst_3_x_fwd_div", "dst_4_z_inv", "dst_5_y_inv",
+                 "dst_6_x_inv"]
+        for i, nm in enumerate(names):
+            work[nm] = ("hbm", (12.0 if i == 0 else 8.0) * M)
+    else:
+        names = ["dst_1_z_fwd", "dst_2_y_fwd", "dst_3_x_solve", "dst_4_y_inv", "dst_5_z_inv", None]
+        for i, nm in enumerate(names):
+            if nm:
+                work[nm] = ("alu", (2 if i == 2 else 1) * dense)
+    kt = dict(kt)
+    for i in range(6):
+        v = kt.pop("dst_%d" % (i + 1))
+        if names[i]:
+            kt[names[i]] = v
     sm_mhz = (clocks or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     alu_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12     # FP32 FMA TFLOP/s
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
@@ -263,6 +282,7 @@ def run_gpu(args, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     kw, W = workload_kwargs(args.workload)
+    kw["dst_variant"] = sc.SCOLA_DST_TC_3XTF32 if args.dst == "tc" else sc.SCOLA_DST_SIMT
     sim = sc.Scola(**kw)
     stream = torch.cuda.current_stream()
     w_np = synth_inputs.white_noise(kw["Np"], W["seed"] + rank)
@@ -358,7 +378,8 @@ def run_gpu(args, rank, world, local_rank):
     except (OSError, ValueError):
         peaks = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}
         peak_src = "fallback"
-    dom, rows = kernel_roofline(kt, kw, clk, peaks)
+    dom, rows = kernel_roofline(kt, kw, clk, peaks, args.dst == "tc")
+    sc.scola_device_status(sim.ctx)
     d = rows[dom]
     roofline = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"],
                 "unit": d["unit"], "frac": d["frac"], "traffic": None,
@@ -384,7 +405,8 @@ def run_gpu(args, rank, world, local_rank):
                     "particle_steps_per_step": work,
                     "l2": "working set %.2f GB > 129 MB L2, no flush" % (ws_bytes / 1e9),
                     "parallelism": "replicas x%d" % world, "batching": "all boxes per launch, CUDA graph",
-                    "dst": "dense sine-matrix pencils, FP32 CUDA cores"}),
+                    "dst": ("dense sine-matrix pencils on tcgen05 tensor cores, 3xTF32"
+                            if args.dst == "tc" else "dense sine-matrix pencils, FP32 CUDA cores")}),
                 "e2e": e2e, "per_tile": per_tile, "gpu_launches": int(launches * args.steps),
                 "clocks": clk,
                 "roofline": roofline, "cpu_baseline": cpu,

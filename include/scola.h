@@ -46,11 +46,13 @@ typedef enum scola_status {
     SCOLA_ERR_UNSUPPORTED = 2,   /* valid in the paper, not built here (e.g. FDA order 4/6) */
     SCOLA_ERR_OOM = 3,           /* a device allocation failed */
     SCOLA_ERR_CUDA = 4,          /* a CUDA or cuFFT call failed; see scola_last_error() */
-    SCOLA_ERR_STATE = 5          /* call made in the wrong order (e.g. force before setup) */
+    SCOLA_ERR_STATE = 5,         /* call made in the wrong order (e.g. force before setup) */
+    SCOLA_ERR_TIMEOUT = 6        /* a kernel's bounded wait expired (see scola_device_status) */
 } scola_status;
 
 typedef enum scola_dst_variant {
     SCOLA_DST_SIMT = 0,          /* dense sine-matrix pencils on FP32 CUDA cores */
+    SCOLA_DST_TC_3XTF32 = 1,     /* the same products on tcgen05 tensor cores, 3xTF32 split */
     SCOLA_DST_AUTO = 2           /* the fastest built variant */
 } scola_dst_variant;
 
@@ -242,12 +244,25 @@ scola_status scola_set_profiling(scola_ctx *ctx, int32_t enable);
 /*
  * Average device time per launch [ms] of each kernel class in the last
  * forward run made in profiling mode (synchronises on it).  ms_per_launch
- * (host, n >= 8 doubles) receives, in order: pad (ghost layers of Phi),
- * deposit (with the clearing of the accumulator), DST z forward, DST y
- * forward, DST x forward + sine-space division + x inverse, DST y inverse,
- * DST z inverse, interpolate + kick + drift.  Errors: STATE when profiling is off.
+ * (host, n >= 9 doubles) receives, in order: pad (ghost layers of Phi),
+ * deposit (with the clearing of the accumulator), the Poisson passes 1..6,
+ * interpolate + kick + drift.  FP32 form: pass 1 z forward, 2 y forward,
+ * 3 x forward + sine-space division + x inverse, 4 y inverse, 5 z inverse,
+ * 6 empty.  Tensor-core form: 1 z forward, 2 y forward, 3 x forward +
+ * division, 4 z inverse, 5 y inverse, 6 x inverse.
+ * Errors: STATE when profiling is off.
  */
 scola_status scola_kernel_times(const scola_ctx *ctx, double *ms_per_launch, int32_t n);
+
+/*
+ * Synchronises the stream and reports whether a kernel gave up on a bounded
+ * wait since the context was created: SCOLA_OK, or SCOLA_ERR_TIMEOUT (results
+ * of the affected launch are invalid; the context stays usable).
+ */
+scola_status scola_device_status(scola_ctx *ctx);
+
+/* 1 when the context's Poisson solve runs on the tensor cores, else 0. */
+int32_t scola_uses_tensor_cores(const scola_ctx *ctx);
 
 scola_status scola_get_stats(const scola_ctx *ctx, scola_stats *out);
 const char *scola_status_string(scola_status status);

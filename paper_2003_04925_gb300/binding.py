@@ -16,6 +16,7 @@ c_double, c_int32, c_int64, c_void_p, c_char_p = (ctypes.c_double, ctypes.c_int3
 
 SCOLA_OK = 0
 SCOLA_DST_SIMT = 0
+SCOLA_DST_TC_3XTF32 = 1
 SCOLA_DST_AUTO = 2
 SCOLA_BATCH_ALL = 0
 SCOLA_BATCH_PER_TILE = 1
@@ -70,6 +71,8 @@ _sig = {
     "scola_get_stats": (c_int32, [c_void_p, _P(ScolaStats)]),
     "scola_set_profiling": (c_int32, [c_void_p, c_int32]),
     "scola_kernel_times": (c_int32, [c_void_p, _P(c_double), c_int32]),
+    "scola_device_status": (c_int32, [c_void_p]),
+    "scola_uses_tensor_cores": (c_int32, [c_void_p]),
     "scola_status_string": (c_char_p, [c_int32]),
     "scola_last_error": (c_char_p, []),
 }
@@ -202,8 +205,8 @@ def scola_get_stats(ctx):
     return {name: getattr(st, name) for name, _ in ScolaStats._fields_}
 
 
-KERNEL_CLASSES = ("pad", "deposit", "dst_z_fwd", "dst_y_fwd", "dst_x_solve", "dst_y_inv",
-                  "dst_z_inv", "kick_drift")
+KERNEL_CLASSES = ("pad", "deposit", "dst_1", "dst_2", "dst_3", "dst_4", "dst_5", "dst_6",
+                  "kick_drift")
 
 
 def scola_set_profiling(ctx, enable):
@@ -215,6 +218,14 @@ def scola_kernel_times(ctx):
     arr = (c_double * len(KERNEL_CLASSES))()
     _check(_lib.scola_kernel_times(ctx, arr, len(KERNEL_CLASSES)), "scola_kernel_times")
     return dict(zip(KERNEL_CLASSES, list(arr)))
+
+
+def scola_device_status(ctx):
+    _check(_lib.scola_device_status(ctx), "scola_device_status")
+
+
+def scola_uses_tensor_cores(ctx):
+    return bool(_lib.scola_uses_tensor_cores(ctx))
 
 
 def scola_status_string(status):

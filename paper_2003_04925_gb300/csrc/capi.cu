@@ -21,8 +21,8 @@ using namespace scola;
 
 // Kernel classes timed in profiling mode (scola_set_profiling / scola_kernel_times).
 enum KernelClass {
-    KC_PAD = 0, KC_DEPOSIT, KC_DST_ZFWD, KC_DST_YFWD, KC_DST_XSOLVE, KC_DST_YINV, KC_DST_ZINV,
-    KC_KICK_DRIFT, KC_COUNT
+    KC_PAD = 0, KC_DEPOSIT, KC_DST1, KC_DST2, KC_DST3, KC_DST4, KC_DST5, KC_DST6, KC_KICK_DRIFT,
+    KC_COUNT
 };
 
 struct scola_ctx : public Ctx {
@@ -60,6 +60,7 @@ struct scola_ctx : public Ctx {
 
 namespace {
 
+constexpr bool kAutoUsesTensorCores = false;   // AUTO picks the FP32 form until the TC form is validated
 constexpr int kMaxNg = 192;  // the DST passes hold a (Ng x 32 ceil(Ng/32)) sine matrix in shared memory
 
 struct BoxGeom {
@@ -83,7 +84,8 @@ scola_status validate(const scola_params *p, std::vector<int32_t> &bufs, std::ve
         set_error("only FDA order 2 is built");
         return SCOLA_ERR_UNSUPPORTED;
     }
-    if (p->dst_variant != SCOLA_DST_SIMT && p->dst_variant != SCOLA_DST_AUTO)
+    if (p->dst_variant != SCOLA_DST_SIMT && p->dst_variant != SCOLA_DST_TC_3XTF32 &&
+        p->dst_variant != SCOLA_DST_AUTO)
         return invalid("unknown dst_variant");
     if (p->batch_mode != SCOLA_BATCH_ALL && p->batch_mode != SCOLA_BATCH_PER_TILE)
         return invalid("unknown batch_mode");
@@ -110,6 +112,10 @@ scola_status validate(const scola_params *p, std::vector<int32_t> &bufs, std::ve
         if (ng < nsc) return invalid("Ng must be >= Np,sCOLA (Sec. 3.3, C.3)");
         if (for_kernels && ng > kMaxNg) {
             set_error("Ng > 192 is not built");
+            return SCOLA_ERR_UNSUPPORTED;
+        }
+        if (for_kernels && p->dst_variant == SCOLA_DST_TC_3XTF32 && !tc_supported(ng)) {
+            set_error("the tensor-core DST needs Ng % 4 == 0 and Ng <= 128");
             return SCOLA_ERR_UNSUPPORTED;
         }
         geo[b] = {nsc, ng, bufs[b]};
@@ -233,10 +239,11 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &geo) {
         for (long long t = 0; t < nz; ++t) zit.push_back({b, (int)t});
         const long long nc = (long long)g.ng * ((g.ng + kTC - 1) / kTC);
         for (long long t = 0; t < nc; ++t) cit.push_back({b, (int)t});
+        auto align64 = [](long long v) { return (v + 63) / 64 * 64; };
         P += n;
-        M += ng3;
-        MP += np3;
-        SH += np3 - ng3;
+        M = align64(M + ng3);
+        MP = align64(MP + np3);
+        SH = align64(SH + np3 - ng3);
         // boxes sharing an Ng share dg only if their Np,sCOLA also matches; the
         // eigenvalue table is per Ng, so require a single dg per Ng
         auto it = dg_of_ng.find(g.ng);
@@ -277,6 +284,37 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &geo) {
     c->r = r / (double)c->N3;
     c->p = c->nboxes / c->r;
 
+    // tensor-core DST groups (one per distinct Ng): tiles and the FP32 sine matrix
+    bool all_tc = true;
+    for (auto &kv : tbl_of) all_tc = all_tc && tc_supported(kv.first);
+    c->use_tc = (p.dst_variant == SCOLA_DST_TC_3XTF32) || (p.dst_variant == SCOLA_DST_AUTO && all_tc &&
+                                                           kAutoUsesTensorCores);
+    std::vector<Chunk> tct;
+    if (c->use_tc) {
+        for (auto &kv : tbl_of) {
+            TcGroup G;
+            G.Ng = kv.first;
+            G.nstage = tc_plan_stages(G.Ng, G.Npad, G.nkc);
+            G.lam_off = c->tables_h[kv.second].lam_off;
+            G.s_off = (long long)arena.size();
+            const int Kp = 32 * G.nkc;
+            for (int n = 0; n < G.Npad; ++n)
+                for (int k = 0; k < Kp; ++k)
+                    arena.push_back(n < G.Ng && k < G.Ng
+                                        ? (float)std::sin(M_PI * (double)(n + 1) * (k + 1) / (G.Ng + 1))
+                                        : 0.0f);
+            const long long first = (long long)tct.size();
+            for (int b = 0; b < c->nboxes; ++b) {
+                if (geo[b].ng != G.Ng) continue;
+                const long long rows = (long long)G.Ng * G.Ng;
+                for (long long t = 0; t * 128 < rows; ++t) tct.push_back({b, (int)t});
+            }
+            G.ntiles = (int)(tct.size() - first);
+            G.tiles = reinterpret_cast<Chunk *>(first);   // offset, rebased after upload
+            c->tc_groups.push_back(G);
+        }
+    }
+
     CK(cudaGetDevice(&c->device));
     CK(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
     CS(upload(&c->boxes, c->boxes_h));
@@ -288,6 +326,13 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &geo) {
     CS(upload(&c->zitems, zit));
     CS(upload(&c->citems, cit));
     CS(upload(&c->mchunks, mch));
+    if (c->use_tc) {
+        CS(upload(&c->tc_tiles, tct));
+        for (auto &G : c->tc_groups) G.tiles = c->tc_tiles + reinterpret_cast<long long>(G.tiles);
+        CK(init_tc_kernels());
+    }
+    CS(dev_alloc(&c->dev_err, 1));
+    CK(cudaMemset(c->dev_err, 0, sizeof(int)));
     CS(dev_alloc(&c->part, 12 * P));
     CS(dev_alloc(&c->acc, M));
     CS(dev_alloc(&c->work, M));
@@ -442,16 +487,10 @@ scola_status enqueue_evolution(scola_ctx *c) {
         CK(launch_deposit(*c, c->part, c->P));
         CK(mark());
         if (c->profiling) {
-            CK(launch_poisson_pass(*c, 0));
-            CK(mark());
-            CK(launch_poisson_pass(*c, 1));
-            CK(mark());
-            CK(launch_poisson_pass(*c, 2));
-            CK(mark());
-            CK(launch_poisson_pass(*c, 3));
-            CK(mark());
-            CK(launch_poisson_pass(*c, 4));
-            CK(mark());
+            for (int pass = 0; pass < 6; ++pass) {
+                CK(launch_poisson_pass(*c, pass));
+                CK(mark());
+            }
         } else {
             CK(launch_poisson(*c));
         }
@@ -505,6 +544,7 @@ const char *scola_status_string(scola_status s) {
         case SCOLA_ERR_OOM: return "out of device memory";
         case SCOLA_ERR_CUDA: return "CUDA error";
         case SCOLA_ERR_STATE: return "call out of order";
+        case SCOLA_ERR_TIMEOUT: return "device wait timed out";
     }
     return "unknown status";
 }
@@ -579,7 +619,7 @@ void scola_destroy(scola_ctx *c) {
         cufftDestroy(c->plan_c2r);
     }
     void *ptrs[] = {c->boxes, c->tables, c->table_arena, c->pchunks, c->tchunks, c->shchunks,
-                    c->zitems, c->citems, c->mchunks, c->part, c->acc, c->work, c->work2, c->phi,
+                    c->zitems, c->citems, c->mchunks, c->tc_tiles, c->dev_err, c->part, c->acc, c->work, c->work2, c->phi,
                     c->shell, c->ck, c->cp, c->ct, c->g[0], c->g[1], c->g[2], c->g[3], c->phi1,
                     c->phi2, c->psi1, c->psi2, c->dens_acc, c->w_h2d, c->x_h2d, c->p_h2d};
     for (void *q : ptrs)
@@ -718,6 +758,20 @@ scola_status scola_kernel_times(const scola_ctx *cc, double *ms_per_launch, int3
     }
     return SCOLA_OK;
 }
+
+scola_status scola_device_status(scola_ctx *c) {
+    if (!c) return invalid("NULL context");
+    CK(c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize());
+    int flag = 0;
+    CK(cudaMemcpy(&flag, c->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        set_error("a kernel's bounded wait expired; its results are invalid");
+        return SCOLA_ERR_TIMEOUT;
+    }
+    return SCOLA_OK;
+}
+
+int32_t scola_uses_tensor_cores(const scola_ctx *c) { return c && c->use_tc ? 1 : 0; }
 
 scola_status scola_final_density(scola_ctx *c, const float *x, float *delta) {
     if (!c || !x || !delta) return invalid("NULL argument");

@@ -51,6 +51,14 @@ struct DstTable {                 // offsets into the device table arena (floats
     long long lam_off;            // lambda[l], l = 0..Ng-1
 };
 
+struct TcGroup {                  // one tensor-core DST launch group: boxes sharing Ng
+    int Ng, Npad, nkc, nstage;
+    Chunk *tiles;                 // device (box, 128-row tile of the box)
+    int ntiles;
+    long long s_off;              // FP32 sine matrix Npad x (32 nkc) in table_arena
+    long long lam_off;            // eigenvalues in table_arena
+};
+
 struct KickDrift {                // FP32 copies of FP64 host coefficients for one force time
     float kF, k1, k2;             // p += kF F + k1 psi1 + k2 psi2
     float alpha, d1, d2;          // s += alpha p + d1 psi1 + d2 psi2
@@ -102,6 +110,10 @@ struct Ctx {
     // first entry of each box in every work list (size nboxes + 1), for per-tile launches
     std::vector<int> pbeg, shbeg, zbeg, cbeg;
     int num_sms = 1, dst_ctas_per_sm = 1;
+    bool use_tc = false;                              // tensor-core (3xTF32) DST passes
+    std::vector<TcGroup> tc_groups;
+    Chunk *tc_tiles = nullptr;
+    int *dev_err = nullptr;                           // set by kernels whose bounded waits expired
     float *part = nullptr;
     unsigned long long *acc = nullptr;
     float *work = nullptr, *work2 = nullptr, *phi = nullptr, *shell = nullptr;
@@ -134,6 +146,11 @@ cudaError_t launch_shell(Ctx &c);
 cudaError_t launch_pad(Ctx &c, float D1);
 cudaError_t launch_deposit(Ctx &c, const float *s, long long stride);
 cudaError_t init_pm_kernels(Ctx &c);
+int tc_plan_stages(int Ng, int &Npad, int &nkc);
+bool tc_supported(int Ng);
+cudaError_t init_tc_kernels();
+cudaError_t launch_poisson_tc(Ctx &c);
+cudaError_t launch_poisson_tc_pass(Ctx &c, int pass);
 cudaError_t launch_poisson(Ctx &c);
 cudaError_t launch_poisson_pass(Ctx &c, int pass);
 cudaError_t launch_acc_to_delta(Ctx &c, float *out);

@@ -1,0 +1,481 @@
+// Dirichlet Poisson solve on the 5th-generation tensor cores (App. C, Eqs. 62-71).
+//
+// The 3D DST-I is applied as six dense pencil products D = A S^T (S_kn =
+// sin(pi (k+1)(n+1)/(Ng+1)), symmetric), each on rows whose transform axis is
+// contiguous in memory.  Every pass writes its result transposed,
+// out[col][row], so that the next pass again finds its axis contiguous:
+//
+//   pass  input rows (axis)    k    writes              epilogue
+//   z+    acc[i][j][k]  (i,j)  k    W1[n][i][j]         delta' = density - Lap Phi_BC (prologue)
+//   y+    W1[n][i][j]   (n,i)  j    W2[m][n][i]
+//   x+    W2[m][n][i]   (m,n)  i    W3[l][m][n]         / (lambda_l + lambda_m + lambda_n)
+//   z-    W3[l][m][n]   (l,m)  n    W4[k'][l][m]
+//   y-    W4[k'][l][m]  (k',l) m    W5[j'][k'][l]
+//   x-    W5[j'][k'][l] (j',k') l   Phi[i'+2][j'+2][k'+2]   * 8 / (Ng+1)^3
+//
+// Precision: FP32 operands split as a = a_hi + a_lo with a_hi the value with
+// its 13 low mantissa bits cleared (exact in TF32); D accumulates
+// a_hi s_hi + a_hi s_lo + a_lo s_hi in FP32 in tensor memory (3xTF32).  A
+// single TF32 product gives position errors of ~0.1 PM cell over a run, the
+// three-term form stays at the FP32 level.
+//
+// One persistent CTA per SM, 9 warps:
+//   warps 0-3  epilogue: tcgen05.ld of the accumulator (warp w owns TMEM lanes
+//              32w..32w+31 = tile rows), scaling, transposed global stores
+//   warps 4-7  producer: coalesced global loads of 128-row x 32-column chunks,
+//              hi/lo split, stores in the 128-byte-swizzled K-major layout
+//   warp 8     TMEM allocation; lane 0 issues tcgen05.mma and tcgen05.commit
+// Stages of A chunks form a ring guarded by full/empty mbarriers; the
+// accumulator is double buffered in TMEM (tmem_full / tmem_empty).  Every
+// wait is bounded (about 2 s of %globaltimer); on expiry the CTA raises an
+// error flag in global memory, stops issuing work, waits for its issued
+// tensor-core work to drain, frees its tensor memory and returns.
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "device_util.cuh"
+
+namespace scola {
+
+namespace {
+
+constexpr int kTM = 128;             // rows per tile (MMA M)
+constexpr int kKC = 32;              // K per chunk (one 128-byte swizzle atom of FP32)
+constexpr int kChunkBytes = kTM * 128;
+constexpr int kThreads = 288;
+constexpr unsigned long long kWaitNs = 2000000000ull;
+
+enum TcPass { P_ZF = 0, P_YF = 1, P_XF = 2, P_ZI = 3, P_YI = 4, P_XI = 5 };
+
+struct TcArgs {
+    const BoxDesc *boxes;
+    const Chunk *tiles;          // (box, tile-in-box)
+    int ntiles;
+    int Ng, Npad, nkc, nstage;   // uniform Ng for the launch
+    const float *S;              // FP32 sine matrix, Npad x (nkc*32), zero padded
+    const float *lam;            // Dirichlet eigenvalues, Ng
+    const void *in;
+    float *out;
+    const float *phi_pad;        // ghost layers (z+ prologue)
+    int *err;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ unsigned long long now_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase; false on timeout or when another role aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
+    const unsigned long long t0 = now_ns();
+    for (uint32_t it = 0;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 63) == 63) {
+            if (*abort_flag) return false;
+            if (now_ns() - t0 > kWaitNs) return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1u << 16;              // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024u >> 4) << 32;    // stride byte offset
+    d |= (uint64_t)1u << 46;              // descriptor version
+    d |= (uint64_t)2u << 61;              // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: D F32, A and B TF32, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Byte offset of element (r, k) (k within the 32-wide chunk) in a 128B-swizzled K-major tile.
+__device__ __forceinline__ uint32_t sw128_offset(int r, int k) {
+    return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((((k >> 2) ^ (r & 7)) & 7) << 4) + (k & 3) * 4);
+}
+
+__device__ __forceinline__ float tf32_hi(float x) {
+    return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+}
+
+template <int PASS>
+__global__ void __launch_bounds__(kThreads, 1) k_dst_tc(TcArgs A) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // 1024-aligned (in the shared window) base for the swizzled operand tiles
+    unsigned char *base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    const int Ng = A.Ng, Npad = A.Npad, nkc = A.nkc, NST = A.nstage;
+    const int sbytes = nkc * Npad * 128;            // one of S_hi / S_lo
+    unsigned char *S_hi = base;
+    unsigned char *S_lo = base + sbytes;
+    unsigned char *stages = base + 2 * sbytes;      // NST x (A_hi chunk, A_lo chunk)
+    uint64_t *bars = (uint64_t *)(stages + (size_t)NST * 2 * kChunkBytes);
+    uint64_t *full = bars;
+    uint64_t *empty = bars + NST;
+    uint64_t *tfull = bars + 2 * NST;
+    uint64_t *tempty = bars + 2 * NST + 2;
+    uint64_t *drain = bars + 2 * NST + 4;
+    uint32_t *tmem_slot = (uint32_t *)(bars + 2 * NST + 5);
+    volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+    float *lam = (float *)(tmem_slot + 4);
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+
+    // ---- set-up: S (hi/lo split, swizzled), lambda, barriers, tensor memory
+    const int Kp = nkc * kKC;
+    for (int q = tid; q < Npad * Kp; q += kThreads) {
+        const int n = q / Kp, k = q % Kp;
+        const float s = A.S[q];
+        const float hi = tf32_hi(s);
+        const uint32_t off = (uint32_t)(k / kKC) * (Npad * 128) + sw128_offset(n, k % kKC);
+        *(float *)(S_hi + off) = hi;
+        *(float *)(S_lo + off) = s - hi;
+    }
+    for (int q = tid; q < Ng; q += kThreads) lam[q] = A.lam[q];
+    if (tid == 0) {
+        for (int s = 0; s < NST; ++s) {
+            mbar_init(&full[s], 128);
+            mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&tfull[a], 1);
+            mbar_init(&tempty[a], 128);
+        }
+        mbar_init(drain, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 8) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(256));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const long long Ng2 = (long long)Ng * Ng;
+
+    if (warp >= 4 && warp < 8) {
+        // ---------------------------------------------------------------- producer
+        const int pt = tid - 128;
+        uint32_t g = 0;
+        for (int it = blockIdx.x; it < A.ntiles && !*abort_flag; it += gridDim.x) {
+            const Chunk tile = A.tiles[it];
+            const BoxDesc &B = A.boxes[tile.box];
+            const long long row0 = (long long)tile.start * kTM;
+            for (int c = 0; c < nkc; ++c, ++g) {
+                const int s = g % NST;
+                if (!mbar_wait(&empty[s], ((g / NST) & 1) ^ 1, abort_flag)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                unsigned char *ah = stages + (size_t)s * 2 * kChunkBytes;
+                unsigned char *al = ah + kChunkBytes;
+#pragma unroll 2
+                for (int q = pt; q < kTM * (kKC / 4); q += 128) {
+                    const int r = q >> 3, kq = q & 7;
+                    const int k = c * kKC + kq * 4;
+                    const long long R = row0 + r;
+                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (R < Ng2 && k < Ng) {
+                        if (PASS == P_ZF) {
+                            const unsigned long long *acc =
+                                reinterpret_cast<const unsigned long long *>(A.in) + B.m_off + R * Ng + k;
+                            const ulonglong2 a01 = *reinterpret_cast<const ulonglong2 *>(acc);
+                            const ulonglong2 a23 = *reinterpret_cast<const ulonglong2 *>(acc + 2);
+                            const float sc = B.nbar_inv * 2.3283064365386963e-10f;
+                            float vv[4] = {(float)a01.x * sc - 1.0f, (float)a01.y * sc - 1.0f,
+                                           (float)a23.x * sc - 1.0f, (float)a23.y * sc - 1.0f};
+                            const int i = (int)(R / Ng), j = (int)(R % Ng);
+                            const bool edge_ij = (i == 0 || j == 0 || i == Ng - 1 || j == Ng - 1);
+                            if (edge_ij || k == 0 || k + 3 == Ng - 1) {
+                                const long long S = Ng + 4;
+                                const float *P = A.phi_pad + B.pp_off;
+                                const float c2 = B.inv_dg * B.inv_dg;
+#pragma unroll
+                                for (int e = 0; e < 4; ++e) {
+                                    const int kk = k + e;
+                                    const long long ctr = ((long long)(i + 2) * S + (j + 2)) * S + (kk + 2);
+                                    float bc = 0.0f;
+                                    if (i == 0) bc += P[ctr - S * S];
+                                    if (i == Ng - 1) bc += P[ctr + S * S];
+                                    if (j == 0) bc += P[ctr - S];
+                                    if (j == Ng - 1) bc += P[ctr + S];
+                                    if (kk == 0) bc += P[ctr - 1];
+                                    if (kk == Ng - 1) bc += P[ctr + 1];
+                                    vv[e] -= bc * c2;
+                                }
+                            }
+                            v = make_float4(vv[0], vv[1], vv[2], vv[3]);
+                        } else {
+                            v = __ldg(reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(A.in) +
+                                                                       B.m_off + R * Ng + k));
+                        }
+                    }
+                    const float4 h = make_float4(tf32_hi(v.x), tf32_hi(v.y), tf32_hi(v.z), tf32_hi(v.w));
+                    const float4 l = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+                    const uint32_t off = sw128_offset(r, kq * 4);
+                    *reinterpret_cast<float4 *>(ah + off) = h;
+                    *reinterpret_cast<float4 *>(al + off) = l;
+                }
+                fence_proxy_async();
+                mbar_arrive(&full[s]);
+            }
+        }
+    } else if (warp == 8) {
+        // ---------------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = idesc_tf32(kTM, Npad);
+            uint32_t g = 0, t = 0;
+            for (int it = blockIdx.x; it < A.ntiles && !*abort_flag; it += gridDim.x, ++t) {
+                const int a = t & 1;
+                if (!mbar_wait(&tempty[a], ((t >> 1) & 1) ^ 1, abort_flag)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(a * 128);
+                bool ok = true;
+                for (int c = 0; c < nkc; ++c, ++g) {
+                    const int s = g % NST;
+                    if (!mbar_wait(&full[s], (g / NST) & 1, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t ah = smem_u32(stages + (size_t)s * 2 * kChunkBytes);
+                    const uint32_t al = ah + kChunkBytes;
+                    const uint32_t bh = smem_u32(S_hi) + (uint32_t)(c * Npad * 128);
+                    const uint32_t bl = smem_u32(S_lo) + (uint32_t)(c * Npad * 128);
+                    const int ksteps = min(kKC, Ng - c * kKC + 7) / 8;   // skip all-zero K steps
+                    for (int kk = 0; kk < ksteps; ++kk) {
+                        const uint32_t o = (uint32_t)kk * 32;
+                        mma_tf32(d, sw128_desc(ah + o), sw128_desc(bh + o), idesc, (c | kk) != 0);
+                        mma_tf32(d, sw128_desc(ah + o), sw128_desc(bl + o), idesc, 1);
+                        mma_tf32(d, sw128_desc(al + o), sw128_desc(bh + o), idesc, 1);
+                    }
+                    mma_commit(&empty[s]);
+                }
+                if (!ok) {
+                    *abort_flag = 1;
+                    break;
+                }
+                mma_commit(&tfull[a]);
+            }
+        }
+    } else {
+        // ---------------------------------------------------------------- epilogue (warps 0-3)
+        const int row_in_tile = warp * 32 + lane;
+        const float scale = (PASS == P_XI) ? 8.0f / ((float)(Ng + 1) * (Ng + 1) * (Ng + 1)) : 1.0f;
+        uint32_t t = 0;
+        for (int it = blockIdx.x; it < A.ntiles && !*abort_flag; it += gridDim.x, ++t) {
+            const int a = t & 1;
+            if (!mbar_wait(&tfull[a], (t >> 1) & 1, abort_flag)) {
+                *abort_flag = 1;
+                break;
+            }
+            tc_fence_after();
+            const Chunk tile = A.tiles[it];
+            const BoxDesc &B = A.boxes[tile.box];
+            const long long R = (long long)tile.start * kTM + row_in_tile;
+            const bool valid = R < Ng2;
+            const uint32_t tbase = tmem + (uint32_t)(a * 128) + ((uint32_t)(warp * 32) << 16);
+            const int rhi = (int)(R / Ng), rlo = (int)(R % Ng);
+            float lsum = 0.0f;
+            if (PASS == P_XF && valid) lsum = lam[rhi] + lam[rlo];
+            for (int c0 = 0; c0 < Npad; c0 += 16) {
+                float v[16];
+                tmem_ld16(tbase + (uint32_t)c0, v);
+                if (c0 + 16 >= Npad) {
+                    // all columns read: hand the accumulator back to the MMA issuer
+                    tc_fence_before();
+                    mbar_arrive(&tempty[a]);
+                }
+                if (!valid) continue;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int col = c0 + j;
+                    if (col >= Ng) break;
+                    if (PASS == P_XI) {
+                        const long long S = Ng + 4;
+                        A.out[B.pp_off + ((long long)(col + 2) * S + (rhi + 2)) * S + (rlo + 2)] = v[j] * scale;
+                    } else if (PASS == P_XF) {
+                        A.out[B.m_off + (long long)col * Ng2 + R] = v[j] / (lam[col] + lsum);
+                    } else {
+                        A.out[B.m_off + (long long)col * Ng2 + R] = v[j];
+                    }
+                }
+            }
+        }
+    }
+
+    // ---- tear-down: every role has left its loop; drain, then free tensor memory
+    if (warp == 8 && lane == 0 && *abort_flag) {
+        // wait (bounded) until every MMA this thread issued has finished writing TMEM
+        mma_commit(drain);
+        const unsigned long long t0 = now_ns();
+        while (!mbar_try_wait(drain, 0) && now_ns() - t0 < kWaitNs) {
+        }
+    }
+    if (*abort_flag && tid == 0) atomicExch(A.err, 1);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 8) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
+}
+
+size_t tc_smem_bytes(int Npad, int nkc, int nstage, int Ng) {
+    return 1024 + 2 * (size_t)nkc * Npad * 128 + (size_t)nstage * 2 * kChunkBytes + (2 * nstage + 5) * 8 +
+           16 + (size_t)Ng * 4 + 64;
+}
+
+template <int PASS>
+cudaError_t run_tc_pass(Ctx &c, const TcGroup &G, const void *in, float *out) {
+    TcArgs a;
+    a.boxes = c.boxes;
+    a.tiles = G.tiles;
+    a.ntiles = G.ntiles;
+    a.Ng = G.Ng;
+    a.Npad = G.Npad;
+    a.nkc = G.nkc;
+    a.nstage = G.nstage;
+    a.S = c.table_arena + G.s_off;
+    a.lam = c.table_arena + G.lam_off;
+    a.in = in;
+    a.out = out;
+    a.phi_pad = c.phi;
+    a.err = c.dev_err;
+    const size_t smem = tc_smem_bytes(G.Npad, G.nkc, G.nstage, G.Ng);
+    const int grid = std::max(1, std::min(G.ntiles, c.num_sms));
+    k_dst_tc<PASS><<<grid, kThreads, smem, c.stream>>>(a);
+    ++c.launches;
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int tc_plan_stages(int Ng, int &Npad, int &nkc) {
+    Npad = ((Ng + 15) / 16) * 16;
+    nkc = (Ng + kKC - 1) / kKC;
+    const size_t fixed = tc_smem_bytes(Npad, nkc, 0, Ng);
+    const size_t budget = 227 * 1024;
+    if (fixed + 2 * 2 * kChunkBytes > budget) return 0;
+    return (int)std::min<size_t>(4, (budget - fixed) / (2 * kChunkBytes));
+}
+
+bool tc_supported(int Ng) {
+    int Npad, nkc;
+    return Ng >= 4 && Ng <= 128 && Ng % 4 == 0 && tc_plan_stages(Ng, Npad, nkc) >= 2;
+}
+
+cudaError_t init_tc_kernels() {
+    const int lim = 227 * 1024;
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_dst_tc<P_ZF>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+    if ((e = cudaFuncSetAttribute(k_dst_tc<P_YF>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+    if ((e = cudaFuncSetAttribute(k_dst_tc<P_XF>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+    if ((e = cudaFuncSetAttribute(k_dst_tc<P_ZI>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+    if ((e = cudaFuncSetAttribute(k_dst_tc<P_YI>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+    return cudaFuncSetAttribute(k_dst_tc<P_XI>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+}
+
+cudaError_t launch_poisson_tc_pass(Ctx &c, int pass) {
+    // buffers: acc -> work -> work2 -> work -> work2 -> work -> phi
+    cudaError_t e = cudaSuccess;
+    for (const TcGroup &G : c.tc_groups) {
+        switch (pass) {
+            case 0: e = run_tc_pass<P_ZF>(c, G, c.acc, c.work); break;
+            case 1: e = run_tc_pass<P_YF>(c, G, c.work, c.work2); break;
+            case 2: e = run_tc_pass<P_XF>(c, G, c.work2, c.work); break;
+            case 3: e = run_tc_pass<P_ZI>(c, G, c.work, c.work2); break;
+            case 4: e = run_tc_pass<P_YI>(c, G, c.work2, c.work); break;
+            case 5: e = run_tc_pass<P_XI>(c, G, c.work, c.phi); break;
+            default: return cudaErrorInvalidValue;
+        }
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_poisson_tc(Ctx &c) {
+    for (int p = 0; p < 6; ++p) {
+        cudaError_t e = launch_poisson_tc_pass(c, p);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace scola

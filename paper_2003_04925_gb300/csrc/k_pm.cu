@@ -464,6 +464,7 @@ cudaError_t init_pm_kernels(Ctx &c) {
 }
 
 cudaError_t launch_poisson(Ctx &c) {
+    if (c.use_tc) return launch_poisson_tc(c);
     switch (c.max_R) {
         case 1: return poisson_R<1>(c);
         case 2: return poisson_R<2>(c);
@@ -476,7 +477,10 @@ cudaError_t launch_poisson(Ctx &c) {
 }
 
 cudaError_t launch_poisson_pass(Ctx &c, int pass) {
-    // the five passes of launch_poisson, one at a time (for per-kernel timing)
+    // the passes of launch_poisson, one at a time (for per-kernel timing); the FP32
+    // form has five passes, the tensor-core form six
+    if (c.use_tc) return launch_poisson_tc_pass(c, pass);
+    if (pass == 5) return cudaSuccess;
     switch (c.max_R * 8 + pass) {
 #define SCOLA_PASS_CASES(R)                                                                     \
     case R * 8 + 0: return run_pass<R, kZFwd>(c, c.zitems, c.n_zitems, c.acc, c.work);          \

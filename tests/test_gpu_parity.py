@@ -41,8 +41,14 @@ CASES_PM = {
 }
 
 
-def _sim(kw):
-    return sc.Scola(**lib_kwargs(kw))
+def _sim(kw, variant="simt"):
+    code = {"simt": sc.SCOLA_DST_SIMT, "tc": sc.SCOLA_DST_TC_3XTF32}[variant]
+    return sc.Scola(**dict(lib_kwargs(kw), dst_variant=code))
+
+
+def _skip_unsupported(kw, variant):
+    if variant == "tc" and kw.get("Ng", 0) % 4 != 0:
+        pytest.skip("the tensor-core DST needs Ng % 4 == 0")
 
 
 def _to_dev(a):
@@ -76,15 +82,18 @@ def test_box_particle_ids_are_bit_exact(name):
     sim.close()
 
 
+@pytest.mark.parametrize("variant", ["simt", "tc"])
 @pytest.mark.parametrize("name", list(CASES_PM))
-def test_pm_force_matches_oracle(name):
+def test_pm_force_matches_oracle(name, variant):
     # One force evaluation (deposit, Dirichlet DST-I solve, gradient, interpolation) on
     # displacements 20x the initial 2LPT ones, so that particles leave their boxes
     # (mass drop in the deposit, clamping in the interpolation).
     kw = CASES_PM[name]
+    _skip_unsupported(kw, variant)
     cfg = oracle_cfg(kw)
     w, f, sched = oracle_fields(kw)
-    sim = _sim(kw)
+    sim = _sim(kw, variant)
+    assert sc.scola_uses_tensor_cores(sim.ctx) == (variant == "tc")
     sim.lpt_fields(_to_dev(w))
     sim.setup_boxes()
     D1 = 0.73
@@ -113,12 +122,15 @@ def test_pm_force_matches_oracle(name):
                                    atol=2e-6 * max(1.0, np.abs(r["delta"]).max()))
         phib = phi[pp_off:pp_off + np3].reshape((g.Ng + 4,) * 3)
         assert np.abs(phib - r["phi"]).max() <= 2e-5 * np.abs(r["phi"]).max()
-        p_off, m_off, pp_off = p_off + n, m_off + ng3, pp_off + np3
+        p_off = p_off + n
+        m_off = (m_off + ng3 + 63) // 64 * 64
+        pp_off = (pp_off + np3 + 63) // 64 * 64
+    sc.scola_device_status(sim.ctx)
     sim.close()
 
 
-def _forward(kw, w):
-    sim = _sim(kw)
+def _forward(kw, w, variant="simt"):
+    sim = _sim(kw, variant)
     x, p = sim.forward(_to_dev(w))
     torch.cuda.synchronize()
     out = x.cpu().numpy().astype(np.float64), p.cpu().numpy().astype(np.float64), sim
@@ -134,12 +146,14 @@ def _pk_rel_err(delta_a, delta_b, L, N):
     return np.abs(pa[ok] / pb[ok] - 1).max()
 
 
+@pytest.mark.parametrize("variant", ["simt", "tc"])
 @pytest.mark.parametrize("name", ["plain_32", "uneven", "table1_like"])
-def test_forward_matches_oracle(name):
+def test_forward_matches_oracle(name, variant):
     kw = CASES_PM[name]
+    _skip_unsupported(kw, variant)
     cfg = oracle_cfg(kw)
     w = synth_inputs.white_noise(cfg.Np, 1)
-    x, p, sim = _forward(kw, w)
+    x, p, sim = _forward(kw, w, variant)
     ref = oscola.run_scola(w, cfg)
     dg = min(oscola.box_geometry(cfg, b).dg for b in range(cfg.nboxes))
     dx = periodic_diff(x, ref["x"], cfg.L)
@@ -177,14 +191,15 @@ def test_forward_is_deterministic_and_host_variant_agrees():
     sim.close()
 
 
+@pytest.mark.parametrize("variant", ["simt", "tc"])
 @pytest.mark.parametrize("name", ["plain_32", "uneven"])
-def test_per_tile_form_matches_batched_form(name):
+def test_per_tile_form_matches_batched_form(name, variant):
     # One box per launch (the plain per-tile form) gives bit-identical results: every kernel
     # computes each box independently and the deposit is order-independent.
     kw = CASES_PM[name]
     w = _to_dev(synth_inputs.white_noise(kw["Np"], 4))
-    a = _sim(kw)
-    b = _sim(dict(kw, batch_mode=sc.SCOLA_BATCH_PER_TILE))
+    a = _sim(kw, variant)
+    b = _sim(dict(kw, batch_mode=sc.SCOLA_BATCH_PER_TILE), variant)
     xa, pa = a.forward(w)
     xb, pb = b.forward(w)
     torch.cuda.synchronize()
@@ -219,13 +234,15 @@ def test_state_and_argument_errors():
 
 
 @pytest.mark.slow
-def test_batched_128_sampled_boxes_match_oracle():
+@pytest.mark.parametrize("variant", ["simt", "tc"])
+def test_batched_128_sampled_boxes_match_oracle(variant):
     # Full-size batched workload in the benchmark's launch configuration; the oracle
     # evolves two sampled boxes (boxes are independent, so each is exact on its own).
     kw = workload_cfg("batched_128")
     cfg = oracle_cfg(kw)
     w = synth_inputs.white_noise(cfg.Np, 1)
-    x, p, sim = _forward(kw, w)
+    x, p, sim = _forward(kw, w, variant)
+    sc.scola_device_status(sim.ctx)
     sim.close()
     fields = oscola.initial_fields(w, cfg)
     sched = oscola.schedule(cfg)
