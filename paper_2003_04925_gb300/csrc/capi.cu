@@ -290,6 +290,7 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &geo) {
     c->use_tc = (p.dst_variant == SCOLA_DST_TC_3XTF32) || (p.dst_variant == SCOLA_DST_AUTO && all_tc &&
                                                            kAutoUsesTensorCores);
     std::vector<Chunk> tct;
+    std::vector<int> box_tile_beg(c->nboxes, 0), box_tile_end(c->nboxes, 0);
     if (c->use_tc) {
         for (auto &kv : tbl_of) {
             TcGroup G;
@@ -307,12 +308,17 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &geo) {
             for (int b = 0; b < c->nboxes; ++b) {
                 if (geo[b].ng != G.Ng) continue;
                 const long long rows = (long long)G.Ng * G.Ng;
+                box_tile_beg[b] = (int)tct.size();
                 for (long long t = 0; t * 128 < rows; ++t) tct.push_back({b, (int)t});
+                box_tile_end[b] = (int)tct.size();
             }
             G.ntiles = (int)(tct.size() - first);
             G.tiles = reinterpret_cast<Chunk *>(first);   // offset, rebased after upload
             c->tc_groups.push_back(G);
         }
+        // per-box ranges (each box's tiles are contiguous within its group)
+        c->tc_tile_beg = box_tile_beg;
+        c->tc_tile_end = box_tile_end;
     }
 
     CK(cudaGetDevice(&c->device));
@@ -426,7 +432,10 @@ struct BoxView {
     Chunk *pch, *sh, *z, *cl;
     int npch, nsh, nz, ncl;
     long long off, len;
+    int tcv;
     BoxView(scola_ctx *cc, int b) : c(cc) {
+        tcv = c->tc_view_box;
+        c->tc_view_box = b;
         pch = c->pchunks; sh = c->shchunks; z = c->zitems; cl = c->citems;
         npch = c->n_pchunks; nsh = c->n_shchunks; nz = c->n_zitems; ncl = c->n_citems;
         off = c->acc_clear_off; len = c->acc_clear_len;
@@ -446,6 +455,7 @@ struct BoxView {
         c->pchunks = pch; c->shchunks = sh; c->zitems = z; c->citems = cl;
         c->n_pchunks = npch; c->n_shchunks = nsh; c->n_zitems = nz; c->n_citems = ncl;
         c->acc_clear_off = off; c->acc_clear_len = len;
+        c->tc_view_box = tcv;
     }
 };
 

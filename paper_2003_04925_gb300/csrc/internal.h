@@ -113,6 +113,8 @@ struct Ctx {
     bool use_tc = false;                              // tensor-core (3xTF32) DST passes
     std::vector<TcGroup> tc_groups;
     Chunk *tc_tiles = nullptr;
+    std::vector<int> tc_tile_beg, tc_tile_end;        // each box's tile range in tc_tiles
+    int tc_view_box = -1;                             // >= 0: TC passes restricted to this box
     int *dev_err = nullptr;                           // set by kernels whose bounded waits expired
     float *part = nullptr;
     unsigned long long *acc = nullptr;

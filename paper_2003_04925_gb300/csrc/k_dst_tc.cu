@@ -22,8 +22,10 @@
 // One persistent CTA per SM, 9 warps:
 //   warps 0-3  epilogue: tcgen05.ld of the accumulator (warp w owns TMEM lanes
 //              32w..32w+31 = tile rows), scaling, transposed global stores
-//   warps 4-7  producer: coalesced global loads of 128-row x 32-column chunks,
-//              hi/lo split, stores in the 128-byte-swizzled K-major layout
+//   warps 4-7  producer: cp.async copies of 128-row x 32-column chunks into a
+//              ring of raw staging buffers, DEPTH chunks ahead; each thread then
+//              splits the bytes it copied into hi/lo and stores them in the
+//              128-byte-swizzled K-major layout of the MMA stage
 //   warp 8     TMEM allocation; lane 0 issues tcgen05.mma and tcgen05.commit
 // Stages of A chunks form a ring guarded by full/empty mbarriers; the
 // accumulator is double buffered in TMEM (tmem_full / tmem_empty).  Every
@@ -52,7 +54,7 @@ struct TcArgs {
     const BoxDesc *boxes;
     const Chunk *tiles;          // (box, tile-in-box)
     int ntiles;
-    int Ng, Npad, nkc, nstage;   // uniform Ng for the launch
+    int Ng, Npad, nkc, nstage;   // uniform Ng for the launch; nstage = hi/lo MMA stages
     const float *S;              // FP32 sine matrix, Npad x (nkc*32), zero padded
     const float *lam;            // Dirichlet eigenvalues, Ng
     const void *in;
@@ -101,6 +103,18 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volati
             if (now_ns() - t0 > kWaitNs) return false;
         }
     }
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 __device__ __forceinline__ void fence_proxy_async() {
@@ -168,8 +182,16 @@ __device__ __forceinline__ float tf32_hi(float x) {
     return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
 }
 
+// Bytes of one raw staging chunk: FP32 inputs, or 64-bit fixed-point counts in pass 1.
 template <int PASS>
+__host__ __device__ constexpr int raw_chunk_bytes() {
+    return PASS == 0 ? 2 * kChunkBytes : kChunkBytes;
+}
+
+template <int PASS, int DEPTH>
 __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(TcArgs A) {
+    constexpr int RS = DEPTH + 1;                   // raw staging ring
+    constexpr int RAWB = raw_chunk_bytes<PASS>();
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-aligned (in the shared window) base for the swizzled operand tiles
     unsigned char *base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
@@ -178,7 +200,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(TcArgs A) {
     unsigned char *S_hi = base;
     unsigned char *S_lo = base + sbytes;
     unsigned char *stages = base + 2 * sbytes;      // NST x (A_hi chunk, A_lo chunk)
-    uint64_t *bars = (uint64_t *)(stages + (size_t)NST * 2 * kChunkBytes);
+    unsigned char *raw = stages + (size_t)NST * 2 * kChunkBytes;   // RS raw chunks
+    uint64_t *bars = (uint64_t *)(raw + (size_t)RS * RAWB);
     uint64_t *full = bars;
     uint64_t *empty = bars + NST;
     uint64_t *tfull = bars + 2 * NST;
@@ -230,71 +253,113 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(TcArgs A) {
 
     if (warp >= 4 && warp < 8) {
         // ---------------------------------------------------------------- producer
+        // chunk g of this CTA = tile (blockIdx.x + (g / nkc) gridDim.x), K-chunk g % nkc.
+        // Thread pt copies and later converts items q = pt + 128 e (e < 8): row q >> 3,
+        // float4 group q & 7 of the chunk.
         const int pt = tid - 128;
-        uint32_t g = 0;
-        for (int it = blockIdx.x; it < A.ntiles && !*abort_flag; it += gridDim.x) {
-            const Chunk tile = A.tiles[it];
-            const BoxDesc &B = A.boxes[tile.box];
-            const long long row0 = (long long)tile.start * kTM;
-            for (int c = 0; c < nkc; ++c, ++g) {
-                const int s = g % NST;
-                if (!mbar_wait(&empty[s], ((g / NST) & 1) ^ 1, abort_flag)) {
-                    *abort_flag = 1;
-                    break;
-                }
-                unsigned char *ah = stages + (size_t)s * 2 * kChunkBytes;
-                unsigned char *al = ah + kChunkBytes;
-#pragma unroll 2
-                for (int q = pt; q < kTM * (kKC / 4); q += 128) {
+        const uint32_t raw_s = smem_u32(raw);
+        const long long my_tiles = A.ntiles > (int)blockIdx.x
+                                       ? (A.ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+        const long long nchunks = my_tiles * nkc;
+        auto issue = [&](long long g) {
+            if (g < nchunks) {
+                const int it = (int)blockIdx.x + (int)(g / nkc) * (int)gridDim.x;
+                const int c = (int)(g % nkc);
+                const Chunk tile = A.tiles[it];
+                const BoxDesc &B = A.boxes[tile.box];
+                const int row0 = tile.start * kTM;
+                const uint32_t dst0 = raw_s + (uint32_t)((g % RS) * RAWB);
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const int q = pt + 128 * e;
                     const int r = q >> 3, kq = q & 7;
                     const int k = c * kKC + kq * 4;
-                    const long long R = row0 + r;
-                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (R < Ng2 && k < Ng) {
-                        if (PASS == P_ZF) {
-                            const unsigned long long *acc =
-                                reinterpret_cast<const unsigned long long *>(A.in) + B.m_off + R * Ng + k;
-                            const ulonglong2 a01 = *reinterpret_cast<const ulonglong2 *>(acc);
-                            const ulonglong2 a23 = *reinterpret_cast<const ulonglong2 *>(acc + 2);
-                            const float sc = B.nbar_inv * 2.3283064365386963e-10f;
-                            float vv[4] = {(float)a01.x * sc - 1.0f, (float)a01.y * sc - 1.0f,
-                                           (float)a23.x * sc - 1.0f, (float)a23.y * sc - 1.0f};
-                            const int i = (int)(R / Ng), j = (int)(R % Ng);
-                            const bool edge_ij = (i == 0 || j == 0 || i == Ng - 1 || j == Ng - 1);
-                            if (edge_ij || k == 0 || k + 3 == Ng - 1) {
-                                const long long S = Ng + 4;
-                                const float *P = A.phi_pad + B.pp_off;
-                                const float c2 = B.inv_dg * B.inv_dg;
+                    const int R = row0 + r;
+                    const bool ok = (long long)R < Ng2 && k < Ng;
+                    const uint32_t off = sw128_offset(r, kq * 4);
+                    if (PASS == P_ZF) {
+                        const unsigned long long *src = reinterpret_cast<const unsigned long long *>(A.in) +
+                                                        B.m_off + (ok ? (long long)R * Ng + k : 0);
+                        cp_async16(dst0 + 2 * off, src, ok ? 16u : 0u);
+                        cp_async16(dst0 + 2 * off + 16, src + 2, ok ? 16u : 0u);
+                    } else {
+                        const float *src = reinterpret_cast<const float *>(A.in) + B.m_off +
+                                           (ok ? (long long)R * Ng + k : 0);
+                        cp_async16(dst0 + off, src, ok ? 16u : 0u);
+                    }
+                }
+            }
+            cp_async_commit();
+        };
+        for (int d = 0; d < DEPTH; ++d) issue(d);
+        for (long long g = 0; g < nchunks && !*abort_flag; ++g) {
+            issue(g + DEPTH);
+            cp_async_wait<DEPTH>();
+            const int s = (int)(g % NST);
+            if (!mbar_wait(&empty[s], (uint32_t)(((g / NST) & 1) ^ 1), abort_flag)) {
+                *abort_flag = 1;
+                break;
+            }
+            const int it = (int)blockIdx.x + (int)(g / nkc) * (int)gridDim.x;
+            const int c = (int)(g % nkc);
+            const Chunk tile = A.tiles[it];
+            const BoxDesc &B = A.boxes[tile.box];
+            const int row0 = tile.start * kTM;
+            unsigned char *ah = stages + (size_t)s * 2 * kChunkBytes;
+            unsigned char *al = ah + kChunkBytes;
+            const unsigned char *rw = raw + (size_t)(g % RS) * RAWB;
 #pragma unroll
-                                for (int e = 0; e < 4; ++e) {
-                                    const int kk = k + e;
-                                    const long long ctr = ((long long)(i + 2) * S + (j + 2)) * S + (kk + 2);
-                                    float bc = 0.0f;
-                                    if (i == 0) bc += P[ctr - S * S];
-                                    if (i == Ng - 1) bc += P[ctr + S * S];
-                                    if (j == 0) bc += P[ctr - S];
-                                    if (j == Ng - 1) bc += P[ctr + S];
-                                    if (kk == 0) bc += P[ctr - 1];
-                                    if (kk == Ng - 1) bc += P[ctr + 1];
-                                    vv[e] -= bc * c2;
-                                }
+            for (int e = 0; e < 8; ++e) {
+                const int q = pt + 128 * e;
+                const int r = q >> 3, kq = q & 7;
+                const uint32_t off = sw128_offset(r, kq * 4);
+                float4 v;
+                if (PASS == P_ZF) {
+                    const ulonglong2 a01 = *reinterpret_cast<const ulonglong2 *>(rw + 2 * off);
+                    const ulonglong2 a23 = *reinterpret_cast<const ulonglong2 *>(rw + 2 * off + 16);
+                    const int k = c * kKC + kq * 4;
+                    const int R = row0 + r;
+                    float vv[4] = {0.f, 0.f, 0.f, 0.f};
+                    if ((long long)R < Ng2 && k < Ng) {
+                        const float sc = B.nbar_inv * 2.3283064365386963e-10f;
+                        vv[0] = (float)a01.x * sc - 1.0f;
+                        vv[1] = (float)a01.y * sc - 1.0f;
+                        vv[2] = (float)a23.x * sc - 1.0f;
+                        vv[3] = (float)a23.y * sc - 1.0f;
+                        const int i = R / Ng, j = R - (R / Ng) * Ng;
+                        const bool edge_ij = (i == 0 || j == 0 || i == Ng - 1 || j == Ng - 1);
+                        if (edge_ij || k == 0 || k + 3 == Ng - 1) {
+                            const int S = Ng + 4;
+                            const float *P = A.phi_pad + B.pp_off;
+                            const float c2 = B.inv_dg * B.inv_dg;
+#pragma unroll
+                            for (int e2 = 0; e2 < 4; ++e2) {
+                                const int kk = k + e2;
+                                const long long ctr = ((long long)(i + 2) * S + (j + 2)) * S + (kk + 2);
+                                float bc = 0.0f;
+                                if (i == 0) bc += P[ctr - (long long)S * S];
+                                if (i == Ng - 1) bc += P[ctr + (long long)S * S];
+                                if (j == 0) bc += P[ctr - S];
+                                if (j == Ng - 1) bc += P[ctr + S];
+                                if (kk == 0) bc += P[ctr - 1];
+                                if (kk == Ng - 1) bc += P[ctr + 1];
+                                vv[e2] -= bc * c2;
                             }
-                            v = make_float4(vv[0], vv[1], vv[2], vv[3]);
-                        } else {
-                            v = __ldg(reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(A.in) +
-                                                                       B.m_off + R * Ng + k));
                         }
                     }
-                    const float4 h = make_float4(tf32_hi(v.x), tf32_hi(v.y), tf32_hi(v.z), tf32_hi(v.w));
-                    const float4 l = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
-                    const uint32_t off = sw128_offset(r, kq * 4);
-                    *reinterpret_cast<float4 *>(ah + off) = h;
-                    *reinterpret_cast<float4 *>(al + off) = l;
+                    v = make_float4(vv[0], vv[1], vv[2], vv[3]);
+                } else {
+                    v = *reinterpret_cast<const float4 *>(rw + off);
                 }
-                fence_proxy_async();
-                mbar_arrive(&full[s]);
+                const float4 h = make_float4(tf32_hi(v.x), tf32_hi(v.y), tf32_hi(v.z), tf32_hi(v.w));
+                const float4 l = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+                *reinterpret_cast<float4 *>(ah + off) = h;
+                *reinterpret_cast<float4 *>(al + off) = l;
             }
+            fence_proxy_async();
+            mbar_arrive(&full[s]);
         }
+        cp_async_wait<0>();
     } else if (warp == 8) {
         // ---------------------------------------------------------------- MMA issuer
         if (lane == 0) {
@@ -397,13 +462,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(TcArgs A) {
     if (warp == 8) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
 }
 
-size_t tc_smem_bytes(int Npad, int nkc, int nstage, int Ng) {
-    return 1024 + 2 * (size_t)nkc * Npad * 128 + (size_t)nstage * 2 * kChunkBytes + (2 * nstage + 5) * 8 +
-           16 + (size_t)Ng * 4 + 64;
+size_t tc_smem_bytes(int Npad, int nkc, int nstage, int Ng, int raw_bytes) {
+    return 1024 + 2 * (size_t)nkc * Npad * 128 + (size_t)nstage * 2 * kChunkBytes + (size_t)raw_bytes +
+           (2 * nstage + 5) * 8 + 16 + (size_t)Ng * 4 + 64;
+}
+
+constexpr size_t kSmemBudget = 227 * 1024;
+constexpr int kDeep = 4, kShallow = 1;
+
+// Deepest raw ring (DEPTH chunks ahead) that fits next to S and the MMA stages.
+template <int PASS>
+int pick_depth(const TcGroup &G) {
+    if (tc_smem_bytes(G.Npad, G.nkc, G.nstage, G.Ng, (kDeep + 1) * raw_chunk_bytes<PASS>()) <= kSmemBudget)
+        return kDeep;
+    return kShallow;
 }
 
 template <int PASS>
 cudaError_t run_tc_pass(Ctx &c, const TcGroup &G, const void *in, float *out) {
+    const int depth = pick_depth<PASS>(G);
     TcArgs a;
     a.boxes = c.boxes;
     a.tiles = G.tiles;
@@ -418,9 +495,12 @@ cudaError_t run_tc_pass(Ctx &c, const TcGroup &G, const void *in, float *out) {
     a.out = out;
     a.phi_pad = c.phi;
     a.err = c.dev_err;
-    const size_t smem = tc_smem_bytes(G.Npad, G.nkc, G.nstage, G.Ng);
+    const size_t smem = tc_smem_bytes(G.Npad, G.nkc, G.nstage, G.Ng, (depth + 1) * raw_chunk_bytes<PASS>());
     const int grid = std::max(1, std::min(G.ntiles, c.num_sms));
-    k_dst_tc<PASS><<<grid, kThreads, smem, c.stream>>>(a);
+    if (depth == kDeep)
+        k_dst_tc<PASS, kDeep><<<grid, kThreads, smem, c.stream>>>(a);
+    else
+        k_dst_tc<PASS, kShallow><<<grid, kThreads, smem, c.stream>>>(a);
     ++c.launches;
     return cudaGetLastError();
 }
@@ -428,12 +508,12 @@ cudaError_t run_tc_pass(Ctx &c, const TcGroup &G, const void *in, float *out) {
 }  // namespace
 
 int tc_plan_stages(int Ng, int &Npad, int &nkc) {
+    // two hi/lo MMA stages; the raw ring takes what is left (at least 2 chunks of pass 1)
     Npad = ((Ng + 15) / 16) * 16;
     nkc = (Ng + kKC - 1) / kKC;
-    const size_t fixed = tc_smem_bytes(Npad, nkc, 0, Ng);
-    const size_t budget = 227 * 1024;
-    if (fixed + 2 * 2 * kChunkBytes > budget) return 0;
-    return (int)std::min<size_t>(4, (budget - fixed) / (2 * kChunkBytes));
+    const int nst = 2;
+    if (tc_smem_bytes(Npad, nkc, nst, Ng, (kShallow + 1) * raw_chunk_bytes<P_ZF>()) > kSmemBudget) return 0;
+    return nst;
 }
 
 bool tc_supported(int Ng) {
@@ -441,21 +521,39 @@ bool tc_supported(int Ng) {
     return Ng >= 4 && Ng <= 128 && Ng % 4 == 0 && tc_plan_stages(Ng, Npad, nkc) >= 2;
 }
 
+template <int PASS>
+cudaError_t set_tc_attr() {
+    const int lim = (int)kSmemBudget;
+    cudaError_t e = cudaFuncSetAttribute(k_dst_tc<PASS, kDeep>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_dst_tc<PASS, kShallow>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+}
+
 cudaError_t init_tc_kernels() {
-    const int lim = 227 * 1024;
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_dst_tc<P_ZF>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-    if ((e = cudaFuncSetAttribute(k_dst_tc<P_YF>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-    if ((e = cudaFuncSetAttribute(k_dst_tc<P_XF>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-    if ((e = cudaFuncSetAttribute(k_dst_tc<P_ZI>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-    if ((e = cudaFuncSetAttribute(k_dst_tc<P_YI>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-    return cudaFuncSetAttribute(k_dst_tc<P_XI>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    if ((e = set_tc_attr<P_ZF>())) return e;
+    if ((e = set_tc_attr<P_YF>())) return e;
+    if ((e = set_tc_attr<P_XF>())) return e;
+    if ((e = set_tc_attr<P_ZI>())) return e;
+    if ((e = set_tc_attr<P_YI>())) return e;
+    return set_tc_attr<P_XI>();
 }
 
 cudaError_t launch_poisson_tc_pass(Ctx &c, int pass) {
     // buffers: acc -> work -> work2 -> work -> work2 -> work -> phi
     cudaError_t e = cudaSuccess;
-    for (const TcGroup &G : c.tc_groups) {
+    std::vector<TcGroup> one;
+    if (c.tc_view_box >= 0) {
+        // per-tile form: only the tiles of one box (a contiguous range of its group)
+        for (const TcGroup &G : c.tc_groups) {
+            if (G.Ng != c.boxes_h[c.tc_view_box].Ng) continue;
+            TcGroup V = G;
+            V.tiles = c.tc_tiles + c.tc_tile_beg[c.tc_view_box];
+            V.ntiles = c.tc_tile_end[c.tc_view_box] - c.tc_tile_beg[c.tc_view_box];
+            one.push_back(V);
+        }
+    }
+    for (const TcGroup &G : (c.tc_view_box >= 0 ? one : c.tc_groups)) {
         switch (pass) {
             case 0: e = run_tc_pass<P_ZF>(c, G, c.acc, c.work); break;
             case 1: e = run_tc_pass<P_YF>(c, G, c.work, c.work2); break;
