@@ -264,6 +264,36 @@ scola_status scola_device_status(scola_ctx *ctx);
 /* 1 when the context's Poisson solve runs on the tensor cores, else 0. */
 int32_t scola_uses_tensor_cores(const scola_ctx *ctx);
 
+/*
+ * Box density without any allocation.  The paper has no counterpart: this is
+ * an interface for callers that cannot allocate device memory at the point
+ * where they need a density (for example code running while a stream is being
+ * captured into a CUDA graph, or a service that forbids allocations outside
+ * its own memory pool).  It computes the same B^sCOLA cloud-in-cell density as
+ * scola_pm_force's delta output for one box, needs no context, and calls no
+ * cudaMalloc, cudaFree or allocating library routine.
+ *   s_dev      device, 3 x nsc^3 FP32 displacements s = x - q of the box
+ *              particles, [component][particle], box-local order
+ *              (bi*nsc + bj)*nsc + bk, particle b at q_loc = (b + 1/2) dq
+ *   nsc        particles per side of the box (Np,sCOLA)
+ *   ng         PM cells per side (Ng >= nsc); ng^3 <= 128^3 = 2,097,152
+ *   dq         lattice spacing L / Np [Mpc/h]
+ *   delta_dev  device, ng^3 FP32, receives delta = n / nbar - 1 per interior cell
+ *   stream     cudaStream_t for the work (NULL = legacy default stream)
+ * Scratch: a fixed 16 MiB device array (128^3 64-bit counters) in the
+ * library, held by every GPU that loads the library until the process exits.
+ * Every call shares it and it keeps the previous call's contents; each call
+ * clears the part it uses first.  Calls whose work overlaps on the GPU
+ * (different streams or host threads) race on the scratch: serialise them.
+ * The first call on each device looks up the scratch's device address with
+ * cudaGetSymbolAddress (with that device current); make that first call
+ * before any stream capture begins.
+ * Errors: INVALID_ARG (NULL pointers, ng < nsc, ng^3 above the maximum),
+ * CUDA.
+ */
+scola_status scola_box_density_noalloc(const float *s_dev, int32_t nsc, int32_t ng, double dq,
+                                       float *delta_dev, void *stream);
+
 scola_status scola_get_stats(const scola_ctx *ctx, scola_stats *out);
 const char *scola_status_string(scola_status status);
 const char *scola_last_error(void);

@@ -73,6 +73,7 @@ _sig = {
     "scola_kernel_times": (c_int32, [c_void_p, _P(c_double), c_int32]),
     "scola_device_status": (c_int32, [c_void_p]),
     "scola_uses_tensor_cores": (c_int32, [c_void_p]),
+    "scola_box_density_noalloc": (c_int32, [c_void_p, c_int32, c_int32, c_double, c_void_p, c_void_p]),
     "scola_status_string": (c_char_p, [c_int32]),
     "scola_last_error": (c_char_p, []),
 }
@@ -226,6 +227,12 @@ def scola_device_status(ctx):
 
 def scola_uses_tensor_cores(ctx):
     return bool(_lib.scola_uses_tensor_cores(ctx))
+
+
+def scola_box_density_noalloc(s, nsc, ng, dq, delta, stream=0):
+    """One box's B^sCOLA density with the library's fixed scratch (no allocation)."""
+    _check(_lib.scola_box_density_noalloc(_ptr(s), int(nsc), int(ng), float(dq), _ptr(delta),
+                                          c_void_p(stream or None)), "scola_box_density_noalloc")
 
 
 def scola_status_string(status):
