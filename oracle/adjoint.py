@@ -1,0 +1,285 @@
+"""FP64 adjoint of the sCOLA forward run (vector-Jacobian products, hand derived).
+
+Test infrastructure (see ``oracle/__init__``).
+
+Loss:  Lval = sum_c (delta_f(c) - delta_t(c))^2  over the periodic N^3 CIC density of
+the final positions (Sec. 4.1), as a function of the white noise w.  The
+gradient is assembled backwards through every step of ``scola.run_scola``:
+
+  delta_f = CIC(x)                      -> lam_x = dCIC/dx^T lam_delta        (weight gradients)
+  x = (q + s_n) mod L  (tile particles) -> lam_s(n) = lam_x
+  KDK in reverse (App. B, Eqs. 53-54), per box, with the displacements s_k of
+  every force evaluation recomputed forward and kept (checkpoints):
+      drift  s_k+1 = s_k + alpha p + d1 Psi1 + d2 Psi2
+             -> lam_p += alpha lam_s,  lam_Psi1 += d1 lam_s,  lam_Psi2 += d2 lam_s
+      kick   p += kF F(s_k) + k1 Psi1 + k2 Psi2
+             -> lam_F = kF lam_p,  lam_Psi1 += k1 lam_p,  lam_Psi2 += k2 lam_p
+      force  F(s) = B-bar(grad Phi[delta(s), Phi_BC])  (Sec. 3.4)
+             -> lam_s += dF/ds^T lam_F through (i) the interpolation weights,
+                (ii) the mesh: lam_G = CIC deposit of lam_F, lam_Phi = -div lam_G,
+                lam_delta' = Dirichlet solve of lam_Phi (the Dirichlet Laplacian is
+                symmetric), lam_s += d delta/ds^T lam_delta (deposit weights), and
+                lam_Phi_BC from the ghost layers and the boundary source of Eq. 62
+  L-     s_0 = -D1(a_i) Psi1 + D2(a_i) Psi2 -> lam_Psi1, lam_Psi2
+  C.3    Phi_BC = D1(a_K) * trilinear(phi1) -> lam_phi1 (trilinear transpose)
+  C.2    Psi = central gradient            -> lam_phi = -div lam_Psi
+  A.2    phi2 = Lap^-1 S(phi1), S bilinear in the second derivatives of phi1
+         phi1 = Lap^-1 delta_i              (symmetric Fourier operators)
+  A.1    delta_i = colour(w)                (real symmetric filter)
+
+Pins (tests/test_oracle_adjoint.py): dot-product identities <J v, u> = <v, J^T u>
+for each linear piece, and FP64 central finite differences of the whole loss
+along random directions.
+"""
+import numpy as np
+
+from . import boundary, ics, lpt, pm, scola, stats, tiling
+
+
+# ----------------------------------------------------------------------------- CIC pieces
+def _corner_weights(u):
+    """i0, and for each of the 8 corners: offsets, weight, d weight / du (per axis)."""
+    i0 = np.floor(u).astype(np.int64)
+    f = u - i0
+    out = []
+    for dx in (0, 1):
+        for dy in (0, 1):
+            for dz in (0, 1):
+                d = np.array([dx, dy, dz])
+                w1 = [f[:, a] if d[a] else 1.0 - f[:, a] for a in range(3)]
+                g1 = [np.ones_like(f[:, a]) if d[a] else -np.ones_like(f[:, a]) for a in range(3)]
+                w = w1[0] * w1[1] * w1[2]
+                dw = np.stack([g1[0] * w1[1] * w1[2], w1[0] * g1[1] * w1[2], w1[0] * w1[1] * g1[2]], 1)
+                out.append((d, w, dw))
+    return i0, out
+
+
+def periodic_density_vjp(x, L, N, Np, lam_delta):
+    """lam_x = d(CIC density on N^3)/dx^T lam_delta  (Sec. 4.1 density, periodic)."""
+    d = L / N
+    u = np.asarray(x, dtype=np.float64) / d - 0.5
+    i0, corners = _corner_weights(u)
+    scale = float(N) ** 3 / float(Np) ** 3
+    lam = np.zeros_like(u)
+    for off, w, dw in corners:
+        c = (i0 + off) % N
+        v = lam_delta[c[:, 0], c[:, 1], c[:, 2]]
+        lam += dw * v[:, None]
+    return lam * scale / d
+
+
+def box_density_vjp(xloc, dg, Ng, Nsc, lam_delta):
+    """lam_s = d(B^sCOLA density)/ds^T lam_delta over the interior cells (Sec. 3.4.1)."""
+    u = pm.mesh_coordinate(xloc, dg)
+    i0, corners = _corner_weights(u)
+    lam = np.zeros_like(u)
+    inv_nbar = (Ng / Nsc) ** 3
+    for off, w, dw in corners:
+        c = i0 + off
+        inside = np.all((c >= 0) & (c < Ng), axis=1)
+        v = np.zeros(len(u))
+        v[inside] = lam_delta[c[inside, 0], c[inside, 1], c[inside, 2]]
+        lam += dw * v[:, None]
+    return lam * inv_nbar / dg
+
+
+def interp_vjp(phi_pad, xloc, dg, lam_F):
+    """VJP of F = interpolate_gradient(phi_pad, x): returns (lam_x, lam_phi_pad)."""
+    Ng = phi_pad.shape[0] - 4
+    u_raw = pm.mesh_coordinate(xloc, dg)
+    u = np.clip(u_raw, -1.0, float(Ng))
+    free = (u == u_raw).astype(np.float64)               # d u / d u_raw (0 where clamped)
+    i0 = np.minimum(np.floor(u).astype(np.int64), Ng - 1)
+    f = u - i0
+    P = phi_pad
+    lam_x = np.zeros_like(u)
+    lam_G = np.zeros((3,) + P.shape)                     # adjoint of the gradient mesh
+    for dx in (0, 1):
+        for dy in (0, 1):
+            for dz in (0, 1):
+                d = (dx, dy, dz)
+                w1 = [f[:, a] if d[a] else 1.0 - f[:, a] for a in range(3)]
+                g1 = [1.0 if d[a] else -1.0 for a in range(3)]
+                w = w1[0] * w1[1] * w1[2]
+                dw = np.stack([g1[0] * w1[1] * w1[2], w1[0] * g1[1] * w1[2], w1[0] * w1[1] * g1[2]], 1)
+                cx, cy, cz = i0[:, 0] + dx + 2, i0[:, 1] + dy + 2, i0[:, 2] + dz + 2
+                G = np.stack([(P[cx + 1, cy, cz] - P[cx - 1, cy, cz]),
+                              (P[cx, cy + 1, cz] - P[cx, cy - 1, cz]),
+                              (P[cx, cy, cz + 1] - P[cx, cy, cz - 1])], 1) / (2.0 * dg)
+                # direct term: d w / d u * (G . lam_F)
+                lam_x += dw * np.sum(G * lam_F, axis=1)[:, None]
+                for a in range(3):
+                    np.add.at(lam_G[a], (cx, cy, cz), w * lam_F[:, a])
+    lam_x *= free / dg
+    # G_a(c) = (P(c + e_a) - P(c - e_a)) / (2 dg)  ->  lam_P(c +- e_a) += +- lam_G_a(c) / (2 dg)
+    lam_P = np.zeros_like(P)
+    for a in range(3):
+        g = lam_G[a] / (2.0 * dg)
+        sl_p = [slice(None)] * 3
+        sl_m = [slice(None)] * 3
+        src_p = [slice(None)] * 3
+        src_m = [slice(None)] * 3
+        sl_p[a], src_p[a] = slice(1, None), slice(None, -1)   # lam_P[c+1] += g[c]
+        sl_m[a], src_m[a] = slice(None, -1), slice(1, None)   # lam_P[c-1] -= g[c]
+        lam_P[tuple(sl_p)] += g[tuple(src_p)]
+        lam_P[tuple(sl_m)] -= g[tuple(src_m)]
+    return lam_x, lam_P
+
+
+def laplacian_on_interior_T(lam_int, dg):
+    """Adjoint of ``pm.laplacian_on_interior`` (padded -> interior)."""
+    Ng = lam_int.shape[0]
+    out = np.zeros((Ng + 4,) * 3)
+    c = slice(2, Ng + 2)
+    out[c, c, c] += -6.0 * lam_int
+    out[3:Ng + 3, c, c] += lam_int
+    out[1:Ng + 1, c, c] += lam_int
+    out[c, 3:Ng + 3, c] += lam_int
+    out[c, 1:Ng + 1, c] += lam_int
+    out[c, c, 3:Ng + 3] += lam_int
+    out[c, c, 1:Ng + 1] += lam_int
+    return out / dg**2
+
+
+def box_force_vjp(xloc, dg, Ng, Nsc, phi_bc_padded, lam_F):
+    """VJP of ``pm.box_force`` (F only): returns (lam_x, lam_phi_bc_padded)."""
+    delta, _ = pm.cic_deposit_box(xloc, dg, Ng, Nsc)
+    phi = pm.dirichlet_potential(delta, phi_bc_padded, dg)
+    lam_x, lam_P = interp_vjp(phi, xloc, dg, lam_F)
+    inside = boundary.interior_mask(Ng)
+    lam_int = lam_P[2:Ng + 2, 2:Ng + 2, 2:Ng + 2]
+    lam_src = pm.zero_bc_poisson(lam_int, dg)            # self-adjoint Dirichlet solve
+    lam_bc = np.where(inside, 0.0, lam_P)                # ghost layers take Phi_BC directly
+    lam_bc -= np.where(inside, 0.0, laplacian_on_interior_T(lam_src, dg))
+    lam_x += box_density_vjp(xloc, dg, Ng, Nsc, lam_src)
+    return lam_x, lam_bc
+
+
+def trilinear_periodic_T(vals, L, N, X):
+    """Adjoint of ``boundary.trilinear_periodic`` (grid -> points): scatter to the grid."""
+    d = L / N
+    u = X / d - 0.5
+    i0 = np.floor(u).astype(np.int64)
+    f = u - i0
+    out = np.zeros((N, N, N))
+    for dx in (0, 1):
+        for dy in (0, 1):
+            for dz in (0, 1):
+                w = ((f[:, 0] if dx else 1 - f[:, 0]) * (f[:, 1] if dy else 1 - f[:, 1])
+                     * (f[:, 2] if dz else 1 - f[:, 2]))
+                np.add.at(out, ((i0[:, 0] + dx) % N, (i0[:, 1] + dy) % N, (i0[:, 2] + dz) % N), w * vals)
+    return out
+
+
+def bc_shell_T(lam_shell, L, N, origin, dg, Ng):
+    """Adjoint of ``boundary.bc_shell`` with respect to phi1."""
+    c = boundary.padded_cell_index(Ng).astype(np.float64)
+    cx, cy, cz = np.meshgrid(c, c, c, indexing="ij")
+    X = np.stack([origin[0] + (cx.ravel() + 0.5) * dg, origin[1] + (cy.ravel() + 0.5) * dg,
+                  origin[2] + (cz.ravel() + 0.5) * dg], axis=1)
+    vals = np.where(boundary.interior_mask(Ng), 0.0, lam_shell).ravel()
+    return trilinear_periodic_T(vals, L, N, X)
+
+
+def central_gradient_T(g, L):
+    """Adjoint of ``lpt.central_gradient``: the central difference is antisymmetric."""
+    N = g.shape[1]
+    d = L / N
+    return -sum((np.roll(g[a], -1, axis=a) - np.roll(g[a], 1, axis=a)) / (2.0 * d) for a in range(3))
+
+
+def lpt_vjp(delta, L, lam_phi1, lam_psi1, lam_psi2):
+    """lam_delta_i from the adjoints of phi1, Psi1 and Psi2 (Eqs. 5-6, C.2)."""
+    N = delta.shape[0]
+    d = L / N
+    lam = lpt.laplacian_symbol(N, L)
+    inv = lambda fk: np.where(lam != 0, fk / np.where(lam != 0, lam, 1.0), 0.0)
+    kx, ky, kz = ics.fourier_wavenumbers(N, L)
+    D = [np.sin(kx * d) / d, np.sin(ky * d) / d, np.sin(kz * d) / d]
+    phi1_k = inv(np.fft.rfftn(delta))
+    sec = lambda i, j, fk: np.fft.irfftn(-D[i] * D[j] * fk, s=delta.shape, axes=(0, 1, 2))
+    xx, yy, zz = sec(0, 0, phi1_k), sec(1, 1, phi1_k), sec(2, 2, phi1_k)
+    xy, xz, yz = sec(0, 1, phi1_k), sec(0, 2, phi1_k), sec(1, 2, phi1_k)
+    lam_phi2 = central_gradient_T(lam_psi2, L)
+    lam_S = np.fft.irfftn(inv(np.fft.rfftn(lam_phi2)), s=delta.shape, axes=(0, 1, 2))
+    parts = [((0, 0), lam_S * (yy + zz)), ((1, 1), lam_S * (xx + zz)), ((2, 2), lam_S * (xx + yy)),
+             ((0, 1), -2.0 * lam_S * xy), ((0, 2), -2.0 * lam_S * xz), ((1, 2), -2.0 * lam_S * yz)]
+    lam_phi1_k = np.fft.rfftn(lam_phi1 + central_gradient_T(lam_psi1, L))
+    for (i, j), v in parts:
+        lam_phi1_k = lam_phi1_k + (-D[i] * D[j]) * np.fft.rfftn(v)
+    return np.fft.irfftn(inv(lam_phi1_k), s=delta.shape, axes=(0, 1, 2))
+
+
+# ----------------------------------------------------------------------------- full run
+def loss_and_grad(w, cfg, delta_target):
+    """Lval(w) and dLval/dw for the final-density loss of one sCOLA run."""
+    w = np.asarray(w, dtype=np.float64)
+    fields = scola.initial_fields(w, cfg)
+    sched = scola.schedule(cfg)
+    n = len(sched["alpha"])
+    Np3 = cfg.Np**3
+    # forward, keeping every box's displacements at each force evaluation
+    boxes = []
+    for b in range(cfg.nboxes):
+        g = scola.box_geometry(cfg, b)
+        ids = tiling.box_global_ids(cfg.Np, cfg.Ntiles, g.t, g.Nbuf)
+        psi1 = fields.psi1.reshape(3, -1)[:, ids].T
+        psi2 = fields.psi2.reshape(3, -1)[:, ids].T
+        qloc = (tiling.box_local_lattice(g.Nsc) + 0.5) * (cfg.L / cfg.Np)
+        shell = boundary.bc_shell(fields.phi1, cfg.L, g.origin, g.dg, g.Ng)
+        s = -sched["D1_i"] * psi1 + sched["D2_i"] * psi2
+        p = np.zeros_like(s)
+        ss = []
+        for k in range(n + 1):
+            ss.append(s)
+            F = pm.box_force(qloc + s, g.dg, g.Ng, g.Nsc, sched["D1"][k] * shell)["F"]
+            D1, D2 = sched["D1"][k], sched["D2"][k]
+            p = p + sched["beta"][k] * (F - D1 * psi1 + (D2 - D1 * D1) * psi2)
+            if k < n:
+                s = s + sched["alpha"][k] * p - sched["dD1"][k] * psi1 + sched["dD2"][k] * psi2
+        boxes.append(dict(g=g, ids=ids, psi1=psi1, psi2=psi2, qloc=qloc, shell=shell, ss=ss, s=s))
+    s_glob = np.zeros((Np3, 3))
+    for bx in boxes:
+        keep = tiling.tile_interior_mask(cfg.Np, cfg.Ntiles, bx["g"].Nbuf)
+        s_glob[bx["ids"][keep]] = bx["s"][keep]
+    x = np.mod(scola.lattice_positions(cfg.Np, cfg.L) + s_glob, cfg.L)
+    delta_f = stats.cic_density_periodic(x, cfg.L, cfg.Np, cfg.Np)
+    resid = delta_f - delta_target
+    value = float(np.sum(resid**2))
+    lam_x = periodic_density_vjp(x, cfg.L, cfg.Np, cfg.Np, 2.0 * resid)
+
+    lam_psi1 = np.zeros((Np3, 3))
+    lam_psi2 = np.zeros((Np3, 3))
+    lam_phi1 = np.zeros_like(fields.phi1)
+    for bx in boxes:
+        g = bx["g"]
+        keep = tiling.tile_interior_mask(cfg.Np, cfg.Ntiles, g.Nbuf)
+        lam_s = np.zeros_like(bx["s"])
+        lam_s[keep] = lam_x[bx["ids"][keep]]
+        lam_p = np.zeros_like(lam_s)
+        lp1 = np.zeros_like(lam_s)
+        lp2 = np.zeros_like(lam_s)
+        lam_shell = np.zeros((g.Ng + 4,) * 3)
+        for k in range(n, -1, -1):
+            if k < n:
+                lam_p = lam_p + sched["alpha"][k] * lam_s
+                lp1 = lp1 - sched["dD1"][k] * lam_s
+                lp2 = lp2 + sched["dD2"][k] * lam_s
+            b = sched["beta"][k]
+            D1, D2 = sched["D1"][k], sched["D2"][k]
+            lam_F = b * lam_p
+            lp1 = lp1 - b * D1 * lam_p
+            lp2 = lp2 + b * (D2 - D1 * D1) * lam_p
+            lx, lbc = box_force_vjp(bx["qloc"] + bx["ss"][k], g.dg, g.Ng, g.Nsc, D1 * bx["shell"], lam_F)
+            lam_s = lam_s + lx
+            lam_shell += D1 * lbc
+        lp1 = lp1 - sched["D1_i"] * lam_s
+        lp2 = lp2 + sched["D2_i"] * lam_s
+        np.add.at(lam_psi1, bx["ids"], lp1)
+        np.add.at(lam_psi2, bx["ids"], lp2)
+        lam_phi1 += bc_shell_T(lam_shell, cfg.L, cfg.Np, g.origin, g.dg, g.Ng)
+    N = cfg.Np
+    lam_delta = lpt_vjp(fields.delta, cfg.L, lam_phi1, lam_psi1.T.reshape(3, N, N, N),
+                        lam_psi2.T.reshape(3, N, N, N))
+    lam_w = ics.initial_density(lam_delta, cfg.L, cfg.Om, cfg.h, cfg.ns, cfg.sigma8)
+    return value, lam_w

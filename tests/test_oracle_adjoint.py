@@ -1,0 +1,97 @@
+"""Pins of the oracle's hand-derived adjoint: dot-product identities for the linear pieces and
+FP64 central finite differences for the nonlinear ones and for the whole final-density loss."""
+import numpy as np
+import pytest
+
+import synth_inputs
+from oracle import adjoint, boundary, lpt, pm, scola, stats
+
+
+def _fd(f, x, dx, eps):
+    return (f(x + eps * dx) - f(x - eps * dx)) / (2 * eps)
+
+
+def test_interpolation_vjp_dot_product_and_positions():
+    Ng, dg = 6, 1.3
+    phi = synth_inputs.random_field((Ng + 4,) * 3, 1)
+    x = synth_inputs.random_positions(40, -0.3 * dg, (Ng + 0.3) * dg, 2)
+    u = synth_inputs.random_field((40, 3), 3)
+    # linear in phi: <F(v), u> = <v, J^T u>
+    v = synth_inputs.random_field((Ng + 4,) * 3, 4)
+    Fv, _ = pm.interpolate_gradient(v, x, dg)
+    _, lam_P = adjoint.interp_vjp(phi, x, dg, u)
+    assert abs(np.sum(Fv * u) - np.sum(v * lam_P)) < 1e-11 * np.abs(Fv * u).sum()
+    # positions: central differences
+    lam_x, _ = adjoint.interp_vjp(phi, x, dg, u)
+    dx = synth_inputs.random_field((40, 3), 5)
+    g = lambda xx: np.sum(pm.interpolate_gradient(phi, xx, dg)[0] * u)
+    assert abs(_fd(g, x, dx, 1e-6) - np.sum(lam_x * dx)) < 1e-6 * np.abs(lam_x * dx).sum()
+
+
+def test_box_force_vjp_finite_differences():
+    Nsc, Ng, dg = 5, 6, 1.0
+    q = (np.indices((Nsc,) * 3).reshape(3, -1).T + 0.5) * (Ng * dg / Nsc)
+    s = 0.6 * synth_inputs.random_field(q.shape, 6)
+    bc = synth_inputs.random_field((Ng + 4,) * 3, 7)
+    bc[boundary.interior_mask(Ng)] = 0.0
+    u = synth_inputs.random_field(q.shape, 8)
+    lam_x, lam_bc = adjoint.box_force_vjp(q + s, dg, Ng, Nsc, bc, u)
+    ds = synth_inputs.random_field(q.shape, 9)
+    dbc = synth_inputs.random_field(bc.shape, 10)
+    dbc[boundary.interior_mask(Ng)] = 0.0
+    fx = lambda ss: np.sum(pm.box_force(q + ss, dg, Ng, Nsc, bc)["F"] * u)
+    fb = lambda bb: np.sum(pm.box_force(q + s, dg, Ng, Nsc, bb)["F"] * u)
+    assert abs(_fd(fx, s, ds, 1e-6) - np.sum(lam_x * ds)) < 1e-5 * np.abs(lam_x * ds).sum()
+    assert abs(_fd(fb, bc, dbc, 1e-3) - np.sum(lam_bc * dbc)) < 1e-9 * np.abs(lam_bc * dbc).sum()
+
+
+def test_periodic_density_vjp_finite_differences():
+    N, Np, L = 6, 6, 12.0
+    x = synth_inputs.random_positions(Np**3, 0.0, L, 11)
+    lam = synth_inputs.random_field((N,) * 3, 12)
+    g = adjoint.periodic_density_vjp(x, L, N, Np, lam)
+    dx = synth_inputs.random_field(x.shape, 13)
+    f = lambda xx: np.sum(stats.cic_density_periodic(xx, L, N, Np) * lam)
+    assert abs(_fd(f, x, dx, 1e-6) - np.sum(g * dx)) < 1e-6 * np.abs(g * dx).sum()
+
+
+def test_shell_transpose_dot_product():
+    N, L, Ng = 8, 20.0, 5
+    origin, dg = np.array([-3.0, 4.0, 11.0]), 2.2
+    v = synth_inputs.random_field((N,) * 3, 14)
+    u = synth_inputs.random_field((Ng + 4,) * 3, 15)
+    lhs = np.sum(boundary.bc_shell(v, L, origin, dg, Ng) * u)
+    rhs = np.sum(v * adjoint.bc_shell_T(u, L, N, origin, dg, Ng))
+    assert abs(lhs - rhs) < 1e-12 * np.abs(u).sum() * np.abs(v).max()
+
+
+def test_lpt_vjp_finite_differences():
+    N, L = 8, 30.0
+    delta = synth_inputs.random_field((N,) * 3, 16)
+    delta -= delta.mean()
+    a1 = synth_inputs.random_field((N,) * 3, 17)
+    a2 = synth_inputs.random_field((3, N, N, N), 18)
+    a3 = synth_inputs.random_field((3, N, N, N), 19)
+
+    def f(d):
+        phi1, phi2, psi1, psi2 = lpt.lpt_fields(d, L)
+        return np.sum(phi1 * a1) + np.sum(psi1 * a2) + np.sum(psi2 * a3)
+
+    g = adjoint.lpt_vjp(delta, L, a1, a2, a3)
+    dd = synth_inputs.random_field((N,) * 3, 20)
+    assert abs(_fd(f, delta, dd, 1e-4) - np.sum(g * dd)) < 1e-8 * np.abs(g * dd).sum()
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("ratio", [1, 2])
+def test_whole_loss_gradient_finite_differences(ratio):
+    cfg = scola.ScolaConfig(L=48.0, Np=12, Ntiles=2, Nbuf=2, mesh_ratio=ratio, nsteps=2, a_i=0.05)
+    w = synth_inputs.white_noise(12, 21).astype(np.float64)
+    target = stats.cic_density_periodic(
+        scola.run_scola(synth_inputs.white_noise(12, 22), cfg)["x"], cfg.L, cfg.Np, cfg.Np)
+    val, grad = adjoint.loss_and_grad(w, cfg, target)
+    f = lambda ww: adjoint.loss_and_grad(ww, cfg, target)[0]
+    for seed in (23, 24):
+        d = synth_inputs.random_field(w.shape, seed)
+        fd = _fd(f, w, d, 1e-6)
+        assert abs(fd - np.sum(grad * d)) < 1e-5 * (abs(fd) + 1e-12), (fd, np.sum(grad * d))
