@@ -40,8 +40,9 @@ def parse():
     ap.add_argument("--impl", default="scola", choices=["scola", "reference"])
     ap.add_argument("--workload", default="batched_128")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--dst", default="tc", choices=["tc", "simt"],
-                    help="Poisson-solve form: tensor-core 3xTF32 (tc) or FP32 CUDA cores (simt)")
+    ap.add_argument("--dst", default="tc4", choices=["tc", "tc4", "simt"],
+                    help="Poisson-solve form: tensor-core 4xTF32 (tc4, default), 3xTF32 (tc) or FP32 "
+                         "CUDA cores (simt)")
     ap.add_argument("--forward-only", action="store_true",
                     help="only W + K forward runs of the batched form (for ncu launch lists)")
     return ap.parse_args()
@@ -217,6 +218,53 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- adjoint cost
+def adjoint_cost(sc, torch, dst, steps):
+    """Backward / forward device time on the adjoint workload (128^3, 4^3 tiles, 48^3 meshes)."""
+    import numpy as np
+    import synth_inputs
+    kw, W = workload_kwargs("adjoint_128")
+    kw["dst_variant"] = {"tc": sc.SCOLA_DST_TC_3XTF32, "tc4": sc.SCOLA_DST_TC_4XTF32,
+                         "simt": sc.SCOLA_DST_SIMT}[dst]
+    plain = sc.Scola(**kw)
+    sim = sc.Scola(**kw)
+    sim.enable_checkpointing(True)
+    w = torch.from_numpy(synth_inputs.white_noise(kw["Np"], W["seed"])).cuda()
+    wt = torch.from_numpy(synth_inputs.white_noise(kw["Np"], W["target_seed"])).cuda()
+    xt, _ = plain.forward(wt)
+    target = plain.final_density(xt).clone()
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    for _ in range(2):
+        x, _ = sim.forward(w)
+        d = sim.final_density(x)
+        sim.backward(2.0 * (d - target))
+        plain.forward(w)
+    torch.cuda.synchronize()
+    t_plain = t_fwd = t_bwd = 0.0
+    for _ in range(steps):
+        ev[0].record(stream)
+        plain.forward(w)
+        ev[1].record(stream)
+        x, _ = sim.forward(w)
+        d = sim.final_density(x)
+        lam = 2.0 * (d - target)
+        ev[2].record(stream)
+        sim.backward(lam)
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+        t_plain += ev[0].elapsed_time(ev[1])
+        t_fwd += ev[1].elapsed_time(ev[2])
+        t_bwd += ev[2].elapsed_time(ev[3])
+    sc.scola_device_status(sim.ctx)
+    plain.close()
+    sim.close()
+    t_plain, t_fwd, t_bwd = t_plain / steps, t_fwd / steps, t_bwd / steps
+    return {"workload": "adjoint_128", "ms_forward": t_plain, "ms_forward_checkpointed": t_fwd,
+            "ms_backward": t_bwd, "adjoint_over_forward": t_bwd / t_plain,
+            "loss": "sum over the 128^3 CIC mesh of (delta - delta_target)^2, target from seed 2"}
+
+
 # ----------------------------------------------------------------------------- roofline
 def kernel_roofline(kt, kw, clocks, peaks, tc):
     """Algorithmic bytes or flops per launch of each kernel class and the dominant one.
@@ -282,7 +330,8 @@ def run_gpu(args, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     kw, W = workload_kwargs(args.workload)
-    kw["dst_variant"] = sc.SCOLA_DST_TC_3XTF32 if args.dst == "tc" else sc.SCOLA_DST_SIMT
+    kw["dst_variant"] = {"tc": sc.SCOLA_DST_TC_3XTF32, "tc4": sc.SCOLA_DST_TC_4XTF32,
+                         "simt": sc.SCOLA_DST_SIMT}[args.dst]
     sim = sc.Scola(**kw)
     stream = torch.cuda.current_stream()
     w_np = synth_inputs.white_noise(kw["Np"], W["seed"] + rank)
@@ -378,7 +427,7 @@ def run_gpu(args, rank, world, local_rank):
     except (OSError, ValueError):
         peaks = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}
         peak_src = "fallback"
-    dom, rows = kernel_roofline(kt, kw, clk, peaks, args.dst == "tc")
+    dom, rows = kernel_roofline(kt, kw, clk, peaks, args.dst != "simt")
     sc.scola_device_status(sim.ctx)
     d = rows[dom]
     roofline = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"],
@@ -388,6 +437,8 @@ def run_gpu(args, rank, world, local_rank):
                 "kernels": {k: {"ms_per_launch": round(v["ms"], 5), "share": round(v["share"], 4),
                                 "frac": round(v["frac"], 4), "bound": v["bound"]}
                             for k, v in rows.items()}}
+
+    adj = adjoint_cost(sc, torch, args.dst, max(2, min(args.steps, 5)))
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -405,9 +456,11 @@ def run_gpu(args, rank, world, local_rank):
                     "particle_steps_per_step": work,
                     "l2": "working set %.2f GB > 129 MB L2, no flush" % (ws_bytes / 1e9),
                     "parallelism": "replicas x%d" % world, "batching": "all boxes per launch, CUDA graph",
-                    "dst": ("dense sine-matrix pencils on tcgen05 tensor cores, 3xTF32"
-                            if args.dst == "tc" else "dense sine-matrix pencils, FP32 CUDA cores")}),
-                "e2e": e2e, "per_tile": per_tile, "gpu_launches": int(launches * args.steps),
+                    "dst": {"tc": "dense sine-matrix pencils on tcgen05 tensor cores, 3xTF32",
+                            "tc4": "dense sine-matrix pencils on tcgen05 tensor cores, 4xTF32",
+                            "simt": "dense sine-matrix pencils, FP32 CUDA cores"}[args.dst]}),
+                "e2e": e2e, "per_tile": per_tile, "adjoint": adj,
+                "gpu_launches": int(launches * args.steps),
                 "clocks": clk,
                 "roofline": roofline, "cpu_baseline": cpu,
                 "stats": {k: v for k, v in sim.stats().items() if k in ("ms_lpt", "ms_evolve", "r", "p")}}

@@ -53,7 +53,8 @@ typedef enum scola_status {
 typedef enum scola_dst_variant {
     SCOLA_DST_SIMT = 0,          /* dense sine-matrix pencils on FP32 CUDA cores */
     SCOLA_DST_TC_3XTF32 = 1,     /* the same products on tcgen05 tensor cores, 3xTF32 split */
-    SCOLA_DST_AUTO = 2           /* the fastest built variant */
+    SCOLA_DST_TC_4XTF32 = 3,     /* as 1, plus the lo x lo product (four TF32 products) */
+    SCOLA_DST_AUTO = 2           /* 4xTF32 tensor cores when every Ng allows it, else FP32 cores */
 } scola_dst_variant;
 
 typedef enum scola_batch_mode {
@@ -83,6 +84,11 @@ typedef enum scola_batch_mode {
  *   fda_order    finite-difference order; only 2 is built
  *   dst_variant  one of scola_dst_variant
  *   batch_mode   one of scola_batch_mode (same results, different launch shapes)
+ *   box_first, box_count  evolve only boxes [box_first, box_first + box_count)
+ *                of the tiling (both 0: all boxes).  Boxes never communicate
+ *                (Sec. 3.2), so several contexts (for example one per GPU) can
+ *                split a run; each writes only its own tiles' particles and
+ *                leaves the other entries of x and p untouched.
  */
 typedef struct scola_params {
     double L;
@@ -95,6 +101,8 @@ typedef struct scola_params {
     int32_t dst_variant;
     int32_t nsteps;
     int32_t batch_mode;
+    int32_t box_first;
+    int32_t box_count;
     int32_t reserved;            /* must be 0 */
     double Om, OL, h, ns, sigma8;
     double a_i, a_f;
@@ -263,6 +271,31 @@ scola_status scola_device_status(scola_ctx *ctx);
 
 /* 1 when the context's Poisson solve runs on the tensor cores, else 0. */
 int32_t scola_uses_tensor_cores(const scola_ctx *ctx);
+
+/*
+ * Adjoint support.  With checkpointing enabled, scola_forward also stores the
+ * displacements of every box particle at every force evaluation (the
+ * per-step checkpoints: (nsteps + 1) x 3 x P floats) and the context keeps
+ * the adjoint work arrays.  Batched form only.  Synchronises the stream.
+ */
+scola_status scola_set_checkpointing(scola_ctx *ctx, int32_t enable);
+
+/*
+ * Gradient of a loss of the final density with respect to the white noise,
+ * for the last scola_forward run on this context (made with checkpointing on).
+ *   lam_delta_dev  device, Np^3 FP32: dLoss/d delta_final, where delta_final
+ *                  is the periodic CIC density of scola_final_density (Sec. 4.1)
+ *                  of that run's positions
+ *   lam_w_dev      device, Np^3 FP32, receives dLoss/dw
+ * Hand-written vector-Jacobian products of every step, in reverse: the
+ * density, the untiling, the KDK sequence with the recomputed mesh force at
+ * each checkpoint (interpolation weights, gradient mesh, the self-adjoint
+ * Dirichlet solve, the boundary source and ghost layers, deposit weights,
+ * App. B-C), L-, the boundary shell (C.3), 2LPT (Eqs. 5-6) and the colouring
+ * (A.1).  Shared accumulations use FP32 atomics, so results can differ in the
+ * last bits between calls.  Errors: STATE without a checkpointed forward run.
+ */
+scola_status scola_backward(scola_ctx *ctx, const float *lam_delta_dev, float *lam_w_dev);
 
 /*
  * Box density without any allocation.  The paper has no counterpart: this is

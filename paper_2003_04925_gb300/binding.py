@@ -17,6 +17,7 @@ c_double, c_int32, c_int64, c_void_p, c_char_p = (ctypes.c_double, ctypes.c_int3
 SCOLA_OK = 0
 SCOLA_DST_SIMT = 0
 SCOLA_DST_TC_3XTF32 = 1
+SCOLA_DST_TC_4XTF32 = 3
 SCOLA_DST_AUTO = 2
 SCOLA_BATCH_ALL = 0
 SCOLA_BATCH_PER_TILE = 1
@@ -33,7 +34,7 @@ class ScolaParams(ctypes.Structure):
         ("L", c_double), ("Np", c_int32), ("Ntiles", c_int32), ("Nbuf", c_int32),
         ("mesh_ratio", c_int32), ("Ng", c_int32), ("fda_order", c_int32),
         ("dst_variant", c_int32), ("nsteps", c_int32), ("batch_mode", c_int32),
-        ("reserved", c_int32),
+        ("box_first", c_int32), ("box_count", c_int32), ("reserved", c_int32),
         ("Om", c_double), ("OL", c_double), ("h", c_double), ("ns", c_double),
         ("sigma8", c_double), ("a_i", c_double), ("a_f", c_double), ("nLPT", c_double),
         ("buffers", ctypes.POINTER(c_int32)),
@@ -73,6 +74,8 @@ _sig = {
     "scola_kernel_times": (c_int32, [c_void_p, _P(c_double), c_int32]),
     "scola_device_status": (c_int32, [c_void_p]),
     "scola_uses_tensor_cores": (c_int32, [c_void_p]),
+    "scola_set_checkpointing": (c_int32, [c_void_p, c_int32]),
+    "scola_backward": (c_int32, [c_void_p, c_void_p, c_void_p]),
     "scola_box_density_noalloc": (c_int32, [c_void_p, c_int32, c_int32, c_double, c_void_p, c_void_p]),
     "scola_status_string": (c_char_p, [c_int32]),
     "scola_last_error": (c_char_p, []),
@@ -109,11 +112,13 @@ def _ptr(x):
 
 def make_params(L, Np, Ntiles, Nbuf=0, mesh_ratio=1, Ng=0, nsteps=10, Om=0.3, OL=0.7, h=0.7,
                 ns=0.96, sigma8=0.8, a_i=0.02, a_f=1.0, nLPT=-2.5, fda_order=2,
-                dst_variant=SCOLA_DST_AUTO, batch_mode=SCOLA_BATCH_ALL, buffers=None):
+                dst_variant=SCOLA_DST_AUTO, batch_mode=SCOLA_BATCH_ALL, buffers=None, box_first=0,
+                box_count=0):
     """Build a ScolaParams; ``buffers`` (per-tile widths) is kept alive on the struct."""
     p = ScolaParams(L=L, Np=Np, Ntiles=Ntiles, Nbuf=Nbuf, mesh_ratio=mesh_ratio, Ng=Ng,
                     fda_order=fda_order, dst_variant=dst_variant, nsteps=nsteps,
-                    batch_mode=batch_mode, reserved=0, Om=Om, OL=OL,
+                    batch_mode=batch_mode, box_first=box_first, box_count=box_count, reserved=0,
+                    Om=Om, OL=OL,
                     h=h, ns=ns, sigma8=sigma8, a_i=a_i, a_f=a_f, nLPT=nLPT)
     if buffers is not None:
         arr = (c_int32 * len(buffers))(*[int(b) for b in buffers])
@@ -227,6 +232,14 @@ def scola_device_status(ctx):
 
 def scola_uses_tensor_cores(ctx):
     return bool(_lib.scola_uses_tensor_cores(ctx))
+
+
+def scola_set_checkpointing(ctx, enable):
+    _check(_lib.scola_set_checkpointing(ctx, 1 if enable else 0), "scola_set_checkpointing")
+
+
+def scola_backward(ctx, lam_delta, lam_w):
+    _check(_lib.scola_backward(ctx, _ptr(lam_delta), _ptr(lam_w)), "scola_backward")
 
 
 def scola_box_density_noalloc(s, nsc, ng, dq, delta, stream=0):

@@ -60,7 +60,7 @@ struct scola_ctx : public Ctx {
 
 namespace {
 
-constexpr bool kAutoUsesTensorCores = false;   // AUTO picks the FP32 form until the TC form is validated
+constexpr bool kAutoUsesTensorCores = true;    // AUTO: four-product tensor-core form where supported
 constexpr int kMaxNg = 192;  // the DST passes hold a (Ng x 32 ceil(Ng/32)) sine matrix in shared memory
 
 struct BoxGeom {
@@ -85,7 +85,7 @@ scola_status validate(const scola_params *p, std::vector<int32_t> &bufs, std::ve
         return SCOLA_ERR_UNSUPPORTED;
     }
     if (p->dst_variant != SCOLA_DST_SIMT && p->dst_variant != SCOLA_DST_TC_3XTF32 &&
-        p->dst_variant != SCOLA_DST_AUTO)
+        p->dst_variant != SCOLA_DST_TC_4XTF32 && p->dst_variant != SCOLA_DST_AUTO)
         return invalid("unknown dst_variant");
     if (p->batch_mode != SCOLA_BATCH_ALL && p->batch_mode != SCOLA_BATCH_PER_TILE)
         return invalid("unknown batch_mode");
@@ -102,6 +102,9 @@ scola_status validate(const scola_params *p, std::vector<int32_t> &bufs, std::ve
         for (long long b = 0; b < nb; ++b) bufs[b] = p->buffers[b];
     }
     if (p->Ng == 0 && p->mesh_ratio < 1) return invalid("mesh_ratio must be >= 1 when Ng == 0");
+    if (p->box_first < 0 || p->box_count < 0 || (long long)p->box_first + p->box_count > nb ||
+        (p->box_count == 0 && p->box_first != 0))
+        return invalid("box_first/box_count must select a range of boxes (or both be 0)");
     const int ntile = p->Np / p->Ntiles;
     geo.resize(nb);
     for (long long b = 0; b < nb; ++b) {
@@ -114,7 +117,8 @@ scola_status validate(const scola_params *p, std::vector<int32_t> &bufs, std::ve
             set_error("Ng > 192 is not built");
             return SCOLA_ERR_UNSUPPORTED;
         }
-        if (for_kernels && p->dst_variant == SCOLA_DST_TC_3XTF32 && !tc_supported(ng)) {
+        if (for_kernels && (p->dst_variant == SCOLA_DST_TC_3XTF32 || p->dst_variant == SCOLA_DST_TC_4XTF32) &&
+            !tc_supported(ng)) {
             set_error("the tensor-core DST needs Ng % 4 == 0 and Ng <= 128");
             return SCOLA_ERR_UNSUPPORTED;
         }
@@ -148,8 +152,12 @@ void add_chunks(std::vector<Chunk> &v, int box, long long n, int per) {
     for (long long s = 0; s < n; s += per) v.push_back({box, (int)s});
 }
 
-scola_status build(scola_ctx *c, const std::vector<BoxGeom> &geo) {
+scola_status build(scola_ctx *c, const std::vector<BoxGeom> &all_geo) {
     const scola_params &p = c->prm;
+    // the boxes this context evolves: all, or the range [box_first, box_first + box_count)
+    const int first = p.box_count ? p.box_first : 0;
+    const int count = p.box_count ? p.box_count : (int)all_geo.size();
+    const std::vector<BoxGeom> geo(all_geo.begin() + first, all_geo.begin() + first + count);
     c->Np = p.Np;
     c->Ntiles = p.Ntiles;
     c->nboxes = (int)geo.size();
@@ -195,7 +203,7 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &geo) {
     }
 
     // boxes and work lists
-    std::vector<Chunk> pch, tch, shch, zit, cit, mch;
+    std::vector<Chunk> pch, tch, shch, zit, cit, mch, ppch;
     long long P = 0, M = 0, MP = 0, SH = 0;
     std::map<int, double> dg_of_ng;
     for (int b = 0; b < c->nboxes; ++b) {
@@ -203,6 +211,7 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &geo) {
         c->shbeg.push_back((int)shch.size());
         c->zbeg.push_back((int)zit.size());
         c->cbeg.push_back((int)cit.size());
+        c->mbeg.push_back((int)mch.size());
         const BoxGeom &g = geo[b];
         BoxDesc B;
         std::memset(&B, 0, sizeof(B));
@@ -210,9 +219,10 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &geo) {
         B.Ng = g.ng;
         B.Nbuf = g.nbuf;
         B.tbl = tbl_of[g.ng];
-        B.tx = b / (p.Ntiles * p.Ntiles);
-        B.ty = (b / p.Ntiles) % p.Ntiles;
-        B.tz = b % p.Ntiles;
+        const int gb = first + b;                      // box id in the whole tiling
+        B.tx = gb / (p.Ntiles * p.Ntiles);
+        B.ty = (gb / p.Ntiles) % p.Ntiles;
+        B.tz = gb % p.Ntiles;
         B.p_off = P;
         B.m_off = M;
         B.pp_off = MP;
@@ -235,6 +245,7 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &geo) {
         add_chunks(tch, b, (long long)ntile * ntile * ntile, kChunk);
         add_chunks(shch, b, np3 - ng3, kChunk);
         add_chunks(mch, b, ng3, kChunk);
+        add_chunks(ppch, b, np3, kChunk);
         const long long nz = ((long long)g.ng * g.ng + kTC - 1) / kTC;
         for (long long t = 0; t < nz; ++t) zit.push_back({b, (int)t});
         const long long nc = (long long)g.ng * ((g.ng + kTC - 1) / kTC);
@@ -258,6 +269,7 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &geo) {
     c->shbeg.push_back((int)shch.size());
     c->zbeg.push_back((int)zit.size());
     c->cbeg.push_back((int)cit.size());
+    c->mbeg.push_back((int)mch.size());
     for (auto &T : c->tables_h) {
         const double dg = dg_of_ng[T.Ng];
         for (int l = 0; l < T.Ng; ++l) {
@@ -279,16 +291,18 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &geo) {
     c->n_zitems = (int)zit.size();
     c->n_citems = (int)cit.size();
     c->n_mchunks = (int)mch.size();
+    c->n_ppchunks = (int)ppch.size();
     double r = 0;
-    for (const auto &g : geo) r += std::pow((double)g.nsc, 3);
+    for (const auto &g : all_geo) r += std::pow((double)g.nsc, 3);
     c->r = r / (double)c->N3;
-    c->p = c->nboxes / c->r;
+    c->p = (double)all_geo.size() / c->r;
 
     // tensor-core DST groups (one per distinct Ng): tiles and the FP32 sine matrix
     bool all_tc = true;
     for (auto &kv : tbl_of) all_tc = all_tc && tc_supported(kv.first);
-    c->use_tc = (p.dst_variant == SCOLA_DST_TC_3XTF32) || (p.dst_variant == SCOLA_DST_AUTO && all_tc &&
-                                                           kAutoUsesTensorCores);
+    c->use_tc = (p.dst_variant == SCOLA_DST_TC_3XTF32) || (p.dst_variant == SCOLA_DST_TC_4XTF32) ||
+                (p.dst_variant == SCOLA_DST_AUTO && all_tc && kAutoUsesTensorCores);
+    c->tc_lo_lo = p.dst_variant == SCOLA_DST_TC_4XTF32 || p.dst_variant == SCOLA_DST_AUTO;
     std::vector<Chunk> tct;
     std::vector<int> box_tile_beg(c->nboxes, 0), box_tile_end(c->nboxes, 0);
     if (c->use_tc) {
@@ -332,6 +346,7 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &geo) {
     CS(upload(&c->zitems, zit));
     CS(upload(&c->citems, cit));
     CS(upload(&c->mchunks, mch));
+    CS(upload(&c->ppchunks, ppch));
     if (c->use_tc) {
         CS(upload(&c->tc_tiles, tct));
         for (auto &G : c->tc_groups) G.tiles = c->tc_tiles + reinterpret_cast<long long>(G.tiles);
@@ -429,15 +444,18 @@ KickDrift kick_drift_coefficients(const TimeTable &t, int k) {
 // Restricts every work list (and the accumulator clear) to one box; restores on destruction.
 struct BoxView {
     scola_ctx *c;
-    Chunk *pch, *sh, *z, *cl;
-    int npch, nsh, nz, ncl;
+    Chunk *pch, *sh, *z, *cl, *mc;
+    int npch, nsh, nz, ncl, nmc;
     long long off, len;
     int tcv;
     BoxView(scola_ctx *cc, int b) : c(cc) {
         tcv = c->tc_view_box;
         c->tc_view_box = b;
-        pch = c->pchunks; sh = c->shchunks; z = c->zitems; cl = c->citems;
+        pch = c->pchunks; sh = c->shchunks; z = c->zitems; cl = c->citems; mc = c->mchunks;
         npch = c->n_pchunks; nsh = c->n_shchunks; nz = c->n_zitems; ncl = c->n_citems;
+        nmc = c->n_mchunks;
+        c->mchunks = mc + c->mbeg[b];
+        c->n_mchunks = c->mbeg[b + 1] - c->mbeg[b];
         off = c->acc_clear_off; len = c->acc_clear_len;
         c->pchunks = pch + c->pbeg[b];
         c->n_pchunks = c->pbeg[b + 1] - c->pbeg[b];
@@ -452,8 +470,9 @@ struct BoxView {
         c->acc_clear_len = (long long)B.Ng * B.Ng * B.Ng;
     }
     ~BoxView() {
-        c->pchunks = pch; c->shchunks = sh; c->zitems = z; c->citems = cl;
+        c->pchunks = pch; c->shchunks = sh; c->zitems = z; c->citems = cl; c->mchunks = mc;
         c->n_pchunks = npch; c->n_shchunks = nsh; c->n_zitems = nz; c->n_citems = ncl;
+        c->n_mchunks = nmc;
         c->acc_clear_off = off; c->acc_clear_len = len;
         c->tc_view_box = tcv;
     }
@@ -491,6 +510,9 @@ scola_status enqueue_evolution(scola_ctx *c) {
         return cudaEventRecordWithFlags(c->prof_ev[ei++], c->stream, cudaEventRecordExternal);
     };
     for (int k = 0; k <= n; ++k) {
+        if (c->checkpointing)
+            CK(cudaMemcpyAsync(c->ckpt + (size_t)k * 3 * c->P, c->part, sizeof(float) * 3 * (size_t)c->P,
+                               cudaMemcpyDeviceToDevice, c->stream));
         CK(mark());
         CK(launch_pad(*c, (float)c->tt.D1[k]));
         CK(mark());
@@ -629,7 +651,9 @@ void scola_destroy(scola_ctx *c) {
         cufftDestroy(c->plan_c2r);
     }
     void *ptrs[] = {c->boxes, c->tables, c->table_arena, c->pchunks, c->tchunks, c->shchunks,
-                    c->zitems, c->citems, c->mchunks, c->tc_tiles, c->dev_err, c->part, c->acc, c->work, c->work2, c->phi,
+                    c->zitems, c->citems, c->mchunks, c->ppchunks, c->tc_tiles, c->dev_err, c->ckpt,
+                    c->adj, c->lamG, c->lam_phi_pad, c->adj_in, c->adj_out, c->lam_shell, c->lamPsi1,
+                    c->lamPsi2, c->lam_phi1, c->lam_phi2, c->d2, c->lam_d2, c->part, c->acc, c->work, c->work2, c->phi,
                     c->shell, c->ck, c->cp, c->ct, c->g[0], c->g[1], c->g[2], c->g[3], c->phi1,
                     c->phi2, c->psi1, c->psi2, c->dens_acc, c->w_h2d, c->x_h2d, c->p_h2d};
     for (void *q : ptrs)
@@ -705,7 +729,95 @@ scola_status scola_forward(scola_ctx *c, const float *w, float *x, float *p) {
     CK(launch_scatter(*c, x, p));
     CK(cudaEventRecord(c->ev[2], c->stream));
     c->setup_done = true;
+    c->have_forward = true;
     c->stats.kernel_launches = (c->launches - before) + c->graph_kernels;
+    return SCOLA_OK;
+}
+
+scola_status scola_set_checkpointing(scola_ctx *c, int32_t enable) {
+    if (!c) return invalid("NULL context");
+    const bool on = enable != 0;
+    if (on && c->prm.batch_mode == SCOLA_BATCH_PER_TILE) {
+        set_error("the adjoint runs on the batched form only");
+        return SCOLA_ERR_UNSUPPORTED;
+    }
+    if (on == c->checkpointing) return SCOLA_OK;
+    CK(c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize());
+    if (c->evolve_exec) {
+        CK(cudaGraphExecDestroy(c->evolve_exec));
+        c->evolve_exec = nullptr;
+    }
+    c->checkpointing = on;
+    c->have_forward = false;
+    if (on && !c->ckpt) {
+        const long long P = c->P, N3 = c->N3;
+        CS(dev_alloc(&c->ckpt, (long long)(c->prm.nsteps + 1) * 3 * P));
+        CS(dev_alloc(&c->adj, 15 * P));
+        CS(dev_alloc(&c->lamG, 3 * c->MP));
+        CS(dev_alloc(&c->lam_phi_pad, c->MP));
+        CS(dev_alloc(&c->adj_in, c->M));
+        CS(dev_alloc(&c->adj_out, c->MP));
+        CS(dev_alloc(&c->lam_shell, c->SH));
+        CS(dev_alloc(&c->lamPsi1, 3 * N3));
+        CS(dev_alloc(&c->lamPsi2, 3 * N3));
+        CS(dev_alloc(&c->lam_phi1, N3));
+        CS(dev_alloc(&c->lam_phi2, N3));
+        CS(dev_alloc(&c->d2, 6 * N3));
+        CS(dev_alloc(&c->lam_d2, 6 * N3));
+    }
+    return SCOLA_OK;
+}
+
+scola_status scola_backward(scola_ctx *c, const float *lam_delta, float *lam_w) {
+    if (!c || !lam_delta || !lam_w) return invalid("NULL argument");
+    if (!c->checkpointing || !c->have_forward) {
+        set_error("scola_backward needs checkpointing enabled before the forward run it differentiates");
+        return SCOLA_ERR_STATE;
+    }
+    const long long P = c->P, N3 = c->N3;
+    const size_t fb = sizeof(float);
+    CK(cudaMemsetAsync(c->adj, 0, fb * 15 * P, c->stream));
+    CK(cudaMemsetAsync(c->lam_shell, 0, fb * c->SH, c->stream));
+    CK(cudaMemsetAsync(c->lamPsi1, 0, fb * 3 * N3, c->stream));
+    CK(cudaMemsetAsync(c->lamPsi2, 0, fb * 3 * N3, c->stream));
+    CK(cudaMemsetAsync(c->lam_phi1, 0, fb * N3, c->stream));
+    // final density -> tile particles
+    CK(launch_adj_final(*c, lam_delta, c->adj));
+    const int n = (int)c->tt.alpha.size();
+    for (int k = n; k >= 0; --k) {
+        CK(launch_adj_kick_drift(*c, c->adj, kick_drift_coefficients(c->tt, k)));
+        const float *sk = c->ckpt + (size_t)k * 3 * P;
+        CK(launch_pad(*c, (float)c->tt.D1[k]));
+        CK(launch_deposit(*c, sk, P));
+        CK(launch_poisson(*c));
+        CK(cudaMemsetAsync(c->lamG, 0, fb * 3 * c->MP, c->stream));
+        CK(launch_adj_interp(*c, sk, c->adj, c->lamG));
+        CK(launch_adj_div(*c, c->lamG, c->lam_phi_pad, c->adj_in));
+        CK(launch_poisson_buffers(*c, c->adj_in, false, c->work, c->work2, c->adj_out));
+        CK(launch_adj_shell(*c, c->lam_phi_pad, c->adj_out, (float)c->tt.D1[k], c->lam_shell));
+        CK(launch_adj_deposit(*c, sk, c->adj_out, c->adj));
+    }
+    CK(launch_adj_init_scatter(*c, c->adj, c->lamPsi1, c->lamPsi2));
+    CK(launch_adj_shell_to_phi1(*c, c->lam_shell, c->lam_phi1));
+    // full-box 2LPT and colouring adjoints (symmetric Fourier operators)
+    CK(launch_neg_div(*c, c->lamPsi1, 1, c->lam_phi1));
+    CK(launch_neg_div(*c, c->lamPsi2, 0, c->lam_phi2));
+    CF(cufftExecR2C(c->plan_r2c, c->lam_phi2, c->ct));
+    CK(launch_inv_laplacian(*c, c->ct, c->ct, (float)(1.0 / (double)N3)));
+    CF(cufftExecC2R(c->plan_c2r, c->ct, c->g[0]));                // lam_S
+    const int pairs[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+    for (int q = 0; q < 6; ++q) {
+        CK(launch_second_derivative(*c, c->cp, c->ct, pairs[q][0], pairs[q][1]));
+        CF(cufftExecC2R(c->plan_c2r, c->ct, c->d2 + (size_t)q * N3));
+    }
+    CK(launch_adj_source(*c, c->g[0], c->d2, c->lam_d2));
+    CF(cufftExecR2C(c->plan_r2c, c->lam_phi1, c->ck));
+    for (int q = 0; q < 6; ++q) {
+        CF(cufftExecR2C(c->plan_r2c, c->lam_d2 + (size_t)q * N3, c->ct));
+        CK(launch_spec_d2_accumulate(*c, c->ct, c->ck, pairs[q][0], pairs[q][1]));
+    }
+    CK(launch_adj_colour(*c, c->ck, c->ct));
+    CF(cufftExecC2R(c->plan_c2r, c->ct, lam_w));
     return SCOLA_OK;
 }
 

@@ -108,9 +108,10 @@ struct Ctx {
     long long sin_half_off = 0, sin_full_off = 0;     // LPT-grid sine tables in table_arena
     long long acc_clear_off = 0, acc_clear_len = 0;   // accumulator range the deposit clears
     // first entry of each box in every work list (size nboxes + 1), for per-tile launches
-    std::vector<int> pbeg, shbeg, zbeg, cbeg;
+    std::vector<int> pbeg, shbeg, zbeg, cbeg, mbeg;
     int num_sms = 1, dst_ctas_per_sm = 1;
     bool use_tc = false;                              // tensor-core (3xTF32) DST passes
+    bool tc_lo_lo = false;                            // four-product TF32 form
     std::vector<TcGroup> tc_groups;
     Chunk *tc_tiles = nullptr;
     std::vector<int> tc_tile_beg, tc_tile_end;        // each box's tile range in tc_tiles
@@ -127,6 +128,15 @@ struct Ctx {
     cufftHandle plan_r2c = 0, plan_c2r = 0;
     bool have_plans = false;
     unsigned long long *dens_acc = nullptr;
+
+    // adjoint (scola_set_checkpointing / scola_backward)
+    bool checkpointing = false, have_forward = false;
+    float *ckpt = nullptr;                            // (nsteps+1) x 3 x P displacements
+    float *adj = nullptr;                             // 15 x P backward particle state
+    float *lamG = nullptr, *lam_phi_pad = nullptr, *adj_in = nullptr, *adj_out = nullptr;
+    float *lam_shell = nullptr, *lamPsi1 = nullptr, *lamPsi2 = nullptr;
+    float *lam_phi1 = nullptr, *lam_phi2 = nullptr, *d2 = nullptr, *lam_d2 = nullptr;
+    Chunk *ppchunks = nullptr; int n_ppchunks = 0;    // padded mesh cells
 
     cudaGraphExec_t evolve_exec = nullptr;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -153,14 +163,33 @@ bool tc_supported(int Ng);
 cudaError_t init_tc_kernels();
 cudaError_t launch_poisson_tc(Ctx &c);
 cudaError_t launch_poisson_tc_pass(Ctx &c, int pass);
+cudaError_t launch_poisson_tc_buffers(Ctx &c, const void *in, bool in_acc, float *w1, float *w2,
+                                      float *out_pad);
+cudaError_t launch_poisson_buffers(Ctx &c, const void *in, bool in_acc, float *w1, float *w2,
+                                   float *out_pad);
 cudaError_t launch_poisson(Ctx &c);
 cudaError_t launch_poisson_pass(Ctx &c, int pass);
 cudaError_t launch_acc_to_delta(Ctx &c, float *out);
+cudaError_t launch_density_source(Ctx &c, float *out);
 cudaError_t launch_interp(Ctx &c, const float *s, long long stride, float *F);
 cudaError_t launch_kick_drift(Ctx &c, const KickDrift &kd);
 cudaError_t launch_scatter(Ctx &c, float *x, float *p);
 cudaError_t launch_box_ids(Ctx &c, int64_t *gid);
 cudaError_t launch_final_density(Ctx &c, const float *x, float *delta);
+
+cudaError_t launch_adj_colour(Ctx &c, const cufftComplex *in, cufftComplex *out);
+cudaError_t launch_adj_final(Ctx &c, const float *lam_delta, float *adj);
+cudaError_t launch_adj_kick_drift(Ctx &c, float *adj, const KickDrift &kd);
+cudaError_t launch_adj_interp(Ctx &c, const float *s, float *adj, float *lamG);
+cudaError_t launch_adj_div(Ctx &c, const float *lamG, float *lam_phi_pad, float *interior_out);
+cudaError_t launch_adj_shell(Ctx &c, const float *lam_phi_pad, const float *lam_src_pad, float D1,
+                             float *lam_shell);
+cudaError_t launch_adj_deposit(Ctx &c, const float *s, const float *lam_src_pad, float *adj);
+cudaError_t launch_adj_init_scatter(Ctx &c, const float *adj, float *lamPsi1, float *lamPsi2);
+cudaError_t launch_adj_shell_to_phi1(Ctx &c, const float *lam_shell, float *lam_phi1);
+cudaError_t launch_neg_div(Ctx &c, const float *g, int accumulate, float *out);
+cudaError_t launch_adj_source(Ctx &c, const float *lamS, const float *d2, float *lam_d2);
+cudaError_t launch_spec_d2_accumulate(Ctx &c, const cufftComplex *in, cufftComplex *acc, int i, int j);
 
 void set_error(const std::string &msg);
 

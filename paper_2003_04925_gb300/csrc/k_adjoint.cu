@@ -1,0 +1,475 @@
+// Adjoint (vector-Jacobian products) of the sCOLA forward run, for the gradient of a
+// loss of the final density with respect to the white noise.
+//
+// Per box particle the backward state is 5 rows of 3 x P floats (adj arena):
+//   lam_s (0..2), lam_p (3..5), lam_Psi1 (6..8), lam_Psi2 (9..11), lam_F (12..14).
+// Reverse KDK (App. B, Eqs. 53-54), at every force evaluation k = n .. 0:
+//   drift  s += alpha p + d1 Psi1 + d2 Psi2   -> lam_p += alpha lam_s, lam_Psi += d lam_s
+//   kick   p += kF F + k1 Psi1 + k2 Psi2      -> lam_F = kF lam_p,   lam_Psi += k lam_p
+//   force  F(s_k): recomputed mesh potential at the checkpointed s_k, then
+//     k_adj_interp   lam_s += (d weights / ds) (G . lam_F)   (direct term, clamp aware)
+//                    lam_G += weights * lam_F                (3 channels, padded grid)
+//     k_adj_div      lam_Phi = -div lam_G (transpose of the central difference);
+//                    interior part -> Dirichlet solve (self-adjoint), ghosts kept
+//     k_adj_shell    lam_shell += D1(a_k) (lam_Phi_ghost - boundary-source transpose)
+//     k_adj_deposit  lam_s += (d deposit weights / ds) lam_delta'
+// then L-: lam_Psi1 -= D1(a_i) lam_s, lam_Psi2 += D2(a_i) lam_s, scattered to the
+// full-box arrays, and the shells' adjoint scattered to phi1 (trilinear transpose).
+// The 2LPT and colouring adjoints (Fourier, symmetric operators) are in capi.cu.
+// Accumulations shared between particles use FP32 atomics (sum order varies).
+#include "device_util.cuh"
+
+namespace scola {
+
+namespace {
+
+__device__ __forceinline__ void corner_setup(const BoxDesc &B, const int b[3], const float s[3],
+                                             float lo, float hi, int cap, int i0[3], float f[3],
+                                             float free_[3]) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float u_raw = fmaf(s[a], B.inv_dg, fmaf((float)b[a], B.q2u, 0.5f * B.q2u - 0.5f));
+        const float u = fminf(fmaxf(u_raw, lo), hi);
+        free_[a] = (u == u_raw) ? 1.0f : 0.0f;
+        int fl = (int)floorf(u);
+        fl = min(fl, cap);
+        i0[a] = fl;
+        f[a] = u - (float)fl;
+    }
+}
+
+// Final tile particles: lam_s = d(periodic CIC density)/dx^T lam_delta (Sec. 4.1).
+__global__ void __launch_bounds__(kChunk)
+k_adj_final(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
+            const float *__restrict__ part, long long P, int Np, int Ntile, float dq, float L,
+            const float *__restrict__ lam_delta, float *__restrict__ adj) {
+    const Chunk ch = chunks[blockIdx.x];
+    const BoxDesc &B = boxes[ch.box];
+    const int lt = ch.start + threadIdx.x;
+    if (lt >= Ntile * Ntile * Ntile) return;
+    int ti, tj, tk;
+    decode_local(lt, Ntile, ti, tj, tk);
+    const int Nsc = B.Nsc;
+    const long long gi = B.p_off + ((long long)(ti + B.Nbuf) * Nsc + (tj + B.Nbuf)) * Nsc + (tk + B.Nbuf);
+    const int g[3] = {B.tx * Ntile + ti, B.ty * Ntile + tj, B.tz * Ntile + tk};
+    const float invL = 1.0f / L, inv_d = (float)Np / L;
+    int i0[3];
+    float f[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float xv = ((float)g[a] + 0.5f) * dq + part[a * P + gi];
+        xv -= L * floorf(xv * invL);
+        if (xv >= L) xv -= L;
+        if (xv < 0.0f) xv += L;
+        const float u = xv * inv_d - 0.5f;
+        const float fl = floorf(u);
+        i0[a] = (int)fl;
+        f[a] = u - fl;
+    }
+    const long long NN = (long long)Np * Np;
+    float lam[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int dx = 0; dx < 2; ++dx)
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+            for (int dz = 0; dz < 2; ++dz) {
+                const float wx = dx ? f[0] : 1.f - f[0], wy = dy ? f[1] : 1.f - f[1],
+                            wz = dz ? f[2] : 1.f - f[2];
+                const float v = lam_delta[wrap(i0[0] + dx, Np) * NN + (long long)wrap(i0[1] + dy, Np) * Np +
+                                          wrap(i0[2] + dz, Np)];
+                lam[0] += (dx ? 1.f : -1.f) * wy * wz * v;
+                lam[1] += wx * (dy ? 1.f : -1.f) * wz * v;
+                lam[2] += wx * wy * (dz ? 1.f : -1.f) * v;
+            }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) adj[a * P + gi] = lam[a] * inv_d;
+}
+
+__global__ void __launch_bounds__(kChunk)
+k_adj_kick_drift(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
+                 float *__restrict__ adj, long long P, KickDrift kd) {
+    const Chunk ch = chunks[blockIdx.x];
+    const BoxDesc &B = boxes[ch.box];
+    const int local = ch.start + threadIdx.x;
+    if (local >= B.Nsc * B.Nsc * B.Nsc) return;
+    const long long gi = B.p_off + local;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float ls = adj[a * P + gi];
+        float lp = adj[(3 + a) * P + gi];
+        float l1 = adj[(6 + a) * P + gi];
+        float l2 = adj[(9 + a) * P + gi];
+        if (kd.drift) {
+            lp = fmaf(kd.alpha, ls, lp);
+            l1 = fmaf(kd.d1, ls, l1);
+            l2 = fmaf(kd.d2, ls, l2);
+        }
+        l1 = fmaf(kd.k1, lp, l1);
+        l2 = fmaf(kd.k2, lp, l2);
+        adj[(3 + a) * P + gi] = lp;
+        adj[(6 + a) * P + gi] = l1;
+        adj[(9 + a) * P + gi] = l2;
+        adj[(12 + a) * P + gi] = kd.kF * lp;
+    }
+}
+
+__global__ void __launch_bounds__(kChunk)
+k_adj_interp(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
+             const float *__restrict__ s, long long P, const float *__restrict__ phi,
+             float *__restrict__ adj, float *__restrict__ lamG, long long MP) {
+    const Chunk ch = chunks[blockIdx.x];
+    const BoxDesc &B = boxes[ch.box];
+    const int Nsc = B.Nsc, Ng = B.Ng;
+    const int local = ch.start + threadIdx.x;
+    if (local >= Nsc * Nsc * Nsc) return;
+    const long long gi = B.p_off + local;
+    int b[3];
+    decode_local(local, Nsc, b[0], b[1], b[2]);
+    const float sv[3] = {s[gi], s[P + gi], s[2 * P + gi]};
+    const float lF[3] = {adj[12 * P + gi], adj[13 * P + gi], adj[14 * P + gi]};
+    int i0[3];
+    float f[3], fr[3];
+    corner_setup(B, b, sv, -1.0f, (float)Ng, Ng - 1, i0, f, fr);
+    const long long S1 = Ng + 4, S2 = S1 * S1;
+    const long long base = B.pp_off + ((long long)(i0[0] + 2) * S1 + (i0[1] + 2)) * S1 + (i0[2] + 2);
+    const float *Pp = phi + base;
+    const float h = 0.5f * B.inv_dg;
+    float dir[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int dx = 0; dx < 2; ++dx)
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+            for (int dz = 0; dz < 2; ++dz) {
+                const long long o = dx * S2 + dy * S1 + dz;
+                const float G0 = (Pp[o + S2] - Pp[o - S2]) * h;
+                const float G1 = (Pp[o + S1] - Pp[o - S1]) * h;
+                const float G2 = (Pp[o + 1] - Pp[o - 1]) * h;
+                const float gl = G0 * lF[0] + G1 * lF[1] + G2 * lF[2];
+                const float wx = dx ? f[0] : 1.f - f[0], wy = dy ? f[1] : 1.f - f[1],
+                            wz = dz ? f[2] : 1.f - f[2];
+                dir[0] += (dx ? 1.f : -1.f) * wy * wz * gl;
+                dir[1] += wx * (dy ? 1.f : -1.f) * wz * gl;
+                dir[2] += wx * wy * (dz ? 1.f : -1.f) * gl;
+                const float w = wx * wy * wz;
+                atomicAdd(lamG + base + o, w * lF[0]);
+                atomicAdd(lamG + MP + base + o, w * lF[1]);
+                atomicAdd(lamG + 2 * MP + base + o, w * lF[2]);
+            }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) adj[a * P + gi] += dir[a] * fr[a] * B.inv_dg;
+}
+
+// lam_Phi(c) = sum_a (lam_G_a(c - e_a) - lam_G_a(c + e_a)) / (2 dg) over the padded grid.
+__global__ void __launch_bounds__(kChunk)
+k_adj_div(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
+          const float *__restrict__ lamG, long long MP, float *__restrict__ lam_phi_pad,
+          float *__restrict__ interior_out) {
+    const Chunk ch = chunks[blockIdx.x];
+    const BoxDesc &B = boxes[ch.box];
+    const int Ng = B.Ng, S = Ng + 4;
+    const long long n = (long long)S * S * S;
+    const long long idx = (long long)ch.start + threadIdx.x;
+    if (idx >= n) return;
+    int p[3];
+    decode_local((int)idx, S, p[0], p[1], p[2]);
+    const long long strides[3] = {(long long)S * S, S, 1};
+    const long long here = B.pp_off + idx;
+    float v = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float *G = lamG + a * MP;
+        if (p[a] > 0) v += G[here - strides[a]];
+        if (p[a] < S - 1) v -= G[here + strides[a]];
+    }
+    v *= 0.5f * B.inv_dg;
+    const bool inside = p[0] >= 2 && p[0] < Ng + 2 && p[1] >= 2 && p[1] < Ng + 2 && p[2] >= 2 && p[2] < Ng + 2;
+    if (inside)
+        interior_out[B.m_off + ((long long)(p[0] - 2) * Ng + (p[1] - 2)) * Ng + (p[2] - 2)] = v;
+    else
+        lam_phi_pad[here] = v;
+}
+
+// lam_shell += D1 (lam_Phi_ghost - transpose of the boundary source of Eq. 62).
+__global__ void __launch_bounds__(kChunk)
+k_adj_shell(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
+            const float *__restrict__ lam_phi_pad, const float *__restrict__ lam_src_pad, float D1,
+            float *__restrict__ lam_shell) {
+    const Chunk ch = chunks[blockIdx.x];
+    const BoxDesc &B = boxes[ch.box];
+    const int Ng = B.Ng;
+    const long long idx = (long long)ch.start + threadIdx.x;
+    if (idx >= shell_count(Ng)) return;
+    int p[3];
+    shell_coord(idx, Ng, p[0], p[1], p[2]);
+    const long long S = Ng + 4;
+    const long long strides[3] = {S * S, S, 1};
+    const long long here = B.pp_off + ((long long)p[0] * S + p[1]) * S + p[2];
+    float v = lam_phi_pad[here];
+    const float c2 = B.inv_dg * B.inv_dg;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int o1 = (a + 1) % 3, o2 = (a + 2) % 3;
+        const bool others = p[o1] >= 2 && p[o1] < Ng + 2 && p[o2] >= 2 && p[o2] < Ng + 2;
+        if (!others) continue;
+        if (p[a] == 1) v -= lam_src_pad[here + strides[a]] * c2;
+        if (p[a] == Ng + 2) v -= lam_src_pad[here - strides[a]] * c2;
+    }
+    lam_shell[B.sh_off + idx] += D1 * v;
+}
+
+__global__ void __launch_bounds__(kChunk)
+k_adj_deposit(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
+              const float *__restrict__ s, long long P, const float *__restrict__ lam_src_pad,
+              float *__restrict__ adj) {
+    const Chunk ch = chunks[blockIdx.x];
+    const BoxDesc &B = boxes[ch.box];
+    const int Nsc = B.Nsc, Ng = B.Ng;
+    const int local = ch.start + threadIdx.x;
+    if (local >= Nsc * Nsc * Nsc) return;
+    const long long gi = B.p_off + local;
+    int b[3];
+    decode_local(local, Nsc, b[0], b[1], b[2]);
+    const float sv[3] = {s[gi], s[P + gi], s[2 * P + gi]};
+    int i0[3];
+    float f[3], fr[3];
+    corner_setup(B, b, sv, -2.0f, (float)Ng + 1.0f, Ng + 1, i0, f, fr);
+    const long long S = Ng + 4;
+    float lam[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int dx = 0; dx < 2; ++dx) {
+        const int cx = i0[0] + dx;
+        if ((unsigned)cx >= (unsigned)Ng) continue;
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy) {
+            const int cy = i0[1] + dy;
+            if ((unsigned)cy >= (unsigned)Ng) continue;
+#pragma unroll
+            for (int dz = 0; dz < 2; ++dz) {
+                const int cz = i0[2] + dz;
+                if ((unsigned)cz >= (unsigned)Ng) continue;
+                const float v = lam_src_pad[B.pp_off + ((long long)(cx + 2) * S + (cy + 2)) * S + (cz + 2)];
+                const float wx = dx ? f[0] : 1.f - f[0], wy = dy ? f[1] : 1.f - f[1],
+                            wz = dz ? f[2] : 1.f - f[2];
+                lam[0] += (dx ? 1.f : -1.f) * wy * wz * v;
+                lam[1] += wx * (dy ? 1.f : -1.f) * wz * v;
+                lam[2] += wx * wy * (dz ? 1.f : -1.f) * v;
+            }
+        }
+    }
+    const float sc = B.nbar_inv * B.inv_dg;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) adj[a * P + gi] += lam[a] * sc * fr[a];
+}
+
+// L- adjoint and scatter of lam_Psi1, lam_Psi2 to the full-box arrays (3 x N^3 each).
+__global__ void __launch_bounds__(kChunk)
+k_adj_init_scatter(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
+                   const float *__restrict__ adj, long long P, int Np, int Ntile, long long N3,
+                   float D1i, float D2i, float *__restrict__ lamPsi1, float *__restrict__ lamPsi2) {
+    const Chunk ch = chunks[blockIdx.x];
+    const BoxDesc &B = boxes[ch.box];
+    const int Nsc = B.Nsc;
+    const int local = ch.start + threadIdx.x;
+    if (local >= Nsc * Nsc * Nsc) return;
+    const long long gi = B.p_off + local;
+    int bi, bj, bk;
+    decode_local(local, Nsc, bi, bj, bk);
+    const int gx = wrap(B.tx * Ntile - B.Nbuf + bi, Np);
+    const int gy = wrap(B.ty * Ntile - B.Nbuf + bj, Np);
+    const int gz = wrap(B.tz * Ntile - B.Nbuf + bk, Np);
+    const long long gid = ((long long)gx * Np + gy) * Np + gz;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float ls = adj[a * P + gi];
+        atomicAdd(lamPsi1 + a * N3 + gid, adj[(6 + a) * P + gi] - D1i * ls);
+        atomicAdd(lamPsi2 + a * N3 + gid, adj[(9 + a) * P + gi] + D2i * ls);
+    }
+}
+
+// Trilinear transpose of C.3: lam_phi1 += sum over shell cells of weights * lam_shell.
+__global__ void __launch_bounds__(kChunk)
+k_adj_shell_to_phi1(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
+                    const float *__restrict__ lam_shell, int N, double d_lpt,
+                    float *__restrict__ lam_phi1) {
+    const Chunk ch = chunks[blockIdx.x];
+    const BoxDesc &B = boxes[ch.box];
+    const long long idx = (long long)ch.start + threadIdx.x;
+    if (idx >= shell_count(B.Ng)) return;
+    const float lv = lam_shell[B.sh_off + idx];
+    if (lv == 0.0f) return;
+    int pc[3];
+    shell_coord(idx, B.Ng, pc[0], pc[1], pc[2]);
+    int i0[3];
+    double f[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double X = B.origin_d[a] + ((double)(pc[a] - 2) + 0.5) * B.dg_d;
+        const double u = X / d_lpt - 0.5;
+        const double fl = floor(u);
+        i0[a] = (int)fl;
+        f[a] = u - fl;
+    }
+    const long long NN = (long long)N * N;
+#pragma unroll
+    for (int dx = 0; dx < 2; ++dx)
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+            for (int dz = 0; dz < 2; ++dz) {
+                const double w = (dx ? f[0] : 1.0 - f[0]) * (dy ? f[1] : 1.0 - f[1]) * (dz ? f[2] : 1.0 - f[2]);
+                atomicAdd(lam_phi1 + wrap(i0[0] + dx, N) * NN + (long long)wrap(i0[1] + dy, N) * N +
+                              wrap(i0[2] + dz, N),
+                          (float)(w * lv));
+            }
+}
+
+// out = -sum_a central_difference_a(g_a) (+ out when accumulate): transpose of the gradient.
+__global__ void k_neg_div(const float *__restrict__ g, int N, float inv_2d, int accumulate,
+                          float *__restrict__ out) {
+    const long long N3 = (long long)N * N * N;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < N3;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(idx % N);
+        const long long t = idx / N;
+        const int j = (int)(t % N);
+        const int i = (int)(t / N);
+        const long long NN = (long long)N * N;
+        const int ip = i + 1 == N ? 0 : i + 1, im = i == 0 ? N - 1 : i - 1;
+        const int jp = j + 1 == N ? 0 : j + 1, jm = j == 0 ? N - 1 : j - 1;
+        const int kp = k + 1 == N ? 0 : k + 1, km = k == 0 ? N - 1 : k - 1;
+        const long long row = (long long)i * NN + (long long)j * N;
+        const float v = (g[(long long)ip * NN + (long long)j * N + k] - g[(long long)im * NN + (long long)j * N + k]) +
+                        (g[N3 + (long long)i * NN + (long long)jp * N + k] -
+                         g[N3 + (long long)i * NN + (long long)jm * N + k]) +
+                        (g[2 * N3 + row + kp] - g[2 * N3 + row + km]);
+        out[idx] = (accumulate ? out[idx] : 0.0f) - v * inv_2d;
+    }
+}
+
+// lam_ij products of the second-order source (transpose of Eq. 6's bilinear form).
+__global__ void k_adj_source(const float *__restrict__ lamS, const float *__restrict__ d2, long long n,
+                             float *__restrict__ lam_d2) {
+    // d2: xx, yy, zz, xy, xz, yz (6 x n); lam_d2 same layout
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float ls = lamS[i];
+        const float xx = d2[i], yy = d2[n + i], zz = d2[2 * n + i];
+        lam_d2[i] = ls * (yy + zz);
+        lam_d2[n + i] = ls * (xx + zz);
+        lam_d2[2 * n + i] = ls * (xx + yy);
+        lam_d2[3 * n + i] = -2.0f * ls * d2[3 * n + i];
+        lam_d2[4 * n + i] = -2.0f * ls * d2[4 * n + i];
+        lam_d2[5 * n + i] = -2.0f * ls * d2[5 * n + i];
+    }
+}
+
+// acc_hat += (-D_i D_j) in_hat  (spectral second derivative, symmetric)
+__global__ void k_spec_d2_accumulate(const cufftComplex *__restrict__ in, cufftComplex *__restrict__ acc,
+                                     int N, const float *__restrict__ s_full, int ai, int aj) {
+    const int Nz = N / 2 + 1;
+    const long long n = (long long)N * N * Nz;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+         idx += (long long)gridDim.x * blockDim.x) {
+        int c[3];
+        c[2] = (int)(idx % Nz);
+        const long long t = idx / Nz;
+        c[1] = (int)(t % N);
+        c[0] = (int)(t / N);
+        const float m = -s_full[c[ai]] * s_full[c[aj]];
+        cufftComplex a = acc[idx];
+        const cufftComplex v = in[idx];
+        a.x = fmaf(m, v.x, a.x);
+        a.y = fmaf(m, v.y, a.y);
+        acc[idx] = a;
+    }
+}
+
+int grid_for(long long n, int block) {
+    long long g = (n + block - 1) / block;
+    return (int)(g < 8192 ? (g > 0 ? g : 1) : 8192);
+}
+
+}  // namespace
+
+cudaError_t launch_adj_final(Ctx &c, const float *lam_delta, float *adj) {
+    const int Ntile = c.Np / c.Ntiles;
+    k_adj_final<<<c.n_tchunks, kChunk, 0, c.stream>>>(c.boxes, c.tchunks, c.part, c.P, c.Np, Ntile,
+                                                       (float)c.dq, (float)c.L, lam_delta, adj);
+    ++c.launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_kick_drift(Ctx &c, float *adj, const KickDrift &kd) {
+    k_adj_kick_drift<<<c.n_pchunks, kChunk, 0, c.stream>>>(c.boxes, c.pchunks, adj, c.P, kd);
+    ++c.launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_interp(Ctx &c, const float *s, float *adj, float *lamG) {
+    k_adj_interp<<<c.n_pchunks, kChunk, 0, c.stream>>>(c.boxes, c.pchunks, s, c.P, c.phi, adj, lamG, c.MP);
+    ++c.launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_div(Ctx &c, const float *lamG, float *lam_phi_pad, float *interior_out) {
+    k_adj_div<<<c.n_ppchunks, kChunk, 0, c.stream>>>(c.boxes, c.ppchunks, lamG, c.MP, lam_phi_pad,
+                                                      interior_out);
+    ++c.launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_shell(Ctx &c, const float *lam_phi_pad, const float *lam_src_pad, float D1,
+                             float *lam_shell) {
+    k_adj_shell<<<c.n_shchunks, kChunk, 0, c.stream>>>(c.boxes, c.shchunks, lam_phi_pad, lam_src_pad, D1,
+                                                        lam_shell);
+    ++c.launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_deposit(Ctx &c, const float *s, const float *lam_src_pad, float *adj) {
+    k_adj_deposit<<<c.n_pchunks, kChunk, 0, c.stream>>>(c.boxes, c.pchunks, s, c.P, lam_src_pad, adj);
+    ++c.launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_init_scatter(Ctx &c, const float *adj, float *lamPsi1, float *lamPsi2) {
+    const int Ntile = c.Np / c.Ntiles;
+    k_adj_init_scatter<<<c.n_pchunks, kChunk, 0, c.stream>>>(c.boxes, c.pchunks, adj, c.P, c.Np, Ntile, c.N3,
+                                                              (float)c.tt.D1_i, (float)c.tt.D2_i, lamPsi1,
+                                                              lamPsi2);
+    ++c.launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_shell_to_phi1(Ctx &c, const float *lam_shell, float *lam_phi1) {
+    k_adj_shell_to_phi1<<<c.n_shchunks, kChunk, 0, c.stream>>>(c.boxes, c.shchunks, lam_shell, c.Np,
+                                                                c.L / c.Np, lam_phi1);
+    ++c.launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_neg_div(Ctx &c, const float *g, int accumulate, float *out) {
+    const double d = c.L / c.Np;
+    k_neg_div<<<grid_for(c.N3, 256), 256, 0, c.stream>>>(g, c.Np, (float)(0.5 / d), accumulate, out);
+    ++c.launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_source(Ctx &c, const float *lamS, const float *d2, float *lam_d2) {
+    k_adj_source<<<grid_for(c.N3, 256), 256, 0, c.stream>>>(lamS, d2, c.N3, lam_d2);
+    ++c.launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spec_d2_accumulate(Ctx &c, const cufftComplex *in, cufftComplex *acc, int i, int j) {
+    const int N = c.Np;
+    const long long n = (long long)N * N * (N / 2 + 1);
+    k_spec_d2_accumulate<<<grid_for(n, 256), 256, 0, c.stream>>>(in, acc, N, c.table_arena + c.sin_full_off,
+                                                                  i, j);
+    ++c.launches;
+    return cudaGetLastError();
+}
+
+}  // namespace scola

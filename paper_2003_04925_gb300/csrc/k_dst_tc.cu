@@ -15,9 +15,10 @@
 //
 // Precision: FP32 operands split as a = a_hi + a_lo with a_hi the value with
 // its 13 low mantissa bits cleared (exact in TF32); D accumulates
-// a_hi s_hi + a_hi s_lo + a_lo s_hi in FP32 in tensor memory (3xTF32).  A
-// single TF32 product gives position errors of ~0.1 PM cell over a run, the
-// three-term form stays at the FP32 level.
+// a_hi s_hi + a_hi s_lo + a_lo s_hi in FP32 in tensor memory (3xTF32), and
+// a_lo s_lo as well in the four-product form.  A single TF32 product gives
+// position errors of ~0.1 PM cell over a run, the three-term form stays near
+// the FP32 level.
 //
 // One persistent CTA per SM, 9 warps:
 //   warps 0-3  epilogue: tcgen05.ld of the accumulator (warp w owns TMEM lanes
@@ -61,6 +62,7 @@ struct TcArgs {
     float *out;
     const float *phi_pad;        // ghost layers (z+ prologue)
     int *err;
+    int lo_lo;                   // 1: also accumulate a_lo s_lo (four TF32 products)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -266,7 +268,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(TcArgs A) {
                 const int it = (int)blockIdx.x + (int)(g / nkc) * (int)gridDim.x;
                 const int c = (int)(g % nkc);
                 const Chunk tile = A.tiles[it];
-                const BoxDesc &B = A.boxes[tile.box];
+                const long long m_off = A.boxes[tile.box].m_off;
                 const int row0 = tile.start * kTM;
                 const uint32_t dst0 = raw_s + (uint32_t)((g % RS) * RAWB);
 #pragma unroll
@@ -276,16 +278,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(TcArgs A) {
                     const int k = c * kKC + kq * 4;
                     const int R = row0 + r;
                     const bool ok = (long long)R < Ng2 && k < Ng;
-                    const uint32_t off = sw128_offset(r, kq * 4);
                     if (PASS == P_ZF) {
+                        // 64-bit counts: the two 16-byte halves of an item go to two planes,
+                        // item q at 16 q in each (conflict-free reads)
                         const unsigned long long *src = reinterpret_cast<const unsigned long long *>(A.in) +
-                                                        B.m_off + (ok ? (long long)R * Ng + k : 0);
-                        cp_async16(dst0 + 2 * off, src, ok ? 16u : 0u);
-                        cp_async16(dst0 + 2 * off + 16, src + 2, ok ? 16u : 0u);
+                                                        m_off + (ok ? (long long)R * Ng + k : 0);
+                        cp_async16(dst0 + 16u * q, src, ok ? 16u : 0u);
+                        cp_async16(dst0 + kChunkBytes + 16u * q, src + 2, ok ? 16u : 0u);
                     } else {
-                        const float *src = reinterpret_cast<const float *>(A.in) + B.m_off +
+                        const float *src = reinterpret_cast<const float *>(A.in) + m_off +
                                            (ok ? (long long)R * Ng + k : 0);
-                        cp_async16(dst0 + off, src, ok ? 16u : 0u);
+                        cp_async16(dst0 + sw128_offset(r, kq * 4), src, ok ? 16u : 0u);
                     }
                 }
             }
@@ -303,8 +306,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(TcArgs A) {
             const int it = (int)blockIdx.x + (int)(g / nkc) * (int)gridDim.x;
             const int c = (int)(g % nkc);
             const Chunk tile = A.tiles[it];
-            const BoxDesc &B = A.boxes[tile.box];
             const int row0 = tile.start * kTM;
+            float nbar_sc = 0.f, c2 = 0.f;
+            long long pp_off = 0;
+            if (PASS == P_ZF) {
+                const BoxDesc &B = A.boxes[tile.box];
+                nbar_sc = B.nbar_inv * 2.3283064365386963e-10f;
+                c2 = B.inv_dg * B.inv_dg;
+                pp_off = B.pp_off;
+            }
             unsigned char *ah = stages + (size_t)s * 2 * kChunkBytes;
             unsigned char *al = ah + kChunkBytes;
             const unsigned char *rw = raw + (size_t)(g % RS) * RAWB;
@@ -315,23 +325,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(TcArgs A) {
                 const uint32_t off = sw128_offset(r, kq * 4);
                 float4 v;
                 if (PASS == P_ZF) {
-                    const ulonglong2 a01 = *reinterpret_cast<const ulonglong2 *>(rw + 2 * off);
-                    const ulonglong2 a23 = *reinterpret_cast<const ulonglong2 *>(rw + 2 * off + 16);
+                    const ulonglong2 a01 = *reinterpret_cast<const ulonglong2 *>(rw + 16 * q);
+                    const ulonglong2 a23 = *reinterpret_cast<const ulonglong2 *>(rw + kChunkBytes + 16 * q);
                     const int k = c * kKC + kq * 4;
                     const int R = row0 + r;
                     float vv[4] = {0.f, 0.f, 0.f, 0.f};
                     if ((long long)R < Ng2 && k < Ng) {
-                        const float sc = B.nbar_inv * 2.3283064365386963e-10f;
-                        vv[0] = (float)a01.x * sc - 1.0f;
-                        vv[1] = (float)a01.y * sc - 1.0f;
-                        vv[2] = (float)a23.x * sc - 1.0f;
-                        vv[3] = (float)a23.y * sc - 1.0f;
+                        vv[0] = (float)a01.x * nbar_sc - 1.0f;
+                        vv[1] = (float)a01.y * nbar_sc - 1.0f;
+                        vv[2] = (float)a23.x * nbar_sc - 1.0f;
+                        vv[3] = (float)a23.y * nbar_sc - 1.0f;
                         const int i = R / Ng, j = R - (R / Ng) * Ng;
                         const bool edge_ij = (i == 0 || j == 0 || i == Ng - 1 || j == Ng - 1);
                         if (edge_ij || k == 0 || k + 3 == Ng - 1) {
                             const int S = Ng + 4;
-                            const float *P = A.phi_pad + B.pp_off;
-                            const float c2 = B.inv_dg * B.inv_dg;
+                            const float *P = A.phi_pad + pp_off;
 #pragma unroll
                             for (int e2 = 0; e2 < 4; ++e2) {
                                 const int kk = k + e2;
@@ -391,6 +399,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(TcArgs A) {
                         mma_tf32(d, sw128_desc(ah + o), sw128_desc(bh + o), idesc, (c | kk) != 0);
                         mma_tf32(d, sw128_desc(ah + o), sw128_desc(bl + o), idesc, 1);
                         mma_tf32(d, sw128_desc(al + o), sw128_desc(bh + o), idesc, 1);
+                        if (A.lo_lo) mma_tf32(d, sw128_desc(al + o), sw128_desc(bl + o), idesc, 1);
                     }
                     mma_commit(&empty[s]);
                 }
@@ -414,11 +423,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(TcArgs A) {
             }
             tc_fence_after();
             const Chunk tile = A.tiles[it];
-            const BoxDesc &B = A.boxes[tile.box];
-            const long long R = (long long)tile.start * kTM + row_in_tile;
+            const long long m_off = A.boxes[tile.box].m_off;
+            const long long pp_off = A.boxes[tile.box].pp_off;
+            float *const out = A.out;
+            const int Ri = tile.start * kTM + row_in_tile;
+            const long long R = Ri;
             const bool valid = R < Ng2;
             const uint32_t tbase = tmem + (uint32_t)(a * 128) + ((uint32_t)(warp * 32) << 16);
-            const int rhi = (int)(R / Ng), rlo = (int)(R % Ng);
+            const int rhi = Ri / Ng, rlo = Ri - (Ri / Ng) * Ng;
             float lsum = 0.0f;
             if (PASS == P_XF && valid) lsum = lam[rhi] + lam[rlo];
             for (int c0 = 0; c0 < Npad; c0 += 16) {
@@ -436,11 +448,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(TcArgs A) {
                     if (col >= Ng) break;
                     if (PASS == P_XI) {
                         const long long S = Ng + 4;
-                        A.out[B.pp_off + ((long long)(col + 2) * S + (rhi + 2)) * S + (rlo + 2)] = v[j] * scale;
+                        out[pp_off + ((long long)(col + 2) * S + (rhi + 2)) * S + (rlo + 2)] = v[j] * scale;
                     } else if (PASS == P_XF) {
-                        A.out[B.m_off + (long long)col * Ng2 + R] = v[j] / (lam[col] + lsum);
+                        out[m_off + (long long)col * Ng2 + R] = __fdividef(v[j], lam[col] + lsum);
                     } else {
-                        A.out[B.m_off + (long long)col * Ng2 + R] = v[j];
+                        out[m_off + (long long)col * Ng2 + R] = v[j];
                     }
                 }
             }
@@ -495,6 +507,7 @@ cudaError_t run_tc_pass(Ctx &c, const TcGroup &G, const void *in, float *out) {
     a.out = out;
     a.phi_pad = c.phi;
     a.err = c.dev_err;
+    a.lo_lo = c.tc_lo_lo ? 1 : 0;
     const size_t smem = tc_smem_bytes(G.Npad, G.nkc, G.nstage, G.Ng, (depth + 1) * raw_chunk_bytes<PASS>());
     const int grid = std::max(1, std::min(G.ntiles, c.num_sms));
     if (depth == kDeep)
@@ -539,23 +552,31 @@ cudaError_t init_tc_kernels() {
     return set_tc_attr<P_XI>();
 }
 
-cudaError_t launch_poisson_tc_pass(Ctx &c, int pass) {
-    // buffers: acc -> work -> work2 -> work -> work2 -> work -> phi
-    cudaError_t e = cudaSuccess;
+// The launch groups: every Ng group, or in the per-tile form only the current box's tiles.
+std::vector<TcGroup> active_groups(const Ctx &c) {
+    if (c.tc_view_box < 0) return c.tc_groups;
     std::vector<TcGroup> one;
-    if (c.tc_view_box >= 0) {
-        // per-tile form: only the tiles of one box (a contiguous range of its group)
-        for (const TcGroup &G : c.tc_groups) {
-            if (G.Ng != c.boxes_h[c.tc_view_box].Ng) continue;
-            TcGroup V = G;
-            V.tiles = c.tc_tiles + c.tc_tile_beg[c.tc_view_box];
-            V.ntiles = c.tc_tile_end[c.tc_view_box] - c.tc_tile_beg[c.tc_view_box];
-            one.push_back(V);
-        }
+    for (const TcGroup &G : c.tc_groups) {
+        if (G.Ng != c.boxes_h[c.tc_view_box].Ng) continue;
+        TcGroup V = G;
+        V.tiles = c.tc_tiles + c.tc_tile_beg[c.tc_view_box];
+        V.ntiles = c.tc_tile_end[c.tc_view_box] - c.tc_tile_beg[c.tc_view_box];
+        one.push_back(V);
     }
-    for (const TcGroup &G : (c.tc_view_box >= 0 ? one : c.tc_groups)) {
+    return one;
+}
+
+cudaError_t launch_poisson_tc_pass(Ctx &c, int pass) {
+    // buffers: density source -> work2 -> work -> work2 -> work -> work2 -> work -> phi
+    cudaError_t e = cudaSuccess;
+    if (pass == 0) {
+        // the density source in the interior layout (all boxes of the view), then pass 1 on it
+        e = launch_density_source(c, c.work2);
+        if (e != cudaSuccess) return e;
+    }
+    for (const TcGroup &G : active_groups(c)) {
         switch (pass) {
-            case 0: e = run_tc_pass<P_ZF>(c, G, c.acc, c.work); break;
+            case 0: e = run_tc_pass<P_YF>(c, G, c.work2, c.work); break;
             case 1: e = run_tc_pass<P_YF>(c, G, c.work, c.work2); break;
             case 2: e = run_tc_pass<P_XF>(c, G, c.work2, c.work); break;
             case 3: e = run_tc_pass<P_ZI>(c, G, c.work, c.work2); break;
@@ -571,6 +592,23 @@ cudaError_t launch_poisson_tc_pass(Ctx &c, int pass) {
 cudaError_t launch_poisson_tc(Ctx &c) {
     for (int p = 0; p < 6; ++p) {
         cudaError_t e = launch_poisson_tc_pass(c, p);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+// (launch_poisson in k_pm.cu uses the same sequence through launch_poisson_buffers.)
+
+cudaError_t launch_poisson_tc_buffers(Ctx &c, const void *in, bool in_acc, float *w1, float *w2,
+                                      float *out_pad) {
+    // a float input skips the density prologue: the first pass is then a plain rotating pass
+    cudaError_t e = cudaSuccess;
+    for (const TcGroup &G : active_groups(c)) {
+        e = in_acc ? run_tc_pass<P_ZF>(c, G, in, w1) : run_tc_pass<P_YF>(c, G, in, w1);
+        if (e == cudaSuccess) e = run_tc_pass<P_YF>(c, G, w1, w2);
+        if (e == cudaSuccess) e = run_tc_pass<P_XF>(c, G, w2, w1);
+        if (e == cudaSuccess) e = run_tc_pass<P_ZI>(c, G, w1, w2);
+        if (e == cudaSuccess) e = run_tc_pass<P_YI>(c, G, w2, w1);
+        if (e == cudaSuccess) e = run_tc_pass<P_XI>(c, G, w1, out_pad);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

@@ -51,6 +51,34 @@ __global__ void k_colour(cufftComplex *ck, int N, double kf, double A, double ns
     }
 }
 
+// Adjoint of colouring after the inverse Laplacian: out = in * amp(k) / (Lambda(k) N^3), k = 0 -> 0.
+__global__ void k_adj_colour(const cufftComplex *in, cufftComplex *out, int N, double kf, double A,
+                             double ns, double Omh, double inv_d3, double norm, const float *s_half,
+                             float inv_d2) {
+    const int Nz = N / 2 + 1;
+    const long long n = (long long)N * N * Nz;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int kz = (int)(idx % Nz);
+        const long long t = idx / Nz;
+        const int ky = (int)(t % N);
+        const int kx = (int)(t / N);
+        const double nx = wavenumber(kx, N), ny = wavenumber(ky, N), nz = kz;
+        const double k = kf * sqrt(nx * nx + ny * ny + nz * nz);
+        float m = 0.0f;
+        if (k > 0) {
+            const double T = bbks_T_dev(k, Omh);
+            const float sx = s_half[kx], sy = s_half[ky], sz = s_half[kz];
+            const float lam = -4.0f * inv_d2 * (sx * sx + sy * sy + sz * sz);
+            m = (float)(sqrt(A * pow(k, ns) * T * T * inv_d3) * norm) / lam;
+        }
+        cufftComplex v = in[idx];
+        v.x *= m;
+        v.y *= m;
+        out[idx] = v;
+    }
+}
+
 __global__ void k_inv_lap(const cufftComplex *in, cufftComplex *out, int N, const float *s_half,
                           float inv_d2, float scale) {
     const int Nz = N / 2 + 1;
@@ -143,6 +171,19 @@ cudaError_t launch_colour(Ctx &c, cufftComplex *ck) {
     k_colour<<<grid_for(n, 256), 256, 0, c.stream>>>(ck, N, 2.0 * M_PI / c.L, c.pk_amp,
                                                       c.prm.ns, c.prm.Om * c.prm.h,
                                                       1.0 / (d * d * d), 1.0 / N3);
+    ++c.launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_colour(Ctx &c, const cufftComplex *in, cufftComplex *out) {
+    const int N = c.Np;
+    const long long n = (long long)N * N * (N / 2 + 1);
+    const double d = c.L / N;
+    const double N3 = (double)N * N * N;
+    k_adj_colour<<<grid_for(n, 256), 256, 0, c.stream>>>(in, out, N, 2.0 * M_PI / c.L, c.pk_amp, c.prm.ns,
+                                                          c.prm.Om * c.prm.h, 1.0 / (d * d * d), 1.0 / N3,
+                                                          c.table_arena + c.sin_half_off,
+                                                          (float)(1.0 / (d * d)));
     ++c.launches;
     return cudaGetLastError();
 }

@@ -90,7 +90,7 @@ k_pad(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
 }
 
 // ------------------------------------------------------------------ DST passes
-enum Pass { kZFwd = 0, kYFwd = 1, kXSolve = 2, kYInv = 3, kZInv = 4 };
+enum Pass { kZFwd = 0, kYFwd = 1, kXSolve = 2, kYInv = 3, kZInv = 4, kZFwdF = 5 };
 
 // acc[r][j] = sum_i ST[i][tl + 32 r] X[i][c0 + j]   (Y = S X on a column tile)
 template <int R>
@@ -144,11 +144,14 @@ k_dst(const BoxDesc *__restrict__ boxes, const DstTable *__restrict__ tables,
             __syncthreads();
         }
         const long long Ng2 = (long long)Ng * Ng;
+        // box fields in registers: the stores below could otherwise force reloads
+        const long long m_off = B.m_off, pp_off = B.pp_off;
+        const float nbar_sc = B.nbar_inv * 2.3283064365386963e-10f, c2 = B.inv_dg * B.inv_dg;
         // ---- load the column tile X[t][c]
         int ncols;
         long long zp0 = 0;     // first pencil (z passes)
         int plane = 0, k0 = 0; // (plane, column offset) for y/x passes
-        if (PASS == kZFwd || PASS == kZInv) {
+        if (PASS == kZFwd || PASS == kZFwdF || PASS == kZInv) {
             zp0 = (long long)item.start * kTC;
             ncols = (int)min((long long)kTC, Ng2 - zp0);
             for (int q = tid; q < Ng * kTC; q += blockDim.x) {
@@ -159,12 +162,12 @@ k_dst(const BoxDesc *__restrict__ boxes, const DstTable *__restrict__ tables,
                     if (PASS == kZFwd) {
                         const unsigned long long *acc =
                             reinterpret_cast<const unsigned long long *>(in_v);
-                        const long long cell = B.m_off + p * Ng + t;
-                        v = (float)acc[cell] * (B.nbar_inv * 2.3283064365386963e-10f) - 1.0f;
+                        const long long cell = m_off + p * Ng + t;
+                        v = (float)acc[cell] * nbar_sc - 1.0f;
                         const int i = (int)(p / Ng), j = (int)(p % Ng), k = t;
                         if (i == 0 || j == 0 || k == 0 || i == Ng - 1 || j == Ng - 1 || k == Ng - 1) {
                             const long long S = Ng + 4;
-                            const float *P = phi_pad + B.pp_off;
+                            const float *P = phi_pad + pp_off;
                             const long long ctr = ((long long)(i + 2) * S + (j + 2)) * S + (k + 2);
                             float bc = 0.0f;
                             if (i == 0) bc += P[ctr - S * S];
@@ -173,11 +176,11 @@ k_dst(const BoxDesc *__restrict__ boxes, const DstTable *__restrict__ tables,
                             if (j == Ng - 1) bc += P[ctr + S];
                             if (k == 0) bc += P[ctr - 1];
                             if (k == Ng - 1) bc += P[ctr + 1];
-                            v -= bc * (B.inv_dg * B.inv_dg);
+                            v -= bc * c2;
                         }
                     } else {
                         const float *in = reinterpret_cast<const float *>(in_v);
-                        v = in[B.m_off + p * Ng + t];
+                        v = in[m_off + p * Ng + t];
                     }
                 }
                 X[t * kXS + c] = v;
@@ -189,7 +192,7 @@ k_dst(const BoxDesc *__restrict__ boxes, const DstTable *__restrict__ tables,
             ncols = min(kTC, Ng - k0);
             const float *in = reinterpret_cast<const float *>(in_v);
             // y passes: element (t = j, k) of plane i; x pass: element (t = i, k) of plane j
-            const long long base = B.m_off + (PASS == kXSolve ? (long long)plane * Ng : (long long)plane * Ng2) + k0;
+            const long long base = m_off + (PASS == kXSolve ? (long long)plane * Ng : (long long)plane * Ng2) + k0;
             const long long tstride = (PASS == kXSolve) ? Ng2 : Ng;
             for (int q = tid; q < Ng * kTC; q += blockDim.x) {
                 const int c = q % kTC, t = q / kTC;
@@ -223,7 +226,7 @@ k_dst(const BoxDesc *__restrict__ boxes, const DstTable *__restrict__ tables,
 
         // ---- store
         if (PASS == kYFwd || PASS == kYInv || PASS == kXSolve) {
-            const long long base = B.m_off + (PASS == kXSolve ? (long long)plane * Ng : (long long)plane * Ng2) + k0;
+            const long long base = m_off + (PASS == kXSolve ? (long long)plane * Ng : (long long)plane * Ng2) + k0;
             const long long tstride = (PASS == kXSolve) ? Ng2 : Ng;
 #pragma unroll
             for (int r = 0; r < R; ++r) {
@@ -251,12 +254,12 @@ k_dst(const BoxDesc *__restrict__ boxes, const DstTable *__restrict__ tables,
                 const int t = q % Ng, c = q / Ng;
                 if (c < ncols) {
                     const long long p = zp0 + c;
-                    if (PASS == kZFwd) {
-                        out[B.m_off + p * Ng + t] = X[t * kXS + c];
+                    if (PASS == kZFwd || PASS == kZFwdF) {
+                        out[m_off + p * Ng + t] = X[t * kXS + c];
                     } else {
                         const long long S = Ng + 4;
                         const int i = (int)(p / Ng), j = (int)(p % Ng);
-                        out[B.pp_off + ((long long)(i + 2) * S + (j + 2)) * S + 2 + t] = X[t * kXS + c];
+                        out[pp_off + ((long long)(i + 2) * S + (j + 2)) * S + 2 + t] = X[t * kXS + c];
                     }
                 }
             }
@@ -343,7 +346,7 @@ k_interp(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
     F[2 * stride + gi] = f[2];
 }
 
-__global__ void __launch_bounds__(kChunk)
+__global__ void __launch_bounds__(kChunk, 5)
 k_kick_drift(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
              float *__restrict__ part, long long P, const float *__restrict__ phi, KickDrift kd) {
     const Chunk ch = chunks[blockIdx.x];
@@ -375,6 +378,46 @@ k_kick_drift(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks
     }
 }
 
+// delta' = density - Lap Phi_BC (Eq. 62) from the fixed-point counts, 4 consecutive cells per
+// thread (Ng % 4 == 0), written in the interior layout: the source of the tensor-core solve.
+__global__ void __launch_bounds__(64)
+k_density_source(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
+                 const unsigned long long *__restrict__ acc, const float *__restrict__ phi_pad,
+                 float *__restrict__ out) {
+    const Chunk ch = chunks[blockIdx.x];
+    const BoxDesc &B = boxes[ch.box];
+    const int Ng = B.Ng;
+    const long long m_off = B.m_off, pp_off = B.pp_off;
+    const float sc = B.nbar_inv * 2.3283064365386963e-10f, c2 = B.inv_dg * B.inv_dg;
+    const int cell0 = ch.start + 4 * threadIdx.x;
+    if ((long long)cell0 >= (long long)Ng * Ng * Ng) return;
+    const ulonglong2 a01 = *reinterpret_cast<const ulonglong2 *>(acc + m_off + cell0);
+    const ulonglong2 a23 = *reinterpret_cast<const ulonglong2 *>(acc + m_off + cell0 + 2);
+    float v[4] = {(float)a01.x * sc - 1.0f, (float)a01.y * sc - 1.0f, (float)a23.x * sc - 1.0f,
+                  (float)a23.y * sc - 1.0f};
+    const int k = cell0 % Ng;
+    const int t = cell0 / Ng;
+    const int j = t % Ng, i = t / Ng;
+    if (i == 0 || j == 0 || i == Ng - 1 || j == Ng - 1 || k == 0 || k + 3 == Ng - 1) {
+        const long long S = Ng + 4;
+        const float *P = phi_pad + pp_off;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int kk = k + e;
+            const long long ctr = ((long long)(i + 2) * S + (j + 2)) * S + (kk + 2);
+            float bc = 0.0f;
+            if (i == 0) bc += P[ctr - S * S];
+            if (i == Ng - 1) bc += P[ctr + S * S];
+            if (j == 0) bc += P[ctr - S];
+            if (j == Ng - 1) bc += P[ctr + S];
+            if (kk == 0) bc += P[ctr - 1];
+            if (kk == Ng - 1) bc += P[ctr + 1];
+            v[e] -= bc * c2;
+        }
+    }
+    *reinterpret_cast<float4 *>(out + m_off + cell0) = make_float4(v[0], v[1], v[2], v[3]);
+}
+
 __global__ void k_acc_to_delta(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
                                const unsigned long long *__restrict__ acc, float *__restrict__ out) {
     const Chunk ch = chunks[blockIdx.x];
@@ -404,6 +447,7 @@ template <int R>
 cudaError_t set_attrs_R() {
     const int lim = 227 * 1024;
     cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_dst<R, kZFwdF>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
     if ((e = cudaFuncSetAttribute(k_dst<R, kZFwd>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
     if ((e = cudaFuncSetAttribute(k_dst<R, kYFwd>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
     if ((e = cudaFuncSetAttribute(k_dst<R, kXSolve>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
@@ -421,13 +465,17 @@ int ctas_per_sm_R(int ngmax) {
 }
 
 template <int R>
-cudaError_t poisson_R(Ctx &c) {
+cudaError_t poisson_R(Ctx &c, const void *in, bool in_acc, float *w1, float *w2, float *out_pad) {
     cudaError_t e;
-    if ((e = run_pass<R, kZFwd>(c, c.zitems, c.n_zitems, c.acc, c.work)) != cudaSuccess) return e;
-    if ((e = run_pass<R, kYFwd>(c, c.citems, c.n_citems, c.work, c.work2)) != cudaSuccess) return e;
-    if ((e = run_pass<R, kXSolve>(c, c.citems, c.n_citems, c.work2, c.work)) != cudaSuccess) return e;
-    if ((e = run_pass<R, kYInv>(c, c.citems, c.n_citems, c.work, c.work2)) != cudaSuccess) return e;
-    return run_pass<R, kZInv>(c, c.zitems, c.n_zitems, c.work2, c.phi);
+    if (in_acc) {
+        if ((e = run_pass<R, kZFwd>(c, c.zitems, c.n_zitems, in, w1)) != cudaSuccess) return e;
+    } else {
+        if ((e = run_pass<R, kZFwdF>(c, c.zitems, c.n_zitems, in, w1)) != cudaSuccess) return e;
+    }
+    if ((e = run_pass<R, kYFwd>(c, c.citems, c.n_citems, w1, w2)) != cudaSuccess) return e;
+    if ((e = run_pass<R, kXSolve>(c, c.citems, c.n_citems, w2, w1)) != cudaSuccess) return e;
+    if ((e = run_pass<R, kYInv>(c, c.citems, c.n_citems, w1, w2)) != cudaSuccess) return e;
+    return run_pass<R, kZInv>(c, c.zitems, c.n_zitems, w2, out_pad);
 }
 
 }  // namespace
@@ -463,17 +511,28 @@ cudaError_t init_pm_kernels(Ctx &c) {
     return cudaSuccess;
 }
 
-cudaError_t launch_poisson(Ctx &c) {
-    if (c.use_tc) return launch_poisson_tc(c);
+cudaError_t launch_poisson_buffers(Ctx &c, const void *in, bool in_acc, float *w1, float *w2,
+                                   float *out_pad) {
+    if (c.use_tc) return launch_poisson_tc_buffers(c, in, in_acc, w1, w2, out_pad);
     switch (c.max_R) {
-        case 1: return poisson_R<1>(c);
-        case 2: return poisson_R<2>(c);
-        case 3: return poisson_R<3>(c);
-        case 4: return poisson_R<4>(c);
-        case 5: return poisson_R<5>(c);
-        case 6: return poisson_R<6>(c);
+        case 1: return poisson_R<1>(c, in, in_acc, w1, w2, out_pad);
+        case 2: return poisson_R<2>(c, in, in_acc, w1, w2, out_pad);
+        case 3: return poisson_R<3>(c, in, in_acc, w1, w2, out_pad);
+        case 4: return poisson_R<4>(c, in, in_acc, w1, w2, out_pad);
+        case 5: return poisson_R<5>(c, in, in_acc, w1, w2, out_pad);
+        case 6: return poisson_R<6>(c, in, in_acc, w1, w2, out_pad);
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_poisson(Ctx &c) {
+    if (c.use_tc) {
+        // tensor-core form: coalesced conversion of the counts, then six float passes
+        cudaError_t e = launch_density_source(c, c.work2);
+        if (e != cudaSuccess) return e;
+        return launch_poisson_buffers(c, c.work2, false, c.work, c.work2, c.phi);
+    }
+    return launch_poisson_buffers(c, c.acc, true, c.work, c.work2, c.phi);
 }
 
 cudaError_t launch_poisson_pass(Ctx &c, int pass) {
@@ -507,6 +566,12 @@ cudaError_t launch_interp(Ctx &c, const float *s, long long stride, float *F) {
 
 cudaError_t launch_kick_drift(Ctx &c, const KickDrift &kd) {
     k_kick_drift<<<c.n_pchunks, kChunk, 0, c.stream>>>(c.boxes, c.pchunks, c.part, c.P, c.phi, kd);
+    ++c.launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_density_source(Ctx &c, float *out) {
+    k_density_source<<<c.n_mchunks, 64, 0, c.stream>>>(c.boxes, c.mchunks, c.acc, c.phi, out);
     ++c.launches;
     return cudaGetLastError();
 }

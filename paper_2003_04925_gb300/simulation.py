@@ -80,3 +80,32 @@ class Scola:
 
     def stats(self):
         return B.scola_get_stats(self.ctx)
+
+    def enable_checkpointing(self, on=True):
+        B.scola_set_checkpointing(self.ctx, on)
+
+    def backward(self, lam_delta):
+        """dLoss/dw from dLoss/d(final density) for the last checkpointed forward run."""
+        N = self.Np
+        lam_w = self._empty(N, N, N)
+        B.scola_backward(self.ctx, lam_delta.contiguous(), lam_w)
+        return lam_w
+
+
+class ScolaDensity(torch.autograd.Function):
+    """w (Np^3 white noise) -> final periodic CIC density (Np^3), differentiable.
+
+    The forward pass runs the whole sCOLA simulation with per-step checkpoints;
+    the backward pass runs the library's hand-written adjoint kernels.
+    """
+
+    @staticmethod
+    def forward(ctx, w, sim):
+        sim.enable_checkpointing(True)
+        x, _ = sim.forward(w)
+        ctx.sim = sim
+        return sim.final_density(x)
+
+    @staticmethod
+    def backward(ctx, grad_delta):
+        return ctx.sim.backward(grad_delta), None

@@ -42,12 +42,12 @@ CASES_PM = {
 
 
 def _sim(kw, variant="simt"):
-    code = {"simt": sc.SCOLA_DST_SIMT, "tc": sc.SCOLA_DST_TC_3XTF32}[variant]
+    code = {"simt": sc.SCOLA_DST_SIMT, "tc": sc.SCOLA_DST_TC_3XTF32, "tc4": sc.SCOLA_DST_TC_4XTF32}[variant]
     return sc.Scola(**dict(lib_kwargs(kw), dst_variant=code))
 
 
 def _skip_unsupported(kw, variant):
-    if variant == "tc" and kw.get("Ng", 0) % 4 != 0:
+    if variant.startswith("tc") and kw.get("Ng", 0) % 4 != 0:
         pytest.skip("the tensor-core DST needs Ng % 4 == 0")
 
 
@@ -146,7 +146,7 @@ def _pk_rel_err(delta_a, delta_b, L, N):
     return np.abs(pa[ok] / pb[ok] - 1).max()
 
 
-@pytest.mark.parametrize("variant", ["simt", "tc"])
+@pytest.mark.parametrize("variant", ["simt", "tc", "tc4"])
 @pytest.mark.parametrize("name", ["plain_32", "uneven", "table1_like"])
 def test_forward_matches_oracle(name, variant):
     kw = CASES_PM[name]
@@ -206,6 +206,30 @@ def test_per_tile_form_matches_batched_form(name, variant):
     assert torch.equal(xa, xb) and torch.equal(pa, pb)
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("variant", ["simt", "tc"])
+def test_box_ranges_merge_to_the_full_run(variant):
+    # Boxes never communicate, so contexts evolving disjoint box ranges (one per GPU in a
+    # sharded run) write disjoint tiles whose union is the full run, bit for bit.
+    from paper_2003_04925_gb300 import shard
+    kw = CASES_PM["uneven"]
+    w = _to_dev(synth_inputs.white_noise(kw["Np"], 8))
+    full = _sim(kw, variant)
+    xf, pf = full.forward(w)
+    torch.cuda.synchronize()
+    nsc, ng, _, _ = sc.scola_tiling_info(sc.make_params(**lib_kwargs(kw)))
+    ranges = shard.box_ranges([shard.box_cost(a, b) for a, b in zip(nsc, ng)], 3)
+    n = kw["Np"] ** 3
+    xm = torch.full((n, 3), float("nan"), device="cuda")
+    pm_ = torch.full((n, 3), float("nan"), device="cuda")
+    for first, count in ranges:
+        part = _sim(dict(kw, box_first=first, box_count=count), variant)
+        part.forward(w, xm, pm_)
+        torch.cuda.synchronize()
+        part.close()
+    assert torch.equal(xm, xf) and torch.equal(pm_, pf)
+    full.close()
 
 
 def test_zero_amplitude_keeps_the_lattice():
