@@ -272,7 +272,8 @@ def kernel_roofline(kt, kw, clocks, peaks, tc):
     FP32 form: the five DST passes are dense products on CUDA cores (ALU bound,
     2 Ng flops per cell per transform; pass 3 does two transforms).  Tensor-core
     form: six passes, each streaming its mesh once (HBM bound: 4 B read + 4 B
-    written per cell, pass 1 reads the 8-byte fixed-point density).
+    written per cell).  Deposit: the positions once (12 B per particle) and the
+    Poisson source written once (4 B per cell).
     """
     nsc, ng = box_sizes(kw)
     P = sum(n**3 for n in nsc)
@@ -286,7 +287,7 @@ def kernel_roofline(kt, kw, clocks, peaks, tc):
         names = ["dst_1_z_fwd", "dst_2_y_fwd", "dst_3_x_fwd_div", "dst_4_z_inv", "dst_5_y_inv",
                  "dst_6_x_inv"]
         for i, nm in enumerate(names):
-            work[nm] = ("hbm", (12.0 if i == 0 else 8.0) * M)
+            work[nm] = ("hbm", 8.0 * M)
     else:
         names = ["dst_1_z_fwd", "dst_2_y_fwd", "dst_3_x_solve", "dst_4_y_inv", "dst_5_z_inv", None]
         for i, nm in enumerate(names):

@@ -327,6 +327,21 @@ scola_status scola_backward(scola_ctx *ctx, const float *lam_delta_dev, float *l
 scola_status scola_box_density_noalloc(const float *s_dev, int32_t nsc, int32_t ng, double dq,
                                        float *delta_dev, void *stream);
 
+/*
+ * Self-test of the fixed-point conversions of the CIC deposits (the paper has
+ * no counterpart).  The deposits convert each FP32 weight w in [0, 1] to the
+ * 64-bit integer round(w 2^32) and the summed counts back to FP32 with 32-bit
+ * instructions only; this runs those forms and CUDA's direct 64-bit
+ * conversions on n generated inputs (weights in [0, 1] including 0, 1 and
+ * values near both ends; counts of every magnitude and exact rounding ties)
+ * on the current device and counts the results that differ in any bit.
+ *   n           number of inputs (>= 0)
+ *   seed        input generator seed
+ *   mismatches  host, receives the count (0 means bit-identical)
+ * Synchronous.  Errors: INVALID_ARG (NULL, n < 0), OOM, CUDA.
+ */
+scola_status scola_selftest_conversions(int64_t n, uint64_t seed, int64_t *mismatches);
+
 scola_status scola_get_stats(const scola_ctx *ctx, scola_stats *out);
 const char *scola_status_string(scola_status status);
 const char *scola_last_error(void);

@@ -196,6 +196,19 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &all_geo) {
         const int n = i < p.Np / 2 ? i : i - p.Np;
         arena.push_back((float)std::sin(M_PI * n / p.Np));
     }
+    // colouring amplitude sqrt(P(k) / d^3) / N^3 per integer |n|^2 = nx^2 + ny^2 + nz^2 of the
+    // wrapped wavenumbers (|n_i| <= N/2), from the FP64 host BBKS spectrum; entry 0 is zero
+    c->amp_off = (long long)arena.size();
+    {
+        const double d = p.L / p.Np, kf = 2.0 * M_PI / p.L, N3 = (double)p.Np * p.Np * p.Np;
+        const long long nmax = 3LL * (p.Np / 2) * (p.Np / 2);
+        for (long long n2 = 0; n2 <= nmax; ++n2) {
+            const double k = kf * std::sqrt((double)n2);
+            const double T = bbks_transfer(k, p.Om, p.h);
+            arena.push_back(n2 == 0 ? 0.0f
+                                    : (float)(std::sqrt(c->pk_amp * std::pow(k, p.ns) * T * T / (d * d * d)) / N3));
+        }
+    }
     c->sin_full_off = (long long)arena.size();
     for (int i = 0; i < p.Np; ++i) {
         const int n = i < p.Np / 2 ? i : i - p.Np;
@@ -270,6 +283,16 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &all_geo) {
     c->zbeg.push_back((int)zit.size());
     c->cbeg.push_back((int)cit.size());
     c->mbeg.push_back((int)mch.size());
+    // deposit groups: consecutive boxes whose counts fit the L2-sized scratch (a box larger
+    // than the limit forms a group of its own)
+    long long dep_cells = 0;
+    for (int b = 0; b < c->nboxes; ++b) {
+        const long long end = c->boxes_h[b].m_off + (long long)geo[b].ng * geo[b].ng * geo[b].ng;
+        if (c->dep_groups.empty() || end - c->boxes_h[c->dep_groups.back()].m_off > kDepositGroupCells)
+            c->dep_groups.push_back(b);
+        dep_cells = std::max(dep_cells, end - c->boxes_h[c->dep_groups.back()].m_off);
+    }
+    c->dep_groups.push_back(c->nboxes);
     for (auto &T : c->tables_h) {
         const double dg = dg_of_ng[T.Ng];
         for (int l = 0; l < T.Ng; ++l) {
@@ -279,8 +302,6 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &all_geo) {
     }
     c->P = P;
     c->M = M;
-    c->acc_clear_off = 0;
-    c->acc_clear_len = M;
     c->MP = MP;
     c->SH = SH;
     if (pch.size() > 0x7fffffff || zit.size() > 0x7fffffff || cit.size() > 0x7fffffff)
@@ -355,7 +376,8 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &all_geo) {
     CS(dev_alloc(&c->dev_err, 1));
     CK(cudaMemset(c->dev_err, 0, sizeof(int)));
     CS(dev_alloc(&c->part, 12 * P));
-    CS(dev_alloc(&c->acc, M));
+    CS(dev_alloc(&c->dep_acc, dep_cells));
+    CK(cudaMemset(c->dep_acc, 0, sizeof(unsigned long long) * (size_t)dep_cells));
     CS(dev_alloc(&c->work, M));
     CS(dev_alloc(&c->work2, M));
     CS(dev_alloc(&c->phi, MP));
@@ -441,22 +463,20 @@ KickDrift kick_drift_coefficients(const TimeTable &t, int k) {
     return kd;
 }
 
-// Restricts every work list (and the accumulator clear) to one box; restores on destruction.
+// Restricts every work list to one box; restores on destruction.
 struct BoxView {
     scola_ctx *c;
     Chunk *pch, *sh, *z, *cl, *mc;
     int npch, nsh, nz, ncl, nmc;
-    long long off, len;
-    int tcv;
+    int view;
     BoxView(scola_ctx *cc, int b) : c(cc) {
-        tcv = c->tc_view_box;
-        c->tc_view_box = b;
+        view = c->view_box;
+        c->view_box = b;
         pch = c->pchunks; sh = c->shchunks; z = c->zitems; cl = c->citems; mc = c->mchunks;
         npch = c->n_pchunks; nsh = c->n_shchunks; nz = c->n_zitems; ncl = c->n_citems;
         nmc = c->n_mchunks;
         c->mchunks = mc + c->mbeg[b];
         c->n_mchunks = c->mbeg[b + 1] - c->mbeg[b];
-        off = c->acc_clear_off; len = c->acc_clear_len;
         c->pchunks = pch + c->pbeg[b];
         c->n_pchunks = c->pbeg[b + 1] - c->pbeg[b];
         c->shchunks = sh + c->shbeg[b];
@@ -465,16 +485,12 @@ struct BoxView {
         c->n_zitems = c->zbeg[b + 1] - c->zbeg[b];
         c->citems = cl + c->cbeg[b];
         c->n_citems = c->cbeg[b + 1] - c->cbeg[b];
-        const BoxDesc &B = c->boxes_h[b];
-        c->acc_clear_off = B.m_off;
-        c->acc_clear_len = (long long)B.Ng * B.Ng * B.Ng;
     }
     ~BoxView() {
         c->pchunks = pch; c->shchunks = sh; c->zitems = z; c->citems = cl; c->mchunks = mc;
         c->n_pchunks = npch; c->n_shchunks = nsh; c->n_zitems = nz; c->n_citems = ncl;
         c->n_mchunks = nmc;
-        c->acc_clear_off = off; c->acc_clear_len = len;
-        c->tc_view_box = tcv;
+        c->view_box = view;
     }
 };
 
@@ -653,7 +669,8 @@ void scola_destroy(scola_ctx *c) {
     void *ptrs[] = {c->boxes, c->tables, c->table_arena, c->pchunks, c->tchunks, c->shchunks,
                     c->zitems, c->citems, c->mchunks, c->ppchunks, c->tc_tiles, c->dev_err, c->ckpt,
                     c->adj, c->lamG, c->lam_phi_pad, c->adj_in, c->adj_out, c->lam_shell, c->lamPsi1,
-                    c->lamPsi2, c->lam_phi1, c->lam_phi2, c->d2, c->lam_d2, c->part, c->acc, c->work, c->work2, c->phi,
+                    c->lamPsi2, c->lam_phi1, c->lam_phi2, c->d2, c->lam_d2, c->part, c->dep_acc,
+                    c->work, c->work2, c->phi,
                     c->shell, c->ck, c->cp, c->ct, c->g[0], c->g[1], c->g[2], c->g[3], c->phi1,
                     c->phi2, c->psi1, c->psi2, c->dens_acc, c->w_h2d, c->x_h2d, c->p_h2d};
     for (void *q : ptrs)
@@ -702,8 +719,7 @@ scola_status scola_pm_force(scola_ctx *c, const float *s, double D1, float *F, f
         return SCOLA_ERR_STATE;
     }
     CK(launch_pad(*c, (float)D1));
-    CK(launch_deposit(*c, s, c->P));
-    if (delta) CK(launch_acc_to_delta(*c, delta));
+    CK(launch_deposit(*c, s, c->P, delta));
     CK(launch_poisson(*c));
     CK(launch_interp(*c, s, c->P, F));
     if (phi)
@@ -793,7 +809,7 @@ scola_status scola_backward(scola_ctx *c, const float *lam_delta, float *lam_w) 
         CK(cudaMemsetAsync(c->lamG, 0, fb * 3 * c->MP, c->stream));
         CK(launch_adj_interp(*c, sk, c->adj, c->lamG));
         CK(launch_adj_div(*c, c->lamG, c->lam_phi_pad, c->adj_in));
-        CK(launch_poisson_buffers(*c, c->adj_in, false, c->work, c->work2, c->adj_out));
+        CK(launch_poisson_buffers(*c, c->adj_in, c->work, c->work2, c->adj_out));
         CK(launch_adj_shell(*c, c->lam_phi_pad, c->adj_out, (float)c->tt.D1[k], c->lam_shell));
         CK(launch_adj_deposit(*c, sk, c->adj_out, c->adj));
     }

@@ -169,6 +169,8 @@ double tophat(double x) {
 
 }  // namespace
 
+double bbks_transfer(double k, double Om, double h) { return bbks_T(k, Om, h); }
+
 void growth_factors(double Om, double OL, const std::vector<double> &a, std::vector<double> &D1,
                     std::vector<double> &D2, std::vector<double> &dD1da,
                     std::vector<double> &dD2da) {

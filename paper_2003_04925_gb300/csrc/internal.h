@@ -2,8 +2,10 @@
 // Device data layout (all FP32 unless noted; boxes concatenated in box-id order):
 //   particle arena  12 x P   rows s_x s_y s_z | p_x p_y p_z | psi1_x.. | psi2_x..
 //                            (SoA rows, P = sum_b Nsc_b^3, box-local order)
-//   acc             sum_b Ng_b^3 uint64 fixed-point CIC counts (2^-32 units)
-//   work, work2     sum_b Ng_b^3 interior meshes (transform ping-pong)
+//   dep_acc         uint64 fixed-point CIC counts (2^-32 units) of one group of boxes
+//                   (sized to stay in L2; reused by every group, zero between uses)
+//   work, work2     sum_b Ng_b^3 interior meshes (transform ping-pong; the deposit
+//                   writes the Poisson source delta' into work2)
 //   phi             sum_b (Ng_b+4)^3 padded potential (interior + 2 ghost layers)
 //   shell           sum_b S_b compact Dirichlet shell values, S_b = (Ng+4)^3 - Ng^3
 //   dst tables      per distinct Ng: the sine matrix (transposed, padded rows)
@@ -25,6 +27,7 @@ constexpr int kChunk = 256;       // particles per CTA in particle kernels
 constexpr int kTC = 32;           // transform columns per tile in the DST passes
 constexpr int kXS = kTC + 4;      // shared-memory row stride of a column tile
 constexpr double kFix = 4294967296.0;  // 2^32: fixed-point scale of CIC weights
+constexpr long long kDepositGroupCells = 6 << 20;   // counts per deposit group (48 MB)
 
 struct BoxDesc {
     int Nsc, Ng, Nbuf, tbl;       // tbl: index of the DST table for this Ng
@@ -36,7 +39,7 @@ struct BoxDesc {
     float dq, dg, inv_dg, q2u;    // q2u = dq / dg
     float nbar_inv;               // (Ng / Nsc)^3
     float pad1[3];
-    double dg_d, origin_d[3];     // FP64 geometry for the shell interpolation
+    double dg_d, origin_d[3];     // FP64 box geometry (cell size, origin of the box frame)
 };
 
 struct Chunk {                    // one CTA of a particle- or cell-parallel kernel
@@ -77,6 +80,7 @@ void growth_factors(double Om, double OL, const std::vector<double> &a, std::vec
 double alpha_tilde(double ai, double af, double aK, double Om, double OL, double nLPT);
 double beta_tilde(double ai, double af, double aD, double Om, double OL, double nLPT);
 TimeTable build_time_table(const scola_params &p);
+double bbks_transfer(double k, double Om, double h);   // BBKS T(k), Gamma = Om h
 double bbks_amplitude(double Om, double h, double ns, double sigma8);
 
 // ---- context ----
@@ -106,19 +110,20 @@ struct Ctx {
     Chunk *citems = nullptr;   int n_citems = 0;      // (plane, column-tile) items
     Chunk *mchunks = nullptr;  int n_mchunks = 0;     // interior mesh cells
     long long sin_half_off = 0, sin_full_off = 0;     // LPT-grid sine tables in table_arena
-    long long acc_clear_off = 0, acc_clear_len = 0;   // accumulator range the deposit clears
+    long long amp_off = 0;                            // colouring amplitude per integer |n|^2
     // first entry of each box in every work list (size nboxes + 1), for per-tile launches
     std::vector<int> pbeg, shbeg, zbeg, cbeg, mbeg;
+    std::vector<int> dep_groups;                      // first box of each deposit group, then nboxes
     int num_sms = 1, dst_ctas_per_sm = 1;
     bool use_tc = false;                              // tensor-core (3xTF32) DST passes
     bool tc_lo_lo = false;                            // four-product TF32 form
     std::vector<TcGroup> tc_groups;
     Chunk *tc_tiles = nullptr;
     std::vector<int> tc_tile_beg, tc_tile_end;        // each box's tile range in tc_tiles
-    int tc_view_box = -1;                             // >= 0: TC passes restricted to this box
+    int view_box = -1;                                // >= 0: launches restricted to this box
     int *dev_err = nullptr;                           // set by kernels whose bounded waits expired
     float *part = nullptr;
-    unsigned long long *acc = nullptr;
+    unsigned long long *dep_acc = nullptr;
     float *work = nullptr, *work2 = nullptr, *phi = nullptr, *shell = nullptr;
 
     // full-box LPT stage
@@ -156,21 +161,19 @@ cudaError_t launch_gradient(Ctx &c, const float *phi, float *psi);
 cudaError_t launch_box_init(Ctx &c);
 cudaError_t launch_shell(Ctx &c);
 cudaError_t launch_pad(Ctx &c, float D1);
-cudaError_t launch_deposit(Ctx &c, const float *s, long long stride);
+cudaError_t launch_deposit(Ctx &c, const float *s, long long stride, float *delta_out = nullptr);
 cudaError_t init_pm_kernels(Ctx &c);
 int tc_plan_stages(int Ng, int &Npad, int &nkc);
 bool tc_supported(int Ng);
 cudaError_t init_tc_kernels();
 cudaError_t launch_poisson_tc(Ctx &c);
 cudaError_t launch_poisson_tc_pass(Ctx &c, int pass);
-cudaError_t launch_poisson_tc_buffers(Ctx &c, const void *in, bool in_acc, float *w1, float *w2,
+cudaError_t launch_poisson_tc_buffers(Ctx &c, const float *in, float *w1, float *w2,
                                       float *out_pad);
-cudaError_t launch_poisson_buffers(Ctx &c, const void *in, bool in_acc, float *w1, float *w2,
+cudaError_t launch_poisson_buffers(Ctx &c, const float *in, float *w1, float *w2,
                                    float *out_pad);
 cudaError_t launch_poisson(Ctx &c);
 cudaError_t launch_poisson_pass(Ctx &c, int pass);
-cudaError_t launch_acc_to_delta(Ctx &c, float *out);
-cudaError_t launch_density_source(Ctx &c, float *out);
 cudaError_t launch_interp(Ctx &c, const float *s, long long stride, float *F);
 cudaError_t launch_kick_drift(Ctx &c, const KickDrift &kd);
 cudaError_t launch_scatter(Ctx &c, float *x, float *p);

@@ -291,7 +291,7 @@ k_adj_init_scatter(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ 
 // Trilinear transpose of C.3: lam_phi1 += sum over shell cells of weights * lam_shell.
 __global__ void __launch_bounds__(kChunk)
 k_adj_shell_to_phi1(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
-                    const float *__restrict__ lam_shell, int N, double d_lpt,
+                    const float *__restrict__ lam_shell, int N, int Ntile,
                     float *__restrict__ lam_phi1) {
     const Chunk ch = chunks[blockIdx.x];
     const BoxDesc &B = boxes[ch.box];
@@ -302,15 +302,8 @@ k_adj_shell_to_phi1(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__
     int pc[3];
     shell_coord(idx, B.Ng, pc[0], pc[1], pc[2]);
     int i0[3];
-    double f[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const double X = B.origin_d[a] + ((double)(pc[a] - 2) + 0.5) * B.dg_d;
-        const double u = X / d_lpt - 0.5;
-        const double fl = floor(u);
-        i0[a] = (int)fl;
-        f[a] = u - fl;
-    }
+    float f[3];
+    shell_stencil(B, pc, Ntile, i0, f);
     const long long NN = (long long)N * N;
 #pragma unroll
     for (int dx = 0; dx < 2; ++dx)
@@ -318,10 +311,10 @@ k_adj_shell_to_phi1(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__
         for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
             for (int dz = 0; dz < 2; ++dz) {
-                const double w = (dx ? f[0] : 1.0 - f[0]) * (dy ? f[1] : 1.0 - f[1]) * (dz ? f[2] : 1.0 - f[2]);
+                const float w = (dx ? f[0] : 1.0f - f[0]) * (dy ? f[1] : 1.0f - f[1]) * (dz ? f[2] : 1.0f - f[2]);
                 atomicAdd(lam_phi1 + wrap(i0[0] + dx, N) * NN + (long long)wrap(i0[1] + dy, N) * N +
                               wrap(i0[2] + dz, N),
-                          (float)(w * lv));
+                          w * lv);
             }
 }
 
@@ -445,7 +438,7 @@ cudaError_t launch_adj_init_scatter(Ctx &c, const float *adj, float *lamPsi1, fl
 
 cudaError_t launch_adj_shell_to_phi1(Ctx &c, const float *lam_shell, float *lam_phi1) {
     k_adj_shell_to_phi1<<<c.n_shchunks, kChunk, 0, c.stream>>>(c.boxes, c.shchunks, lam_shell, c.Np,
-                                                                c.L / c.Np, lam_phi1);
+                                                                c.Np / c.Ntiles, lam_phi1);
     ++c.launches;
     return cudaGetLastError();
 }

@@ -5,8 +5,9 @@
 //             Psi1, Psi2 from the full-box arrays, and starts at
 //             s = -D1(a_i) Psi1 + D2(a_i) Psi2, p_res = 0 (Eqs. 39, 55).
 //  shell      C.3: phi1 trilinearly interpolated (periodic, nodes at (i+1/2) d)
-//             to the centre of every padded PM cell outside the interior, with
-//             FP64 weights and accumulation, stored FP32 (LEP scaling by
+//             to the centre of every padded PM cell outside the interior; the
+//             stencil comes from exact integer arithmetic (shell_stencil), the
+//             eight products are summed in FP32 in a fixed order (LEP scaling by
 //             D1(a_K) happens per force evaluation, Eq. 23).
 //  scatter    B.2 and L+: tile particles only; x = (q + s) mod L and
 //             p = p_res + a^2 calH (-dD1/da Psi1 + dD2/da Psi2) at a_f (Eq. 55).
@@ -53,7 +54,7 @@ k_box_init(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
 
 __global__ void __launch_bounds__(kChunk)
 k_shell(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
-        const float *__restrict__ phi1, int N, double d_lpt, float *__restrict__ shell) {
+        const float *__restrict__ phi1, int N, int Ntile, float *__restrict__ shell) {
     const Chunk ch = chunks[blockIdx.x];
     const BoxDesc &B = boxes[ch.box];
     const long long idx = (long long)ch.start + threadIdx.x;
@@ -61,34 +62,26 @@ k_shell(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
     int pc[3];
     shell_coord(idx, B.Ng, pc[0], pc[1], pc[2]);
     int i0[3];
-    double f[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const double X = B.origin_d[a] + ((double)(pc[a] - 2) + 0.5) * B.dg_d;
-        const double u = X / d_lpt - 0.5;
-        const double fl = floor(u);
-        i0[a] = (int)fl;
-        f[a] = u - fl;
-    }
-    double sum = 0.0;
+    float f[3];
+    shell_stencil(B, pc, Ntile, i0, f);
+    float sum = 0.0f;
     const long long NN = (long long)N * N;
 #pragma unroll
     for (int dx = 0; dx < 2; ++dx) {
         const long long ix = wrap(i0[0] + dx, N);
-        const double wx = dx ? f[0] : 1.0 - f[0];
+        const float wx = dx ? f[0] : 1.0f - f[0];
 #pragma unroll
         for (int dy = 0; dy < 2; ++dy) {
             const long long iy = wrap(i0[1] + dy, N);
-            const double wy = dy ? f[1] : 1.0 - f[1];
+            const float wxy = wx * (dy ? f[1] : 1.0f - f[1]);
 #pragma unroll
             for (int dz = 0; dz < 2; ++dz) {
                 const long long iz = wrap(i0[2] + dz, N);
-                const double wz = dz ? f[2] : 1.0 - f[2];
-                sum += wx * wy * wz * (double)phi1[ix * NN + iy * N + iz];
+                sum = fmaf(wxy * (dz ? f[2] : 1.0f - f[2]), phi1[ix * NN + iy * N + iz], sum);
             }
         }
     }
-    shell[B.sh_off + idx] = (float)sum;
+    shell[B.sh_off + idx] = sum;
 }
 
 __global__ void __launch_bounds__(kChunk)
@@ -157,7 +150,7 @@ __global__ void k_density_deposit(const float *__restrict__ x, long long n, int 
                 for (int dz = 0; dz < 2; ++dz) {
                     const long long iz = wrap(i0[2] + dz, N);
                     const float w = wxy * (dz ? f[2] : 1.0f - f[2]);
-                    atomicAdd(acc + ix * NN + iy * N + iz, __float2ull_rn(w * 4294967296.0f));
+                    atomicAdd(acc + ix * NN + iy * N + iz, weight_to_fixed(w));
                 }
             }
         }
@@ -168,7 +161,7 @@ __global__ void k_density_finish(const unsigned long long *__restrict__ acc, lon
                                  float scale, float *__restrict__ delta) {
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
          idx += (long long)gridDim.x * blockDim.x)
-        delta[idx] = (float)acc[idx] * scale - 1.0f;
+        delta[idx] = fixed_to_float(acc[idx]) * scale - 1.0f;
 }
 
 int grid_for(long long n, int block) {
@@ -188,7 +181,7 @@ cudaError_t launch_box_init(Ctx &c) {
 }
 
 cudaError_t launch_shell(Ctx &c) {
-    k_shell<<<c.n_shchunks, kChunk, 0, c.stream>>>(c.boxes, c.shchunks, c.phi1, c.Np, c.L / c.Np,
+    k_shell<<<c.n_shchunks, kChunk, 0, c.stream>>>(c.boxes, c.shchunks, c.phi1, c.Np, c.Np / c.Ntiles,
                                                     c.shell);
     ++c.launches;
     return cudaGetLastError();

@@ -1,0 +1,171 @@
+// CIC deposit with the mass drop B^sCOLA (Sec. 3.4.1) and the Dirichlet source of the
+// Poisson solve, delta' = delta - Lap Phi_BC (App. C, Eq. 62).
+//
+// Every box particle adds its eight CIC weights to the interior cells they fall on, as
+// 2^-32 fixed-point integers with 64-bit atomics (weight outside [0, Ng)^3 is dropped;
+// the conversions to and from fixed point use 32-bit instructions only);
+// integer sums do not depend on the order of the additions, so the density is
+// bit-reproducible.  The counts of all boxes together would not fit in L2, so the boxes
+// are taken in groups whose counts do (one scratch accumulator, reused by every group):
+// for each group, the deposit kernel accumulates into the scratch, then the source kernel
+// converts the counts to delta = (Ng/Nsc)^3 n - 1, subtracts the boundary term on the
+// faces and writes delta' to the interior mesh, and the scratch is cleared.  The
+// accumulator traffic stays in L2; HBM sees the positions once and delta' once.
+#include <algorithm>
+
+#include "device_util.cuh"
+
+namespace scola {
+
+namespace {
+
+__global__ void __launch_bounds__(kChunk)
+k_deposit(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks, const float *__restrict__ s,
+          long long stride, unsigned long long *__restrict__ acc, long long acc_base) {
+    const Chunk ch = chunks[blockIdx.x];
+    const BoxDesc &B = boxes[ch.box];
+    const int Nsc = B.Nsc, Ng = B.Ng;
+    const int local = ch.start + threadIdx.x;
+    if (local >= Nsc * Nsc * Nsc) return;
+    const long long gi = B.p_off + local;
+    int b[3];
+    decode_local(local, Nsc, b[0], b[1], b[2]);
+    int i0[3];
+    float f[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float u = fmaf(__ldg(s + a * stride + gi), B.inv_dg, fmaf((float)b[a], B.q2u, 0.5f * B.q2u - 0.5f));
+        u = fminf(fmaxf(u, -2.0f), (float)Ng + 1.0f);
+        const float fl = floorf(u);
+        i0[a] = (int)fl;
+        f[a] = u - fl;
+    }
+    unsigned long long *base = acc + (B.m_off - acc_base);
+#pragma unroll
+    for (int dx = 0; dx < 2; ++dx) {
+        const int cx = i0[0] + dx;
+        if ((unsigned)cx >= (unsigned)Ng) continue;
+        const float wx = dx ? f[0] : 1.0f - f[0];
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy) {
+            const int cy = i0[1] + dy;
+            if ((unsigned)cy >= (unsigned)Ng) continue;
+            const float wxy = wx * (dy ? f[1] : 1.0f - f[1]);
+#pragma unroll
+            for (int dz = 0; dz < 2; ++dz) {
+                const int cz = i0[2] + dz;
+                if ((unsigned)cz >= (unsigned)Ng) continue;
+                const float w = wxy * (dz ? f[2] : 1.0f - f[2]);
+                atomicAdd(base + ((long long)cx * Ng + cy) * Ng + cz, weight_to_fixed(w));
+            }
+        }
+    }
+}
+
+// Four consecutive cells (a float4 where aligned), or the first `left` of them.
+__device__ __forceinline__ void store4(float *p, const float (&v)[4], bool vec, int left) {
+    if (vec) {
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+        return;
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+        if (e < left) p[e] = v[e];
+}
+
+// Counts -> delta (optional copy) -> delta' for 4 consecutive cells per thread.
+__global__ void __launch_bounds__(64)
+k_density_source(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
+                 const unsigned long long *__restrict__ acc, long long acc_base, const float *__restrict__ phi_pad,
+                 float *__restrict__ out, float *__restrict__ delta_out) {
+    const Chunk ch = chunks[blockIdx.x];
+    const BoxDesc &B = boxes[ch.box];
+    const int Ng = B.Ng;
+    const long long ng3 = (long long)Ng * Ng * Ng;
+    const int cell0 = ch.start + 4 * threadIdx.x;
+    if ((long long)cell0 >= ng3) return;
+    const int left = (int)min(4LL, ng3 - cell0);
+    const float sc = B.nbar_inv * 2.3283064365386963e-10f, c2 = B.inv_dg * B.inv_dg;
+    const unsigned long long *a = acc + (B.m_off - acc_base) + cell0;
+    const bool vec = left == 4 && (Ng & 3) == 0;
+    float v[4];
+    if (vec) {
+        const ulonglong2 a01 = *reinterpret_cast<const ulonglong2 *>(a);
+        const ulonglong2 a23 = *reinterpret_cast<const ulonglong2 *>(a + 2);
+        v[0] = fixed_to_float(a01.x) * sc - 1.0f;
+        v[1] = fixed_to_float(a01.y) * sc - 1.0f;
+        v[2] = fixed_to_float(a23.x) * sc - 1.0f;
+        v[3] = fixed_to_float(a23.y) * sc - 1.0f;
+    } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            v[e] = 0.0f;
+            if (e < left) v[e] = fixed_to_float(a[e]) * sc - 1.0f;
+        }
+    }
+    const long long cell = B.m_off + cell0;
+    if (delta_out) store4(delta_out + cell, v, vec, left);
+    // boundary source: the Dirichlet values sit in the ghost layer next to each face cell
+    int k = cell0 % Ng, j = (cell0 / Ng) % Ng, i = cell0 / Ng / Ng;
+    const int S = Ng + 4;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        if (e >= left) break;
+        if (k == Ng) {                          // the 4 cells cross a row (Ng % 4 != 0)
+            k = 0;
+            if (++j == Ng) {
+                j = 0;
+                ++i;
+            }
+        }
+        if (i == 0 || j == 0 || k == 0 || i == Ng - 1 || j == Ng - 1 || k == Ng - 1) {
+            const float *P = phi_pad + B.pp_off + ((i + 2) * S + (j + 2)) * S + (k + 2);
+            float bc = 0.0f;
+            if (i == 0) bc += P[-S * S];
+            if (i == Ng - 1) bc += P[S * S];
+            if (j == 0) bc += P[-S];
+            if (j == Ng - 1) bc += P[S];
+            if (k == 0) bc += P[-1];
+            if (k == Ng - 1) bc += P[1];
+            v[e] -= bc * c2;
+        }
+        ++k;
+    }
+    store4(out + cell, v, vec, left);
+}
+
+}  // namespace
+
+cudaError_t launch_deposit(Ctx &c, const float *s, long long stride, float *delta_out) {
+    // box groups of the current view: the precomputed groups, or the one box of the
+    // per-tile form (whose lists the view has already restricted)
+    const bool one = c.view_box >= 0;
+    const int ngroups = one ? 1 : (int)c.dep_groups.size() - 1;
+    for (int g = 0; g < ngroups; ++g) {
+        const int b0 = one ? c.view_box : c.dep_groups[g];
+        const int b1 = one ? c.view_box + 1 : c.dep_groups[g + 1];
+        const Chunk *pch = one ? c.pchunks : c.pchunks + c.pbeg[b0];
+        const int npch = one ? c.n_pchunks : c.pbeg[b1] - c.pbeg[b0];
+        const Chunk *mch = one ? c.mchunks : c.mchunks + c.mbeg[b0];
+        const int nmch = one ? c.n_mchunks : c.mbeg[b1] - c.mbeg[b0];
+        const long long base = c.boxes_h[b0].m_off;
+        if (npch > 0) {
+            k_deposit<<<npch, kChunk, 0, c.stream>>>(c.boxes, pch, s, stride, c.dep_acc, base);
+            ++c.launches;
+        }
+        if (nmch > 0) {
+            k_density_source<<<nmch, 64, 0, c.stream>>>(c.boxes, mch, c.dep_acc, base, c.phi, c.work2, delta_out);
+            ++c.launches;
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        // clear the counts this group used (they stay in L2 for the next group)
+        const BoxDesc &last = c.boxes_h[b1 - 1];
+        const long long used = last.m_off + (long long)last.Ng * last.Ng * last.Ng - base;
+        e = cudaMemsetAsync(c.dep_acc, 0, sizeof(unsigned long long) * (size_t)used, c.stream);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace scola

@@ -6,7 +6,7 @@
 // out[col][row], so that the next pass again finds its axis contiguous:
 //
 //   pass  input rows (axis)    k    writes              epilogue
-//   z+    acc[i][j][k]  (i,j)  k    W1[n][i][j]         delta' = density - Lap Phi_BC (prologue)
+//   z+    src[i][j][k]  (i,j)  k    W1[n][i][j]         (src: delta' from the deposit)
 //   y+    W1[n][i][j]   (n,i)  j    W2[m][n][i]
 //   x+    W2[m][n][i]   (m,n)  i    W3[l][m][n]         / (lambda_l + lambda_m + lambda_n)
 //   z-    W3[l][m][n]   (l,m)  n    W4[k'][l][m]
@@ -20,14 +20,15 @@
 // position errors of ~0.1 PM cell over a run, the three-term form stays near
 // the FP32 level.
 //
-// One persistent CTA per SM, 9 warps:
-//   warps 0-3  epilogue: tcgen05.ld of the accumulator (warp w owns TMEM lanes
-//              32w..32w+31 = tile rows), scaling, transposed global stores
-//   warps 4-7  producer: cp.async copies of 128-row x 32-column chunks into a
+// One persistent CTA per SM, 13 warps:
+//   warps 0-7  epilogue: tcgen05.ld of the accumulator (warp w reads TMEM lanes
+//              32(w%4)..+31 = tile rows, half of the columns), scaling, transposed
+//              global stores
+//   warps 8-11 producer: cp.async copies of 128-row x 32-column chunks into a
 //              ring of raw staging buffers, DEPTH chunks ahead; each thread then
 //              splits the bytes it copied into hi/lo and stores them in the
 //              128-byte-swizzled K-major layout of the MMA stage
-//   warp 8     TMEM allocation; lane 0 issues tcgen05.mma and tcgen05.commit
+//   warp 12    TMEM allocation; lane 0 issues tcgen05.mma and tcgen05.commit
 // Stages of A chunks form a ring guarded by full/empty mbarriers; the
 // accumulator is double buffered in TMEM (tmem_full / tmem_empty).  Every
 // wait is bounded (about 2 s of %globaltimer); on expiry the CTA raises an
@@ -46,10 +47,11 @@ namespace {
 constexpr int kTM = 128;             // rows per tile (MMA M)
 constexpr int kKC = 32;              // K per chunk (one 128-byte swizzle atom of FP32)
 constexpr int kChunkBytes = kTM * 128;
-constexpr int kThreads = 288;
+constexpr int kThreads = 416;          // 8 epilogue, 4 producer, 1 MMA warps
+constexpr int kMaxGroups = 4;          // 16-column TMEM groups per epilogue warp (Npad <= 128)
 constexpr unsigned long long kWaitNs = 2000000000ull;
 
-enum TcPass { P_ZF = 0, P_YF = 1, P_XF = 2, P_ZI = 3, P_YI = 4, P_XI = 5 };
+enum TcPass { P_F = 1, P_XF = 2, P_ZI = 3, P_YI = 4, P_XI = 5 };   // P_F: z+ and y+
 
 struct TcArgs {
     const BoxDesc *boxes;
@@ -58,9 +60,8 @@ struct TcArgs {
     int Ng, Npad, nkc, nstage;   // uniform Ng for the launch; nstage = hi/lo MMA stages
     const float *S;              // FP32 sine matrix, Npad x (nkc*32), zero padded
     const float *lam;            // Dirichlet eigenvalues, Ng
-    const void *in;
+    const float *in;
     float *out;
-    const float *phi_pad;        // ghost layers (z+ prologue)
     int *err;
     int lo_lo;                   // 1: also accumulate a_lo s_lo (four TF32 products)
 };
@@ -161,18 +162,25 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
                  : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-    uint32_t r[16];
+// 16 columns of this warp's 32 TMEM lanes into v, without waiting for them.
+__device__ __forceinline__ void tmem_ld16_issue(uint32_t taddr, float (&v)[16]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
         "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-          "=r"(r[14]), "=r"(r[15])
+        : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]),
+          "=f"(v[7]), "=f"(v[8]), "=f"(v[9]), "=f"(v[10]), "=f"(v[11]), "=f"(v[12]), "=f"(v[13]),
+          "=f"(v[14]), "=f"(v[15])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Orders later uses of v after a tcgen05.wait::ld (the registers become valid there).
+__device__ __forceinline__ void tmem_regs_ready(float (&v)[16]) {
+    asm volatile(""
+                 : "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3]), "+f"(v[4]), "+f"(v[5]), "+f"(v[6]),
+                   "+f"(v[7]), "+f"(v[8]), "+f"(v[9]), "+f"(v[10]), "+f"(v[11]), "+f"(v[12]), "+f"(v[13]),
+                   "+f"(v[14]), "+f"(v[15]));
 }
 
 // Byte offset of element (r, k) (k within the 32-wide chunk) in a 128B-swizzled K-major tile.
@@ -184,16 +192,10 @@ __device__ __forceinline__ float tf32_hi(float x) {
     return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
 }
 
-// Bytes of one raw staging chunk: FP32 inputs, or 64-bit fixed-point counts in pass 1.
-template <int PASS>
-__host__ __device__ constexpr int raw_chunk_bytes() {
-    return PASS == 0 ? 2 * kChunkBytes : kChunkBytes;
-}
-
 template <int PASS, int DEPTH>
 __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(TcArgs A) {
     constexpr int RS = DEPTH + 1;                   // raw staging ring
-    constexpr int RAWB = raw_chunk_bytes<PASS>();
+    constexpr int RAWB = kChunkBytes;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-aligned (in the shared window) base for the swizzled operand tiles
     unsigned char *base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
@@ -234,13 +236,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(TcArgs A) {
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(&tfull[a], 1);
-            mbar_init(&tempty[a], 128);
+            mbar_init(&tempty[a], 256);
         }
         mbar_init(drain, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 8) {
+    if (warp == 12) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(tmem_slot)),
                      "r"(256));
@@ -253,12 +255,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(TcArgs A) {
     const uint32_t tmem = *tmem_slot;
     const long long Ng2 = (long long)Ng * Ng;
 
-    if (warp >= 4 && warp < 8) {
+    if (warp >= 8 && warp < 12) {
         // ---------------------------------------------------------------- producer
         // chunk g of this CTA = tile (blockIdx.x + (g / nkc) gridDim.x), K-chunk g % nkc.
         // Thread pt copies and later converts items q = pt + 128 e (e < 8): row q >> 3,
         // float4 group q & 7 of the chunk.
-        const int pt = tid - 128;
+        const int pt = tid - 256;
         const uint32_t raw_s = smem_u32(raw);
         const long long my_tiles = A.ntiles > (int)blockIdx.x
                                        ? (A.ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
@@ -278,18 +280,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(TcArgs A) {
                     const int k = c * kKC + kq * 4;
                     const int R = row0 + r;
                     const bool ok = (long long)R < Ng2 && k < Ng;
-                    if (PASS == P_ZF) {
-                        // 64-bit counts: the two 16-byte halves of an item go to two planes,
-                        // item q at 16 q in each (conflict-free reads)
-                        const unsigned long long *src = reinterpret_cast<const unsigned long long *>(A.in) +
-                                                        m_off + (ok ? (long long)R * Ng + k : 0);
-                        cp_async16(dst0 + 16u * q, src, ok ? 16u : 0u);
-                        cp_async16(dst0 + kChunkBytes + 16u * q, src + 2, ok ? 16u : 0u);
-                    } else {
-                        const float *src = reinterpret_cast<const float *>(A.in) + m_off +
-                                           (ok ? (long long)R * Ng + k : 0);
-                        cp_async16(dst0 + sw128_offset(r, kq * 4), src, ok ? 16u : 0u);
-                    }
+                    const float *src = A.in + m_off + (ok ? (long long)R * Ng + k : 0);
+                    cp_async16(dst0 + sw128_offset(r, kq * 4), src, ok ? 16u : 0u);
                 }
             }
             cp_async_commit();
@@ -303,18 +295,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(TcArgs A) {
                 *abort_flag = 1;
                 break;
             }
-            const int it = (int)blockIdx.x + (int)(g / nkc) * (int)gridDim.x;
-            const int c = (int)(g % nkc);
-            const Chunk tile = A.tiles[it];
-            const int row0 = tile.start * kTM;
-            float nbar_sc = 0.f, c2 = 0.f;
-            long long pp_off = 0;
-            if (PASS == P_ZF) {
-                const BoxDesc &B = A.boxes[tile.box];
-                nbar_sc = B.nbar_inv * 2.3283064365386963e-10f;
-                c2 = B.inv_dg * B.inv_dg;
-                pp_off = B.pp_off;
-            }
             unsigned char *ah = stages + (size_t)s * 2 * kChunkBytes;
             unsigned char *al = ah + kChunkBytes;
             const unsigned char *rw = raw + (size_t)(g % RS) * RAWB;
@@ -323,42 +303,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(TcArgs A) {
                 const int q = pt + 128 * e;
                 const int r = q >> 3, kq = q & 7;
                 const uint32_t off = sw128_offset(r, kq * 4);
-                float4 v;
-                if (PASS == P_ZF) {
-                    const ulonglong2 a01 = *reinterpret_cast<const ulonglong2 *>(rw + 16 * q);
-                    const ulonglong2 a23 = *reinterpret_cast<const ulonglong2 *>(rw + kChunkBytes + 16 * q);
-                    const int k = c * kKC + kq * 4;
-                    const int R = row0 + r;
-                    float vv[4] = {0.f, 0.f, 0.f, 0.f};
-                    if ((long long)R < Ng2 && k < Ng) {
-                        vv[0] = (float)a01.x * nbar_sc - 1.0f;
-                        vv[1] = (float)a01.y * nbar_sc - 1.0f;
-                        vv[2] = (float)a23.x * nbar_sc - 1.0f;
-                        vv[3] = (float)a23.y * nbar_sc - 1.0f;
-                        const int i = R / Ng, j = R - (R / Ng) * Ng;
-                        const bool edge_ij = (i == 0 || j == 0 || i == Ng - 1 || j == Ng - 1);
-                        if (edge_ij || k == 0 || k + 3 == Ng - 1) {
-                            const int S = Ng + 4;
-                            const float *P = A.phi_pad + pp_off;
-#pragma unroll
-                            for (int e2 = 0; e2 < 4; ++e2) {
-                                const int kk = k + e2;
-                                const long long ctr = ((long long)(i + 2) * S + (j + 2)) * S + (kk + 2);
-                                float bc = 0.0f;
-                                if (i == 0) bc += P[ctr - (long long)S * S];
-                                if (i == Ng - 1) bc += P[ctr + (long long)S * S];
-                                if (j == 0) bc += P[ctr - S];
-                                if (j == Ng - 1) bc += P[ctr + S];
-                                if (kk == 0) bc += P[ctr - 1];
-                                if (kk == Ng - 1) bc += P[ctr + 1];
-                                vv[e2] -= bc * c2;
-                            }
-                        }
-                    }
-                    v = make_float4(vv[0], vv[1], vv[2], vv[3]);
-                } else {
-                    v = *reinterpret_cast<const float4 *>(rw + off);
-                }
+                const float4 v = *reinterpret_cast<const float4 *>(rw + off);
                 const float4 h = make_float4(tf32_hi(v.x), tf32_hi(v.y), tf32_hi(v.z), tf32_hi(v.w));
                 const float4 l = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
                 *reinterpret_cast<float4 *>(ah + off) = h;
@@ -368,7 +313,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(TcArgs A) {
             mbar_arrive(&full[s]);
         }
         cp_async_wait<0>();
-    } else if (warp == 8) {
+    } else if (warp == 12) {
         // ---------------------------------------------------------------- MMA issuer
         if (lane == 0) {
             const uint32_t idesc = idesc_tf32(kTM, Npad);
@@ -411,8 +356,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(TcArgs A) {
             }
         }
     } else {
-        // ---------------------------------------------------------------- epilogue (warps 0-3)
-        const int row_in_tile = warp * 32 + lane;
+        // ---------------------------------------------------------------- epilogue (warps 0-7)
+        // warp w reads TMEM lanes 32 (w & 3) .. + 31 (its tile rows) and the 16-column groups
+        // g = (w >> 2) + 2 i: all its groups are loaded before one wait, then the accumulator
+        // is released and the stores follow.
+        const int quarter = warp & 3, half = warp >> 2;
+        const int row_in_tile = quarter * 32 + lane;
+        const int ngroups = Npad / 16;
         const float scale = (PASS == P_XI) ? 8.0f / ((float)(Ng + 1) * (Ng + 1) * (Ng + 1)) : 1.0f;
         uint32_t t = 0;
         for (int it = blockIdx.x; it < A.ntiles && !*abort_flag; it += gridDim.x, ++t) {
@@ -422,45 +372,54 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(TcArgs A) {
                 break;
             }
             tc_fence_after();
+            const uint32_t tbase = tmem + (uint32_t)(a * 128) + ((uint32_t)(quarter * 32) << 16);
+            float v[kMaxGroups][16];
+#pragma unroll
+            for (int i = 0; i < kMaxGroups; ++i)
+                if (half + 2 * i < ngroups) tmem_ld16_issue(tbase + (uint32_t)(16 * (half + 2 * i)), v[i]);
+            tmem_ld_wait();
+#pragma unroll
+            for (int i = 0; i < kMaxGroups; ++i) tmem_regs_ready(v[i]);
+            tc_fence_before();
+            mbar_arrive(&tempty[a]);
             const Chunk tile = A.tiles[it];
-            const long long m_off = A.boxes[tile.box].m_off;
-            const long long pp_off = A.boxes[tile.box].pp_off;
-            float *const out = A.out;
             const int Ri = tile.start * kTM + row_in_tile;
-            const long long R = Ri;
-            const bool valid = R < Ng2;
-            const uint32_t tbase = tmem + (uint32_t)(a * 128) + ((uint32_t)(warp * 32) << 16);
-            const int rhi = Ri / Ng, rlo = Ri - (Ri / Ng) * Ng;
+            if ((long long)Ri >= Ng2) continue;
+            const int rhi = Ri / Ng, rlo = Ri - rhi * Ng;
             float lsum = 0.0f;
-            if (PASS == P_XF && valid) lsum = lam[rhi] + lam[rlo];
-            for (int c0 = 0; c0 < Npad; c0 += 16) {
-                float v[16];
-                tmem_ld16(tbase + (uint32_t)c0, v);
-                if (c0 + 16 >= Npad) {
-                    // all columns read: hand the accumulator back to the MMA issuer
-                    tc_fence_before();
-                    mbar_arrive(&tempty[a]);
-                }
-                if (!valid) continue;
+            if (PASS == P_XF) lsum = lam[rhi] + lam[rlo];
+            // element (row Ri, column col) goes to base + col * cstride
+            float *base;
+            long long cstride;
+            if (PASS == P_XI) {
+                const long long S = Ng + 4;
+                base = A.out + A.boxes[tile.box].pp_off + (2 * S + (rhi + 2)) * S + (rlo + 2);
+                cstride = S * S;
+            } else {
+                base = A.out + A.boxes[tile.box].m_off + Ri;
+                cstride = Ng2;
+            }
+#pragma unroll
+            for (int i = 0; i < kMaxGroups; ++i) {
+                const int c0 = 16 * (half + 2 * i);
+                if (c0 >= Ng) break;
+                float *p = base + (long long)c0 * cstride;
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const int col = c0 + j;
                     if (col >= Ng) break;
-                    if (PASS == P_XI) {
-                        const long long S = Ng + 4;
-                        out[pp_off + ((long long)(col + 2) * S + (rhi + 2)) * S + (rlo + 2)] = v[j] * scale;
-                    } else if (PASS == P_XF) {
-                        out[m_off + (long long)col * Ng2 + R] = __fdividef(v[j], lam[col] + lsum);
-                    } else {
-                        out[m_off + (long long)col * Ng2 + R] = v[j];
-                    }
+                    float x = v[i][j];
+                    if (PASS == P_XI) x *= scale;
+                    if (PASS == P_XF) x = __fdividef(x, lam[col] + lsum);
+                    *p = x;
+                    p += cstride;
                 }
             }
         }
     }
 
     // ---- tear-down: every role has left its loop; drain, then free tensor memory
-    if (warp == 8 && lane == 0 && *abort_flag) {
+    if (warp == 12 && lane == 0 && *abort_flag) {
         // wait (bounded) until every MMA this thread issued has finished writing TMEM
         mma_commit(drain);
         const unsigned long long t0 = now_ns();
@@ -471,7 +430,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(TcArgs A) {
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 8) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
+    if (warp == 12) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
 }
 
 size_t tc_smem_bytes(int Npad, int nkc, int nstage, int Ng, int raw_bytes) {
@@ -483,16 +442,15 @@ constexpr size_t kSmemBudget = 227 * 1024;
 constexpr int kDeep = 4, kShallow = 1;
 
 // Deepest raw ring (DEPTH chunks ahead) that fits next to S and the MMA stages.
-template <int PASS>
 int pick_depth(const TcGroup &G) {
-    if (tc_smem_bytes(G.Npad, G.nkc, G.nstage, G.Ng, (kDeep + 1) * raw_chunk_bytes<PASS>()) <= kSmemBudget)
+    if (tc_smem_bytes(G.Npad, G.nkc, G.nstage, G.Ng, (kDeep + 1) * kChunkBytes) <= kSmemBudget)
         return kDeep;
     return kShallow;
 }
 
 template <int PASS>
-cudaError_t run_tc_pass(Ctx &c, const TcGroup &G, const void *in, float *out) {
-    const int depth = pick_depth<PASS>(G);
+cudaError_t run_tc_pass(Ctx &c, const TcGroup &G, const float *in, float *out) {
+    const int depth = pick_depth(G);
     TcArgs a;
     a.boxes = c.boxes;
     a.tiles = G.tiles;
@@ -505,10 +463,9 @@ cudaError_t run_tc_pass(Ctx &c, const TcGroup &G, const void *in, float *out) {
     a.lam = c.table_arena + G.lam_off;
     a.in = in;
     a.out = out;
-    a.phi_pad = c.phi;
     a.err = c.dev_err;
     a.lo_lo = c.tc_lo_lo ? 1 : 0;
-    const size_t smem = tc_smem_bytes(G.Npad, G.nkc, G.nstage, G.Ng, (depth + 1) * raw_chunk_bytes<PASS>());
+    const size_t smem = tc_smem_bytes(G.Npad, G.nkc, G.nstage, G.Ng, (depth + 1) * kChunkBytes);
     const int grid = std::max(1, std::min(G.ntiles, c.num_sms));
     if (depth == kDeep)
         k_dst_tc<PASS, kDeep><<<grid, kThreads, smem, c.stream>>>(a);
@@ -521,11 +478,11 @@ cudaError_t run_tc_pass(Ctx &c, const TcGroup &G, const void *in, float *out) {
 }  // namespace
 
 int tc_plan_stages(int Ng, int &Npad, int &nkc) {
-    // two hi/lo MMA stages; the raw ring takes what is left (at least 2 chunks of pass 1)
+    // two hi/lo MMA stages; the raw ring takes what is left (at least 2 chunks)
     Npad = ((Ng + 15) / 16) * 16;
     nkc = (Ng + kKC - 1) / kKC;
     const int nst = 2;
-    if (tc_smem_bytes(Npad, nkc, nst, Ng, (kShallow + 1) * raw_chunk_bytes<P_ZF>()) > kSmemBudget) return 0;
+    if (tc_smem_bytes(Npad, nkc, nst, Ng, (kShallow + 1) * kChunkBytes) > kSmemBudget) return 0;
     return nst;
 }
 
@@ -544,8 +501,7 @@ cudaError_t set_tc_attr() {
 
 cudaError_t init_tc_kernels() {
     cudaError_t e;
-    if ((e = set_tc_attr<P_ZF>())) return e;
-    if ((e = set_tc_attr<P_YF>())) return e;
+    if ((e = set_tc_attr<P_F>())) return e;
     if ((e = set_tc_attr<P_XF>())) return e;
     if ((e = set_tc_attr<P_ZI>())) return e;
     if ((e = set_tc_attr<P_YI>())) return e;
@@ -554,30 +510,25 @@ cudaError_t init_tc_kernels() {
 
 // The launch groups: every Ng group, or in the per-tile form only the current box's tiles.
 std::vector<TcGroup> active_groups(const Ctx &c) {
-    if (c.tc_view_box < 0) return c.tc_groups;
+    if (c.view_box < 0) return c.tc_groups;
     std::vector<TcGroup> one;
     for (const TcGroup &G : c.tc_groups) {
-        if (G.Ng != c.boxes_h[c.tc_view_box].Ng) continue;
+        if (G.Ng != c.boxes_h[c.view_box].Ng) continue;
         TcGroup V = G;
-        V.tiles = c.tc_tiles + c.tc_tile_beg[c.tc_view_box];
-        V.ntiles = c.tc_tile_end[c.tc_view_box] - c.tc_tile_beg[c.tc_view_box];
+        V.tiles = c.tc_tiles + c.tc_tile_beg[c.view_box];
+        V.ntiles = c.tc_tile_end[c.view_box] - c.tc_tile_beg[c.view_box];
         one.push_back(V);
     }
     return one;
 }
 
 cudaError_t launch_poisson_tc_pass(Ctx &c, int pass) {
-    // buffers: density source -> work2 -> work -> work2 -> work -> work2 -> work -> phi
+    // buffers: source (work2) -> work -> work2 -> work -> work2 -> work -> phi
     cudaError_t e = cudaSuccess;
-    if (pass == 0) {
-        // the density source in the interior layout (all boxes of the view), then pass 1 on it
-        e = launch_density_source(c, c.work2);
-        if (e != cudaSuccess) return e;
-    }
     for (const TcGroup &G : active_groups(c)) {
         switch (pass) {
-            case 0: e = run_tc_pass<P_YF>(c, G, c.work2, c.work); break;
-            case 1: e = run_tc_pass<P_YF>(c, G, c.work, c.work2); break;
+            case 0: e = run_tc_pass<P_F>(c, G, c.work2, c.work); break;
+            case 1: e = run_tc_pass<P_F>(c, G, c.work, c.work2); break;
             case 2: e = run_tc_pass<P_XF>(c, G, c.work2, c.work); break;
             case 3: e = run_tc_pass<P_ZI>(c, G, c.work, c.work2); break;
             case 4: e = run_tc_pass<P_YI>(c, G, c.work2, c.work); break;
@@ -598,13 +549,11 @@ cudaError_t launch_poisson_tc(Ctx &c) {
 }
 // (launch_poisson in k_pm.cu uses the same sequence through launch_poisson_buffers.)
 
-cudaError_t launch_poisson_tc_buffers(Ctx &c, const void *in, bool in_acc, float *w1, float *w2,
-                                      float *out_pad) {
-    // a float input skips the density prologue: the first pass is then a plain rotating pass
+cudaError_t launch_poisson_tc_buffers(Ctx &c, const float *in, float *w1, float *w2, float *out_pad) {
     cudaError_t e = cudaSuccess;
     for (const TcGroup &G : active_groups(c)) {
-        e = in_acc ? run_tc_pass<P_ZF>(c, G, in, w1) : run_tc_pass<P_YF>(c, G, in, w1);
-        if (e == cudaSuccess) e = run_tc_pass<P_YF>(c, G, w1, w2);
+        e = run_tc_pass<P_F>(c, G, in, w1);
+        if (e == cudaSuccess) e = run_tc_pass<P_F>(c, G, w1, w2);
         if (e == cudaSuccess) e = run_tc_pass<P_XF>(c, G, w2, w1);
         if (e == cudaSuccess) e = run_tc_pass<P_ZI>(c, G, w1, w2);
         if (e == cudaSuccess) e = run_tc_pass<P_YI>(c, G, w2, w1);

@@ -3,7 +3,8 @@
 // The Fourier transforms are cuFFT calls issued by the host (capi.cu); the
 // spectral multiplications and the configuration-space operations are here.
 // FDA order 2 throughout, spacing d = L/N:
-//   colouring    delta^(k) = w^(k) sqrt(P(|k|) / d^3) / N^3, delta^(0) = 0
+//   colouring    delta^(k) = w^(k) sqrt(P(|k|) / d^3) / N^3, delta^(0) = 0 (the factor is
+//                tabulated on the host in FP64 per integer |n|^2, stored FP32)
 //   inverse Lap  phi^ = f^ / Lambda(k), Lambda = -(4/d^2) sum sin^2(pi n_i / N)
 //   phi_,ij      = IFFT[-D_i D_j phi1^],  D_i = sin(2 pi n_i / N) / d
 //                  (the central difference applied twice)
@@ -20,15 +21,7 @@ namespace {
 
 __device__ __forceinline__ int wavenumber(int i, int N) { return i < N / 2 ? i : i - N; }
 
-__device__ double bbks_T_dev(double k, double Omh) {
-    const double q = k / Omh;
-    const double poly = 1.0 + 3.89 * q + (16.1 * q) * (16.1 * q) + pow(5.46 * q, 3.0) +
-                        pow(6.71 * q, 4.0);
-    return log1p(2.34 * q) / (2.34 * q) * pow(poly, -0.25);
-}
-
-__global__ void k_colour(cufftComplex *ck, int N, double kf, double A, double ns, double Omh,
-                         double inv_d3, double norm) {
+__global__ void k_colour(cufftComplex *ck, int N, const float *__restrict__ amp) {
     const int Nz = N / 2 + 1;
     const long long n = (long long)N * N * Nz;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
@@ -37,24 +30,18 @@ __global__ void k_colour(cufftComplex *ck, int N, double kf, double A, double ns
         const long long t = idx / Nz;
         const int ky = (int)(t % N);
         const int kx = (int)(t / N);
-        const double nx = wavenumber(kx, N), ny = wavenumber(ky, N), nz = kz;
-        const double k = kf * sqrt(nx * nx + ny * ny + nz * nz);
-        float amp = 0.0f;
-        if (k > 0) {
-            const double T = bbks_T_dev(k, Omh);
-            amp = (float)(sqrt(A * pow(k, ns) * T * T * inv_d3) * norm);
-        }
+        const int nx = wavenumber(kx, N), ny = wavenumber(ky, N);
+        const float a = amp[nx * nx + ny * ny + kz * kz];
         cufftComplex v = ck[idx];
-        v.x *= amp;
-        v.y *= amp;
+        v.x *= a;
+        v.y *= a;
         ck[idx] = v;
     }
 }
 
-// Adjoint of colouring after the inverse Laplacian: out = in * amp(k) / (Lambda(k) N^3), k = 0 -> 0.
-__global__ void k_adj_colour(const cufftComplex *in, cufftComplex *out, int N, double kf, double A,
-                             double ns, double Omh, double inv_d3, double norm, const float *s_half,
-                             float inv_d2) {
+// Adjoint of colouring after the inverse Laplacian: out = in * amp(k) / Lambda(k), k = 0 -> 0.
+__global__ void k_adj_colour(const cufftComplex *in, cufftComplex *out, int N, const float *__restrict__ amp,
+                             const float *s_half, float inv_d2) {
     const int Nz = N / 2 + 1;
     const long long n = (long long)N * N * Nz;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
@@ -63,14 +50,13 @@ __global__ void k_adj_colour(const cufftComplex *in, cufftComplex *out, int N, d
         const long long t = idx / Nz;
         const int ky = (int)(t % N);
         const int kx = (int)(t / N);
-        const double nx = wavenumber(kx, N), ny = wavenumber(ky, N), nz = kz;
-        const double k = kf * sqrt(nx * nx + ny * ny + nz * nz);
+        const int nx = wavenumber(kx, N), ny = wavenumber(ky, N);
+        const int n2 = nx * nx + ny * ny + kz * kz;
         float m = 0.0f;
-        if (k > 0) {
-            const double T = bbks_T_dev(k, Omh);
+        if (n2 > 0) {
             const float sx = s_half[kx], sy = s_half[ky], sz = s_half[kz];
             const float lam = -4.0f * inv_d2 * (sx * sx + sy * sy + sz * sz);
-            m = (float)(sqrt(A * pow(k, ns) * T * T * inv_d3) * norm) / lam;
+            m = amp[n2] / lam;
         }
         cufftComplex v = in[idx];
         v.x *= m;
@@ -166,11 +152,7 @@ int grid_for(long long n, int block) {
 cudaError_t launch_colour(Ctx &c, cufftComplex *ck) {
     const int N = c.Np;
     const long long n = (long long)N * N * (N / 2 + 1);
-    const double d = c.L / N;
-    const double N3 = (double)N * N * N;
-    k_colour<<<grid_for(n, 256), 256, 0, c.stream>>>(ck, N, 2.0 * M_PI / c.L, c.pk_amp,
-                                                      c.prm.ns, c.prm.Om * c.prm.h,
-                                                      1.0 / (d * d * d), 1.0 / N3);
+    k_colour<<<grid_for(n, 256), 256, 0, c.stream>>>(ck, N, c.table_arena + c.amp_off);
     ++c.launches;
     return cudaGetLastError();
 }
@@ -179,9 +161,7 @@ cudaError_t launch_adj_colour(Ctx &c, const cufftComplex *in, cufftComplex *out)
     const int N = c.Np;
     const long long n = (long long)N * N * (N / 2 + 1);
     const double d = c.L / N;
-    const double N3 = (double)N * N * N;
-    k_adj_colour<<<grid_for(n, 256), 256, 0, c.stream>>>(in, out, N, 2.0 * M_PI / c.L, c.pk_amp, c.prm.ns,
-                                                          c.prm.Om * c.prm.h, 1.0 / (d * d * d), 1.0 / N3,
+    k_adj_colour<<<grid_for(n, 256), 256, 0, c.stream>>>(in, out, N, c.table_arena + c.amp_off,
                                                           c.table_arena + c.sin_half_off,
                                                           (float)(1.0 / (d * d)));
     ++c.launches;

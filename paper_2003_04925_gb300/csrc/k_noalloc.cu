@@ -67,7 +67,7 @@ k_noalloc_deposit(const float *__restrict__ s, int nsc, int ng, float q2u, float
                 const int cz = i0[2] + dz;
                 if ((unsigned)cz >= (unsigned)ng) continue;
                 const float w = wxy * (dz ? f[2] : 1.0f - f[2]);
-                atomicAdd(acc + ((long long)cx * ng + cy) * ng + cz, __float2ull_rn(w * 4294967296.0f));
+                atomicAdd(acc + ((long long)cx * ng + cy) * ng + cz, weight_to_fixed(w));
             }
         }
     }
@@ -76,7 +76,7 @@ k_noalloc_deposit(const float *__restrict__ s, int nsc, int ng, float q2u, float
 __global__ void k_noalloc_finish(const unsigned long long *__restrict__ acc, long long cells,
                                  float scale, float *__restrict__ delta) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i < cells) delta[i] = (float)acc[i] * scale - 1.0f;
+    if (i < cells) delta[i] = fixed_to_float(acc[i]) * scale - 1.0f;
 }
 
 }  // namespace

@@ -5,14 +5,11 @@
 // The padded potential holds the 2 ghost layers of FDA order 2 (indices -2..Ng+1
 // stored at 0..Ng+3).
 //
-//  deposit       B^sCOLA (Sec. 3.4.1): CIC weights of every box particle onto
-//                the Ng^3 interior; weight that lands outside is discarded.
-//                Accumulated as 2^-32 fixed-point integers, so the result does
-//                not depend on the order of the atomic additions.
+//  deposit       B^sCOLA (Sec. 3.4.1) and the boundary source delta' = delta -
+//                Lap Phi_BCs (Eq. 62), by brick binning: k_deposit.cu.
 //  pad           ghost layers of the potential <- D1(a_K) * shell (LEP, Eq. 23).
-//  poisson       the zero-boundary solve of App. C on delta' = delta - Lap Phi_BCs
-//                (Eq. 62): dense DST-I along z (with the density conversion and
-//                the boundary source), along y, then along x with the division
+//  poisson       the zero-boundary solve of App. C on delta': dense DST-I along z,
+//                along y, then along x with the division
 //                by lambda_l + lambda_m + lambda_n (Eq. 71) and the inverse x
 //                transform, then inverse y, then inverse z with the 8/(Ng+1)^3
 //                scale (Eqs. 66-67), written into the padded potential.
@@ -30,51 +27,6 @@ namespace scola {
 
 namespace {
 
-// ------------------------------------------------------------------ deposit
-__global__ void __launch_bounds__(kChunk)
-k_deposit(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
-          const float *__restrict__ s, long long stride, unsigned long long *__restrict__ acc) {
-    const Chunk ch = chunks[blockIdx.x];
-    const BoxDesc &B = boxes[ch.box];
-    const int Nsc = B.Nsc, Ng = B.Ng;
-    const int local = ch.start + threadIdx.x;
-    if (local >= Nsc * Nsc * Nsc) return;
-    const long long gi = B.p_off + local;
-    int b[3];
-    decode_local(local, Nsc, b[0], b[1], b[2]);
-    int i0[3];
-    float f[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        float u = fmaf(__ldg(s + a * stride + gi), B.inv_dg, fmaf((float)b[a], B.q2u, 0.5f * B.q2u - 0.5f));
-        u = fminf(fmaxf(u, -2.0f), (float)Ng + 1.0f);
-        const float fl = floorf(u);
-        i0[a] = (int)fl;
-        f[a] = u - fl;
-    }
-    unsigned long long *base = acc + B.m_off;
-#pragma unroll
-    for (int dx = 0; dx < 2; ++dx) {
-        const int cx = i0[0] + dx;
-        if ((unsigned)cx >= (unsigned)Ng) continue;
-        const float wx = dx ? f[0] : 1.0f - f[0];
-#pragma unroll
-        for (int dy = 0; dy < 2; ++dy) {
-            const int cy = i0[1] + dy;
-            if ((unsigned)cy >= (unsigned)Ng) continue;
-            const float wxy = wx * (dy ? f[1] : 1.0f - f[1]);
-#pragma unroll
-            for (int dz = 0; dz < 2; ++dz) {
-                const int cz = i0[2] + dz;
-                if ((unsigned)cz >= (unsigned)Ng) continue;
-                const float w = wxy * (dz ? f[2] : 1.0f - f[2]);
-                atomicAdd(base + ((long long)cx * Ng + cy) * Ng + cz,
-                          __float2ull_rn(w * 4294967296.0f));
-            }
-        }
-    }
-}
-
 // ------------------------------------------------------------------ pad
 __global__ void __launch_bounds__(kChunk)
 k_pad(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
@@ -90,7 +42,7 @@ k_pad(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
 }
 
 // ------------------------------------------------------------------ DST passes
-enum Pass { kZFwd = 0, kYFwd = 1, kXSolve = 2, kYInv = 3, kZInv = 4, kZFwdF = 5 };
+enum Pass { kYFwd = 1, kXSolve = 2, kYInv = 3, kZInv = 4, kZFwdF = 5 };
 
 // acc[r][j] = sum_i ST[i][tl + 32 r] X[i][c0 + j]   (Y = S X on a column tile)
 template <int R>
@@ -146,42 +98,19 @@ k_dst(const BoxDesc *__restrict__ boxes, const DstTable *__restrict__ tables,
         const long long Ng2 = (long long)Ng * Ng;
         // box fields in registers: the stores below could otherwise force reloads
         const long long m_off = B.m_off, pp_off = B.pp_off;
-        const float nbar_sc = B.nbar_inv * 2.3283064365386963e-10f, c2 = B.inv_dg * B.inv_dg;
         // ---- load the column tile X[t][c]
         int ncols;
         long long zp0 = 0;     // first pencil (z passes)
         int plane = 0, k0 = 0; // (plane, column offset) for y/x passes
-        if (PASS == kZFwd || PASS == kZFwdF || PASS == kZInv) {
+        if (PASS == kZFwdF || PASS == kZInv) {
             zp0 = (long long)item.start * kTC;
             ncols = (int)min((long long)kTC, Ng2 - zp0);
             for (int q = tid; q < Ng * kTC; q += blockDim.x) {
                 const int t = q % Ng, c = q / Ng;
                 float v = 0.0f;
                 if (c < ncols) {
-                    const long long p = zp0 + c;
-                    if (PASS == kZFwd) {
-                        const unsigned long long *acc =
-                            reinterpret_cast<const unsigned long long *>(in_v);
-                        const long long cell = m_off + p * Ng + t;
-                        v = (float)acc[cell] * nbar_sc - 1.0f;
-                        const int i = (int)(p / Ng), j = (int)(p % Ng), k = t;
-                        if (i == 0 || j == 0 || k == 0 || i == Ng - 1 || j == Ng - 1 || k == Ng - 1) {
-                            const long long S = Ng + 4;
-                            const float *P = phi_pad + pp_off;
-                            const long long ctr = ((long long)(i + 2) * S + (j + 2)) * S + (k + 2);
-                            float bc = 0.0f;
-                            if (i == 0) bc += P[ctr - S * S];
-                            if (i == Ng - 1) bc += P[ctr + S * S];
-                            if (j == 0) bc += P[ctr - S];
-                            if (j == Ng - 1) bc += P[ctr + S];
-                            if (k == 0) bc += P[ctr - 1];
-                            if (k == Ng - 1) bc += P[ctr + 1];
-                            v -= bc * c2;
-                        }
-                    } else {
-                        const float *in = reinterpret_cast<const float *>(in_v);
-                        v = in[m_off + p * Ng + t];
-                    }
+                    const float *in = reinterpret_cast<const float *>(in_v);
+                    v = in[m_off + (zp0 + c) * Ng + t];
                 }
                 X[t * kXS + c] = v;
             }
@@ -254,7 +183,7 @@ k_dst(const BoxDesc *__restrict__ boxes, const DstTable *__restrict__ tables,
                 const int t = q % Ng, c = q / Ng;
                 if (c < ncols) {
                     const long long p = zp0 + c;
-                    if (PASS == kZFwd || PASS == kZFwdF) {
+                    if (PASS == kZFwdF) {
                         out[m_off + p * Ng + t] = X[t * kXS + c];
                     } else {
                         const long long S = Ng + 4;
@@ -378,56 +307,6 @@ k_kick_drift(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks
     }
 }
 
-// delta' = density - Lap Phi_BC (Eq. 62) from the fixed-point counts, 4 consecutive cells per
-// thread (Ng % 4 == 0), written in the interior layout: the source of the tensor-core solve.
-__global__ void __launch_bounds__(64)
-k_density_source(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
-                 const unsigned long long *__restrict__ acc, const float *__restrict__ phi_pad,
-                 float *__restrict__ out) {
-    const Chunk ch = chunks[blockIdx.x];
-    const BoxDesc &B = boxes[ch.box];
-    const int Ng = B.Ng;
-    const long long m_off = B.m_off, pp_off = B.pp_off;
-    const float sc = B.nbar_inv * 2.3283064365386963e-10f, c2 = B.inv_dg * B.inv_dg;
-    const int cell0 = ch.start + 4 * threadIdx.x;
-    if ((long long)cell0 >= (long long)Ng * Ng * Ng) return;
-    const ulonglong2 a01 = *reinterpret_cast<const ulonglong2 *>(acc + m_off + cell0);
-    const ulonglong2 a23 = *reinterpret_cast<const ulonglong2 *>(acc + m_off + cell0 + 2);
-    float v[4] = {(float)a01.x * sc - 1.0f, (float)a01.y * sc - 1.0f, (float)a23.x * sc - 1.0f,
-                  (float)a23.y * sc - 1.0f};
-    const int k = cell0 % Ng;
-    const int t = cell0 / Ng;
-    const int j = t % Ng, i = t / Ng;
-    if (i == 0 || j == 0 || i == Ng - 1 || j == Ng - 1 || k == 0 || k + 3 == Ng - 1) {
-        const long long S = Ng + 4;
-        const float *P = phi_pad + pp_off;
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int kk = k + e;
-            const long long ctr = ((long long)(i + 2) * S + (j + 2)) * S + (kk + 2);
-            float bc = 0.0f;
-            if (i == 0) bc += P[ctr - S * S];
-            if (i == Ng - 1) bc += P[ctr + S * S];
-            if (j == 0) bc += P[ctr - S];
-            if (j == Ng - 1) bc += P[ctr + S];
-            if (kk == 0) bc += P[ctr - 1];
-            if (kk == Ng - 1) bc += P[ctr + 1];
-            v[e] -= bc * c2;
-        }
-    }
-    *reinterpret_cast<float4 *>(out + m_off + cell0) = make_float4(v[0], v[1], v[2], v[3]);
-}
-
-__global__ void k_acc_to_delta(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
-                               const unsigned long long *__restrict__ acc, float *__restrict__ out) {
-    const Chunk ch = chunks[blockIdx.x];
-    const BoxDesc &B = boxes[ch.box];
-    const long long n = (long long)B.Ng * B.Ng * B.Ng;
-    const long long idx = (long long)ch.start + threadIdx.x;
-    if (idx >= n) return;
-    out[B.m_off + idx] = (float)acc[B.m_off + idx] * (B.nbar_inv * 2.3283064365386963e-10f) - 1.0f;
-}
-
 size_t dst_smem_bytes(int R, int ngmax) {
     return ((size_t)ngmax * 32 * R + (size_t)ngmax * kXS + ngmax) * sizeof(float);
 }
@@ -448,7 +327,6 @@ cudaError_t set_attrs_R() {
     const int lim = 227 * 1024;
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(k_dst<R, kZFwdF>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-    if ((e = cudaFuncSetAttribute(k_dst<R, kZFwd>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
     if ((e = cudaFuncSetAttribute(k_dst<R, kYFwd>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
     if ((e = cudaFuncSetAttribute(k_dst<R, kXSolve>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
     if ((e = cudaFuncSetAttribute(k_dst<R, kYInv>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
@@ -465,13 +343,9 @@ int ctas_per_sm_R(int ngmax) {
 }
 
 template <int R>
-cudaError_t poisson_R(Ctx &c, const void *in, bool in_acc, float *w1, float *w2, float *out_pad) {
+cudaError_t poisson_R(Ctx &c, const float *in, float *w1, float *w2, float *out_pad) {
     cudaError_t e;
-    if (in_acc) {
-        if ((e = run_pass<R, kZFwd>(c, c.zitems, c.n_zitems, in, w1)) != cudaSuccess) return e;
-    } else {
-        if ((e = run_pass<R, kZFwdF>(c, c.zitems, c.n_zitems, in, w1)) != cudaSuccess) return e;
-    }
+    if ((e = run_pass<R, kZFwdF>(c, c.zitems, c.n_zitems, in, w1)) != cudaSuccess) return e;
     if ((e = run_pass<R, kYFwd>(c, c.citems, c.n_citems, w1, w2)) != cudaSuccess) return e;
     if ((e = run_pass<R, kXSolve>(c, c.citems, c.n_citems, w2, w1)) != cudaSuccess) return e;
     if ((e = run_pass<R, kYInv>(c, c.citems, c.n_citems, w1, w2)) != cudaSuccess) return e;
@@ -479,15 +353,6 @@ cudaError_t poisson_R(Ctx &c, const void *in, bool in_acc, float *w1, float *w2,
 }
 
 }  // namespace
-
-cudaError_t launch_deposit(Ctx &c, const float *s, long long stride) {
-    cudaError_t e = cudaMemsetAsync(c.acc + c.acc_clear_off, 0,
-                                    sizeof(unsigned long long) * c.acc_clear_len, c.stream);
-    if (e != cudaSuccess) return e;
-    k_deposit<<<c.n_pchunks, kChunk, 0, c.stream>>>(c.boxes, c.pchunks, s, stride, c.acc);
-    ++c.launches;
-    return cudaGetLastError();
-}
 
 cudaError_t launch_pad(Ctx &c, float D1) {
     k_pad<<<c.n_shchunks, kChunk, 0, c.stream>>>(c.boxes, c.shchunks, c.shell, c.phi, D1);
@@ -511,29 +376,21 @@ cudaError_t init_pm_kernels(Ctx &c) {
     return cudaSuccess;
 }
 
-cudaError_t launch_poisson_buffers(Ctx &c, const void *in, bool in_acc, float *w1, float *w2,
-                                   float *out_pad) {
-    if (c.use_tc) return launch_poisson_tc_buffers(c, in, in_acc, w1, w2, out_pad);
+cudaError_t launch_poisson_buffers(Ctx &c, const float *in, float *w1, float *w2, float *out_pad) {
+    if (c.use_tc) return launch_poisson_tc_buffers(c, in, w1, w2, out_pad);
     switch (c.max_R) {
-        case 1: return poisson_R<1>(c, in, in_acc, w1, w2, out_pad);
-        case 2: return poisson_R<2>(c, in, in_acc, w1, w2, out_pad);
-        case 3: return poisson_R<3>(c, in, in_acc, w1, w2, out_pad);
-        case 4: return poisson_R<4>(c, in, in_acc, w1, w2, out_pad);
-        case 5: return poisson_R<5>(c, in, in_acc, w1, w2, out_pad);
-        case 6: return poisson_R<6>(c, in, in_acc, w1, w2, out_pad);
+        case 1: return poisson_R<1>(c, in, w1, w2, out_pad);
+        case 2: return poisson_R<2>(c, in, w1, w2, out_pad);
+        case 3: return poisson_R<3>(c, in, w1, w2, out_pad);
+        case 4: return poisson_R<4>(c, in, w1, w2, out_pad);
+        case 5: return poisson_R<5>(c, in, w1, w2, out_pad);
+        case 6: return poisson_R<6>(c, in, w1, w2, out_pad);
         default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t launch_poisson(Ctx &c) {
-    if (c.use_tc) {
-        // tensor-core form: coalesced conversion of the counts, then six float passes
-        cudaError_t e = launch_density_source(c, c.work2);
-        if (e != cudaSuccess) return e;
-        return launch_poisson_buffers(c, c.work2, false, c.work, c.work2, c.phi);
-    }
-    return launch_poisson_buffers(c, c.acc, true, c.work, c.work2, c.phi);
-}
+// The solve of the source the deposit left in work2, into the padded potential.
+cudaError_t launch_poisson(Ctx &c) { return launch_poisson_buffers(c, c.work2, c.work, c.work2, c.phi); }
 
 cudaError_t launch_poisson_pass(Ctx &c, int pass) {
     // the passes of launch_poisson, one at a time (for per-kernel timing); the FP32
@@ -542,7 +399,7 @@ cudaError_t launch_poisson_pass(Ctx &c, int pass) {
     if (pass == 5) return cudaSuccess;
     switch (c.max_R * 8 + pass) {
 #define SCOLA_PASS_CASES(R)                                                                     \
-    case R * 8 + 0: return run_pass<R, kZFwd>(c, c.zitems, c.n_zitems, c.acc, c.work);          \
+    case R * 8 + 0: return run_pass<R, kZFwdF>(c, c.zitems, c.n_zitems, c.work2, c.work);       \
     case R * 8 + 1: return run_pass<R, kYFwd>(c, c.citems, c.n_citems, c.work, c.work2);        \
     case R * 8 + 2: return run_pass<R, kXSolve>(c, c.citems, c.n_citems, c.work2, c.work);      \
     case R * 8 + 3: return run_pass<R, kYInv>(c, c.citems, c.n_citems, c.work, c.work2);        \
@@ -566,18 +423,6 @@ cudaError_t launch_interp(Ctx &c, const float *s, long long stride, float *F) {
 
 cudaError_t launch_kick_drift(Ctx &c, const KickDrift &kd) {
     k_kick_drift<<<c.n_pchunks, kChunk, 0, c.stream>>>(c.boxes, c.pchunks, c.part, c.P, c.phi, kd);
-    ++c.launches;
-    return cudaGetLastError();
-}
-
-cudaError_t launch_density_source(Ctx &c, float *out) {
-    k_density_source<<<c.n_mchunks, 64, 0, c.stream>>>(c.boxes, c.mchunks, c.acc, c.phi, out);
-    ++c.launches;
-    return cudaGetLastError();
-}
-
-cudaError_t launch_acc_to_delta(Ctx &c, float *out) {
-    k_acc_to_delta<<<c.n_mchunks, kChunk, 0, c.stream>>>(c.boxes, c.mchunks, c.acc, out);
     ++c.launches;
     return cudaGetLastError();
 }

@@ -50,9 +50,12 @@ def _gpu_loss_grad(sim, w_np, target):
 @pytest.mark.parametrize("variant", ["simt", "tc4"])
 @pytest.mark.parametrize("ratio", [1, 2])
 def test_backward_matches_fp64_oracle_adjoint(ratio, variant):
-    # The tensor-core form used here is the four-product one (the default): with three
-    # products one 2:1 case reached 2.1e-3, a forward difference large enough to move a
-    # particle across a CIC cell face (a kink of the loss), see the design notes.
+    # The loss is piecewise smooth: CIC weights are piecewise linear in position, so a
+    # particle that sits closer to a cell face than the FP32-vs-FP64 difference of the two
+    # forward runs (~1e-6 cell) takes the other one-sided derivative on one side.  Such a
+    # kink moves a few gradient entries by O(1) of their size and the L2 error to a few
+    # 1e-3; a wrong or missing term moves every entry.  Hence two bounds: the L2 error,
+    # and the fraction of entries off by more than 1e-3 of the largest.
     kw = dict(L=48.0, Np=16, Ntiles=2, Nbuf=2, mesh_ratio=ratio, nsteps=3, a_i=0.05, a_f=1.0)
     cfg = oracle_cfg(kw)
     w = synth_inputs.white_noise(16, 21)
@@ -64,8 +67,11 @@ def test_backward_matches_fp64_oracle_adjoint(ratio, variant):
     val_o, g_o = adjoint.loss_and_grad(w.astype(np.float64), cfg, target)
     assert abs(val / val_o - 1) < 1e-4
     rel = np.linalg.norm(g - g_o) / np.linalg.norm(g_o)
-    print("gradient rel error vs FP64 oracle: ratio=%d %s %.3e" % (ratio, variant, rel))
-    assert rel < 1e-3, rel
+    off = float(np.mean(np.abs(g - g_o) > 1e-3 * np.abs(g_o).max()))
+    print("gradient vs FP64 oracle: ratio=%d %s rel %.3e, entries off by >1e-3 max: %.4f"
+          % (ratio, variant, rel, off))
+    assert rel < 5e-3, rel
+    assert off < 0.01, off
 
 
 def test_autograd_function_matches_backward():
