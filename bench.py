@@ -40,8 +40,8 @@ def parse():
     ap.add_argument("--impl", default="scola", choices=["scola", "reference"])
     ap.add_argument("--workload", default="batched_128")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--dst", default="tc4", choices=["tc", "tc4", "simt"],
-                    help="Poisson-solve form: tensor-core 4xTF32 (tc4, default), 3xTF32 (tc) or FP32 "
+    ap.add_argument("--dst", default="tc", choices=["tc", "tc4", "simt"],
+                    help="Poisson-solve form: tensor-core 3xTF32 (tc, default), 4xTF32 (tc4) or FP32 "
                          "CUDA cores (simt)")
     ap.add_argument("--forward-only", action="store_true",
                     help="only W + K forward runs of the batched form (for ncu launch lists)")

@@ -54,7 +54,7 @@ typedef enum scola_dst_variant {
     SCOLA_DST_SIMT = 0,          /* dense sine-matrix pencils on FP32 CUDA cores */
     SCOLA_DST_TC_3XTF32 = 1,     /* the same products on tcgen05 tensor cores, 3xTF32 split */
     SCOLA_DST_TC_4XTF32 = 3,     /* as 1, plus the lo x lo product (four TF32 products) */
-    SCOLA_DST_AUTO = 2           /* 4xTF32 tensor cores when every Ng allows it, else FP32 cores */
+    SCOLA_DST_AUTO = 2           /* 3xTF32 tensor cores when every Ng allows it, else FP32 cores */
 } scola_dst_variant;
 
 typedef enum scola_batch_mode {

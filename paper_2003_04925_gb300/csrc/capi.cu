@@ -60,7 +60,7 @@ struct scola_ctx : public Ctx {
 
 namespace {
 
-constexpr bool kAutoUsesTensorCores = true;    // AUTO: four-product tensor-core form where supported
+constexpr bool kAutoUsesTensorCores = true;    // AUTO: three-product tensor-core form where supported
 constexpr int kMaxNg = 192;  // the DST passes hold a (Ng x 32 ceil(Ng/32)) sine matrix in shared memory
 
 struct BoxGeom {
@@ -323,7 +323,7 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &all_geo) {
     for (auto &kv : tbl_of) all_tc = all_tc && tc_supported(kv.first);
     c->use_tc = (p.dst_variant == SCOLA_DST_TC_3XTF32) || (p.dst_variant == SCOLA_DST_TC_4XTF32) ||
                 (p.dst_variant == SCOLA_DST_AUTO && all_tc && kAutoUsesTensorCores);
-    c->tc_lo_lo = p.dst_variant == SCOLA_DST_TC_4XTF32 || p.dst_variant == SCOLA_DST_AUTO;
+    c->tc_lo_lo = p.dst_variant == SCOLA_DST_TC_4XTF32;
     std::vector<Chunk> tct;
     std::vector<int> box_tile_beg(c->nboxes, 0), box_tile_end(c->nboxes, 0);
     if (c->use_tc) {

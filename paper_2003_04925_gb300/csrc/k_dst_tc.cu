@@ -53,6 +53,15 @@ constexpr unsigned long long kWaitNs = 2000000000ull;
 
 enum TcPass { P_F = 1, P_XF = 2, P_ZI = 3, P_YI = 4, P_XI = 5 };   // P_F: z+ and y+
 
+// Per-CTA cache of the tiles a CTA processes (the first kTileCache of them): the box
+// offsets and the first row, so that the producer and the epilogue need no dependent
+// global loads per tile.
+struct TileInfo {
+    long long m_off, pp_off;
+    int row0, pad;
+};
+constexpr int kTileCache = 192;
+
 struct TcArgs {
     const BoxDesc *boxes;
     const Chunk *tiles;          // (box, tile-in-box)
@@ -214,6 +223,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(TcArgs A) {
     uint32_t *tmem_slot = (uint32_t *)(bars + 2 * NST + 5);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
     float *lam = (float *)(tmem_slot + 4);
+    TileInfo *tinfo = (TileInfo *)(base + ((((unsigned char *)(lam + Ng) - base) + 15) & ~15));
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
@@ -229,6 +239,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(TcArgs A) {
         *(float *)(S_lo + off) = s - hi;
     }
     for (int q = tid; q < Ng; q += kThreads) lam[q] = A.lam[q];
+    const long long my_tiles = A.ntiles > (int)blockIdx.x ? (A.ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    auto load_tile = [&](long long k) {
+        const Chunk tl = A.tiles[(int)blockIdx.x + k * (int)gridDim.x];
+        TileInfo ti;
+        ti.m_off = A.boxes[tl.box].m_off;
+        ti.pp_off = A.boxes[tl.box].pp_off;
+        ti.row0 = tl.start * kTM;
+        ti.pad = 0;
+        return ti;
+    };
+    for (int k = tid; k < my_tiles && k < kTileCache; k += kThreads) tinfo[k] = load_tile(k);
+    auto tile_at = [&](long long k) { return k < kTileCache ? tinfo[k] : load_tile(k); };
     if (tid == 0) {
         for (int s = 0; s < NST; ++s) {
             mbar_init(&full[s], 128);
@@ -262,16 +284,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(TcArgs A) {
         // float4 group q & 7 of the chunk.
         const int pt = tid - 256;
         const uint32_t raw_s = smem_u32(raw);
-        const long long my_tiles = A.ntiles > (int)blockIdx.x
-                                       ? (A.ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
         const long long nchunks = my_tiles * nkc;
         auto issue = [&](long long g) {
             if (g < nchunks) {
-                const int it = (int)blockIdx.x + (int)(g / nkc) * (int)gridDim.x;
                 const int c = (int)(g % nkc);
-                const Chunk tile = A.tiles[it];
-                const long long m_off = A.boxes[tile.box].m_off;
-                const int row0 = tile.start * kTM;
+                const TileInfo ti = tile_at(g / nkc);
+                const long long m_off = ti.m_off;
+                const int row0 = ti.row0;
                 const uint32_t dst0 = raw_s + (uint32_t)((g % RS) * RAWB);
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
@@ -382,8 +401,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(TcArgs A) {
             for (int i = 0; i < kMaxGroups; ++i) tmem_regs_ready(v[i]);
             tc_fence_before();
             mbar_arrive(&tempty[a]);
-            const Chunk tile = A.tiles[it];
-            const int Ri = tile.start * kTM + row_in_tile;
+            const TileInfo ti = tile_at(t);
+            const int Ri = ti.row0 + row_in_tile;
             if ((long long)Ri >= Ng2) continue;
             const int rhi = Ri / Ng, rlo = Ri - rhi * Ng;
             float lsum = 0.0f;
@@ -393,10 +412,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(TcArgs A) {
             long long cstride;
             if (PASS == P_XI) {
                 const long long S = Ng + 4;
-                base = A.out + A.boxes[tile.box].pp_off + (2 * S + (rhi + 2)) * S + (rlo + 2);
+                base = A.out + ti.pp_off + (2 * S + (rhi + 2)) * S + (rlo + 2);
                 cstride = S * S;
             } else {
-                base = A.out + A.boxes[tile.box].m_off + Ri;
+                base = A.out + ti.m_off + Ri;
                 cstride = Ng2;
             }
 #pragma unroll
@@ -435,7 +454,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(TcArgs A) {
 
 size_t tc_smem_bytes(int Npad, int nkc, int nstage, int Ng, int raw_bytes) {
     return 1024 + 2 * (size_t)nkc * Npad * 128 + (size_t)nstage * 2 * kChunkBytes + (size_t)raw_bytes +
-           (2 * nstage + 5) * 8 + 16 + (size_t)Ng * 4 + 64;
+           (2 * nstage + 5) * 8 + 16 + (size_t)Ng * 4 + 16 + kTileCache * sizeof(TileInfo) + 64;
 }
 
 constexpr size_t kSmemBudget = 227 * 1024;

@@ -47,37 +47,37 @@ def _gpu_loss_grad(sim, w_np, target):
     return float(np.sum((dd - target) ** 2)), g.cpu().numpy().astype(np.float64)
 
 
-@pytest.mark.parametrize("variant", ["simt", "tc4"])
+@pytest.mark.parametrize("variant", ["simt", "tc", "tc4"])
 @pytest.mark.parametrize("ratio", [1, 2])
 def test_backward_matches_fp64_oracle_adjoint(ratio, variant):
     # The loss is piecewise smooth: CIC weights are piecewise linear in position, so a
     # particle that sits closer to a cell face than the FP32-vs-FP64 difference of the two
-    # forward runs (~1e-6 cell) takes the other one-sided derivative on one side.  Such a
-    # kink moves a few gradient entries by O(1) of their size and the L2 error to a few
-    # 1e-3; a wrong or missing term moves every entry.  Hence two bounds: the L2 error,
-    # and the fraction of entries off by more than 1e-3 of the largest.
+    # forward runs takes the other one-sided derivative there (a kink).  Seen once: the
+    # tensor-core run of seed 21 at 2:1 gives 2.1e-3 while seeds 23-26 give ~5e-5.  A
+    # wrong or missing term moves every seed; hence the median over three seeds is held
+    # to 1e-3 and every seed to 5e-3.
     kw = dict(L=48.0, Np=16, Ntiles=2, Nbuf=2, mesh_ratio=ratio, nsteps=3, a_i=0.05, a_f=1.0)
     cfg = oracle_cfg(kw)
-    w = synth_inputs.white_noise(16, 21)
     target = _target(kw, 22)
     sim = _sim(kw, variant)
-    val, g = _gpu_loss_grad(sim, w, target)
-    _pkg().scola_device_status(sim.ctx)
+    rels = []
+    for seed in (21, 23, 24):
+        w = synth_inputs.white_noise(16, seed)
+        val, g = _gpu_loss_grad(sim, w, target)
+        _pkg().scola_device_status(sim.ctx)
+        val_o, g_o = adjoint.loss_and_grad(w.astype(np.float64), cfg, target)
+        assert abs(val / val_o - 1) < 1e-4
+        rels.append(np.linalg.norm(g - g_o) / np.linalg.norm(g_o))
+        print("gradient vs FP64 oracle: ratio=%d %s seed %d rel %.3e" % (ratio, variant, seed, rels[-1]))
     sim.close()
-    val_o, g_o = adjoint.loss_and_grad(w.astype(np.float64), cfg, target)
-    assert abs(val / val_o - 1) < 1e-4
-    rel = np.linalg.norm(g - g_o) / np.linalg.norm(g_o)
-    off = float(np.mean(np.abs(g - g_o) > 1e-3 * np.abs(g_o).max()))
-    print("gradient vs FP64 oracle: ratio=%d %s rel %.3e, entries off by >1e-3 max: %.4f"
-          % (ratio, variant, rel, off))
-    assert rel < 5e-3, rel
-    assert off < 0.01, off
+    assert np.median(rels) < 1e-3, rels
+    assert max(rels) < 5e-3, rels
 
 
 def test_autograd_function_matches_backward():
     sc = _pkg()
     kw = dict(L=48.0, Np=16, Ntiles=2, Nbuf=2, mesh_ratio=1, nsteps=3, a_i=0.05, a_f=1.0)
-    sim = _sim(kw, "tc4")
+    sim = _sim(kw, "tc")
     target = torch.from_numpy(_target(kw, 22).astype(np.float32)).cuda()
     w = torch.from_numpy(synth_inputs.white_noise(16, 21)).cuda().requires_grad_(True)
     loss = ((sc.ScolaDensity.apply(w, sim) - target) ** 2).sum()
@@ -92,7 +92,7 @@ def test_adjoint_workload_central_differences():
     # 128^3 particles, 64 boxes, 48^3 meshes, 10 steps; FP32 central differences of the
     # loss along random directions against <grad, v>.
     kw = workload_cfg("adjoint_128")
-    sim = _sim(kw, "tc4")
+    sim = _sim(kw, "tc")
     w = synth_inputs.white_noise(128, 1).astype(np.float64)
     # target: the final density of a second seed (computed on the GPU, then held fixed)
     wt = torch.from_numpy(synth_inputs.white_noise(128, 2)).cuda()
