@@ -174,8 +174,8 @@ scola_status scola_lpt_fields(scola_ctx *ctx, const float *w_dev, float *delta_d
  * C.1-C.3 for every box from the fields of the last scola_lpt_fields call:
  * gather Psi1, Psi2 of the box particles, set s = -D1(a_i) Psi1 + D2(a_i) Psi2,
  * p_res = 0 (L-, Eq. 55), and precompute the Dirichlet shell (phi1 trilinearly
- * interpolated to the padded PM cells outside the interior, FP64 accumulation;
- * C.3, Eq. 23).  Errors: STATE if scola_lpt_fields has not run.
+ * interpolated to the padded PM cells outside the interior; C.3, Eq. 23).
+ * Errors: STATE if scola_lpt_fields has not run.
  */
 scola_status scola_setup_boxes(scola_ctx *ctx);
 
@@ -189,9 +189,11 @@ scola_status scola_setup_boxes(scola_ctx *ctx);
  *             box-local particle order (bi*Nsc + bj)*Nsc + bk
  *   D1        growth factor scaling the boundary shell
  *   F_dev     device, 3 x P FP32, receives grad Phi at the particles
- *   delta_dev device, sum_b Ng^3 FP32 interior densities (delta, before the
- *             boundary correction), or NULL
- *   phi_dev   device, sum_b (Ng+4)^3 FP32 padded potentials, or NULL
+ *   delta_dev device, scola_mesh_cell_count() FP32: box b's interior densities
+ *             (delta, before the boundary correction) as Ng^3 cells [i][j][k]
+ *             from offset m_off[b] of scola_box_offsets, or NULL
+ *   phi_dev   device, scola_padded_cell_count() FP32: box b's padded potential
+ *             as (Ng+4)^3 cells from offset pp_off[b], or NULL
  * P = scola_box_particle_count().  Errors: STATE before scola_setup_boxes.
  */
 scola_status scola_pm_force(scola_ctx *ctx, const float *s_dev, double D1, float *F_dev,
@@ -200,9 +202,19 @@ scola_status scola_pm_force(scola_ctx *ctx, const float *s_dev, double D1, float
 /* Total number of box particles P (sum over boxes of Np,sCOLA^3). */
 int64_t scola_box_particle_count(const scola_ctx *ctx);
 
-/* Total interior and padded mesh sizes (sum over boxes of Ng^3 and (Ng+4)^3). */
+/* Sizes of the interior and padded mesh arrays: the boxes' Ng^3 and (Ng+4)^3
+ * cells at the offsets of scola_box_offsets, with alignment gaps between boxes. */
 int64_t scola_mesh_cell_count(const scola_ctx *ctx);
 int64_t scola_padded_cell_count(const scola_ctx *ctx);
+
+/*
+ * Where each box of the context sits in the mesh arrays (the layout of
+ * scola_pm_force's delta and phi outputs).
+ *   m_off, pp_off  host, nboxes int64 each: first interior / padded cell of box b
+ *   nboxes         the context's box count (scola_get_stats().nboxes)
+ * Errors: INVALID_ARG (NULL, nboxes different from the context's).
+ */
+scola_status scola_box_offsets(const scola_ctx *ctx, int64_t *m_off, int64_t *pp_off, int32_t nboxes);
 
 /*
  * Tile assignment (Sec. 3.2): global particle id of every box particle, in

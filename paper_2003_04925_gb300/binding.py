@@ -77,6 +77,7 @@ _sig = {
     "scola_set_checkpointing": (c_int32, [c_void_p, c_int32]),
     "scola_backward": (c_int32, [c_void_p, c_void_p, c_void_p]),
     "scola_box_density_noalloc": (c_int32, [c_void_p, c_int32, c_int32, c_double, c_void_p, c_void_p]),
+    "scola_box_offsets": (c_int32, [c_void_p, _P(c_int64), _P(c_int64), c_int32]),
     "scola_selftest_conversions": (c_int32, [c_int64, ctypes.c_uint64, _P(c_int64)]),
     "scola_status_string": (c_char_p, [c_int32]),
     "scola_last_error": (c_char_p, []),
@@ -247,6 +248,14 @@ def scola_box_density_noalloc(s, nsc, ng, dq, delta, stream=0):
     """One box's B^sCOLA density with the library's fixed scratch (no allocation)."""
     _check(_lib.scola_box_density_noalloc(_ptr(s), int(nsc), int(ng), float(dq), _ptr(delta),
                                           c_void_p(stream or None)), "scola_box_density_noalloc")
+
+
+def scola_box_offsets(ctx, nboxes):
+    """(m_off, pp_off): each box's first interior and padded cell in the mesh arrays."""
+    m = (c_int64 * nboxes)()
+    pp = (c_int64 * nboxes)()
+    _check(_lib.scola_box_offsets(ctx, m, pp, int(nboxes)), "scola_box_offsets")
+    return list(m), list(pp)
 
 
 def scola_selftest_conversions(n, seed=1):

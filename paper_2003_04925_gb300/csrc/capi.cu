@@ -236,6 +236,13 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &all_geo) {
         B.tx = gb / (p.Ntiles * p.Ntiles);
         B.ty = (gb / p.Ntiles) % p.Ntiles;
         B.tz = gb % p.Ntiles;
+        // interior meshes start at multiples of lcm(64, Ng): aligned, and a whole number of
+        // Ng-float rows from the buffer start (the tensor-core passes address them as rows)
+        {
+            long long q = 64;
+            while (q % g.ng) q += 64;
+            M = (M + q - 1) / q * q;
+        }
         B.p_off = P;
         B.m_off = M;
         B.pp_off = MP;
@@ -265,7 +272,7 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &all_geo) {
         for (long long t = 0; t < nc; ++t) cit.push_back({b, (int)t});
         auto align64 = [](long long v) { return (v + 63) / 64 * 64; };
         P += n;
-        M = align64(M + ng3);
+        M = align64(M + ng3);   // (the next box rounds up further)
         MP = align64(MP + np3);
         SH = align64(SH + np3 - ng3);
         // boxes sharing an Ng share dg only if their Np,sCOLA also matches; the
@@ -344,7 +351,7 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &all_geo) {
                 if (geo[b].ng != G.Ng) continue;
                 const long long rows = (long long)G.Ng * G.Ng;
                 box_tile_beg[b] = (int)tct.size();
-                for (long long t = 0; t * 128 < rows; ++t) tct.push_back({b, (int)t});
+                for (long long t = 0; t * kTcTileRows < rows; ++t) tct.push_back({b, (int)t});
                 box_tile_end[b] = (int)tct.size();
             }
             G.ntiles = (int)(tct.size() - first);
@@ -686,6 +693,16 @@ void scola_destroy(scola_ctx *c) {
 int64_t scola_box_particle_count(const scola_ctx *c) { return c ? c->P : 0; }
 int64_t scola_mesh_cell_count(const scola_ctx *c) { return c ? c->M : 0; }
 int64_t scola_padded_cell_count(const scola_ctx *c) { return c ? c->MP : 0; }
+
+scola_status scola_box_offsets(const scola_ctx *c, int64_t *m_off, int64_t *pp_off, int32_t nboxes) {
+    if (!c || !m_off || !pp_off) return invalid("NULL argument");
+    if (nboxes != c->nboxes) return invalid("nboxes differs from the context's box count");
+    for (int b = 0; b < nboxes; ++b) {
+        m_off[b] = c->boxes_h[b].m_off;
+        pp_off[b] = c->boxes_h[b].pp_off;
+    }
+    return SCOLA_OK;
+}
 
 scola_status scola_lpt_fields(scola_ctx *c, const float *w, float *delta, float *phi1, float *phi2,
                               float *psi1, float *psi2) {

@@ -26,6 +26,7 @@ namespace scola {
 constexpr int kChunk = 256;       // particles per CTA in particle kernels
 constexpr int kTC = 32;           // transform columns per tile in the DST passes
 constexpr int kXS = kTC + 4;      // shared-memory row stride of a column tile
+constexpr int kTcTileRows = 256;  // data rows per tensor-core DST tile (the MMA N)
 constexpr double kFix = 4294967296.0;  // 2^32: fixed-point scale of CIC weights
 constexpr long long kDepositGroupCells = 6 << 20;   // counts per deposit group (48 MB)
 
@@ -56,7 +57,7 @@ struct DstTable {                 // offsets into the device table arena (floats
 
 struct TcGroup {                  // one tensor-core DST launch group: boxes sharing Ng
     int Ng, Npad, nkc, nstage;
-    Chunk *tiles;                 // device (box, 128-row tile of the box)
+    Chunk *tiles;                 // device (box, kTcTileRows-row tile of the box)
     int ntiles;
     long long s_off;              // FP32 sine matrix Npad x (32 nkc) in table_arena
     long long lam_off;            // eigenvalues in table_arena

@@ -73,16 +73,21 @@ __device__ __forceinline__ void store4(float *p, const float (&v)[4], bool vec, 
         if (e < left) p[e] = v[e];
 }
 
-// Counts -> delta (optional copy) -> delta' for 4 consecutive cells per thread.
-__global__ void __launch_bounds__(64)
-k_density_source(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
+// Counts -> delta (optional copy) -> delta' for 4 consecutive cells per thread; a CTA takes
+// kSourceChunks consecutive 256-cell chunks of the list (64 threads each).
+constexpr int kSourceChunks = 4;
+
+__global__ void __launch_bounds__(64 * kSourceChunks)
+k_density_source(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks, int nchunks,
                  const unsigned long long *__restrict__ acc, long long acc_base, const float *__restrict__ phi_pad,
                  float *__restrict__ out, float *__restrict__ delta_out) {
-    const Chunk ch = chunks[blockIdx.x];
+    const int ci = blockIdx.x * kSourceChunks + (threadIdx.x >> 6);
+    if (ci >= nchunks) return;
+    const Chunk ch = chunks[ci];
     const BoxDesc &B = boxes[ch.box];
     const int Ng = B.Ng;
     const long long ng3 = (long long)Ng * Ng * Ng;
-    const int cell0 = ch.start + 4 * threadIdx.x;
+    const int cell0 = ch.start + 4 * (threadIdx.x & 63);
     if ((long long)cell0 >= ng3) return;
     const int left = (int)min(4LL, ng3 - cell0);
     const float sc = B.nbar_inv * 2.3283064365386963e-10f, c2 = B.inv_dg * B.inv_dg;
@@ -154,7 +159,8 @@ cudaError_t launch_deposit(Ctx &c, const float *s, long long stride, float *delt
             ++c.launches;
         }
         if (nmch > 0) {
-            k_density_source<<<nmch, 64, 0, c.stream>>>(c.boxes, mch, c.dep_acc, base, c.phi, c.work2, delta_out);
+            k_density_source<<<(nmch + kSourceChunks - 1) / kSourceChunks, 64 * kSourceChunks, 0, c.stream>>>(
+                c.boxes, mch, nmch, c.dep_acc, base, c.phi, c.work2, delta_out);
             ++c.launches;
         }
         cudaError_t e = cudaGetLastError();

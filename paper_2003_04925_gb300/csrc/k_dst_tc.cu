@@ -1,8 +1,13 @@
 // Dirichlet Poisson solve on the 5th-generation tensor cores (App. C, Eqs. 62-71).
 //
-// The 3D DST-I is applied as six dense pencil products D = A S^T (S_kn =
-// sin(pi (k+1)(n+1)/(Ng+1)), symmetric), each on rows whose transform axis is
-// contiguous in memory.  Every pass writes its result transposed,
+// The 3D DST-I is applied as six dense pencil products over rows whose transform
+// axis is contiguous in memory.  For a tile of 256 such rows X (256 x Ng) a pass
+// computes D^T = S X^T on the tensor cores (S_kn = sin(pi (k+1)(n+1)/(Ng+1)),
+// symmetric): the sine matrix is the M = 128 operand (rows n < Ng, resident in
+// shared memory for the whole launch) and the data rows are the N = 256 operand, so
+// every MMA instruction runs at the full N width of the tensor pipe.  TMEM lane n of
+// the accumulator holds output column n for all 256 rows, and each epilogue thread
+// writes contiguous runs of out[n][row]: every pass stores its result transposed,
 // out[col][row], so that the next pass again finds its axis contiguous:
 //
 //   pass  input rows (axis)    k    writes              epilogue
@@ -15,28 +20,32 @@
 //
 // Precision: FP32 operands split as a = a_hi + a_lo with a_hi the value with
 // its 13 low mantissa bits cleared (exact in TF32); D accumulates
-// a_hi s_hi + a_hi s_lo + a_lo s_hi in FP32 in tensor memory (3xTF32), and
-// a_lo s_lo as well in the four-product form.  A single TF32 product gives
+// s_hi x_hi + s_hi x_lo + s_lo x_hi in FP32 in tensor memory (3xTF32), and
+// s_lo x_lo as well in the four-product form.  A single TF32 product gives
 // position errors of ~0.1 PM cell over a run, the three-term form stays near
 // the FP32 level.
 //
-// One persistent CTA per SM, 13 warps:
+// One persistent CTA per SM, 18 warps:
 //   warps 0-7  epilogue: tcgen05.ld of the accumulator (warp w reads TMEM lanes
-//              32(w%4)..+31 = tile rows, half of the columns), scaling, transposed
-//              global stores
-//   warps 8-11 producer: cp.async copies of 128-row x 32-column chunks into a
-//              ring of raw staging buffers, DEPTH chunks ahead; each thread then
-//              splits the bytes it copied into hi/lo and stores them in the
-//              128-byte-swizzled K-major layout of the MMA stage
-//   warp 12    TMEM allocation; lane 0 issues tcgen05.mma and tcgen05.commit
-// Stages of A chunks form a ring guarded by full/empty mbarriers; the
-// accumulator is double buffered in TMEM (tmem_full / tmem_empty).  Every
-// wait is bounded (about 2 s of %globaltimer); on expiry the CTA raises an
-// error flag in global memory, stops issuing work, waits for its issued
-// tensor-core work to drain, frees its tensor memory and returns.
+//              32(w%4)..+31 = output columns, half of the 256 rows), a 32 x 32
+//              transpose through shared memory, scaling, coalesced global stores
+//   warps 8-15 converters: the lo parts of each landed stage (the raw FP32 values
+//              serve as the hi operand)
+//   warp 16    TMEM allocation; lane 0 issues tcgen05.mma and tcgen05.commit
+//   warp 17    lane 0 issues the tensor copies (TMA) of 256-row x 16-column chunks of
+//              the data into a ring of MMA stages (64-byte-swizzled K-major)
+// Stages form a ring guarded by full/empty mbarriers; the accumulator is double
+// buffered in TMEM (tmem_full / tmem_empty, 2 x 256 columns).  Every wait is
+// bounded (about 2 s of %globaltimer); on expiry the CTA raises an error flag in
+// global memory, stops issuing work, waits for its issued tensor-core work to
+// drain, frees its tensor memory and returns.
+#include <cuda.h>
 #include <stdint.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "device_util.cuh"
 
@@ -44,12 +53,20 @@ namespace scola {
 
 namespace {
 
-constexpr int kTM = 128;             // rows per tile (MMA M)
-constexpr int kKC = 32;              // K per chunk (one 128-byte swizzle atom of FP32)
-constexpr int kChunkBytes = kTM * 128;
-constexpr int kThreads = 416;          // 8 epilogue, 4 producer, 1 MMA warps
-constexpr int kMaxGroups = 4;          // 16-column TMEM groups per epilogue warp (Npad <= 128)
+constexpr int kTM = 128;             // MMA M: rows of the sine matrix (output index n < Ng <= 128)
+constexpr int kTN = kTcTileRows;     // MMA N: data rows per tile (256)
+constexpr int kKA = 32;              // K per sine-matrix chunk (one 128-byte swizzle row of FP32)
+constexpr int kKB = 16;              // K per data chunk (one 64-byte swizzle row of FP32)
+constexpr int kHalfBytes = kTN * 64; // one data chunk, hi or lo (16 KB)
+constexpr int kStageBytes = 2 * kHalfBytes;
+constexpr int kThreads = 576;        // 8 epilogue, 8 converter, 1 MMA, 1 TMA warps
+constexpr int kProducers = 256;      // converter threads; each splits kHalfBytes / 16 / kProducers units per chunk
+constexpr int kUnits = kHalfBytes / 16 / kProducers;
+constexpr int kTmemCols = 2 * kTN;   // double-buffered accumulator
 constexpr unsigned long long kWaitNs = 2000000000ull;
+
+// Per epilogue warp: a 32 x 33 float block for transposing 32 columns x 32 rows.
+constexpr int kXposeBytes = 32 * 33 * 4;
 
 enum TcPass { P_F = 1, P_XF = 2, P_ZI = 3, P_YI = 4, P_XI = 5 };   // P_F: z+ and y+
 
@@ -60,13 +77,14 @@ struct TileInfo {
     long long m_off, pp_off;
     int row0, pad;
 };
-constexpr int kTileCache = 192;
+constexpr int kTileCache = 96;
 
 struct TcArgs {
+    CUtensorMap in_map;          // the input as rows of Ng floats (64-byte swizzle boxes 16 x 256)
     const BoxDesc *boxes;
     const Chunk *tiles;          // (box, tile-in-box)
     int ntiles;
-    int Ng, Npad, nkc, nstage;   // uniform Ng for the launch; nstage = hi/lo MMA stages
+    int Ng, Npad, nkc, nstage;   // uniform Ng for the launch; nkc sine chunks; nstage data stages
     const float *S;              // FP32 sine matrix, Npad x (nkc*32), zero padded
     const float *lam;            // Dirichlet eigenvalues, Ng
     const float *in;
@@ -97,7 +115,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, 1000;\n\t"
         "selp.b32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
         : "r"(smem_u32(bar)), "r"(parity)
@@ -117,16 +135,18 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volati
     }
 }
 
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t src_bytes) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes)
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
 }
 
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+// 2D tensor copy global -> shared: box (x .. x + 15, y .. y + 255) of the map, completing on bar.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
 }
 
 __device__ __forceinline__ void fence_proxy_async() {
@@ -148,6 +168,16 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
     d |= (uint64_t)(1024u >> 4) << 32;    // stride byte offset
     d |= (uint64_t)1u << 46;              // descriptor version
     d |= (uint64_t)2u << 61;              // 128-byte swizzle
+    return d;
+}
+
+// The same for the 64-byte swizzle: 64-byte rows, 8-row groups 512 B apart.
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1u << 16;              // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(512u >> 4) << 32;     // stride byte offset
+    d |= (uint64_t)1u << 46;              // descriptor version
+    d |= (uint64_t)4u << 61;              // 64-byte swizzle
     return d;
 }
 
@@ -197,30 +227,37 @@ __device__ __forceinline__ uint32_t sw128_offset(int r, int k) {
     return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((((k >> 2) ^ (r & 7)) & 7) << 4) + (k & 3) * 4);
 }
 
+// Byte offset of element (r, k) (k within the 16-wide chunk) in a 64B-swizzled K-major tile.
+__device__ __forceinline__ uint32_t sw64_offset(int r, int k) {
+    return (uint32_t)(r * 64 + ((((k >> 2) ^ (r >> 1)) & 3) << 4) + (k & 3) * 4);
+}
+
 __device__ __forceinline__ float tf32_hi(float x) {
     return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
 }
 
-template <int PASS, int DEPTH>
-__global__ void __launch_bounds__(kThreads, 1) k_dst_tc(TcArgs A) {
-    constexpr int RS = DEPTH + 1;                   // raw staging ring
-    constexpr int RAWB = kChunkBytes;
+template <int PASS>
+__global__ void __launch_bounds__(kThreads, 1) k_dst_tc(const __grid_constant__ TcArgs A) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-aligned (in the shared window) base for the swizzled operand tiles
     unsigned char *base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-    const int Ng = A.Ng, Npad = A.Npad, nkc = A.nkc, NST = A.nstage;
-    const int sbytes = nkc * Npad * 128;            // one of S_hi / S_lo
+    const int Ng = A.Ng, nka = A.nkc, NST = A.nstage;
+    const int nkb = (Ng + kKB - 1) / kKB;                 // data chunks per tile
+    const uint32_t sch = (uint32_t)((Ng + 7) / 8) * 1024; // one sine chunk (hi or lo), Ng rows
+    // The M = 128 operand reads 128 rows from each sine chunk; rows >= Ng come from what
+    // follows (the next chunk, or the stages) and only feed TMEM lanes that are never read.
     unsigned char *S_hi = base;
-    unsigned char *S_lo = base + sbytes;
-    unsigned char *stages = base + 2 * sbytes;      // NST x (A_hi chunk, A_lo chunk)
-    unsigned char *raw = stages + (size_t)NST * 2 * kChunkBytes;   // RS raw chunks
-    uint64_t *bars = (uint64_t *)(raw + (size_t)RS * RAWB);
-    uint64_t *full = bars;
-    uint64_t *empty = bars + NST;
-    uint64_t *tfull = bars + 2 * NST;
-    uint64_t *tempty = bars + 2 * NST + 2;
-    uint64_t *drain = bars + 2 * NST + 4;
-    uint32_t *tmem_slot = (uint32_t *)(bars + 2 * NST + 5);
+    unsigned char *S_lo = base + nka * sch;
+    unsigned char *stages = base + 2 * nka * sch;
+    float *xpose = (float *)(stages + (size_t)NST * kStageBytes);     // 8 x kXposeBytes
+    uint64_t *bars = (uint64_t *)((unsigned char *)xpose + 8 * kXposeBytes);
+    uint64_t *full = bars;                 // converted (MMA may read the stage)
+    uint64_t *empty = bars + NST;          // consumed (the stage may be reloaded)
+    uint64_t *loaded = bars + 2 * NST;     // the tensor copy into the stage has landed
+    uint64_t *tfull = bars + 3 * NST;
+    uint64_t *tempty = bars + 3 * NST + 2;
+    uint64_t *drain = bars + 3 * NST + 4;
+    uint32_t *tmem_slot = (uint32_t *)(bars + 3 * NST + 5);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
     float *lam = (float *)(tmem_slot + 4);
     TileInfo *tinfo = (TileInfo *)(base + ((((unsigned char *)(lam + Ng) - base) + 15) & ~15));
@@ -228,15 +265,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(TcArgs A) {
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
 
-    // ---- set-up: S (hi/lo split, swizzled), lambda, barriers, tensor memory
-    const int Kp = nkc * kKC;
-    for (int q = tid; q < Npad * Kp; q += kThreads) {
+    // ---- set-up: S (hi/lo split, swizzled), lambda, tile table, barriers, tensor memory
+    const int Kp = nka * kKA;
+    for (int q = tid; q < Ng * Kp; q += kThreads) {
         const int n = q / Kp, k = q % Kp;
-        const float s = A.S[q];
-        const float hi = tf32_hi(s);
-        const uint32_t off = (uint32_t)(k / kKC) * (Npad * 128) + sw128_offset(n, k % kKC);
+        const float sv = A.S[q];
+        const float hi = tf32_hi(sv);
+        const uint32_t off = (uint32_t)(k / kKA) * sch + sw128_offset(n, k % kKA);
         *(float *)(S_hi + off) = hi;
-        *(float *)(S_lo + off) = s - hi;
+        *(float *)(S_lo + off) = sv - hi;
     }
     for (int q = tid; q < Ng; q += kThreads) lam[q] = A.lam[q];
     const long long my_tiles = A.ntiles > (int)blockIdx.x ? (A.ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
@@ -245,7 +282,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(TcArgs A) {
         TileInfo ti;
         ti.m_off = A.boxes[tl.box].m_off;
         ti.pp_off = A.boxes[tl.box].pp_off;
-        ti.row0 = tl.start * kTM;
+        ti.row0 = tl.start * kTN;
         ti.pad = 0;
         return ti;
     };
@@ -253,8 +290,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(TcArgs A) {
     auto tile_at = [&](long long k) { return k < kTileCache ? tinfo[k] : load_tile(k); };
     if (tid == 0) {
         for (int s = 0; s < NST; ++s) {
-            mbar_init(&full[s], 128);
+            mbar_init(&full[s], kProducers);
             mbar_init(&empty[s], 1);
+            mbar_init(&loaded[s], 1);
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(&tfull[a], 1);
@@ -264,10 +302,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(TcArgs A) {
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 12) {
+    if (warp == 16) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(tmem_slot)),
-                     "r"(256));
+                     "r"(kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     fence_proxy_async();
@@ -277,93 +315,96 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(TcArgs A) {
     const uint32_t tmem = *tmem_slot;
     const long long Ng2 = (long long)Ng * Ng;
 
-    if (warp >= 8 && warp < 12) {
-        // ---------------------------------------------------------------- producer
-        // chunk g of this CTA = tile (blockIdx.x + (g / nkc) gridDim.x), K-chunk g % nkc.
-        // Thread pt copies and later converts items q = pt + 128 e (e < 8): row q >> 3,
-        // float4 group q & 7 of the chunk.
+    const long long nchunks = my_tiles * nkb;
+    if (warp >= 8 && warp < 16) {
+        // ---------------------------------------------------------------- converters
+        // chunk h of this CTA = tile h / nkb, columns 16 (h % nkb) .. + 15, in stage h % NST.
+        // The tensor core reads the raw FP32 values as the hi operand (it ignores the 13 low
+        // mantissa bits, which is the truncation tf32_hi computes); thread pt writes the lo
+        // parts of the 16-byte units q = pt + kProducers e (row q >> 2, unit q & 3).
         const int pt = tid - 256;
-        const uint32_t raw_s = smem_u32(raw);
-        const long long nchunks = my_tiles * nkc;
-        auto issue = [&](long long g) {
-            if (g < nchunks) {
-                const int c = (int)(g % nkc);
-                const TileInfo ti = tile_at(g / nkc);
-                const long long m_off = ti.m_off;
-                const int row0 = ti.row0;
-                const uint32_t dst0 = raw_s + (uint32_t)((g % RS) * RAWB);
+        uint32_t soff[kUnits];
 #pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const int q = pt + 128 * e;
-                    const int r = q >> 3, kq = q & 7;
-                    const int k = c * kKC + kq * 4;
-                    const int R = row0 + r;
-                    const bool ok = (long long)R < Ng2 && k < Ng;
-                    const float *src = A.in + m_off + (ok ? (long long)R * Ng + k : 0);
-                    cp_async16(dst0 + sw128_offset(r, kq * 4), src, ok ? 16u : 0u);
-                }
-            }
-            cp_async_commit();
-        };
-        for (int d = 0; d < DEPTH; ++d) issue(d);
-        for (long long g = 0; g < nchunks && !*abort_flag; ++g) {
-            issue(g + DEPTH);
-            cp_async_wait<DEPTH>();
-            const int s = (int)(g % NST);
-            if (!mbar_wait(&empty[s], (uint32_t)(((g / NST) & 1) ^ 1), abort_flag)) {
+        for (int e = 0; e < kUnits; ++e) {
+            const int q = pt + kProducers * e;
+            soff[e] = sw64_offset(q >> 2, 4 * (q & 3));
+        }
+        for (long long h = 0; h < nchunks && !*abort_flag; ++h) {
+            const int s = (int)(h % NST);
+            if (!mbar_wait(&loaded[s], (uint32_t)((h / NST) & 1), abort_flag)) {
                 *abort_flag = 1;
                 break;
             }
-            unsigned char *ah = stages + (size_t)s * 2 * kChunkBytes;
-            unsigned char *al = ah + kChunkBytes;
-            const unsigned char *rw = raw + (size_t)(g % RS) * RAWB;
+            const unsigned char *xh = stages + (size_t)s * kStageBytes;
+            unsigned char *xl = stages + (size_t)s * kStageBytes + kHalfBytes;
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const int q = pt + 128 * e;
-                const int r = q >> 3, kq = q & 7;
-                const uint32_t off = sw128_offset(r, kq * 4);
-                const float4 v = *reinterpret_cast<const float4 *>(rw + off);
-                const float4 h = make_float4(tf32_hi(v.x), tf32_hi(v.y), tf32_hi(v.z), tf32_hi(v.w));
-                const float4 l = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
-                *reinterpret_cast<float4 *>(ah + off) = h;
-                *reinterpret_cast<float4 *>(al + off) = l;
+            for (int e = 0; e < kUnits; ++e) {
+                const float4 v = *reinterpret_cast<const float4 *>(xh + soff[e]);
+                *reinterpret_cast<float4 *>(xl + soff[e]) = make_float4(
+                    v.x - tf32_hi(v.x), v.y - tf32_hi(v.y), v.z - tf32_hi(v.z), v.w - tf32_hi(v.w));
             }
             fence_proxy_async();
             mbar_arrive(&full[s]);
         }
-        cp_async_wait<0>();
-    } else if (warp == 12) {
+    } else if (warp == 17) {
+        // ---------------------------------------------------------------- tensor copies
+        // lane 0 loads chunk g into stage g % NST as soon as the MMA has released it; on an
+        // abort it waits (bounded) for the copies it issued before the CTA may exit
+        if (lane == 0) {
+            long long g = 0;
+            for (; g < nchunks && !*abort_flag; ++g) {
+                const int s = (int)(g % NST);
+                if (!mbar_wait(&empty[s], (uint32_t)(((g / NST) & 1) ^ 1), abort_flag)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                const TileInfo ti = tile_at(g / nkb);
+                mbar_arrive_expect_tx(&loaded[s], kHalfBytes);
+                tma_load_2d(smem_u32(stages + (size_t)s * kStageBytes), &A.in_map, (int)(g % nkb) * kKB,
+                            (int)(ti.m_off / Ng + ti.row0), &loaded[s]);
+            }
+            if (*abort_flag) {
+                const unsigned long long t0 = now_ns();
+                for (long long h = g - NST > 0 ? g - NST : 0; h < g; ++h)
+                    while (!mbar_try_wait(&loaded[h % NST], (uint32_t)((h / NST) & 1)) && now_ns() - t0 < kWaitNs) {
+                    }
+            }
+        }
+    } else if (warp == 16) {
         // ---------------------------------------------------------------- MMA issuer
         if (lane == 0) {
-            const uint32_t idesc = idesc_tf32(kTM, Npad);
-            uint32_t g = 0, t = 0;
-            for (int it = blockIdx.x; it < A.ntiles && !*abort_flag; it += gridDim.x, ++t) {
+            const uint32_t idesc = idesc_tf32(kTM, kTN);
+            const uint32_t shi = smem_u32(S_hi), slo = smem_u32(S_lo), st0 = smem_u32(stages);
+            long long g = 0;
+            uint32_t t = 0;
+            for (long long it = 0; it < my_tiles && !*abort_flag; ++it, ++t) {
                 const int a = t & 1;
                 if (!mbar_wait(&tempty[a], ((t >> 1) & 1) ^ 1, abort_flag)) {
                     *abort_flag = 1;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t d = tmem + (uint32_t)(a * 128);
+                const uint32_t d = tmem + (uint32_t)(a * kTN);
                 bool ok = true;
-                for (int c = 0; c < nkc; ++c, ++g) {
-                    const int s = g % NST;
-                    if (!mbar_wait(&full[s], (g / NST) & 1, abort_flag)) {
+                for (int c = 0; c < nkb; ++c, ++g) {
+                    const int s = (int)(g % NST);
+                    if (!mbar_wait(&full[s], (uint32_t)((g / NST) & 1), abort_flag)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t ah = smem_u32(stages + (size_t)s * 2 * kChunkBytes);
-                    const uint32_t al = ah + kChunkBytes;
-                    const uint32_t bh = smem_u32(S_hi) + (uint32_t)(c * Npad * 128);
-                    const uint32_t bl = smem_u32(S_lo) + (uint32_t)(c * Npad * 128);
-                    const int ksteps = min(kKC, Ng - c * kKC + 7) / 8;   // skip all-zero K steps
-                    for (int kk = 0; kk < ksteps; ++kk) {
-                        const uint32_t o = (uint32_t)kk * 32;
-                        mma_tf32(d, sw128_desc(ah + o), sw128_desc(bh + o), idesc, (c | kk) != 0);
-                        mma_tf32(d, sw128_desc(ah + o), sw128_desc(bl + o), idesc, 1);
-                        mma_tf32(d, sw128_desc(al + o), sw128_desc(bh + o), idesc, 1);
-                        if (A.lo_lo) mma_tf32(d, sw128_desc(al + o), sw128_desc(bl + o), idesc, 1);
+                    const uint32_t xh = st0 + (uint32_t)s * kStageBytes, xl = xh + kHalfBytes;
+#pragma unroll
+                    for (int kk = 0; kk < kKB / 8; ++kk) {
+                        const int kg = c * kKB + kk * 8;
+                        if (kg >= Ng) break;                      // all-zero K step
+                        const uint32_t ao = (uint32_t)(kg / kKA) * sch + (uint32_t)((kg % kKA) / 8) * 32;
+                        const uint64_t ahi = sw128_desc(shi + ao), alo = sw128_desc(slo + ao);
+                        const uint64_t bhi = sw64_desc(xh + kk * 32), blo = sw64_desc(xl + kk * 32);
+                        mma_tf32(d, ahi, bhi, idesc, (c | kk) != 0);
+                        mma_tf32(d, ahi, blo, idesc, 1);
+                        mma_tf32(d, alo, bhi, idesc, 1);
+                        if (A.lo_lo) mma_tf32(d, alo, blo, idesc, 1);
                     }
                     mma_commit(&empty[s]);
                 }
@@ -376,69 +417,72 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(TcArgs A) {
         }
     } else {
         // ---------------------------------------------------------------- epilogue (warps 0-7)
-        // warp w reads TMEM lanes 32 (w & 3) .. + 31 (its tile rows) and the 16-column groups
-        // g = (w >> 2) + 2 i: all its groups are loaded before one wait, then the accumulator
-        // is released and the stores follow.
+        // warp w reads TMEM lanes 32 (w & 3) + lane (output columns n) and rows
+        // 128 (w >> 2) .. + 127 of the tile, 32 at a time, and transposes each 32 x 32 block
+        // through shared memory, so that a store instruction writes 32 consecutive rows of
+        // one column (128 bytes).  All epilogue warps follow every tile's barriers, also
+        // those whose lanes are all >= Ng.
         const int quarter = warp & 3, half = warp >> 2;
-        const int row_in_tile = quarter * 32 + lane;
-        const int ngroups = Npad / 16;
+        const int n0 = quarter * 32;
+        const int ncol = Ng - n0 < 32 ? Ng - n0 : 32;        // valid columns of this warp (may be <= 0)
         const float scale = (PASS == P_XI) ? 8.0f / ((float)(Ng + 1) * (Ng + 1) * (Ng + 1)) : 1.0f;
+        const long long S = Ng + 4;
+        float *buf = xpose + warp * (kXposeBytes / 4);
         uint32_t t = 0;
-        for (int it = blockIdx.x; it < A.ntiles && !*abort_flag; it += gridDim.x, ++t) {
+        for (long long it = 0; it < my_tiles && !*abort_flag; ++it, ++t) {
             const int a = t & 1;
             if (!mbar_wait(&tfull[a], (t >> 1) & 1, abort_flag)) {
                 *abort_flag = 1;
                 break;
             }
             tc_fence_after();
-            const uint32_t tbase = tmem + (uint32_t)(a * 128) + ((uint32_t)(quarter * 32) << 16);
-            float v[kMaxGroups][16];
-#pragma unroll
-            for (int i = 0; i < kMaxGroups; ++i)
-                if (half + 2 * i < ngroups) tmem_ld16_issue(tbase + (uint32_t)(16 * (half + 2 * i)), v[i]);
-            tmem_ld_wait();
-#pragma unroll
-            for (int i = 0; i < kMaxGroups; ++i) tmem_regs_ready(v[i]);
-            tc_fence_before();
-            mbar_arrive(&tempty[a]);
-            const TileInfo ti = tile_at(t);
-            const int Ri = ti.row0 + row_in_tile;
-            if ((long long)Ri >= Ng2) continue;
-            const int rhi = Ri / Ng, rlo = Ri - rhi * Ng;
-            float lsum = 0.0f;
-            if (PASS == P_XF) lsum = lam[rhi] + lam[rlo];
-            // element (row Ri, column col) goes to base + col * cstride
-            float *base;
-            long long cstride;
-            if (PASS == P_XI) {
-                const long long S = Ng + 4;
-                base = A.out + ti.pp_off + (2 * S + (rhi + 2)) * S + (rlo + 2);
-                cstride = S * S;
-            } else {
-                base = A.out + ti.m_off + Ri;
-                cstride = Ng2;
-            }
-#pragma unroll
-            for (int i = 0; i < kMaxGroups; ++i) {
-                const int c0 = 16 * (half + 2 * i);
-                if (c0 >= Ng) break;
-                float *p = base + (long long)c0 * cstride;
+            const TileInfo ti = tile_at(it);
+            const uint32_t tbase = tmem + (uint32_t)(a * kTN + half * 128) + ((uint32_t)n0 << 16);
+#pragma unroll 1
+            for (int rnd = 0; rnd < 4; ++rnd) {
+                float v0[16], v1[16];
+                if (ncol > 0) {
+                    tmem_ld16_issue(tbase + (uint32_t)(rnd * 32), v0);
+                    tmem_ld16_issue(tbase + (uint32_t)(rnd * 32 + 16), v1);
+                    tmem_ld_wait();
+                    tmem_regs_ready(v0);
+                    tmem_regs_ready(v1);
+                }
+                if (rnd == 3) {
+                    // every column of this accumulator is in registers: release it
+                    tc_fence_before();
+                    mbar_arrive(&tempty[a]);
+                }
+                if (ncol <= 0) continue;
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    const int col = c0 + j;
-                    if (col >= Ng) break;
-                    float x = v[i][j];
-                    if (PASS == P_XI) x *= scale;
-                    if (PASS == P_XF) x = __fdividef(x, lam[col] + lsum);
-                    *p = x;
-                    p += cstride;
+                    buf[lane * 33 + j] = v0[j];
+                    buf[lane * 33 + 16 + j] = v1[j];
                 }
+                __syncwarp();
+                // this lane now stores row R of the warp's columns
+                const long long R = (long long)ti.row0 + half * 128 + rnd * 32 + lane;
+                if (R < Ng2) {
+                    const int rhi = (int)(R / Ng), rlo = (int)(R - (long long)(R / Ng) * Ng);
+                    if (PASS == P_XI) {
+                        float *p = A.out + ti.pp_off + ((long long)(n0 + 2) * S + (rhi + 2)) * S + (rlo + 2);
+                        for (int c = 0; c < ncol; ++c, p += S * S) *p = buf[c * 33 + lane] * scale;
+                    } else if (PASS == P_XF) {
+                        const float lr = lam[rhi] + lam[rlo];
+                        float *p = A.out + ti.m_off + (long long)n0 * Ng2 + R;
+                        for (int c = 0; c < ncol; ++c, p += Ng2) *p = __fdividef(buf[c * 33 + lane], lam[n0 + c] + lr);
+                    } else {
+                        float *p = A.out + ti.m_off + (long long)n0 * Ng2 + R;
+                        for (int c = 0; c < ncol; ++c, p += Ng2) *p = buf[c * 33 + lane];
+                    }
+                }
+                __syncwarp();
             }
         }
     }
 
     // ---- tear-down: every role has left its loop; drain, then free tensor memory
-    if (warp == 12 && lane == 0 && *abort_flag) {
+    if (warp == 16 && lane == 0 && *abort_flag) {
         // wait (bounded) until every MMA this thread issued has finished writing TMEM
         mma_commit(drain);
         const unsigned long long t0 = now_ns();
@@ -449,28 +493,61 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(TcArgs A) {
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 12) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
+    if (warp == 16) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 
-size_t tc_smem_bytes(int Npad, int nkc, int nstage, int Ng, int raw_bytes) {
-    return 1024 + 2 * (size_t)nkc * Npad * 128 + (size_t)nstage * 2 * kChunkBytes + (size_t)raw_bytes +
-           (2 * nstage + 5) * 8 + 16 + (size_t)Ng * 4 + 16 + kTileCache * sizeof(TileInfo) + 64;
+size_t tc_smem_bytes(int Ng, int nkc, int nstage) {
+    const size_t sch = (size_t)((Ng + 7) / 8) * 1024;
+    return 1024 + 2 * (size_t)nkc * sch + (size_t)nstage * kStageBytes + 8 * kXposeBytes + (3 * nstage + 5) * 8 + 16 +
+           (size_t)Ng * 4 + 16 + kTileCache * sizeof(TileInfo) + 64;
 }
 
 constexpr size_t kSmemBudget = 227 * 1024;
-constexpr int kDeep = 4, kShallow = 1;
 
-// Deepest raw ring (DEPTH chunks ahead) that fits next to S and the MMA stages.
-int pick_depth(const TcGroup &G) {
-    if (tc_smem_bytes(G.Npad, G.nkc, G.nstage, G.Ng, (kDeep + 1) * kChunkBytes) <= kSmemBudget)
-        return kDeep;
-    return kShallow;
+// The input buffer as a 2D tensor of rows of Ng floats (box m_off are multiples of Ng), for
+// 16 x 256 tensor copies with the 64-byte swizzle of the MMA stages; encoded once per
+// (buffer, Ng) through the driver entry point.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+cudaError_t input_map(Ctx &c, const float *buf, int Ng, CUtensorMap *out) {
+    static std::mutex mu;
+    static std::map<std::pair<std::pair<const void *, long long>, int>, CUtensorMap> cache;
+    static EncodeTiledFn encode = nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    const auto key = std::make_pair(std::make_pair((const void *)buf, c.M), Ng);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+        *out = it->second;
+        return cudaSuccess;
+    }
+    if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return e != cudaSuccess ? e : cudaErrorNotSupported;
+        encode = (EncodeTiledFn)fn;
+    }
+    CUtensorMap m;
+    const cuuint64_t dims[2] = {(cuuint64_t)Ng, (cuuint64_t)(c.M / Ng)};
+    const cuuint64_t strides[1] = {(cuuint64_t)Ng * sizeof(float)};
+    const cuuint32_t box[2] = {(cuuint32_t)kKB, (cuuint32_t)kTN};
+    const cuuint32_t estr[2] = {1, 1};
+    if (encode(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(buf), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    cache[key] = m;
+    *out = m;
+    return cudaSuccess;
 }
 
 template <int PASS>
 cudaError_t run_tc_pass(Ctx &c, const TcGroup &G, const float *in, float *out) {
-    const int depth = pick_depth(G);
     TcArgs a;
+    cudaError_t me = input_map(c, in, G.Ng, &a.in_map);
+    if (me != cudaSuccess) return me;
     a.boxes = c.boxes;
     a.tiles = G.tiles;
     a.ntiles = G.ntiles;
@@ -484,12 +561,9 @@ cudaError_t run_tc_pass(Ctx &c, const TcGroup &G, const float *in, float *out) {
     a.out = out;
     a.err = c.dev_err;
     a.lo_lo = c.tc_lo_lo ? 1 : 0;
-    const size_t smem = tc_smem_bytes(G.Npad, G.nkc, G.nstage, G.Ng, (depth + 1) * kChunkBytes);
+    const size_t smem = tc_smem_bytes(G.Ng, G.nkc, G.nstage);
     const int grid = std::max(1, std::min(G.ntiles, c.num_sms));
-    if (depth == kDeep)
-        k_dst_tc<PASS, kDeep><<<grid, kThreads, smem, c.stream>>>(a);
-    else
-        k_dst_tc<PASS, kShallow><<<grid, kThreads, smem, c.stream>>>(a);
+    k_dst_tc<PASS><<<grid, kThreads, smem, c.stream>>>(a);
     ++c.launches;
     return cudaGetLastError();
 }
@@ -497,12 +571,12 @@ cudaError_t run_tc_pass(Ctx &c, const TcGroup &G, const float *in, float *out) {
 }  // namespace
 
 int tc_plan_stages(int Ng, int &Npad, int &nkc) {
-    // two hi/lo MMA stages; the raw ring takes what is left (at least 2 chunks)
+    // as many data stages (up to 4) as fit next to the resident sine matrix, at least 2
     Npad = ((Ng + 15) / 16) * 16;
-    nkc = (Ng + kKC - 1) / kKC;
-    const int nst = 2;
-    if (tc_smem_bytes(Npad, nkc, nst, Ng, (kShallow + 1) * kChunkBytes) > kSmemBudget) return 0;
-    return nst;
+    nkc = (Ng + kKA - 1) / kKA;
+    for (int nst = 4; nst >= 2; --nst)
+        if (tc_smem_bytes(Ng, nkc, nst) <= kSmemBudget) return nst;
+    return 0;
 }
 
 bool tc_supported(int Ng) {
@@ -513,9 +587,7 @@ bool tc_supported(int Ng) {
 template <int PASS>
 cudaError_t set_tc_attr() {
     const int lim = (int)kSmemBudget;
-    cudaError_t e = cudaFuncSetAttribute(k_dst_tc<PASS, kDeep>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_dst_tc<PASS, kShallow>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    return cudaFuncSetAttribute(k_dst_tc<PASS>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
 }
 
 cudaError_t init_tc_kernels() {

@@ -67,6 +67,10 @@ class Scola:
         B.scola_pm_force(self.ctx, s.contiguous(), D1, F, delta, phi)
         return F, delta, phi
 
+    def box_offsets(self):
+        """(m_off, pp_off) of every box in the mesh arrays of pm_force."""
+        return B.scola_box_offsets(self.ctx, self.stats()["nboxes"])
+
     def box_particle_ids(self):
         gid = self._empty(self.P, dtype=torch.int64)
         B.scola_box_particle_ids(self.ctx, gid)
