@@ -317,6 +317,30 @@ def kernel_roofline(kt, kw, clocks, peaks, tc):
     return dom, rows
 
 
+def measured_traffic(workload, dst):
+    """DRAM bytes per force evaluation of each kernel class from the committed ncu capture
+    (profiles/traffic_<workload>.json), or None for a class whose source files changed since
+    the capture (their hash no longer matches)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic_%s.json" % workload)
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return {}
+    if rec.get("dst") != dst:
+        return {}
+    out = {}
+    for name, c in rec["classes"].items():
+        m = hashlib.sha256()
+        try:
+            for f in c["files"]:
+                m.update(open(os.path.join(ROOT, f), "rb").read())
+        except OSError:
+            continue
+        out[name] = c["bytes"] if m.hexdigest()[:16] == c["sha256_16"] else None
+    return out
+
+
 def run_gpu(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -431,12 +455,18 @@ def run_gpu(args, rank, world, local_rank):
     dom, rows = kernel_roofline(kt, kw, clk, peaks, args.dst != "simt")
     sc.scola_device_status(sim.ctx)
     d = rows[dom]
+    # ncu DRAM bytes per evaluation, keyed by class (dst_i: the i-th pass)
+    traffic = measured_traffic(args.workload, args.dst)
+    cls = {k: ("dst_%s" % k.split("_")[1] if k.startswith("dst_") else k) for k in rows}
     roofline = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"],
-                "unit": d["unit"], "frac": d["frac"], "traffic": None,
+                "unit": d["unit"], "frac": d["frac"], "traffic": traffic.get(cls[dom]),
+                "traffic_source": "profiles/traffic_%s.json (ncu, DRAM read + write per force evaluation; "
+                                  "null where the kernel changed since the capture)" % args.workload,
                 "peak_source": peak_src if d["bound"] == "hbm" else
                 "FP32 FMA: 152 SMs x 128 lanes x 2 flop x median SM clock under load",
                 "kernels": {k: {"ms_per_launch": round(v["ms"], 5), "share": round(v["share"], 4),
-                                "frac": round(v["frac"], 4), "bound": v["bound"]}
+                                "frac": round(v["frac"], 4), "bound": v["bound"],
+                                "traffic": traffic.get(cls[k])}
                             for k, v in rows.items()}}
 
     adj = adjoint_cost(sc, torch, args.dst, max(2, min(args.steps, 5)))
