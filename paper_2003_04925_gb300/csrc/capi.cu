@@ -245,6 +245,9 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &all_geo) {
         }
         B.p_off = P;
         B.m_off = M;
+        // padded boxes start 2 floats past a 64-float boundary: with Ng % 4 == 0 the interior
+        // cells of every padded row (index 2 .. Ng+1) then start 16-byte aligned
+        MP += 2;
         B.pp_off = MP;
         B.sh_off = SH;
         const double Lsc = g.nsc * c->dq;

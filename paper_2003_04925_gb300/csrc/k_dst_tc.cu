@@ -135,6 +135,11 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volati
     }
 }
 
+// Prefetch `bytes` (a multiple of 16, 16-byte aligned) of global memory into L2.
+__device__ __forceinline__ void prefetch_l2(const void *src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
@@ -359,6 +364,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(const __grid_constant__ 
                     break;
                 }
                 const TileInfo ti = tile_at(g / nkb);
+                if (g % nkb == 0 && g / nkb + 1 < my_tiles) {
+                    // the next tile's rows are one contiguous block: start bringing it into L2
+                    const TileInfo tn = tile_at(g / nkb + 1);
+                    const long long rows = min((long long)kTN, Ng2 - tn.row0);
+                    prefetch_l2(A.in + tn.m_off + (long long)tn.row0 * Ng, (uint32_t)(rows * Ng * sizeof(float)));
+                }
                 mbar_arrive_expect_tx(&loaded[s], kHalfBytes);
                 tma_load_2d(smem_u32(stages + (size_t)s * kStageBytes), &A.in_map, (int)(g % nkb) * kKB,
                             (int)(ti.m_off / Ng + ti.row0), &loaded[s]);
@@ -419,9 +430,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(const __grid_constant__ 
         // ---------------------------------------------------------------- epilogue (warps 0-7)
         // warp w reads TMEM lanes 32 (w & 3) + lane (output columns n) and rows
         // 128 (w >> 2) .. + 127 of the tile, 32 at a time, and transposes each 32 x 32 block
-        // through shared memory, so that a store instruction writes 32 consecutive rows of
-        // one column (128 bytes).  All epilogue warps follow every tile's barriers, also
-        // those whose lanes are all >= Ng.
+        // through shared memory in 16-byte units, so that a 16-byte store instruction writes
+        // 32 consecutive rows (128 bytes) of each of four columns.  All epilogue warps follow
+        // every tile's barriers, also those whose lanes are all >= Ng.
         const int quarter = warp & 3, half = warp >> 2;
         const int n0 = quarter * 32;
         const int ncol = Ng - n0 < 32 ? Ng - n0 : 32;        // valid columns of this warp (may be <= 0)
@@ -454,26 +465,42 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(const __grid_constant__ 
                     mbar_arrive(&tempty[a]);
                 }
                 if (ncol <= 0) continue;
+                // lane n -> row n of the block (its column's 32 rows), as 16-byte units
+                float4 *brow = reinterpret_cast<float4 *>(buf + lane * 32);
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    buf[lane * 33 + j] = v0[j];
-                    buf[lane * 33 + 16 + j] = v1[j];
+                for (int u = 0; u < 4; ++u) {
+                    brow[u ^ (lane & 7)] = make_float4(v0[4 * u], v0[4 * u + 1], v0[4 * u + 2], v0[4 * u + 3]);
+                    brow[(u + 4) ^ (lane & 7)] = make_float4(v1[4 * u], v1[4 * u + 1], v1[4 * u + 2], v1[4 * u + 3]);
                 }
                 __syncwarp();
-                // this lane now stores row R of the warp's columns
-                const long long R = (long long)ti.row0 + half * 128 + rnd * 32 + lane;
+                // this lane stores rows R .. R + 3 of columns n0 + 8 (lane >> 3) + c, c < 8:
+                // eight lanes cover 32 consecutive rows (128 bytes) of one column
+                const int ru = lane & 7, cg = lane >> 3;
+                const long long R = (long long)ti.row0 + half * 128 + rnd * 32 + 4 * ru;
                 if (R < Ng2) {
                     const int rhi = (int)(R / Ng), rlo = (int)(R - (long long)(R / Ng) * Ng);
-                    if (PASS == P_XI) {
-                        float *p = A.out + ti.pp_off + ((long long)(n0 + 2) * S + (rhi + 2)) * S + (rlo + 2);
-                        for (int c = 0; c < ncol; ++c, p += S * S) *p = buf[c * 33 + lane] * scale;
-                    } else if (PASS == P_XF) {
-                        const float lr = lam[rhi] + lam[rlo];
-                        float *p = A.out + ti.m_off + (long long)n0 * Ng2 + R;
-                        for (int c = 0; c < ncol; ++c, p += Ng2) *p = __fdividef(buf[c * 33 + lane], lam[n0 + c] + lr);
-                    } else {
-                        float *p = A.out + ti.m_off + (long long)n0 * Ng2 + R;
-                        for (int c = 0; c < ncol; ++c, p += Ng2) *p = buf[c * 33 + lane];
+                    float4 lr;
+                    if (PASS == P_XF)
+                        lr = make_float4(lam[rhi] + lam[rlo], lam[rhi] + lam[rlo + 1], lam[rhi] + lam[rlo + 2],
+                                         lam[rhi] + lam[rlo + 3]);
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        const int nl = cg * 8 + c;
+                        if (nl >= ncol) break;
+                        float4 x = reinterpret_cast<const float4 *>(buf + nl * 32)[ru ^ (nl & 7)];
+                        if (PASS == P_XI) {
+                            // rows R .. R + 3 share rhi (Ng % 4 == 0); padded boxes start 2 floats
+                            // past a 64-float boundary, so interior rows are 16-byte aligned
+                            float *p = A.out + ti.pp_off + ((long long)(n0 + nl + 2) * S + (rhi + 2)) * S + (rlo + 2);
+                            *reinterpret_cast<float4 *>(p) = make_float4(x.x * scale, x.y * scale, x.z * scale, x.w * scale);
+                        } else {
+                            if (PASS == P_XF) {
+                                const float ln = lam[n0 + nl];
+                                x = make_float4(__fdividef(x.x, ln + lr.x), __fdividef(x.y, ln + lr.y),
+                                                __fdividef(x.z, ln + lr.z), __fdividef(x.w, ln + lr.w));
+                            }
+                            *reinterpret_cast<float4 *>(A.out + ti.m_off + (long long)(n0 + nl) * Ng2 + R) = x;
+                        }
                     }
                 }
                 __syncwarp();
