@@ -494,11 +494,22 @@ def run_gpu(args, rank, world, local_rank):
                 "gpu_launches": int(launches * args.steps),
                 "clocks": clk,
                 "roofline": roofline, "cpu_baseline": cpu,
-                "stats": {k: v for k, v in sim.stats().items() if k in ("ms_lpt", "ms_evolve", "r", "p")}}
+                "stats": {k: v for k, v in sim.stats().items() if k in ("ms_lpt", "ms_evolve", "r", "p")},
+                "deposit_autotune": deposit_choice(sc, sim.stats())}
         print(json.dumps(line), flush=True)
     sim.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def deposit_choice(sc, st):
+    """The deposit form the context's autotuner kept and the candidates it timed (ms per
+    deposit of all boxes; every form gives the same density bit for bit)."""
+    names = ("sorted bricks, 256 threads", "sorted bricks, 512 threads", "L2 fixed-point atomics")
+    form = {sc.SCOLA_DEPOSIT_SORTED: "sorted bricks, %d threads" % st["deposit_threads"],
+            sc.SCOLA_DEPOSIT_ATOMIC: names[2]}.get(st["deposit_form"], "not tuned")
+    return {"kept": form, "candidates_ms": {n: round(t, 4) for n, t in zip(names, st["ms_deposit_candidates"])
+                                            if t > 0}}
 
 
 def main():

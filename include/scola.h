@@ -57,6 +57,15 @@ typedef enum scola_dst_variant {
     SCOLA_DST_AUTO = 2           /* 3xTF32 tensor cores when every Ng allows it, else FP32 cores */
 } scola_dst_variant;
 
+typedef enum scola_deposit_form {
+    SCOLA_DEPOSIT_AUTO = 0,      /* the faster of the forms below on this context's boxes, timed
+                                    once with CUDA events before the first evolution */
+    SCOLA_DEPOSIT_SORTED = 1,    /* particles sorted by 16^3-cell brick, each brick's counts
+                                    reduced in shared memory (256 or 512 threads, timed) */
+    SCOLA_DEPOSIT_ATOMIC = 2     /* 64-bit fixed-point atomics into an L2-resident scratch,
+                                    boxes taken in groups whose counts fit L2 */
+} scola_deposit_form;
+
 typedef enum scola_batch_mode {
     SCOLA_BATCH_ALL = 0,         /* every box in each launch (batched form) */
     SCOLA_BATCH_PER_TILE = 1     /* one box per launch, boxes in turn (plain per-tile form) */
@@ -84,6 +93,9 @@ typedef enum scola_batch_mode {
  *   fda_order    finite-difference order; only 2 is built
  *   dst_variant  one of scola_dst_variant
  *   batch_mode   one of scola_batch_mode (same results, different launch shapes)
+ *   deposit_form one of scola_deposit_form.  Every form sums the CIC weights as
+ *                2^-32 fixed-point integers, so all give the same density bit for
+ *                bit; the choice changes only the speed
  *   box_first, box_count  evolve only boxes [box_first, box_first + box_count)
  *                of the tiling (both 0: all boxes).  Boxes never communicate
  *                (Sec. 3.2), so several contexts (for example one per GPU) can
@@ -103,7 +115,7 @@ typedef struct scola_params {
     int32_t batch_mode;
     int32_t box_first;
     int32_t box_count;
-    int32_t reserved;            /* must be 0 */
+    int32_t deposit_form;        /* one of scola_deposit_form */
     double Om, OL, h, ns, sigma8;
     double a_i, a_f;
     double nLPT;
@@ -119,9 +131,16 @@ typedef struct scola_stats {
     int64_t mesh_cells;           /* sum over boxes of Ng^3 */
     int32_t force_evaluations;    /* nsteps + 1 */
     double r, p;                  /* over-simulation r (Eq. 20), parallelisation potential p (Eq. 21) */
-    double ms_lpt;                /* initial-condition and 2LPT stage, device time */
+    double ms_lpt;                /* initial-condition and 2LPT stage, device time (on the
+                                     first call, plus the deposit autotuner's runs) */
     double ms_evolve;             /* gather + evolution + scatter, device time */
     int64_t kernel_launches;      /* kernels launched by the last forward call */
+    int32_t deposit_form;         /* the form in use: SCOLA_DEPOSIT_SORTED or _ATOMIC (0 before
+                                     the first scola_forward / scola_setup_boxes) */
+    int32_t deposit_threads;      /* threads per brick CTA of the sorted form, else 0 */
+    double ms_deposit_candidates[3]; /* autotuner timings of one deposit (all boxes, or box 0 in
+                                     the per-tile form): sorted/256, sorted/512, atomic;
+                                     0 = not timed */
 } scola_stats;
 
 /*

@@ -21,6 +21,9 @@ SCOLA_DST_TC_4XTF32 = 3
 SCOLA_DST_AUTO = 2
 SCOLA_BATCH_ALL = 0
 SCOLA_BATCH_PER_TILE = 1
+SCOLA_DEPOSIT_AUTO = 0
+SCOLA_DEPOSIT_SORTED = 1
+SCOLA_DEPOSIT_ATOMIC = 2
 
 
 class ScolaError(RuntimeError):
@@ -34,7 +37,7 @@ class ScolaParams(ctypes.Structure):
         ("L", c_double), ("Np", c_int32), ("Ntiles", c_int32), ("Nbuf", c_int32),
         ("mesh_ratio", c_int32), ("Ng", c_int32), ("fda_order", c_int32),
         ("dst_variant", c_int32), ("nsteps", c_int32), ("batch_mode", c_int32),
-        ("box_first", c_int32), ("box_count", c_int32), ("reserved", c_int32),
+        ("box_first", c_int32), ("box_count", c_int32), ("deposit_form", c_int32),
         ("Om", c_double), ("OL", c_double), ("h", c_double), ("ns", c_double),
         ("sigma8", c_double), ("a_i", c_double), ("a_f", c_double), ("nLPT", c_double),
         ("buffers", ctypes.POINTER(c_int32)),
@@ -46,6 +49,8 @@ class ScolaStats(ctypes.Structure):
         ("nboxes", c_int32), ("box_particles", c_int64), ("mesh_cells", c_int64),
         ("force_evaluations", c_int32), ("r", c_double), ("p", c_double),
         ("ms_lpt", c_double), ("ms_evolve", c_double), ("kernel_launches", c_int64),
+        ("deposit_form", c_int32), ("deposit_threads", c_int32),
+        ("ms_deposit_candidates", c_double * 3),
     ]
 
 
@@ -115,11 +120,12 @@ def _ptr(x):
 def make_params(L, Np, Ntiles, Nbuf=0, mesh_ratio=1, Ng=0, nsteps=10, Om=0.3, OL=0.7, h=0.7,
                 ns=0.96, sigma8=0.8, a_i=0.02, a_f=1.0, nLPT=-2.5, fda_order=2,
                 dst_variant=SCOLA_DST_AUTO, batch_mode=SCOLA_BATCH_ALL, buffers=None, box_first=0,
-                box_count=0):
+                box_count=0, deposit_form=SCOLA_DEPOSIT_AUTO):
     """Build a ScolaParams; ``buffers`` (per-tile widths) is kept alive on the struct."""
     p = ScolaParams(L=L, Np=Np, Ntiles=Ntiles, Nbuf=Nbuf, mesh_ratio=mesh_ratio, Ng=Ng,
                     fda_order=fda_order, dst_variant=dst_variant, nsteps=nsteps,
-                    batch_mode=batch_mode, box_first=box_first, box_count=box_count, reserved=0,
+                    batch_mode=batch_mode, box_first=box_first, box_count=box_count,
+                    deposit_form=deposit_form,
                     Om=Om, OL=OL,
                     h=h, ns=ns, sigma8=sigma8, a_i=a_i, a_f=a_f, nLPT=nLPT)
     if buffers is not None:
@@ -210,7 +216,9 @@ def scola_time_table(params):
 def scola_get_stats(ctx):
     st = ScolaStats()
     _check(_lib.scola_get_stats(ctx, ctypes.byref(st)), "scola_get_stats")
-    return {name: getattr(st, name) for name, _ in ScolaStats._fields_}
+    out = {name: getattr(st, name) for name, _ in ScolaStats._fields_}
+    out["ms_deposit_candidates"] = list(out["ms_deposit_candidates"])
+    return out
 
 
 KERNEL_CLASSES = ("pad", "deposit", "dst_1", "dst_2", "dst_3", "dst_4", "dst_5", "dst_6",

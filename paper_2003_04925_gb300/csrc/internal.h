@@ -32,14 +32,16 @@ constexpr long long kDepositGroupCells = 6 << 20;   // counts per deposit group 
 
 struct BoxDesc {
     int Nsc, Ng, Nbuf, tbl;       // tbl: index of the DST table for this Ng
-    int tx, ty, tz, pad0;
+    int tx, ty, tz;
+    int nbe;                      // sorted deposit: key bricks per axis, ceil(Ng / 16) + 1
     long long p_off;              // first particle in the arena
     long long m_off;              // first interior mesh cell
     long long pp_off;             // first padded mesh cell
     long long sh_off;             // first compact shell value
     float dq, dg, inv_dg, q2u;    // q2u = dq / dg
     float nbar_inv;               // (Ng / Nsc)^3
-    float pad1[3];
+    int key_off;                  // sorted deposit: first key of the box (8 nbe^3 keys per box)
+    float pad1[2];
     double dg_d, origin_d[3];     // FP64 box geometry (cell size, origin of the box frame)
 };
 
@@ -125,6 +127,15 @@ struct Ctx {
     int *dev_err = nullptr;                           // set by kernels whose bounded waits expired
     float *part = nullptr;
     unsigned long long *dep_acc = nullptr;
+    // sorted deposit (k_deposit_sorted.cu): per-key counts, slice offsets, fill cursors; the
+    // entries (one per box particle at most); the real bricks (box, brick in box)
+    int deposit_form = 0;                             // 0: sorted bricks, 1: L2 fixed-point atomics
+    int deposit_threads = 512;                        // threads per brick CTA of the sorted form
+    bool tuned = false;                               // the autotuner has picked the forms above
+    int *kcount = nullptr, *koffs = nullptr, *kcursor = nullptr;
+    float4 *sentries = nullptr;
+    Chunk *sbricks = nullptr;  int n_sbricks = 0;
+    std::vector<int> sbbeg;
     float *work = nullptr, *work2 = nullptr, *phi = nullptr, *shell = nullptr;
 
     // full-box LPT stage
@@ -163,7 +174,10 @@ cudaError_t launch_box_init(Ctx &c);
 cudaError_t launch_shell(Ctx &c);
 cudaError_t launch_pad(Ctx &c, float D1);
 cudaError_t launch_deposit(Ctx &c, const float *s, long long stride, float *delta_out = nullptr);
+cudaError_t launch_deposit_atomic(Ctx &c, const float *s, long long stride, float *delta_out);
+cudaError_t launch_deposit_sorted(Ctx &c, const float *s, long long stride, float *delta_out);
 cudaError_t init_pm_kernels(Ctx &c);
+cudaError_t init_deposit_kernels();
 int tc_plan_stages(int Ng, int &Npad, int &nkc);
 bool tc_supported(int Ng);
 cudaError_t init_tc_kernels();

@@ -141,7 +141,7 @@ k_density_source(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ ch
 
 }  // namespace
 
-cudaError_t launch_deposit(Ctx &c, const float *s, long long stride, float *delta_out) {
+cudaError_t launch_deposit_atomic(Ctx &c, const float *s, long long stride, float *delta_out) {
     // box groups of the current view: the precomputed groups, or the one box of the
     // per-tile form (whose lists the view has already restricted)
     const bool one = c.view_box >= 0;
@@ -172,6 +172,12 @@ cudaError_t launch_deposit(Ctx &c, const float *s, long long stride, float *delt
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+// The deposit in the form the context selected (both give bit-identical delta').
+cudaError_t launch_deposit(Ctx &c, const float *s, long long stride, float *delta_out) {
+    return c.deposit_form == 0 ? launch_deposit_sorted(c, s, stride, delta_out)
+                               : launch_deposit_atomic(c, s, stride, delta_out);
 }
 
 }  // namespace scola

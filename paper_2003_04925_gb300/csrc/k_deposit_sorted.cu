@@ -1,0 +1,287 @@
+// CIC deposit B^sCOLA (Sec. 3.4.1) and the Poisson source delta' = delta - Lap Phi_BC
+// (App. C, Eq. 62) by sorting the particles by brick and reducing in shared memory.
+//
+// The interior mesh of a box is cut into bricks of 16^3 cells; brick b owns cells
+// [16 b, 16 b + 16) along each axis.  A particle whose clamped mesh coordinate has integer
+// part i0 puts CIC weight on cells i0 and i0 + 1 along each axis.  It is keyed by the
+// brick that owns its upper corner, ((i0 + 1) >> 4) per axis, and by a 3-bit class whose
+// bit a says that its lower corner lies in the brick below along axis a ((i0_a + 1) is a
+// multiple of 16).  The key grid has one extra brick per axis (index nb = ceil(Ng / 16))
+// for particles whose upper corner is just outside the mesh.  Particles with no corner
+// inside the mesh are dropped (their weight is outside, as B^sCOLA requires).
+//
+//   count  per-key entry counts (one warp-aggregated atomic per distinct key in a warp)
+//   scan   per-box exclusive prefix sums of the counts: each key's slice of the box's list
+//   fill   every particle writes (f_x, f_y, f_z, packed i0) into its key's slice
+//   brick  one CTA per real brick reads its own 8 class slices and the slices of its 7
+//          upper neighbours whose class bits point back at it (about 1.2 entries per
+//          particle), adds the CIC weights that fall in its cells to 2^-32 fixed-point
+//          counters in shared memory, then writes delta and delta' for its cells.
+// Integer sums do not depend on the order of the additions, so the result is the same
+// for any order of the entries within a slice.
+#include "device_util.cuh"
+
+namespace scola {
+
+namespace {
+
+constexpr int kBrick = 16;
+constexpr int kBrickCells = kBrick * kBrick * kBrick;
+
+// The (neighbour offset d, class c) pairs with (c & d) == d: the slices a brick reads.
+constexpr int kSegments = 27;
+__constant__ int kSegD[kSegments] = {0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 2, 2, 2, 2, 3, 3, 4, 4, 4, 4, 5, 5, 6, 6, 7};
+__constant__ int kSegC[kSegments] = {0, 1, 2, 3, 4, 5, 6, 7, 1, 3, 5, 7, 2, 3, 6, 7, 3, 7, 4, 5, 6, 7, 5, 7, 6, 7, 7};
+
+struct SortEntry {
+    int key;          // box-local key ((bx nbe + by) nbe + bz) 8 + class, or -1 (no weight inside)
+    float4 e;         // f_x, f_y, f_z, packed i0 (+2, 10 bits per axis)
+};
+
+__device__ __forceinline__ SortEntry sort_entry(const BoxDesc &B, const float *__restrict__ s, long long stride,
+                                                int local) {
+    const int Nsc = B.Nsc, Ng = B.Ng, nbe = B.nbe;
+    int b[3];
+    decode_local(local, Nsc, b[0], b[1], b[2]);
+    const long long gi = B.p_off + local;
+    int i0[3];
+    float f[3];
+    bool inside = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float u = fmaf(__ldg(s + a * stride + gi), B.inv_dg, fmaf((float)b[a], B.q2u, 0.5f * B.q2u - 0.5f));
+        u = fminf(fmaxf(u, -2.0f), (float)Ng + 1.0f);
+        const float fl = floorf(u);
+        i0[a] = (int)fl;
+        f[a] = u - fl;
+        inside = inside && i0[a] >= -1 && i0[a] < Ng;
+    }
+    SortEntry r;
+    r.key = -1;
+    r.e = make_float4(f[0], f[1], f[2],
+                      __int_as_float((i0[0] + 2) | ((i0[1] + 2) << 10) | ((i0[2] + 2) << 20)));
+    if (inside) {
+        const int cls = (((i0[0] + 1) & (kBrick - 1)) == 0 ? 1 : 0) | (((i0[1] + 1) & (kBrick - 1)) == 0 ? 2 : 0) |
+                        (((i0[2] + 1) & (kBrick - 1)) == 0 ? 4 : 0);
+        r.key = ((((i0[0] + 1) >> 4) * nbe + ((i0[1] + 1) >> 4)) * nbe + ((i0[2] + 1) >> 4)) * 8 + cls;
+    }
+    return r;
+}
+
+// FILL = false: add each key's entries of this chunk to the counts.  FILL = true: reserve
+// slots through the cursors and write the entries.  One atomic per distinct key per warp.
+template <bool FILL>
+__global__ void __launch_bounds__(kChunk)
+k_sort_bin(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks, const float *__restrict__ s,
+           long long stride, int *__restrict__ ctr, float4 *__restrict__ entries) {
+    const Chunk ch = chunks[blockIdx.x];
+    const BoxDesc &B = boxes[ch.box];
+    const int local = ch.start + threadIdx.x;
+    SortEntry se;
+    se.key = -1;
+    if (local < B.Nsc * B.Nsc * B.Nsc) se = sort_entry(B, s, stride, local);
+    const unsigned peers = __match_any_sync(0xffffffffu, se.key);   // every lane takes part
+    const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+    int* const kc = ctr + B.key_off;
+    if (!FILL) {
+        if (se.key >= 0 && lane == leader) atomicAdd(kc + se.key, __popc(peers));
+        return;
+    }
+    int base = 0;
+    if (se.key >= 0 && lane == leader) base = atomicAdd(kc + se.key, __popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (se.key >= 0) entries[B.p_off + base + __popc(peers & ((1u << lane) - 1u))] = se.e;
+}
+
+// Exclusive prefix sums of one box's key counts (one CTA of 1024 threads per box).
+__global__ void __launch_bounds__(1024)
+k_sort_scan(const BoxDesc *__restrict__ boxes, int box0, const int *__restrict__ cnt, int *__restrict__ offs,
+            int *__restrict__ cursor) {
+    const BoxDesc &B = boxes[box0 + blockIdx.x];
+    const int n = B.nbe * B.nbe * B.nbe * 8, off = B.key_off;
+    __shared__ int wsum[32];
+    __shared__ int carry;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < n; base += 1024) {
+        const int i = base + tid;
+        const int v = i < n ? cnt[off + i] : 0;
+        int x = v;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, d);
+            if (lane >= d) x += y;
+        }
+        if (lane == 31) wsum[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            int w = wsum[lane];
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, w, d);
+                if (lane >= d) w += y;
+            }
+            wsum[lane] = w;
+        }
+        __syncthreads();
+        const int excl = carry + (warp ? wsum[warp - 1] : 0) + x - v;
+        if (i < n) {
+            offs[off + i] = excl;
+            cursor[off + i] = excl;
+        }
+        __syncthreads();
+        if (tid == 1023) carry = excl + v;
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ void store4(float *p, const float (&v)[4], bool vec, int left) {
+    if (vec) {
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+        return;
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+        if (e < left) p[e] = v[e];
+}
+
+// One CTA of T threads per real brick (item.start = brick index in the box, nb^3 of them).
+template <int kBrickThreads>
+__global__ void __launch_bounds__(kBrickThreads, kBrickThreads == 256 ? 5 : 3)
+k_sort_brick(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ items, const int *__restrict__ cnt,
+             const int *__restrict__ offs, const float4 *__restrict__ entries, const float *__restrict__ phi_pad,
+             float *__restrict__ out, float *__restrict__ delta_out) {
+    __shared__ __align__(16) unsigned long long acc[kBrickCells];
+    __shared__ int seg_o[kSegments], seg_start[kSegments + 1];
+    const Chunk it = items[blockIdx.x];
+    const BoxDesc &B = boxes[it.box];
+    const int Ng = B.Ng, nbe = B.nbe, nb = nbe - 1;
+    const int tid = threadIdx.x;
+    const int bz = it.start % nb, bt = it.start / nb, by = bt % nb, bx = bt / nb;
+    const int x0 = bx * kBrick, y0 = by * kBrick, z0 = bz * kBrick;
+    for (int q = tid; q < kBrickCells / 2; q += kBrickThreads)
+        reinterpret_cast<ulonglong2 *>(acc)[q] = make_ulonglong2(0ull, 0ull);
+    const float4 *list = entries + B.p_off;
+    // the 27 slices this brick reads: neighbour offset d (bit a: +1 along axis a) and class
+    // c with (c & d) == d; warp 0 loads their counts and offsets and scans the counts
+    if (tid < 32) {
+        int n = 0;
+        if (tid < kSegments) {
+            const int d = kSegD[tid], c = kSegC[tid];
+            const int key = B.key_off + (((bx + (d & 1)) * nbe + (by + ((d >> 1) & 1))) * nbe + (bz + (d >> 2))) * 8 + c;
+            n = cnt[key];
+            seg_o[tid] = offs[key];
+        }
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, n, o);
+            if (tid >= o) n += y;
+        }
+        if (tid < kSegments) seg_start[tid + 1] = n;
+        if (tid == 0) seg_start[0] = 0;
+    }
+    __syncthreads();
+    const int total = seg_start[kSegments];
+    for (int e = tid; e < total; e += kBrickThreads) {
+        int lo = 0, hi = kSegments;              // seg_start[lo] <= e < seg_start[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (seg_start[mid] <= e) lo = mid;
+            else hi = mid;
+        }
+        const float4 v = list[seg_o[lo] + e - seg_start[lo]];
+        const int pk = __float_as_int(v.w);
+        const int lx = (pk & 1023) - 2 - x0, ly = ((pk >> 10) & 1023) - 2 - y0, lz = ((pk >> 20) & 1023) - 2 - z0;
+#pragma unroll
+        for (int ex = 0; ex < 2; ++ex) {
+            const int cx = lx + ex;
+            if ((unsigned)cx >= (unsigned)kBrick || x0 + cx >= Ng) continue;
+            const float wx = ex ? v.x : 1.0f - v.x;
+#pragma unroll
+            for (int ey = 0; ey < 2; ++ey) {
+                const int cy = ly + ey;
+                if ((unsigned)cy >= (unsigned)kBrick || y0 + cy >= Ng) continue;
+                const float wxy = wx * (ey ? v.y : 1.0f - v.y);
+#pragma unroll
+                for (int ez = 0; ez < 2; ++ez) {
+                    const int cz = lz + ez;
+                    if ((unsigned)cz >= (unsigned)kBrick || z0 + cz >= Ng) continue;
+                    atomicAdd(&acc[(cx * kBrick + cy) * kBrick + cz], weight_to_fixed(wxy * (ez ? v.z : 1.0f - v.z)));
+                }
+            }
+        }
+    }
+    __syncthreads();
+    // cells: item q -> (x, y) row of the brick, 4 consecutive z cells
+    const float sc = B.nbar_inv * 2.3283064365386963e-10f, c2 = B.inv_dg * B.inv_dg;
+    const int S = Ng + 4;
+    for (int q = tid; q < kBrickCells / 4; q += kBrickThreads) {
+        const int lz = (q % (kBrick / 4)) * 4, ly = (q / (kBrick / 4)) % kBrick, lx = q / (kBrick * kBrick / 4);
+        const int i = x0 + lx, j = y0 + ly, k = z0 + lz;
+        if (i >= Ng || j >= Ng || k >= Ng) continue;
+        const ulonglong2 *a = reinterpret_cast<const ulonglong2 *>(acc + (lx * kBrick + ly) * kBrick + lz);
+        const ulonglong2 a01 = a[0], a23 = a[1];
+        float v[4];
+        v[0] = fixed_to_float(a01.x) * sc - 1.0f;
+        v[1] = fixed_to_float(a01.y) * sc - 1.0f;
+        v[2] = fixed_to_float(a23.x) * sc - 1.0f;
+        v[3] = fixed_to_float(a23.y) * sc - 1.0f;
+        const long long cell = B.m_off + ((long long)i * Ng + j) * Ng + k;
+        const bool vec = k + 4 <= Ng && (Ng & 3) == 0;
+        if (delta_out) store4(delta_out + cell, v, vec, Ng - k);
+        if (i == 0 || j == 0 || i == Ng - 1 || j == Ng - 1 || k == 0 || k + 4 >= Ng) {
+            const float *P = phi_pad + B.pp_off + ((i + 2) * S + (j + 2)) * S + (k + 2);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int kk = k + e;
+                if (kk >= Ng) break;
+                float bc = 0.0f;
+                if (i == 0) bc += P[e - S * S];
+                if (i == Ng - 1) bc += P[e + S * S];
+                if (j == 0) bc += P[e - S];
+                if (j == Ng - 1) bc += P[e + S];
+                if (kk == 0) bc += P[e - 1];
+                if (kk == Ng - 1) bc += P[e + 1];
+                v[e] -= bc * c2;
+            }
+        }
+        store4(out + cell, v, vec, Ng - k);
+    }
+}
+
+}  // namespace
+
+// Shared memory is the brick kernel's occupancy limit: ask for the largest carveout.
+cudaError_t init_deposit_kernels() {
+    cudaError_t e = cudaFuncSetAttribute(k_sort_brick<256>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_sort_brick<512>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                cudaSharedmemCarveoutMaxShared);
+}
+
+cudaError_t launch_deposit_sorted(Ctx &c, const float *s, long long stride, float *delta_out) {
+    // the boxes of the current view: all, or one in the per-tile form
+    const int box0 = c.view_box >= 0 ? c.view_box : 0;
+    const int nbox = c.view_box >= 0 ? 1 : c.nboxes;
+    const BoxDesc &first = c.boxes_h[box0];
+    const BoxDesc &last = c.boxes_h[box0 + nbox - 1];
+    const long long k0 = first.key_off;
+    const long long nk = last.key_off + 8LL * last.nbe * last.nbe * last.nbe - k0;
+    cudaError_t e = cudaMemsetAsync(c.kcount + k0, 0, sizeof(int) * (size_t)nk, c.stream);
+    if (e != cudaSuccess) return e;
+    k_sort_bin<false><<<c.n_pchunks, kChunk, 0, c.stream>>>(c.boxes, c.pchunks, s, stride, c.kcount, nullptr);
+    k_sort_scan<<<nbox, 1024, 0, c.stream>>>(c.boxes, box0, c.kcount, c.koffs, c.kcursor);
+    k_sort_bin<true><<<c.n_pchunks, kChunk, 0, c.stream>>>(c.boxes, c.pchunks, s, stride, c.kcursor, c.sentries);
+    if (c.deposit_threads == 256)
+        k_sort_brick<256><<<c.n_sbricks, 256, 0, c.stream>>>(c.boxes, c.sbricks, c.kcount, c.koffs, c.sentries,
+                                                               c.phi, c.work2, delta_out);
+    else
+        k_sort_brick<512><<<c.n_sbricks, 512, 0, c.stream>>>(c.boxes, c.sbricks, c.kcount, c.koffs, c.sentries,
+                                                               c.phi, c.work2, delta_out);
+    c.launches += 4;
+    return cudaGetLastError();
+}
+
+}  // namespace scola

@@ -11,6 +11,10 @@ def workload_cfg(name, **over):
     W = dict(synth_inputs.WORKLOADS[name])
     kw = dict(L=W["L"], Np=W["Np"], Ntiles=W["Ntiles"], Nbuf=W["Nbuf"], mesh_ratio=W["mesh_ratio"],
               nsteps=W["nsteps"], a_i=W["a_i"], a_f=W["a_f"])
+    if W["Nbuf"] == "uneven":
+        kw["buffers"] = [int(b) for b in synth_inputs.uneven_buffers(W["Ntiles"], W["buffer_seed"],
+                                                                      W["buffer_choices"])]
+        kw["Nbuf"] = 0
     kw.update(over)
     return kw
 
@@ -64,3 +68,29 @@ def box_initial_displacements(cfg, fields, sched, b):
 
 def oracle_shell(cfg, fields, g):
     return boundary.bc_shell(fields.phi1, cfg.L, g.origin, g.dg, g.Ng)
+
+
+def sampled_box_errors(cfg, fields, sched, x, p, boxes, cache=None):
+    """Errors of a GPU run (final x, p of every particle) on sampled boxes against the oracle's
+    evolution of those boxes (boxes are independent, so each is exact on its own): per box the
+    final-position RMS and max error in PM cells (tile particles) and the momentum RMS error
+    relative to the RMS momentum.  ``cache`` (a dict) keeps the oracle's box results."""
+    out = []
+    q = oscola.lattice_positions(cfg.Np, cfg.L)
+    for b in boxes:
+        r = cache.get(b) if cache is not None else None
+        if r is None:
+            r = oscola.evolve_box(cfg, b, fields, sched)
+            if cache is not None:
+                cache[b] = r
+        g = r["geometry"]
+        keep = tiling.tile_interior_mask(cfg.Np, cfg.Ntiles, g.Nbuf)
+        ids = r["ids"][keep]
+        xr = np.mod(q[ids] + r["s"][keep], cfg.L)
+        dx = np.linalg.norm(periodic_diff(x[ids], xr, cfg.L), axis=1) / g.dg
+        pr = r["p"][keep]
+        dp = np.linalg.norm(np.asarray(p[ids], np.float64) - pr, axis=1)
+        out.append(dict(box=int(b), Nsc=int(g.Nsc), Ng=int(g.Ng),
+                        pos_rms_cells=float(np.sqrt(np.mean(dx**2))), pos_max_cells=float(dx.max()),
+                        mom_rms_rel=float(np.sqrt(np.mean(dp**2)) / np.sqrt(np.mean(np.sum(pr**2, 1))))))
+    return out

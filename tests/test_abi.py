@@ -54,6 +54,39 @@ def test_validation_errors_without_gpu(lib):
     bad = lib.make_params(L=100.0, Np=32, Ntiles=2, Nbuf=10)          # box larger than the lattice
     with pytest.raises(lib.ScolaError):
         lib.scola_tiling_info(bad)
+    bad = lib.make_params(L=100.0, Np=32, Ntiles=2, Nbuf=4, deposit_form=3)
+    with pytest.raises(lib.ScolaError) as e:
+        lib.scola_tiling_info(bad)
+    assert e.value.status == 1
+
+
+def test_struct_layout_matches_header(lib, tmp_path):
+    """Field offsets and sizes of the ctypes structures equal those a C compiler gives the
+    header's structures."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    from paper_2003_04925_gb300.binding import ScolaParams, ScolaStats
+    lines = ['#include <stdio.h>', '#include "scola.h"', "int main(void) {"]
+    for cls, cname in ((ScolaParams, "scola_params"), (ScolaStats, "scola_stats")):
+        lines.append('printf("%s sizeof %%zu\\n", sizeof(%s));' % (cname, cname))
+        for f, _ in cls._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (cname, f, cname, f))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for ln in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        a, b, v = ln.split()
+        got[(a, b)] = int(v)
+    for cls, cname in ((ScolaParams, "scola_params"), (ScolaStats, "scola_stats")):
+        assert got[(cname, "sizeof")] == ctypes.sizeof(cls), cname
+        for f, _ in cls._fields_:
+            assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)
 
 
 def test_tiling_info_matches_oracle_and_table1(lib):

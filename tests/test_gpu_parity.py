@@ -14,7 +14,7 @@ import torch
 
 import synth_inputs
 from gpu_common import (box_initial_displacements, lib_kwargs, oracle_cfg, oracle_fields,
-                        oracle_shell, periodic_diff, workload_cfg)
+                        oracle_shell, periodic_diff, sampled_box_errors, workload_cfg)
 from oracle import pm, scola as oscola, stats, tiling
 
 pytestmark = pytest.mark.gpu
@@ -207,6 +207,48 @@ def test_per_tile_form_matches_batched_form(name, variant):
     b.close()
 
 
+@pytest.mark.parametrize("name", list(CASES_PM))
+def test_deposit_forms_are_bit_identical(name):
+    # Every deposit form sums 2^-32 fixed-point weights, so the sorted-brick form (256 and
+    # 512 threads), the atomic form and the autotuned choice give the same delta' and the
+    # same run bit for bit, batched and per tile.
+    kw = CASES_PM[name]
+    w_np = synth_inputs.white_noise(kw["Np"], 5)
+    w = _to_dev(w_np)
+    cfg = oracle_cfg(kw)
+    _, f, sched = oracle_fields(kw)
+    s_cat = np.concatenate([20.0 * box_initial_displacements(cfg, f, sched, b)[2]
+                            for b in range(cfg.nboxes)]).T.copy()
+    s_dev = _to_dev(s_cat)
+    outs = []
+    for form in (sc.SCOLA_DEPOSIT_SORTED, sc.SCOLA_DEPOSIT_ATOMIC, sc.SCOLA_DEPOSIT_AUTO):
+        for mode in (sc.SCOLA_BATCH_ALL, sc.SCOLA_BATCH_PER_TILE):
+            sim = sc.Scola(**dict(lib_kwargs(kw), deposit_form=form, batch_mode=mode))
+            sim.lpt_fields(w)
+            sim.setup_boxes()
+            _, delta, _ = sim.pm_force(s_dev, 0.73, want_delta=True)
+            x, p = sim.forward(w)
+            torch.cuda.synchronize()
+            st = sim.stats()
+            want = {sc.SCOLA_DEPOSIT_SORTED: (sc.SCOLA_DEPOSIT_SORTED,),
+                    sc.SCOLA_DEPOSIT_ATOMIC: (sc.SCOLA_DEPOSIT_ATOMIC,),
+                    sc.SCOLA_DEPOSIT_AUTO: (sc.SCOLA_DEPOSIT_SORTED, sc.SCOLA_DEPOSIT_ATOMIC)}[form]
+            assert st["deposit_form"] in want
+            timed = [t > 0 for t in st["ms_deposit_candidates"]]
+            assert timed == {sc.SCOLA_DEPOSIT_SORTED: [True, True, False],
+                             sc.SCOLA_DEPOSIT_ATOMIC: [False, False, True],
+                             sc.SCOLA_DEPOSIT_AUTO: [True, True, True]}[form]
+            # interior cells only (the gaps between boxes' meshes are not written)
+            m_offs, _ = sim.box_offsets()
+            d = torch.cat([delta[m:m + g.Ng**3] for m, g in
+                           zip(m_offs, (oscola.box_geometry(cfg, b) for b in range(cfg.nboxes)))])
+            outs.append((d, x.clone(), p.clone()))
+            sc.scola_device_status(sim.ctx)
+            sim.close()
+    for d, x, p in outs[1:]:
+        assert torch.equal(d, outs[0][0]) and torch.equal(x, outs[0][1]) and torch.equal(p, outs[0][2])
+
+
 @pytest.mark.parametrize("variant", ["simt", "tc"])
 def test_box_ranges_merge_to_the_full_run(variant):
     # Boxes never communicate, so contexts evolving disjoint box ranges (one per GPU in a
@@ -277,3 +319,30 @@ def test_batched_128_sampled_boxes_match_oracle(variant):
         dx = periodic_diff(x[ids], xr, cfg.L)
         rms = np.sqrt(np.mean(np.sum(dx**2, 1))) / r["geometry"].dg
         assert rms <= 1e-3, (b, rms)
+
+
+_UNEVEN_CACHE = {}
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("variant", ["simt", "tc", "tc4"])
+def test_uneven_256_sampled_boxes_match_oracle(variant):
+    # The uneven-buffer workload (256^3 particles, 4^3 tiles, buffers drawn from {4, 8, 16},
+    # 1:1 meshes of 72, 80 and 96 cells in one launch), in the benchmark's launch form; the
+    # oracle evolves one box of each size.  Prints the errors of each DST form (FP32 cores,
+    # 3xTF32 and 4xTF32 tensor cores) against the FP64 oracle.
+    import json
+    kw = workload_cfg("uneven_256")
+    cfg = oracle_cfg(kw)
+    w, fields, sched = oracle_fields(kw)
+    x, p, sim = _forward(kw, w, variant)
+    sc.scola_device_status(sim.ctx)
+    sim.close()
+    nsc = [oscola.box_geometry(cfg, b).Nsc for b in range(cfg.nboxes)]
+    boxes = [nsc.index(n) for n in sorted(set(nsc))]
+    assert len(boxes) == 3
+    errs = sampled_box_errors(cfg, fields, sched, x, p, boxes, _UNEVEN_CACHE)
+    print(json.dumps({"workload": "uneven_256", "dst": variant, "boxes": errs}))
+    for e in errs:
+        assert e["pos_rms_cells"] <= 1e-3, e
+        assert e["mom_rms_rel"] <= 1e-3, e
