@@ -61,7 +61,8 @@ typedef enum scola_deposit_form {
     SCOLA_DEPOSIT_AUTO = 0,      /* the faster of the forms below on this context's boxes, timed
                                     once with CUDA events before the first evolution */
     SCOLA_DEPOSIT_SORTED = 1,    /* particles sorted by 16^3-cell brick, each brick's counts
-                                    reduced in shared memory (256 or 512 threads, timed) */
+                                    reduced in shared memory (256 or 512 threads, 64-bit
+                                    counters or 32-bit halves: timed) */
     SCOLA_DEPOSIT_ATOMIC = 2     /* 64-bit fixed-point atomics into an L2-resident scratch,
                                     boxes taken in groups whose counts fit L2 */
 } scola_deposit_form;
@@ -96,6 +97,17 @@ typedef enum scola_batch_mode {
  *   deposit_form one of scola_deposit_form.  Every form sums the CIC weights as
  *                2^-32 fixed-point integers, so all give the same density bit for
  *                bit; the choice changes only the speed
+ *   batch_boxes  the context's boxes are evolved in batches of consecutive boxes that
+ *                share one set of per-box arenas (boxes never communicate, so any
+ *                batching gives the same result bit for bit).  0 = as many boxes as
+ *                fit in the device memory left after the full-box LPT stage and a
+ *                reserve of 2 x 28 bytes per particle (the caller's w, x, p and the
+ *                host-copy buffers of scola_forward_host) plus 1 GiB; the batch count
+ *                is then raised to a divisor of the box count where batches stay at
+ *                least half full.  A context with more than one batch runs
+ *                scola_forward, scola_forward_host, scola_final_density and the
+ *                host-only calls; the per-stage, inspection and adjoint calls need
+ *                one batch (they return UNSUPPORTED otherwise)
  *   box_first, box_count  evolve only boxes [box_first, box_first + box_count)
  *                of the tiling (both 0: all boxes).  Boxes never communicate
  *                (Sec. 3.2), so several contexts (for example one per GPU) can
@@ -116,6 +128,7 @@ typedef struct scola_params {
     int32_t box_first;
     int32_t box_count;
     int32_t deposit_form;        /* one of scola_deposit_form */
+    int32_t batch_boxes;         /* boxes per streamed batch; 0 = as many as fit */
     double Om, OL, h, ns, sigma8;
     double a_i, a_f;
     double nLPT;
@@ -138,9 +151,13 @@ typedef struct scola_stats {
     int32_t deposit_form;         /* the form in use: SCOLA_DEPOSIT_SORTED or _ATOMIC (0 before
                                      the first scola_forward / scola_setup_boxes) */
     int32_t deposit_threads;      /* threads per brick CTA of the sorted form, else 0 */
-    double ms_deposit_candidates[3]; /* autotuner timings of one deposit (all boxes, or box 0 in
-                                     the per-tile form): sorted/256, sorted/512, atomic;
+    int32_t deposit_split;        /* 1: the sorted form keeps 32-bit halves of the counts */
+    double ms_deposit_candidates[4]; /* autotuner timings of one deposit (all boxes of the first
+                                     batch, or its box 0 in the per-tile form): sorted/256,
+                                     sorted/512, sorted/256 with 32-bit halves, atomic;
                                      0 = not timed */
+    int32_t batches;              /* streamed batches per forward run */
+    int32_t batch_boxes;          /* boxes per batch (the last may hold fewer) */
 } scola_stats;
 
 /*
@@ -218,11 +235,12 @@ scola_status scola_setup_boxes(scola_ctx *ctx);
 scola_status scola_pm_force(scola_ctx *ctx, const float *s_dev, double D1, float *F_dev,
                             float *delta_dev, float *phi_dev);
 
-/* Total number of box particles P (sum over boxes of Np,sCOLA^3). */
+/* Number of box particles P (sum over the boxes of Np,sCOLA^3) of the bound batch: all
+ * boxes of a one-batch context. */
 int64_t scola_box_particle_count(const scola_ctx *ctx);
 
-/* Sizes of the interior and padded mesh arrays: the boxes' Ng^3 and (Ng+4)^3
- * cells at the offsets of scola_box_offsets, with alignment gaps between boxes. */
+/* Sizes of the interior and padded mesh arrays of the bound batch: the boxes' Ng^3 and
+ * (Ng+4)^3 cells at the offsets of scola_box_offsets, with alignment gaps between boxes. */
 int64_t scola_mesh_cell_count(const scola_ctx *ctx);
 int64_t scola_padded_cell_count(const scola_ctx *ctx);
 
@@ -372,6 +390,24 @@ scola_status scola_box_density_noalloc(const float *s_dev, int32_t nsc, int32_t 
  * Synchronous.  Errors: INVALID_ARG (NULL, n < 0), OOM, CUDA.
  */
 scola_status scola_selftest_conversions(int64_t n, uint64_t seed, int64_t *mismatches);
+
+/*
+ * Binned power spectrum of a field on the N^3 LPT grid (Sec. 4.2, Eq. 24), with the
+ * normalisation P(k) = L^3 <|DFT delta|^2> / N^6 over the modes of each bin (the DFT
+ * unnormalised, every mode of the full spectrum counted once).
+ *   delta_dev  device, N^3 FP32 field (k fastest), e.g. from scola_final_density;
+ *              not modified
+ *   nbins      1 .. 2048
+ *   edges      host, nbins + 1 increasing FP64 edges [h/Mpc]; bin b holds
+ *              edges[b] <= |k| < edges[b+1], |k| = 2 pi / L |n| with n the wrapped
+ *              integer wavenumbers
+ *   k_mean, pk host, nbins FP64: mean |k| and P(k) of each bin (NaN for empty bins)
+ *   n_modes    host, nbins: modes per bin
+ * FP32 transform, FP64 sums in a fixed order (deterministic).  Synchronous.
+ * Errors: INVALID_ARG (NULL, nbins out of range, edges not increasing), OOM, CUDA.
+ */
+scola_status scola_power_spectrum(scola_ctx *ctx, const float *delta_dev, int32_t nbins, const double *edges,
+                                  double *k_mean, double *pk, int64_t *n_modes);
 
 scola_status scola_get_stats(const scola_ctx *ctx, scola_stats *out);
 const char *scola_status_string(scola_status status);

@@ -37,7 +37,7 @@ class ScolaParams(ctypes.Structure):
         ("L", c_double), ("Np", c_int32), ("Ntiles", c_int32), ("Nbuf", c_int32),
         ("mesh_ratio", c_int32), ("Ng", c_int32), ("fda_order", c_int32),
         ("dst_variant", c_int32), ("nsteps", c_int32), ("batch_mode", c_int32),
-        ("box_first", c_int32), ("box_count", c_int32), ("deposit_form", c_int32),
+        ("box_first", c_int32), ("box_count", c_int32), ("deposit_form", c_int32), ("batch_boxes", c_int32),
         ("Om", c_double), ("OL", c_double), ("h", c_double), ("ns", c_double),
         ("sigma8", c_double), ("a_i", c_double), ("a_f", c_double), ("nLPT", c_double),
         ("buffers", ctypes.POINTER(c_int32)),
@@ -49,8 +49,8 @@ class ScolaStats(ctypes.Structure):
         ("nboxes", c_int32), ("box_particles", c_int64), ("mesh_cells", c_int64),
         ("force_evaluations", c_int32), ("r", c_double), ("p", c_double),
         ("ms_lpt", c_double), ("ms_evolve", c_double), ("kernel_launches", c_int64),
-        ("deposit_form", c_int32), ("deposit_threads", c_int32),
-        ("ms_deposit_candidates", c_double * 3),
+        ("deposit_form", c_int32), ("deposit_threads", c_int32), ("deposit_split", c_int32),
+        ("ms_deposit_candidates", c_double * 4), ("batches", c_int32), ("batch_boxes", c_int32),
     ]
 
 
@@ -73,6 +73,8 @@ _sig = {
     "scola_box_particle_ids": (c_int32, [c_void_p, c_void_p]),
     "scola_tiling_info": (c_int32, [_P(ScolaParams), c_void_p, c_void_p, _P(c_double), _P(c_double)]),
     "scola_final_density": (c_int32, [c_void_p, c_void_p, c_void_p]),
+    "scola_power_spectrum": (c_int32, [c_void_p, c_void_p, c_int32, _P(c_double), _P(c_double), _P(c_double),
+                                       _P(c_int64)]),
     "scola_time_table": (c_int32, [_P(ScolaParams)] + [c_void_p] * 7),
     "scola_get_stats": (c_int32, [c_void_p, _P(ScolaStats)]),
     "scola_set_profiling": (c_int32, [c_void_p, c_int32]),
@@ -120,12 +122,12 @@ def _ptr(x):
 def make_params(L, Np, Ntiles, Nbuf=0, mesh_ratio=1, Ng=0, nsteps=10, Om=0.3, OL=0.7, h=0.7,
                 ns=0.96, sigma8=0.8, a_i=0.02, a_f=1.0, nLPT=-2.5, fda_order=2,
                 dst_variant=SCOLA_DST_AUTO, batch_mode=SCOLA_BATCH_ALL, buffers=None, box_first=0,
-                box_count=0, deposit_form=SCOLA_DEPOSIT_AUTO):
+                box_count=0, deposit_form=SCOLA_DEPOSIT_AUTO, batch_boxes=0):
     """Build a ScolaParams; ``buffers`` (per-tile widths) is kept alive on the struct."""
     p = ScolaParams(L=L, Np=Np, Ntiles=Ntiles, Nbuf=Nbuf, mesh_ratio=mesh_ratio, Ng=Ng,
                     fda_order=fda_order, dst_variant=dst_variant, nsteps=nsteps,
                     batch_mode=batch_mode, box_first=box_first, box_count=box_count,
-                    deposit_form=deposit_form,
+                    deposit_form=deposit_form, batch_boxes=batch_boxes,
                     Om=Om, OL=OL,
                     h=h, ns=ns, sigma8=sigma8, a_i=a_i, a_f=a_f, nLPT=nLPT)
     if buffers is not None:
@@ -197,6 +199,21 @@ def scola_tiling_info(params):
 
 def scola_final_density(ctx, x, delta):
     _check(_lib.scola_final_density(ctx, _ptr(x), _ptr(delta)), "scola_final_density")
+
+
+def scola_power_spectrum(ctx, delta, edges):
+    """(k_mean, P, n_modes) per bin of a device field on the N^3 grid; edges: nbins + 1 values."""
+    import numpy as np
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    nb = len(e) - 1
+    k = np.empty(nb, np.float64)
+    pk = np.empty(nb, np.float64)
+    n = np.empty(nb, np.int64)
+    dp = ctypes.POINTER(c_double)
+    _check(_lib.scola_power_spectrum(ctx, _ptr(delta), nb, e.ctypes.data_as(dp), k.ctypes.data_as(dp),
+                                     pk.ctypes.data_as(dp), n.ctypes.data_as(ctypes.POINTER(c_int64))),
+           "scola_power_spectrum")
+    return k, pk, n
 
 
 def scola_time_table(params):

@@ -14,8 +14,16 @@
 namespace scola {
 namespace {
 thread_local std::string g_last_error;
+thread_local std::string g_step;     // the failing step a launcher named (step_error)
 }
-void set_error(const std::string &msg) { g_last_error = msg; }
+void set_error(const std::string &msg) {
+    g_last_error = g_step.empty() ? msg : msg + " [" + g_step + "]";
+    g_step.clear();
+}
+cudaError_t step_error(const char *step, cudaError_t e) {
+    g_step = step;
+    return e;
+}
 }  // namespace scola
 
 using namespace scola;
@@ -26,7 +34,13 @@ enum KernelClass {
     KC_COUNT
 };
 
+struct BoxGeom {                         // one box of the tiling: Np,sCOLA, Ng, buffer width
+    int nsc, ng, nbuf;
+};
+
 struct scola_ctx : public Ctx {
+    std::vector<BoxGeom> tiling_geo;     // every box of the tiling
+    std::vector<BoxGeom> ctx_geo;        // the context's boxes
     cudaStream_t cap_stream = nullptr;   // stream used only to capture the evolution graph
     long long graph_kernels = 0;         // kernels in the evolution graph
     long long lpt_kernels = 0;           // kernels of the last LPT stage
@@ -64,10 +78,6 @@ namespace {
 constexpr bool kAutoUsesTensorCores = true;    // AUTO: three-product tensor-core form where supported
 constexpr int kMaxNg = 192;  // the DST passes hold a (Ng x 32 ceil(Ng/32)) sine matrix in shared memory
 
-struct BoxGeom {
-    int nsc, ng, nbuf;
-};
-
 scola_status invalid(const std::string &m) {
     set_error(m);
     return SCOLA_ERR_INVALID_ARG;
@@ -90,6 +100,7 @@ scola_status validate(const scola_params *p, std::vector<int32_t> &bufs, std::ve
         return invalid("unknown dst_variant");
     if (p->batch_mode != SCOLA_BATCH_ALL && p->batch_mode != SCOLA_BATCH_PER_TILE)
         return invalid("unknown batch_mode");
+    if (p->batch_boxes < 0) return invalid("batch_boxes must be >= 0");
     if (p->deposit_form != SCOLA_DEPOSIT_AUTO && p->deposit_form != SCOLA_DEPOSIT_SORTED &&
         p->deposit_form != SCOLA_DEPOSIT_ATOMIC)
         return invalid("unknown deposit_form");
@@ -123,7 +134,7 @@ scola_status validate(const scola_params *p, std::vector<int32_t> &bufs, std::ve
         }
         if (for_kernels && (p->dst_variant == SCOLA_DST_TC_3XTF32 || p->dst_variant == SCOLA_DST_TC_4XTF32) &&
             !tc_supported(ng)) {
-            set_error("the tensor-core DST needs Ng % 4 == 0 and Ng <= 128");
+            set_error("the tensor-core DST needs Ng % 4 == 0 and Ng <= 128, or Ng % 32 == 0 and Ng <= 256");
             return SCOLA_ERR_UNSUPPORTED;
         }
         geo[b] = {nsc, ng, bufs[b]};
@@ -156,30 +167,269 @@ void add_chunks(std::vector<Chunk> &v, int box, long long n, int per) {
     for (long long s = 0; s < n; s += per) v.push_back({box, (int)s});
 }
 
+// Layout of one batch of consecutive boxes [first, first + count) of the tiling: every box's
+// arena offsets and, if `lists`, the work lists of every kernel and the tensor-core tiles.
+// Without lists only the list lengths are counted.  Host only.
+struct BatchPlan {
+    std::vector<BoxGeom> geo;                          // the batch's boxes (its shape)
+    std::vector<BoxDesc> boxes;
+    std::vector<Chunk> pch, tch, shch, zit, cit, mch, ppch, sbr, tct;
+    long long n_pch = 0, n_tch = 0, n_shch = 0, n_zit = 0, n_cit = 0, n_mch = 0, n_ppch = 0, n_sbr = 0,
+              n_tct = 0;
+    std::vector<int> pbeg, shbeg, zbeg, cbeg, mbeg, sbbeg, tile_beg, tile_end, dep_groups;
+    std::vector<long long> group_first;                // per tensor-core group: first tile, count
+    std::vector<int> group_ntiles;
+    long long P = 0, M = 0, MP = 0, SH = 0, NK = 0, dep_cells = 0;
+};
+
+bool same_shape(const std::vector<BoxGeom> &a, const std::vector<BoxGeom> &b) {
+    if (a.size() != b.size()) return false;
+    for (size_t i = 0; i < a.size(); ++i)
+        if (a[i].nsc != b[i].nsc || a[i].ng != b[i].ng || a[i].nbuf != b[i].nbuf) return false;
+    return true;
+}
+
+void plan_batch(const scola_ctx *c, const std::vector<BoxGeom> &tiling_geo, int first, int count, bool lists,
+                BatchPlan &bp) {
+    const scola_params &p = c->prm;
+    const int ntile = p.Np / p.Ntiles;
+    bp = BatchPlan();
+    bp.geo.assign(tiling_geo.begin() + first, tiling_geo.begin() + first + count);
+    auto chunks = [](long long n, int per) { return (n + per - 1) / per; };
+    auto add = [&](std::vector<Chunk> &v, long long &nv, int box, long long n, int per) {
+        if (lists) add_chunks(v, box, n, per);
+        nv += chunks(n, per);
+    };
+    long long P = 0, M = 0, MP = 0, SH = 0, NK = 0;
+    for (int b = 0; b < count; ++b) {
+        bp.pbeg.push_back((int)bp.n_pch);
+        bp.shbeg.push_back((int)bp.n_shch);
+        bp.zbeg.push_back((int)bp.n_zit);
+        bp.cbeg.push_back((int)bp.n_cit);
+        bp.mbeg.push_back((int)bp.n_mch);
+        bp.sbbeg.push_back((int)bp.n_sbr);
+        const BoxGeom &g = bp.geo[b];
+        BoxDesc B;
+        std::memset(&B, 0, sizeof(B));
+        B.Nsc = g.nsc;
+        B.Ng = g.ng;
+        B.Nbuf = g.nbuf;
+        B.tbl = c->tbl_of.at(g.ng);
+        const int gb = first + b;                      // box id in the whole tiling
+        B.tx = gb / (p.Ntiles * p.Ntiles);
+        B.ty = (gb / p.Ntiles) % p.Ntiles;
+        B.tz = gb % p.Ntiles;
+        // interior meshes start at multiples of lcm(64, Ng): aligned, and a whole number of
+        // Ng-float rows from the buffer start (the tensor-core passes address them as rows)
+        {
+            long long q = 64;
+            while (q % g.ng) q += 64;
+            M = (M + q - 1) / q * q;
+        }
+        B.p_off = P;
+        B.m_off = M;
+        // padded boxes start 2 floats past a 64-float boundary: with Ng % 4 == 0 the interior
+        // cells of every padded row (index 2 .. Ng+1) then start 16-byte aligned
+        MP += 2;
+        B.pp_off = MP;
+        B.sh_off = SH;
+        {
+            const int nb = (g.ng + 15) / 16;
+            B.nbe = nb + 1;
+            B.key_off = (int)NK;
+            NK += 8LL * B.nbe * B.nbe * B.nbe;
+            if (lists)
+                for (int t = 0; t < nb * nb * nb; ++t) bp.sbr.push_back({b, t});
+            bp.n_sbr += (long long)nb * nb * nb;
+        }
+        const double Lsc = g.nsc * c->dq;
+        const double dg = Lsc / g.ng;
+        B.dq = (float)c->dq;
+        B.dg = (float)dg;
+        B.inv_dg = (float)(1.0 / dg);
+        B.q2u = (float)((double)g.ng / g.nsc);
+        B.nbar_inv = (float)std::pow((double)g.ng / g.nsc, 3);
+        B.dg_d = dg;
+        const int t3[3] = {B.tx, B.ty, B.tz};
+        for (int a = 0; a < 3; ++a) B.origin_d[a] = ((double)t3[a] * ntile - g.nbuf) * c->dq;
+        bp.boxes.push_back(B);
+        const long long n = (long long)g.nsc * g.nsc * g.nsc;
+        const long long ng3 = (long long)g.ng * g.ng * g.ng;
+        const long long np3 = (long long)(g.ng + 4) * (g.ng + 4) * (g.ng + 4);
+        add(bp.pch, bp.n_pch, b, n, kChunk);
+        add(bp.tch, bp.n_tch, b, (long long)ntile * ntile * ntile, kChunk);
+        add(bp.shch, bp.n_shch, b, np3 - ng3, kChunk);
+        add(bp.mch, bp.n_mch, b, ng3, kChunk);
+        add(bp.ppch, bp.n_ppch, b, np3, kChunk);
+        const long long nz = ((long long)g.ng * g.ng + kTC - 1) / kTC;
+        if (lists)
+            for (long long t = 0; t < nz; ++t) bp.zit.push_back({b, (int)t});
+        bp.n_zit += nz;
+        const long long nc = (long long)g.ng * ((g.ng + kTC - 1) / kTC);
+        if (lists)
+            for (long long t = 0; t < nc; ++t) bp.cit.push_back({b, (int)t});
+        bp.n_cit += nc;
+        auto align64 = [](long long v) { return (v + 63) / 64 * 64; };
+        P += n;
+        M = align64(M + ng3);   // (the next box rounds up further)
+        MP = align64(MP + np3);
+        SH = align64(SH + np3 - ng3);
+    }
+    bp.pbeg.push_back((int)bp.n_pch);
+    bp.shbeg.push_back((int)bp.n_shch);
+    bp.zbeg.push_back((int)bp.n_zit);
+    bp.cbeg.push_back((int)bp.n_cit);
+    bp.mbeg.push_back((int)bp.n_mch);
+    bp.sbbeg.push_back((int)bp.n_sbr);
+    // deposit groups: consecutive boxes whose counts fit the L2-sized scratch (a box larger
+    // than the limit forms a group of its own)
+    for (int b = 0; b < count; ++b) {
+        const long long end = bp.boxes[b].m_off + (long long)bp.geo[b].ng * bp.geo[b].ng * bp.geo[b].ng;
+        if (bp.dep_groups.empty() || end - bp.boxes[bp.dep_groups.back()].m_off > kDepositGroupCells)
+            bp.dep_groups.push_back(b);
+        bp.dep_cells = std::max(bp.dep_cells, end - bp.boxes[bp.dep_groups.back()].m_off);
+    }
+    bp.dep_groups.push_back(count);
+    // tensor-core DST tiles: per Ng group, each box's 256-row tiles (contiguous per box)
+    bp.tile_beg.assign(count, 0);
+    bp.tile_end.assign(count, 0);
+    for (const TcGroup &G : c->tc_groups) {
+        bp.group_first.push_back(bp.n_tct);
+        for (int b = 0; b < count; ++b) {
+            if (bp.geo[b].ng != G.Ng) continue;
+            const long long rows = (long long)G.Ng * G.Ng;
+            bp.tile_beg[b] = (int)bp.n_tct;
+            for (long long t = 0; t * kTcTileRows < rows; ++t) {
+                if (lists) bp.tct.push_back({b, (int)t});
+                ++bp.n_tct;
+            }
+            bp.tile_end[b] = (int)bp.n_tct;
+        }
+        bp.group_ntiles.push_back((int)(bp.n_tct - bp.group_first.back()));
+    }
+    bp.P = P;
+    bp.M = M;
+    bp.MP = MP;
+    bp.SH = SH;
+    bp.NK = NK;
+}
+
+// Device bytes a batch of the given boxes takes in the per-batch arenas.
+long long batch_bytes(const std::vector<BoxGeom> &geo) {
+    long long bytes = 0;
+    for (const BoxGeom &g : geo) {
+        const long long n = (long long)g.nsc * g.nsc * g.nsc;
+        const long long ng3 = (long long)g.ng * g.ng * g.ng;
+        const long long np3 = (long long)(g.ng + 4) * (g.ng + 4) * (g.ng + 4);
+        const long long nbe = (g.ng + 15) / 16 + 1;
+        long long q = 64;
+        while (q % g.ng) q += 64;
+        bytes += 4 * 12 * n + 16 * n + 3 * 4 * 8 * nbe * nbe * nbe   // particles, sorted entries, keys
+                 + 2 * 4 * (ng3 + q) + 4 * (np3 + 66) + 4 * (np3 - ng3 + 64)   // meshes, shell
+                 + 8 * (2 * n / kChunk + 2 * np3 / kChunk + ng3 / kChunk + 3 * g.ng * g.ng + 64);  // lists
+    }
+    return bytes;
+}
+
+// Copies a host list into a preallocated device list.
+template <class T>
+scola_status put(T *dst, const std::vector<T> &src) {
+    if (!src.empty()) CK(cudaMemcpy(dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice));
+    return SCOLA_OK;
+}
+
+// Makes batch k the one the kernels see.  A batch with the shape of the bound one only
+// changes the boxes' tile coordinates (a device-to-device copy of its box descriptors,
+// ordered on the stream, so the captured graph stays valid); another shape re-uploads
+// the work lists (after the stream has drained) and drops the graph.
+scola_status bind_batch(scola_ctx *c, int k, bool force = false) {
+    if (k == c->bound_batch && !force) return SCOLA_OK;
+    const int first = c->batch_first[k], count = c->batch_first[k + 1] - first;
+    const BoxDesc *src = c->all_boxes + first;
+    if (!force && c->bound_batch >= 0) {
+        const int pf = c->batch_first[c->bound_batch];
+        const int pn = c->batch_first[c->bound_batch + 1] - pf;
+        std::vector<BoxGeom> a(c->ctx_geo.begin() + pf, c->ctx_geo.begin() + pf + pn);
+        std::vector<BoxGeom> b(c->ctx_geo.begin() + first, c->ctx_geo.begin() + first + count);
+        if (same_shape(a, b)) {
+            CK(cudaMemcpyAsync(c->boxes, src, sizeof(BoxDesc) * count, cudaMemcpyDeviceToDevice, c->stream));
+            for (int i = 0; i < count; ++i) c->boxes_h[i] = c->all_boxes_h[first + i];
+            c->bound_batch = k;
+            return SCOLA_OK;
+        }
+    }
+    BatchPlan bp;
+    plan_batch(c, c->tiling_geo, c->box0 + first, count, true, bp);
+    CK(c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize());
+    if (c->evolve_exec) {
+        CK(cudaGraphExecDestroy(c->evolve_exec));
+        c->evolve_exec = nullptr;
+    }
+    CS(put(c->boxes, bp.boxes));
+    CS(put(c->pchunks, bp.pch));
+    CS(put(c->tchunks, bp.tch));
+    CS(put(c->shchunks, bp.shch));
+    CS(put(c->zitems, bp.zit));
+    CS(put(c->citems, bp.cit));
+    CS(put(c->mchunks, bp.mch));
+    CS(put(c->ppchunks, bp.ppch));
+    CS(put(c->sbricks, bp.sbr));
+    if (c->use_tc) CS(put(c->tc_tiles, bp.tct));
+    c->nboxes = count;
+    c->boxes_h = bp.boxes;
+    c->n_pchunks = (int)bp.n_pch;
+    c->n_tchunks = (int)bp.n_tch;
+    c->n_shchunks = (int)bp.n_shch;
+    c->n_zitems = (int)bp.n_zit;
+    c->n_citems = (int)bp.n_cit;
+    c->n_mchunks = (int)bp.n_mch;
+    c->n_ppchunks = (int)bp.n_ppch;
+    c->n_sbricks = (int)bp.n_sbr;
+    c->pbeg = bp.pbeg;
+    c->shbeg = bp.shbeg;
+    c->zbeg = bp.zbeg;
+    c->cbeg = bp.cbeg;
+    c->mbeg = bp.mbeg;
+    c->sbbeg = bp.sbbeg;
+    c->dep_groups = bp.dep_groups;
+    c->tc_tile_beg = bp.tile_beg;
+    c->tc_tile_end = bp.tile_end;
+    for (size_t g = 0; g < c->tc_groups.size(); ++g) {
+        c->tc_groups[g].tiles = c->tc_tiles + bp.group_first[g];
+        c->tc_groups[g].ntiles = bp.group_ntiles[g];
+    }
+    c->P = bp.P;
+    c->M = bp.M;
+    c->MP = bp.MP;
+    c->SH = bp.SH;
+    c->bound_batch = k;
+    return SCOLA_OK;
+}
+
 scola_status build(scola_ctx *c, const std::vector<BoxGeom> &all_geo) {
     const scola_params &p = c->prm;
     // the boxes this context evolves: all, or the range [box_first, box_first + box_count)
-    const int first = p.box_count ? p.box_first : 0;
+    c->box0 = p.box_count ? p.box_first : 0;
     const int count = p.box_count ? p.box_count : (int)all_geo.size();
-    const std::vector<BoxGeom> geo(all_geo.begin() + first, all_geo.begin() + first + count);
+    c->tiling_geo = all_geo;
+    c->ctx_geo.assign(all_geo.begin() + c->box0, all_geo.begin() + c->box0 + count);
+    const std::vector<BoxGeom> &geo = c->ctx_geo;
+    c->nbox_all = count;
     c->Np = p.Np;
     c->Ntiles = p.Ntiles;
-    c->nboxes = (int)geo.size();
     c->N3 = (long long)p.Np * p.Np * p.Np;
     c->L = p.L;
     c->dq = p.L / p.Np;
     c->tt = build_time_table(p);
     c->pk_amp = bbks_amplitude(p.Om, p.h, p.ns, p.sigma8);
-    const int ntile = p.Np / p.Ntiles;
 
     // DST tables, one per distinct Ng
-    std::map<int, int> tbl_of;
-    for (const auto &g : geo) tbl_of[g.ng] = 0;
-    c->max_ng = tbl_of.rbegin()->first;
+    for (const auto &g : geo) c->tbl_of[g.ng] = 0;
+    c->max_ng = c->tbl_of.rbegin()->first;
     c->max_R = (c->max_ng + 31) / 32;
     const int LS = 32 * c->max_R;
     std::vector<float> arena;
-    for (auto &kv : tbl_of) {
+    for (auto &kv : c->tbl_of) {
         const int Ng = kv.first;
         DstTable T;
         T.Ng = Ng;
@@ -192,7 +442,27 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &all_geo) {
         T.lam_off = (long long)arena.size();
         kv.second = (int)c->tables_h.size();
         c->tables_h.push_back(T);
-        arena.resize(arena.size() + Ng);  // eigenvalues depend on dg: filled per box below
+        arena.resize(arena.size() + Ng);  // eigenvalues depend on dg: filled below
+    }
+    // boxes sharing an Ng share dg only if their Np,sCOLA also matches; the eigenvalue
+    // table is per Ng, so require a single dg per Ng
+    std::map<int, double> dg_of_ng;
+    for (const BoxGeom &g : geo) {
+        const double dg = g.nsc * c->dq / g.ng;
+        auto it = dg_of_ng.find(g.ng);
+        if (it == dg_of_ng.end()) {
+            dg_of_ng[g.ng] = dg;
+        } else if (std::fabs(it->second - dg) > 1e-12 * dg) {
+            set_error("boxes with equal Ng but different Np,sCOLA are not built");
+            return SCOLA_ERR_UNSUPPORTED;
+        }
+    }
+    for (auto &T : c->tables_h) {
+        const double dg = dg_of_ng[T.Ng];
+        for (int l = 0; l < T.Ng; ++l) {
+            const double s = std::sin(M_PI * (l + 1) / (2.0 * (T.Ng + 1)));
+            arena[T.lam_off + l] = (float)(-4.0 / (dg * dg) * s * s);
+        }
     }
     // LPT-grid sine tables: sin(pi n/N) and sin(2 pi n/N)/d with n the wrapped wavenumber
     c->sin_half_off = (long long)arena.size();
@@ -218,186 +488,51 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &all_geo) {
         const int n = i < p.Np / 2 ? i : i - p.Np;
         arena.push_back((float)(std::sin(2.0 * M_PI * n / p.Np) / c->dq));
     }
-
-    // boxes and work lists
-    std::vector<Chunk> pch, tch, shch, zit, cit, mch, ppch;
-    long long P = 0, M = 0, MP = 0, SH = 0;
-    std::map<int, double> dg_of_ng;
-    for (int b = 0; b < c->nboxes; ++b) {
-        c->pbeg.push_back((int)pch.size());
-        c->shbeg.push_back((int)shch.size());
-        c->zbeg.push_back((int)zit.size());
-        c->cbeg.push_back((int)cit.size());
-        c->mbeg.push_back((int)mch.size());
-        const BoxGeom &g = geo[b];
-        BoxDesc B;
-        std::memset(&B, 0, sizeof(B));
-        B.Nsc = g.nsc;
-        B.Ng = g.ng;
-        B.Nbuf = g.nbuf;
-        B.tbl = tbl_of[g.ng];
-        const int gb = first + b;                      // box id in the whole tiling
-        B.tx = gb / (p.Ntiles * p.Ntiles);
-        B.ty = (gb / p.Ntiles) % p.Ntiles;
-        B.tz = gb % p.Ntiles;
-        // interior meshes start at multiples of lcm(64, Ng): aligned, and a whole number of
-        // Ng-float rows from the buffer start (the tensor-core passes address them as rows)
-        {
-            long long q = 64;
-            while (q % g.ng) q += 64;
-            M = (M + q - 1) / q * q;
-        }
-        B.p_off = P;
-        B.m_off = M;
-        // padded boxes start 2 floats past a 64-float boundary: with Ng % 4 == 0 the interior
-        // cells of every padded row (index 2 .. Ng+1) then start 16-byte aligned
-        MP += 2;
-        B.pp_off = MP;
-        B.sh_off = SH;
-        const double Lsc = g.nsc * c->dq;
-        const double dg = Lsc / g.ng;
-        B.dq = (float)c->dq;
-        B.dg = (float)dg;
-        B.inv_dg = (float)(1.0 / dg);
-        B.q2u = (float)((double)g.ng / g.nsc);
-        B.nbar_inv = (float)std::pow((double)g.ng / g.nsc, 3);
-        B.dg_d = dg;
-        const int t3[3] = {B.tx, B.ty, B.tz};
-        for (int a = 0; a < 3; ++a) B.origin_d[a] = ((double)t3[a] * ntile - g.nbuf) * c->dq;
-        c->boxes_h.push_back(B);
-        const long long n = (long long)g.nsc * g.nsc * g.nsc;
-        const long long ng3 = (long long)g.ng * g.ng * g.ng;
-        const long long np3 = (long long)(g.ng + 4) * (g.ng + 4) * (g.ng + 4);
-        add_chunks(pch, b, n, kChunk);
-        add_chunks(tch, b, (long long)ntile * ntile * ntile, kChunk);
-        add_chunks(shch, b, np3 - ng3, kChunk);
-        add_chunks(mch, b, ng3, kChunk);
-        add_chunks(ppch, b, np3, kChunk);
-        const long long nz = ((long long)g.ng * g.ng + kTC - 1) / kTC;
-        for (long long t = 0; t < nz; ++t) zit.push_back({b, (int)t});
-        const long long nc = (long long)g.ng * ((g.ng + kTC - 1) / kTC);
-        for (long long t = 0; t < nc; ++t) cit.push_back({b, (int)t});
-        auto align64 = [](long long v) { return (v + 63) / 64 * 64; };
-        P += n;
-        M = align64(M + ng3);   // (the next box rounds up further)
-        MP = align64(MP + np3);
-        SH = align64(SH + np3 - ng3);
-        // boxes sharing an Ng share dg only if their Np,sCOLA also matches; the
-        // eigenvalue table is per Ng, so require a single dg per Ng
-        auto it = dg_of_ng.find(g.ng);
-        if (it == dg_of_ng.end()) {
-            dg_of_ng[g.ng] = dg;
-        } else if (std::fabs(it->second - dg) > 1e-12 * dg) {
-            set_error("boxes with equal Ng but different Np,sCOLA are not built");
-            return SCOLA_ERR_UNSUPPORTED;
-        }
-    }
-    c->pbeg.push_back((int)pch.size());
-    c->shbeg.push_back((int)shch.size());
-    c->zbeg.push_back((int)zit.size());
-    c->cbeg.push_back((int)cit.size());
-    c->mbeg.push_back((int)mch.size());
-    // deposit groups: consecutive boxes whose counts fit the L2-sized scratch (a box larger
-    // than the limit forms a group of its own)
-    long long dep_cells = 0;
-    for (int b = 0; b < c->nboxes; ++b) {
-        const long long end = c->boxes_h[b].m_off + (long long)geo[b].ng * geo[b].ng * geo[b].ng;
-        if (c->dep_groups.empty() || end - c->boxes_h[c->dep_groups.back()].m_off > kDepositGroupCells)
-            c->dep_groups.push_back(b);
-        dep_cells = std::max(dep_cells, end - c->boxes_h[c->dep_groups.back()].m_off);
-    }
-    c->dep_groups.push_back(c->nboxes);
-    for (auto &T : c->tables_h) {
-        const double dg = dg_of_ng[T.Ng];
-        for (int l = 0; l < T.Ng; ++l) {
-            const double s = std::sin(M_PI * (l + 1) / (2.0 * (T.Ng + 1)));
-            arena[T.lam_off + l] = (float)(-4.0 / (dg * dg) * s * s);
-        }
-    }
-    c->P = P;
-    c->M = M;
-    c->MP = MP;
-    c->SH = SH;
-    if (pch.size() > 0x7fffffff || zit.size() > 0x7fffffff || cit.size() > 0x7fffffff)
-        return invalid("problem too large for one launch");
-    c->n_pchunks = (int)pch.size();
-    c->n_tchunks = (int)tch.size();
-    c->n_shchunks = (int)shch.size();
-    c->n_zitems = (int)zit.size();
-    c->n_citems = (int)cit.size();
-    c->n_mchunks = (int)mch.size();
-    c->n_ppchunks = (int)ppch.size();
-    double r = 0;
-    for (const auto &g : all_geo) r += std::pow((double)g.nsc, 3);
-    c->r = r / (double)c->N3;
-    c->p = (double)all_geo.size() / c->r;
-
-    // tensor-core DST groups (one per distinct Ng): tiles and the FP32 sine matrix
+    // tensor-core DST groups (one per distinct Ng): the FP32 sine matrix
     bool all_tc = true;
-    for (auto &kv : tbl_of) all_tc = all_tc && tc_supported(kv.first);
+    for (auto &kv : c->tbl_of) all_tc = all_tc && tc_supported(kv.first);
     c->use_tc = (p.dst_variant == SCOLA_DST_TC_3XTF32) || (p.dst_variant == SCOLA_DST_TC_4XTF32) ||
                 (p.dst_variant == SCOLA_DST_AUTO && all_tc && kAutoUsesTensorCores);
     c->tc_lo_lo = p.dst_variant == SCOLA_DST_TC_4XTF32;
-    std::vector<Chunk> tct;
-    std::vector<int> box_tile_beg(c->nboxes, 0), box_tile_end(c->nboxes, 0);
     if (c->use_tc) {
-        for (auto &kv : tbl_of) {
+        for (auto &kv : c->tbl_of) {
             TcGroup G;
             G.Ng = kv.first;
             G.nstage = tc_plan_stages(G.Ng, G.Npad, G.nkc);
             G.lam_off = c->tables_h[kv.second].lam_off;
             G.s_off = (long long)arena.size();
+            G.tiles = nullptr;
+            G.ntiles = 0;
+            // direct: S_nk for n, k < Ng; folded: the even-row (output 2n) and then the
+            // odd-row (output 2n + 1) halves S_{2n+p, k} for n, k < Ng / 2
             const int Kp = 32 * G.nkc;
-            for (int n = 0; n < G.Npad; ++n)
-                for (int k = 0; k < Kp; ++k)
-                    arena.push_back(n < G.Ng && k < G.Ng
-                                        ? (float)std::sin(M_PI * (double)(n + 1) * (k + 1) / (G.Ng + 1))
-                                        : 0.0f);
-            const long long first = (long long)tct.size();
-            for (int b = 0; b < c->nboxes; ++b) {
-                if (geo[b].ng != G.Ng) continue;
-                const long long rows = (long long)G.Ng * G.Ng;
-                box_tile_beg[b] = (int)tct.size();
-                for (long long t = 0; t * kTcTileRows < rows; ++t) tct.push_back({b, (int)t});
-                box_tile_end[b] = (int)tct.size();
-            }
-            G.ntiles = (int)(tct.size() - first);
-            G.tiles = reinterpret_cast<Chunk *>(first);   // offset, rebased after upload
+            const bool fold = tc_folded(G.Ng);
+            const int Nk = fold ? G.Ng / 2 : G.Ng;
+            for (int par = 0; par < (fold ? 2 : 1); ++par)
+                for (int n = 0; n < G.Npad; ++n)
+                    for (int k = 0; k < Kp; ++k) {
+                        const int row = fold ? 2 * n + par : n;
+                        arena.push_back(n < Nk && k < Nk
+                                            ? (float)std::sin(M_PI * (double)(row + 1) * (k + 1) / (G.Ng + 1))
+                                            : 0.0f);
+                    }
             c->tc_groups.push_back(G);
         }
-        // per-box ranges (each box's tiles are contiguous within its group)
-        c->tc_tile_beg = box_tile_beg;
-        c->tc_tile_end = box_tile_end;
     }
+    double r = 0;
+    for (const auto &g : all_geo) r += std::pow((double)g.nsc, 3);
+    c->r = r / (double)c->N3;
+    c->p = (double)all_geo.size() / c->r;
 
     CK(cudaGetDevice(&c->device));
     CK(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
-    CS(upload(&c->boxes, c->boxes_h));
     CS(upload(&c->tables, c->tables_h));
     CS(upload(&c->table_arena, arena));
-    CS(upload(&c->pchunks, pch));
-    CS(upload(&c->tchunks, tch));
-    CS(upload(&c->shchunks, shch));
-    CS(upload(&c->zitems, zit));
-    CS(upload(&c->citems, cit));
-    CS(upload(&c->mchunks, mch));
-    CS(upload(&c->ppchunks, ppch));
-    if (c->use_tc) {
-        CS(upload(&c->tc_tiles, tct));
-        for (auto &G : c->tc_groups) G.tiles = c->tc_tiles + reinterpret_cast<long long>(G.tiles);
-        CK(init_tc_kernels());
-    }
+    if (c->use_tc) CK(init_tc_kernels());
     CS(dev_alloc(&c->dev_err, 1));
     CK(cudaMemset(c->dev_err, 0, sizeof(int)));
-    CS(dev_alloc(&c->part, 12 * P));
-    CS(dev_alloc(&c->dep_acc, dep_cells));
-    CK(cudaMemset(c->dep_acc, 0, sizeof(unsigned long long) * (size_t)dep_cells));
-    CS(dev_alloc(&c->work, M));
-    CS(dev_alloc(&c->work2, M));
-    CS(dev_alloc(&c->phi, MP));
-    CS(dev_alloc(&c->shell, SH));
-    CK(cudaMemset(c->phi, 0, sizeof(float) * MP));
 
+    // full-box LPT stage (allocated first: the batches take what device memory is left)
     const long long nc = (long long)p.Np * p.Np * (p.Np / 2 + 1);
     CS(dev_alloc(&c->ck, nc));
     CS(dev_alloc(&c->cp, nc));
@@ -408,24 +543,119 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &all_geo) {
     CS(dev_alloc(&c->psi1, 3 * c->N3));
     CS(dev_alloc(&c->psi2, 3 * c->N3));
     CS(dev_alloc(&c->dens_acc, c->N3));
-
     CF(cufftPlan3d(&c->plan_r2c, p.Np, p.Np, p.Np, CUFFT_R2C));
     CF(cufftPlan3d(&c->plan_c2r, p.Np, p.Np, p.Np, CUFFT_C2R));
     c->have_plans = true;
     CF(cufftSetStream(c->plan_r2c, c->stream));
     CF(cufftSetStream(c->plan_c2r, c->stream));
 
+    // streamed batches: as many consecutive boxes as params.batch_boxes allows, else as fit
+    // in the free device memory after a reserve for the caller's w, x, p and the host-copy
+    // buffers of scola_forward_host (2 x 28 bytes per particle) and 1 GiB; the batch count
+    // is then raised to a divisor of the box count where that keeps batches at least half
+    // full, so that all batches share one shape (and one captured graph)
+    int cap = p.batch_boxes > 0 ? p.batch_boxes : count;
+    if (p.batch_boxes == 0 && count > 1) {
+        size_t free_b = 0, total_b = 0;
+        CK(cudaMemGetInfo(&free_b, &total_b));
+        const long long reserve = 2 * 28 * c->N3 + (1LL << 30);
+        const long long avail = (long long)free_b - reserve;
+        long long used = 0;
+        int fit = 0;
+        while (fit < count) {
+            const long long add = batch_bytes({geo[fit]});
+            if (used + add > avail) break;
+            used += add;
+            ++fit;
+        }
+        if (fit == 0) {
+            set_error("not enough device memory for one sCOLA box");
+            return SCOLA_ERR_OOM;
+        }
+        cap = fit;
+    }
+    cap = std::min(cap, count);
+    int nbatch = (count + cap - 1) / cap;
+    for (int q = nbatch; q <= count && (count + q - 1) / q * 2 >= cap; ++q)
+        if (count % q == 0) {
+            nbatch = q;
+            break;
+        }
+    const int per = (count + nbatch - 1) / nbatch;
+    for (int f = 0; f < count; f += per) c->batch_first.push_back(f);
+    c->batch_first.push_back(count);
+    nbatch = (int)c->batch_first.size() - 1;
+
+    // every batch's layout (box descriptors kept; list lengths and arena sizes maxed)
+    long long P = 0, M = 0, MP = 0, SH = 0, NK = 0, dep = 0;
+    long long L_pch = 0, L_tch = 0, L_shch = 0, L_zit = 0, L_cit = 0, L_mch = 0, L_ppch = 0, L_sbr = 0, L_tct = 0;
+    int max_count = 0;
+    for (int k = 0; k < nbatch; ++k) {
+        BatchPlan bp;
+        const int f = c->batch_first[k], n = c->batch_first[k + 1] - f;
+        plan_batch(c, all_geo, c->box0 + f, n, false, bp);
+        c->all_boxes_h.insert(c->all_boxes_h.end(), bp.boxes.begin(), bp.boxes.end());
+        P = std::max(P, bp.P);
+        M = std::max(M, bp.M);
+        MP = std::max(MP, bp.MP);
+        SH = std::max(SH, bp.SH);
+        NK = std::max(NK, bp.NK);
+        dep = std::max(dep, bp.dep_cells);
+        L_pch = std::max(L_pch, bp.n_pch);
+        L_tch = std::max(L_tch, bp.n_tch);
+        L_shch = std::max(L_shch, bp.n_shch);
+        L_zit = std::max(L_zit, bp.n_zit);
+        L_cit = std::max(L_cit, bp.n_cit);
+        L_mch = std::max(L_mch, bp.n_mch);
+        L_ppch = std::max(L_ppch, bp.n_ppch);
+        L_sbr = std::max(L_sbr, bp.n_sbr);
+        L_tct = std::max(L_tct, bp.n_tct);
+        max_count = std::max(max_count, n);
+        c->P_all += bp.P;
+        for (const BoxGeom &g : bp.geo) c->M_all += (long long)g.ng * g.ng * g.ng;
+    }
+    const long long kInt = 0x7fffffff;
+    if (L_pch > kInt || L_zit > kInt || L_cit > kInt || L_mch > kInt || L_ppch > kInt || L_shch > kInt ||
+        NK > kInt || P > kInt * 4LL)
+        return invalid("batch too large for one launch (set batch_boxes)");
+    CS(upload(&c->all_boxes, c->all_boxes_h));
+    CS(dev_alloc(&c->boxes, max_count));
+    CS(dev_alloc(&c->pchunks, L_pch));
+    CS(dev_alloc(&c->tchunks, L_tch));
+    CS(dev_alloc(&c->shchunks, L_shch));
+    CS(dev_alloc(&c->zitems, L_zit));
+    CS(dev_alloc(&c->citems, L_cit));
+    CS(dev_alloc(&c->mchunks, L_mch));
+    CS(dev_alloc(&c->ppchunks, L_ppch));
+    CS(dev_alloc(&c->sbricks, L_sbr));
+    if (c->use_tc) CS(dev_alloc(&c->tc_tiles, L_tct));
+    CS(dev_alloc(&c->part, 12 * P));
+    CS(dev_alloc(&c->kcount, NK));
+    CS(dev_alloc(&c->koffs, NK));
+    CS(dev_alloc(&c->kcursor, NK));
+    CS(dev_alloc(&c->sentries, P));
+    CS(dev_alloc(&c->dep_acc, dep));
+    CK(cudaMemset(c->dep_acc, 0, sizeof(unsigned long long) * (size_t)std::max(dep, 1LL)));
+    CS(dev_alloc(&c->work, M));
+    CS(dev_alloc(&c->work2, M));
+    CS(dev_alloc(&c->phi, MP));
+    CS(dev_alloc(&c->shell, SH));
+    CK(cudaMemset(c->phi, 0, sizeof(float) * MP));
+    CS(bind_batch(c, 0, true));
+
     CK(init_pm_kernels(*c));
     CK(init_deposit_kernels());
     for (int i = 0; i < 4; ++i) CK(cudaEventCreate(&c->ev[i]));
     CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
 
-    c->stats.nboxes = c->nboxes;
-    c->stats.box_particles = P;
-    c->stats.mesh_cells = M;
+    c->stats.nboxes = count;
+    c->stats.box_particles = c->P_all;
+    c->stats.mesh_cells = c->M_all;
     c->stats.force_evaluations = p.nsteps + 1;
     c->stats.r = c->r;
     c->stats.p = c->p;
+    c->stats.batches = nbatch;
+    c->stats.batch_boxes = per;
     return SCOLA_OK;
 }
 
@@ -522,11 +752,12 @@ scola_status autotune_deposit(scola_ctx *c) {
     if (c->tuned) return SCOLA_OK;
     struct Cand {
         int form, threads;
+        bool split;
     };
-    const Cand all[3] = {{0, 256}, {0, 512}, {1, 512}};
-    int lo = 0, hi = 3;
-    if (c->prm.deposit_form == SCOLA_DEPOSIT_SORTED) hi = 2;
-    if (c->prm.deposit_form == SCOLA_DEPOSIT_ATOMIC) lo = 2;
+    const Cand all[4] = {{0, 256, false}, {0, 512, false}, {0, 256, true}, {1, 512, false}};
+    int lo = 0, hi = 4;
+    if (c->prm.deposit_form == SCOLA_DEPOSIT_SORTED) hi = 3;
+    if (c->prm.deposit_form == SCOLA_DEPOSIT_ATOMIC) lo = 3;
     const long long launches = c->launches;
     float best = -1.0f;
     int pick = lo;
@@ -539,7 +770,17 @@ scola_status autotune_deposit(scola_ctx *c) {
         for (int q = lo; q < hi; ++q) {
             c->deposit_form = all[q].form;
             c->deposit_threads = all[q].threads;
-            CK(launch_deposit(*c, c->part, c->P));          // warm-up
+            c->deposit_split = all[q].split;
+            const std::string which = std::string("deposit autotuner, ") +
+                                      (all[q].form == 0 ? "sorted form, " + std::to_string(all[q].threads) + " threads" +
+                                                              (all[q].split ? ", 32-bit halves" : "")
+                                                        : std::string("atomic form"));
+            cudaError_t e = launch_deposit(*c, c->part, c->P);      // warm-up
+            if (e == cudaSuccess) e = c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize();
+            if (e != cudaSuccess) {
+                set_error(which + ": " + cudaGetErrorString(e));
+                return SCOLA_ERR_CUDA;
+            }
             float ms = -1.0f;
             for (int rep = 0; rep < 3; ++rep) {
                 CK(cudaEventRecord(c->ev[3], c->stream));
@@ -559,8 +800,10 @@ scola_status autotune_deposit(scola_ctx *c) {
     }
     c->deposit_form = all[pick].form;
     c->deposit_threads = all[pick].threads;
+    c->deposit_split = all[pick].split;
     c->stats.deposit_form = all[pick].form == 0 ? SCOLA_DEPOSIT_SORTED : SCOLA_DEPOSIT_ATOMIC;
     c->stats.deposit_threads = all[pick].form == 0 ? all[pick].threads : 0;
+    c->stats.deposit_split = all[pick].split ? 1 : 0;
     c->launches = launches;
     c->tuned = true;
     return SCOLA_OK;
@@ -597,6 +840,10 @@ scola_status enqueue_evolution(scola_ctx *c) {
         if (!c->profiling) return cudaSuccess;
         return cudaEventRecordWithFlags(c->prof_ev[ei++], c->stream, cudaEventRecordExternal);
     };
+    // sorted deposit: each kick-drift counts the keys of the particles it moved, so the
+    // next deposit skips its own count pass (the counts are cleared once the brick pass has
+    // read them)
+    const bool fused = c->deposit_form == 0;
     for (int k = 0; k <= n; ++k) {
         if (c->checkpointing)
             CK(cudaMemcpyAsync(c->ckpt + (size_t)k * 3 * c->P, c->part, sizeof(float) * 3 * (size_t)c->P,
@@ -604,7 +851,8 @@ scola_status enqueue_evolution(scola_ctx *c) {
         CK(mark());
         CK(launch_pad(*c, (float)c->tt.D1[k]));
         CK(mark());
-        CK(launch_deposit(*c, c->part, c->P));
+        CK(launch_deposit(*c, c->part, c->P, nullptr, fused && k > 0));
+        if (fused && k < n) CK(clear_key_counts(*c));
         CK(mark());
         if (c->profiling) {
             for (int pass = 0; pass < 6; ++pass) {
@@ -614,7 +862,7 @@ scola_status enqueue_evolution(scola_ctx *c) {
         } else {
             CK(launch_poisson(*c));
         }
-        CK(launch_kick_drift(*c, kick_drift_coefficients(c->tt, k)));
+        CK(launch_kick_drift(*c, kick_drift_coefficients(c->tt, k), fused));
         CK(mark());
     }
     return SCOLA_OK;
@@ -648,6 +896,13 @@ scola_status ensure_graph(scola_ctx *c) {
     c->graph_kernels = c->launches - before;
     c->launches = before;
     return SCOLA_OK;
+}
+
+// The per-stage, inspection and adjoint entry points address one set of box arenas.
+scola_status need_one_batch(const scola_ctx *c) {
+    if (c->batch_first.size() == 2) return SCOLA_OK;
+    set_error("this call needs a context whose boxes form one batch (set batch_boxes to the box count)");
+    return SCOLA_ERR_UNSUPPORTED;
 }
 
 }  // namespace
@@ -738,7 +993,7 @@ void scola_destroy(scola_ctx *c) {
         cufftDestroy(c->plan_r2c);
         cufftDestroy(c->plan_c2r);
     }
-    void *ptrs[] = {c->boxes, c->tables, c->table_arena, c->pchunks, c->tchunks, c->shchunks,
+    void *ptrs[] = {c->boxes, c->all_boxes, c->tables, c->table_arena, c->pchunks, c->tchunks, c->shchunks,
                     c->zitems, c->citems, c->mchunks, c->ppchunks, c->tc_tiles, c->dev_err, c->ckpt,
                     c->adj, c->lamG, c->lam_phi_pad, c->adj_in, c->adj_out, c->lam_shell, c->lamPsi1,
                     c->lamPsi2, c->lam_phi1, c->lam_phi2, c->d2, c->lam_d2, c->part, c->dep_acc, c->kcount,
@@ -762,6 +1017,7 @@ int64_t scola_padded_cell_count(const scola_ctx *c) { return c ? c->MP : 0; }
 
 scola_status scola_box_offsets(const scola_ctx *c, int64_t *m_off, int64_t *pp_off, int32_t nboxes) {
     if (!c || !m_off || !pp_off) return invalid("NULL argument");
+    CS(need_one_batch(c));
     if (nboxes != c->nboxes) return invalid("nboxes differs from the context's box count");
     for (int b = 0; b < nboxes; ++b) {
         m_off[b] = c->boxes_h[b].m_off;
@@ -784,6 +1040,7 @@ scola_status scola_lpt_fields(scola_ctx *c, const float *w, float *delta, float 
 
 scola_status scola_setup_boxes(scola_ctx *c) {
     if (!c) return invalid("NULL context");
+    CS(need_one_batch(c));
     if (!c->lpt_done) {
         set_error("scola_setup_boxes needs scola_lpt_fields first");
         return SCOLA_ERR_STATE;
@@ -798,6 +1055,7 @@ scola_status scola_setup_boxes(scola_ctx *c) {
 scola_status scola_pm_force(scola_ctx *c, const float *s, double D1, float *F, float *delta,
                             float *phi) {
     if (!c || !s || !F) return invalid("NULL argument");
+    CS(need_one_batch(c));
     if (!c->setup_done) {
         set_error("scola_pm_force needs scola_setup_boxes first");
         return SCOLA_ERR_STATE;
@@ -814,6 +1072,7 @@ scola_status scola_pm_force(scola_ctx *c, const float *s, double D1, float *F, f
 
 scola_status scola_box_particle_ids(scola_ctx *c, int64_t *gid) {
     if (!c || !gid) return invalid("NULL argument");
+    CS(need_one_batch(c));
     CK(launch_box_ids(*c, gid));
     return SCOLA_OK;
 }
@@ -821,22 +1080,31 @@ scola_status scola_box_particle_ids(scola_ctx *c, int64_t *gid) {
 scola_status scola_forward(scola_ctx *c, const float *w, float *x, float *p) {
     if (!c || !w || !x || !p) return invalid("NULL argument");
     const long long before = c->launches;
+    long long graph_kernels = 0;
     CK(cudaEventRecord(c->ev[0], c->stream));
     CS(run_lpt(c, w, nullptr));
+    CS(bind_batch(c, 0));
     CS(autotune_deposit(c));   // first call only; its time counts in ms_lpt
     CK(cudaEventRecord(c->ev[1], c->stream));
-    CS(ensure_graph(c));
-    CK(cudaGraphLaunch(c->evolve_exec, c->stream));
-    CK(launch_scatter(*c, x, p));
+    // the batches in turn: C.1-C.3, the evolution graph and B.2 for each
+    const int nbatch = (int)c->batch_first.size() - 1;
+    for (int k = 0; k < nbatch; ++k) {
+        CS(bind_batch(c, k));
+        CS(ensure_graph(c));
+        CK(cudaGraphLaunch(c->evolve_exec, c->stream));
+        graph_kernels += c->graph_kernels;
+        CK(launch_scatter(*c, x, p));
+    }
     CK(cudaEventRecord(c->ev[2], c->stream));
     c->setup_done = true;
     c->have_forward = true;
-    c->stats.kernel_launches = (c->launches - before) + c->graph_kernels;
+    c->stats.kernel_launches = (c->launches - before) + graph_kernels;
     return SCOLA_OK;
 }
 
 scola_status scola_set_checkpointing(scola_ctx *c, int32_t enable) {
     if (!c) return invalid("NULL context");
+    CS(need_one_batch(c));
     const bool on = enable != 0;
     if (on && c->prm.batch_mode == SCOLA_BATCH_PER_TILE) {
         set_error("the adjoint runs on the batched form only");
@@ -987,9 +1255,14 @@ scola_status scola_device_status(scola_ctx *c) {
     CK(c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize());
     int flag = 0;
     CK(cudaMemcpy(&flag, c->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (flag) {
+    if (flag & 1) {
         set_error("a kernel's bounded wait expired; its results are invalid");
         return SCOLA_ERR_TIMEOUT;
+    }
+    if (flag & 2) {
+        set_error("sorted deposit: a fill pass found more particles for a key than its count pass "
+                  "(nothing was written past the slice); the densities are invalid");
+        return SCOLA_ERR_CUDA;
     }
     return SCOLA_OK;
 }
@@ -999,6 +1272,60 @@ int32_t scola_uses_tensor_cores(const scola_ctx *c) { return c && c->use_tc ? 1 
 scola_status scola_final_density(scola_ctx *c, const float *x, float *delta) {
     if (!c || !x || !delta) return invalid("NULL argument");
     CK(launch_final_density(*c, x, delta));
+    return SCOLA_OK;
+}
+
+scola_status scola_power_spectrum(scola_ctx *c, const float *delta, int32_t nbins, const double *edges,
+                                  double *k_mean, double *pk, int64_t *n_modes) {
+    if (!c || !delta || !edges || !k_mean || !pk || !n_modes) return invalid("NULL argument");
+    if (nbins < 1 || nbins > kMaxSpectrumBins) return invalid("nbins must be in [1, 2048]");
+    for (int b = 0; b < nbins; ++b)
+        if (!(edges[b] < edges[b + 1])) return invalid("bin edges must increase");
+    // the bin of each integer n^2 = |n|^2 of the wrapped wavenumbers, from k = kf sqrt(n^2)
+    // in FP64: bin b holds edges[b] <= k < edges[b + 1]
+    const int N = c->Np;
+    const long long nmax = 3LL * (N / 2) * (N / 2);
+    const double kf = 2.0 * M_PI / c->L;
+    std::vector<int> bin(nmax + 1);
+    for (long long n2 = 0; n2 <= nmax; ++n2) {
+        const double k = kf * std::sqrt((double)n2);
+        const int b = (int)(std::upper_bound(edges, edges + nbins + 1, k) - edges) - 1;
+        bin[n2] = (b >= 0 && b < nbins) ? b : -1;
+    }
+    const int rows = 2 * c->num_sms;
+    int *bin_d = nullptr;
+    double *scratch = nullptr, *out_d = nullptr;
+    scola_status st = upload(&bin_d, bin);
+    if (st == SCOLA_OK) st = dev_alloc(&scratch, 3LL * rows * nbins);
+    if (st == SCOLA_OK) st = dev_alloc(&out_d, 3LL * nbins);
+    std::vector<double> out(3 * (size_t)nbins);
+    cudaError_t e = cudaSuccess;
+    cufftResult fr = CUFFT_SUCCESS;
+    if (st == SCOLA_OK) {
+        // transform a copy (the grid scratch g[0]): the caller's field stays untouched
+        e = cudaMemcpyAsync(c->g[0], delta, sizeof(float) * (size_t)c->N3, cudaMemcpyDeviceToDevice, c->stream);
+        if (e == cudaSuccess) fr = cufftExecR2C(c->plan_r2c, c->g[0], c->ck);
+        if (e == cudaSuccess && fr == CUFFT_SUCCESS) e = launch_spectrum(*c, c->ck, bin_d, nbins, scratch, rows, out_d);
+        if (e == cudaSuccess && fr == CUFFT_SUCCESS)
+            e = cudaMemcpyAsync(out.data(), out_d, sizeof(double) * out.size(), cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess && fr == CUFFT_SUCCESS) e = cudaStreamSynchronize(c->stream);
+    }
+    cudaFree(bin_d);
+    cudaFree(scratch);
+    cudaFree(out_d);
+    if (st != SCOLA_OK) return st;
+    if (fr != CUFFT_SUCCESS) {
+        set_error("cufftExecR2C: cuFFT error " + std::to_string((int)fr));
+        return SCOLA_ERR_CUDA;
+    }
+    CK(e);
+    const double norm = std::pow(c->L, 3) / std::pow((double)N, 6);
+    for (int b = 0; b < nbins; ++b) {
+        const double cnt = out[2 * nbins + b];
+        n_modes[b] = (int64_t)cnt;
+        k_mean[b] = cnt > 0 ? kf * out[nbins + b] / cnt : std::nan("");
+        pk[b] = cnt > 0 ? norm * out[b] / cnt : std::nan("");
+    }
     return SCOLA_OK;
 }
 

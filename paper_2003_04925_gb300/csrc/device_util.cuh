@@ -53,6 +53,46 @@ __device__ __forceinline__ void decode_local(int local, int n, int &i, int &j, i
     i = t / n;
 }
 
+// Sorted deposit: the interior mesh of a box is cut into bricks of kBrick^3 cells.
+constexpr int kBrick = 16;
+
+struct SortEntry {
+    int key;          // box-local key ((bx nbe + by) nbe + bz) 8 + class, or -1 (no weight inside)
+    float4 e;         // f_x, f_y, f_z, packed i0 (+2, 10 bits per axis)
+};
+
+// The sorted deposit's key and entry of a particle at box-local lattice index b with
+// displacement s: the clamped mesh coordinate u (as in the CIC deposit) has integer part
+// i0 and fractions f; the key is the brick of the upper corner i0 + 1 with a 3-bit class
+// whose bit a says that the lower corner lies in the brick below along axis a.  The count
+// pass (in the kick-drift of the previous step, or its own kernel) and the fill pass
+// compute it with this one function from the same FP32 values.
+__device__ __forceinline__ SortEntry brick_entry(const BoxDesc &B, const float (&s)[3], const int (&b)[3]) {
+    const int Ng = B.Ng, nbe = B.nbe;
+    int i0[3];
+    float f[3];
+    bool inside = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float u = fmaf(s[a], B.inv_dg, fmaf((float)b[a], B.q2u, 0.5f * B.q2u - 0.5f));
+        u = fminf(fmaxf(u, -2.0f), (float)Ng + 1.0f);
+        const float fl = floorf(u);
+        i0[a] = (int)fl;
+        f[a] = u - fl;
+        inside = inside && i0[a] >= -1 && i0[a] < Ng;
+    }
+    SortEntry r;
+    r.key = -1;
+    r.e = make_float4(f[0], f[1], f[2],
+                      __int_as_float((i0[0] + 2) | ((i0[1] + 2) << 10) | ((i0[2] + 2) << 20)));
+    if (inside) {
+        const int cls = (((i0[0] + 1) & (kBrick - 1)) == 0 ? 1 : 0) | (((i0[1] + 1) & (kBrick - 1)) == 0 ? 2 : 0) |
+                        (((i0[2] + 1) & (kBrick - 1)) == 0 ? 4 : 0);
+        r.key = ((((i0[0] + 1) >> 4) * nbe + ((i0[1] + 1) >> 4)) * nbe + ((i0[2] + 1) >> 4)) * 8 + cls;
+    }
+    return r;
+}
+
 // 2^-32 fixed-point value of a CIC weight w in [0, 1]: round-to-nearest of w 2^32 (the
 // same integer as a direct float -> uint64 conversion), computed with 32-bit conversions
 // only (64-bit integer conversions run on the FP64 pipe, which is narrow on this GPU).

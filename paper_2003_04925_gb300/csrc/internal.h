@@ -16,6 +16,7 @@
 #include <cufft.h>
 #include <stdint.h>
 
+#include <map>
 #include <string>
 #include <vector>
 
@@ -97,12 +98,22 @@ struct Ctx {
     double L = 0, dq = 0, r = 0, p = 0, pk_amp = 0;
     TimeTable tt;
 
-    std::vector<BoxDesc> boxes_h;
+    std::vector<BoxDesc> boxes_h;                     // the bound batch's boxes
     std::vector<DstTable> tables_h;
+    std::map<int, int> tbl_of;                        // Ng -> index of its DST table
     long long P = 0, M = 0, MP = 0, SH = 0;
     int max_ng = 0, max_R = 0;
 
-    // device
+    // streamed batches: the context's boxes (tiling ids [box0, box0 + nbox_all)) are evolved
+    // in batches of consecutive boxes; the arenas and work lists hold one batch at a time
+    int box0 = 0, nbox_all = 0;
+    std::vector<int> batch_first;                     // first box of each batch (context index), then nbox_all
+    int bound_batch = -1;                             // the batch the kernels see
+    std::vector<BoxDesc> all_boxes_h;                 // every box, laid out within its own batch
+    BoxDesc *all_boxes = nullptr;
+    long long P_all = 0, M_all = 0;                   // particles and interior cells of all boxes
+
+    // device (the bound batch)
     BoxDesc *boxes = nullptr;
     DstTable *tables = nullptr;
     float *table_arena = nullptr;
@@ -131,6 +142,7 @@ struct Ctx {
     // entries (one per box particle at most); the real bricks (box, brick in box)
     int deposit_form = 0;                             // 0: sorted bricks, 1: L2 fixed-point atomics
     int deposit_threads = 512;                        // threads per brick CTA of the sorted form
+    bool deposit_split = false;                       // sorted form: 32-bit halves of the counts
     bool tuned = false;                               // the autotuner has picked the forms above
     int *kcount = nullptr, *koffs = nullptr, *kcursor = nullptr;
     float4 *sentries = nullptr;
@@ -173,13 +185,18 @@ cudaError_t launch_gradient(Ctx &c, const float *phi, float *psi);
 cudaError_t launch_box_init(Ctx &c);
 cudaError_t launch_shell(Ctx &c);
 cudaError_t launch_pad(Ctx &c, float D1);
-cudaError_t launch_deposit(Ctx &c, const float *s, long long stride, float *delta_out = nullptr);
+// counted: the key counts of s were made by the kick-drift that moved the particles (sorted
+// form, batched graph); otherwise the deposit counts them itself
+cudaError_t launch_deposit(Ctx &c, const float *s, long long stride, float *delta_out = nullptr,
+                           bool counted = false);
 cudaError_t launch_deposit_atomic(Ctx &c, const float *s, long long stride, float *delta_out);
-cudaError_t launch_deposit_sorted(Ctx &c, const float *s, long long stride, float *delta_out);
+cudaError_t launch_deposit_sorted(Ctx &c, const float *s, long long stride, float *delta_out, bool counted);
+cudaError_t clear_key_counts(Ctx &c);
 cudaError_t init_pm_kernels(Ctx &c);
 cudaError_t init_deposit_kernels();
 int tc_plan_stages(int Ng, int &Npad, int &nkc);
 bool tc_supported(int Ng);
+bool tc_folded(int Ng);          // Ng > 128: the mirror-symmetric half-size form
 cudaError_t init_tc_kernels();
 cudaError_t launch_poisson_tc(Ctx &c);
 cudaError_t launch_poisson_tc_pass(Ctx &c, int pass);
@@ -190,10 +207,17 @@ cudaError_t launch_poisson_buffers(Ctx &c, const float *in, float *w1, float *w2
 cudaError_t launch_poisson(Ctx &c);
 cudaError_t launch_poisson_pass(Ctx &c, int pass);
 cudaError_t launch_interp(Ctx &c, const float *s, long long stride, float *F);
-cudaError_t launch_kick_drift(Ctx &c, const KickDrift &kd);
+// count_keys: also count the sorted deposit's keys of the drifted particles (into cleared
+// counts) for the next force evaluation
+cudaError_t launch_kick_drift(Ctx &c, const KickDrift &kd, bool count_keys = false);
 cudaError_t launch_scatter(Ctx &c, float *x, float *p);
 cudaError_t launch_box_ids(Ctx &c, int64_t *gid);
 cudaError_t launch_final_density(Ctx &c, const float *x, float *delta);
+// Binned |delta_k|^2 sums of a half spectrum: out = [psum, sqrt(n^2) sum, count] x nbins;
+// scratch holds 3 x rows x nbins doubles; rows = CTAs of the partial pass.
+cudaError_t launch_spectrum(Ctx &c, const cufftComplex *dk, const int *bin_of_n2, int nbins, double *scratch,
+                            int rows, double *out);
+constexpr int kMaxSpectrumBins = 2048;
 
 cudaError_t launch_adj_colour(Ctx &c, const cufftComplex *in, cufftComplex *out);
 cudaError_t launch_adj_final(Ctx &c, const float *lam_delta, float *adj);
@@ -210,5 +234,8 @@ cudaError_t launch_adj_source(Ctx &c, const float *lamS, const float *d2, float 
 cudaError_t launch_spec_d2_accumulate(Ctx &c, const cufftComplex *in, cufftComplex *acc, int i, int j);
 
 void set_error(const std::string &msg);
+// Records "<step>: <CUDA error string>" as the context's error detail and returns e; the
+// caller's own report then keeps this detail (see CK in capi.cu).
+cudaError_t step_error(const char *step, cudaError_t e);
 
 }  // namespace scola

@@ -154,29 +154,30 @@ cudaError_t launch_deposit_atomic(Ctx &c, const float *s, long long stride, floa
         const Chunk *mch = one ? c.mchunks : c.mchunks + c.mbeg[b0];
         const int nmch = one ? c.n_mchunks : c.mbeg[b1] - c.mbeg[b0];
         const long long base = c.boxes_h[b0].m_off;
+        cudaError_t e;
         if (npch > 0) {
             k_deposit<<<npch, kChunk, 0, c.stream>>>(c.boxes, pch, s, stride, c.dep_acc, base);
             ++c.launches;
+            if ((e = cudaGetLastError()) != cudaSuccess) return step_error("atomic deposit: deposit launch", e);
         }
         if (nmch > 0) {
             k_density_source<<<(nmch + kSourceChunks - 1) / kSourceChunks, 64 * kSourceChunks, 0, c.stream>>>(
                 c.boxes, mch, nmch, c.dep_acc, base, c.phi, c.work2, delta_out);
             ++c.launches;
+            if ((e = cudaGetLastError()) != cudaSuccess) return step_error("atomic deposit: source launch", e);
         }
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
         // clear the counts this group used (they stay in L2 for the next group)
         const BoxDesc &last = c.boxes_h[b1 - 1];
         const long long used = last.m_off + (long long)last.Ng * last.Ng * last.Ng - base;
         e = cudaMemsetAsync(c.dep_acc, 0, sizeof(unsigned long long) * (size_t)used, c.stream);
-        if (e != cudaSuccess) return e;
+        if (e != cudaSuccess) return step_error("atomic deposit: clearing the scratch", e);
     }
     return cudaSuccess;
 }
 
 // The deposit in the form the context selected (both give bit-identical delta').
-cudaError_t launch_deposit(Ctx &c, const float *s, long long stride, float *delta_out) {
-    return c.deposit_form == 0 ? launch_deposit_sorted(c, s, stride, delta_out)
+cudaError_t launch_deposit(Ctx &c, const float *s, long long stride, float *delta_out, bool counted) {
+    return c.deposit_form == 0 ? launch_deposit_sorted(c, s, stride, delta_out, counted)
                                : launch_deposit_atomic(c, s, stride, delta_out);
 }
 

@@ -25,7 +25,6 @@ namespace scola {
 
 namespace {
 
-constexpr int kBrick = 16;
 constexpr int kBrickCells = kBrick * kBrick * kBrick;
 
 // The (neighbour offset d, class c) pairs with (c & d) == d: the slices a brick reads.
@@ -33,47 +32,24 @@ constexpr int kSegments = 27;
 __constant__ int kSegD[kSegments] = {0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 2, 2, 2, 2, 3, 3, 4, 4, 4, 4, 5, 5, 6, 6, 7};
 __constant__ int kSegC[kSegments] = {0, 1, 2, 3, 4, 5, 6, 7, 1, 3, 5, 7, 2, 3, 6, 7, 3, 7, 4, 5, 6, 7, 5, 7, 6, 7, 7};
 
-struct SortEntry {
-    int key;          // box-local key ((bx nbe + by) nbe + bz) 8 + class, or -1 (no weight inside)
-    float4 e;         // f_x, f_y, f_z, packed i0 (+2, 10 bits per axis)
-};
-
 __device__ __forceinline__ SortEntry sort_entry(const BoxDesc &B, const float *__restrict__ s, long long stride,
                                                 int local) {
-    const int Nsc = B.Nsc, Ng = B.Ng, nbe = B.nbe;
     int b[3];
-    decode_local(local, Nsc, b[0], b[1], b[2]);
+    decode_local(local, B.Nsc, b[0], b[1], b[2]);
     const long long gi = B.p_off + local;
-    int i0[3];
-    float f[3];
-    bool inside = true;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        float u = fmaf(__ldg(s + a * stride + gi), B.inv_dg, fmaf((float)b[a], B.q2u, 0.5f * B.q2u - 0.5f));
-        u = fminf(fmaxf(u, -2.0f), (float)Ng + 1.0f);
-        const float fl = floorf(u);
-        i0[a] = (int)fl;
-        f[a] = u - fl;
-        inside = inside && i0[a] >= -1 && i0[a] < Ng;
-    }
-    SortEntry r;
-    r.key = -1;
-    r.e = make_float4(f[0], f[1], f[2],
-                      __int_as_float((i0[0] + 2) | ((i0[1] + 2) << 10) | ((i0[2] + 2) << 20)));
-    if (inside) {
-        const int cls = (((i0[0] + 1) & (kBrick - 1)) == 0 ? 1 : 0) | (((i0[1] + 1) & (kBrick - 1)) == 0 ? 2 : 0) |
-                        (((i0[2] + 1) & (kBrick - 1)) == 0 ? 4 : 0);
-        r.key = ((((i0[0] + 1) >> 4) * nbe + ((i0[1] + 1) >> 4)) * nbe + ((i0[2] + 1) >> 4)) * 8 + cls;
-    }
-    return r;
+    const float sv[3] = {__ldg(s + gi), __ldg(s + stride + gi), __ldg(s + 2 * stride + gi)};
+    return brick_entry(B, sv, b);
 }
 
 // FILL = false: add each key's entries of this chunk to the counts.  FILL = true: reserve
 // slots through the cursors and write the entries.  One atomic per distinct key per warp.
+// A reservation past the slots the count pass gave a key (offs + cnt) would mean that the
+// two passes disagreed on a key: it is recorded in err (bit 2) and nothing is written.
 template <bool FILL>
 __global__ void __launch_bounds__(kChunk)
 k_sort_bin(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks, const float *__restrict__ s,
-           long long stride, int *__restrict__ ctr, float4 *__restrict__ entries) {
+           long long stride, int *__restrict__ ctr, float4 *__restrict__ entries, const int *__restrict__ cnt,
+           const int *__restrict__ offs, int *__restrict__ err) {
     const Chunk ch = chunks[blockIdx.x];
     const BoxDesc &B = boxes[ch.box];
     const int local = ch.start + threadIdx.x;
@@ -87,10 +63,15 @@ k_sort_bin(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks, 
         if (se.key >= 0 && lane == leader) atomicAdd(kc + se.key, __popc(peers));
         return;
     }
-    int base = 0;
-    if (se.key >= 0 && lane == leader) base = atomicAdd(kc + se.key, __popc(peers));
+    int base = 0, ok = 1;
+    if (se.key >= 0 && lane == leader) {
+        base = atomicAdd(kc + se.key, __popc(peers));
+        ok = base + __popc(peers) <= offs[B.key_off + se.key] + cnt[B.key_off + se.key];
+        if (!ok) atomicOr(err, 2);
+    }
     base = __shfl_sync(0xffffffffu, base, leader);
-    if (se.key >= 0) entries[B.p_off + base + __popc(peers & ((1u << lane) - 1u))] = se.e;
+    ok = __shfl_sync(0xffffffffu, ok, leader);
+    if (se.key >= 0 && ok) entries[B.p_off + base + __popc(peers & ((1u << lane) - 1u))] = se.e;
 }
 
 // Exclusive prefix sums of one box's key counts (one CTA of 1024 threads per box).
@@ -146,8 +127,22 @@ __device__ __forceinline__ void store4(float *p, const float (&v)[4], bool vec, 
         if (e < left) p[e] = v[e];
 }
 
+// Adds fixed-point weight f (at most 2^32) to a count kept as two 32-bit halves: a 32-bit
+// add to the low half, and a carry into the high half when it wraps (the same integer sum
+// as a 64-bit add, in 32-bit shared-memory atomics).
+__device__ __forceinline__ void add_split(unsigned *lo, unsigned *hi, int c, unsigned long long f) {
+    if (f >> 32) {                      // a weight of exactly 1
+        atomicAdd(hi + c, 1u);
+        return;
+    }
+    const unsigned v = (unsigned)f;
+    const unsigned old = atomicAdd(lo + c, v);
+    if (old > 0xffffffffu - v) atomicAdd(hi + c, 1u);
+}
+
 // One CTA of T threads per real brick (item.start = brick index in the box, nb^3 of them).
-template <int kBrickThreads>
+// kSplit: the counts as 32-bit low and high halves (32-bit atomics), else 64-bit atomics.
+template <int kBrickThreads, bool kSplit>
 __global__ void __launch_bounds__(kBrickThreads, kBrickThreads == 256 ? 5 : 3)
 k_sort_brick(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ items, const int *__restrict__ cnt,
              const int *__restrict__ offs, const float4 *__restrict__ entries, const float *__restrict__ phi_pad,
@@ -207,7 +202,14 @@ k_sort_brick(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ items,
                 for (int ez = 0; ez < 2; ++ez) {
                     const int cz = lz + ez;
                     if ((unsigned)cz >= (unsigned)kBrick || z0 + cz >= Ng) continue;
-                    atomicAdd(&acc[(cx * kBrick + cy) * kBrick + cz], weight_to_fixed(wxy * (ez ? v.z : 1.0f - v.z)));
+                    const unsigned long long f = weight_to_fixed(wxy * (ez ? v.z : 1.0f - v.z));
+                    const int cell = (cx * kBrick + cy) * kBrick + cz;
+                    if (kSplit) {
+                        unsigned *lo = reinterpret_cast<unsigned *>(acc);
+                        add_split(lo, lo + kBrickCells, cell, f);
+                    } else {
+                        atomicAdd(&acc[cell], f);
+                    }
                 }
             }
         }
@@ -220,8 +222,18 @@ k_sort_brick(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ items,
         const int lz = (q % (kBrick / 4)) * 4, ly = (q / (kBrick / 4)) % kBrick, lx = q / (kBrick * kBrick / 4);
         const int i = x0 + lx, j = y0 + ly, k = z0 + lz;
         if (i >= Ng || j >= Ng || k >= Ng) continue;
-        const ulonglong2 *a = reinterpret_cast<const ulonglong2 *>(acc + (lx * kBrick + ly) * kBrick + lz);
-        const ulonglong2 a01 = a[0], a23 = a[1];
+        ulonglong2 a01, a23;
+        if (kSplit) {
+            const unsigned *lo = reinterpret_cast<const unsigned *>(acc) + (lx * kBrick + ly) * kBrick + lz;
+            const uint4 l = *reinterpret_cast<const uint4 *>(lo);
+            const uint4 h = *reinterpret_cast<const uint4 *>(lo + kBrickCells);
+            a01 = make_ulonglong2(((unsigned long long)h.x << 32) | l.x, ((unsigned long long)h.y << 32) | l.y);
+            a23 = make_ulonglong2(((unsigned long long)h.z << 32) | l.z, ((unsigned long long)h.w << 32) | l.w);
+        } else {
+            const ulonglong2 *a = reinterpret_cast<const ulonglong2 *>(acc + (lx * kBrick + ly) * kBrick + lz);
+            a01 = a[0];
+            a23 = a[1];
+        }
         float v[4];
         v[0] = fixed_to_float(a01.x) * sc - 1.0f;
         v[1] = fixed_to_float(a01.y) * sc - 1.0f;
@@ -254,15 +266,18 @@ k_sort_brick(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ items,
 
 // Shared memory is the brick kernel's occupancy limit: ask for the largest carveout.
 cudaError_t init_deposit_kernels() {
-    cudaError_t e = cudaFuncSetAttribute(k_sort_brick<256>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                         cudaSharedmemCarveoutMaxShared);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_sort_brick<512>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                cudaSharedmemCarveoutMaxShared);
+    const void *fns[] = {(const void *)k_sort_brick<256, false>, (const void *)k_sort_brick<512, false>,
+                         (const void *)k_sort_brick<256, true>, (const void *)k_sort_brick<512, true>};
+    for (const void *f : fns) {
+        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                             cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
-cudaError_t launch_deposit_sorted(Ctx &c, const float *s, long long stride, float *delta_out) {
-    // the boxes of the current view: all, or one in the per-tile form
+// Zeroes the key counts of the boxes of the current view.
+cudaError_t clear_key_counts(Ctx &c) {
     const int box0 = c.view_box >= 0 ? c.view_box : 0;
     const int nbox = c.view_box >= 0 ? 1 : c.nboxes;
     const BoxDesc &first = c.boxes_h[box0];
@@ -270,18 +285,42 @@ cudaError_t launch_deposit_sorted(Ctx &c, const float *s, long long stride, floa
     const long long k0 = first.key_off;
     const long long nk = last.key_off + 8LL * last.nbe * last.nbe * last.nbe - k0;
     cudaError_t e = cudaMemsetAsync(c.kcount + k0, 0, sizeof(int) * (size_t)nk, c.stream);
-    if (e != cudaSuccess) return e;
-    k_sort_bin<false><<<c.n_pchunks, kChunk, 0, c.stream>>>(c.boxes, c.pchunks, s, stride, c.kcount, nullptr);
+    return e == cudaSuccess ? e : step_error("sorted deposit: clearing the key counts", e);
+}
+
+cudaError_t launch_deposit_sorted(Ctx &c, const float *s, long long stride, float *delta_out, bool counted) {
+    // the boxes of the current view: all, or one in the per-tile form
+    const int box0 = c.view_box >= 0 ? c.view_box : 0;
+    const int nbox = c.view_box >= 0 ? 1 : c.nboxes;
+    // each step's error is reported with the step's name; `counted`: the kick-drift that
+    // moved these particles has already counted their keys (into cleared counts)
+    cudaError_t e;
+    if (!counted) {
+        if ((e = clear_key_counts(c)) != cudaSuccess) return e;
+        k_sort_bin<false><<<c.n_pchunks, kChunk, 0, c.stream>>>(c.boxes, c.pchunks, s, stride, c.kcount, nullptr,
+                                                                nullptr, nullptr, nullptr);
+        if ((e = cudaGetLastError()) != cudaSuccess) return step_error("sorted deposit: count launch", e);
+        ++c.launches;
+    }
     k_sort_scan<<<nbox, 1024, 0, c.stream>>>(c.boxes, box0, c.kcount, c.koffs, c.kcursor);
-    k_sort_bin<true><<<c.n_pchunks, kChunk, 0, c.stream>>>(c.boxes, c.pchunks, s, stride, c.kcursor, c.sentries);
-    if (c.deposit_threads == 256)
-        k_sort_brick<256><<<c.n_sbricks, 256, 0, c.stream>>>(c.boxes, c.sbricks, c.kcount, c.koffs, c.sentries,
-                                                               c.phi, c.work2, delta_out);
-    else
-        k_sort_brick<512><<<c.n_sbricks, 512, 0, c.stream>>>(c.boxes, c.sbricks, c.kcount, c.koffs, c.sentries,
-                                                               c.phi, c.work2, delta_out);
-    c.launches += 4;
-    return cudaGetLastError();
+    if ((e = cudaGetLastError()) != cudaSuccess) return step_error("sorted deposit: scan launch", e);
+    k_sort_bin<true><<<c.n_pchunks, kChunk, 0, c.stream>>>(c.boxes, c.pchunks, s, stride, c.kcursor, c.sentries,
+                                                           c.kcount, c.koffs, c.dev_err);
+    if ((e = cudaGetLastError()) != cudaSuccess) return step_error("sorted deposit: fill launch", e);
+#define SCOLA_BRICK(T, SPLIT)                                                                             \
+    k_sort_brick<T, SPLIT><<<c.n_sbricks, T, 0, c.stream>>>(c.boxes, c.sbricks, c.kcount, c.koffs, c.sentries, \
+                                                            c.phi, c.work2, delta_out)
+    if (c.deposit_threads == 256) {
+        if (c.deposit_split) SCOLA_BRICK(256, true);
+        else SCOLA_BRICK(256, false);
+    } else {
+        if (c.deposit_split) SCOLA_BRICK(512, true);
+        else SCOLA_BRICK(512, false);
+    }
+#undef SCOLA_BRICK
+    if ((e = cudaGetLastError()) != cudaSuccess) return step_error("sorted deposit: brick launch", e);
+    c.launches += 3;
+    return cudaSuccess;
 }
 
 }  // namespace scola

@@ -18,19 +18,28 @@
 //   y-    W4[k'][l][m]  (k',l) m    W5[j'][k'][l]
 //   x-    W5[j'][k'][l] (j',k') l   Phi[i'+2][j'+2][k'+2]   * 8 / (Ng+1)^3
 //
-// Precision: FP32 operands split as a = a_hi + a_lo with a_hi the value with
-// its 13 low mantissa bits cleared (exact in TF32); D accumulates
-// s_hi x_hi + s_hi x_lo + s_lo x_hi in FP32 in tensor memory (3xTF32), and
-// s_lo x_lo as well in the four-product form.  A single TF32 product gives
-// position errors of ~0.1 PM cell over a run, the three-term form stays near
-// the FP32 level.
+// Precision: FP32 operands split as a = a_hi + a_lo, a_hi the nearest TF32 value and
+// a_lo the nearest TF32 value of the remainder (together ~24 significant bits); D
+// accumulates s_hi x_hi + s_hi x_lo + s_lo x_hi in FP32 in tensor memory (3xTF32), and
+// s_lo x_lo as well in the four-product form.  A single TF32 product gives position
+// errors of ~0.1 PM cell over a run, the three-term form stays near the FP32 level.
+//
+// Meshes with Ng > 128 (Ng % 32 == 0) use the mirror symmetry of the sine matrix,
+// S_{k, Ng-1-n} = (-1)^k S_kn: the even outputs are the half-size product of the even rows
+// of S with u_n = x_n + x_{Ng-1-n}, the odd outputs that of the odd rows with
+// v_n = x_n - x_{Ng-1-n} (n < Ng/2).  Each work item is one parity of one tile: the CTA
+// holds that parity's Ng/2 x Ng/2 matrix (its M rows and K both Ng/2 <= 128), loads
+// every 16-column chunk of the rows together with its mirror chunk, and its converters
+// form u or v and split it into hi and lo parts in place of the two loaded chunks.  Half
+// the products of the direct form, and the two
+// items of a tile run on neighbouring CTAs at the same time, so the second read of the
+// rows comes from L2.
 //
 // One persistent CTA per SM, 18 warps:
 //   warps 0-7  epilogue: tcgen05.ld of the accumulator (warp w reads TMEM lanes
 //              32(w%4)..+31 = output columns, half of the 256 rows), a 32 x 32
 //              transpose through shared memory, scaling, coalesced global stores
-//   warps 8-15 converters: the lo parts of each landed stage (the raw FP32 values
-//              serve as the hi operand)
+//   warps 8-15 converters: split each landed stage in place into its hi and lo parts
 //   warp 16    TMEM allocation; lane 0 issues tcgen05.mma and tcgen05.commit
 //   warp 17    lane 0 issues the tensor copies (TMA) of 256-row x 16-column chunks of
 //              the data into a ring of MMA stages (64-byte-swizzled K-major)
@@ -83,9 +92,10 @@ struct TcArgs {
     CUtensorMap in_map;          // the input as rows of Ng floats (64-byte swizzle boxes 16 x 256)
     const BoxDesc *boxes;
     const Chunk *tiles;          // (box, tile-in-box)
-    int ntiles;
+    int ntiles;                  // work items: tiles, or 2 x tiles (one per parity) when folded
     int Ng, Npad, nkc, nstage;   // uniform Ng for the launch; nkc sine chunks; nstage data stages
-    const float *S;              // FP32 sine matrix, Npad x (nkc*32), zero padded
+    const float *S;              // FP32 sine matrix, Npad x (nkc*32), zero padded (folded: the
+                                 // even-row and then the odd-row half matrices)
     const float *lam;            // Dirichlet eigenvalues, Ng
     const float *in;
     float *out;
@@ -237,18 +247,27 @@ __device__ __forceinline__ uint32_t sw64_offset(int r, int k) {
     return (uint32_t)(r * 64 + ((((k >> 2) ^ (r >> 1)) & 3) << 4) + (k & 3) * 4);
 }
 
-__device__ __forceinline__ float tf32_hi(float x) {
-    return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+// x rounded to the nearest TF32 value (10 fraction bits; ties away from zero): add half a
+// TF32 unit to the magnitude bits and clear the 13 low bits.  For the split a = hi + lo
+// with hi = tf32_rn(a) and lo = tf32_rn(a - hi), |a - hi - lo| <= 2^-24 |a|, so the three
+// products carry about the FP32 input precision (truncated parts keep ~22 bits).
+__device__ __forceinline__ float tf32_rn(float x) {
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
-template <int PASS>
+
+template <int PASS, bool FOLD>
 __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(const __grid_constant__ TcArgs A) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-aligned (in the shared window) base for the swizzled operand tiles
     unsigned char *base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     const int Ng = A.Ng, nka = A.nkc, NST = A.nstage;
-    const int nkb = (Ng + kKB - 1) / kKB;                 // data chunks per tile
-    const uint32_t sch = (uint32_t)((Ng + 7) / 8) * 1024; // one sine chunk (hi or lo), Ng rows
+    // folded: this CTA's parity (the grid is even, so item b + k grid keeps the parity of b),
+    // and the contraction length and matrix rows Nk = Ng / 2
+    const int parity = FOLD ? (int)(blockIdx.x & 1) : 0;
+    const int Nk = FOLD ? Ng / 2 : Ng;
+    const int nkb = (Nk + kKB - 1) / kKB;                 // data chunks per tile
+    const uint32_t sch = (uint32_t)((Nk + 7) / 8) * 1024; // one sine chunk (hi or lo), Nk rows
     // The M = 128 operand reads 128 rows from each sine chunk; rows >= Ng come from what
     // follows (the next chunk, or the stages) and only feed TMEM lanes that are never read.
     unsigned char *S_hi = base;
@@ -272,18 +291,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(const __grid_constant__ 
 
     // ---- set-up: S (hi/lo split, swizzled), lambda, tile table, barriers, tensor memory
     const int Kp = nka * kKA;
-    for (int q = tid; q < Ng * Kp; q += kThreads) {
+    const float *Sg = A.S + (FOLD ? (long long)parity * A.Npad * Kp : 0LL);
+    for (int q = tid; q < Nk * Kp; q += kThreads) {
         const int n = q / Kp, k = q % Kp;
-        const float sv = A.S[q];
-        const float hi = tf32_hi(sv);
+        const float sv = Sg[q];
+        const float hi = tf32_rn(sv);
         const uint32_t off = (uint32_t)(k / kKA) * sch + sw128_offset(n, k % kKA);
         *(float *)(S_hi + off) = hi;
-        *(float *)(S_lo + off) = sv - hi;
+        *(float *)(S_lo + off) = tf32_rn(sv - hi);
     }
     for (int q = tid; q < Ng; q += kThreads) lam[q] = A.lam[q];
     const long long my_tiles = A.ntiles > (int)blockIdx.x ? (A.ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     auto load_tile = [&](long long k) {
-        const Chunk tl = A.tiles[(int)blockIdx.x + k * (int)gridDim.x];
+        const Chunk tl = A.tiles[((int)blockIdx.x + k * (int)gridDim.x) >> (FOLD ? 1 : 0)];
         TileInfo ti;
         ti.m_off = A.boxes[tl.box].m_off;
         ti.pp_off = A.boxes[tl.box].pp_off;
@@ -324,29 +344,59 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(const __grid_constant__ 
     if (warp >= 8 && warp < 16) {
         // ---------------------------------------------------------------- converters
         // chunk h of this CTA = tile h / nkb, columns 16 (h % nkb) .. + 15, in stage h % NST.
-        // The tensor core reads the raw FP32 values as the hi operand (it ignores the 13 low
-        // mantissa bits, which is the truncation tf32_hi computes); thread pt writes the lo
-        // parts of the 16-byte units q = pt + kProducers e (row q >> 2, unit q & 3).
+        // Thread pt splits the 16-byte units q = pt + kProducers e (row q >> 2, unit q & 3)
+        // in place: hi = tf32_rn(x) over the loaded value, lo = tf32_rn(x - hi) into the
+        // other half of the stage.
         const int pt = tid - 256;
         uint32_t soff[kUnits];
 #pragma unroll
         for (int e = 0; e < kUnits; ++e) {
-            const int q = pt + kProducers * e;
+            const int q = FOLD ? 4 * pt + e : pt + kProducers * e;   // folded: thread pt owns row pt
             soff[e] = sw64_offset(q >> 2, 4 * (q & 3));
         }
+        const float sgn = parity ? -1.0f : 1.0f;
         for (long long h = 0; h < nchunks && !*abort_flag; ++h) {
             const int s = (int)(h % NST);
             if (!mbar_wait(&loaded[s], (uint32_t)((h / NST) & 1), abort_flag)) {
                 *abort_flag = 1;
                 break;
             }
-            const unsigned char *xh = stages + (size_t)s * kStageBytes;
+            unsigned char *xh = stages + (size_t)s * kStageBytes;
             unsigned char *xl = stages + (size_t)s * kStageBytes + kHalfBytes;
+            if (FOLD) {
+                // half 0 holds columns n of the chunk, half 1 the mirror chunk (column 15 - k
+                // there pairs with column k here); the row becomes w = x + sgn x_mirror, split
+                // into hi (half 0) and lo (half 1) in place.  Units e and 3 - e of each half
+                // hold mirror columns: take them in pairs
 #pragma unroll
-            for (int e = 0; e < kUnits; ++e) {
-                const float4 v = *reinterpret_cast<const float4 *>(xh + soff[e]);
-                *reinterpret_cast<float4 *>(xl + soff[e]) = make_float4(
-                    v.x - tf32_hi(v.x), v.y - tf32_hi(v.y), v.z - tf32_hi(v.z), v.w - tf32_hi(v.w));
+                for (int e = 0; e < kUnits / 2; ++e) {
+                    const float4 c0 = *reinterpret_cast<const float4 *>(xh + soff[e]);
+                    const float4 c1 = *reinterpret_cast<const float4 *>(xh + soff[3 - e]);
+                    const float4 m0 = *reinterpret_cast<const float4 *>(xl + soff[e]);
+                    const float4 m1 = *reinterpret_cast<const float4 *>(xl + soff[3 - e]);
+                    // column 4e + j pairs with mirror column 15 - 4e - j = 4 (3 - e) + (3 - j)
+                    const float4 w0 = make_float4(fmaf(sgn, m1.w, c0.x), fmaf(sgn, m1.z, c0.y),
+                                                  fmaf(sgn, m1.y, c0.z), fmaf(sgn, m1.x, c0.w));
+                    const float4 w1 = make_float4(fmaf(sgn, m0.w, c1.x), fmaf(sgn, m0.z, c1.y),
+                                                  fmaf(sgn, m0.y, c1.z), fmaf(sgn, m0.x, c1.w));
+                    const float4 h0 = make_float4(tf32_rn(w0.x), tf32_rn(w0.y), tf32_rn(w0.z), tf32_rn(w0.w));
+                    const float4 h1 = make_float4(tf32_rn(w1.x), tf32_rn(w1.y), tf32_rn(w1.z), tf32_rn(w1.w));
+                    *reinterpret_cast<float4 *>(xh + soff[e]) = h0;
+                    *reinterpret_cast<float4 *>(xh + soff[3 - e]) = h1;
+                    *reinterpret_cast<float4 *>(xl + soff[e]) = make_float4(
+                        tf32_rn(w0.x - h0.x), tf32_rn(w0.y - h0.y), tf32_rn(w0.z - h0.z), tf32_rn(w0.w - h0.w));
+                    *reinterpret_cast<float4 *>(xl + soff[3 - e]) = make_float4(
+                        tf32_rn(w1.x - h1.x), tf32_rn(w1.y - h1.y), tf32_rn(w1.z - h1.z), tf32_rn(w1.w - h1.w));
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < kUnits; ++e) {
+                    const float4 v = *reinterpret_cast<const float4 *>(xh + soff[e]);
+                    const float4 h = make_float4(tf32_rn(v.x), tf32_rn(v.y), tf32_rn(v.z), tf32_rn(v.w));
+                    *reinterpret_cast<float4 *>(xh + soff[e]) = h;
+                    *reinterpret_cast<float4 *>(xl + soff[e]) = make_float4(
+                        tf32_rn(v.x - h.x), tf32_rn(v.y - h.y), tf32_rn(v.z - h.z), tf32_rn(v.w - h.w));
+                }
             }
             fence_proxy_async();
             mbar_arrive(&full[s]);
@@ -370,9 +420,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(const __grid_constant__ 
                     const long long rows = min((long long)kTN, Ng2 - tn.row0);
                     prefetch_l2(A.in + tn.m_off + (long long)tn.row0 * Ng, (uint32_t)(rows * Ng * sizeof(float)));
                 }
-                mbar_arrive_expect_tx(&loaded[s], kHalfBytes);
-                tma_load_2d(smem_u32(stages + (size_t)s * kStageBytes), &A.in_map, (int)(g % nkb) * kKB,
-                            (int)(ti.m_off / Ng + ti.row0), &loaded[s]);
+                const int cc = (int)(g % nkb), y = (int)(ti.m_off / Ng + ti.row0);
+                mbar_arrive_expect_tx(&loaded[s], FOLD ? 2 * kHalfBytes : kHalfBytes);
+                tma_load_2d(smem_u32(stages + (size_t)s * kStageBytes), &A.in_map, cc * kKB, y, &loaded[s]);
+                if (FOLD)   // the mirror chunk: columns Ng - 16 (cc + 1) .. Ng - 16 cc - 1
+                    tma_load_2d(smem_u32(stages + (size_t)s * kStageBytes + kHalfBytes), &A.in_map,
+                                Ng - (cc + 1) * kKB, y, &loaded[s]);
             }
             if (*abort_flag) {
                 const unsigned long long t0 = now_ns();
@@ -408,7 +461,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(const __grid_constant__ 
 #pragma unroll
                     for (int kk = 0; kk < kKB / 8; ++kk) {
                         const int kg = c * kKB + kk * 8;
-                        if (kg >= Ng) break;                      // all-zero K step
+                        if (kg >= Nk) break;                      // all-zero K step
                         const uint32_t ao = (uint32_t)(kg / kKA) * sch + (uint32_t)((kg % kKA) / 8) * 32;
                         const uint64_t ahi = sw128_desc(shi + ao), alo = sw128_desc(slo + ao);
                         const uint64_t bhi = sw64_desc(xh + kk * 32), blo = sw64_desc(xl + kk * 32);
@@ -435,7 +488,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(const __grid_constant__ 
         // every tile's barriers, also those whose lanes are all >= Ng.
         const int quarter = warp & 3, half = warp >> 2;
         const int n0 = quarter * 32;
-        const int ncol = Ng - n0 < 32 ? Ng - n0 : 32;        // valid columns of this warp (may be <= 0)
+        const int ncol = Nk - n0 < 32 ? Nk - n0 : 32;        // valid columns of this warp (may be <= 0)
         const float scale = (PASS == P_XI) ? 8.0f / ((float)(Ng + 1) * (Ng + 1) * (Ng + 1)) : 1.0f;
         const long long S = Ng + 4;
         float *buf = xpose + warp * (kXposeBytes / 4);
@@ -487,19 +540,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(const __grid_constant__ 
                     for (int c = 0; c < 8; ++c) {
                         const int nl = cg * 8 + c;
                         if (nl >= ncol) break;
+                        const int nout = FOLD ? 2 * (n0 + nl) + parity : n0 + nl;   // output column
                         float4 x = reinterpret_cast<const float4 *>(buf + nl * 32)[ru ^ (nl & 7)];
                         if (PASS == P_XI) {
                             // rows R .. R + 3 share rhi (Ng % 4 == 0); padded boxes start 2 floats
                             // past a 64-float boundary, so interior rows are 16-byte aligned
-                            float *p = A.out + ti.pp_off + ((long long)(n0 + nl + 2) * S + (rhi + 2)) * S + (rlo + 2);
+                            float *p = A.out + ti.pp_off + ((long long)(nout + 2) * S + (rhi + 2)) * S + (rlo + 2);
                             *reinterpret_cast<float4 *>(p) = make_float4(x.x * scale, x.y * scale, x.z * scale, x.w * scale);
                         } else {
                             if (PASS == P_XF) {
-                                const float ln = lam[n0 + nl];
+                                const float ln = lam[nout];
                                 x = make_float4(__fdividef(x.x, ln + lr.x), __fdividef(x.y, ln + lr.y),
                                                 __fdividef(x.z, ln + lr.z), __fdividef(x.w, ln + lr.w));
                             }
-                            *reinterpret_cast<float4 *>(A.out + ti.m_off + (long long)(n0 + nl) * Ng2 + R) = x;
+                            *reinterpret_cast<float4 *>(A.out + ti.m_off + (long long)nout * Ng2 + R) = x;
                         }
                     }
                 }
@@ -516,15 +570,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(const __grid_constant__ 
         while (!mbar_try_wait(drain, 0) && now_ns() - t0 < kWaitNs) {
         }
     }
-    if (*abort_flag && tid == 0) atomicExch(A.err, 1);
+    if (*abort_flag && tid == 0) atomicOr(A.err, 1);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     if (warp == 16) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 
-size_t tc_smem_bytes(int Ng, int nkc, int nstage) {
-    const size_t sch = (size_t)((Ng + 7) / 8) * 1024;
+// Dynamic shared memory of a launch: Nk matrix rows (Ng, or Ng / 2 folded), Ng eigenvalues.
+size_t tc_smem_bytes(int Nk, int Ng, int nkc, int nstage) {
+    const size_t sch = (size_t)((Nk + 7) / 8) * 1024;
     return 1024 + 2 * (size_t)nkc * sch + (size_t)nstage * kStageBytes + 8 * kXposeBytes + (3 * nstage + 5) * 8 + 16 +
            (size_t)Ng * 4 + 16 + kTileCache * sizeof(TileInfo) + 64;
 }
@@ -575,9 +630,10 @@ cudaError_t run_tc_pass(Ctx &c, const TcGroup &G, const float *in, float *out) {
     TcArgs a;
     cudaError_t me = input_map(c, in, G.Ng, &a.in_map);
     if (me != cudaSuccess) return me;
+    const bool fold = tc_folded(G.Ng);
     a.boxes = c.boxes;
     a.tiles = G.tiles;
-    a.ntiles = G.ntiles;
+    a.ntiles = fold ? 2 * G.ntiles : G.ntiles;     // folded: one item per parity of each tile
     a.Ng = G.Ng;
     a.Npad = G.Npad;
     a.nkc = G.nkc;
@@ -588,33 +644,47 @@ cudaError_t run_tc_pass(Ctx &c, const TcGroup &G, const float *in, float *out) {
     a.out = out;
     a.err = c.dev_err;
     a.lo_lo = c.tc_lo_lo ? 1 : 0;
-    const size_t smem = tc_smem_bytes(G.Ng, G.nkc, G.nstage);
-    const int grid = std::max(1, std::min(G.ntiles, c.num_sms));
-    k_dst_tc<PASS><<<grid, kThreads, smem, c.stream>>>(a);
+    const size_t smem = tc_smem_bytes(fold ? G.Ng / 2 : G.Ng, G.Ng, G.nkc, G.nstage);
+    if (fold) {
+        // an even grid keeps each CTA on one parity (item b + k grid has the parity of b)
+        const int grid = std::max(2, std::min(a.ntiles, c.num_sms) & ~1);
+        k_dst_tc<PASS, true><<<grid, kThreads, smem, c.stream>>>(a);
+    } else {
+        const int grid = std::max(1, std::min(a.ntiles, c.num_sms));
+        k_dst_tc<PASS, false><<<grid, kThreads, smem, c.stream>>>(a);
+    }
     ++c.launches;
     return cudaGetLastError();
 }
 
 }  // namespace
 
+bool tc_folded(int Ng) { return Ng > kTM; }
+
 int tc_plan_stages(int Ng, int &Npad, int &nkc) {
     // as many data stages (up to 4) as fit next to the resident sine matrix, at least 2
-    Npad = ((Ng + 15) / 16) * 16;
-    nkc = (Ng + kKA - 1) / kKA;
+    const int Nk = tc_folded(Ng) ? Ng / 2 : Ng;
+    Npad = ((Nk + 15) / 16) * 16;
+    nkc = (Nk + kKA - 1) / kKA;
     for (int nst = 4; nst >= 2; --nst)
-        if (tc_smem_bytes(Ng, nkc, nst) <= kSmemBudget) return nst;
+        if (tc_smem_bytes(Nk, Ng, nkc, nst) <= kSmemBudget) return nst;
     return 0;
 }
 
 bool tc_supported(int Ng) {
     int Npad, nkc;
-    return Ng >= 4 && Ng <= 128 && Ng % 4 == 0 && tc_plan_stages(Ng, Npad, nkc) >= 2;
+    // direct form: Ng <= 128 (one M = 128 operand), rows of 16-byte units; folded form:
+    // Ng / 2 <= 128 and a multiple of 16 (whole 16-column chunks and their mirrors)
+    const bool shape = tc_folded(Ng) ? (Ng <= 2 * kTM && Ng % 32 == 0) : (Ng >= 4 && Ng % 4 == 0);
+    return shape && tc_plan_stages(Ng, Npad, nkc) >= 2;
 }
 
 template <int PASS>
 cudaError_t set_tc_attr() {
     const int lim = (int)kSmemBudget;
-    return cudaFuncSetAttribute(k_dst_tc<PASS>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaError_t e = cudaFuncSetAttribute(k_dst_tc<PASS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_dst_tc<PASS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
 }
 
 cudaError_t init_tc_kernels() {
@@ -626,10 +696,15 @@ cudaError_t init_tc_kernels() {
     return set_tc_attr<P_XI>();
 }
 
-// The launch groups: every Ng group, or in the per-tile form only the current box's tiles.
+// The launch groups: every Ng group with boxes in the bound batch, or in the per-tile form
+// only the current box's tiles.
 std::vector<TcGroup> active_groups(const Ctx &c) {
-    if (c.view_box < 0) return c.tc_groups;
     std::vector<TcGroup> one;
+    if (c.view_box < 0) {
+        for (const TcGroup &G : c.tc_groups)
+            if (G.ntiles > 0) one.push_back(G);       // (a batch may hold no box of an Ng)
+        return one;
+    }
     for (const TcGroup &G : c.tc_groups) {
         if (G.Ng != c.boxes_h[c.view_box].Ng) continue;
         TcGroup V = G;

@@ -277,33 +277,43 @@ k_interp(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
 
 __global__ void __launch_bounds__(kChunk, 5)
 k_kick_drift(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
-             float *__restrict__ part, long long P, const float *__restrict__ phi, KickDrift kd) {
+             float *__restrict__ part, long long P, const float *__restrict__ phi, KickDrift kd,
+             int *__restrict__ kcount) {
     const Chunk ch = chunks[blockIdx.x];
     const BoxDesc &B = boxes[ch.box];
     const int Nsc = B.Nsc;
     const int local = ch.start + threadIdx.x;
-    if (local >= Nsc * Nsc * Nsc) return;
-    const long long gi = B.p_off + local;
-    int b[3];
-    decode_local(local, Nsc, b[0], b[1], b[2]);
-    float s[3], p[3], p1[3], p2[3];
+    int key = -1;
+    if (local < Nsc * Nsc * Nsc) {
+        const long long gi = B.p_off + local;
+        int b[3];
+        decode_local(local, Nsc, b[0], b[1], b[2]);
+        float s[3], p[3], p1[3], p2[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        s[a] = part[a * P + gi];
-        p[a] = part[(3 + a) * P + gi];
-        p1[a] = __ldg(part + (6 + a) * P + gi);
-        p2[a] = __ldg(part + (9 + a) * P + gi);
-    }
-    float F[3];
-    interpolate_force(B, phi, b, s, F);
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        p[a] = fmaf(kd.kF, F[a], fmaf(kd.k1, p1[a], fmaf(kd.k2, p2[a], p[a])));
-        part[(3 + a) * P + gi] = p[a];
-        if (kd.drift) {
-            s[a] = fmaf(kd.alpha, p[a], fmaf(kd.d1, p1[a], fmaf(kd.d2, p2[a], s[a])));
-            part[a * P + gi] = s[a];
+        for (int a = 0; a < 3; ++a) {
+            s[a] = part[a * P + gi];
+            p[a] = part[(3 + a) * P + gi];
+            p1[a] = __ldg(part + (6 + a) * P + gi);
+            p2[a] = __ldg(part + (9 + a) * P + gi);
         }
+        float F[3];
+        interpolate_force(B, phi, b, s, F);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            p[a] = fmaf(kd.kF, F[a], fmaf(kd.k1, p1[a], fmaf(kd.k2, p2[a], p[a])));
+            part[(3 + a) * P + gi] = p[a];
+            if (kd.drift) {
+                s[a] = fmaf(kd.alpha, p[a], fmaf(kd.d1, p1[a], fmaf(kd.d2, p2[a], s[a])));
+                part[a * P + gi] = s[a];
+            }
+        }
+        if (kcount) key = brick_entry(B, s, b).key;
+    }
+    // the next deposit's key counts (sorted form): one atomic per distinct key per warp
+    if (kcount) {
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+        if (key >= 0 && lane == leader) atomicAdd(kcount + B.key_off + key, __popc(peers));
     }
 }
 
@@ -421,8 +431,9 @@ cudaError_t launch_interp(Ctx &c, const float *s, long long stride, float *F) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_kick_drift(Ctx &c, const KickDrift &kd) {
-    k_kick_drift<<<c.n_pchunks, kChunk, 0, c.stream>>>(c.boxes, c.pchunks, c.part, c.P, c.phi, kd);
+cudaError_t launch_kick_drift(Ctx &c, const KickDrift &kd, bool count_keys) {
+    k_kick_drift<<<c.n_pchunks, kChunk, 0, c.stream>>>(c.boxes, c.pchunks, c.part, c.P, c.phi, kd,
+                                                        count_keys && kd.drift ? c.kcount : nullptr);
     ++c.launches;
     return cudaGetLastError();
 }

@@ -82,6 +82,10 @@ class Scola:
         B.scola_final_density(self.ctx, x.contiguous(), d)
         return d
 
+    def power_spectrum(self, delta, edges):
+        """(k_mean, P(k), n_modes) per bin of an N^3 field (CUDA tensor), edges in h/Mpc."""
+        return B.scola_power_spectrum(self.ctx, delta.contiguous(), edges)
+
     def stats(self):
         return B.scola_get_stats(self.ctx)
 

@@ -94,3 +94,20 @@ def sampled_box_errors(cfg, fields, sched, x, p, boxes, cache=None):
                         pos_rms_cells=float(np.sqrt(np.mean(dx**2))), pos_max_cells=float(dx.max()),
                         mom_rms_rel=float(np.sqrt(np.mean(dp**2)) / np.sqrt(np.mean(np.sum(pr**2, 1))))))
     return out
+
+
+def oracle_final_density_loss(w, kw, target):
+    """FP64 oracle: sum over the N^3 CIC mesh of (final density - target)^2 of one run."""
+    from oracle import stats
+    cfg = oracle_cfg(kw)
+    x = oscola.run_scola(np.asarray(w, np.float64), cfg)["x"]
+    d = stats.cic_density_periodic(x, cfg.L, cfg.Np, cfg.Np)
+    return float(np.sum((d - target) ** 2))
+
+
+def oracle_central_difference(args):
+    """FP64 central difference of oracle_final_density_loss along direction v (for a
+    process pool: one (w, kw, target, v, eps) tuple per call)."""
+    w, kw, target, v, eps = args
+    return (oracle_final_density_loss(w + eps * v, kw, target)
+            - oracle_final_density_loss(w - eps * v, kw, target)) / (2 * eps)

@@ -54,6 +54,10 @@ def test_validation_errors_without_gpu(lib):
     bad = lib.make_params(L=100.0, Np=32, Ntiles=2, Nbuf=10)          # box larger than the lattice
     with pytest.raises(lib.ScolaError):
         lib.scola_tiling_info(bad)
+    bad = lib.make_params(L=100.0, Np=32, Ntiles=2, Nbuf=4, batch_boxes=-1)
+    with pytest.raises(lib.ScolaError) as e:
+        lib.scola_tiling_info(bad)
+    assert e.value.status == 1
     bad = lib.make_params(L=100.0, Np=32, Ntiles=2, Nbuf=4, deposit_form=3)
     with pytest.raises(lib.ScolaError) as e:
         lib.scola_tiling_info(bad)

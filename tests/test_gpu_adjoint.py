@@ -5,6 +5,8 @@ differences to 1e-5) on small runs, through the torch.autograd.Function, and
 against FP32 central differences along random directions at the size of the
 adjoint workload (128^3 particles, 4^3 tiles, buffer 8, 48^3 mesh, 10 steps).
 """
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -88,9 +90,44 @@ def test_autograd_function_matches_backward():
 
 
 @pytest.mark.slow
+def test_gradient_matches_fp64_central_differences():
+    # The 32^3 workload (8 boxes of 24^3 particles and cells, 10 steps): the GPU gradient
+    # (3xTF32 tensor cores) against FP64 central differences of the oracle's loss along 64
+    # random directions.  With eps = 1e-5 in FP64 the differences cross no CIC kink and carry
+    # no truncation error at this level, so they give the derivative of the FP64 run.
+    import json
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    from gpu_common import oracle_central_difference
+    kw = workload_cfg("plain_32")
+    target = _target(kw, 22)
+    w = synth_inputs.white_noise(32, 21).astype(np.float64)
+    sim = _sim(kw, "tc")
+    _, g = _gpu_loss_grad(sim, w, target)
+    _pkg().scola_device_status(sim.ctx)
+    sim.close()
+    vs = [synth_inputs.random_field(w.shape, 500 + k) for k in range(64)]
+    # a spawned pool: forked children of a CUDA process are not safe
+    with ProcessPoolExecutor(max_workers=min(16, os.cpu_count() or 1), mp_context=mp.get_context("spawn")) as ex:
+        fd = np.asarray(list(ex.map(oracle_central_difference, [(w, kw, target, v, 1e-5) for v in vs])))
+    gv = np.asarray([float(np.sum(g * v)) for v in vs])
+    errs = np.abs(fd - gv) / np.abs(fd)
+    agg = float(np.linalg.norm(fd - gv) / np.linalg.norm(fd))
+    print(json.dumps({"workload": "plain_32", "directions": 64, "eps": 1e-5, "median_rel_err": float(np.median(errs)),
+                      "rel_l2_over_directions": agg, "max_rel_err": float(errs.max())}))
+    assert np.median(errs) < 1e-3, errs
+    assert agg < 1e-3, agg
+
+
+@pytest.mark.slow
 def test_adjoint_workload_central_differences():
     # 128^3 particles, 64 boxes, 48^3 meshes, 10 steps; FP32 central differences of the
-    # loss along random directions against <grad, v>.
+    # loss along 64 random directions against <grad, v>.  The FP32 forward run limits the
+    # differences: the discrepancy levels off near 7e-3-1e-2 as eps shrinks from 2e-3 to
+    # 5e-4 (and grows with eps above that, where the step crosses CIC kinks), so the bound
+    # here is 2e-2 on the median and on the relative L2 error over all directions; the FP64
+    # central differences on the 32^3 workload above check the gradient to 1e-3.
+    import json
     kw = workload_cfg("adjoint_128")
     sim = _sim(kw, "tc")
     w = synth_inputs.white_noise(128, 1).astype(np.float64)
@@ -105,11 +142,43 @@ def test_adjoint_workload_central_differences():
         d = sim.final_density(x).cpu().numpy().astype(np.float64)
         return float(np.sum((d - target) ** 2))
 
-    errs = []
-    for seed in range(8):
+    fd, gv = [], []
+    eps = 1e-3
+    for seed in range(64):
         v = synth_inputs.random_field(w.shape, 300 + seed)
-        eps = 2e-3
-        fd = (loss(w + eps * v) - loss(w - eps * v)) / (2 * eps)
-        errs.append(abs(fd - np.sum(g * v)) / abs(fd))
+        fd.append((loss(w + eps * v) - loss(w - eps * v)) / (2 * eps))
+        gv.append(float(np.sum(g * v)))
     sim.close()
-    assert np.median(errs) < 1e-2, errs
+    fd, gv = np.asarray(fd), np.asarray(gv)
+    errs = np.abs(fd - gv) / np.abs(fd)
+    agg = float(np.linalg.norm(fd - gv) / np.linalg.norm(fd))
+    print(json.dumps({"directions": len(errs), "eps": eps, "median_rel_err": float(np.median(errs)),
+                      "rel_l2_over_directions": agg, "max_rel_err": float(errs.max())}))
+    assert np.median(errs) < 2e-2, errs
+    assert agg < 2e-2, agg
+
+
+@pytest.mark.slow
+def test_adjoint_workload_matches_fp64_oracle_adjoint():
+    # The same loss at full size: the GPU gradient (3xTF32 tensor cores, FP32 elsewhere)
+    # against the FP64 oracle adjoint of the same loss and target.  The loss is piecewise
+    # smooth (CIC weights are piecewise linear): where the FP32 and FP64 runs put a
+    # particle on different sides of a cell face the two adjoints take different one-sided
+    # derivatives.  With 2M particles over 11 force evaluations that moves the gradient by
+    # ~2e-3 here (small runs: ~5e-5, one kinked seed 2e-3), hence the bound 5e-3.
+    import json
+    kw = workload_cfg("adjoint_128")
+    cfg = oracle_cfg(kw)
+    sim = _sim(kw, "tc")
+    w = synth_inputs.white_noise(128, 1)
+    wt = torch.from_numpy(synth_inputs.white_noise(128, 2)).cuda()
+    xt, _ = sim.forward(wt)
+    target = sim.final_density(xt).cpu().numpy().astype(np.float64)
+    val, g = _gpu_loss_grad(sim, w, target)
+    _pkg().scola_device_status(sim.ctx)
+    sim.close()
+    val_o, g_o = adjoint.loss_and_grad(w.astype(np.float64), cfg, target)
+    rel = float(np.linalg.norm(g - g_o) / np.linalg.norm(g_o))
+    print(json.dumps({"workload": "adjoint_128", "loss_rel_diff": abs(val / val_o - 1), "grad_rel_l2": rel}))
+    assert abs(val / val_o - 1) < 1e-4
+    assert rel < 5e-3, rel
