@@ -279,9 +279,8 @@ def kernel_roofline(kt, kw, clocks, peaks, tc):
     P = sum(n**3 for n in nsc)
     M = sum(g**3 for g in ng)
     MP = sum((g + 4) ** 3 for g in ng)
-    SH = MP - M
     dense = sum(2.0 * g * g**3 for g in ng)          # flops of one dense DST-I along one axis
-    work = {"pad": ("hbm", 8.0 * SH), "deposit": ("hbm", 12.0 * P + 4.0 * M),
+    work = {"deposit": ("hbm", 12.0 * P + 4.0 * M),
             "kick_drift": ("hbm", 72.0 * P + 4.0 * MP)}
     if tc:
         names = ["dst_1_z_fwd", "dst_2_y_fwd", "dst_3_x_fwd_div", "dst_4_z_inv", "dst_5_y_inv",

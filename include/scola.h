@@ -301,9 +301,9 @@ scola_status scola_set_profiling(scola_ctx *ctx, int32_t enable);
 /*
  * Average device time per launch [ms] of each kernel class in the last
  * forward run made in profiling mode (synchronises on it).  ms_per_launch
- * (host, n >= 9 doubles) receives, in order: pad (ghost layers of Phi),
- * deposit (with the clearing of the accumulator), the Poisson passes 1..6,
- * interpolate + kick + drift.  FP32 form: pass 1 z forward, 2 y forward,
+ * (host, n >= 8 doubles) receives, in order: deposit (with the boundary source
+ * and the clearing of its counters), the Poisson passes 1..6, interpolate +
+ * kick + drift.  FP32 form: pass 1 z forward, 2 y forward,
  * 3 x forward + sine-space division + x inverse, 4 y inverse, 5 z inverse,
  * 6 empty.  Tensor-core form: 1 z forward, 2 y forward, 3 x forward +
  * division, 4 z inverse, 5 y inverse, 6 x inverse.

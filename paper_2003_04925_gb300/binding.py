@@ -238,8 +238,7 @@ def scola_get_stats(ctx):
     return out
 
 
-KERNEL_CLASSES = ("pad", "deposit", "dst_1", "dst_2", "dst_3", "dst_4", "dst_5", "dst_6",
-                  "kick_drift")
+KERNEL_CLASSES = ("deposit", "dst_1", "dst_2", "dst_3", "dst_4", "dst_5", "dst_6", "kick_drift")
 
 
 def scola_set_profiling(ctx, enable):

@@ -30,7 +30,7 @@ using namespace scola;
 
 // Kernel classes timed in profiling mode (scola_set_profiling / scola_kernel_times).
 enum KernelClass {
-    KC_PAD = 0, KC_DEPOSIT, KC_DST1, KC_DST2, KC_DST3, KC_DST4, KC_DST5, KC_DST6, KC_KICK_DRIFT,
+    KC_DEPOSIT = 0, KC_DST1, KC_DST2, KC_DST3, KC_DST4, KC_DST5, KC_DST6, KC_KICK_DRIFT,
     KC_COUNT
 };
 
@@ -708,6 +708,14 @@ KickDrift kick_drift_coefficients(const TimeTable &t, int k) {
     return kd;
 }
 
+// The forward kick reads the stored potential Phi / D1(a_k): its force coefficient carries
+// the factor D1 (the adjoint works with Phi itself and uses kick_drift_coefficients).
+KickDrift forward_kick(const TimeTable &t, int k) {
+    KickDrift kd = kick_drift_coefficients(t, k);
+    kd.kF = (float)(t.beta[k] * t.D1[k]);
+    return kd;
+}
+
 // Restricts every work list to one box; restores on destruction.
 struct BoxView {
     scola_ctx *c;
@@ -766,7 +774,8 @@ scola_status autotune_deposit(scola_ctx *c) {
         if (c->prm.batch_mode == SCOLA_BATCH_PER_TILE) view.reset(new BoxView(c, 0));
         CK(launch_box_init(*c));
         CK(launch_shell(*c));
-        CK(launch_pad(*c, (float)c->tt.D1[0]));
+        CK(launch_pad(*c, 1.0f));
+        const float inv_D1 = (float)(1.0 / c->tt.D1[0]);
         for (int q = lo; q < hi; ++q) {
             c->deposit_form = all[q].form;
             c->deposit_threads = all[q].threads;
@@ -775,7 +784,7 @@ scola_status autotune_deposit(scola_ctx *c) {
                                       (all[q].form == 0 ? "sorted form, " + std::to_string(all[q].threads) + " threads" +
                                                               (all[q].split ? ", 32-bit halves" : "")
                                                         : std::string("atomic form"));
-            cudaError_t e = launch_deposit(*c, c->part, c->P);      // warm-up
+            cudaError_t e = launch_deposit(*c, c->part, c->P, inv_D1);      // warm-up
             if (e == cudaSuccess) e = c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize();
             if (e != cudaSuccess) {
                 set_error(which + ": " + cudaGetErrorString(e));
@@ -784,7 +793,7 @@ scola_status autotune_deposit(scola_ctx *c) {
             float ms = -1.0f;
             for (int rep = 0; rep < 3; ++rep) {
                 CK(cudaEventRecord(c->ev[3], c->stream));
-                CK(launch_deposit(*c, c->part, c->P));
+                CK(launch_deposit(*c, c->part, c->P, inv_D1));
                 CK(cudaEventRecord(c->ev[2], c->stream));
                 CK(cudaEventSynchronize(c->ev[2]));
                 float t = 0.0f;
@@ -817,11 +826,11 @@ scola_status enqueue_evolution_per_tile(scola_ctx *c) {
         BoxView v(c, b);
         CK(launch_box_init(*c));
         CK(launch_shell(*c));
+        CK(launch_pad(*c, 1.0f));
         for (int k = 0; k <= n; ++k) {
-            CK(launch_pad(*c, (float)c->tt.D1[k]));
-            CK(launch_deposit(*c, c->part, c->P));
+            CK(launch_deposit(*c, c->part, c->P, (float)(1.0 / c->tt.D1[k])));
             CK(launch_poisson(*c));
-            CK(launch_kick_drift(*c, kick_drift_coefficients(c->tt, k)));
+            CK(launch_kick_drift(*c, forward_kick(c->tt, k)));
         }
     }
     return SCOLA_OK;
@@ -834,6 +843,7 @@ scola_status enqueue_evolution(scola_ctx *c) {
     if (c->prm.batch_mode == SCOLA_BATCH_PER_TILE) return enqueue_evolution_per_tile(c);
     CK(launch_box_init(*c));
     CK(launch_shell(*c));
+    CK(launch_pad(*c, 1.0f));
     const int n = (int)c->tt.alpha.size();
     int ei = 0;
     auto mark = [&]() -> cudaError_t {
@@ -849,9 +859,7 @@ scola_status enqueue_evolution(scola_ctx *c) {
             CK(cudaMemcpyAsync(c->ckpt + (size_t)k * 3 * c->P, c->part, sizeof(float) * 3 * (size_t)c->P,
                                cudaMemcpyDeviceToDevice, c->stream));
         CK(mark());
-        CK(launch_pad(*c, (float)c->tt.D1[k]));
-        CK(mark());
-        CK(launch_deposit(*c, c->part, c->P, nullptr, fused && k > 0));
+        CK(launch_deposit(*c, c->part, c->P, (float)(1.0 / c->tt.D1[k]), nullptr, fused && k > 0));
         if (fused && k < n) CK(clear_key_counts(*c));
         CK(mark());
         if (c->profiling) {
@@ -862,7 +870,7 @@ scola_status enqueue_evolution(scola_ctx *c) {
         } else {
             CK(launch_poisson(*c));
         }
-        CK(launch_kick_drift(*c, kick_drift_coefficients(c->tt, k), fused));
+        CK(launch_kick_drift(*c, forward_kick(c->tt, k), fused));
         CK(mark());
     }
     return SCOLA_OK;
@@ -1048,6 +1056,7 @@ scola_status scola_setup_boxes(scola_ctx *c) {
     CS(autotune_deposit(c));
     CK(launch_box_init(*c));
     CK(launch_shell(*c));
+    CK(launch_pad(*c, 1.0f));
     c->setup_done = true;
     return SCOLA_OK;
 }
@@ -1060,13 +1069,11 @@ scola_status scola_pm_force(scola_ctx *c, const float *s, double D1, float *F, f
         set_error("scola_pm_force needs scola_setup_boxes first");
         return SCOLA_ERR_STATE;
     }
-    CK(launch_pad(*c, (float)D1));
-    CK(launch_deposit(*c, s, c->P, delta));
+    // the solve gives Phi / D1 next to the unscaled shell in the ghost layers
+    CK(launch_deposit(*c, s, c->P, (float)(1.0 / D1), delta));
     CK(launch_poisson(*c));
-    CK(launch_interp(*c, s, c->P, F));
-    if (phi)
-        CK(cudaMemcpyAsync(phi, c->phi, sizeof(float) * (size_t)c->MP, cudaMemcpyDeviceToDevice,
-                           c->stream));
+    CK(launch_interp(*c, s, c->P, F, (float)D1));
+    if (phi) CK(launch_scaled_copy(*c, c->phi, phi, c->MP, (float)D1));
     return SCOLA_OK;
 }
 
@@ -1156,11 +1163,10 @@ scola_status scola_backward(scola_ctx *c, const float *lam_delta, float *lam_w) 
     for (int k = n; k >= 0; --k) {
         CK(launch_adj_kick_drift(*c, c->adj, kick_drift_coefficients(c->tt, k)));
         const float *sk = c->ckpt + (size_t)k * 3 * P;
-        CK(launch_pad(*c, (float)c->tt.D1[k]));
-        CK(launch_deposit(*c, sk, P));
+        CK(launch_deposit(*c, sk, P, (float)(1.0 / c->tt.D1[k])));
         CK(launch_poisson(*c));
         CK(cudaMemsetAsync(c->lamG, 0, fb * 3 * c->MP, c->stream));
-        CK(launch_adj_interp(*c, sk, c->adj, c->lamG));
+        CK(launch_adj_interp(*c, sk, c->adj, c->lamG, (float)c->tt.D1[k]));
         CK(launch_adj_div(*c, c->lamG, c->lam_phi_pad, c->adj_in));
         CK(launch_poisson_buffers(*c, c->adj_in, c->work, c->work2, c->adj_out));
         CK(launch_adj_shell(*c, c->lam_phi_pad, c->adj_out, (float)c->tt.D1[k], c->lam_shell));

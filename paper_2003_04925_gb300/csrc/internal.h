@@ -184,13 +184,18 @@ cudaError_t launch_gradient(Ctx &c, const float *phi, float *psi);
 
 cudaError_t launch_box_init(Ctx &c);
 cudaError_t launch_shell(Ctx &c);
+// Ghost layers of the padded potential <- D1 x shell.  The solve runs on Phi / D1(a_K), so
+// the ghost layers hold the unscaled shell (D1 = 1), written once per forward run.
 cudaError_t launch_pad(Ctx &c, float D1);
 // counted: the key counts of s were made by the kick-drift that moved the particles (sorted
 // form, batched graph); otherwise the deposit counts them itself
-cudaError_t launch_deposit(Ctx &c, const float *s, long long stride, float *delta_out = nullptr,
+// inv_D1: the Poisson source is delta / D1(a_K) minus the boundary term of the unscaled
+// shell, so that the solve gives Phi / D1 (delta_out receives delta itself)
+cudaError_t launch_deposit(Ctx &c, const float *s, long long stride, float inv_D1, float *delta_out = nullptr,
                            bool counted = false);
-cudaError_t launch_deposit_atomic(Ctx &c, const float *s, long long stride, float *delta_out);
-cudaError_t launch_deposit_sorted(Ctx &c, const float *s, long long stride, float *delta_out, bool counted);
+cudaError_t launch_deposit_atomic(Ctx &c, const float *s, long long stride, float inv_D1, float *delta_out);
+cudaError_t launch_deposit_sorted(Ctx &c, const float *s, long long stride, float inv_D1, float *delta_out,
+                                  bool counted);
 cudaError_t clear_key_counts(Ctx &c);
 cudaError_t init_pm_kernels(Ctx &c);
 cudaError_t init_deposit_kernels();
@@ -206,7 +211,9 @@ cudaError_t launch_poisson_buffers(Ctx &c, const float *in, float *w1, float *w2
                                    float *out_pad);
 cudaError_t launch_poisson(Ctx &c);
 cudaError_t launch_poisson_pass(Ctx &c, int pass);
-cudaError_t launch_interp(Ctx &c, const float *s, long long stride, float *F);
+// F = D1 x gradient of the stored potential Phi / D1
+cudaError_t launch_interp(Ctx &c, const float *s, long long stride, float *F, float D1);
+cudaError_t launch_scaled_copy(Ctx &c, const float *in, float *out, long long n, float a);
 // count_keys: also count the sorted deposit's keys of the drifted particles (into cleared
 // counts) for the next force evaluation
 cudaError_t launch_kick_drift(Ctx &c, const KickDrift &kd, bool count_keys = false);
@@ -222,7 +229,7 @@ constexpr int kMaxSpectrumBins = 2048;
 cudaError_t launch_adj_colour(Ctx &c, const cufftComplex *in, cufftComplex *out);
 cudaError_t launch_adj_final(Ctx &c, const float *lam_delta, float *adj);
 cudaError_t launch_adj_kick_drift(Ctx &c, float *adj, const KickDrift &kd);
-cudaError_t launch_adj_interp(Ctx &c, const float *s, float *adj, float *lamG);
+cudaError_t launch_adj_interp(Ctx &c, const float *s, float *adj, float *lamG, float D1);
 cudaError_t launch_adj_div(Ctx &c, const float *lamG, float *lam_phi_pad, float *interior_out);
 cudaError_t launch_adj_shell(Ctx &c, const float *lam_phi_pad, const float *lam_src_pad, float D1,
                              float *lam_shell);

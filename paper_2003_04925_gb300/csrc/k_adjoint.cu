@@ -116,7 +116,7 @@ k_adj_kick_drift(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ ch
 
 __global__ void __launch_bounds__(kChunk)
 k_adj_interp(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
-             const float *__restrict__ s, long long P, const float *__restrict__ phi,
+             const float *__restrict__ s, long long P, const float *__restrict__ phi, float D1,
              float *__restrict__ adj, float *__restrict__ lamG, long long MP) {
     const Chunk ch = chunks[blockIdx.x];
     const BoxDesc &B = boxes[ch.box];
@@ -134,7 +134,7 @@ k_adj_interp(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks
     const long long S1 = Ng + 4, S2 = S1 * S1;
     const long long base = B.pp_off + ((long long)(i0[0] + 2) * S1 + (i0[1] + 2)) * S1 + (i0[2] + 2);
     const float *Pp = phi + base;
-    const float h = 0.5f * B.inv_dg;
+    const float h = 0.5f * B.inv_dg * D1;     // the stored potential is Phi / D1
     float dir[3] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int dx = 0; dx < 2; ++dx)
@@ -400,8 +400,8 @@ cudaError_t launch_adj_kick_drift(Ctx &c, float *adj, const KickDrift &kd) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_adj_interp(Ctx &c, const float *s, float *adj, float *lamG) {
-    k_adj_interp<<<c.n_pchunks, kChunk, 0, c.stream>>>(c.boxes, c.pchunks, s, c.P, c.phi, adj, lamG, c.MP);
+cudaError_t launch_adj_interp(Ctx &c, const float *s, float *adj, float *lamG, float D1) {
+    k_adj_interp<<<c.n_pchunks, kChunk, 0, c.stream>>>(c.boxes, c.pchunks, s, c.P, c.phi, D1, adj, lamG, c.MP);
     ++c.launches;
     return cudaGetLastError();
 }

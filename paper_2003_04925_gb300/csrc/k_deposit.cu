@@ -80,7 +80,7 @@ constexpr int kSourceChunks = 4;
 __global__ void __launch_bounds__(64 * kSourceChunks)
 k_density_source(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks, int nchunks,
                  const unsigned long long *__restrict__ acc, long long acc_base, const float *__restrict__ phi_pad,
-                 float *__restrict__ out, float *__restrict__ delta_out) {
+                 float inv_D1, float *__restrict__ out, float *__restrict__ delta_out) {
     const int ci = blockIdx.x * kSourceChunks + (threadIdx.x >> 6);
     if (ci >= nchunks) return;
     const Chunk ch = chunks[ci];
@@ -110,7 +110,10 @@ k_density_source(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ ch
     }
     const long long cell = B.m_off + cell0;
     if (delta_out) store4(delta_out + cell, v, vec, left);
-    // boundary source: the Dirichlet values sit in the ghost layer next to each face cell
+#pragma unroll
+    for (int e = 0; e < 4; ++e) v[e] *= inv_D1;
+    // boundary source: the Dirichlet values (unscaled shell) sit in the ghost layer next to
+    // each face cell
     int k = cell0 % Ng, j = (cell0 / Ng) % Ng, i = cell0 / Ng / Ng;
     const int S = Ng + 4;
 #pragma unroll
@@ -141,7 +144,7 @@ k_density_source(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ ch
 
 }  // namespace
 
-cudaError_t launch_deposit_atomic(Ctx &c, const float *s, long long stride, float *delta_out) {
+cudaError_t launch_deposit_atomic(Ctx &c, const float *s, long long stride, float inv_D1, float *delta_out) {
     // box groups of the current view: the precomputed groups, or the one box of the
     // per-tile form (whose lists the view has already restricted)
     const bool one = c.view_box >= 0;
@@ -162,7 +165,7 @@ cudaError_t launch_deposit_atomic(Ctx &c, const float *s, long long stride, floa
         }
         if (nmch > 0) {
             k_density_source<<<(nmch + kSourceChunks - 1) / kSourceChunks, 64 * kSourceChunks, 0, c.stream>>>(
-                c.boxes, mch, nmch, c.dep_acc, base, c.phi, c.work2, delta_out);
+                c.boxes, mch, nmch, c.dep_acc, base, c.phi, inv_D1, c.work2, delta_out);
             ++c.launches;
             if ((e = cudaGetLastError()) != cudaSuccess) return step_error("atomic deposit: source launch", e);
         }
@@ -176,9 +179,10 @@ cudaError_t launch_deposit_atomic(Ctx &c, const float *s, long long stride, floa
 }
 
 // The deposit in the form the context selected (both give bit-identical delta').
-cudaError_t launch_deposit(Ctx &c, const float *s, long long stride, float *delta_out, bool counted) {
-    return c.deposit_form == 0 ? launch_deposit_sorted(c, s, stride, delta_out, counted)
-                               : launch_deposit_atomic(c, s, stride, delta_out);
+cudaError_t launch_deposit(Ctx &c, const float *s, long long stride, float inv_D1, float *delta_out,
+                           bool counted) {
+    return c.deposit_form == 0 ? launch_deposit_sorted(c, s, stride, inv_D1, delta_out, counted)
+                               : launch_deposit_atomic(c, s, stride, inv_D1, delta_out);
 }
 
 }  // namespace scola

@@ -140,13 +140,48 @@ __device__ __forceinline__ void add_split(unsigned *lo, unsigned *hi, int c, uns
     if (old > 0xffffffffu - v) atomicAdd(hi + c, 1u);
 }
 
+// Adds the CIC weights of one entry (fractions v.xyz, packed lower cell v.w) that fall in the
+// brick [x0, x0 + 16) x [y0, ..) x [z0, ..) to its counters.  kFull: the brick lies inside
+// the mesh, so only the brick bounds need checking.
+template <bool kSplit, bool kFull>
+__device__ __forceinline__ void deposit_entry(unsigned long long *acc, const float4 v, int x0, int y0, int z0,
+                                              int Ng) {
+    const int pk = __float_as_int(v.w);
+    const int lx = (pk & 1023) - 2 - x0, ly = ((pk >> 10) & 1023) - 2 - y0, lz = ((pk >> 20) & 1023) - 2 - z0;
+#pragma unroll
+    for (int ex = 0; ex < 2; ++ex) {
+        const int cx = lx + ex;
+        if ((unsigned)cx >= (unsigned)kBrick || (!kFull && x0 + cx >= Ng)) continue;
+        const float wx = ex ? v.x : 1.0f - v.x;
+#pragma unroll
+        for (int ey = 0; ey < 2; ++ey) {
+            const int cy = ly + ey;
+            if ((unsigned)cy >= (unsigned)kBrick || (!kFull && y0 + cy >= Ng)) continue;
+            const float wxy = wx * (ey ? v.y : 1.0f - v.y);
+#pragma unroll
+            for (int ez = 0; ez < 2; ++ez) {
+                const int cz = lz + ez;
+                if ((unsigned)cz >= (unsigned)kBrick || (!kFull && z0 + cz >= Ng)) continue;
+                const unsigned long long f = weight_to_fixed(wxy * (ez ? v.z : 1.0f - v.z));
+                const int cell = (cx * kBrick + cy) * kBrick + cz;
+                if (kSplit) {
+                    unsigned *lo = reinterpret_cast<unsigned *>(acc);
+                    add_split(lo, lo + kBrickCells, cell, f);
+                } else {
+                    atomicAdd(&acc[cell], f);
+                }
+            }
+        }
+    }
+}
+
 // One CTA of T threads per real brick (item.start = brick index in the box, nb^3 of them).
 // kSplit: the counts as 32-bit low and high halves (32-bit atomics), else 64-bit atomics.
 template <int kBrickThreads, bool kSplit>
 __global__ void __launch_bounds__(kBrickThreads, kBrickThreads == 256 ? 5 : 3)
 k_sort_brick(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ items, const int *__restrict__ cnt,
              const int *__restrict__ offs, const float4 *__restrict__ entries, const float *__restrict__ phi_pad,
-             float *__restrict__ out, float *__restrict__ delta_out) {
+             float inv_D1, float *__restrict__ out, float *__restrict__ delta_out) {
     __shared__ __align__(16) unsigned long long acc[kBrickCells];
     __shared__ int seg_o[kSegments], seg_start[kSegments + 1];
     const Chunk it = items[blockIdx.x];
@@ -177,47 +212,40 @@ k_sort_brick(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ items,
         if (tid == 0) seg_start[0] = 0;
     }
     __syncthreads();
-    const int total = seg_start[kSegments];
-    for (int e = tid; e < total; e += kBrickThreads) {
-        int lo = 0, hi = kSegments;              // seg_start[lo] <= e < seg_start[hi]
+    // the brick's own 8 class slices are consecutive keys, hence one contiguous range: two
+    // entries per thread and iteration (both loads in flight); then the spill slices of the
+    // seven upper neighbours, located by a search over their 19 segment starts
+    const int own = seg_start[8], total = seg_start[kSegments];
+    const float4 *own_list = list + seg_o[0];
+    const bool full = x0 + kBrick <= Ng && y0 + kBrick <= Ng && z0 + kBrick <= Ng;
+    for (int e = tid; e < own; e += 2 * kBrickThreads) {
+        const bool two = e + kBrickThreads < own;
+        const float4 v0 = own_list[e];
+        const float4 v1 = two ? own_list[e + kBrickThreads] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (full) {
+            deposit_entry<kSplit, true>(acc, v0, x0, y0, z0, Ng);
+            if (two) deposit_entry<kSplit, true>(acc, v1, x0, y0, z0, Ng);
+        } else {
+            deposit_entry<kSplit, false>(acc, v0, x0, y0, z0, Ng);
+            if (two) deposit_entry<kSplit, false>(acc, v1, x0, y0, z0, Ng);
+        }
+    }
+    for (int e = own + tid; e < total; e += kBrickThreads) {
+        int lo = 8, hi = kSegments;              // seg_start[lo] <= e < seg_start[hi]
         while (hi - lo > 1) {
             const int mid = (lo + hi) >> 1;
             if (seg_start[mid] <= e) lo = mid;
             else hi = mid;
         }
         const float4 v = list[seg_o[lo] + e - seg_start[lo]];
-        const int pk = __float_as_int(v.w);
-        const int lx = (pk & 1023) - 2 - x0, ly = ((pk >> 10) & 1023) - 2 - y0, lz = ((pk >> 20) & 1023) - 2 - z0;
-#pragma unroll
-        for (int ex = 0; ex < 2; ++ex) {
-            const int cx = lx + ex;
-            if ((unsigned)cx >= (unsigned)kBrick || x0 + cx >= Ng) continue;
-            const float wx = ex ? v.x : 1.0f - v.x;
-#pragma unroll
-            for (int ey = 0; ey < 2; ++ey) {
-                const int cy = ly + ey;
-                if ((unsigned)cy >= (unsigned)kBrick || y0 + cy >= Ng) continue;
-                const float wxy = wx * (ey ? v.y : 1.0f - v.y);
-#pragma unroll
-                for (int ez = 0; ez < 2; ++ez) {
-                    const int cz = lz + ez;
-                    if ((unsigned)cz >= (unsigned)kBrick || z0 + cz >= Ng) continue;
-                    const unsigned long long f = weight_to_fixed(wxy * (ez ? v.z : 1.0f - v.z));
-                    const int cell = (cx * kBrick + cy) * kBrick + cz;
-                    if (kSplit) {
-                        unsigned *lo = reinterpret_cast<unsigned *>(acc);
-                        add_split(lo, lo + kBrickCells, cell, f);
-                    } else {
-                        atomicAdd(&acc[cell], f);
-                    }
-                }
-            }
-        }
+        if (full) deposit_entry<kSplit, true>(acc, v, x0, y0, z0, Ng);
+        else deposit_entry<kSplit, false>(acc, v, x0, y0, z0, Ng);
     }
     __syncthreads();
     // cells: item q -> (x, y) row of the brick, 4 consecutive z cells
     const float sc = B.nbar_inv * 2.3283064365386963e-10f, c2 = B.inv_dg * B.inv_dg;
     const int S = Ng + 4;
+    const bool edge = x0 == 0 || y0 == 0 || z0 == 0 || x0 + kBrick >= Ng || y0 + kBrick >= Ng || z0 + kBrick >= Ng;
     for (int q = tid; q < kBrickCells / 4; q += kBrickThreads) {
         const int lz = (q % (kBrick / 4)) * 4, ly = (q / (kBrick / 4)) % kBrick, lx = q / (kBrick * kBrick / 4);
         const int i = x0 + lx, j = y0 + ly, k = z0 + lz;
@@ -242,7 +270,9 @@ k_sort_brick(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ items,
         const long long cell = B.m_off + ((long long)i * Ng + j) * Ng + k;
         const bool vec = k + 4 <= Ng && (Ng & 3) == 0;
         if (delta_out) store4(delta_out + cell, v, vec, Ng - k);
-        if (i == 0 || j == 0 || i == Ng - 1 || j == Ng - 1 || k == 0 || k + 4 >= Ng) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) v[e] *= inv_D1;
+        if (edge && (i == 0 || j == 0 || i == Ng - 1 || j == Ng - 1 || k == 0 || k + 4 >= Ng)) {
             const float *P = phi_pad + B.pp_off + ((i + 2) * S + (j + 2)) * S + (k + 2);
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
@@ -288,7 +318,8 @@ cudaError_t clear_key_counts(Ctx &c) {
     return e == cudaSuccess ? e : step_error("sorted deposit: clearing the key counts", e);
 }
 
-cudaError_t launch_deposit_sorted(Ctx &c, const float *s, long long stride, float *delta_out, bool counted) {
+cudaError_t launch_deposit_sorted(Ctx &c, const float *s, long long stride, float inv_D1, float *delta_out,
+                                  bool counted) {
     // the boxes of the current view: all, or one in the per-tile form
     const int box0 = c.view_box >= 0 ? c.view_box : 0;
     const int nbox = c.view_box >= 0 ? 1 : c.nboxes;
@@ -309,7 +340,7 @@ cudaError_t launch_deposit_sorted(Ctx &c, const float *s, long long stride, floa
     if ((e = cudaGetLastError()) != cudaSuccess) return step_error("sorted deposit: fill launch", e);
 #define SCOLA_BRICK(T, SPLIT)                                                                             \
     k_sort_brick<T, SPLIT><<<c.n_sbricks, T, 0, c.stream>>>(c.boxes, c.sbricks, c.kcount, c.koffs, c.sentries, \
-                                                            c.phi, c.work2, delta_out)
+                                                            c.phi, inv_D1, c.work2, delta_out)
     if (c.deposit_threads == 256) {
         if (c.deposit_split) SCOLA_BRICK(256, true);
         else SCOLA_BRICK(256, false);

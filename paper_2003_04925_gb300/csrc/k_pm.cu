@@ -257,7 +257,7 @@ __device__ __forceinline__ void interpolate_force(const BoxDesc &B, const float 
 
 __global__ void __launch_bounds__(kChunk)
 k_interp(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
-         const float *__restrict__ s, long long stride, const float *__restrict__ phi,
+         const float *__restrict__ s, long long stride, const float *__restrict__ phi, float D1,
          float *__restrict__ F) {
     const Chunk ch = chunks[blockIdx.x];
     const BoxDesc &B = boxes[ch.box];
@@ -270,9 +270,9 @@ k_interp(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
     float sv[3] = {s[gi], s[stride + gi], s[2 * stride + gi]};
     float f[3];
     interpolate_force(B, phi, b, sv, f);
-    F[gi] = f[0];
-    F[stride + gi] = f[1];
-    F[2 * stride + gi] = f[2];
+    F[gi] = D1 * f[0];
+    F[stride + gi] = D1 * f[1];
+    F[2 * stride + gi] = D1 * f[2];
 }
 
 __global__ void __launch_bounds__(kChunk, 5)
@@ -425,8 +425,22 @@ cudaError_t launch_poisson_pass(Ctx &c, int pass) {
     }
 }
 
-cudaError_t launch_interp(Ctx &c, const float *s, long long stride, float *F) {
-    k_interp<<<c.n_pchunks, kChunk, 0, c.stream>>>(c.boxes, c.pchunks, s, stride, c.phi, F);
+cudaError_t launch_interp(Ctx &c, const float *s, long long stride, float *F, float D1) {
+    k_interp<<<c.n_pchunks, kChunk, 0, c.stream>>>(c.boxes, c.pchunks, s, stride, c.phi, D1, F);
+    ++c.launches;
+    return cudaGetLastError();
+}
+
+namespace {
+__global__ void k_scaled_copy(const float *__restrict__ in, float *__restrict__ out, long long n, float a) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = a * in[i];
+}
+}  // namespace
+
+cudaError_t launch_scaled_copy(Ctx &c, const float *in, float *out, long long n, float a) {
+    const long long g = (n + 255) / 256;
+    k_scaled_copy<<<(int)(g < 8192 ? (g > 0 ? g : 1) : 8192), 256, 0, c.stream>>>(in, out, n, a);
     ++c.launches;
     return cudaGetLastError();
 }
