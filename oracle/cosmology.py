@@ -22,7 +22,9 @@ Time coefficients.  Modified discretisation of App. B with u(a) = a^nLPT,
 t(a) = a (Eq. 60):
     alpha~(ai, af, aK) = aK^-nLPT  * int_ai^af a^(nLPT-2)/calH(a) da
     beta~(ai, af, aD)  = -(3/2) Om (af^nLPT - ai^nLPT) / (nLPT aD^nLPT calH(aD))
-The integral uses adaptive Simpson quadrature written out below.
+The integral uses adaptive Simpson quadrature written out below.  Standard
+discretisation (App. B, the alternative the paper describes before adopting the
+modified one): alpha_p = int_ai^af da/(a^2 calH), beta_delta = -(3/2) Om int da/(a calH).
 
 KDK schedule (Eq. 52, read with the product running over the n-1 inner steps
 so that no drift is applied twice; half-step times are arithmetic means in a):
@@ -152,8 +154,21 @@ def beta_tilde(ai, af, aD, Om, OL, nLPT=-2.5):
             / (nLPT * aD ** nLPT * float(conformal_hubble(aD, Om, OL))))
 
 
-def kdk_schedule(a_i, a_f, nsteps, Om, OL, nLPT=-2.5):
+def alpha_standard(ai, af, Om, OL):
+    """Standard drift factor (App. B, Eq. 50 with t = a): int_ai^af da / (a^2 calH(a))."""
+    return adaptive_simpson(lambda x: float(drift_prefactor(x, Om, OL)), ai, af)
+
+
+def beta_standard(ai, af, Om, OL):
+    """Standard kick factor (App. B, Eq. 50 with t = a): -(3/2) Om int_ai^af da / (a calH(a))."""
+    return adaptive_simpson(lambda x: float(kick_prefactor(x, Om, OL)), ai, af)
+
+
+def kdk_schedule(a_i, a_f, nsteps, Om, OL, nLPT=-2.5, stepping="modified"):
     """Coefficients of the KDK sequence (Eq. 52 with the COLA operators Eqs. 53-54).
+
+    stepping: "modified" (u(a) = a^nLPT factors, the paper's choice) or "standard"
+    (the time integrals of the drift and kick prefactors over each interval, App. B).
 
     Time steps are linear in a.  Returns a dict with, for each of the
     nsteps + 1 force evaluations k (force at a_k):
@@ -176,8 +191,14 @@ def kdk_schedule(a_i, a_f, nsteps, Om, OL, nLPT=-2.5):
     for k in range(n + 1):
         kick_from[k] = a[0] if k == 0 else ah[k - 1]
         kick_to[k] = ah[k] if k < n else a[n]
-        beta[k] = beta_tilde(kick_from[k], kick_to[k], a[k], Om, OL, nLPT)
-    alpha = np.array([alpha_tilde(a[k], a[k + 1], ah[k], Om, OL, nLPT) for k in range(n)])
+        if stepping == "standard":
+            beta[k] = beta_standard(kick_from[k], kick_to[k], Om, OL)
+        else:
+            beta[k] = beta_tilde(kick_from[k], kick_to[k], a[k], Om, OL, nLPT)
+    if stepping == "standard":
+        alpha = np.array([alpha_standard(a[k], a[k + 1], Om, OL) for k in range(n)])
+    else:
+        alpha = np.array([alpha_tilde(a[k], a[k + 1], ah[k], Om, OL, nLPT) for k in range(n)])
     dD1 = D1[1:] - D1[:-1]
     dD2 = D2[1:] - D2[:-1]
     return {

@@ -52,6 +52,8 @@ class ScolaConfig:
     a_f: float = 1.0
     nsteps: int = 10
     nLPT: float = -2.5
+    stepping: str = "modified"   # KDK time factors: "modified" (u = a^nLPT) or "standard" (App. B)
+    lpt_order: int = 2           # 2: 2LPT frame; 1: Zel'dovich frame (phi2 = Psi2 = 0)
 
     @property
     def Ntile(self):
@@ -107,11 +109,16 @@ def initial_fields(w, cfg):
         raise ValueError("white noise must be Np^3 (LPT grid N = Np)")
     delta = ics.initial_density(w, cfg.L, cfg.Om, cfg.h, cfg.ns, cfg.sigma8)
     phi1, phi2, psi1, psi2 = lpt.lpt_fields(delta, cfg.L)
+    if cfg.lpt_order == 1:
+        # Zel'dovich approximation: first-order displacements only (the COLA frame and the
+        # initial positions use Psi1 alone)
+        phi2 = np.zeros_like(phi2)
+        psi2 = np.zeros_like(psi2)
     return InitialFields(delta, phi1, phi2, psi1, psi2)
 
 
 def schedule(cfg):
-    return cosmology.kdk_schedule(cfg.a_i, cfg.a_f, cfg.nsteps, cfg.Om, cfg.OL, cfg.nLPT)
+    return cosmology.kdk_schedule(cfg.a_i, cfg.a_f, cfg.nsteps, cfg.Om, cfg.OL, cfg.nLPT, cfg.stepping)
 
 
 def lpt_momentum(a, dD1da, dD2da, psi1, psi2, cfg):

@@ -107,3 +107,43 @@ def test_schedule_structure():
     assert sched["kick_from"][0] == 0.02 and sched["kick_to"][-1] == 1.0
     np.testing.assert_allclose(sched["kick_to"][:-1], sched["kick_from"][1:])
     assert np.all(sched["beta"] < 0) and np.all(sched["alpha"] > 0)
+
+
+def test_standard_factors_edS_closed_form():
+    # Standard discretisation (App. B): alpha_p = int da / (a^2 calH), beta_delta =
+    # -(3/2) Om int da / (a calH).  In EdS (Om = 1, calH = a^-1/2) these are
+    # 2 (ai^-1/2 - af^-1/2) and -3 (af^1/2 - ai^1/2).
+    for ai, af in [(0.02, 0.069), (0.3, 0.35), (0.9, 1.0)]:
+        assert abs(cosmology.alpha_standard(ai, af, 1.0, 0.0) / (2 * (ai**-0.5 - af**-0.5)) - 1) < 1e-12
+        assert abs(cosmology.beta_standard(ai, af, 1.0, 0.0) / (-3 * (af**0.5 - ai**0.5)) - 1) < 1e-12
+
+
+def test_standard_schedule_uses_interval_integrals():
+    sched = cosmology.kdk_schedule(0.02, 1.0, 10, 0.3, 0.7, stepping="standard")
+    for k in range(10):
+        assert sched["alpha"][k] == cosmology.alpha_standard(sched["a"][k], sched["a"][k + 1], 0.3, 0.7)
+    for k in range(11):
+        assert sched["beta"][k] == cosmology.beta_standard(sched["kick_from"][k], sched["kick_to"][k], 0.3, 0.7)
+    # the modified factors differ on these long steps (not the same scheme by mistake)
+    mod = cosmology.kdk_schedule(0.02, 1.0, 10, 0.3, 0.7)
+    assert abs(mod["alpha"][0] / sched["alpha"][0] - 1) > 1e-3
+
+
+def test_standard_kdk_converges_to_linear_growth_trajectory():
+    # The same exact trajectory as above (trivial LPT frame, F = D1(a) G) with the standard
+    # factors: second-order convergence.
+    Om, OL, ai, af = 0.3, 0.7, 0.02, 1.0
+    G = np.array([[1.0, -2.0, 0.5]])
+    zero = np.zeros_like(G)
+    errs = []
+    for n in (40, 80, 160):
+        sched = cosmology.kdk_schedule(ai, af, n, Om, OL, stepping="standard")
+        s0 = -sched["D1_i"] * G
+        p0 = -ai**2 * cosmology.conformal_hubble(ai, Om, OL) * sched["dD1da_i"] * G
+        s, p, _ = scola.kdk_integrate(s0, p0, zero, zero, sched, lambda k, s: (sched["D1"][k] * G, None))
+        s_exact = -sched["D1_f"] * G
+        p_exact = -af**2 * cosmology.conformal_hubble(af, Om, OL) * sched["dD1da_f"] * G
+        errs.append(max(np.abs(s - s_exact).max() / np.abs(s_exact).max(),
+                        np.abs(p - p_exact).max() / np.abs(p_exact).max()))
+    assert errs[2] < 5e-3
+    assert errs[0] / errs[1] > 3.5 and errs[1] / errs[2] > 3.5

@@ -31,6 +31,20 @@ def test_lpt_force_mode_follows_2lpt_exactly():
         assert np.abs(b["p_res"]).max() < 1e-14 * np.abs(f.psi1).max()
 
 
+def test_zeldovich_lpt_force_mode_follows_1lpt_exactly():
+    # Zel'dovich frame (lpt_order 1): Psi2 = 0, and the LPT-force mode lands on
+    # x = q - D1(a_f) Psi1 with p_res = 0; the 2LPT run from the same noise does not.
+    cfg = _cfg(nsteps=5, lpt_order=1)
+    w = synth_inputs.white_noise(16, 5)
+    out = scola.run_scola(w, cfg, force_mode="lpt")
+    f, sch = out["fields"], out["sched"]
+    assert np.all(f.psi2 == 0.0) and np.all(f.phi2 == 0.0)
+    s_za = (-sch["D1_f"] * f.psi1).reshape(3, -1).T
+    np.testing.assert_allclose(out["s"], s_za, atol=1e-12 * np.abs(s_za).max())
+    two = scola.run_scola(w, _cfg(nsteps=5), force_mode="lpt")
+    assert np.abs(two["s"] - s_za).max() > 1e-6 * np.abs(s_za).max()
+
+
 def test_small_amplitude_residual_scales_linearly():
     # At vanishing amplitude the dynamics is linear: Psi_res / Psi_LPT is eps-independent
     # and small at large scales (the residual is the PM discretisation error).
