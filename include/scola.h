@@ -67,6 +67,12 @@ typedef enum scola_deposit_form {
                                     boxes taken in groups whose counts fit L2 */
 } scola_deposit_form;
 
+typedef enum scola_time_stepping {
+    SCOLA_STEPPING_MODIFIED = 0, /* modified KDK factors with u(a) = a^nLPT (App. B; the paper's runs) */
+    SCOLA_STEPPING_STANDARD = 1  /* standard KDK factors: interval integrals of the drift and
+                                    kick prefactors (App. B) */
+} scola_time_stepping;
+
 typedef enum scola_batch_mode {
     SCOLA_BATCH_ALL = 0,         /* every box in each launch (batched form) */
     SCOLA_BATCH_PER_TILE = 1     /* one box per launch, boxes in turn (plain per-tile form) */
@@ -108,6 +114,10 @@ typedef enum scola_batch_mode {
  *                scola_forward, scola_forward_host, scola_final_density and the
  *                host-only calls; the per-stage, inspection and adjoint calls need
  *                one batch (they return UNSUPPORTED otherwise)
+ *   time_stepping one of scola_time_stepping
+ *   lpt_order    2: initial conditions and the COLA frame from 2LPT (Eqs. 5-6, 39);
+ *                1: the Zel'dovich approximation (Psi2 = 0: first-order displacements,
+ *                frame and L+/L- from Psi1 alone, Sec. 2.2)
  *   box_first, box_count  evolve only boxes [box_first, box_first + box_count)
  *                of the tiling (both 0: all boxes).  Boxes never communicate
  *                (Sec. 3.2), so several contexts (for example one per GPU) can
@@ -129,6 +139,8 @@ typedef struct scola_params {
     int32_t box_count;
     int32_t deposit_form;        /* one of scola_deposit_form */
     int32_t batch_boxes;         /* boxes per streamed batch; 0 = as many as fit */
+    int32_t time_stepping;       /* one of scola_time_stepping */
+    int32_t lpt_order;           /* 2: 2LPT frame (the paper's runs); 1: Zel'dovich frame */
     double Om, OL, h, ns, sigma8;
     double a_i, a_f;
     double nLPT;
@@ -314,7 +326,10 @@ scola_status scola_kernel_times(const scola_ctx *ctx, double *ms_per_launch, int
 /*
  * Synchronises the stream and reports whether a kernel gave up on a bounded
  * wait since the context was created: SCOLA_OK, or SCOLA_ERR_TIMEOUT (results
- * of the affected launch are invalid; the context stays usable).
+ * of the affected launch are invalid; the context stays usable), or
+ * SCOLA_ERR_CUDA when the sorted deposit's fill pass found more particles for a
+ * key than its count pass (nothing is written past the slot range; the
+ * densities of that launch are invalid).
  */
 scola_status scola_device_status(scola_ctx *ctx);
 
@@ -325,7 +340,8 @@ int32_t scola_uses_tensor_cores(const scola_ctx *ctx);
  * Adjoint support.  With checkpointing enabled, scola_forward also stores the
  * displacements of every box particle at every force evaluation (the
  * per-step checkpoints: (nsteps + 1) x 3 x P floats) and the context keeps
- * the adjoint work arrays.  Batched form only.  Synchronises the stream.
+ * the adjoint work arrays.  Batched form, 2LPT frame and one batch only
+ * (UNSUPPORTED otherwise).  Synchronises the stream.
  */
 scola_status scola_set_checkpointing(scola_ctx *ctx, int32_t enable);
 

@@ -9,7 +9,7 @@ package fails loudly if the library has not been built.
 """
 from .binding import (  # noqa: F401
     EXPORTED, KERNEL_CLASSES, SCOLA_BATCH_ALL, SCOLA_BATCH_PER_TILE, SCOLA_DEPOSIT_ATOMIC,
-    SCOLA_DEPOSIT_AUTO, SCOLA_DEPOSIT_SORTED, SCOLA_DST_AUTO, SCOLA_DST_SIMT,
+    SCOLA_DEPOSIT_AUTO, SCOLA_DEPOSIT_SORTED, SCOLA_STEPPING_MODIFIED, SCOLA_STEPPING_STANDARD, SCOLA_DST_AUTO, SCOLA_DST_SIMT,
     SCOLA_DST_TC_3XTF32, SCOLA_DST_TC_4XTF32, ScolaError, ScolaParams, make_params,
     scola_backward, scola_box_density_noalloc, scola_box_offsets, scola_box_particle_count, scola_box_particle_ids,
     scola_create, scola_destroy, scola_device_status, scola_final_density, scola_forward,

@@ -21,6 +21,8 @@ SCOLA_DST_TC_4XTF32 = 3
 SCOLA_DST_AUTO = 2
 SCOLA_BATCH_ALL = 0
 SCOLA_BATCH_PER_TILE = 1
+SCOLA_STEPPING_MODIFIED = 0
+SCOLA_STEPPING_STANDARD = 1
 SCOLA_DEPOSIT_AUTO = 0
 SCOLA_DEPOSIT_SORTED = 1
 SCOLA_DEPOSIT_ATOMIC = 2
@@ -38,6 +40,7 @@ class ScolaParams(ctypes.Structure):
         ("mesh_ratio", c_int32), ("Ng", c_int32), ("fda_order", c_int32),
         ("dst_variant", c_int32), ("nsteps", c_int32), ("batch_mode", c_int32),
         ("box_first", c_int32), ("box_count", c_int32), ("deposit_form", c_int32), ("batch_boxes", c_int32),
+        ("time_stepping", c_int32), ("lpt_order", c_int32),
         ("Om", c_double), ("OL", c_double), ("h", c_double), ("ns", c_double),
         ("sigma8", c_double), ("a_i", c_double), ("a_f", c_double), ("nLPT", c_double),
         ("buffers", ctypes.POINTER(c_int32)),
@@ -122,12 +125,14 @@ def _ptr(x):
 def make_params(L, Np, Ntiles, Nbuf=0, mesh_ratio=1, Ng=0, nsteps=10, Om=0.3, OL=0.7, h=0.7,
                 ns=0.96, sigma8=0.8, a_i=0.02, a_f=1.0, nLPT=-2.5, fda_order=2,
                 dst_variant=SCOLA_DST_AUTO, batch_mode=SCOLA_BATCH_ALL, buffers=None, box_first=0,
-                box_count=0, deposit_form=SCOLA_DEPOSIT_AUTO, batch_boxes=0):
+                box_count=0, deposit_form=SCOLA_DEPOSIT_AUTO, batch_boxes=0,
+                time_stepping=SCOLA_STEPPING_MODIFIED, lpt_order=2):
     """Build a ScolaParams; ``buffers`` (per-tile widths) is kept alive on the struct."""
     p = ScolaParams(L=L, Np=Np, Ntiles=Ntiles, Nbuf=Nbuf, mesh_ratio=mesh_ratio, Ng=Ng,
                     fda_order=fda_order, dst_variant=dst_variant, nsteps=nsteps,
                     batch_mode=batch_mode, box_first=box_first, box_count=box_count,
                     deposit_form=deposit_form, batch_boxes=batch_boxes,
+                    time_stepping=time_stepping, lpt_order=lpt_order,
                     Om=Om, OL=OL,
                     h=h, ns=ns, sigma8=sigma8, a_i=a_i, a_f=a_f, nLPT=nLPT)
     if buffers is not None:

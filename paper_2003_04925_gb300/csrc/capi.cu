@@ -101,6 +101,9 @@ scola_status validate(const scola_params *p, std::vector<int32_t> &bufs, std::ve
     if (p->batch_mode != SCOLA_BATCH_ALL && p->batch_mode != SCOLA_BATCH_PER_TILE)
         return invalid("unknown batch_mode");
     if (p->batch_boxes < 0) return invalid("batch_boxes must be >= 0");
+    if (p->time_stepping != SCOLA_STEPPING_MODIFIED && p->time_stepping != SCOLA_STEPPING_STANDARD)
+        return invalid("unknown time_stepping");
+    if (p->lpt_order != 1 && p->lpt_order != 2) return invalid("lpt_order must be 1 or 2");
     if (p->deposit_form != SCOLA_DEPOSIT_AUTO && p->deposit_form != SCOLA_DEPOSIT_SORTED &&
         p->deposit_form != SCOLA_DEPOSIT_ATOMIC)
         return invalid("unknown deposit_form");
@@ -673,6 +676,15 @@ scola_status run_lpt(scola_ctx *c, const float *w, float *delta_out) {
     CK(launch_inv_laplacian(*c, c->ck, c->cp, 1.0f));
     CK(cudaMemcpyAsync(c->ct, c->cp, cbytes, cudaMemcpyDeviceToDevice, c->stream));
     CF(cufftExecC2R(c->plan_c2r, c->ct, c->phi1));
+    CK(launch_gradient(*c, c->phi1, c->psi1));
+    if (c->prm.lpt_order == 1) {
+        // Zel'dovich frame: no second-order potential or displacements
+        CK(cudaMemsetAsync(c->phi2, 0, sizeof(float) * (size_t)c->N3, c->stream));
+        CK(cudaMemsetAsync(c->psi2, 0, sizeof(float) * 3 * (size_t)c->N3, c->stream));
+        c->lpt_kernels = c->launches - before;
+        c->lpt_done = true;
+        return SCOLA_OK;
+    }
     for (int a = 0; a < 3; ++a) {
         CK(launch_second_derivative(*c, c->cp, c->ct, a, a));
         CF(cufftExecC2R(c->plan_c2r, c->ct, c->g[a]));
@@ -687,7 +699,6 @@ scola_status run_lpt(scola_ctx *c, const float *w, float *delta_out) {
     CF(cufftExecR2C(c->plan_r2c, c->g[3], c->ct));
     CK(launch_inv_laplacian(*c, c->ct, c->ct, invN3));
     CF(cufftExecC2R(c->plan_c2r, c->ct, c->phi2));
-    CK(launch_gradient(*c, c->phi1, c->psi1));
     CK(launch_gradient(*c, c->phi2, c->psi2));
     c->lpt_kernels = c->launches - before;
     c->lpt_done = true;
@@ -1115,6 +1126,10 @@ scola_status scola_set_checkpointing(scola_ctx *c, int32_t enable) {
     const bool on = enable != 0;
     if (on && c->prm.batch_mode == SCOLA_BATCH_PER_TILE) {
         set_error("the adjoint runs on the batched form only");
+        return SCOLA_ERR_UNSUPPORTED;
+    }
+    if (on && c->prm.lpt_order != 2) {
+        set_error("the adjoint is built for the 2LPT frame only");
         return SCOLA_ERR_UNSUPPORTED;
     }
     if (on == c->checkpointing) return SCOLA_OK;

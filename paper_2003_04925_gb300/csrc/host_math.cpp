@@ -11,6 +11,7 @@
 // Modified time stepping u(a) = a^nLPT (App. B, Eq. 60):
 //   alpha~(ai, af, aK) = aK^-nLPT int_ai^af a^(nLPT-2) / calH da   (Gauss-Legendre)
 //   beta~(ai, af, aD)  = -(3/2) Om (af^n - ai^n) / (n aD^n calH(aD))
+// Standard time stepping (App. B): alpha_p = int da/(a^2 calH), beta = -(3/2) Om int da/(a calH).
 // KDK sequence (Eq. 52, product over the n-1 inner steps, half steps at the
 // arithmetic mean): K(a0->a1/2; F(a0)), then for k = 0..n-1
 // D(ak->ak+1; p(ak+1/2)), K(ak+1/2 -> ak+3/2 or an; F(ak+1)).
@@ -213,6 +214,17 @@ double beta_tilde(double ai, double af, double aD, double Om, double OL, double 
            (nLPT * std::pow(aD, nLPT) * conformal_hubble(aD, Om, OL));
 }
 
+// Standard factors (App. B): the drift and kick prefactors integrated over the interval.
+double alpha_standard(double ai, double af, double Om, double OL) {
+    auto f = [&](double a) { return 1.0 / (a * a * conformal_hubble(a, Om, OL)); };
+    return composite_gl(f, ai, af, 16, 20);
+}
+
+double beta_standard(double ai, double af, double Om, double OL) {
+    auto f = [&](double a) { return -1.5 * Om / (a * conformal_hubble(a, Om, OL)); };
+    return composite_gl(f, ai, af, 16, 20);
+}
+
 TimeTable build_time_table(const scola_params &p) {
     TimeTable t;
     const int n = p.nsteps;
@@ -241,13 +253,17 @@ TimeTable build_time_table(const scola_params &p) {
     for (int k = 0; k <= n; ++k) {
         t.kick_from[k] = (k == 0) ? t.a[0] : t.a_half[k - 1];
         t.kick_to[k] = (k < n) ? t.a_half[k] : t.a[n];
-        t.beta[k] = beta_tilde(t.kick_from[k], t.kick_to[k], t.a[k], p.Om, p.OL, p.nLPT);
+        t.beta[k] = p.time_stepping == SCOLA_STEPPING_STANDARD
+                        ? beta_standard(t.kick_from[k], t.kick_to[k], p.Om, p.OL)
+                        : beta_tilde(t.kick_from[k], t.kick_to[k], t.a[k], p.Om, p.OL, p.nLPT);
     }
     t.alpha.resize(n);
     t.dD1.resize(n);
     t.dD2.resize(n);
     for (int k = 0; k < n; ++k) {
-        t.alpha[k] = alpha_tilde(t.a[k], t.a[k + 1], t.a_half[k], p.Om, p.OL, p.nLPT);
+        t.alpha[k] = p.time_stepping == SCOLA_STEPPING_STANDARD
+                         ? alpha_standard(t.a[k], t.a[k + 1], p.Om, p.OL)
+                         : alpha_tilde(t.a[k], t.a[k + 1], t.a_half[k], p.Om, p.OL, p.nLPT);
         t.dD1[k] = t.D1[k + 1] - t.D1[k];
         t.dD2[k] = t.D2[k + 1] - t.D2[k];
     }

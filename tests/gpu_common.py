@@ -21,8 +21,10 @@ def workload_cfg(name, **over):
 
 def oracle_cfg(kw):
     keys = ("L", "Np", "Ntiles", "Nbuf", "mesh_ratio", "Ng", "nsteps", "a_i", "a_f", "Om", "OL", "h",
-            "ns", "sigma8", "nLPT")
+            "ns", "sigma8", "nLPT", "lpt_order")
     d = {k: kw[k] for k in keys if k in kw}
+    if "time_stepping" in kw:
+        d["stepping"] = ("modified", "standard")[kw["time_stepping"]]
     if "buffers" in kw:
         d["Nbuf"] = list(kw["buffers"])
     return oscola.ScolaConfig(**d)

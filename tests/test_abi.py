@@ -54,6 +54,11 @@ def test_validation_errors_without_gpu(lib):
     bad = lib.make_params(L=100.0, Np=32, Ntiles=2, Nbuf=10)          # box larger than the lattice
     with pytest.raises(lib.ScolaError):
         lib.scola_tiling_info(bad)
+    for bad in (lib.make_params(L=100.0, Np=32, Ntiles=2, Nbuf=4, time_stepping=2),
+                lib.make_params(L=100.0, Np=32, Ntiles=2, Nbuf=4, lpt_order=3)):
+        with pytest.raises(lib.ScolaError) as e:
+            lib.scola_tiling_info(bad)
+        assert e.value.status == 1
     bad = lib.make_params(L=100.0, Np=32, Ntiles=2, Nbuf=4, batch_boxes=-1)
     with pytest.raises(lib.ScolaError) as e:
         lib.scola_tiling_info(bad)
@@ -107,14 +112,17 @@ def test_tiling_info_matches_oracle_and_table1(lib):
     assert abs(r - tiling.oversimulation(64, 2, bufs)[0]) < 1e-12
 
 
+@pytest.mark.parametrize("stepping", ["modified", "standard"])
 @pytest.mark.parametrize("Om,OL,nsteps", [(0.3, 0.7, 20), (1.0, 0.0, 10), (0.25, 0.6, 7)])
-def test_time_table_matches_oracle(lib, Om, OL, nsteps):
+def test_time_table_matches_oracle(lib, Om, OL, nsteps, stepping):
     # Two independent FP64 routes (Dormand-Prince + Gauss-Legendre here, RK4 + adaptive
-    # Simpson in the oracle) to the App. B coefficients must agree to ~1e-10.
+    # Simpson in the oracle) to the App. B coefficients must agree to ~1e-10, for the
+    # modified and the standard time factors.
     from oracle import cosmology
-    prm = lib.make_params(L=100.0, Np=32, Ntiles=2, Nbuf=4, nsteps=nsteps, Om=Om, OL=OL)
+    code = {"modified": lib.SCOLA_STEPPING_MODIFIED, "standard": lib.SCOLA_STEPPING_STANDARD}[stepping]
+    prm = lib.make_params(L=100.0, Np=32, Ntiles=2, Nbuf=4, nsteps=nsteps, Om=Om, OL=OL, time_stepping=code)
     t = lib.scola_time_table(prm)
-    o = cosmology.kdk_schedule(0.02, 1.0, nsteps, Om, OL)
+    o = cosmology.kdk_schedule(0.02, 1.0, nsteps, Om, OL, stepping=stepping)
     for k_lib, k_or in [("a_force", "a"), ("D1", "D1"), ("D2", "D2"), ("beta", "beta"),
                         ("alpha", "alpha"), ("dD1", "dD1"), ("dD2", "dD2")]:
         np.testing.assert_allclose(t[k_lib], o[k_or], rtol=1e-9, atol=1e-13, err_msg=k_lib)

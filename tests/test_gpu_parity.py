@@ -474,3 +474,26 @@ def test_power_spectrum_matches_oracle():
         np.testing.assert_allclose(pk[full], pk_o[full], rtol=2e-5)
     assert n.sum() == 32**3          # the linear bins hold every mode of the grid once
     sim.close()
+
+
+@pytest.mark.parametrize("variant", ["simt", "tc"])
+@pytest.mark.parametrize("option", ["standard_stepping", "zeldovich"])
+def test_forward_options_match_oracle(option, variant):
+    # The standard KDK time factors (App. B) and the Zel'dovich frame (first-order LPT
+    # only) on the 32^3 workload: the same acceptance bounds as the default form.
+    over = {"standard_stepping": dict(time_stepping=1), "zeldovich": dict(lpt_order=1)}[option]
+    kw = dict(CASES_PM["plain_32"], **over)
+    cfg = oracle_cfg(kw)
+    w = synth_inputs.white_noise(cfg.Np, 1)
+    x, p, sim = _forward(kw, w, variant)
+    sim.close()
+    ref = oscola.run_scola(w, cfg)
+    dg = oscola.box_geometry(cfg, 0).dg
+    rms = np.sqrt(np.mean(np.sum(periodic_diff(x, ref["x"], cfg.L) ** 2, axis=1))) / dg
+    prel = np.sqrt(np.mean(np.sum((p - ref["p"]) ** 2, 1)) / np.mean(np.sum(ref["p"] ** 2, 1)))
+    print("forward %s %s: position RMS %.3e PM cells, momentum RMS %.3e relative" % (option, variant, rms, prel))
+    assert rms <= 1e-3, rms
+    assert prel <= 1e-3, prel
+    # the option changes the run: against the default form the difference is far above rounding
+    base = oscola.run_scola(w, oracle_cfg(CASES_PM["plain_32"]))
+    assert np.sqrt(np.mean(np.sum(periodic_diff(base["x"], ref["x"], cfg.L) ** 2, axis=1))) / dg > 1e-2
