@@ -54,6 +54,8 @@ class ScolaConfig:
     nLPT: float = -2.5
     stepping: str = "modified"   # KDK time factors: "modified" (u = a^nLPT) or "standard" (App. B)
     lpt_order: int = 2           # 2: 2LPT frame; 1: Zel'dovich frame (phi2 = Psi2 = 0)
+    a_final: list = None         # per-tile final scale factors (box-id order), None: a_f for all
+                                 # (light-cone scheduling, Sec. 5: tiles need not share a_f)
 
     @property
     def Ntile(self):
@@ -121,6 +123,17 @@ def schedule(cfg):
     return cosmology.kdk_schedule(cfg.a_i, cfg.a_f, cfg.nsteps, cfg.Om, cfg.OL, cfg.nLPT, cfg.stepping)
 
 
+def box_final_a(cfg, b):
+    """The final scale factor of box b: its entry of a_final, else a_f."""
+    return cfg.a_f if cfg.a_final is None else float(cfg.a_final[b])
+
+
+def box_schedule(cfg, b):
+    """KDK coefficients of box b: nsteps steps linear in a from a_i to its final a."""
+    return cosmology.kdk_schedule(cfg.a_i, box_final_a(cfg, b), cfg.nsteps, cfg.Om, cfg.OL, cfg.nLPT,
+                                  cfg.stepping)
+
+
 def lpt_momentum(a, dD1da, dD2da, psi1, psi2, cfg):
     """p_LPT(a) = a^2 calH(a) (-dD1/da Psi1 + dD2/da Psi2)  (Eq. 55, t = a)."""
     return a * a * cosmology.conformal_hubble(a, cfg.Om, cfg.OL) * (-dD1da * psi1 + dD2da * psi2)
@@ -153,8 +166,11 @@ def evolve_box(cfg, b, fields, sched, force_mode="pm", delta_fn=None, phi_bc_fn=
     and ``phi_bc_fn(k)`` override the interior density and the padded Phi_BCs
     at force evaluation k (consistency pin of Sec. 4.3).
     Returns a dict: ids (global ids, box order), s, p (final, L+ applied),
-    p_res, geometry, deposited (per step), clamped (per step).
+    p_res, geometry, deposited (per step), clamped (per step).  With per-tile final
+    scale factors (cfg.a_final) the box follows its own schedule (``sched`` unused).
     """
+    if cfg.a_final is not None:
+        sched = box_schedule(cfg, b)
     g = box_geometry(cfg, b)
     ids = tiling.box_global_ids(cfg.Np, cfg.Ntiles, g.t, g.Nbuf)
     psi1 = fields.psi1.reshape(3, -1)[:, ids].T
@@ -177,7 +193,7 @@ def evolve_box(cfg, b, fields, sched, force_mode="pm", delta_fn=None, phi_bc_fn=
         return r["F"], (r["deposited"], int(r["clamped"].sum()))
 
     s, p, diags = kdk_integrate(s0, p0, psi1, psi2, sched, force)
-    p_final = p + lpt_momentum(cfg.a_f, sched["dD1da_f"], sched["dD2da_f"], psi1, psi2, cfg)
+    p_final = p + lpt_momentum(box_final_a(cfg, b), sched["dD1da_f"], sched["dD2da_f"], psi1, psi2, cfg)
     out = {"ids": ids, "s": s, "p": p_final, "p_res": p, "geometry": g}
     if force_mode == "pm":
         out["deposited"] = [d[0] for d in diags]

@@ -45,6 +45,26 @@ def test_zeldovich_lpt_force_mode_follows_1lpt_exactly():
     assert np.abs(two["s"] - s_za).max() > 1e-6 * np.abs(s_za).max()
 
 
+def test_light_cone_lpt_force_mode_lands_on_each_tiles_final_a():
+    # Per-tile final scale factors (light-cone scheduling): in the LPT-force mode every
+    # tile lands exactly on x_LPT at its own a_f, with p = p_LPT(a_f) (Eqs. 39, 55).
+    from oracle import cosmology
+    a_fin = [1.0, 0.8, 0.6, 0.45, 0.9, 0.7, 0.55, 0.35]
+    cfg = _cfg(nsteps=5, a_final=a_fin)
+    w = synth_inputs.white_noise(16, 5)
+    out = scola.run_scola(w, cfg, force_mode="lpt")
+    f = out["fields"]
+    for b, r in enumerate(out["boxes"]):
+        af = a_fin[b]
+        g = cosmology.growth_factors(np.array([af]), cfg.Om, cfg.OL)
+        psi1 = f.psi1.reshape(3, -1)[:, r["ids"]].T
+        psi2 = f.psi2.reshape(3, -1)[:, r["ids"]].T
+        s_lpt = -g["D1"][0] * psi1 + g["D2"][0] * psi2
+        np.testing.assert_allclose(r["s"], s_lpt, atol=1e-9 * np.abs(s_lpt).max())
+        p_lpt = af**2 * cosmology.conformal_hubble(af, cfg.Om, cfg.OL) * (-g["dD1da"][0] * psi1 + g["dD2da"][0] * psi2)
+        np.testing.assert_allclose(r["p"], p_lpt, atol=1e-9 * np.abs(p_lpt).max())
+
+
 def test_small_amplitude_residual_scales_linearly():
     # At vanishing amplitude the dynamics is linear: Psi_res / Psi_LPT is eps-independent
     # and small at large scales (the residual is the PM discretisation error).
