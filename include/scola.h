@@ -115,6 +115,13 @@ typedef enum scola_batch_mode {
  *                host-only calls; the per-stage, inspection and adjoint calls need
  *                one batch (they return UNSUPPORTED otherwise)
  *   time_stepping one of scola_time_stepping
+ *   a_final      optional per-tile final scale factors (host array of Ntiles^3, box-id
+ *                order, each > a_i), copied by scola_create; NULL = a_f for every tile.
+ *                Boxes never communicate, so each tile may stop at its own scale factor
+ *                (light-cone scheduling, Sec. 5): tile t takes nsteps steps linear in a
+ *                from a_i to a_final[t], and its particles leave scola_forward at that
+ *                time (positions and momenta with L+ at a_final[t]).  All boxes still go
+ *                through each launch together.  The adjoint needs a common a_f
  *   lpt_order    2: initial conditions and the COLA frame from 2LPT (Eqs. 5-6, 39);
  *                1: the Zel'dovich approximation (Psi2 = 0: first-order displacements,
  *                frame and L+/L- from Psi1 alone, Sec. 2.2)
@@ -145,6 +152,7 @@ typedef struct scola_params {
     double a_i, a_f;
     double nLPT;
     const int32_t *buffers;
+    const double *a_final;       /* per-tile final scale factors (light-cone scheduling) or NULL */
 } scola_params;
 
 typedef struct scola_ctx scola_ctx;

@@ -43,7 +43,7 @@ class ScolaParams(ctypes.Structure):
         ("time_stepping", c_int32), ("lpt_order", c_int32),
         ("Om", c_double), ("OL", c_double), ("h", c_double), ("ns", c_double),
         ("sigma8", c_double), ("a_i", c_double), ("a_f", c_double), ("nLPT", c_double),
-        ("buffers", ctypes.POINTER(c_int32)),
+        ("buffers", ctypes.POINTER(c_int32)), ("a_final", ctypes.POINTER(c_double)),
     ]
 
 
@@ -126,7 +126,7 @@ def make_params(L, Np, Ntiles, Nbuf=0, mesh_ratio=1, Ng=0, nsteps=10, Om=0.3, OL
                 ns=0.96, sigma8=0.8, a_i=0.02, a_f=1.0, nLPT=-2.5, fda_order=2,
                 dst_variant=SCOLA_DST_AUTO, batch_mode=SCOLA_BATCH_ALL, buffers=None, box_first=0,
                 box_count=0, deposit_form=SCOLA_DEPOSIT_AUTO, batch_boxes=0,
-                time_stepping=SCOLA_STEPPING_MODIFIED, lpt_order=2):
+                time_stepping=SCOLA_STEPPING_MODIFIED, lpt_order=2, a_final=None):
     """Build a ScolaParams; ``buffers`` (per-tile widths) is kept alive on the struct."""
     p = ScolaParams(L=L, Np=Np, Ntiles=Ntiles, Nbuf=Nbuf, mesh_ratio=mesh_ratio, Ng=Ng,
                     fda_order=fda_order, dst_variant=dst_variant, nsteps=nsteps,
@@ -139,6 +139,10 @@ def make_params(L, Np, Ntiles, Nbuf=0, mesh_ratio=1, Ng=0, nsteps=10, Om=0.3, OL
         arr = (c_int32 * len(buffers))(*[int(b) for b in buffers])
         p._buffers_keepalive = arr
         p.buffers = ctypes.cast(arr, ctypes.POINTER(c_int32))
+    if a_final is not None:
+        arr = (c_double * len(a_final))(*[float(a) for a in a_final])
+        p._a_final_keepalive = arr
+        p.a_final = ctypes.cast(arr, ctypes.POINTER(c_double))
     return p
 
 

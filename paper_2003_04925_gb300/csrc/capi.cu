@@ -39,6 +39,8 @@ struct BoxGeom {                         // one box of the tiling: Np,sCOLA, Ng,
 };
 
 struct scola_ctx : public Ctx {
+    std::vector<double> a_final;         // per-tile final scale factors (empty: a_f for all)
+    float *all_coef = nullptr, *all_coefL = nullptr;   // every context box's coefficients
     std::vector<BoxGeom> tiling_geo;     // every box of the tiling
     std::vector<BoxGeom> ctx_geo;        // the context's boxes
     cudaStream_t cap_stream = nullptr;   // stream used only to capture the evolution graph
@@ -104,6 +106,12 @@ scola_status validate(const scola_params *p, std::vector<int32_t> &bufs, std::ve
     if (p->time_stepping != SCOLA_STEPPING_MODIFIED && p->time_stepping != SCOLA_STEPPING_STANDARD)
         return invalid("unknown time_stepping");
     if (p->lpt_order != 1 && p->lpt_order != 2) return invalid("lpt_order must be 1 or 2");
+    if (p->a_final) {
+        const long long nt = (long long)p->Ntiles * p->Ntiles * p->Ntiles;
+        for (long long t = 0; t < nt; ++t)
+            if (!(p->a_final[t] > p->a_i) || !std::isfinite(p->a_final[t]))
+                return invalid("every a_final must be a finite scale factor above a_i");
+    }
     if (p->deposit_form != SCOLA_DEPOSIT_AUTO && p->deposit_form != SCOLA_DEPOSIT_SORTED &&
         p->deposit_form != SCOLA_DEPOSIT_ATOMIC)
         return invalid("unknown deposit_form");
@@ -341,6 +349,18 @@ scola_status put(T *dst, const std::vector<T> &src) {
     return SCOLA_OK;
 }
 
+// Per-tile final scale factors: the batch's boxes' coefficient tables into the fixed buffers
+// the kernels (and the captured graph) read.
+scola_status bind_coefficients(scola_ctx *c, int first, int count) {
+    if (!c->coef) return SCOLA_OK;
+    const size_t per = (size_t)c->coef_nk * 8;
+    CK(cudaMemcpyAsync(c->coef, c->all_coef + (size_t)first * per, sizeof(float) * per * count,
+                       cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->coefL, c->all_coefL + 2 * (size_t)first, sizeof(float) * 2 * count,
+                       cudaMemcpyDeviceToDevice, c->stream));
+    return SCOLA_OK;
+}
+
 // Makes batch k the one the kernels see.  A batch with the shape of the bound one only
 // changes the boxes' tile coordinates (a device-to-device copy of its box descriptors,
 // ordered on the stream, so the captured graph stays valid); another shape re-uploads
@@ -356,6 +376,7 @@ scola_status bind_batch(scola_ctx *c, int k, bool force = false) {
         std::vector<BoxGeom> b(c->ctx_geo.begin() + first, c->ctx_geo.begin() + first + count);
         if (same_shape(a, b)) {
             CK(cudaMemcpyAsync(c->boxes, src, sizeof(BoxDesc) * count, cudaMemcpyDeviceToDevice, c->stream));
+            CS(bind_coefficients(c, first, count));
             for (int i = 0; i < count; ++i) c->boxes_h[i] = c->all_boxes_h[first + i];
             c->bound_batch = k;
             return SCOLA_OK;
@@ -405,9 +426,12 @@ scola_status bind_batch(scola_ctx *c, int k, bool force = false) {
     c->M = bp.M;
     c->MP = bp.MP;
     c->SH = bp.SH;
+    CS(bind_coefficients(c, first, count));
     c->bound_batch = k;
     return SCOLA_OK;
 }
+
+scola_status fill_light_cone_tables(scola_ctx *c);
 
 scola_status build(scola_ctx *c, const std::vector<BoxGeom> &all_geo) {
     const scola_params &p = c->prm;
@@ -644,6 +668,11 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &all_geo) {
     CS(dev_alloc(&c->phi, MP));
     CS(dev_alloc(&c->shell, SH));
     CK(cudaMemset(c->phi, 0, sizeof(float) * MP));
+    if (!c->a_final.empty()) {
+        CS(fill_light_cone_tables(c));
+        CS(dev_alloc(&c->coef, (long long)max_count * c->coef_nk * 8));
+        CS(dev_alloc(&c->coefL, 2LL * max_count));
+    }
     CS(bind_batch(c, 0, true));
 
     CK(init_pm_kernels(*c));
@@ -725,6 +754,42 @@ KickDrift forward_kick(const TimeTable &t, int k) {
     KickDrift kd = kick_drift_coefficients(t, k);
     kd.kF = (float)(t.beta[k] * t.D1[k]);
     return kd;
+}
+
+// Per-tile final scale factors: every context box's FP64 time table (one per distinct a_final)
+// reduced to the FP32 coefficients the kernels read (layout in Ctx::coef).
+scola_status fill_light_cone_tables(scola_ctx *c) {
+    const int n = c->prm.nsteps;
+    c->coef_nk = n + 1;
+    std::map<double, TimeTable> tabs;
+    std::vector<float> coef((size_t)c->nbox_all * c->coef_nk * 8, 0.0f), coefL(2 * (size_t)c->nbox_all);
+    for (int i = 0; i < c->nbox_all; ++i) {
+        const double af = c->a_final[c->box0 + i];
+        auto it = tabs.find(af);
+        if (it == tabs.end()) {
+            scola_params q = c->prm;
+            q.a_f = af;
+            it = tabs.emplace(af, build_time_table(q)).first;
+        }
+        const TimeTable &t = it->second;
+        for (int k = 0; k <= n; ++k) {
+            const KickDrift kd = forward_kick(t, k);
+            float *e = &coef[((size_t)i * c->coef_nk + k) * 8];
+            e[0] = kd.kF;
+            e[1] = kd.k1;
+            e[2] = kd.k2;
+            e[3] = kd.alpha;
+            e[4] = kd.d1;
+            e[5] = kd.d2;
+            e[6] = (float)(1.0 / t.D1[k]);
+        }
+        const double pref = af * af * t.Hconf_f;
+        coefL[2 * i] = (float)(-pref * t.dD1da_f);
+        coefL[2 * i + 1] = (float)(pref * t.dD2da_f);
+    }
+    CS(upload(&c->all_coef, coef));
+    CS(upload(&c->all_coefL, coefL));
+    return SCOLA_OK;
 }
 
 // Restricts every work list to one box; restores on destruction.
@@ -839,9 +904,9 @@ scola_status enqueue_evolution_per_tile(scola_ctx *c) {
         CK(launch_shell(*c));
         CK(launch_pad(*c, 1.0f));
         for (int k = 0; k <= n; ++k) {
-            CK(launch_deposit(*c, c->part, c->P, (float)(1.0 / c->tt.D1[k])));
+            CK(launch_deposit(*c, c->part, c->P, (float)(1.0 / c->tt.D1[k]), nullptr, false, k));
             CK(launch_poisson(*c));
-            CK(launch_kick_drift(*c, forward_kick(c->tt, k)));
+            CK(launch_kick_drift(*c, forward_kick(c->tt, k), false, k));
         }
     }
     return SCOLA_OK;
@@ -870,7 +935,7 @@ scola_status enqueue_evolution(scola_ctx *c) {
             CK(cudaMemcpyAsync(c->ckpt + (size_t)k * 3 * c->P, c->part, sizeof(float) * 3 * (size_t)c->P,
                                cudaMemcpyDeviceToDevice, c->stream));
         CK(mark());
-        CK(launch_deposit(*c, c->part, c->P, (float)(1.0 / c->tt.D1[k]), nullptr, fused && k > 0));
+        CK(launch_deposit(*c, c->part, c->P, (float)(1.0 / c->tt.D1[k]), nullptr, fused && k > 0, k));
         if (fused && k < n) CK(clear_key_counts(*c));
         CK(mark());
         if (c->profiling) {
@@ -881,7 +946,7 @@ scola_status enqueue_evolution(scola_ctx *c) {
         } else {
             CK(launch_poisson(*c));
         }
-        CK(launch_kick_drift(*c, forward_kick(c->tt, k), fused));
+        CK(launch_kick_drift(*c, forward_kick(c->tt, k), fused, k));
         CK(mark());
     }
     return SCOLA_OK;
@@ -991,6 +1056,9 @@ scola_status scola_create(const scola_params *params, void *stream, scola_ctx **
     c->prm = *params;
     c->prm.buffers = nullptr;
     c->buffers = bufs;
+    if (params->a_final)
+        c->a_final.assign(params->a_final, params->a_final + (long long)params->Ntiles * params->Ntiles * params->Ntiles);
+    c->prm.a_final = nullptr;
     c->stream = reinterpret_cast<cudaStream_t>(stream);
     scola_status s = build(c, geo);
     if (s != SCOLA_OK) {
@@ -1012,7 +1080,7 @@ void scola_destroy(scola_ctx *c) {
         cufftDestroy(c->plan_r2c);
         cufftDestroy(c->plan_c2r);
     }
-    void *ptrs[] = {c->boxes, c->all_boxes, c->tables, c->table_arena, c->pchunks, c->tchunks, c->shchunks,
+    void *ptrs[] = {c->boxes, c->all_boxes, c->all_coef, c->all_coefL, c->coef, c->coefL, c->tables, c->table_arena, c->pchunks, c->tchunks, c->shchunks,
                     c->zitems, c->citems, c->mchunks, c->ppchunks, c->tc_tiles, c->dev_err, c->ckpt,
                     c->adj, c->lamG, c->lam_phi_pad, c->adj_in, c->adj_out, c->lam_shell, c->lamPsi1,
                     c->lamPsi2, c->lam_phi1, c->lam_phi2, c->d2, c->lam_d2, c->part, c->dep_acc, c->kcount,
@@ -1126,6 +1194,10 @@ scola_status scola_set_checkpointing(scola_ctx *c, int32_t enable) {
     const bool on = enable != 0;
     if (on && c->prm.batch_mode == SCOLA_BATCH_PER_TILE) {
         set_error("the adjoint runs on the batched form only");
+        return SCOLA_ERR_UNSUPPORTED;
+    }
+    if (on && !c->a_final.empty()) {
+        set_error("the adjoint needs a common final scale factor (no a_final)");
         return SCOLA_ERR_UNSUPPORTED;
     }
     if (on && c->prm.lpt_order != 2) {

@@ -53,6 +53,12 @@ __device__ __forceinline__ void decode_local(int local, int n, int &i, int &j, i
     i = t / n;
 }
 
+// Per-tile final scale factors: box b's FP32 coefficients at force evaluation k (see Ctx::coef),
+// or null when the launch uses uniform scalars.
+__device__ __forceinline__ const float *box_coef(const float *coef, int box, int k, int nk) {
+    return coef ? coef + ((long long)box * nk + k) * 8 : nullptr;
+}
+
 // Sorted deposit: the interior mesh of a box is cut into bricks of kBrick^3 cells.
 constexpr int kBrick = 16;
 

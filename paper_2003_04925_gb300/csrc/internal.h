@@ -144,6 +144,12 @@ struct Ctx {
     int deposit_threads = 512;                        // threads per brick CTA of the sorted form
     bool deposit_split = false;                       // sorted form: 32-bit halves of the counts
     bool tuned = false;                               // the autotuner has picked the forms above
+    // per-tile final scale factors: per box of the bound batch and force evaluation k, the
+    // FP32 coefficients [kF (forward, x D1), k1, k2, alpha, d1, d2, 1/D1, 0] at
+    // coef[(box (nsteps + 1) + k) 8], and the L+ factors [c1, c2] at coefL[2 box]; null
+    // when every tile ends at a_f (the kernels then take the uniform scalars)
+    float *coef = nullptr, *coefL = nullptr;
+    int coef_nk = 0;
     int *kcount = nullptr, *koffs = nullptr, *kcursor = nullptr;
     float4 *sentries = nullptr;
     Chunk *sbricks = nullptr;  int n_sbricks = 0;
@@ -191,11 +197,13 @@ cudaError_t launch_pad(Ctx &c, float D1);
 // form, batched graph); otherwise the deposit counts them itself
 // inv_D1: the Poisson source is delta / D1(a_K) minus the boundary term of the unscaled
 // shell, so that the solve gives Phi / D1 (delta_out receives delta itself)
+// k >= 0: force evaluation k of the evolution (with per-tile final scale factors the
+// kernels take each box's 1/D1 from the coefficient table); k < 0: inv_D1 for every box
 cudaError_t launch_deposit(Ctx &c, const float *s, long long stride, float inv_D1, float *delta_out = nullptr,
-                           bool counted = false);
-cudaError_t launch_deposit_atomic(Ctx &c, const float *s, long long stride, float inv_D1, float *delta_out);
+                           bool counted = false, int k = -1);
+cudaError_t launch_deposit_atomic(Ctx &c, const float *s, long long stride, float inv_D1, float *delta_out, int k);
 cudaError_t launch_deposit_sorted(Ctx &c, const float *s, long long stride, float inv_D1, float *delta_out,
-                                  bool counted);
+                                  bool counted, int k);
 cudaError_t clear_key_counts(Ctx &c);
 cudaError_t init_pm_kernels(Ctx &c);
 cudaError_t init_deposit_kernels();
@@ -216,7 +224,7 @@ cudaError_t launch_interp(Ctx &c, const float *s, long long stride, float *F, fl
 cudaError_t launch_scaled_copy(Ctx &c, const float *in, float *out, long long n, float a);
 // count_keys: also count the sorted deposit's keys of the drifted particles (into cleared
 // counts) for the next force evaluation
-cudaError_t launch_kick_drift(Ctx &c, const KickDrift &kd, bool count_keys = false);
+cudaError_t launch_kick_drift(Ctx &c, const KickDrift &kd, bool count_keys = false, int k = -1);
 cudaError_t launch_scatter(Ctx &c, float *x, float *p);
 cudaError_t launch_box_ids(Ctx &c, int64_t *gid);
 cudaError_t launch_final_density(Ctx &c, const float *x, float *delta);

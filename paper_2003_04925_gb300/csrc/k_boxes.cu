@@ -87,9 +87,13 @@ k_shell(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
 __global__ void __launch_bounds__(kChunk)
 k_scatter(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
           const float *__restrict__ part, long long P, int Np, int Ntile, float dq, float L,
-          float c1, float c2, float *__restrict__ x, float *__restrict__ p) {
+          float c1, float c2, const float *__restrict__ coefL, float *__restrict__ x, float *__restrict__ p) {
     const Chunk ch = chunks[blockIdx.x];
     const BoxDesc &B = boxes[ch.box];
+    if (coefL) {                       // L+ at this tile's own final scale factor
+        c1 = coefL[2 * ch.box];
+        c2 = coefL[2 * ch.box + 1];
+    }
     const int lt = ch.start + threadIdx.x;
     if (lt >= Ntile * Ntile * Ntile) return;
     int ti, tj, tk;
@@ -194,7 +198,7 @@ cudaError_t launch_scatter(Ctx &c, float *x, float *p) {
     k_scatter<<<c.n_tchunks, kChunk, 0, c.stream>>>(c.boxes, c.tchunks, c.part, c.P, c.Np, Ntile,
                                                      (float)c.dq, (float)c.L,
                                                      (float)(-pref * c.tt.dD1da_f),
-                                                     (float)(pref * c.tt.dD2da_f), x, p);
+                                                     (float)(pref * c.tt.dD2da_f), c.coefL, x, p);
     ++c.launches;
     return cudaGetLastError();
 }

@@ -80,11 +80,13 @@ constexpr int kSourceChunks = 4;
 __global__ void __launch_bounds__(64 * kSourceChunks)
 k_density_source(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks, int nchunks,
                  const unsigned long long *__restrict__ acc, long long acc_base, const float *__restrict__ phi_pad,
-                 float inv_D1, float *__restrict__ out, float *__restrict__ delta_out) {
+                 float inv_D1, const float *__restrict__ coef, int kstep, int nk, float *__restrict__ out,
+                 float *__restrict__ delta_out) {
     const int ci = blockIdx.x * kSourceChunks + (threadIdx.x >> 6);
     if (ci >= nchunks) return;
     const Chunk ch = chunks[ci];
     const BoxDesc &B = boxes[ch.box];
+    if (const float *cf = box_coef(coef, ch.box, kstep, nk)) inv_D1 = cf[6];
     const int Ng = B.Ng;
     const long long ng3 = (long long)Ng * Ng * Ng;
     const int cell0 = ch.start + 4 * (threadIdx.x & 63);
@@ -144,7 +146,9 @@ k_density_source(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ ch
 
 }  // namespace
 
-cudaError_t launch_deposit_atomic(Ctx &c, const float *s, long long stride, float inv_D1, float *delta_out) {
+cudaError_t launch_deposit_atomic(Ctx &c, const float *s, long long stride, float inv_D1, float *delta_out,
+                                  int kstep) {
+    const float *coef = kstep >= 0 ? c.coef : nullptr;
     // box groups of the current view: the precomputed groups, or the one box of the
     // per-tile form (whose lists the view has already restricted)
     const bool one = c.view_box >= 0;
@@ -165,7 +169,7 @@ cudaError_t launch_deposit_atomic(Ctx &c, const float *s, long long stride, floa
         }
         if (nmch > 0) {
             k_density_source<<<(nmch + kSourceChunks - 1) / kSourceChunks, 64 * kSourceChunks, 0, c.stream>>>(
-                c.boxes, mch, nmch, c.dep_acc, base, c.phi, inv_D1, c.work2, delta_out);
+                c.boxes, mch, nmch, c.dep_acc, base, c.phi, inv_D1, coef, kstep, c.coef_nk, c.work2, delta_out);
             ++c.launches;
             if ((e = cudaGetLastError()) != cudaSuccess) return step_error("atomic deposit: source launch", e);
         }
@@ -180,9 +184,9 @@ cudaError_t launch_deposit_atomic(Ctx &c, const float *s, long long stride, floa
 
 // The deposit in the form the context selected (both give bit-identical delta').
 cudaError_t launch_deposit(Ctx &c, const float *s, long long stride, float inv_D1, float *delta_out,
-                           bool counted) {
-    return c.deposit_form == 0 ? launch_deposit_sorted(c, s, stride, inv_D1, delta_out, counted)
-                               : launch_deposit_atomic(c, s, stride, inv_D1, delta_out);
+                           bool counted, int k) {
+    return c.deposit_form == 0 ? launch_deposit_sorted(c, s, stride, inv_D1, delta_out, counted, k)
+                               : launch_deposit_atomic(c, s, stride, inv_D1, delta_out, k);
 }
 
 }  // namespace scola

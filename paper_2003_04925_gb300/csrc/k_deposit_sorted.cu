@@ -181,11 +181,13 @@ template <int kBrickThreads, bool kSplit>
 __global__ void __launch_bounds__(kBrickThreads, kBrickThreads == 256 ? 5 : 3)
 k_sort_brick(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ items, const int *__restrict__ cnt,
              const int *__restrict__ offs, const float4 *__restrict__ entries, const float *__restrict__ phi_pad,
-             float inv_D1, float *__restrict__ out, float *__restrict__ delta_out) {
+             float inv_D1, const float *__restrict__ coef, int kstep, int nk, float *__restrict__ out,
+             float *__restrict__ delta_out) {
     __shared__ __align__(16) unsigned long long acc[kBrickCells];
     __shared__ int seg_o[kSegments], seg_start[kSegments + 1];
     const Chunk it = items[blockIdx.x];
     const BoxDesc &B = boxes[it.box];
+    if (const float *cf = box_coef(coef, it.box, kstep, nk)) inv_D1 = cf[6];
     const int Ng = B.Ng, nbe = B.nbe, nb = nbe - 1;
     const int tid = threadIdx.x;
     const int bz = it.start % nb, bt = it.start / nb, by = bt % nb, bx = bt / nb;
@@ -319,7 +321,8 @@ cudaError_t clear_key_counts(Ctx &c) {
 }
 
 cudaError_t launch_deposit_sorted(Ctx &c, const float *s, long long stride, float inv_D1, float *delta_out,
-                                  bool counted) {
+                                  bool counted, int kstep) {
+    const float *coef = kstep >= 0 ? c.coef : nullptr;
     // the boxes of the current view: all, or one in the per-tile form
     const int box0 = c.view_box >= 0 ? c.view_box : 0;
     const int nbox = c.view_box >= 0 ? 1 : c.nboxes;
@@ -340,7 +343,7 @@ cudaError_t launch_deposit_sorted(Ctx &c, const float *s, long long stride, floa
     if ((e = cudaGetLastError()) != cudaSuccess) return step_error("sorted deposit: fill launch", e);
 #define SCOLA_BRICK(T, SPLIT)                                                                             \
     k_sort_brick<T, SPLIT><<<c.n_sbricks, T, 0, c.stream>>>(c.boxes, c.sbricks, c.kcount, c.koffs, c.sentries, \
-                                                            c.phi, inv_D1, c.work2, delta_out)
+                                                            c.phi, inv_D1, coef, kstep, c.coef_nk, c.work2, delta_out)
     if (c.deposit_threads == 256) {
         if (c.deposit_split) SCOLA_BRICK(256, true);
         else SCOLA_BRICK(256, false);

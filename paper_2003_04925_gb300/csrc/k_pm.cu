@@ -278,9 +278,17 @@ k_interp(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
 __global__ void __launch_bounds__(kChunk, 5)
 k_kick_drift(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
              float *__restrict__ part, long long P, const float *__restrict__ phi, KickDrift kd,
-             int *__restrict__ kcount) {
+             int *__restrict__ kcount, const float *__restrict__ coef, int k, int nk) {
     const Chunk ch = chunks[blockIdx.x];
     const BoxDesc &B = boxes[ch.box];
+    if (const float *c = box_coef(coef, ch.box, k, nk)) {     // this box's own time factors
+        kd.kF = c[0];
+        kd.k1 = c[1];
+        kd.k2 = c[2];
+        kd.alpha = c[3];
+        kd.d1 = c[4];
+        kd.d2 = c[5];
+    }
     const int Nsc = B.Nsc;
     const int local = ch.start + threadIdx.x;
     int key = -1;
@@ -445,9 +453,10 @@ cudaError_t launch_scaled_copy(Ctx &c, const float *in, float *out, long long n,
     return cudaGetLastError();
 }
 
-cudaError_t launch_kick_drift(Ctx &c, const KickDrift &kd, bool count_keys) {
+cudaError_t launch_kick_drift(Ctx &c, const KickDrift &kd, bool count_keys, int k) {
     k_kick_drift<<<c.n_pchunks, kChunk, 0, c.stream>>>(c.boxes, c.pchunks, c.part, c.P, c.phi, kd,
-                                                        count_keys && kd.drift ? c.kcount : nullptr);
+                                                        count_keys && kd.drift ? c.kcount : nullptr,
+                                                        k >= 0 ? c.coef : nullptr, k, c.coef_nk);
     ++c.launches;
     return cudaGetLastError();
 }

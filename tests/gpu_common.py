@@ -21,7 +21,7 @@ def workload_cfg(name, **over):
 
 def oracle_cfg(kw):
     keys = ("L", "Np", "Ntiles", "Nbuf", "mesh_ratio", "Ng", "nsteps", "a_i", "a_f", "Om", "OL", "h",
-            "ns", "sigma8", "nLPT", "lpt_order")
+            "ns", "sigma8", "nLPT", "lpt_order", "a_final")
     d = {k: kw[k] for k in keys if k in kw}
     if "time_stepping" in kw:
         d["stepping"] = ("modified", "standard")[kw["time_stepping"]]

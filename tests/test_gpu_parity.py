@@ -497,3 +497,33 @@ def test_forward_options_match_oracle(option, variant):
     # the option changes the run: against the default form the difference is far above rounding
     base = oscola.run_scola(w, oracle_cfg(CASES_PM["plain_32"]))
     assert np.sqrt(np.mean(np.sum(periodic_diff(base["x"], ref["x"], cfg.L) ** 2, axis=1))) / dg > 1e-2
+
+
+@pytest.mark.parametrize("variant", ["simt", "tc"])
+def test_light_cone_forward_matches_oracle(variant):
+    # Per-tile final scale factors (light-cone scheduling): every tile of the 32^3 workload
+    # stops at its own a_f; the run matches the oracle's, and the tile that ends at the
+    # common a_f equals the uniform run's tile bit for bit.
+    a_fin = [1.0, 0.8, 0.6, 0.45, 0.9, 0.7, 0.55, 0.35]
+    base = CASES_PM["plain_32"]
+    kw = dict(base, a_final=a_fin)
+    cfg = oracle_cfg(kw)
+    w = synth_inputs.white_noise(cfg.Np, 1)
+    x, p, sim = _forward(kw, w, variant)
+    sim.close()
+    ref = oscola.run_scola(w, cfg)
+    dg = oscola.box_geometry(cfg, 0).dg
+    rms = np.sqrt(np.mean(np.sum(periodic_diff(x, ref["x"], cfg.L) ** 2, axis=1))) / dg
+    prel = np.sqrt(np.mean(np.sum((p - ref["p"]) ** 2, 1)) / np.mean(np.sum(ref["p"] ** 2, 1)))
+    print("forward light_cone %s: position RMS %.3e PM cells, momentum RMS %.3e relative" % (variant, rms, prel))
+    assert rms <= 1e-3, rms
+    assert prel <= 1e-3, prel
+    xu, pu, simu = _forward(base, w, variant)
+    simu.close()
+    g = oscola.box_geometry(cfg, 0)
+    ids = tiling.box_global_ids(cfg.Np, cfg.Ntiles, g.t, g.Nbuf)[tiling.tile_interior_mask(cfg.Np, cfg.Ntiles, g.Nbuf)]
+    assert np.array_equal(x[ids], xu[ids]) and np.array_equal(p[ids], pu[ids])
+    # a tile that stops early is elsewhere than in the uniform run
+    g7 = oscola.box_geometry(cfg, 7)
+    ids7 = tiling.box_global_ids(cfg.Np, cfg.Ntiles, g7.t, g7.Nbuf)[tiling.tile_interior_mask(cfg.Np, cfg.Ntiles, g7.Nbuf)]
+    assert np.abs(periodic_diff(x[ids7], xu[ids7], cfg.L)).max() > 0.1 * dg
