@@ -213,8 +213,8 @@ def lpt_vjp(delta, L, lam_phi1, lam_psi1, lam_psi2):
 # ----------------------------------------------------------------------------- full run
 def loss_and_grad(w, cfg, delta_target):
     """Lval(w) and dLval/dw for the final-density loss of one sCOLA run."""
-    if getattr(cfg, "lpt_order", 2) != 2:
-        raise NotImplementedError("the adjoint follows the 2LPT frame only")
+    if getattr(cfg, "lpt_order", 2) != 2 or getattr(cfg, "fda_order", 2) != 2:
+        raise NotImplementedError("the adjoint follows the 2LPT frame and FDA order 2 only")
     w = np.asarray(w, dtype=np.float64)
     fields = scola.initial_fields(w, cfg)
     sched = scola.schedule(cfg)

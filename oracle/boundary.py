@@ -22,14 +22,14 @@ Fourier mode is reproduced to the trilinear error bound.
 import numpy as np
 
 
-def padded_cell_index(Ng):
-    """Padded cell indices c = -2 .. Ng+1 along one axis."""
-    return np.arange(-2, Ng + 2)
+def padded_cell_index(Ng, order=2):
+    """Padded cell indices c = -P .. Ng + P - 1 along one axis, P = 2 N_ghost = order."""
+    return np.arange(-order, Ng + order)
 
 
-def interior_mask(Ng):
-    """True on the Ng^3 interior cells of the padded (Ng + 4)^3 grid."""
-    c = padded_cell_index(Ng)
+def interior_mask(Ng, order=2):
+    """True on the Ng^3 interior cells of the padded (Ng + 2 order)^3 grid."""
+    c = padded_cell_index(Ng, order)
     m = (c >= 0) & (c < Ng)
     return m[:, None, None] & m[None, :, None] & m[None, None, :]
 
@@ -53,18 +53,19 @@ def trilinear_periodic(field, L, X):
     return out
 
 
-def bc_shell(phi1, L, origin, dg, Ng):
+def bc_shell(phi1, L, origin, dg, Ng, order=2):
     """phi1 interpolated to every padded PM cell outside the interior (C.3).
 
     ``origin`` is the box-local frame origin in full-box coordinates.  Returns
-    an (Ng + 4)^3 array, zero on the interior.  Multiply by D1(a_K) for
-    Phi_BCs at a force evaluation (Eq. 23).
+    an (Ng + 2 order)^3 array (order = FDA order: 2 N_ghost ghost layers per side),
+    zero on the interior.  Multiply by D1(a_K) for Phi_BCs at a force evaluation
+    (Eq. 23).
     """
-    c = padded_cell_index(Ng).astype(np.float64)
+    c = padded_cell_index(Ng, order).astype(np.float64)
     cx, cy, cz = np.meshgrid(c, c, c, indexing="ij")
     X = np.stack([origin[0] + (cx.ravel() + 0.5) * dg,
                   origin[1] + (cy.ravel() + 0.5) * dg,
                   origin[2] + (cz.ravel() + 0.5) * dg], axis=1)
-    shell = trilinear_periodic(phi1, L, X).reshape((Ng + 4,) * 3)
-    shell[interior_mask(Ng)] = 0.0
+    shell = trilinear_periodic(phi1, L, X).reshape((Ng + 2 * order,) * 3)
+    shell[interior_mask(Ng, order)] = 0.0
     return shell

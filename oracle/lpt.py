@@ -24,13 +24,17 @@ twice in configuration space; the Laplacian of phi1 returns delta exactly.
 """
 import numpy as np
 
+from . import fda
 from .ics import fourier_wavenumbers
 
 
-def laplacian_symbol(N, L):
-    """FDA-2 Laplacian eigenvalues on the rfftn grid."""
+def laplacian_symbol(N, L, order=2):
+    """Laplacian eigenvalues on the rfftn grid (FDA-2: -(4/d^2) sum sin^2(k d/2); order
+    4 and 6: the sum of the order-n second-derivative symbols, ``fda``)."""
     d = L / N
     kx, ky, kz = fourier_wavenumbers(N, L)
+    if order != 2:
+        return sum(fda.second_derivative_symbol(k, d, order) for k in (kx, ky, kz))
     return -(4.0 / d**2) * (np.sin(kx * d / 2) ** 2 + np.sin(ky * d / 2) ** 2
                             + np.sin(kz * d / 2) ** 2)
 
@@ -42,16 +46,19 @@ def _inverse_laplacian(field_k, lam):
     return out
 
 
-def lpt_potentials(delta, L):
+def lpt_potentials(delta, L, order=2):
     """phi1, phi2 and the second-order source on the LPT grid (Eqs. 5-6)."""
     delta = np.asarray(delta, dtype=np.float64)
     N = delta.shape[0]
     d = L / N
-    lam = laplacian_symbol(N, L)
+    lam = laplacian_symbol(N, L, order)
     phi1_k = _inverse_laplacian(np.fft.rfftn(delta), lam)
     phi1 = np.fft.irfftn(phi1_k, s=delta.shape, axes=(0, 1, 2))
     kx, ky, kz = fourier_wavenumbers(N, L)
-    D = [np.sin(kx * d) / d, np.sin(ky * d) / d, np.sin(kz * d) / d]
+    if order == 2:
+        D = [np.sin(kx * d) / d, np.sin(ky * d) / d, np.sin(kz * d) / d]
+    else:
+        D = [fda.gradient_symbol(k, d, order) for k in (kx, ky, kz)]
 
     def second(i, j):
         return np.fft.irfftn(-D[i] * D[j] * phi1_k, s=delta.shape, axes=(0, 1, 2))
@@ -63,18 +70,23 @@ def lpt_potentials(delta, L):
     return phi1, phi2, source
 
 
-def central_gradient(phi, L):
-    """Periodic FDA-2 gradient at the grid nodes: (phi[i+1] - phi[i-1]) / (2d).
+def central_gradient(phi, L, order=2):
+    """Periodic central gradient at the grid nodes (FDA-2: (phi[i+1] - phi[i-1]) / (2d);
+    order 4, 6: the ``fda`` stencils).
 
     Returns an array of shape (3, N, N, N).
     """
     N = phi.shape[0]
     d = L / N
-    return np.stack([(np.roll(phi, -1, axis=ax) - np.roll(phi, 1, axis=ax)) / (2.0 * d)
-                     for ax in range(3)])
+    if order == 2:
+        return np.stack([(np.roll(phi, -1, axis=ax) - np.roll(phi, 1, axis=ax)) / (2.0 * d)
+                         for ax in range(3)])
+    g = fda.gradient_coefficients(order)
+    return np.stack([sum(gm * (np.roll(phi, -m, axis=ax) - np.roll(phi, m, axis=ax)) for m, gm in
+                         enumerate(g, start=1)) / d for ax in range(3)])
 
 
-def lpt_fields(delta, L):
+def lpt_fields(delta, L, order=2):
     """phi1, phi2, Psi1 = grad phi1, Psi2 = grad phi2 on the LPT grid."""
-    phi1, phi2, _ = lpt_potentials(delta, L)
-    return phi1, phi2, central_gradient(phi1, L), central_gradient(phi2, L)
+    phi1, phi2, _ = lpt_potentials(delta, L, order)
+    return phi1, phi2, central_gradient(phi1, L, order), central_gradient(phi2, L, order)

@@ -29,6 +29,16 @@ coordinate leaves [-1, Ng] is clamped to that range (a reading: the paper is
 silent) and its corner index i0 is capped at Ng - 1 so that both corners stay in
 [-1, Ng].
 
+FDA order 4 and 6 (Sec. 3.1, App. C; ``order`` argument, default 2): the padding is
+2 N_ghost = order cells per side, Phi_BCs fills the N_ghost layers next to the
+interior, the source correction of Eq. 62 uses the order-n Laplacian (it reaches
+N_ghost cells inside), the eigenvalues are App. C's order-n ones (``fda``), and the
+gradient at the CIC corners is the order-n central difference.  Particles are clamped
+to [-N_ghost, Ng + N_ghost - 1] (the accelerations exist on the grid padded by N_ghost,
+Sec. 3.4.2) with i0 capped at Ng + N_ghost - 2.  The DST-I treats the potential as odd
+across each Dirichlet plane; for order > 2 the stencil reaches past the first ghost
+layer, where the paper's solve (App. C) thus sees the odd continuation of Phi~.
+
 Pins (tests/test_oracle_pm.py): the DST-I matrix against scipy's DST-I and the
 orthogonality S S = (Ng + 1)/2 I; the eigenvalues against the stencil; the
 Dirichlet solve against a dense 7-point-Laplacian linear solve with the
@@ -37,6 +47,8 @@ brute-force tent-weight deposit; zero force on a uniform lattice; exact
 gradients of linear and quadratic potentials; deposit/interpolation adjointness.
 """
 import numpy as np
+
+from . import fda
 
 
 def mesh_coordinate(xloc, dg):
@@ -68,24 +80,28 @@ def cic_deposit_box(xloc, dg, Ng, Nsc):
     return rho / nbar - 1.0, float(rho.sum())
 
 
-def laplacian_on_interior(padded, dg):
-    """FDA-2 Laplacian of a padded (Ng + 4)^3 field evaluated on its Ng^3 interior."""
-    Ng = padded.shape[0] - 4
-    c = padded[2:Ng + 2, 2:Ng + 2, 2:Ng + 2]
-    lap = -6.0 * c
-    lap = lap + padded[3:Ng + 3, 2:Ng + 2, 2:Ng + 2] + padded[1:Ng + 1, 2:Ng + 2, 2:Ng + 2]
-    lap = lap + padded[2:Ng + 2, 3:Ng + 3, 2:Ng + 2] + padded[2:Ng + 2, 1:Ng + 1, 2:Ng + 2]
-    lap = lap + padded[2:Ng + 2, 2:Ng + 2, 3:Ng + 3] + padded[2:Ng + 2, 2:Ng + 2, 1:Ng + 1]
+def laplacian_on_interior(padded, dg, order=2):
+    """Order-n FDA Laplacian of a padded (Ng + 2 order)^3 field evaluated on its Ng^3 interior."""
+    P = order
+    Ng = padded.shape[0] - 2 * P
+    s = fda.second_derivative_coefficients(order)
+    inner = slice(P, Ng + P)
+    lap = 3.0 * s[0] * padded[inner, inner, inner]
+    for m in range(1, len(s)):
+        lo, hi = slice(P - m, Ng + P - m), slice(P + m, Ng + P + m)
+        lap = lap + s[m] * (padded[hi, inner, inner] + padded[lo, inner, inner])
+        lap = lap + s[m] * (padded[inner, hi, inner] + padded[inner, lo, inner])
+        lap = lap + s[m] * (padded[inner, inner, hi] + padded[inner, inner, lo])
     return lap / dg**2
 
 
-def modified_density(delta, phi_bc_padded, dg):
+def modified_density(delta, phi_bc_padded, dg, order=2):
     """delta' = delta - Lap Phi_BCs on the interior (App. C, Eq. 62).
 
     ``phi_bc_padded`` is Phi_BCs on the padded grid, zero on the interior, so
     only ghost neighbours of the boundary cells contribute.
     """
-    return delta - laplacian_on_interior(phi_bc_padded, dg)
+    return delta - laplacian_on_interior(phi_bc_padded, dg, order)
 
 
 def dst1_matrix(N):
@@ -109,10 +125,10 @@ def dirichlet_eigenvalues(N, dg):
     return -(4.0 / dg**2) * np.sin(np.pi * l / (2.0 * (N + 1))) ** 2
 
 
-def zero_bc_poisson(source, dg):
+def zero_bc_poisson(source, dg, order=2):
     """Solve Lap Phi~ = source with Phi~ = 0 on the Dirichlet planes (App. C.2, Eqs. 63-71)."""
     N = source.shape[0]
-    lam = dirichlet_eigenvalues(N, dg)
+    lam = dirichlet_eigenvalues(N, dg) if order == 2 else fda.dst_eigenvalues(N, dg, order)
     hat = dst1_3d(source)
     hat = hat / (lam[:, None, None] + lam[None, :, None] + lam[None, None, :])
     return dst1_3d(hat) * (8.0 / (N + 1) ** 3)
@@ -121,46 +137,52 @@ def zero_bc_poisson(source, dg):
 def pad_potential(phi_interior, phi_bc_padded):
     """Phi on the padded grid: the solve inside, Phi_BCs in the ghost layers (Sec. 3.4.2)."""
     Ng = phi_interior.shape[0]
+    P = (phi_bc_padded.shape[0] - Ng) // 2
     out = np.array(phi_bc_padded, dtype=np.float64, copy=True)
-    out[2:Ng + 2, 2:Ng + 2, 2:Ng + 2] = phi_interior
+    out[P:Ng + P, P:Ng + P, P:Ng + P] = phi_interior
     return out
 
 
-def dirichlet_potential(delta, phi_bc_padded, dg):
+def dirichlet_potential(delta, phi_bc_padded, dg, order=2):
     """Padded Phi^sCOLA from the interior density and Phi_BCs (App. C.1-C.2)."""
-    src = modified_density(delta, phi_bc_padded, dg)
-    return pad_potential(zero_bc_poisson(src, dg), phi_bc_padded)
+    src = modified_density(delta, phi_bc_padded, dg, order)
+    return pad_potential(zero_bc_poisson(src, dg, order), phi_bc_padded)
 
 
-def interpolate_gradient(phi_padded, xloc, dg):
-    """grad Phi at the particles: FDA-2 central gradient at the CIC corners, CIC-interpolated.
+def interpolate_gradient(phi_padded, xloc, dg, order=2):
+    """grad Phi at the particles: central gradient (FDA order n) at the CIC corners,
+    CIC-interpolated.
 
     Returns (F, clamped) with F of shape (P, 3) and ``clamped`` a boolean mask
-    of particles whose mesh coordinate was moved back into [-1, Ng].
+    of particles whose mesh coordinate was moved back into [-N_ghost, Ng + N_ghost - 1].
     """
-    Ng = phi_padded.shape[0] - 4
+    pad = order
+    ng = fda.n_ghost(order)
+    Ng = phi_padded.shape[0] - 2 * pad
     u_raw = mesh_coordinate(xloc, dg)
-    u = np.clip(u_raw, -1.0, float(Ng))
+    u = np.clip(u_raw, -float(ng), float(Ng + ng - 1))
     clamped = np.any(u != u_raw, axis=1)
-    i0 = np.minimum(np.floor(u).astype(np.int64), Ng - 1)
+    i0 = np.minimum(np.floor(u).astype(np.int64), Ng + ng - 2)
     f = u - i0
     F = np.zeros_like(u)
     P = phi_padded
+    g = fda.gradient_coefficients(order)
     for dx in (0, 1):
         for dy in (0, 1):
             for dz in (0, 1):
                 w = ((f[:, 0] if dx else 1.0 - f[:, 0]) * (f[:, 1] if dy else 1.0 - f[:, 1])
                      * (f[:, 2] if dz else 1.0 - f[:, 2]))
-                cx = i0[:, 0] + dx + 2
-                cy = i0[:, 1] + dy + 2
-                cz = i0[:, 2] + dz + 2
-                F[:, 0] += w * (P[cx + 1, cy, cz] - P[cx - 1, cy, cz]) / (2.0 * dg)
-                F[:, 1] += w * (P[cx, cy + 1, cz] - P[cx, cy - 1, cz]) / (2.0 * dg)
-                F[:, 2] += w * (P[cx, cy, cz + 1] - P[cx, cy, cz - 1]) / (2.0 * dg)
+                cx = i0[:, 0] + dx + pad
+                cy = i0[:, 1] + dy + pad
+                cz = i0[:, 2] + dz + pad
+                for m, gm in enumerate(g, start=1):
+                    F[:, 0] += w * gm * (P[cx + m, cy, cz] - P[cx - m, cy, cz]) / dg
+                    F[:, 1] += w * gm * (P[cx, cy + m, cz] - P[cx, cy - m, cz]) / dg
+                    F[:, 2] += w * gm * (P[cx, cy, cz + m] - P[cx, cy, cz - m]) / dg
     return F, clamped
 
 
-def box_force(xloc, dg, Ng, Nsc, phi_bc_padded, delta_override=None):
+def box_force(xloc, dg, Ng, Nsc, phi_bc_padded, delta_override=None, order=2):
     """One PM force evaluation in a box: deposit, Dirichlet solve, gradient, interpolation.
 
     ``phi_bc_padded`` is Phi_BCs at this force time (already scaled by D1).
@@ -172,6 +194,6 @@ def box_force(xloc, dg, Ng, Nsc, phi_bc_padded, delta_override=None):
         delta, deposited = cic_deposit_box(xloc, dg, Ng, Nsc)
     else:
         delta, deposited = delta_override, float("nan")
-    phi = dirichlet_potential(delta, phi_bc_padded, dg)
-    F, clamped = interpolate_gradient(phi, xloc, dg)
+    phi = dirichlet_potential(delta, phi_bc_padded, dg, order)
+    F, clamped = interpolate_gradient(phi, xloc, dg, order)
     return {"F": F, "delta": delta, "phi": phi, "deposited": deposited, "clamped": clamped}

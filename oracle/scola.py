@@ -55,6 +55,7 @@ class ScolaConfig:
     stepping: str = "modified"   # KDK time factors: "modified" (u = a^nLPT) or "standard" (App. B)
     lpt_order: int = 2           # 2: 2LPT frame; 1: Zel'dovich frame (phi2 = Psi2 = 0)
     a_final: list = None         # per-tile final scale factors (box-id order), None: a_f for all
+    fda_order: int = 2           # FDA order of gradients and Laplacians: 2, 4, 6 (Sec. 3.1)
                                  # (light-cone scheduling, Sec. 5: tiles need not share a_f)
 
     @property
@@ -110,7 +111,7 @@ def initial_fields(w, cfg):
     if w.shape != (cfg.Np,) * 3:
         raise ValueError("white noise must be Np^3 (LPT grid N = Np)")
     delta = ics.initial_density(w, cfg.L, cfg.Om, cfg.h, cfg.ns, cfg.sigma8)
-    phi1, phi2, psi1, psi2 = lpt.lpt_fields(delta, cfg.L)
+    phi1, phi2, psi1, psi2 = lpt.lpt_fields(delta, cfg.L, cfg.fda_order)
     if cfg.lpt_order == 1:
         # Zel'dovich approximation: first-order displacements only (the COLA frame and the
         # initial positions use Psi1 alone)
@@ -181,7 +182,7 @@ def evolve_box(cfg, b, fields, sched, force_mode="pm", delta_fn=None, phi_bc_fn=
     p0 = np.zeros_like(s0)
     shell = None
     if force_mode == "pm" and phi_bc_fn is None:
-        shell = boundary.bc_shell(fields.phi1, cfg.L, g.origin, g.dg, g.Ng)
+        shell = boundary.bc_shell(fields.phi1, cfg.L, g.origin, g.dg, g.Ng, cfg.fda_order)
 
     def force(k, s):
         D1, D2 = sched["D1"][k], sched["D2"][k]
@@ -189,7 +190,7 @@ def evolve_box(cfg, b, fields, sched, force_mode="pm", delta_fn=None, phi_bc_fn=
             return D1 * psi1 - (D2 - D1 * D1) * psi2, None
         bc = phi_bc_fn(k) if phi_bc_fn is not None else D1 * shell
         dov = delta_fn(k) if delta_fn is not None else None
-        r = pm.box_force(qloc + s, g.dg, g.Ng, g.Nsc, bc, delta_override=dov)
+        r = pm.box_force(qloc + s, g.dg, g.Ng, g.Nsc, bc, delta_override=dov, order=cfg.fda_order)
         return r["F"], (r["deposited"], int(r["clamped"].sum()))
 
     s, p, diags = kdk_integrate(s0, p0, psi1, psi2, sched, force)

@@ -65,6 +65,22 @@ def test_light_cone_lpt_force_mode_lands_on_each_tiles_final_a():
         np.testing.assert_allclose(r["p"], p_lpt, atol=1e-9 * np.abs(p_lpt).max())
 
 
+@pytest.mark.parametrize("order", [4, 6])
+def test_fda_order_lpt_force_mode_and_zero_amplitude(order):
+    # FDA orders 4 and 6 through the whole method: zero amplitude stays exactly zero, and
+    # the LPT-force mode lands exactly on the (order-n) 2LPT trajectory.
+    cfg = _cfg(nsteps=4, fda_order=order)
+    out = scola.run_scola(np.zeros((16,) * 3, np.float32), cfg)
+    assert np.all(out["s"] == 0.0) and np.all(out["p"] == 0.0)
+    w = synth_inputs.white_noise(16, 5)
+    out = scola.run_scola(w, cfg, force_mode="lpt")
+    f, sch = out["fields"], out["sched"]
+    s_lpt = (-sch["D1_f"] * f.psi1 + sch["D2_f"] * f.psi2).reshape(3, -1).T
+    np.testing.assert_allclose(out["s"], s_lpt, atol=1e-12 * np.abs(s_lpt).max())
+    two = scola.initial_fields(w, _cfg(nsteps=4))
+    assert np.abs(two.psi1 - f.psi1).max() > 1e-4 * np.abs(f.psi1).max()    # the order matters
+
+
 def test_small_amplitude_residual_scales_linearly():
     # At vanishing amplitude the dynamics is linear: Psi_res / Psi_LPT is eps-independent
     # and small at large scales (the residual is the PM discretisation error).
