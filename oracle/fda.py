@@ -53,9 +53,11 @@ def gradient_symbol(k, d, order):
 
 
 def second_derivative_symbol(k, d, order):
-    """Fourier symbol of the second derivative (real, <= 0)."""
+    """Fourier symbol of the second derivative (real, <= 0), written as
+    (2/d^2) sum_m s_m (cos(m k d) - 1): the central stencils have s_0 = -2 sum_m s_m, and
+    this form vanishes exactly at k = 0 (no cancellation of s_0 against the sum)."""
     s = second_derivative_coefficients(order)
-    return (s[0] + 2.0 * sum(sm * np.cos(m * k * d) for m, sm in enumerate(s) if m > 0)) / d**2
+    return 2.0 * sum(sm * (np.cos(m * k * d) - 1.0) for m, sm in enumerate(s) if m > 0) / d**2
 
 
 def dst_eigenvalues(N, d, order):

@@ -40,8 +40,10 @@ def laplacian_symbol(N, L, order=2):
 
 
 def _inverse_laplacian(field_k, lam):
+    """field / Lambda with the k = 0 mode set to zero (Eqs. 5-6)."""
     out = np.zeros_like(field_k)
     nz = lam != 0
+    nz[0, 0, 0] = False
     out[nz] = field_k[nz] / lam[nz]
     return out
 

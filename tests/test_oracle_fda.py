@@ -43,6 +43,18 @@ def test_printed_dst_eigenvalues_equal_the_stencil_symbol(order):
 
 
 @pytest.mark.parametrize("order", ORDERS)
+def test_second_derivative_symbol_matches_the_stencil_sum_and_vanishes_at_zero(order):
+    # The cancellation-free form equals s_0 + 2 sum_m s_m cos(m k d) and is exactly 0 at k = 0.
+    d = 0.8
+    s = fda.second_derivative_coefficients(order)
+    assert abs(s[0] + 2 * sum(s[1:])) < 1e-15
+    k = np.linspace(0.0, np.pi / d, 17)
+    direct = (s[0] + 2.0 * sum(sm * np.cos(m * k * d) for m, sm in enumerate(s) if m)) / d**2
+    np.testing.assert_allclose(fda.second_derivative_symbol(k, d, order), direct, atol=1e-13 / d**2)
+    assert fda.second_derivative_symbol(np.zeros(1), d, order)[0] == 0.0
+
+
+@pytest.mark.parametrize("order", ORDERS)
 def test_dst_basis_is_eigenvector_with_odd_continuation(order):
     # The DST-I basis vectors sin(pi l i/(N+1)) vanish at i = 0 and N + 1 and are odd across
     # both planes; the order-n stencil applied to that continuation returns lambda_l times
