@@ -97,7 +97,11 @@ typedef enum scola_batch_mode {
  *   nsteps       COLA drift steps, linear in a (nsteps + 1 force evaluations)
  *   nLPT         exponent of the modified time stepping u(a) = a^nLPT
  *                (App. B, Eq. 60); the paper uses -2.5
- *   fda_order    finite-difference order; only 2 is built
+ *   fda_order    finite-difference order 2, 4 or 6 of every gradient and Laplacian
+ *                (Sec. 3.1; N_ghost = fda_order / 2): the padded potential has fda_order
+ *                ghost layers per side, the boundary source of Eq. 62 reaches N_ghost
+ *                cells inside, and the DST solve uses App. C's order-n eigenvalues.
+ *                The adjoint is built for order 2
  *   dst_variant  one of scola_dst_variant
  *   batch_mode   one of scola_batch_mode (same results, different launch shapes)
  *   deposit_form one of scola_deposit_form.  Every form sums the CIC weights as
@@ -188,7 +192,7 @@ typedef struct scola_stats {
  *   stream  cudaStream_t on which all later work is enqueued (NULL = legacy default)
  *   out     receives the new context
  * Errors: INVALID_ARG (Np % Ntiles != 0, Ng < Np,sCOLA, non-positive sizes,
- * a_i >= a_f, nsteps < 1, Np,sCOLA > Np), UNSUPPORTED (fda_order != 2), OOM, CUDA.
+ * a_i >= a_f, nsteps < 1, Np,sCOLA > Np), UNSUPPORTED (fda_order not 2, 4 or 6), OOM, CUDA.
  * Synchronous.
  */
 scola_status scola_create(const scola_params *params, void *stream, scola_ctx **out);

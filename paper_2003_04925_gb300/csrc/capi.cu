@@ -93,8 +93,8 @@ scola_status validate(const scola_params *p, std::vector<int32_t> &bufs, std::ve
     if (p->Np < 2) return invalid("Np must be >= 2");
     if (p->Ntiles < 1) return invalid("Ntiles must be >= 1");
     if (p->Np % p->Ntiles != 0) return invalid("Np must be a multiple of Ntiles (Sec. 3.2)");
-    if (p->fda_order != 2) {
-        set_error("only FDA order 2 is built");
+    if (p->fda_order != 2 && p->fda_order != 4 && p->fda_order != 6) {
+        set_error("FDA order must be 2, 4 or 6");
         return SCOLA_ERR_UNSUPPORTED;
     }
     if (p->dst_variant != SCOLA_DST_SIMT && p->dst_variant != SCOLA_DST_TC_3XTF32 &&
@@ -239,10 +239,14 @@ void plan_batch(const scola_ctx *c, const std::vector<BoxGeom> &tiling_geo, int 
         }
         B.p_off = P;
         B.m_off = M;
-        // padded boxes start 2 floats past a 64-float boundary: with Ng % 4 == 0 the interior
-        // cells of every padded row (index 2 .. Ng+1) then start 16-byte aligned
-        MP += 2;
+        // padded boxes (G = FDA order ghost layers per side) start G mod 4 floats past a
+        // 64-float boundary: with Ng % 4 == 0 the interior cells of every padded row
+        // (index G .. Ng + G - 1) then start 16-byte aligned
+        const int G = p.fda_order;
+        MP += (G % 4 == 2) ? 2 : 0;
         B.pp_off = MP;
+        B.gpad = G;
+        B.fda = p.fda_order;
         B.sh_off = SH;
         {
             const int nb = (g.ng + 15) / 16;
@@ -266,7 +270,7 @@ void plan_batch(const scola_ctx *c, const std::vector<BoxGeom> &tiling_geo, int 
         bp.boxes.push_back(B);
         const long long n = (long long)g.nsc * g.nsc * g.nsc;
         const long long ng3 = (long long)g.ng * g.ng * g.ng;
-        const long long np3 = (long long)(g.ng + 4) * (g.ng + 4) * (g.ng + 4);
+        const long long np3 = (long long)(g.ng + 2 * G) * (g.ng + 2 * G) * (g.ng + 2 * G);
         add(bp.pch, bp.n_pch, b, n, kChunk);
         add(bp.tch, bp.n_tch, b, (long long)ntile * ntile * ntile, kChunk);
         add(bp.shch, bp.n_shch, b, np3 - ng3, kChunk);
@@ -326,12 +330,12 @@ void plan_batch(const scola_ctx *c, const std::vector<BoxGeom> &tiling_geo, int 
 }
 
 // Device bytes a batch of the given boxes takes in the per-batch arenas.
-long long batch_bytes(const std::vector<BoxGeom> &geo) {
+long long batch_bytes(const std::vector<BoxGeom> &geo, int G) {
     long long bytes = 0;
     for (const BoxGeom &g : geo) {
         const long long n = (long long)g.nsc * g.nsc * g.nsc;
         const long long ng3 = (long long)g.ng * g.ng * g.ng;
-        const long long np3 = (long long)(g.ng + 4) * (g.ng + 4) * (g.ng + 4);
+        const long long np3 = (long long)(g.ng + 2 * G) * (g.ng + 2 * G) * (g.ng + 2 * G);
         const long long nbe = (g.ng + 15) / 16 + 1;
         long long q = 64;
         while (q % g.ng) q += 64;
@@ -487,8 +491,13 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &all_geo) {
     for (auto &T : c->tables_h) {
         const double dg = dg_of_ng[T.Ng];
         for (int l = 0; l < T.Ng; ++l) {
-            const double s = std::sin(M_PI * (l + 1) / (2.0 * (T.Ng + 1)));
-            arena[T.lam_off + l] = (float)(-4.0 / (dg * dg) * s * s);
+            // App. C eigenvalues of the order-n second difference, t = pi l / (2 (Ng + 1))
+            const double t = M_PI * (l + 1) / (2.0 * (T.Ng + 1));
+            const double s1 = std::sin(t), s2 = std::sin(2 * t), s3 = std::sin(3 * t);
+            double lam = -4.0 / (dg * dg) * s1 * s1;
+            if (p.fda_order == 4) lam = (s2 * s2 - 16.0 * s1 * s1) / (3.0 * dg * dg);
+            if (p.fda_order == 6) lam = -(2.0 * s3 * s3 - 27.0 * s2 * s2 + 270.0 * s1 * s1) / (45.0 * dg * dg);
+            arena[T.lam_off + l] = (float)lam;
         }
     }
     // LPT-grid sine tables: sin(pi n/N) and sin(2 pi n/N)/d with n the wrapped wavenumber
@@ -514,6 +523,32 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &all_geo) {
     for (int i = 0; i < p.Np; ++i) {
         const int n = i < p.Np / 2 ? i : i - p.Np;
         arena.push_back((float)(std::sin(2.0 * M_PI * n / p.Np) / c->dq));
+    }
+    // FDA order 4/6 on the LPT grid: per grid index, the 1D second-derivative symbol
+    // (1/d^2)(s0 + 2 sum_m s_m cos(m k d)) and the gradient symbol (2/d) sum_m g_m sin(m k d)
+    if (p.fda_order != 2) {
+        static const double s4[] = {-2.5, 4.0 / 3.0, -1.0 / 12.0}, g4[] = {2.0 / 3.0, -1.0 / 12.0};
+        static const double s6[] = {-49.0 / 18.0, 1.5, -0.15, 1.0 / 90.0}, g6[] = {0.75, -0.15, 1.0 / 60.0};
+        const double *sc = p.fda_order == 4 ? s4 : s6, *gc = p.fda_order == 4 ? g4 : g6;
+        const int ngh = p.fda_order / 2;
+        const double d = c->dq;
+        // (written as 2 sum_m s_m (cos(m k d) - 1), since s0 = -2 sum_m s_m: exactly 0 at k = 0)
+        c->lap1_off = (long long)arena.size();
+        for (int i = 0; i < p.Np; ++i) {
+            const int n = i < p.Np / 2 ? i : i - p.Np;
+            const double kd = 2.0 * M_PI * n / p.Np;
+            double v = 0.0;
+            for (int m = 1; m <= ngh; ++m) v += 2.0 * sc[m] * (std::cos(m * kd) - 1.0);
+            arena.push_back((float)(v / (d * d)));
+        }
+        c->grad1_off = (long long)arena.size();
+        for (int i = 0; i < p.Np; ++i) {
+            const int n = i < p.Np / 2 ? i : i - p.Np;
+            const double kd = 2.0 * M_PI * n / p.Np;
+            double v = 0.0;
+            for (int m = 1; m <= ngh; ++m) v += gc[m - 1] * std::sin(m * kd);
+            arena.push_back((float)(2.0 * v / d));
+        }
     }
     // tensor-core DST groups (one per distinct Ng): the FP32 sine matrix
     bool all_tc = true;
@@ -590,7 +625,7 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &all_geo) {
         long long used = 0;
         int fit = 0;
         while (fit < count) {
-            const long long add = batch_bytes({geo[fit]});
+            const long long add = batch_bytes({geo[fit]}, p.fda_order);
             if (used + add > avail) break;
             used += add;
             ++fit;
@@ -1198,6 +1233,10 @@ scola_status scola_set_checkpointing(scola_ctx *c, int32_t enable) {
     }
     if (on && !c->a_final.empty()) {
         set_error("the adjoint needs a common final scale factor (no a_final)");
+        return SCOLA_ERR_UNSUPPORTED;
+    }
+    if (on && c->prm.fda_order != 2) {
+        set_error("the adjoint is built for FDA order 2 only");
         return SCOLA_ERR_UNSUPPORTED;
     }
     if (on && c->prm.lpt_order != 2) {

@@ -5,45 +5,94 @@
 
 namespace scola {
 
-// Number of padded cells outside the interior: (Ng+4)^3 - Ng^3.
-__host__ __device__ inline long long shell_count(int Ng) {
-    const long long a = Ng + 4;
+// The padded PM grid of a box has P = 2 N_ghost = FDA order ghost layers on every side
+// (padded index pc = c + P, S = Ng + 2P cells per axis).
+
+// Number of padded cells outside the interior: (Ng+2P)^3 - Ng^3.
+__host__ __device__ inline long long shell_count(int Ng, int P) {
+    const long long a = Ng + 2 * P;
     return a * a * a - (long long)Ng * Ng * Ng;
 }
 
-// Padded coordinates (0..Ng+3 per axis) of shell cell `idx`.  Enumeration:
-// the four full i-planes {0, 1, Ng+2, Ng+3}; then, for interior i, the four
-// full j-rows {0, 1, Ng+2, Ng+3}; then, for interior i and j, the four
-// k-cells {0, 1, Ng+2, Ng+3}.
-__device__ inline void shell_coord(long long idx, int Ng, int &pi, int &pj, int &pk) {
-    const int S = Ng + 4;
+// Padded coordinates (0..Ng+2P-1 per axis) of shell cell `idx`.  Enumeration: the 2P
+// full i-planes {0..P-1, Ng+P..Ng+2P-1}; then, for interior i, the 2P full j-rows; then,
+// for interior i and j, the 2P k-cells.
+__device__ inline void shell_coord(long long idx, int Ng, int P, int &pi, int &pj, int &pk) {
+    const int S = Ng + 2 * P;
     const long long plane = (long long)S * S;
-    const long long A = 4 * plane;
+    const long long A = 2LL * P * plane;
     if (idx < A) {
         const int q = (int)(idx / plane);
         const long long r = idx - q * plane;
-        pi = q < 2 ? q : Ng + q;
+        pi = q < P ? q : Ng + q;
         pj = (int)(r / S);
         pk = (int)(r - (long long)pj * S);
         return;
     }
     idx -= A;
-    const long long rowblk = 4LL * S;
+    const long long rowblk = 2LL * P * S;
     const long long B = (long long)Ng * rowblk;
     if (idx < B) {
-        pi = 2 + (int)(idx / rowblk);
+        pi = P + (int)(idx / rowblk);
         const int r = (int)(idx % rowblk);
         const int q = r / S;
-        pj = q < 2 ? q : Ng + q;
+        pj = q < P ? q : Ng + q;
         pk = r - q * S;
         return;
     }
     idx -= B;
-    pi = 2 + (int)(idx / (4LL * Ng));
-    const int r = (int)(idx % (4LL * Ng));
-    pj = 2 + r / 4;
-    const int q = r & 3;
-    pk = q < 2 ? q : Ng + q;
+    pi = P + (int)(idx / (2LL * P * Ng));
+    const int r = (int)(idx % (2LL * P * Ng));
+    pj = P + r / (2 * P);
+    const int q = r % (2 * P);
+    pk = q < P ? q : Ng + q;
+}
+
+// Central-difference coefficients of FDA order 2, 4, 6 (N_ghost = order / 2 terms):
+// gradient f' = (1/d) sum_m g_m (f_{+m} - f_{-m}); second derivative
+// f'' = (1/d^2) (s_0 f + sum_m s_m (f_{+m} + f_{-m})).
+template <int ORDER> struct Fda;
+template <> struct Fda<2> {
+    static constexpr int ng = 1;
+    __device__ static float g(int m) { return 0.5f; }
+    __device__ static float s(int m) { return m == 0 ? -2.0f : 1.0f; }
+};
+template <> struct Fda<4> {
+    static constexpr int ng = 2;
+    __device__ static float g(int m) { return m == 1 ? 2.0f / 3.0f : -1.0f / 12.0f; }
+    __device__ static float s(int m) { return m == 0 ? -2.5f : (m == 1 ? 4.0f / 3.0f : -1.0f / 12.0f); }
+};
+template <> struct Fda<6> {
+    static constexpr int ng = 3;
+    __device__ static float g(int m) { return m == 1 ? 0.75f : (m == 2 ? -0.15f : 1.0f / 60.0f); }
+    __device__ static float s(int m) {
+        return m == 0 ? -49.0f / 18.0f : (m == 1 ? 1.5f : (m == 2 ? -0.15f : 1.0f / 90.0f));
+    }
+};
+
+// Boundary term of Eq. 62 for the interior cell (i, j, k): the order-n Laplacian's
+// contributions of the Dirichlet values in the ghost layers (unscaled by 1/dg^2).  P_c is
+// the padded potential at the cell; S the padded row length.  Per axis: the offsets m
+// that reach past the lower face (m > x) and past the upper face (m >= Ng - x).
+template <int ORDER>
+__device__ __forceinline__ float boundary_term_n(const float *P_c, int i, int j, int k, int Ng, int S) {
+    float bc = 0.0f;
+    const int st[3] = {S * S, S, 1};
+    const int x[3] = {i, j, k};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+#pragma unroll
+        for (int m = 1; m <= Fda<ORDER>::ng; ++m) {
+            if (m > x[a]) bc += Fda<ORDER>::s(m) * P_c[-m * st[a]];
+            if (m >= Ng - x[a]) bc += Fda<ORDER>::s(m) * P_c[m * st[a]];
+        }
+    }
+    return bc;
+}
+
+__device__ __forceinline__ float boundary_term(const float *P_c, int i, int j, int k, int Ng, int S, int order) {
+    return order == 2 ? boundary_term_n<2>(P_c, i, j, k, Ng, S)
+                      : (order == 4 ? boundary_term_n<4>(P_c, i, j, k, Ng, S) : boundary_term_n<6>(P_c, i, j, k, Ng, S));
 }
 
 __device__ __forceinline__ void decode_local(int local, int n, int &i, int &j, int &k) {
@@ -129,7 +178,7 @@ __device__ __forceinline__ void shell_stencil(const BoxDesc &B, const int pc[3],
     const int den = 2 * B.Ng;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const int num = (2 * pc[a] - 3) * B.Nsc - B.Ng;
+        const int num = (2 * (pc[a] - B.gpad) + 1) * B.Nsc - B.Ng;
         int q = num / den, r = num - q * den;
         if (r < 0) {
             r += den;

@@ -42,7 +42,8 @@ struct BoxDesc {
     float dq, dg, inv_dg, q2u;    // q2u = dq / dg
     float nbar_inv;               // (Ng / Nsc)^3
     int key_off;                  // sorted deposit: first key of the box (8 nbe^3 keys per box)
-    float pad1[2];
+    int gpad;                     // ghost layers per side of the padded potential: 2 N_ghost = FDA order
+    int fda;                      // FDA order 2, 4, 6
     double dg_d, origin_d[3];     // FP64 box geometry (cell size, origin of the box frame)
 };
 
@@ -125,6 +126,7 @@ struct Ctx {
     Chunk *mchunks = nullptr;  int n_mchunks = 0;     // interior mesh cells
     long long sin_half_off = 0, sin_full_off = 0;     // LPT-grid sine tables in table_arena
     long long amp_off = 0;                            // colouring amplitude per integer |n|^2
+    long long lap1_off = 0, grad1_off = 0;            // FDA order 4/6: 1D Laplacian and gradient symbols
     // first entry of each box in every work list (size nboxes + 1), for per-tile launches
     std::vector<int> pbeg, shbeg, zbeg, cbeg, mbeg;
     std::vector<int> dep_groups;                      // first box of each deposit group, then nboxes

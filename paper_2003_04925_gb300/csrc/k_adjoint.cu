@@ -19,6 +19,8 @@
 // Accumulations shared between particles use FP32 atomics (sum order varies).
 #include "device_util.cuh"
 
+// (The adjoint is built for FDA order 2: padded grids of Ng + 4 cells, 2 ghost layers.)
+
 namespace scola {
 
 namespace {
@@ -200,9 +202,9 @@ k_adj_shell(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
     const BoxDesc &B = boxes[ch.box];
     const int Ng = B.Ng;
     const long long idx = (long long)ch.start + threadIdx.x;
-    if (idx >= shell_count(Ng)) return;
+    if (idx >= shell_count(Ng, 2)) return;
     int p[3];
-    shell_coord(idx, Ng, p[0], p[1], p[2]);
+    shell_coord(idx, Ng, 2, p[0], p[1], p[2]);
     const long long S = Ng + 4;
     const long long strides[3] = {S * S, S, 1};
     const long long here = B.pp_off + ((long long)p[0] * S + p[1]) * S + p[2];
@@ -296,11 +298,11 @@ k_adj_shell_to_phi1(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__
     const Chunk ch = chunks[blockIdx.x];
     const BoxDesc &B = boxes[ch.box];
     const long long idx = (long long)ch.start + threadIdx.x;
-    if (idx >= shell_count(B.Ng)) return;
+    if (idx >= shell_count(B.Ng, 2)) return;
     const float lv = lam_shell[B.sh_off + idx];
     if (lv == 0.0f) return;
     int pc[3];
-    shell_coord(idx, B.Ng, pc[0], pc[1], pc[2]);
+    shell_coord(idx, B.Ng, 2, pc[0], pc[1], pc[2]);
     int i0[3];
     float f[3];
     shell_stencil(B, pc, Ntile, i0, f);

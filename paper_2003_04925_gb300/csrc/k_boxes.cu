@@ -58,9 +58,9 @@ k_shell(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
     const Chunk ch = chunks[blockIdx.x];
     const BoxDesc &B = boxes[ch.box];
     const long long idx = (long long)ch.start + threadIdx.x;
-    if (idx >= shell_count(B.Ng)) return;
+    if (idx >= shell_count(B.Ng, B.gpad)) return;
     int pc[3];
-    shell_coord(idx, B.Ng, pc[0], pc[1], pc[2]);
+    shell_coord(idx, B.Ng, B.gpad, pc[0], pc[1], pc[2]);
     int i0[3];
     float f[3];
     shell_stencil(B, pc, Ntile, i0, f);

@@ -114,10 +114,10 @@ k_density_source(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ ch
     if (delta_out) store4(delta_out + cell, v, vec, left);
 #pragma unroll
     for (int e = 0; e < 4; ++e) v[e] *= inv_D1;
-    // boundary source: the Dirichlet values (unscaled shell) sit in the ghost layer next to
-    // each face cell
+    // boundary source: the order-n Laplacian's reach into the ghost layers (Dirichlet values,
+    // the unscaled shell) from the cells within N_ghost of a face
     int k = cell0 % Ng, j = (cell0 / Ng) % Ng, i = cell0 / Ng / Ng;
-    const int S = Ng + 4;
+    const int G = B.gpad, ng = B.fda / 2, S = Ng + 2 * G;
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
         if (e >= left) break;
@@ -128,16 +128,9 @@ k_density_source(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ ch
                 ++i;
             }
         }
-        if (i == 0 || j == 0 || k == 0 || i == Ng - 1 || j == Ng - 1 || k == Ng - 1) {
-            const float *P = phi_pad + B.pp_off + ((i + 2) * S + (j + 2)) * S + (k + 2);
-            float bc = 0.0f;
-            if (i == 0) bc += P[-S * S];
-            if (i == Ng - 1) bc += P[S * S];
-            if (j == 0) bc += P[-S];
-            if (j == Ng - 1) bc += P[S];
-            if (k == 0) bc += P[-1];
-            if (k == Ng - 1) bc += P[1];
-            v[e] -= bc * c2;
+        if (i < ng || j < ng || k < ng || i >= Ng - ng || j >= Ng - ng || k >= Ng - ng) {
+            const float *P = phi_pad + B.pp_off + ((i + G) * S + (j + G)) * S + (k + G);
+            v[e] -= boundary_term(P, i, j, k, Ng, S, B.fda) * c2;
         }
         ++k;
     }

@@ -246,7 +246,7 @@ k_sort_brick(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ items,
     __syncthreads();
     // cells: item q -> (x, y) row of the brick, 4 consecutive z cells
     const float sc = B.nbar_inv * 2.3283064365386963e-10f, c2 = B.inv_dg * B.inv_dg;
-    const int S = Ng + 4;
+    const int G = B.gpad, ng = B.fda / 2, S = Ng + 2 * G;
     const bool edge = x0 == 0 || y0 == 0 || z0 == 0 || x0 + kBrick >= Ng || y0 + kBrick >= Ng || z0 + kBrick >= Ng;
     for (int q = tid; q < kBrickCells / 4; q += kBrickThreads) {
         const int lz = (q % (kBrick / 4)) * 4, ly = (q / (kBrick / 4)) % kBrick, lx = q / (kBrick * kBrick / 4);
@@ -274,20 +274,13 @@ k_sort_brick(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ items,
         if (delta_out) store4(delta_out + cell, v, vec, Ng - k);
 #pragma unroll
         for (int e = 0; e < 4; ++e) v[e] *= inv_D1;
-        if (edge && (i == 0 || j == 0 || i == Ng - 1 || j == Ng - 1 || k == 0 || k + 4 >= Ng)) {
-            const float *P = phi_pad + B.pp_off + ((i + 2) * S + (j + 2)) * S + (k + 2);
+        if (edge && (i < ng || j < ng || i >= Ng - ng || j >= Ng - ng || k < ng || k + 4 > Ng - ng)) {
+            // boundary source: the order-n Laplacian's reach into the ghost layers
+            const float *Pc = phi_pad + B.pp_off + ((i + G) * S + (j + G)) * S + (k + G);
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                const int kk = k + e;
-                if (kk >= Ng) break;
-                float bc = 0.0f;
-                if (i == 0) bc += P[e - S * S];
-                if (i == Ng - 1) bc += P[e + S * S];
-                if (j == 0) bc += P[e - S];
-                if (j == Ng - 1) bc += P[e + S];
-                if (kk == 0) bc += P[e - 1];
-                if (kk == Ng - 1) bc += P[e + 1];
-                v[e] -= bc * c2;
+                if (k + e >= Ng) break;
+                v[e] -= boundary_term(Pc + e, i, j, k + e, Ng, S, B.fda) * c2;
             }
         }
         store4(out + cell, v, vec, Ng - k);

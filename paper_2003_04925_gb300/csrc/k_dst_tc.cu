@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(const __grid_constant__ 
         ti.m_off = A.boxes[tl.box].m_off;
         ti.pp_off = A.boxes[tl.box].pp_off;
         ti.row0 = tl.start * kTN;
-        ti.pad = 0;
+        ti.pad = A.boxes[tl.box].gpad;
         return ti;
     };
     for (int k = tid; k < my_tiles && k < kTileCache; k += kThreads) tinfo[k] = load_tile(k);
@@ -490,7 +490,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(const __grid_constant__ 
         const int n0 = quarter * 32;
         const int ncol = Nk - n0 < 32 ? Nk - n0 : 32;        // valid columns of this warp (may be <= 0)
         const float scale = (PASS == P_XI) ? 8.0f / ((float)(Ng + 1) * (Ng + 1) * (Ng + 1)) : 1.0f;
-        const long long S = Ng + 4;
+        // (the padded row length S depends on the box's ghost width: taken per tile below)
         float *buf = xpose + warp * (kXposeBytes / 4);
         uint32_t t = 0;
         for (long long it = 0; it < my_tiles && !*abort_flag; ++it, ++t) {
@@ -543,9 +543,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(const __grid_constant__ 
                         const int nout = FOLD ? 2 * (n0 + nl) + parity : n0 + nl;   // output column
                         float4 x = reinterpret_cast<const float4 *>(buf + nl * 32)[ru ^ (nl & 7)];
                         if (PASS == P_XI) {
-                            // rows R .. R + 3 share rhi (Ng % 4 == 0); padded boxes start 2 floats
-                            // past a 64-float boundary, so interior rows are 16-byte aligned
-                            float *p = A.out + ti.pp_off + ((long long)(nout + 2) * S + (rhi + 2)) * S + (rlo + 2);
+                            // rows R .. R + 3 share rhi (Ng % 4 == 0); padded boxes start so that
+                            // their interior rows are 16-byte aligned (pp_off + G = 0 mod 4)
+                            const int G = ti.pad;
+                            const long long S = Ng + 2 * G;
+                            float *p = A.out + ti.pp_off + ((long long)(nout + G) * S + (rhi + G)) * S + (rlo + G);
                             *reinterpret_cast<float4 *>(p) = make_float4(x.x * scale, x.y * scale, x.z * scale, x.w * scale);
                         } else {
                             if (PASS == P_XF) {

@@ -85,6 +85,48 @@ __global__ void k_inv_lap(const cufftComplex *in, cufftComplex *out, int N, cons
     }
 }
 
+// Order-4/6 inverse Laplacian: Lambda(k) = sum over axes of the 1D second-derivative symbol
+// (lap1, per grid index, including 1/d^2).
+__global__ void k_inv_lap_sym(const cufftComplex *in, cufftComplex *out, int N, const float *lap1, float scale) {
+    const int Nz = N / 2 + 1;
+    const long long n = (long long)N * N * Nz;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int kz = (int)(idx % Nz);
+        const long long t = idx / Nz;
+        const int ky = (int)(t % N);
+        const int kx = (int)(t / N);
+        const float lam = lap1[kx] + lap1[ky] + lap1[kz];
+        cufftComplex v = in[idx];
+        const float m = (lam != 0.0f) ? scale / lam : 0.0f;
+        v.x *= m;
+        v.y *= m;
+        out[idx] = v;
+    }
+}
+
+// Periodic central gradient of FDA order ORDER at the LPT grid nodes.
+template <int ORDER>
+__global__ void k_gradient_n(const float *phi, float *psi, int N, float inv_d) {
+    const long long N3 = (long long)N * N * N;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < N3;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int c[3] = {(int)(idx / ((long long)N * N)), (int)((idx / N) % N), (int)(idx % N)};
+        const long long st[3] = {(long long)N * N, N, 1};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float g = 0.0f;
+#pragma unroll
+            for (int m = 1; m <= Fda<ORDER>::ng; ++m) {
+                const int p = c[a] + m >= N ? c[a] + m - N : c[a] + m;
+                const int q = c[a] - m < 0 ? c[a] - m + N : c[a] - m;
+                g = fmaf(Fda<ORDER>::g(m), phi[idx + (p - c[a]) * st[a]] - phi[idx + (q - c[a]) * st[a]], g);
+            }
+            psi[a * N3 + idx] = g * inv_d;
+        }
+    }
+}
+
 __global__ void k_second_derivative(const cufftComplex *in, cufftComplex *out, int N,
                                     const float *s_full, int ai, int aj) {
     const int Nz = N / 2 + 1;
@@ -172,8 +214,11 @@ cudaError_t launch_inv_laplacian(Ctx &c, const cufftComplex *in, cufftComplex *o
     const int N = c.Np;
     const long long n = (long long)N * N * (N / 2 + 1);
     const double d = c.L / N;
-    k_inv_lap<<<grid_for(n, 256), 256, 0, c.stream>>>(in, out, N, c.table_arena + c.sin_half_off,
-                                                       (float)(1.0 / (d * d)), scale);
+    if (c.prm.fda_order != 2)
+        k_inv_lap_sym<<<grid_for(n, 256), 256, 0, c.stream>>>(in, out, N, c.table_arena + c.lap1_off, scale);
+    else
+        k_inv_lap<<<grid_for(n, 256), 256, 0, c.stream>>>(in, out, N, c.table_arena + c.sin_half_off,
+                                                           (float)(1.0 / (d * d)), scale);
     ++c.launches;
     return cudaGetLastError();
 }
@@ -183,7 +228,7 @@ cudaError_t launch_second_derivative(Ctx &c, const cufftComplex *in, cufftComple
     const int N = c.Np;
     const long long n = (long long)N * N * (N / 2 + 1);
     k_second_derivative<<<grid_for(n, 256), 256, 0, c.stream>>>(
-        in, out, N, c.table_arena + c.sin_full_off, i, j);
+        in, out, N, c.table_arena + (c.prm.fda_order != 2 ? c.grad1_off : c.sin_full_off), i, j);
     ++c.launches;
     return cudaGetLastError();
 }
@@ -203,7 +248,11 @@ cudaError_t launch_source_sub(Ctx &c, const float *t, float *S) {
 
 cudaError_t launch_gradient(Ctx &c, const float *phi, float *psi) {
     const double d = c.L / c.Np;
-    k_gradient<<<grid_for(c.N3, 256), 256, 0, c.stream>>>(phi, psi, c.Np, (float)(0.5 / d));
+    switch (c.prm.fda_order) {
+        case 4: k_gradient_n<4><<<grid_for(c.N3, 256), 256, 0, c.stream>>>(phi, psi, c.Np, (float)(1.0 / d)); break;
+        case 6: k_gradient_n<6><<<grid_for(c.N3, 256), 256, 0, c.stream>>>(phi, psi, c.Np, (float)(1.0 / d)); break;
+        default: k_gradient<<<grid_for(c.N3, 256), 256, 0, c.stream>>>(phi, psi, c.Np, (float)(0.5 / d));
+    }
     ++c.launches;
     return cudaGetLastError();
 }

@@ -34,10 +34,10 @@ k_pad(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
     const Chunk ch = chunks[blockIdx.x];
     const BoxDesc &B = boxes[ch.box];
     const long long idx = (long long)ch.start + threadIdx.x;
-    if (idx >= shell_count(B.Ng)) return;
+    if (idx >= shell_count(B.Ng, B.gpad)) return;
     int pi, pj, pk;
-    shell_coord(idx, B.Ng, pi, pj, pk);
-    const long long S = B.Ng + 4;
+    shell_coord(idx, B.Ng, B.gpad, pi, pj, pk);
+    const long long S = B.Ng + 2 * B.gpad;
     phi[B.pp_off + ((long long)pi * S + pj) * S + pk] = D1 * shell[B.sh_off + idx];
 }
 
@@ -186,9 +186,10 @@ k_dst(const BoxDesc *__restrict__ boxes, const DstTable *__restrict__ tables,
                     if (PASS == kZFwdF) {
                         out[m_off + p * Ng + t] = X[t * kXS + c];
                     } else {
-                        const long long S = Ng + 4;
+                        const int G = B.gpad;
+                        const long long S = Ng + 2 * G;
                         const int i = (int)(p / Ng), j = (int)(p % Ng);
-                        out[pp_off + ((long long)(i + 2) * S + (j + 2)) * S + 2 + t] = X[t * kXS + c];
+                        out[pp_off + ((long long)(i + G) * S + (j + G)) * S + G + t] = X[t * kXS + c];
                     }
                 }
             }
@@ -198,63 +199,94 @@ k_dst(const BoxDesc *__restrict__ boxes, const DstTable *__restrict__ tables,
 }
 
 // ------------------------------------------------------------------ interpolation
+// grad (stored potential) at a particle: the central gradient of FDA order ORDER at the 8
+// CIC corners, CIC-interpolated.  The mesh coordinate is clamped to [-N_ghost,
+// Ng + N_ghost - 1] and the lower corner capped at Ng + N_ghost - 2 (the gradient exists on
+// the grid padded by N_ghost, Sec. 3.4.2).
+template <int ORDER>
 __device__ __forceinline__ void interpolate_force(const BoxDesc &B, const float *__restrict__ phi,
                                                   const int b[3], const float s[3], float F[3]) {
-    const int Ng = B.Ng;
+    const int Ng = B.Ng, G = B.gpad, ng = Fda<ORDER>::ng;
     int i0[3];
     float w[3][2];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         float u = fmaf(s[a], B.inv_dg, fmaf((float)b[a], B.q2u, 0.5f * B.q2u - 0.5f));
-        u = fminf(fmaxf(u, -1.0f), (float)Ng);
+        u = fminf(fmaxf(u, -(float)ng), (float)(Ng + ng - 1));
         int fl = (int)floorf(u);
-        fl = min(fl, Ng - 1);
+        fl = min(fl, Ng + ng - 2);
         i0[a] = fl;
         const float f = u - (float)fl;
         w[a][0] = 1.0f - f;
         w[a][1] = f;
     }
-    const long long S1 = Ng + 4, S2 = S1 * S1;
-    const float *P = phi + B.pp_off + ((long long)(i0[0] + 2) * S1 + (i0[1] + 2)) * S1 + (i0[2] + 2);
-    float core[2][2][2], xm[2][2], xp[2][2], ym[2][2], yp[2][2], zm[2][2], zp[2][2];
+    const long long S1 = Ng + 2 * G, S2 = S1 * S1;
+    const float *P = phi + B.pp_off + ((long long)(i0[0] + G) * S1 + (i0[1] + G)) * S1 + (i0[2] + G);
+    if (ORDER == 2) {
+        float core[2][2][2], xm[2][2], xp[2][2], ym[2][2], yp[2][2], zm[2][2], zp[2][2];
 #pragma unroll
-    for (int a = 0; a < 2; ++a)
+        for (int a = 0; a < 2; ++a)
 #pragma unroll
-        for (int bb = 0; bb < 2; ++bb)
+            for (int bb = 0; bb < 2; ++bb)
 #pragma unroll
-            for (int c = 0; c < 2; ++c) core[a][bb][c] = __ldg(P + a * S2 + bb * S1 + c);
+                for (int c = 0; c < 2; ++c) core[a][bb][c] = __ldg(P + a * S2 + bb * S1 + c);
 #pragma unroll
-    for (int p = 0; p < 2; ++p)
+        for (int p = 0; p < 2; ++p)
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            xm[p][q] = __ldg(P - S2 + p * S1 + q);
-            xp[p][q] = __ldg(P + 2 * S2 + p * S1 + q);
-            ym[p][q] = __ldg(P + p * S2 - S1 + q);
-            yp[p][q] = __ldg(P + p * S2 + 2 * S1 + q);
-            zm[p][q] = __ldg(P + p * S2 + q * S1 - 1);
-            zp[p][q] = __ldg(P + p * S2 + q * S1 + 2);
-        }
-    float fx = 0.0f, fy = 0.0f, fz = 0.0f;
+            for (int q = 0; q < 2; ++q) {
+                xm[p][q] = __ldg(P - S2 + p * S1 + q);
+                xp[p][q] = __ldg(P + 2 * S2 + p * S1 + q);
+                ym[p][q] = __ldg(P + p * S2 - S1 + q);
+                yp[p][q] = __ldg(P + p * S2 + 2 * S1 + q);
+                zm[p][q] = __ldg(P + p * S2 + q * S1 - 1);
+                zp[p][q] = __ldg(P + p * S2 + q * S1 + 2);
+            }
+        float fx = 0.0f, fy = 0.0f, fz = 0.0f;
 #pragma unroll
-    for (int p = 0; p < 2; ++p)
+        for (int p = 0; p < 2; ++p)
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            // x gradient at corners (0|1, p, q)
-            fx += w[1][p] * w[2][q] *
-                  (w[0][0] * (core[1][p][q] - xm[p][q]) + w[0][1] * (xp[p][q] - core[0][p][q]));
-            // y gradient at corners (p, 0|1, q)
-            fy += w[0][p] * w[2][q] *
-                  (w[1][0] * (core[p][1][q] - ym[p][q]) + w[1][1] * (yp[p][q] - core[p][0][q]));
-            // z gradient at corners (p, q, 0|1)
-            fz += w[0][p] * w[1][q] *
-                  (w[2][0] * (core[p][q][1] - zm[p][q]) + w[2][1] * (zp[p][q] - core[p][q][0]));
-        }
-    const float h = 0.5f * B.inv_dg;
-    F[0] = fx * h;
-    F[1] = fy * h;
-    F[2] = fz * h;
+            for (int q = 0; q < 2; ++q) {
+                // x gradient at corners (0|1, p, q)
+                fx += w[1][p] * w[2][q] *
+                      (w[0][0] * (core[1][p][q] - xm[p][q]) + w[0][1] * (xp[p][q] - core[0][p][q]));
+                // y gradient at corners (p, 0|1, q)
+                fy += w[0][p] * w[2][q] *
+                      (w[1][0] * (core[p][1][q] - ym[p][q]) + w[1][1] * (yp[p][q] - core[p][0][q]));
+                // z gradient at corners (p, q, 0|1)
+                fz += w[0][p] * w[1][q] *
+                      (w[2][0] * (core[p][q][1] - zm[p][q]) + w[2][1] * (zp[p][q] - core[p][q][0]));
+            }
+        const float h = 0.5f * B.inv_dg;
+        F[0] = fx * h;
+        F[1] = fy * h;
+        F[2] = fz * h;
+        return;
+    }
+    // orders 4 and 6: sum_m g_m (Phi(c + m e_a) - Phi(c - m e_a)) at every corner c
+    const long long st[3] = {S2, S1, 1};
+    float acc[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int dx = 0; dx < 2; ++dx)
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+            for (int dz = 0; dz < 2; ++dz) {
+                const float wc = w[0][dx] * w[1][dy] * w[2][dz];
+                const float *C = P + dx * S2 + dy * S1 + dz;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    float g = 0.0f;
+#pragma unroll
+                    for (int m = 1; m <= Fda<ORDER>::ng; ++m)
+                        g = fmaf(Fda<ORDER>::g(m), __ldg(C + m * st[a]) - __ldg(C - m * st[a]), g);
+                    acc[a] = fmaf(wc, g, acc[a]);
+                }
+            }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) F[a] = acc[a] * B.inv_dg;
 }
 
+template <int ORDER>
 __global__ void __launch_bounds__(kChunk)
 k_interp(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
          const float *__restrict__ s, long long stride, const float *__restrict__ phi, float D1,
@@ -269,12 +301,13 @@ k_interp(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
     decode_local(local, Nsc, b[0], b[1], b[2]);
     float sv[3] = {s[gi], s[stride + gi], s[2 * stride + gi]};
     float f[3];
-    interpolate_force(B, phi, b, sv, f);
+    interpolate_force<ORDER>(B, phi, b, sv, f);
     F[gi] = D1 * f[0];
     F[stride + gi] = D1 * f[1];
     F[2 * stride + gi] = D1 * f[2];
 }
 
+template <int ORDER>
 __global__ void __launch_bounds__(kChunk, 5)
 k_kick_drift(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
              float *__restrict__ part, long long P, const float *__restrict__ phi, KickDrift kd,
@@ -305,7 +338,7 @@ k_kick_drift(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks
             p2[a] = __ldg(part + (9 + a) * P + gi);
         }
         float F[3];
-        interpolate_force(B, phi, b, s, F);
+        interpolate_force<ORDER>(B, phi, b, s, F);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             p[a] = fmaf(kd.kF, F[a], fmaf(kd.k1, p1[a], fmaf(kd.k2, p2[a], p[a])));
@@ -434,7 +467,11 @@ cudaError_t launch_poisson_pass(Ctx &c, int pass) {
 }
 
 cudaError_t launch_interp(Ctx &c, const float *s, long long stride, float *F, float D1) {
-    k_interp<<<c.n_pchunks, kChunk, 0, c.stream>>>(c.boxes, c.pchunks, s, stride, c.phi, D1, F);
+    switch (c.prm.fda_order) {
+        case 4: k_interp<4><<<c.n_pchunks, kChunk, 0, c.stream>>>(c.boxes, c.pchunks, s, stride, c.phi, D1, F); break;
+        case 6: k_interp<6><<<c.n_pchunks, kChunk, 0, c.stream>>>(c.boxes, c.pchunks, s, stride, c.phi, D1, F); break;
+        default: k_interp<2><<<c.n_pchunks, kChunk, 0, c.stream>>>(c.boxes, c.pchunks, s, stride, c.phi, D1, F);
+    }
     ++c.launches;
     return cudaGetLastError();
 }
@@ -454,9 +491,21 @@ cudaError_t launch_scaled_copy(Ctx &c, const float *in, float *out, long long n,
 }
 
 cudaError_t launch_kick_drift(Ctx &c, const KickDrift &kd, bool count_keys, int k) {
-    k_kick_drift<<<c.n_pchunks, kChunk, 0, c.stream>>>(c.boxes, c.pchunks, c.part, c.P, c.phi, kd,
-                                                        count_keys && kd.drift ? c.kcount : nullptr,
-                                                        k >= 0 ? c.coef : nullptr, k, c.coef_nk);
+    int *kc = count_keys && kd.drift ? c.kcount : nullptr;
+    const float *coef = k >= 0 ? c.coef : nullptr;
+    switch (c.prm.fda_order) {
+        case 4:
+            k_kick_drift<4><<<c.n_pchunks, kChunk, 0, c.stream>>>(c.boxes, c.pchunks, c.part, c.P, c.phi, kd, kc,
+                                                                   coef, k, c.coef_nk);
+            break;
+        case 6:
+            k_kick_drift<6><<<c.n_pchunks, kChunk, 0, c.stream>>>(c.boxes, c.pchunks, c.part, c.P, c.phi, kd, kc,
+                                                                   coef, k, c.coef_nk);
+            break;
+        default:
+            k_kick_drift<2><<<c.n_pchunks, kChunk, 0, c.stream>>>(c.boxes, c.pchunks, c.part, c.P, c.phi, kd, kc,
+                                                                   coef, k, c.coef_nk);
+    }
     ++c.launches;
     return cudaGetLastError();
 }

@@ -21,7 +21,7 @@ def workload_cfg(name, **over):
 
 def oracle_cfg(kw):
     keys = ("L", "Np", "Ntiles", "Nbuf", "mesh_ratio", "Ng", "nsteps", "a_i", "a_f", "Om", "OL", "h",
-            "ns", "sigma8", "nLPT", "lpt_order", "a_final")
+            "ns", "sigma8", "nLPT", "lpt_order", "a_final", "fda_order")
     d = {k: kw[k] for k in keys if k in kw}
     if "time_stepping" in kw:
         d["stepping"] = ("modified", "standard")[kw["time_stepping"]]
@@ -69,7 +69,7 @@ def box_initial_displacements(cfg, fields, sched, b):
 
 
 def oracle_shell(cfg, fields, g):
-    return boundary.bc_shell(fields.phi1, cfg.L, g.origin, g.dg, g.Ng)
+    return boundary.bc_shell(fields.phi1, cfg.L, g.origin, g.dg, g.Ng, cfg.fda_order)
 
 
 def sampled_box_errors(cfg, fields, sched, x, p, boxes, cache=None):

@@ -47,7 +47,7 @@ def test_validation_errors_without_gpu(lib):
     bad = lib.make_params(L=100.0, Np=32, Ntiles=2, Nbuf=4, Ng=20)    # Ng < Np,sCOLA
     with pytest.raises(lib.ScolaError):
         lib.scola_tiling_info(bad)
-    bad = lib.make_params(L=100.0, Np=32, Ntiles=2, Nbuf=4, fda_order=4)
+    bad = lib.make_params(L=100.0, Np=32, Ntiles=2, Nbuf=4, fda_order=8)
     with pytest.raises(lib.ScolaError) as e:
         lib.scola_tiling_info(bad)
     assert e.value.status == 2

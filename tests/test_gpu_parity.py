@@ -38,6 +38,9 @@ CASES_PM = {
     "uneven": dict(L=200.0, Np=64, Ntiles=2, buffers=[4, 8, 16, 4, 8, 4, 16, 8], mesh_ratio=1,
                    nsteps=4, a_i=0.02, a_f=1.0),                 # Ng = 40, 48, 64 in one launch
     "single_box": dict(L=80.0, Np=16, Ntiles=1, Nbuf=0, mesh_ratio=2, nsteps=3, a_i=0.02, a_f=1.0),
+    # FDA orders 4 and 6 (Sec. 3.1): wider stencils, 4 and 6 ghost layers per side
+    "fda4": dict(SMALL, fda_order=4, nsteps=4),
+    "fda6_ratio2": dict(SMALL, mesh_ratio=2, fda_order=6, nsteps=4),
     # Ng = 160 > 128 at 2:1: the tensor-core form folds the sine matrix by its mirror symmetry
     "fold_160": dict(L=80.0, Np=80, Ntiles=1, Nbuf=0, mesh_ratio=2, nsteps=10, a_i=0.02, a_f=1.0),
 }
@@ -57,7 +60,7 @@ def _to_dev(a):
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
 
 
-@pytest.mark.parametrize("name", ["plain_32", "single_box"])
+@pytest.mark.parametrize("name", ["plain_32", "single_box", "fda4", "fda6_ratio2"])
 def test_lpt_fields_match_oracle(name):
     kw = CASES_PM[name]
     w, f, _ = oracle_fields(kw)
@@ -105,7 +108,8 @@ def test_pm_force_matches_oracle(name, variant):
         s = 20.0 * s0
         s_all.append(s)
         qloc = (tiling.box_local_lattice(g.Nsc) + 0.5) * (cfg.L / cfg.Np)
-        refs.append((g, pm.box_force(qloc + s, g.dg, g.Ng, g.Nsc, D1 * oracle_shell(cfg, f, g))))
+        refs.append((g, pm.box_force(qloc + s, g.dg, g.Ng, g.Nsc, D1 * oracle_shell(cfg, f, g),
+                                     order=cfg.fda_order)))
     s_cat = np.concatenate(s_all).T.copy()
     F, delta, phi = sim.pm_force(_to_dev(s_cat), D1, want_delta=True, want_phi=True)
     torch.cuda.synchronize()
@@ -114,8 +118,9 @@ def test_pm_force_matches_oracle(name, variant):
     phi = phi.cpu().numpy().astype(np.float64)
     m_offs, pp_offs = sim.box_offsets()
     p_off = 0
+    G = kw.get("fda_order", 2)
     for (g, r), m_off, pp_off in zip(refs, m_offs, pp_offs):
-        n, ng3, np3 = g.Nsc**3, g.Ng**3, (g.Ng + 4) ** 3
+        n, ng3, np3 = g.Nsc**3, g.Ng**3, (g.Ng + 2 * G) ** 3
         Fb = F[:, p_off:p_off + n].T
         scale = np.abs(r["F"]).max()
         err = np.abs(Fb - r["F"])
@@ -126,7 +131,7 @@ def test_pm_force_matches_oracle(name, variant):
         # 1/nbar = (Ng/Nsc)^3 in delta
         atol = 4 * 2.0**-24 * g.Ng * (g.Ng / g.Nsc) ** 3 + 2e-6 * max(1.0, np.abs(r["delta"]).max())
         np.testing.assert_allclose(delta[m_off:m_off + ng3].reshape((g.Ng,) * 3), r["delta"], atol=atol)
-        phib = phi[pp_off:pp_off + np3].reshape((g.Ng + 4,) * 3)
+        phib = phi[pp_off:pp_off + np3].reshape((g.Ng + 2 * G,) * 3)
         assert np.abs(phib - r["phi"]).max() <= 2e-5 * np.abs(r["phi"]).max()
         p_off = p_off + n
     sc.scola_device_status(sim.ctx)
@@ -151,7 +156,7 @@ def _pk_rel_err(delta_a, delta_b, L, N):
 
 
 @pytest.mark.parametrize("variant", ["simt", "tc", "tc4"])
-@pytest.mark.parametrize("name", ["plain_32", "uneven", "table1_like", "fold_160"])
+@pytest.mark.parametrize("name", ["plain_32", "uneven", "table1_like", "fold_160", "fda4", "fda6_ratio2"])
 def test_forward_matches_oracle(name, variant):
     kw = CASES_PM[name]
     _skip_unsupported(kw, variant)
