@@ -73,6 +73,12 @@ typedef enum scola_time_stepping {
                                     kick prefactors (App. B) */
 } scola_time_stepping;
 
+typedef enum scola_study_mode {   /* bit flags (Sec. 4.3 approximation tests) */
+    SCOLA_STUDY_NONE = 0,            /* the method: delta_int = delta^sCOLA, Phi_BCs = Phi_LEP */
+    SCOLA_STUDY_TRUE_DENSITY = 1,    /* delta_int = delta of the periodic tCOLA run */
+    SCOLA_STUDY_TRUE_POTENTIAL = 2   /* Phi_BCs = Phi of the periodic tCOLA run */
+} scola_study_mode;
+
 typedef enum scola_batch_mode {
     SCOLA_BATCH_ALL = 0,         /* every box in each launch (batched form) */
     SCOLA_BATCH_PER_TILE = 1     /* one box per launch, boxes in turn (plain per-tile form) */
@@ -126,6 +132,16 @@ typedef enum scola_batch_mode {
  *                from a_i to a_final[t], and its particles leave scola_forward at that
  *                time (positions and momenta with L+ at a_final[t]).  All boxes still go
  *                through each launch together.  The adjoint needs a common a_f
+ *   study_mode   bit flags of scola_study_mode (Sec. 4.3).  0 runs the method.  Otherwise
+ *                scola_forward first runs the periodic full-box tCOLA of scola_tcola and
+ *                keeps its density and potential at every force evaluation, then evolves
+ *                the boxes with the interior density (TRUE_DENSITY) and/or the ghost-layer
+ *                potential (TRUE_POTENTIAL) taken from those fields instead of the box
+ *                deposit and the LEP shell.  The box meshes must coincide with cells of the
+ *                full-box mesh (Ng = mesh_ratio * Np,sCOLA), FDA order 2, no a_final, no
+ *                adjoint (UNSUPPORTED otherwise).  The records take 4 (nsteps + 1)
+ *                (mesh_ratio Np)^3 bytes per flag.  With both flags the boxes reproduce the
+ *                tCOLA run up to rounding.  Only scola_forward(_host) is affected
  *   lpt_order    2: initial conditions and the COLA frame from 2LPT (Eqs. 5-6, 39);
  *                1: the Zel'dovich approximation (Psi2 = 0: first-order displacements,
  *                frame and L+/L- from Psi1 alone, Sec. 2.2)
@@ -152,6 +168,7 @@ typedef struct scola_params {
     int32_t batch_boxes;         /* boxes per streamed batch; 0 = as many as fit */
     int32_t time_stepping;       /* one of scola_time_stepping */
     int32_t lpt_order;           /* 2: 2LPT frame (the paper's runs); 1: Zel'dovich frame */
+    int32_t study_mode;          /* scola_study_mode flags; 0 = the method */
     double Om, OL, h, ns, sigma8;
     double a_i, a_f;
     double nLPT;
@@ -182,6 +199,8 @@ typedef struct scola_stats {
                                      0 = not timed */
     int32_t batches;              /* streamed batches per forward run */
     int32_t batch_boxes;          /* boxes per batch (the last may hold fewer) */
+    double ms_tcola;              /* periodic tCOLA run (scola_tcola, or the study-mode records
+                                     of scola_forward), device time; 0 if none ran */
 } scola_stats;
 
 /*
@@ -192,7 +211,8 @@ typedef struct scola_stats {
  *   stream  cudaStream_t on which all later work is enqueued (NULL = legacy default)
  *   out     receives the new context
  * Errors: INVALID_ARG (Np % Ntiles != 0, Ng < Np,sCOLA, non-positive sizes,
- * a_i >= a_f, nsteps < 1, Np,sCOLA > Np), UNSUPPORTED (fda_order not 2, 4 or 6), OOM, CUDA.
+ * a_i >= a_f, nsteps < 1, Np,sCOLA > Np, study_mode outside 0..3), UNSUPPORTED (fda_order
+ * not 2, 4 or 6; a study mode with unaligned box meshes, FDA order 4/6 or a_final), OOM, CUDA.
  * Synchronous.
  */
 scola_status scola_create(const scola_params *params, void *stream, scola_ctx **out);
@@ -352,8 +372,8 @@ int32_t scola_uses_tensor_cores(const scola_ctx *ctx);
  * Adjoint support.  With checkpointing enabled, scola_forward also stores the
  * displacements of every box particle at every force evaluation (the
  * per-step checkpoints: (nsteps + 1) x 3 x P floats) and the context keeps
- * the adjoint work arrays.  Batched form, 2LPT frame and one batch only
- * (UNSUPPORTED otherwise).  Synchronises the stream.
+ * the adjoint work arrays.  Batched form, 2LPT frame, no study mode and one
+ * batch only (UNSUPPORTED otherwise).  Synchronises the stream.
  */
 scola_status scola_set_checkpointing(scola_ctx *ctx, int32_t enable);
 
@@ -436,6 +456,21 @@ scola_status scola_selftest_conversions(int64_t n, uint64_t seed, int64_t *misma
  */
 scola_status scola_power_spectrum(scola_ctx *ctx, const float *delta_dev, int32_t nbins, const double *edges,
                                   double *k_mean, double *pk, int64_t *n_modes);
+
+/*
+ * The periodic full-box tCOLA run (Sec. 2.2; the monolithic simulation that sCOLA
+ * approximates, Sec. 4): initial conditions and LPT as scola_forward, then all Np^3
+ * particles evolved with the same KDK factors on one periodic PM grid of mesh_ratio * Np
+ * cells per side (cells centred at (c + 1/2) dg, dg = L / (mesh_ratio Np)): periodic CIC
+ * deposit (2^-32 fixed point, deterministic), FFT Poisson solve with the FDA-2 Laplacian
+ * symbol (k = 0 removed), FDA-2 central gradient and periodic CIC interpolation.
+ *   w_dev  device, Np^3 white noise (as scola_forward)
+ *   x_dev  device, Np^3 x 3 final positions in [0, L), global-id order
+ *   p_dev  device, Np^3 x 3 final momenta (L+ applied), global-id order
+ * Every particle is written.  FP32 fields and particles; cuFFT transforms.
+ * Errors: INVALID_ARG (NULL), UNSUPPORTED (fda_order != 2), OOM, CUDA.
+ */
+scola_status scola_tcola(scola_ctx *ctx, const float *w_dev, float *x_dev, float *p_dev);
 
 scola_status scola_get_stats(const scola_ctx *ctx, scola_stats *out);
 const char *scola_status_string(scola_status status);

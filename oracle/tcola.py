@@ -8,6 +8,10 @@ monolithic simulation it approximates:
     aligned, as here);
   * Sec. 4.1-4.2: larger buffers bring sCOLA closer to tCOLA.
 
+``run_study`` is the approximation test of Sec. 4.3 itself: sCOLA boxes whose interior
+density (delta_int = delta) and/or boundary potential (Phi_BCs = Phi) come from this
+monolithic run instead of the box deposit and the LEP.
+
 Full-box PM with the same conventions as the box (cells centred at
 (C + 1/2) dg, dg = L / Ng_full, Ng_full = mesh_ratio * Np): periodic CIC deposit
 (operator B, Eq. 9), periodic FDA-2 Poisson solve in Fourier space
@@ -111,3 +115,41 @@ def box_cell_to_full(cfg, geom):
 def restrict_padded(field_full, idx):
     """Padded (Ng + 4)^3 restriction of a full-box grid field."""
     return field_full[np.ix_(idx[0], idx[1], idx[2])]
+
+
+def run_study(w, cfg, true_density=False, true_potential=False, boxes=None):
+    """Sec. 4.3: evolve the sCOLA boxes with delta_int = delta (``true_density``) and/or
+    Phi_BCs = Phi (``true_potential``) taken, at every force evaluation, from the periodic
+    tCOLA run of the same initial conditions; with neither flag this is the method itself.
+
+    Needs aligned grids (box Ng = mesh_ratio * Np,sCOLA) and FDA order 2.  Returns a dict
+    with the tCOLA result ("tcola"), the box results, and the untiled x, p, s.
+    """
+    if cfg.fda_order != 2 or cfg.a_final is not None:
+        raise ValueError("the study modes are written for FDA order 2 and a common a_f")
+    fields = scola.initial_fields(w, cfg)
+    sched = scola.schedule(cfg)
+    ref = run_tcola(cfg, fields, sched, record=True)
+    if boxes is None:
+        boxes = range(cfg.nboxes)
+    results = []
+    for b in boxes:
+        g = scola.box_geometry(cfg, b)
+        if g.Ng != cfg.mesh_ratio * g.Nsc:
+            raise ValueError("the study modes need Ng = mesh_ratio * Np,sCOLA")
+        idx = box_cell_to_full(cfg, g)
+        Ng = g.Ng
+
+        def dfn(k, idx=idx, Ng=Ng):
+            return restrict_padded(ref["deltas"][k], idx)[2:Ng + 2, 2:Ng + 2, 2:Ng + 2]
+
+        def pfn(k, idx=idx, Ng=Ng):
+            p = restrict_padded(ref["phis"][k], idx).copy()
+            p[2:Ng + 2, 2:Ng + 2, 2:Ng + 2] = 0.0      # only the ghost layers are boundary values
+            return p
+
+        results.append(scola.evolve_box(cfg, b, fields, sched,
+                                        delta_fn=dfn if true_density else None,
+                                        phi_bc_fn=pfn if true_potential else None))
+    x, p, s = scola.untile(cfg, results)
+    return {"tcola": ref, "boxes": results, "x": x, "p": p, "s": s, "fields": fields, "sched": sched}

@@ -26,6 +26,9 @@ SCOLA_STEPPING_STANDARD = 1
 SCOLA_DEPOSIT_AUTO = 0
 SCOLA_DEPOSIT_SORTED = 1
 SCOLA_DEPOSIT_ATOMIC = 2
+SCOLA_STUDY_NONE = 0
+SCOLA_STUDY_TRUE_DENSITY = 1
+SCOLA_STUDY_TRUE_POTENTIAL = 2
 
 
 class ScolaError(RuntimeError):
@@ -40,7 +43,7 @@ class ScolaParams(ctypes.Structure):
         ("mesh_ratio", c_int32), ("Ng", c_int32), ("fda_order", c_int32),
         ("dst_variant", c_int32), ("nsteps", c_int32), ("batch_mode", c_int32),
         ("box_first", c_int32), ("box_count", c_int32), ("deposit_form", c_int32), ("batch_boxes", c_int32),
-        ("time_stepping", c_int32), ("lpt_order", c_int32),
+        ("time_stepping", c_int32), ("lpt_order", c_int32), ("study_mode", c_int32),
         ("Om", c_double), ("OL", c_double), ("h", c_double), ("ns", c_double),
         ("sigma8", c_double), ("a_i", c_double), ("a_f", c_double), ("nLPT", c_double),
         ("buffers", ctypes.POINTER(c_int32)), ("a_final", ctypes.POINTER(c_double)),
@@ -54,6 +57,7 @@ class ScolaStats(ctypes.Structure):
         ("ms_lpt", c_double), ("ms_evolve", c_double), ("kernel_launches", c_int64),
         ("deposit_form", c_int32), ("deposit_threads", c_int32), ("deposit_split", c_int32),
         ("ms_deposit_candidates", c_double * 4), ("batches", c_int32), ("batch_boxes", c_int32),
+        ("ms_tcola", c_double),
     ]
 
 
@@ -67,6 +71,7 @@ _sig = {
     "scola_destroy": (None, [c_void_p]),
     "scola_forward": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "scola_forward_host": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "scola_tcola": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "scola_lpt_fields": (c_int32, [c_void_p] + [c_void_p] * 6),
     "scola_setup_boxes": (c_int32, [c_void_p]),
     "scola_pm_force": (c_int32, [c_void_p, c_void_p, c_double, c_void_p, c_void_p, c_void_p]),
@@ -126,13 +131,13 @@ def make_params(L, Np, Ntiles, Nbuf=0, mesh_ratio=1, Ng=0, nsteps=10, Om=0.3, OL
                 ns=0.96, sigma8=0.8, a_i=0.02, a_f=1.0, nLPT=-2.5, fda_order=2,
                 dst_variant=SCOLA_DST_AUTO, batch_mode=SCOLA_BATCH_ALL, buffers=None, box_first=0,
                 box_count=0, deposit_form=SCOLA_DEPOSIT_AUTO, batch_boxes=0,
-                time_stepping=SCOLA_STEPPING_MODIFIED, lpt_order=2, a_final=None):
+                time_stepping=SCOLA_STEPPING_MODIFIED, lpt_order=2, a_final=None, study_mode=SCOLA_STUDY_NONE):
     """Build a ScolaParams; ``buffers`` (per-tile widths) is kept alive on the struct."""
     p = ScolaParams(L=L, Np=Np, Ntiles=Ntiles, Nbuf=Nbuf, mesh_ratio=mesh_ratio, Ng=Ng,
                     fda_order=fda_order, dst_variant=dst_variant, nsteps=nsteps,
                     batch_mode=batch_mode, box_first=box_first, box_count=box_count,
                     deposit_form=deposit_form, batch_boxes=batch_boxes,
-                    time_stepping=time_stepping, lpt_order=lpt_order,
+                    time_stepping=time_stepping, lpt_order=lpt_order, study_mode=study_mode,
                     Om=Om, OL=OL,
                     h=h, ns=ns, sigma8=sigma8, a_i=a_i, a_f=a_f, nLPT=nLPT)
     if buffers is not None:
@@ -159,6 +164,10 @@ def scola_destroy(ctx):
 
 def scola_forward(ctx, w, x, p):
     _check(_lib.scola_forward(ctx, _ptr(w), _ptr(x), _ptr(p)), "scola_forward")
+
+
+def scola_tcola(ctx, w, x, p):
+    _check(_lib.scola_tcola(ctx, _ptr(w), _ptr(x), _ptr(p)), "scola_tcola")
 
 
 def scola_forward_host(ctx, w, x, p):

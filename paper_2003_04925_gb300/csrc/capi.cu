@@ -49,6 +49,8 @@ struct scola_ctx : public Ctx {
     float *w_h2d = nullptr, *x_h2d = nullptr, *p_h2d = nullptr;  // buffers of scola_forward_host
     bool profiling = false;
     std::vector<cudaEvent_t> prof_ev;    // KC_COUNT + 1 events per force evaluation
+    cudaEvent_t tc_ev[2] = {nullptr, nullptr};   // around the last periodic tCOLA run
+    bool tc_timed = false;
 };
 
 #define CK(call)                                                                     \
@@ -106,6 +108,7 @@ scola_status validate(const scola_params *p, std::vector<int32_t> &bufs, std::ve
     if (p->time_stepping != SCOLA_STEPPING_MODIFIED && p->time_stepping != SCOLA_STEPPING_STANDARD)
         return invalid("unknown time_stepping");
     if (p->lpt_order != 1 && p->lpt_order != 2) return invalid("lpt_order must be 1 or 2");
+    if (p->study_mode < 0 || p->study_mode > 3) return invalid("study_mode must be a combination of the study flags");
     if (p->a_final) {
         const long long nt = (long long)p->Ntiles * p->Ntiles * p->Ntiles;
         for (long long t = 0; t < nt; ++t)
@@ -149,6 +152,14 @@ scola_status validate(const scola_params *p, std::vector<int32_t> &bufs, std::ve
             return SCOLA_ERR_UNSUPPORTED;
         }
         geo[b] = {nsc, ng, bufs[b]};
+        if (p->study_mode && ng != p->mesh_ratio * nsc) {
+            set_error("the study modes need box meshes made of full-box mesh cells (Ng = mesh_ratio Np,sCOLA)");
+            return SCOLA_ERR_UNSUPPORTED;
+        }
+    }
+    if (p->study_mode && (p->fda_order != 2 || p->a_final)) {
+        set_error("the study modes are built for FDA order 2 and a common final scale factor");
+        return SCOLA_ERR_UNSUPPORTED;
     }
     return SCOLA_OK;
 }
@@ -437,6 +448,36 @@ scola_status bind_batch(scola_ctx *c, int k, bool force = false) {
 
 scola_status fill_light_cone_tables(scola_ctx *c);
 
+// The periodic tCOLA state (once per context) and, for the study flags set, the records of
+// delta_K and Phi_K at every force evaluation.
+scola_status tcola_alloc(scola_ctx *c) {
+    if (c->tc_part) return SCOLA_OK;
+    if (c->tc_ng < 1) {
+        set_error("the periodic tCOLA grid needs mesh_ratio >= 1");
+        return SCOLA_ERR_UNSUPPORTED;
+    }
+    const int N = c->tc_ng;
+    const long long nk = (long long)N * N * (N / 2 + 1), nrec = (long long)(c->prm.nsteps + 1) * c->tc_n3;
+    CS(dev_alloc(&c->tc_acc, c->tc_n3));
+    CK(cudaMemset(c->tc_acc, 0, sizeof(unsigned long long) * (size_t)c->tc_n3));
+    CS(dev_alloc(&c->tc_delta, c->tc_n3));
+    CS(dev_alloc(&c->tc_phi, c->tc_n3));
+    CS(dev_alloc(&c->tc_dk, nk));
+    if (c->prm.study_mode & SCOLA_STUDY_TRUE_DENSITY) CS(dev_alloc(&c->rec_delta, nrec));
+    if (c->prm.study_mode & SCOLA_STUDY_TRUE_POTENTIAL) CS(dev_alloc(&c->rec_phi, nrec));
+    CF(cufftPlan3d(&c->tc_r2c, N, N, N, CUFFT_R2C));
+    if (cufftPlan3d(&c->tc_c2r, N, N, N, CUFFT_C2R) != CUFFT_SUCCESS) {
+        cufftDestroy(c->tc_r2c);
+        set_error("cufftPlan3d failed for the periodic tCOLA grid");
+        return SCOLA_ERR_CUDA;
+    }
+    c->tc_plans = true;
+    CF(cufftSetStream(c->tc_r2c, c->stream));
+    CF(cufftSetStream(c->tc_c2r, c->stream));
+    CS(dev_alloc(&c->tc_part, 6 * c->N3));
+    return SCOLA_OK;
+}
+
 scola_status build(scola_ctx *c, const std::vector<BoxGeom> &all_geo) {
     const scola_params &p = c->prm;
     // the boxes this context evolves: all, or the range [box_first, box_first + box_count)
@@ -550,6 +591,18 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &all_geo) {
             arena.push_back((float)(2.0 * v / d));
         }
     }
+    // periodic tCOLA grid (Ngf = mesh_ratio Np): the 1D FDA-2 second-derivative symbol
+    // (2 / dg^2)(cos(2 pi n / Ngf) - 1) per grid index, n the wrapped wavenumber
+    if (p.mesh_ratio >= 1) {
+        c->tc_ng = p.mesh_ratio * p.Np;
+        c->tc_n3 = (long long)c->tc_ng * c->tc_ng * c->tc_ng;
+        const double dgf = p.L / c->tc_ng;
+        c->tc_lap_off = (long long)arena.size();
+        for (int i = 0; i < c->tc_ng; ++i) {
+            const int n = i < c->tc_ng / 2 ? i : i - c->tc_ng;
+            arena.push_back((float)(2.0 * (std::cos(2.0 * M_PI * n / c->tc_ng) - 1.0) / (dgf * dgf)));
+        }
+    }
     // tensor-core DST groups (one per distinct Ng): the FP32 sine matrix
     bool all_tc = true;
     for (auto &kv : c->tbl_of) all_tc = all_tc && tc_supported(kv.first);
@@ -610,6 +663,8 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &all_geo) {
     c->have_plans = true;
     CF(cufftSetStream(c->plan_r2c, c->stream));
     CF(cufftSetStream(c->plan_c2r, c->stream));
+    // study modes: the periodic tCOLA state and its records (before the batches are sized)
+    if (p.study_mode) CS(tcola_alloc(c));
 
     // streamed batches: as many consecutive boxes as params.batch_boxes allows, else as fit
     // in the free device memory after a reserve for the caller's w, x, p and the host-copy
@@ -713,6 +768,7 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &all_geo) {
     CK(init_pm_kernels(*c));
     CK(init_deposit_kernels());
     for (int i = 0; i < 4; ++i) CK(cudaEventCreate(&c->ev[i]));
+    for (int i = 0; i < 2; ++i) CK(cudaEventCreate(&c->tc_ev[i]));
     CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
 
     c->stats.nboxes = count;
@@ -789,6 +845,46 @@ KickDrift forward_kick(const TimeTable &t, int k) {
     KickDrift kd = kick_drift_coefficients(t, k);
     kd.kF = (float)(t.beta[k] * t.D1[k]);
     return kd;
+}
+
+// The periodic tCOLA run of all particles from the LPT fields of the last run_lpt, on the
+// context stream.  record: keep delta_K and Phi_K of every force evaluation K for the study
+// flags set (the boxes read them afterwards).
+scola_status run_tcola(scola_ctx *c, bool record) {
+    CS(tcola_alloc(c));
+    CK(cudaEventRecord(c->tc_ev[0], c->stream));
+    CK(launch_tc_init(*c));
+    const int n = (int)c->tt.alpha.size();
+    for (int k = 0; k <= n; ++k) {
+        float *delta = record && c->rec_delta ? c->rec_delta + (size_t)k * c->tc_n3 : c->tc_delta;
+        float *phi = record && c->rec_phi ? c->rec_phi + (size_t)k * c->tc_n3 : c->tc_phi;
+        CK(launch_tc_density(*c, delta));
+        CF(cufftExecR2C(c->tc_r2c, delta, c->tc_dk));
+        CK(launch_tc_green(*c));
+        CF(cufftExecC2R(c->tc_c2r, c->tc_dk, phi));
+        CK(launch_tc_kick_drift(*c, phi, kick_drift_coefficients(c->tt, k)));
+    }
+    CK(cudaEventRecord(c->tc_ev[1], c->stream));
+    c->tc_timed = true;
+    return SCOLA_OK;
+}
+
+// Study inputs of force evaluation k (Sec. 4.3): the ghost layers from the recorded Phi_K
+// (before the source, which reads them), the Poisson source from the recorded delta_K.
+// Returns whether the source was written (else the deposit makes it).
+bool study_inputs(scola_ctx *c, int k, scola_status &st) {
+    st = SCOLA_OK;
+    const float inv_D1 = (float)(1.0 / c->tt.D1[k]);
+    cudaError_t e = cudaSuccess;
+    if (c->prm.study_mode & SCOLA_STUDY_TRUE_POTENTIAL)
+        e = launch_true_pad(*c, c->rec_phi + (size_t)k * c->tc_n3, inv_D1);
+    if (e == cudaSuccess && (c->prm.study_mode & SCOLA_STUDY_TRUE_DENSITY))
+        e = launch_true_source(*c, c->rec_delta + (size_t)k * c->tc_n3, inv_D1);
+    if (e != cudaSuccess) {
+        set_error(std::string("study inputs: ") + cudaGetErrorString(e));
+        st = SCOLA_ERR_CUDA;
+    }
+    return (c->prm.study_mode & SCOLA_STUDY_TRUE_DENSITY) != 0;
 }
 
 // Per-tile final scale factors: every context box's FP64 time table (one per distinct a_final)
@@ -939,7 +1035,10 @@ scola_status enqueue_evolution_per_tile(scola_ctx *c) {
         CK(launch_shell(*c));
         CK(launch_pad(*c, 1.0f));
         for (int k = 0; k <= n; ++k) {
-            CK(launch_deposit(*c, c->part, c->P, (float)(1.0 / c->tt.D1[k]), nullptr, false, k));
+            scola_status st;
+            const bool sourced = study_inputs(c, k, st);
+            CS(st);
+            if (!sourced) CK(launch_deposit(*c, c->part, c->P, (float)(1.0 / c->tt.D1[k]), nullptr, false, k));
             CK(launch_poisson(*c));
             CK(launch_kick_drift(*c, forward_kick(c->tt, k), false, k));
         }
@@ -964,13 +1063,16 @@ scola_status enqueue_evolution(scola_ctx *c) {
     // sorted deposit: each kick-drift counts the keys of the particles it moved, so the
     // next deposit skips its own count pass (the counts are cleared once the brick pass has
     // read them)
-    const bool fused = c->deposit_form == 0;
+    const bool fused = c->deposit_form == 0 && !(c->prm.study_mode & SCOLA_STUDY_TRUE_DENSITY);
     for (int k = 0; k <= n; ++k) {
         if (c->checkpointing)
             CK(cudaMemcpyAsync(c->ckpt + (size_t)k * 3 * c->P, c->part, sizeof(float) * 3 * (size_t)c->P,
                                cudaMemcpyDeviceToDevice, c->stream));
         CK(mark());
-        CK(launch_deposit(*c, c->part, c->P, (float)(1.0 / c->tt.D1[k]), nullptr, fused && k > 0, k));
+        scola_status st;
+        const bool sourced = study_inputs(c, k, st);
+        CS(st);
+        if (!sourced) CK(launch_deposit(*c, c->part, c->P, (float)(1.0 / c->tt.D1[k]), nullptr, fused && k > 0, k));
         if (fused && k < n) CK(clear_key_counts(*c));
         CK(mark());
         if (c->profiling) {
@@ -1115,6 +1217,10 @@ void scola_destroy(scola_ctx *c) {
         cufftDestroy(c->plan_r2c);
         cufftDestroy(c->plan_c2r);
     }
+    if (c->tc_plans) {
+        cufftDestroy(c->tc_r2c);
+        cufftDestroy(c->tc_c2r);
+    }
     void *ptrs[] = {c->boxes, c->all_boxes, c->all_coef, c->all_coefL, c->coef, c->coefL, c->tables, c->table_arena, c->pchunks, c->tchunks, c->shchunks,
                     c->zitems, c->citems, c->mchunks, c->ppchunks, c->tc_tiles, c->dev_err, c->ckpt,
                     c->adj, c->lamG, c->lam_phi_pad, c->adj_in, c->adj_out, c->lam_shell, c->lamPsi1,
@@ -1122,10 +1228,13 @@ void scola_destroy(scola_ctx *c) {
                     c->koffs, c->kcursor, c->sentries, c->sbricks,
                     c->work, c->work2, c->phi,
                     c->shell, c->ck, c->cp, c->ct, c->g[0], c->g[1], c->g[2], c->g[3], c->phi1,
-                    c->phi2, c->psi1, c->psi2, c->dens_acc, c->w_h2d, c->x_h2d, c->p_h2d};
+                    c->phi2, c->psi1, c->psi2, c->dens_acc, c->w_h2d, c->x_h2d, c->p_h2d,
+                    c->tc_part, c->tc_acc, c->tc_delta, c->tc_phi, c->tc_dk, c->rec_delta, c->rec_phi};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     for (auto &e : c->ev)
+        if (e) cudaEventDestroy(e);
+    for (auto &e : c->tc_ev)
         if (e) cudaEventDestroy(e);
     for (auto &e : c->prof_ev)
         if (e) cudaEventDestroy(e);
@@ -1204,6 +1313,8 @@ scola_status scola_forward(scola_ctx *c, const float *w, float *x, float *p) {
     long long graph_kernels = 0;
     CK(cudaEventRecord(c->ev[0], c->stream));
     CS(run_lpt(c, w, nullptr));
+    c->tc_timed = false;
+    if (c->prm.study_mode) CS(run_tcola(c, true));   // the true delta_K and Phi_K (counts in ms_lpt)
     CS(bind_batch(c, 0));
     CS(autotune_deposit(c));   // first call only; its time counts in ms_lpt
     CK(cudaEventRecord(c->ev[1], c->stream));
@@ -1223,10 +1334,29 @@ scola_status scola_forward(scola_ctx *c, const float *w, float *x, float *p) {
     return SCOLA_OK;
 }
 
+scola_status scola_tcola(scola_ctx *c, const float *w, float *x, float *p) {
+    if (!c || !w || !x || !p) return invalid("NULL argument");
+    if (c->prm.fda_order != 2) {
+        set_error("the periodic tCOLA run is built for FDA order 2");
+        return SCOLA_ERR_UNSUPPORTED;
+    }
+    const long long before = c->launches;
+    CS(run_lpt(c, w, nullptr));
+    c->tc_timed = false;
+    CS(run_tcola(c, false));
+    CK(launch_tc_final(*c, x, p));
+    c->stats.kernel_launches = c->launches - before;
+    return SCOLA_OK;
+}
+
 scola_status scola_set_checkpointing(scola_ctx *c, int32_t enable) {
     if (!c) return invalid("NULL context");
     CS(need_one_batch(c));
     const bool on = enable != 0;
+    if (on && c->prm.study_mode) {
+        set_error("the adjoint is not built for the study modes");
+        return SCOLA_ERR_UNSUPPORTED;
+    }
     if (on && c->prm.batch_mode == SCOLA_BATCH_PER_TILE) {
         set_error("the adjoint runs on the batched form only");
         return SCOLA_ERR_UNSUPPORTED;
@@ -1473,6 +1603,14 @@ scola_status scola_get_stats(const scola_ctx *cc, scola_stats *out) {
             out->ms_lpt = a;
             out->ms_evolve = b;
         }
+        cudaGetLastError();
+    }
+    out->ms_tcola = 0.0;
+    if (c->tc_timed && cudaEventQuery(c->tc_ev[1]) != cudaErrorNotReady) {
+        float t = 0;
+        if (cudaEventSynchronize(c->tc_ev[1]) == cudaSuccess &&
+            cudaEventElapsedTime(&t, c->tc_ev[0], c->tc_ev[1]) == cudaSuccess)
+            out->ms_tcola = t;
         cudaGetLastError();
     }
     return SCOLA_OK;

@@ -166,6 +166,19 @@ struct Ctx {
     bool have_plans = false;
     unsigned long long *dens_acc = nullptr;
 
+    // periodic full-box tCOLA (scola_tcola; the study-mode records of scola_forward):
+    // Ngf = mesh_ratio Np cells per side; particle state 6 x N3 (s, p_res rows, global-id
+    // order); fixed-point counts and FP32 work grids of Ngf^3; per force evaluation K the
+    // recorded delta_K and Phi_K ((nsteps + 1) x Ngf^3 each, for the study flags set)
+    int tc_ng = 0;
+    long long tc_n3 = 0, tc_lap_off = 0;              // tc_lap_off: 1D FDA-2 symbol per index in table_arena
+    float *tc_part = nullptr, *tc_delta = nullptr, *tc_phi = nullptr;
+    unsigned long long *tc_acc = nullptr;
+    cufftComplex *tc_dk = nullptr;
+    cufftHandle tc_r2c = 0, tc_c2r = 0;
+    bool tc_plans = false;
+    float *rec_delta = nullptr, *rec_phi = nullptr;
+
     // adjoint (scola_set_checkpointing / scola_backward)
     bool checkpointing = false, have_forward = false;
     float *ckpt = nullptr;                            // (nsteps+1) x 3 x P displacements
@@ -235,6 +248,18 @@ cudaError_t launch_final_density(Ctx &c, const float *x, float *delta);
 cudaError_t launch_spectrum(Ctx &c, const cufftComplex *dk, const int *bin_of_n2, int nbins, double *scratch,
                             int rows, double *out);
 constexpr int kMaxSpectrumBins = 2048;
+
+// periodic tCOLA (k_tcola.cu): particle init, deposit + density (clears the counts),
+// Green's function on tc_dk, kick-drift reading the potential phi, final x and p
+cudaError_t launch_tc_init(Ctx &c);
+cudaError_t launch_tc_density(Ctx &c, float *delta);
+cudaError_t launch_tc_green(Ctx &c);
+cudaError_t launch_tc_kick_drift(Ctx &c, const float *phi, const KickDrift &kd);
+cudaError_t launch_tc_final(Ctx &c, float *x, float *p);
+// study inputs of the bound batch's boxes: the Poisson source from a full-grid delta
+// (into work2), the ghost layers from a full-grid Phi (into the padded potential)
+cudaError_t launch_true_source(Ctx &c, const float *delta, float inv_D1);
+cudaError_t launch_true_pad(Ctx &c, const float *phi, float inv_D1);
 
 cudaError_t launch_adj_colour(Ctx &c, const cufftComplex *in, cufftComplex *out);
 cudaError_t launch_adj_final(Ctx &c, const float *lam_delta, float *adj);

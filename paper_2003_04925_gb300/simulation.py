@@ -45,6 +45,14 @@ class Scola:
         B.scola_forward(self.ctx, w.contiguous(), x, p)
         return x, p
 
+    def tcola(self, w, x=None, p=None):
+        """Periodic full-box tCOLA run of all particles from w -> (x, p), each (Np^3, 3)."""
+        n = self.Np ** 3
+        x = self._empty(n, 3) if x is None else x
+        p = self._empty(n, 3) if p is None else p
+        B.scola_tcola(self.ctx, w.contiguous(), x, p)
+        return x, p
+
     def forward_host(self, w_host, x_host, p_host):
         B.scola_forward_host(self.ctx, w_host, x_host, p_host)
 

@@ -67,6 +67,21 @@ def test_validation_errors_without_gpu(lib):
     with pytest.raises(lib.ScolaError) as e:
         lib.scola_tiling_info(bad)
     assert e.value.status == 1
+    bad = lib.make_params(L=100.0, Np=32, Ntiles=2, Nbuf=4, study_mode=4)
+    with pytest.raises(lib.ScolaError) as e:
+        lib.scola_tiling_info(bad)
+    assert e.value.status == 1
+    # the study modes need box meshes made of full-box cells, FDA order 2 and a common a_f
+    both = lib.SCOLA_STUDY_TRUE_DENSITY | lib.SCOLA_STUDY_TRUE_POTENTIAL
+    for bad in (lib.make_params(L=100.0, Np=32, Ntiles=2, Nbuf=4, Ng=30, study_mode=both),
+                lib.make_params(L=100.0, Np=32, Ntiles=2, Nbuf=4, fda_order=4, study_mode=1),
+                lib.make_params(L=100.0, Np=32, Ntiles=2, Nbuf=4, study_mode=2, a_final=[0.5] * 8)):
+        with pytest.raises(lib.ScolaError) as e:
+            lib.scola_tiling_info(bad)
+        assert e.value.status == 2
+    for ok in (lib.make_params(L=100.0, Np=32, Ntiles=2, Nbuf=4, mesh_ratio=2, study_mode=both),
+               lib.make_params(L=100.0, Np=32, Ntiles=2, Nbuf=4, Ng=24, mesh_ratio=1, study_mode=1)):
+        lib.scola_tiling_info(ok)
 
 
 def test_struct_layout_matches_header(lib, tmp_path):

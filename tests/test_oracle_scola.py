@@ -96,28 +96,6 @@ def test_small_amplitude_residual_scales_linearly():
     assert ratios[0] < 0.5
 
 
-def _true_density_true_potential_run(cfg, w):
-    f = scola.initial_fields(w, cfg)
-    sch = scola.schedule(cfg)
-    ref = tcola.run_tcola(cfg, f, sch, record=True)
-    res = []
-    for b in range(cfg.nboxes):
-        g = scola.box_geometry(cfg, b)
-        idx = tcola.box_cell_to_full(cfg, g)
-        Ng = g.Ng
-
-        def dfn(k, idx=idx, Ng=Ng):
-            return tcola.restrict_padded(ref["deltas"][k], idx)[2:Ng + 2, 2:Ng + 2, 2:Ng + 2]
-
-        def pfn(k, idx=idx, Ng=Ng):
-            p = tcola.restrict_padded(ref["phis"][k], idx).copy()
-            p[2:Ng + 2, 2:Ng + 2, 2:Ng + 2] = 0.0
-            return p
-
-        res.append(scola.evolve_box(cfg, b, f, sch, delta_fn=dfn, phi_bc_fn=pfn))
-    return ref, res
-
-
 @pytest.mark.parametrize("ratio", [1, 2])
 def test_true_density_and_potential_reproduce_tcola(ratio):
     # Sec. 4.3: with delta_int = delta and Phi_BCs = Phi (both from the monolithic run),
@@ -126,13 +104,45 @@ def test_true_density_and_potential_reproduce_tcola(ratio):
     # the DST solve, the ghost padding, gradient, interpolation and the kick/drift path).
     cfg = _cfg(Np=16, Ntiles=2, Nbuf=3, mesh_ratio=ratio, nsteps=3)
     w = synth_inputs.white_noise(16, 9).astype(np.float64) * 0.6
-    ref, res = _true_density_true_potential_run(cfg, w)
+    out = tcola.run_study(w, cfg, true_density=True, true_potential=True)
+    ref, res = out["tcola"], out["boxes"]
     keep = tiling.tile_interior_mask(cfg.Np, cfg.Ntiles, 3)
     for r in res:
         ids = r["ids"][keep]
         scale = np.abs(ref["s"]).max()
         np.testing.assert_allclose(r["s"][keep], ref["s"][ids], atol=1e-9 * scale)
         np.testing.assert_allclose(r["p"][keep], ref["p"][ids], atol=1e-9 * np.abs(ref["p"]).max())
+
+
+def test_single_study_modes_mix_the_two_runs():
+    # Each single substitution of Sec. 4.3 keeps one approximation of the method: its result
+    # differs both from tCOLA and from the plain method, while the untouched side matches the
+    # method's own input.  At the first force evaluation the true density of a box equals
+    # its own deposit in the cells no outside particle reaches (more than the largest
+    # displacement plus one CIC cell from the faces).
+    cfg = _cfg(Np=16, Ntiles=2, Nbuf=3, mesh_ratio=1, nsteps=3)
+    w = synth_inputs.white_noise(16, 9).astype(np.float64) * 0.6
+    method = scola.run_scola(w, cfg)
+    both = tcola.run_study(w, cfg, True, True)
+    for flags in ((True, False), (False, True)):
+        one = tcola.run_study(w, cfg, *flags)
+        d_method = np.abs(one["s"] - method["s"]).max()
+        d_tcola = np.abs(one["s"] - both["tcola"]["s"]).max()
+        assert d_method > 1e-6 and d_tcola > 1e-6, (flags, d_method, d_tcola)
+    from oracle import pm
+    f, sch = method["fields"], method["sched"]
+    ref = both["tcola"]
+    g = scola.box_geometry(cfg, 0)
+    ids = tiling.box_global_ids(cfg.Np, cfg.Ntiles, g.t, g.Nbuf)
+    s0 = (-sch["D1_i"] * f.psi1 + sch["D2_i"] * f.psi2).reshape(3, -1).T[ids]
+    q = (tiling.box_local_lattice(g.Nsc) + 0.5) * (cfg.L / cfg.Np)
+    own = pm.box_force(q + s0, g.dg, g.Ng, g.Nsc, np.zeros((g.Ng + 4,) * 3))["delta"]
+    true = tcola.restrict_padded(ref["deltas"][0], tcola.box_cell_to_full(cfg, g))[2:-2, 2:-2, 2:-2]
+    m = int(np.ceil(np.abs(s0).max() / g.dg)) + 2
+    inner = (slice(m, g.Ng - m),) * 3
+    assert g.Ng - 2 * m >= 2
+    np.testing.assert_allclose(own[inner], true[inner], atol=1e-12)
+    assert np.abs(own - true).max() > 1e-6       # near the faces the outside particles count
 
 
 @pytest.mark.slow
