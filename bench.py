@@ -45,6 +45,10 @@ def parse():
                          "CUDA cores (simt)")
     ap.add_argument("--forward-only", action="store_true",
                     help="only W + K forward runs of the batched form (for ncu launch lists)")
+    ap.add_argument("--batch-boxes", type=int, default=0,
+                    help="boxes per streamed batch (0: the library's choice)")
+    ap.add_argument("--tcola-only", action="store_true",
+                    help="only W + K periodic tCOLA runs of the workload's particles (for ncu captures)")
     return ap.parse_args()
 
 
@@ -265,6 +269,64 @@ def adjoint_cost(sc, torch, dst, steps):
             "loss": "sum over the 128^3 CIC mesh of (delta - delta_target)^2, target from seed 2"}
 
 
+def study_cost(sc, torch, kw, W, steps, peaks):
+    """The approximation-study workload (Sec. 4.3) on the bench configuration: the periodic
+    tCOLA run of all Np^3 particles (mesh_ratio Np cells per side) and the sCOLA run with
+    the true density and potential of that run at every force evaluation.  Device time per
+    run (CUDA events), tCOLA particle-steps/s, and the tCOLA stages per force evaluation with
+    the roofline of the slowest of the stages written here (the Poisson stage is cuFFT).
+
+    Algorithmic bytes per force evaluation (N3 = Np^3 particles, C = Ngf^3 cells):
+      deposit     12 N3 (positions) + 16 C (64-bit counts read and written once)
+      density     20 C (counts read, cleared; delta written)
+      kick_drift  72 N3 (s, p read and written, Psi1, Psi2 read) + 4 C (Phi read once)
+    """
+    import synth_inputs
+    sim = sc.Scola(**dict(kw, study_mode=sc.SCOLA_STUDY_TRUE_DENSITY | sc.SCOLA_STUDY_TRUE_POTENTIAL))
+    n = kw["Np"] ** 3
+    w = torch.from_numpy(synth_inputs.white_noise(kw["Np"], W["seed"])).cuda()
+    x = torch.empty(n, 3, device="cuda")
+    p = torch.empty(n, 3, device="cuda")
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    for _ in range(2):
+        sim.forward(w, x, p)
+        sim.tcola(w, x, p)
+    torch.cuda.synchronize()
+    t_tc = t_st = 0.0
+    for _ in range(steps):
+        ev[0].record(stream)
+        sim.tcola(w, x, p)
+        ev[1].record(stream)
+        sim.forward(w, x, p)
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        t_tc += ev[0].elapsed_time(ev[1])
+        t_st += ev[1].elapsed_time(ev[2])
+    t_tc, t_st = t_tc / steps, t_st / steps
+    sc.scola_set_profiling(sim.ctx, True)
+    sim.tcola(w, x, p)
+    torch.cuda.synchronize()
+    st = sc.scola_tcola_kernel_times(sim.ctx)
+    sc.scola_set_profiling(sim.ctx, False)
+    sc.scola_device_status(sim.ctx)
+    sim.close()
+    C = (kw["mesh_ratio"] * kw["Np"]) ** 3
+    work = {"tc_deposit": 12.0 * n + 16.0 * C, "tc_density": 20.0 * C, "tc_kick_drift": 72.0 * n + 4.0 * C}
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    rows = {k: {"ms_per_eval": round(st[k], 5), "achieved_gbs": work[k] / (st[k] * 1e-3) / 1e9,
+                "frac": work[k] / (st[k] * 1e-3) / 1e9 / hbm} for k in work}
+    dom = max(rows, key=lambda k: rows[k]["ms_per_eval"])
+    return {"workload": "periodic tCOLA of the same %d^3 particles on a %d^3 mesh, and sCOLA with the "
+                        "true density and potential (Sec. 4.3)" % (kw["Np"], kw["mesh_ratio"] * kw["Np"]),
+            "ms_tcola_run": t_tc, "tcola_particle_steps_per_s": n * kw["nsteps"] / (t_tc * 1e-3),
+            "ms_study_run": t_st,
+            "tcola_stages_ms_per_eval": {k: round(v, 5) for k, v in st.items()},
+            "roofline": {"kernel": dom, "bound": "hbm", "achieved": rows[dom]["achieved_gbs"], "peak": hbm,
+                         "unit": "GB/s", "frac": rows[dom]["frac"],
+                         "kernels": rows}}
+
+
 # ----------------------------------------------------------------------------- roofline
 def kernel_roofline(kt, kw, clocks, peaks, tc):
     """Algorithmic bytes or flops per launch of each kernel class and the dominant one.
@@ -356,6 +418,8 @@ def run_gpu(args, rank, world, local_rank):
     kw, W = workload_kwargs(args.workload)
     kw["dst_variant"] = {"tc": sc.SCOLA_DST_TC_3XTF32, "tc4": sc.SCOLA_DST_TC_4XTF32,
                          "simt": sc.SCOLA_DST_SIMT}[args.dst]
+    if args.batch_boxes:
+        kw["batch_boxes"] = args.batch_boxes
     sim = sc.Scola(**kw)
     stream = torch.cuda.current_stream()
     w_np = synth_inputs.white_noise(kw["Np"], W["seed"] + rank)
@@ -363,6 +427,16 @@ def run_gpu(args, rank, world, local_rank):
     n = kw["Np"] ** 3
     x = torch.empty(n, 3, device="cuda")
     p = torch.empty(n, 3, device="cuda")
+    if args.tcola_only:
+        t0 = time.perf_counter()
+        for _ in range(args.warmup + args.steps):
+            sim.tcola(w, x, p)
+        torch.cuda.synchronize()
+        if rank == 0:
+            print(json.dumps({"tcola_only": True, "workload": args.workload, "runs": args.warmup + args.steps,
+                              "ms_per_run": 1e3 * (time.perf_counter() - t0) / max(1, args.warmup + args.steps)}))
+        sim.close()
+        return
     for _ in range(args.warmup):
         sim.forward(w, x, p)
     torch.cuda.synchronize()
@@ -469,6 +543,7 @@ def run_gpu(args, rank, world, local_rank):
                             for k, v in rows.items()}}
 
     adj = adjoint_cost(sc, torch, args.dst, max(2, min(args.steps, 5)))
+    study = study_cost(sc, torch, {k: v for k, v in kw.items()}, W, max(2, min(args.steps, 5)), peaks)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -489,7 +564,7 @@ def run_gpu(args, rank, world, local_rank):
                     "dst": {"tc": "dense sine-matrix pencils on tcgen05 tensor cores, 3xTF32",
                             "tc4": "dense sine-matrix pencils on tcgen05 tensor cores, 4xTF32",
                             "simt": "dense sine-matrix pencils, FP32 CUDA cores"}[args.dst]}),
-                "e2e": e2e, "per_tile": per_tile, "adjoint": adj,
+                "e2e": e2e, "per_tile": per_tile, "adjoint": adj, "study": study,
                 "gpu_launches": int(launches * args.steps),
                 "clocks": clk,
                 "roofline": roofline, "cpu_baseline": cpu,

@@ -356,6 +356,15 @@ scola_status scola_set_profiling(scola_ctx *ctx, int32_t enable);
 scola_status scola_kernel_times(const scola_ctx *ctx, double *ms_per_launch, int32_t n);
 
 /*
+ * Average device time per force evaluation [ms] of the stages of the last periodic tCOLA
+ * run (scola_tcola, or the study-mode records of scola_forward) made in profiling mode.
+ * ms_per_launch (host, n >= 4 doubles) receives: periodic CIC deposit, density (counts ->
+ * delta, clearing the counts), Poisson solve (cuFFT R2C, Green's function, cuFFT C2R),
+ * interpolate + kick + drift.  Errors: STATE when no tCOLA run was profiled.
+ */
+scola_status scola_tcola_kernel_times(const scola_ctx *ctx, double *ms_per_launch, int32_t n);
+
+/*
  * Synchronises the stream and reports whether a kernel gave up on a bounded
  * wait since the context was created: SCOLA_OK, or SCOLA_ERR_TIMEOUT (results
  * of the affected launch are invalid; the context stays usable), or

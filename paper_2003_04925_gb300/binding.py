@@ -87,6 +87,7 @@ _sig = {
     "scola_get_stats": (c_int32, [c_void_p, _P(ScolaStats)]),
     "scola_set_profiling": (c_int32, [c_void_p, c_int32]),
     "scola_kernel_times": (c_int32, [c_void_p, _P(c_double), c_int32]),
+    "scola_tcola_kernel_times": (c_int32, [c_void_p, _P(c_double), c_int32]),
     "scola_device_status": (c_int32, [c_void_p]),
     "scola_uses_tensor_cores": (c_int32, [c_void_p]),
     "scola_set_checkpointing": (c_int32, [c_void_p, c_int32]),
@@ -268,6 +269,16 @@ def scola_kernel_times(ctx):
     arr = (c_double * len(KERNEL_CLASSES))()
     _check(_lib.scola_kernel_times(ctx, arr, len(KERNEL_CLASSES)), "scola_kernel_times")
     return dict(zip(KERNEL_CLASSES, list(arr)))
+
+
+TCOLA_STAGES = ("tc_deposit", "tc_density", "tc_poisson", "tc_kick_drift")
+
+
+def scola_tcola_kernel_times(ctx):
+    """Average ms per force evaluation of each stage of the last profiled tCOLA run."""
+    arr = (c_double * len(TCOLA_STAGES))()
+    _check(_lib.scola_tcola_kernel_times(ctx, arr, len(TCOLA_STAGES)), "scola_tcola_kernel_times")
+    return dict(zip(TCOLA_STAGES, list(arr)))
 
 
 def scola_device_status(ctx):

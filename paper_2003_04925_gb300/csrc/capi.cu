@@ -51,6 +51,8 @@ struct scola_ctx : public Ctx {
     std::vector<cudaEvent_t> prof_ev;    // KC_COUNT + 1 events per force evaluation
     cudaEvent_t tc_ev[2] = {nullptr, nullptr};   // around the last periodic tCOLA run
     bool tc_timed = false;
+    std::vector<cudaEvent_t> tc_prof_ev;  // profiling mode: 5 events per tCOLA force evaluation
+    bool tc_profiled = false;
 };
 
 #define CK(call)                                                                     \
@@ -855,15 +857,31 @@ scola_status run_tcola(scola_ctx *c, bool record) {
     CK(cudaEventRecord(c->tc_ev[0], c->stream));
     CK(launch_tc_init(*c));
     const int n = (int)c->tt.alpha.size();
+    // profiling mode: events between the stages of every force evaluation
+    const bool prof = c->profiling;
+    if (prof && c->tc_prof_ev.empty()) {
+        c->tc_prof_ev.assign(5 * (n + 1), nullptr);
+        for (auto &e : c->tc_prof_ev) CK(cudaEventCreate(&e));
+    }
+    auto mark = [&](int k, int q) -> cudaError_t {
+        return prof ? cudaEventRecord(c->tc_prof_ev[5 * k + q], c->stream) : cudaSuccess;
+    };
     for (int k = 0; k <= n; ++k) {
         float *delta = record && c->rec_delta ? c->rec_delta + (size_t)k * c->tc_n3 : c->tc_delta;
         float *phi = record && c->rec_phi ? c->rec_phi + (size_t)k * c->tc_n3 : c->tc_phi;
+        CK(mark(k, 0));
+        CK(launch_tc_deposit(*c));
+        CK(mark(k, 1));
         CK(launch_tc_density(*c, delta));
+        CK(mark(k, 2));
         CF(cufftExecR2C(c->tc_r2c, delta, c->tc_dk));
         CK(launch_tc_green(*c));
         CF(cufftExecC2R(c->tc_c2r, c->tc_dk, phi));
+        CK(mark(k, 3));
         CK(launch_tc_kick_drift(*c, phi, kick_drift_coefficients(c->tt, k)));
+        CK(mark(k, 4));
     }
+    c->tc_profiled = prof;
     CK(cudaEventRecord(c->tc_ev[1], c->stream));
     c->tc_timed = true;
     return SCOLA_OK;
@@ -1236,6 +1254,8 @@ void scola_destroy(scola_ctx *c) {
         if (e) cudaEventDestroy(e);
     for (auto &e : c->tc_ev)
         if (e) cudaEventDestroy(e);
+    for (auto &e : c->tc_prof_ev)
+        if (e) cudaEventDestroy(e);
     for (auto &e : c->prof_ev)
         if (e) cudaEventDestroy(e);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -1509,6 +1529,25 @@ scola_status scola_kernel_times(const scola_ctx *cc, double *ms_per_launch, int3
             ms_per_launch[q] += ms / nf;
         }
     }
+    return SCOLA_OK;
+}
+
+scola_status scola_tcola_kernel_times(const scola_ctx *cc, double *ms_per_launch, int32_t n) {
+    if (!cc || !ms_per_launch) return invalid("NULL argument");
+    scola_ctx *c = const_cast<scola_ctx *>(cc);
+    if (!c->tc_profiled || n < 4) {
+        set_error("scola_tcola_kernel_times needs a tCOLA run made in profiling mode and room for 4 stages");
+        return SCOLA_ERR_STATE;
+    }
+    CK(cudaEventSynchronize(c->tc_prof_ev.back()));
+    const int nf = c->prm.nsteps + 1;
+    for (int q = 0; q < 4; ++q) ms_per_launch[q] = 0.0;
+    for (int k = 0; k < nf; ++k)
+        for (int q = 0; q < 4; ++q) {
+            float ms = 0;
+            CK(cudaEventElapsedTime(&ms, c->tc_prof_ev[5 * k + q], c->tc_prof_ev[5 * k + q + 1]));
+            ms_per_launch[q] += ms / nf;
+        }
     return SCOLA_OK;
 }
 

@@ -249,9 +249,10 @@ cudaError_t launch_spectrum(Ctx &c, const cufftComplex *dk, const int *bin_of_n2
                             int rows, double *out);
 constexpr int kMaxSpectrumBins = 2048;
 
-// periodic tCOLA (k_tcola.cu): particle init, deposit + density (clears the counts),
-// Green's function on tc_dk, kick-drift reading the potential phi, final x and p
+// periodic tCOLA (k_tcola.cu): particle init, deposit into the counts, density (clears the
+// counts), Green's function on tc_dk, kick-drift reading the potential phi, final x and p
 cudaError_t launch_tc_init(Ctx &c);
+cudaError_t launch_tc_deposit(Ctx &c);
 cudaError_t launch_tc_density(Ctx &c, float *delta);
 cudaError_t launch_tc_green(Ctx &c);
 cudaError_t launch_tc_kick_drift(Ctx &c, const float *phi, const KickDrift &kd);

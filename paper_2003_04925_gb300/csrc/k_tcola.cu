@@ -256,13 +256,16 @@ cudaError_t launch_tc_init(Ctx &c) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_tc_density(Ctx &c, float *delta) {
+cudaError_t launch_tc_deposit(Ctx &c) {
     const int ratio = c.tc_ng / c.Np;
     k_tc_deposit<<<grid_of(c.N3, 256), 256, 0, c.stream>>>(c.tc_part, c.N3, c.Np, c.tc_ng, (float)ratio,
                                                            (float)(c.tc_ng / c.L), c.tc_acc);
     ++c.launches;
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_density(Ctx &c, float *delta) {
+    const int ratio = c.tc_ng / c.Np;
     const float sc = (float)((double)ratio * ratio * ratio / kFix);
     k_tc_density<<<grid_of(c.tc_n3, 256), 256, 0, c.stream>>>(c.tc_acc, c.tc_n3, sc, delta);
     ++c.launches;
