@@ -178,7 +178,7 @@ __device__ __forceinline__ void deposit_entry(unsigned long long *acc, const flo
 // One CTA of T threads per real brick (item.start = brick index in the box, nb^3 of them).
 // kSplit: the counts as 32-bit low and high halves (32-bit atomics), else 64-bit atomics.
 template <int kBrickThreads, bool kSplit>
-__global__ void __launch_bounds__(kBrickThreads, kBrickThreads == 256 ? 5 : 3)
+__global__ void __launch_bounds__(kBrickThreads, kBrickThreads == 256 ? 6 : 3)
 k_sort_brick(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ items, const int *__restrict__ cnt,
              const int *__restrict__ offs, const float4 *__restrict__ entries, const float *__restrict__ phi_pad,
              float inv_D1, const float *__restrict__ coef, int kstep, int nk, float *__restrict__ out,
