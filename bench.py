@@ -40,9 +40,10 @@ def parse():
     ap.add_argument("--impl", default="scola", choices=["scola", "reference"])
     ap.add_argument("--workload", default="batched_128")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--dst", default="tc", choices=["tc", "tc4", "simt"],
-                    help="Poisson-solve form: tensor-core 3xTF32 (tc, default), 4xTF32 (tc4) or FP32 "
-                         "CUDA cores (simt)")
+    ap.add_argument("--dst", default="auto", choices=["auto", "tc", "tc4", "simt"],
+                    help="Poisson-solve form: the library's autotuner (auto, default: the faster of "
+                         "3xTF32 tensor cores and FP32 CUDA cores), tensor-core 3xTF32 (tc), 4xTF32 (tc4) "
+                         "or FP32 CUDA cores (simt)")
     ap.add_argument("--forward-only", action="store_true",
                     help="only W + K forward runs of the batched form (for ncu launch lists)")
     ap.add_argument("--batch-boxes", type=int, default=0,
@@ -416,7 +417,7 @@ def run_gpu(args, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     kw, W = workload_kwargs(args.workload)
-    kw["dst_variant"] = {"tc": sc.SCOLA_DST_TC_3XTF32, "tc4": sc.SCOLA_DST_TC_4XTF32,
+    kw["dst_variant"] = {"auto": sc.SCOLA_DST_AUTO, "tc": sc.SCOLA_DST_TC_3XTF32, "tc4": sc.SCOLA_DST_TC_4XTF32,
                          "simt": sc.SCOLA_DST_SIMT}[args.dst]
     if args.batch_boxes:
         kw["batch_boxes"] = args.batch_boxes
@@ -440,6 +441,11 @@ def run_gpu(args, rank, world, local_rank):
     for _ in range(args.warmup):
         sim.forward(w, x, p)
     torch.cuda.synchronize()
+    dst_tune = dst_choice(sc, sim.stats())
+    if args.dst == "auto":
+        # the form the autotuner kept; every later context of this run asks for it
+        args.dst = "tc" if sc.scola_uses_tensor_cores(sim.ctx) else "simt"
+        kw["dst_variant"] = {"tc": sc.SCOLA_DST_TC_3XTF32, "simt": sc.SCOLA_DST_SIMT}[args.dst]
     if args.forward_only:
         t0 = time.perf_counter()
         for _ in range(args.steps):
@@ -569,7 +575,7 @@ def run_gpu(args, rank, world, local_rank):
                 "clocks": clk,
                 "roofline": roofline, "cpu_baseline": cpu,
                 "stats": {k: v for k, v in sim.stats().items() if k in ("ms_lpt", "ms_evolve", "r", "p")},
-                "deposit_autotune": deposit_choice(sc, sim.stats())}
+                "deposit_autotune": deposit_choice(sc, sim.stats()), "dst_autotune": dst_tune}
         print(json.dumps(line), flush=True)
     sim.close()
     if dist is not None:
@@ -586,6 +592,17 @@ def deposit_choice(sc, st):
             sc.SCOLA_DEPOSIT_ATOMIC: names[3]}.get(st["deposit_form"], "not tuned")
     return {"kept": form, "candidates_ms": {n: round(t, 4) for n, t in zip(names, st["ms_deposit_candidates"])
                                             if t > 0}}
+
+
+def dst_choice(sc, st):
+    """The Poisson-solve form in use and, under the autotuner, the candidates it timed (ms per
+    solve of all boxes; both forms meet the accuracy bound)."""
+    names = {sc.SCOLA_DST_TC_3XTF32: "tensor cores, 3xTF32", sc.SCOLA_DST_TC_4XTF32: "tensor cores, 4xTF32",
+             sc.SCOLA_DST_SIMT: "FP32 CUDA cores"}
+    cand = st["ms_dst_candidates"]
+    return {"kept": names.get(st["dst_form"], "not chosen"),
+            "candidates_ms": {n: round(t, 4) for n, t in zip(("tensor cores, 3xTF32", "FP32 CUDA cores"), cand)
+                              if t > 0}}
 
 
 def main():

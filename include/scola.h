@@ -54,7 +54,9 @@ typedef enum scola_dst_variant {
     SCOLA_DST_SIMT = 0,          /* dense sine-matrix pencils on FP32 CUDA cores */
     SCOLA_DST_TC_3XTF32 = 1,     /* the same products on tcgen05 tensor cores, 3xTF32 split */
     SCOLA_DST_TC_4XTF32 = 3,     /* as 1, plus the lo x lo product (four TF32 products) */
-    SCOLA_DST_AUTO = 2           /* 3xTF32 tensor cores when every Ng allows it, else FP32 cores */
+    SCOLA_DST_AUTO = 2           /* the faster of the 3xTF32 tensor-core and the FP32 forms, timed
+                                    once on the context's boxes before the first evolution (the
+                                    FP32 form alone where some Ng excludes the tensor cores) */
 } scola_dst_variant;
 
 typedef enum scola_deposit_form {
@@ -201,6 +203,11 @@ typedef struct scola_stats {
     int32_t batch_boxes;          /* boxes per batch (the last may hold fewer) */
     double ms_tcola;              /* periodic tCOLA run (scola_tcola, or the study-mode records
                                      of scola_forward), device time; 0 if none ran */
+    int32_t dst_form;             /* the Poisson-solve form in use (scola_dst_variant) once chosen:
+                                     the requested one, or the autotuner's pick under AUTO
+                                     (0 until the first scola_forward / scola_setup_boxes) */
+    double ms_dst_candidates[2];  /* AUTO: autotuner timings of one Poisson solve, tensor-core
+                                     and FP32 forms; 0 = not timed */
 } scola_stats;
 
 /*
@@ -374,7 +381,9 @@ scola_status scola_tcola_kernel_times(const scola_ctx *ctx, double *ms_per_launc
  */
 scola_status scola_device_status(scola_ctx *ctx);
 
-/* 1 when the context's Poisson solve runs on the tensor cores, else 0. */
+/* 1 when the context's Poisson solve runs on the tensor cores, else 0 (under
+ * SCOLA_DST_AUTO: the autotuner's pick once the first scola_forward or
+ * scola_setup_boxes has run; before that, whether the tensor-core form is set up). */
 int32_t scola_uses_tensor_cores(const scola_ctx *ctx);
 
 /*

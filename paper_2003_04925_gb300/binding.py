@@ -57,7 +57,7 @@ class ScolaStats(ctypes.Structure):
         ("ms_lpt", c_double), ("ms_evolve", c_double), ("kernel_launches", c_int64),
         ("deposit_form", c_int32), ("deposit_threads", c_int32), ("deposit_split", c_int32),
         ("ms_deposit_candidates", c_double * 4), ("batches", c_int32), ("batch_boxes", c_int32),
-        ("ms_tcola", c_double),
+        ("ms_tcola", c_double), ("dst_form", c_int32), ("ms_dst_candidates", c_double * 2),
     ]
 
 
@@ -254,6 +254,7 @@ def scola_get_stats(ctx):
     _check(_lib.scola_get_stats(ctx, ctypes.byref(st)), "scola_get_stats")
     out = {name: getattr(st, name) for name, _ in ScolaStats._fields_}
     out["ms_deposit_candidates"] = list(out["ms_deposit_candidates"])
+    out["ms_dst_candidates"] = list(out["ms_dst_candidates"])
     return out
 
 

@@ -81,7 +81,6 @@ struct scola_ctx : public Ctx {
 
 namespace {
 
-constexpr bool kAutoUsesTensorCores = true;    // AUTO: three-product tensor-core form where supported
 constexpr int kMaxNg = 192;  // the DST passes hold a (Ng x 32 ceil(Ng/32)) sine matrix in shared memory
 
 scola_status invalid(const std::string &m) {
@@ -608,8 +607,10 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &all_geo) {
     // tensor-core DST groups (one per distinct Ng): the FP32 sine matrix
     bool all_tc = true;
     for (auto &kv : c->tbl_of) all_tc = all_tc && tc_supported(kv.first);
-    c->use_tc = (p.dst_variant == SCOLA_DST_TC_3XTF32) || (p.dst_variant == SCOLA_DST_TC_4XTF32) ||
-                (p.dst_variant == SCOLA_DST_AUTO && all_tc && kAutoUsesTensorCores);
+    // AUTO: both forms are set up where every Ng allows the tensor-core form, and the
+    // autotuner keeps the faster (autotune_dst); the FP32 form otherwise
+    c->dst_auto = p.dst_variant == SCOLA_DST_AUTO && all_tc;
+    c->use_tc = (p.dst_variant == SCOLA_DST_TC_3XTF32) || (p.dst_variant == SCOLA_DST_TC_4XTF32) || c->dst_auto;
     c->tc_lo_lo = p.dst_variant == SCOLA_DST_TC_4XTF32;
     if (c->use_tc) {
         for (auto &kv : c->tbl_of) {
@@ -1043,6 +1044,53 @@ scola_status autotune_deposit(scola_ctx *c) {
     return SCOLA_OK;
 }
 
+// Poisson-solve autotuner (SCOLA_DST_AUTO where every Ng allows the tensor-core form).  The
+// 3xTF32 tensor-core passes and the FP32 CUDA-core passes both meet the accuracy bound; each
+// solves the context's current source (the boxes of the first batch, or box 0 in the
+// per-tile form) three times after a warm-up, timed with CUDA events, and the faster is kept
+// for the life of the context and its captured graph.  Runs once, after autotune_deposit
+// (whose last candidate leaves a valid source in the mesh).
+scola_status autotune_dst(scola_ctx *c) {
+    if (c->dst_tuned) return SCOLA_OK;
+    if (!c->dst_auto) {
+        c->stats.dst_form = c->use_tc ? (c->tc_lo_lo ? SCOLA_DST_TC_4XTF32 : SCOLA_DST_TC_3XTF32) : SCOLA_DST_SIMT;
+        c->dst_tuned = true;
+        return SCOLA_OK;
+    }
+    const long long launches = c->launches;
+    float t[2] = {-1.0f, -1.0f};
+    {
+        std::unique_ptr<BoxView> view;
+        if (c->prm.batch_mode == SCOLA_BATCH_PER_TILE) view.reset(new BoxView(c, 0));
+        for (int q = 0; q < 2; ++q) {
+            c->use_tc = q == 0;
+            cudaError_t e = launch_poisson(*c);
+            if (e == cudaSuccess) e = c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize();
+            if (e != cudaSuccess) {
+                set_error(std::string("Poisson-solve autotuner, ") + (q == 0 ? "tensor-core form: " : "FP32 form: ") +
+                          cudaGetErrorString(e));
+                return SCOLA_ERR_CUDA;
+            }
+            for (int rep = 0; rep < 3; ++rep) {
+                CK(cudaEventRecord(c->ev[3], c->stream));
+                CK(launch_poisson(*c));
+                CK(cudaEventRecord(c->ev[2], c->stream));
+                CK(cudaEventSynchronize(c->ev[2]));
+                float ms = 0.0f;
+                CK(cudaEventElapsedTime(&ms, c->ev[3], c->ev[2]));
+                if (t[q] < 0.0f || ms < t[q]) t[q] = ms;
+            }
+        }
+    }
+    c->use_tc = t[0] <= t[1];
+    c->stats.ms_dst_candidates[0] = t[0];
+    c->stats.ms_dst_candidates[1] = t[1];
+    c->stats.dst_form = c->use_tc ? SCOLA_DST_TC_3XTF32 : SCOLA_DST_SIMT;
+    c->launches = launches;
+    c->dst_tuned = true;
+    return SCOLA_OK;
+}
+
 // The plain per-tile form: every box evolved on its own, one box per launch, boxes in turn
 // (the paper's one-process-per-box organisation mapped onto one GPU).
 scola_status enqueue_evolution_per_tile(scola_ctx *c) {
@@ -1297,6 +1345,7 @@ scola_status scola_setup_boxes(scola_ctx *c) {
         return SCOLA_ERR_STATE;
     }
     CS(autotune_deposit(c));
+    CS(autotune_dst(c));
     CK(launch_box_init(*c));
     CK(launch_shell(*c));
     CK(launch_pad(*c, 1.0f));
@@ -1337,6 +1386,7 @@ scola_status scola_forward(scola_ctx *c, const float *w, float *x, float *p) {
     if (c->prm.study_mode) CS(run_tcola(c, true));   // the true delta_K and Phi_K (counts in ms_lpt)
     CS(bind_batch(c, 0));
     CS(autotune_deposit(c));   // first call only; its time counts in ms_lpt
+    CS(autotune_dst(c));
     CK(cudaEventRecord(c->ev[1], c->stream));
     // the batches in turn: C.1-C.3, the evolution graph and B.2 for each
     const int nbatch = (int)c->batch_first.size() - 1;

@@ -132,6 +132,7 @@ struct Ctx {
     std::vector<int> dep_groups;                      // first box of each deposit group, then nboxes
     int num_sms = 1, dst_ctas_per_sm = 1;
     bool use_tc = false;                              // tensor-core (3xTF32) DST passes
+    bool dst_auto = false, dst_tuned = false;         // SCOLA_DST_AUTO: the autotuner picks use_tc
     bool tc_lo_lo = false;                            // four-product TF32 form
     std::vector<TcGroup> tc_groups;
     Chunk *tc_tiles = nullptr;

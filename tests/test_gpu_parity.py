@@ -234,7 +234,7 @@ def test_deposit_forms_are_bit_identical(name):
     outs = []
     for form in (sc.SCOLA_DEPOSIT_SORTED, sc.SCOLA_DEPOSIT_ATOMIC, sc.SCOLA_DEPOSIT_AUTO):
         for mode in (sc.SCOLA_BATCH_ALL, sc.SCOLA_BATCH_PER_TILE):
-            sim = sc.Scola(**dict(lib_kwargs(kw), deposit_form=form, batch_mode=mode))
+            sim = sc.Scola(**dict(lib_kwargs(kw), deposit_form=form, batch_mode=mode, dst_variant=sc.SCOLA_DST_SIMT))
             sim.lpt_fields(w)
             sim.setup_boxes()
             _, delta, _ = sim.pm_force(s_dev, 0.73, want_delta=True)
@@ -282,6 +282,35 @@ def test_box_ranges_merge_to_the_full_run(variant):
         part.close()
     assert torch.equal(xm, xf) and torch.equal(pm_, pf)
     full.close()
+
+
+@pytest.mark.parametrize("name", ["plain_32", "table1_like"])
+def test_dst_autotuner_keeps_one_form(name):
+    # SCOLA_DST_AUTO times the tensor-core and the FP32 Poisson solves on the context's own
+    # boxes and keeps the faster; the run then equals, bit for bit, a context that asks for
+    # that form.  Where some Ng excludes the tensor cores (Ng = 25) the FP32 form is taken
+    # without timing.
+    kw = CASES_PM[name]
+    w = _to_dev(synth_inputs.white_noise(kw["Np"], 6))
+    auto = sc.Scola(**dict(lib_kwargs(kw), dst_variant=sc.SCOLA_DST_AUTO))
+    xa, pa = auto.forward(w)
+    torch.cuda.synchronize()
+    st = auto.stats()
+    tc_ok = kw.get("Ng", 0) % 4 == 0
+    if tc_ok:
+        assert st["dst_form"] in (sc.SCOLA_DST_TC_3XTF32, sc.SCOLA_DST_SIMT)
+        assert all(t > 0 for t in st["ms_dst_candidates"])
+        assert (st["dst_form"] == sc.SCOLA_DST_TC_3XTF32) == (st["ms_dst_candidates"][0] <= st["ms_dst_candidates"][1])
+    else:
+        assert st["dst_form"] == sc.SCOLA_DST_SIMT and st["ms_dst_candidates"] == [0.0, 0.0]
+    assert sc.scola_uses_tensor_cores(auto.ctx) == (1 if st["dst_form"] == sc.SCOLA_DST_TC_3XTF32 else 0)
+    auto.close()
+    fixed = sc.Scola(**dict(lib_kwargs(kw), dst_variant=st["dst_form"]))
+    xf, pf = fixed.forward(w)
+    torch.cuda.synchronize()
+    assert fixed.stats()["dst_form"] == st["dst_form"]
+    fixed.close()
+    assert torch.equal(xa, xf) and torch.equal(pa, pf)
 
 
 def test_zero_amplitude_keeps_the_lattice():
@@ -373,13 +402,13 @@ def test_streamed_batches_are_bit_identical(name):
     # returns to its first batch.
     kw = dict(C5_SHAPE, nsteps=3) if name == "c5_shape" else CASES_PM[name]
     w = _to_dev(synth_inputs.white_noise(kw["Np"], 9))
-    one = sc.Scola(**lib_kwargs(kw))
+    one = sc.Scola(**dict(lib_kwargs(kw), dst_variant=sc.SCOLA_DST_TC_3XTF32))
     x1, p1 = one.forward(w)
     torch.cuda.synchronize()
     assert one.stats()["batches"] == 1
     sc.scola_device_status(one.ctx)
     one.close()
-    many = sc.Scola(**dict(lib_kwargs(kw), batch_boxes=3))
+    many = sc.Scola(**dict(lib_kwargs(kw), batch_boxes=3, dst_variant=sc.SCOLA_DST_TC_3XTF32))
     for _ in range(2):
         x2, p2 = many.forward(w)
         torch.cuda.synchronize()
@@ -430,7 +459,7 @@ def test_large_1024_streamed_run():
         pytest.skip("needs about 200 GB of free device memory")
     kw = workload_cfg("large_1024")
     w = _to_dev(synth_inputs.white_noise(kw["Np"], 1))
-    sim = sc.Scola(**lib_kwargs(kw))
+    sim = sc.Scola(**dict(lib_kwargs(kw), dst_variant=sc.SCOLA_DST_TC_3XTF32))
     x, p = sim.forward(w)
     torch.cuda.synchronize()
     sc.scola_device_status(sim.ctx)
@@ -449,7 +478,7 @@ def test_large_1024_streamed_run():
     idx = torch.from_numpy(ids).cuda()
     xs, ps = x[idx].clone(), p[idx].clone()
     del x, p
-    part = sc.Scola(**dict(lib_kwargs(kw), box_first=b0, box_count=2))
+    part = sc.Scola(**dict(lib_kwargs(kw), box_first=b0, box_count=2, dst_variant=sc.SCOLA_DST_TC_3XTF32))
     xm = torch.full((kw["Np"] ** 3, 3), float("nan"), device="cuda")
     pm_ = torch.full((kw["Np"] ** 3, 3), float("nan"), device="cuda")
     part.forward(w, xm, pm_)

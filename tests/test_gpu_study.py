@@ -130,6 +130,27 @@ def test_true_density_and_potential_reproduce_tcola_on_gpu(ratio):
     assert rms_m > 100 * rms
 
 
+def test_study_modes_on_uneven_boxes_match_oracle():
+    # Boxes of Ng = 40, 48 and 64 (per-tile buffers 4, 8, 16) in one launch: each takes its
+    # own restriction of the tCOLA records; true density only, and both substitutions.
+    kw = dict(L=200.0, Np=64, Ntiles=2, buffers=[4, 8, 16, 4, 8, 4, 16, 8], mesh_ratio=1, nsteps=4,
+              a_i=0.02, a_f=1.0)
+    cfg = oracle_cfg(kw)
+    w = synth_inputs.white_noise(cfg.Np, 3)
+    dg = oscola.box_geometry(cfg, 0).dg
+    for mode in (1, 3):
+        sim = _sim(kw, "tc", study_mode=mode)
+        x, p = sim.forward(_dev(w))
+        torch.cuda.synchronize()
+        x, p = _np(x), _np(p)
+        sim.close()
+        ref = tcola.run_study(w, cfg, true_density=bool(mode & 1), true_potential=bool(mode & 2))
+        rms, prel = _errors(x, p, ref["x"], ref["p"], cfg.L, dg)
+        print("study mode %d uneven: position RMS %.3e PM cells, momentum RMS %.3e relative" % (mode, rms, prel))
+        assert rms <= 1e-3, rms
+        assert prel <= 1e-3, prel
+
+
 def test_study_mode_forms_are_bit_identical():
     # The per-tile form, streamed batches and the batched form read the same records and
     # give the same result bit for bit.
