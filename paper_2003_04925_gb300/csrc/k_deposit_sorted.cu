@@ -47,31 +47,57 @@ __device__ __forceinline__ SortEntry sort_entry(const BoxDesc &B, const float *_
 // two passes disagreed on a key: it is recorded in err (bit 2) and nothing is written.
 template <bool FILL>
 __global__ void __launch_bounds__(kChunk)
-k_sort_bin(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks, const float *__restrict__ s,
+k_sort_bin(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks, int nchunks, const float *__restrict__ s,
            long long stride, int *__restrict__ ctr, float4 *__restrict__ entries, const int *__restrict__ cnt,
            const int *__restrict__ offs, int *__restrict__ err) {
-    const Chunk ch = chunks[blockIdx.x];
-    const BoxDesc &B = boxes[ch.box];
-    const int local = ch.start + threadIdx.x;
-    SortEntry se;
-    se.key = -1;
-    if (local < B.Nsc * B.Nsc * B.Nsc) se = sort_entry(B, s, stride, local);
-    const unsigned peers = __match_any_sync(0xffffffffu, se.key);   // every lane takes part
-    const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
-    int* const kc = ctr + B.key_off;
+    // two chunks per CTA: both particles' loads, and then both reservations, are in flight
+    // together
+    SortEntry se[2];
+    int kb[2];
+    long long pb[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        se[u].key = -1;
+        kb[u] = 0;
+        pb[u] = 0;
+        const int ci = 2 * blockIdx.x + u;
+        if (ci < nchunks) {
+            const Chunk ch = chunks[ci];
+            const BoxDesc &B = boxes[ch.box];
+            kb[u] = B.key_off;
+            pb[u] = B.p_off;
+            const int local = ch.start + threadIdx.x;
+            if (local < B.Nsc * B.Nsc * B.Nsc) se[u] = sort_entry(B, s, stride, local);
+        }
+    }
+    const int lane = threadIdx.x & 31;
+    unsigned peers[2];
+    int leader[2], base[2] = {0, 0}, ok[2] = {1, 1};
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        peers[u] = __match_any_sync(0xffffffffu, se[u].key);   // every lane takes part
+        leader[u] = __ffs(peers[u]) - 1;
+    }
     if (!FILL) {
-        if (se.key >= 0 && lane == leader) atomicAdd(kc + se.key, __popc(peers));
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+            if (se[u].key >= 0 && lane == leader[u]) atomicAdd(ctr + kb[u] + se[u].key, __popc(peers[u]));
         return;
     }
-    int base = 0, ok = 1;
-    if (se.key >= 0 && lane == leader) {
-        base = atomicAdd(kc + se.key, __popc(peers));
-        ok = base + __popc(peers) <= offs[B.key_off + se.key] + cnt[B.key_off + se.key];
-        if (!ok) atomicOr(err, 2);
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+        if (se[u].key >= 0 && lane == leader[u]) base[u] = atomicAdd(ctr + kb[u] + se[u].key, __popc(peers[u]));
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        if (se[u].key >= 0 && lane == leader[u]) {
+            ok[u] = base[u] + __popc(peers[u]) <= offs[kb[u] + se[u].key] + cnt[kb[u] + se[u].key];
+            if (!ok[u]) atomicOr(err, 2);
+        }
+        base[u] = __shfl_sync(0xffffffffu, base[u], leader[u]);
+        ok[u] = __shfl_sync(0xffffffffu, ok[u], leader[u]);
+        if (se[u].key >= 0 && ok[u])
+            entries[pb[u] + base[u] + __popc(peers[u] & ((1u << lane) - 1u))] = se[u].e;
     }
-    base = __shfl_sync(0xffffffffu, base, leader);
-    ok = __shfl_sync(0xffffffffu, ok, leader);
-    if (se.key >= 0 && ok) entries[B.p_off + base + __popc(peers & ((1u << lane) - 1u))] = se.e;
 }
 
 // Exclusive prefix sums of one box's key counts (one CTA of 1024 threads per box).
@@ -324,15 +350,15 @@ cudaError_t launch_deposit_sorted(Ctx &c, const float *s, long long stride, floa
     cudaError_t e;
     if (!counted) {
         if ((e = clear_key_counts(c)) != cudaSuccess) return e;
-        k_sort_bin<false><<<c.n_pchunks, kChunk, 0, c.stream>>>(c.boxes, c.pchunks, s, stride, c.kcount, nullptr,
-                                                                nullptr, nullptr, nullptr);
+        k_sort_bin<false><<<(c.n_pchunks + 1) / 2, kChunk, 0, c.stream>>>(c.boxes, c.pchunks, c.n_pchunks, s, stride,
+                                                                          c.kcount, nullptr, nullptr, nullptr, nullptr);
         if ((e = cudaGetLastError()) != cudaSuccess) return step_error("sorted deposit: count launch", e);
         ++c.launches;
     }
     k_sort_scan<<<nbox, 1024, 0, c.stream>>>(c.boxes, box0, c.kcount, c.koffs, c.kcursor);
     if ((e = cudaGetLastError()) != cudaSuccess) return step_error("sorted deposit: scan launch", e);
-    k_sort_bin<true><<<c.n_pchunks, kChunk, 0, c.stream>>>(c.boxes, c.pchunks, s, stride, c.kcursor, c.sentries,
-                                                           c.kcount, c.koffs, c.dev_err);
+    k_sort_bin<true><<<(c.n_pchunks + 1) / 2, kChunk, 0, c.stream>>>(c.boxes, c.pchunks, c.n_pchunks, s, stride,
+                                                                     c.kcursor, c.sentries, c.kcount, c.koffs, c.dev_err);
     if ((e = cudaGetLastError()) != cudaSuccess) return step_error("sorted deposit: fill launch", e);
 #define SCOLA_BRICK(T, SPLIT)                                                                             \
     k_sort_brick<T, SPLIT><<<c.n_sbricks, T, 0, c.stream>>>(c.boxes, c.sbricks, c.kcount, c.koffs, c.sentries, \
