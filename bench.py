@@ -318,13 +318,18 @@ def study_cost(sc, torch, kw, W, steps, peaks):
     rows = {k: {"ms_per_eval": round(st[k], 5), "achieved_gbs": work[k] / (st[k] * 1e-3) / 1e9,
                 "frac": work[k] / (st[k] * 1e-3) / 1e9 / hbm} for k in work}
     dom = max(rows, key=lambda k: rows[k]["ms_per_eval"])
+    traffic = measured_traffic("tcola_128", None) if kw["Np"] == 128 and kw["mesh_ratio"] == 2 else {}
+    for k in rows:
+        rows[k]["traffic"] = traffic.get(k)
     return {"workload": "periodic tCOLA of the same %d^3 particles on a %d^3 mesh, and sCOLA with the "
                         "true density and potential (Sec. 4.3)" % (kw["Np"], kw["mesh_ratio"] * kw["Np"]),
             "ms_tcola_run": t_tc, "tcola_particle_steps_per_s": n * kw["nsteps"] / (t_tc * 1e-3),
             "ms_study_run": t_st,
             "tcola_stages_ms_per_eval": {k: round(v, 5) for k, v in st.items()},
             "roofline": {"kernel": dom, "bound": "hbm", "achieved": rows[dom]["achieved_gbs"], "peak": hbm,
-                         "unit": "GB/s", "frac": rows[dom]["frac"],
+                         "unit": "GB/s", "frac": rows[dom]["frac"], "traffic": rows[dom]["traffic"],
+                         "traffic_source": "profiles/traffic_tcola_128.json (ncu, DRAM read + write per force "
+                                           "evaluation; null where the kernel changed since the capture)",
                          "kernels": rows}}
 
 
