@@ -476,6 +476,19 @@ scola_status scola_power_spectrum(scola_ctx *ctx, const float *delta_dev, int32_
                                   double *k_mean, double *pk, int64_t *n_modes);
 
 /*
+ * Seeded white noise on the N^3 LPT grid (Sec. 3.1, step A.1), generated on the device:
+ * Philox4x32-10 (Salmon, Moraes, Dror and Shaw, SC11 2011) with key (seed mod 2^32,
+ * seed div 2^32); cell i (flat index, k fastest) takes word i % 4 of counter block
+ * (i / 4 mod 2^32, i / 4 div 2^32, 0, 0); a word x gives the uniform
+ * (floor(x / 2^8) + 1/2) 2^-24, and words (0, 1), (2, 3) give two standard normals each by
+ * Box-Muller, sqrt(-2 ln u0) (cos, sin)(2 pi u1), in FP32.  Deterministic for a seed.
+ *   w_dev  device, N^3 floats (caller-owned), written on the context stream
+ * An alternative to passing any caller-made w to scola_forward.
+ * Errors: INVALID_ARG (NULL), CUDA.
+ */
+scola_status scola_generate_white_noise(scola_ctx *ctx, uint64_t seed, float *w_dev);
+
+/*
  * The periodic full-box tCOLA run (Sec. 2.2; the monolithic simulation that sCOLA
  * approximates, Sec. 4): initial conditions and LPT as scola_forward, then all Np^3
  * particles evolved with the same KDK factors on one periodic PM grid of mesh_ratio * Np

@@ -72,6 +72,7 @@ _sig = {
     "scola_forward": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "scola_forward_host": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "scola_tcola": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "scola_generate_white_noise": (c_int32, [c_void_p, ctypes.c_uint64, c_void_p]),
     "scola_lpt_fields": (c_int32, [c_void_p] + [c_void_p] * 6),
     "scola_setup_boxes": (c_int32, [c_void_p]),
     "scola_pm_force": (c_int32, [c_void_p, c_void_p, c_double, c_void_p, c_void_p, c_void_p]),
@@ -165,6 +166,10 @@ def scola_destroy(ctx):
 
 def scola_forward(ctx, w, x, p):
     _check(_lib.scola_forward(ctx, _ptr(w), _ptr(x), _ptr(p)), "scola_forward")
+
+
+def scola_generate_white_noise(ctx, seed, w):
+    _check(_lib.scola_generate_white_noise(ctx, int(seed) & 0xFFFFFFFFFFFFFFFF, _ptr(w)), "scola_generate_white_noise")
 
 
 def scola_tcola(ctx, w, x, p):

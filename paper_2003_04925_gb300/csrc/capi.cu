@@ -1404,6 +1404,12 @@ scola_status scola_forward(scola_ctx *c, const float *w, float *x, float *p) {
     return SCOLA_OK;
 }
 
+scola_status scola_generate_white_noise(scola_ctx *c, uint64_t seed, float *w) {
+    if (!c || !w) return invalid("NULL argument");
+    CK(launch_white_noise(*c, (unsigned long long)seed, w));
+    return SCOLA_OK;
+}
+
 scola_status scola_tcola(scola_ctx *c, const float *w, float *x, float *p) {
     if (!c || !w || !x || !p) return invalid("NULL argument");
     if (c->prm.fda_order != 2) {

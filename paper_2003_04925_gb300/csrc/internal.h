@@ -197,6 +197,7 @@ struct Ctx {
 };
 
 // ---- kernel launchers (k_*.cu); all enqueue on ctx.stream ----
+cudaError_t launch_white_noise(Ctx &c, unsigned long long seed, float *w);
 cudaError_t launch_colour(Ctx &c, cufftComplex *ck);
 cudaError_t launch_inv_laplacian(Ctx &c, const cufftComplex *in, cufftComplex *out, float scale);
 cudaError_t launch_second_derivative(Ctx &c, const cufftComplex *in, cufftComplex *out, int i, int j);

@@ -21,6 +21,65 @@ namespace {
 
 __device__ __forceinline__ int wavenumber(int i, int N) { return i < N / 2 ? i : i - N; }
 
+// White noise (step A.1) from Philox4x32-10 (Salmon et al. 2011): counter block g = (g mod
+// 2^32, g div 2^32, 0, 0) under the key (seed mod 2^32, seed div 2^32); ten rounds that
+// multiply words 0 and 2 by the round multipliers and mix the product halves with words 1
+// and 3 and the key, the key bumped by the Weyl increments before every round after the
+// first.  Each word's top 24 bits give the uniform (x + 1/2) 2^-24 (exact in FP32, in
+// (0, 1)); words (0, 1) and (2, 3) become two standard normals each by Box-Muller:
+// sqrt(-2 ln u0) (cos, sin)(2 pi u1).  Cell i takes word i % 4 of block i / 4.
+constexpr unsigned kPhiloxM0 = 0xD2511F53u, kPhiloxM1 = 0xCD9E8D57u;
+constexpr unsigned kPhiloxW0 = 0x9E3779B9u, kPhiloxW1 = 0xBB67AE85u;
+
+__device__ __forceinline__ uint4 philox4x32_10(unsigned c0, unsigned c1, unsigned k0, unsigned k1) {
+    unsigned c2 = 0u, c3 = 0u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += kPhiloxW0;
+            k1 += kPhiloxW1;
+        }
+        const unsigned hi0 = __umulhi(kPhiloxM0, c0), lo0 = kPhiloxM0 * c0;
+        const unsigned hi1 = __umulhi(kPhiloxM1, c2), lo1 = kPhiloxM1 * c2;
+        const unsigned n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+    }
+    return make_uint4(c0, c1, c2, c3);
+}
+
+__device__ __forceinline__ float unit_uniform(unsigned x) {
+    return ((float)(x >> 8) + 0.5f) * 5.9604644775390625e-8f;   // 2^-24
+}
+
+__global__ void k_white_noise(float *__restrict__ w, long long n, unsigned k0, unsigned k1) {
+    const long long nblk = (n + 3) / 4;
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < nblk;
+         g += (long long)gridDim.x * blockDim.x) {
+        const uint4 x = philox4x32_10((unsigned)g, (unsigned)(g >> 32), k0, k1);
+        float z[4];
+        const float r01 = sqrtf(-2.0f * logf(unit_uniform(x.x)));
+        const float r23 = sqrtf(-2.0f * logf(unit_uniform(x.z)));
+        float s1, c1, s3, c3;
+        sincospif(2.0f * unit_uniform(x.y), &s1, &c1);
+        sincospif(2.0f * unit_uniform(x.w), &s3, &c3);
+        z[0] = r01 * c1;
+        z[1] = r01 * s1;
+        z[2] = r23 * c3;
+        z[3] = r23 * s3;
+        const long long i0 = 4 * g;
+        if (i0 + 4 <= n && (reinterpret_cast<uintptr_t>(w) & 15) == 0) {
+            *reinterpret_cast<float4 *>(w + i0) = make_float4(z[0], z[1], z[2], z[3]);
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if (i0 + e < n) w[i0 + e] = z[e];
+        }
+    }
+}
+
 __global__ void k_colour(cufftComplex *ck, int N, const float *__restrict__ amp) {
     const int Nz = N / 2 + 1;
     const long long n = (long long)N * N * Nz;
@@ -190,6 +249,16 @@ int grid_for(long long n, int block) {
 }
 
 }  // namespace
+
+cudaError_t launch_white_noise(Ctx &c, unsigned long long seed, float *w) {
+    const long long nblk = (c.N3 + 3) / 4;
+    long long grid = (nblk + 255) / 256;
+    if (grid > 8 * (long long)c.num_sms * 8) grid = 8 * (long long)c.num_sms * 8;
+    if (grid < 1) grid = 1;
+    k_white_noise<<<(int)grid, 256, 0, c.stream>>>(w, c.N3, (unsigned)seed, (unsigned)(seed >> 32));
+    ++c.launches;
+    return cudaGetLastError();
+}
 
 cudaError_t launch_colour(Ctx &c, cufftComplex *ck) {
     const int N = c.Np;

@@ -45,6 +45,13 @@ class Scola:
         B.scola_forward(self.ctx, w.contiguous(), x, p)
         return x, p
 
+    def white_noise(self, seed, w=None):
+        """Seeded device white noise on the N^3 LPT grid (Philox4x32-10 + Box-Muller)."""
+        N = self.Np
+        w = self._empty(N, N, N) if w is None else w
+        B.scola_generate_white_noise(self.ctx, seed, w)
+        return w
+
     def tcola(self, w, x=None, p=None):
         """Periodic full-box tCOLA run of all particles from w -> (x, p), each (Np^3, 3)."""
         n = self.Np ** 3

@@ -561,3 +561,28 @@ def test_light_cone_forward_matches_oracle(variant):
     g7 = oscola.box_geometry(cfg, 7)
     ids7 = tiling.box_global_ids(cfg.Np, cfg.Ntiles, g7.t, g7.Nbuf)[tiling.tile_interior_mask(cfg.Np, cfg.Ntiles, g7.Nbuf)]
     assert np.abs(periodic_diff(x[ids7], xu[ids7], cfg.L)).max() > 0.1 * dg
+
+
+@pytest.mark.parametrize("Np", [32, 33])
+def test_device_white_noise_matches_the_reference_generator(Np):
+    # Philox4x32-10 + Box-Muller on the device against the oracle's restatement of the same
+    # definitions (whose Philox is pinned by the published known-answer vectors).  33^3 is not
+    # a multiple of 4 cells: the last block's extra words are not written.
+    from oracle import rng
+    sim = sc.Scola(L=100.0, Np=Np, Ntiles=1, Nbuf=0, mesh_ratio=1, nsteps=1, dst_variant=sc.SCOLA_DST_SIMT)
+    n = Np ** 3
+    w = torch.full((n + 3,), float("nan"), device="cuda")
+    seed = 0x0123_4567_89AB_CDEF
+    sim.white_noise(seed, w)
+    w2 = sim.white_noise(seed)
+    w3 = sim.white_noise(seed + 1)
+    torch.cuda.synchronize()
+    got = w[:n].cpu().numpy().astype(np.float64)
+    assert torch.isnan(w[n:]).all()
+    ref = rng.white_noise(Np, seed)
+    err = np.abs(got - ref)
+    print("device white noise %d^3: max error %.2e, median %.2e" % (Np, err.max(), np.median(err)))
+    assert err.max() <= 1e-5 and np.median(err) <= 1e-6
+    assert torch.equal(w[:n], w2.reshape(-1))
+    assert not torch.equal(w2, w3)
+    sim.close()
