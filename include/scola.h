@@ -476,6 +476,21 @@ scola_status scola_power_spectrum(scola_ctx *ctx, const float *delta_dev, int32_
                                   double *k_mean, double *pk, int64_t *n_modes);
 
 /*
+ * Mass drop and escapes of given box-particle displacements (Sec. 3.4.1-3.4.2), per box:
+ *   s_dev      device, 3 x P displacements in the layout of scola_pm_force
+ *   deposited  host, nboxes: the CIC weight the box's particles leave inside its interior
+ *              mesh (B^sCOLA keeps it and drops the rest; Np,sCOLA^3 minus it is the
+ *              mass drop), summed as 2^-32 fixed-point integers (deterministic)
+ *   escaped    host, nboxes: particles whose mesh coordinate lies outside
+ *              [-N_ghost, Ng + N_ghost - 1] on some axis (the interpolation clamps them)
+ *   nboxes     the context's box count
+ * One batch only (UNSUPPORTED otherwise).  Synchronous.
+ * Errors: INVALID_ARG (NULL, nboxes), UNSUPPORTED, OOM, CUDA.
+ */
+scola_status scola_box_mass(scola_ctx *ctx, const float *s_dev, double *deposited, int32_t *escaped,
+                            int32_t nboxes);
+
+/*
  * Seeded white noise on the N^3 LPT grid (Sec. 3.1, step A.1), generated on the device:
  * Philox4x32-10 (Salmon, Moraes, Dror and Shaw, SC11 2011) with key (seed mod 2^32,
  * seed div 2^32); cell i (flat index, k fastest) takes word i % 4 of counter block

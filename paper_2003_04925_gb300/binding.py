@@ -73,6 +73,7 @@ _sig = {
     "scola_forward_host": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "scola_tcola": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "scola_generate_white_noise": (c_int32, [c_void_p, ctypes.c_uint64, c_void_p]),
+    "scola_box_mass": (c_int32, [c_void_p, c_void_p, _P(c_double), _P(c_int32), c_int32]),
     "scola_lpt_fields": (c_int32, [c_void_p] + [c_void_p] * 6),
     "scola_setup_boxes": (c_int32, [c_void_p]),
     "scola_pm_force": (c_int32, [c_void_p, c_void_p, c_double, c_void_p, c_void_p, c_void_p]),
@@ -166,6 +167,16 @@ def scola_destroy(ctx):
 
 def scola_forward(ctx, w, x, p):
     _check(_lib.scola_forward(ctx, _ptr(w), _ptr(x), _ptr(p)), "scola_forward")
+
+
+def scola_box_mass(ctx, s, nboxes):
+    """Per box: (CIC weight deposited inside the interior mesh, particles clamped)."""
+    import numpy as np
+    dep = np.zeros(nboxes, dtype=np.float64)
+    esc = np.zeros(nboxes, dtype=np.int32)
+    _check(_lib.scola_box_mass(ctx, _ptr(s), dep.ctypes.data_as(_P(c_double)), esc.ctypes.data_as(_P(c_int32)),
+                               nboxes), "scola_box_mass")
+    return dep, esc
 
 
 def scola_generate_white_noise(ctx, seed, w):

@@ -1369,6 +1369,39 @@ scola_status scola_pm_force(scola_ctx *c, const float *s, double D1, float *F, f
     return SCOLA_OK;
 }
 
+scola_status scola_box_mass(scola_ctx *c, const float *s, double *deposited, int32_t *escaped, int32_t nboxes) {
+    if (!c || !s || !deposited || !escaped) return invalid("NULL argument");
+    CS(need_one_batch(c));
+    if (nboxes != c->nboxes) return invalid("nboxes must be the context's box count");
+    unsigned long long *mass = nullptr;
+    int *esc = nullptr;
+    CS(dev_alloc(&mass, nboxes));
+    scola_status st = dev_alloc(&esc, nboxes);
+    cudaError_t e = st == SCOLA_OK ? cudaMemsetAsync(mass, 0, sizeof(unsigned long long) * nboxes, c->stream)
+                                   : cudaSuccess;
+    if (st == SCOLA_OK && e == cudaSuccess) e = cudaMemsetAsync(esc, 0, sizeof(int) * nboxes, c->stream);
+    if (st == SCOLA_OK && e == cudaSuccess) e = launch_box_mass(*c, s, mass, esc);
+    std::vector<unsigned long long> hm(nboxes);
+    std::vector<int> he(nboxes);
+    if (st == SCOLA_OK && e == cudaSuccess)
+        e = cudaMemcpyAsync(hm.data(), mass, sizeof(unsigned long long) * nboxes, cudaMemcpyDeviceToHost, c->stream);
+    if (st == SCOLA_OK && e == cudaSuccess)
+        e = cudaMemcpyAsync(he.data(), esc, sizeof(int) * nboxes, cudaMemcpyDeviceToHost, c->stream);
+    if (st == SCOLA_OK && e == cudaSuccess) e = c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize();
+    cudaFree(mass);
+    if (esc) cudaFree(esc);
+    if (st != SCOLA_OK) return st;
+    if (e != cudaSuccess) {
+        set_error(std::string("scola_box_mass: ") + cudaGetErrorString(e));
+        return SCOLA_ERR_CUDA;
+    }
+    for (int b = 0; b < nboxes; ++b) {
+        deposited[b] = (double)hm[b] / kFix;
+        escaped[b] = he[b];
+    }
+    return SCOLA_OK;
+}
+
 scola_status scola_box_particle_ids(scola_ctx *c, int64_t *gid) {
     if (!c || !gid) return invalid("NULL argument");
     CS(need_one_batch(c));

@@ -244,6 +244,8 @@ cudaError_t launch_scaled_copy(Ctx &c, const float *in, float *out, long long n,
 cudaError_t launch_kick_drift(Ctx &c, const KickDrift &kd, bool count_keys = false, int k = -1);
 cudaError_t launch_scatter(Ctx &c, float *x, float *p);
 cudaError_t launch_box_ids(Ctx &c, int64_t *gid);
+// per box of the bound batch: inside CIC weight (2^-32 fixed point) and clamped-particle count
+cudaError_t launch_box_mass(Ctx &c, const float *s, unsigned long long *mass, int *escaped);
 cudaError_t launch_final_density(Ctx &c, const float *x, float *delta);
 // Binned |delta_k|^2 sums of a half spectrum: out = [psum, sqrt(n^2) sum, count] x nbins;
 // scratch holds 3 x rows x nbins doubles; rows = CTAs of the partial pass.

@@ -168,6 +168,50 @@ __global__ void k_density_finish(const unsigned long long *__restrict__ acc, lon
         delta[idx] = fixed_to_float(acc[idx]) * scale - 1.0f;
 }
 
+// Per box: the CIC weight its particles leave inside the interior mesh (B^sCOLA keeps it,
+// Sec. 3.4.1), as 2^-32 fixed-point sums (deterministic), and the number of particles whose
+// mesh coordinate lies outside [-N_ghost, Ng + N_ghost - 1] on some axis (the force
+// interpolation clamps them back).  The 3D CIC weights factorise, so a particle's inside
+// weight is the product over axes of its 1D weights on cells inside [0, Ng).
+__global__ void __launch_bounds__(kChunk)
+k_box_mass(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks, const float *__restrict__ s,
+           long long stride, unsigned long long *__restrict__ mass, int *__restrict__ escaped) {
+    const Chunk ch = chunks[blockIdx.x];
+    const BoxDesc &B = boxes[ch.box];
+    const int Nsc = B.Nsc, Ng = B.Ng, ng = B.fda / 2;
+    const int local = ch.start + threadIdx.x;
+    unsigned long long f = 0ull;
+    int out = 0;
+    if (local < Nsc * Nsc * Nsc) {
+        const long long gi = B.p_off + local;
+        int b[3];
+        decode_local(local, Nsc, b[0], b[1], b[2]);
+        float w = 1.0f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float u_raw = fmaf(__ldg(s + a * stride + gi), B.inv_dg, fmaf((float)b[a], B.q2u, 0.5f * B.q2u - 0.5f));
+            if (u_raw < -(float)ng || u_raw > (float)(Ng + ng - 1)) out = 1;
+            const float u = fminf(fmaxf(u_raw, -2.0f), (float)Ng + 1.0f);
+            const float fl = floorf(u);
+            const int i0 = (int)fl;
+            const float fr = u - fl;
+            const bool in0 = (unsigned)i0 < (unsigned)Ng, in1 = (unsigned)(i0 + 1) < (unsigned)Ng;
+            w *= in0 && in1 ? 1.0f : (in0 ? 1.0f - fr : (in1 ? fr : 0.0f));
+        }
+        f = weight_to_fixed(w);
+    }
+    // one atomic per warp for each sum (all lanes of a warp belong to the chunk's box)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        f += __shfl_down_sync(0xffffffffu, f, o);
+        out += __shfl_down_sync(0xffffffffu, out, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (f) atomicAdd(mass + ch.box, f);
+        if (out) atomicAdd(escaped + ch.box, out);
+    }
+}
+
 int grid_for(long long n, int block) {
     long long g = (n + block - 1) / block;
     return (int)(g < 16384 ? (g > 0 ? g : 1) : 16384);
@@ -199,6 +243,12 @@ cudaError_t launch_scatter(Ctx &c, float *x, float *p) {
                                                      (float)c.dq, (float)c.L,
                                                      (float)(-pref * c.tt.dD1da_f),
                                                      (float)(pref * c.tt.dD2da_f), c.coefL, x, p);
+    ++c.launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_box_mass(Ctx &c, const float *s, unsigned long long *mass, int *escaped) {
+    k_box_mass<<<c.n_pchunks, kChunk, 0, c.stream>>>(c.boxes, c.pchunks, s, c.P, mass, escaped);
     ++c.launches;
     return cudaGetLastError();
 }

@@ -45,6 +45,10 @@ class Scola:
         B.scola_forward(self.ctx, w.contiguous(), x, p)
         return x, p
 
+    def box_mass(self, s):
+        """Per box: CIC weight left inside the interior mesh and clamped-particle count."""
+        return B.scola_box_mass(self.ctx, s.contiguous(), self.stats()["nboxes"])
+
     def white_noise(self, seed, w=None):
         """Seeded device white noise on the N^3 LPT grid (Philox4x32-10 + Box-Muller)."""
         N = self.Np

@@ -134,6 +134,13 @@ def test_pm_force_matches_oracle(name, variant):
         phib = phi[pp_off:pp_off + np3].reshape((g.Ng + 2 * G,) * 3)
         assert np.abs(phib - r["phi"]).max() <= 2e-5 * np.abs(r["phi"]).max()
         p_off = p_off + n
+    # mass drop and clamped particles of the same displacements (Sec. 3.4.1-3.4.2)
+    dep, esc = sim.box_mass(_to_dev(s_cat))
+    for b, (g, r) in enumerate(refs):
+        assert abs(dep[b] - r["deposited"]) <= 1e-6 * g.Nsc**3, (b, dep[b], r["deposited"])
+        assert abs(int(esc[b]) - int(r["clamped"].sum())) <= 1, (b, esc[b], r["clamped"].sum())
+    if name == "plain_32":
+        assert any(r["deposited"] < g.Nsc**3 - 1.0 for g, r in refs) and esc.sum() > 0
     sc.scola_device_status(sim.ctx)
     sim.close()
 
