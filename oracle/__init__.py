@@ -22,9 +22,14 @@ boundary    Dirichlet boundary potential on the padded PM grid (Sec. 3.3 C.3, Eq
 pm          B^sCOLA deposit, Dirichlet DST-I Poisson solve, FDA gradient and
             interpolation (Sec. 3.4, App. C)
 scola       the KDK driver for sCOLA boxes and the untiling (App. B, Sec. 3.2)
-tcola       periodic full-box tCOLA reference, used only to pin the sCOLA box
-            machinery (Sec. 2.2, Sec. 4.3)
+tcola       periodic full-box tCOLA reference and the approximation-study runs of
+            Sec. 4.3 (sCOLA boxes fed tCOLA's true density and/or potential)
+fda         FDA stencils of order 2, 4, 6 and their symbols (Sec. 3.1, App. C)
+adjoint     the reverse-mode gradient of a final-density loss (FP64 reference of the
+            library's hand-written adjoint)
 stats       final periodic CIC density and the P(k) estimator (Sec. 4.1-4.2, Eq. 24)
+rng         restatement of the library's device white-noise generator (Philox4x32-10,
+            Box-Muller) from the published definitions
 
 Parity status of each part (what pins it) is listed in each module header.
 """
