@@ -312,6 +312,19 @@ scola_status scola_box_offsets(const scola_ctx *ctx, int64_t *m_off, int64_t *pp
 scola_status scola_box_particle_ids(scola_ctx *ctx, int64_t *gid_dev);
 
 /*
+ * Multi-GPU sharding plan (host only, no context needed).  The boxes never communicate
+ * (Sec. 3.2), so a run splits into contiguous box ranges, one per GPU, each evolved by its
+ * own context (params.box_first / box_count) with no collective on the data path.  The
+ * ranges balance the cost Np,sCOLA^3 + Ng^3 of each box: rank r ends its range where the
+ * running cost comes within half a box of (r + 1) / world of the total, leaving at least
+ * one box for every later rank; the last rank takes the rest.
+ *   world        number of ranks, 1 .. Ntiles^3
+ *   first, count host, world int32: each rank's range (together every box exactly once)
+ * Errors: as scola_create's validation; INVALID_ARG (NULL, world out of range).
+ */
+scola_status scola_shard_ranges(const scola_params *params, int32_t world, int32_t *first, int32_t *count);
+
+/*
  * Host-side tiling arithmetic (Sec. 3.2, Eqs. 20-21), no context needed.
  *   box_nsc  host, Ntiles^3 int32 or NULL: Np,sCOLA per box
  *   box_ng   host, Ntiles^3 int32 or NULL: Ng per box

@@ -16,7 +16,7 @@ from .binding import (  # noqa: F401
     scola_create, scola_destroy, scola_device_status, scola_final_density, scola_forward,
     scola_forward_host, scola_generate_white_noise, scola_get_stats, scola_kernel_times, scola_last_error, scola_lpt_fields,
     scola_mesh_cell_count, scola_padded_cell_count, scola_pm_force, scola_power_spectrum, scola_selftest_conversions,
-    scola_set_checkpointing, scola_set_profiling, scola_setup_boxes, scola_status_string,
+    scola_set_checkpointing, scola_set_profiling, scola_shard_ranges, scola_setup_boxes, scola_status_string,
     scola_tcola, scola_tcola_kernel_times, TCOLA_STAGES, scola_tiling_info, scola_time_table, scola_uses_tensor_cores,
 )
 from .simulation import Scola, ScolaDensity  # noqa: F401

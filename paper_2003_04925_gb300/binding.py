@@ -74,6 +74,7 @@ _sig = {
     "scola_tcola": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "scola_generate_white_noise": (c_int32, [c_void_p, ctypes.c_uint64, c_void_p]),
     "scola_box_mass": (c_int32, [c_void_p, c_void_p, _P(c_double), _P(c_int32), c_int32]),
+    "scola_shard_ranges": (c_int32, [_P(ScolaParams), c_int32, _P(c_int32), _P(c_int32)]),
     "scola_lpt_fields": (c_int32, [c_void_p] + [c_void_p] * 6),
     "scola_setup_boxes": (c_int32, [c_void_p]),
     "scola_pm_force": (c_int32, [c_void_p, c_void_p, c_double, c_void_p, c_void_p, c_void_p]),
@@ -167,6 +168,14 @@ def scola_destroy(ctx):
 
 def scola_forward(ctx, w, x, p):
     _check(_lib.scola_forward(ctx, _ptr(w), _ptr(x), _ptr(p)), "scola_forward")
+
+
+def scola_shard_ranges(params, world):
+    """Cost-balanced contiguous (first, count) box ranges for `world` ranks (host only)."""
+    first = (c_int32 * world)()
+    count = (c_int32 * world)()
+    _check(_lib.scola_shard_ranges(ctypes.byref(params), world, first, count), "scola_shard_ranges")
+    return list(zip(list(first), list(count)))
 
 
 def scola_box_mass(ctx, s, nboxes):

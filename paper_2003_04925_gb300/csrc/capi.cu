@@ -1228,6 +1228,44 @@ scola_status scola_tiling_info(const scola_params *params, int32_t *box_nsc, int
     return SCOLA_OK;
 }
 
+scola_status scola_shard_ranges(const scola_params *params, int32_t world, int32_t *first, int32_t *count) {
+    std::vector<int32_t> bufs;
+    std::vector<BoxGeom> geo;
+    CS(validate(params, bufs, geo));
+    if (!first || !count) return invalid("NULL argument");
+    const int n = (int)geo.size();
+    if (world < 1 || world > n) return invalid("world must be between 1 and the box count");
+    // cost of a box: its particle work plus the mesh work of its Poisson solve
+    std::vector<double> cost(n);
+    double total = 0.0;
+    for (int b = 0; b < n; ++b) {
+        cost[b] = std::pow((double)geo[b].nsc, 3) + std::pow((double)geo[b].ng, 3);
+        total += cost[b];
+    }
+    // contiguous ranges: rank r takes boxes while the running cost stays within half a box
+    // of r + 1 world-th of the total, leaving at least one box for every later rank
+    int start = 0;
+    double acc = 0.0;
+    for (int r = 0; r < world; ++r) {
+        if (r == world - 1) {
+            first[r] = start;
+            count[r] = n - start;
+            break;
+        }
+        const double target = total * (r + 1) / world;
+        int end = start + 1;
+        acc += cost[start];
+        while (end < n - (world - 1 - r) && acc + cost[end] / 2.0 <= target) {
+            acc += cost[end];
+            ++end;
+        }
+        first[r] = start;
+        count[r] = end - start;
+        start = end;
+    }
+    return SCOLA_OK;
+}
+
 scola_status scola_time_table(const scola_params *params, double *a_force, double *D1, double *D2,
                               double *beta, double *alpha, double *dD1, double *dD2) {
     std::vector<int32_t> bufs;

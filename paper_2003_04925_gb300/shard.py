@@ -37,6 +37,13 @@ def box_ranges(costs, world):
     return ranges
 
 
+def plan(params, world):
+    """The library's native plan (scola_shard_ranges) for a problem statement: the same
+    cost model and split as ``box_ranges`` over the tiling's boxes."""
+    from . import binding
+    return binding.scola_shard_ranges(params, world)
+
+
 def merge_disjoint(parts, fill_value):
     """Union of per-rank arrays in which each rank filled only its own entries."""
     import numpy as np

@@ -141,3 +141,29 @@ def test_time_table_matches_oracle(lib, Om, OL, nsteps, stepping):
     for k_lib, k_or in [("a_force", "a"), ("D1", "D1"), ("D2", "D2"), ("beta", "beta"),
                         ("alpha", "alpha"), ("dD1", "dD1"), ("dD2", "dD2")]:
         np.testing.assert_allclose(t[k_lib], o[k_or], rtol=1e-9, atol=1e-13, err_msg=k_lib)
+
+
+def test_native_shard_plan_matches_the_cost_model(lib):
+    # scola_shard_ranges (host only) against the package's statement of the same split over
+    # the tiling's boxes; every box exactly once, contiguous, at least one box per rank.
+    from paper_2003_04925_gb300 import shard
+    import synth_inputs
+    bufs = [int(b) for b in synth_inputs.uneven_buffers(4, 3, (4, 8, 16))]
+    cases = [lib.make_params(L=100.0, Np=32, Ntiles=2, Nbuf=4),
+             lib.make_params(L=500.0, Np=256, Ntiles=4, buffers=bufs),
+             lib.make_params(L=250.0, Np=128, Ntiles=4, Nbuf=8, mesh_ratio=2)]
+    for prm in cases:
+        nb = prm.Ntiles ** 3
+        nsc = (ctypes.c_int32 * nb)()
+        ng = (ctypes.c_int32 * nb)()
+        lib.binding._lib.scola_tiling_info(ctypes.byref(prm), nsc, ng, None, None)
+        costs = [shard.box_cost(a, b) for a, b in zip(nsc, ng)]
+        for world in (1, 2, 3, 5, 8, nb):
+            if world > nb:
+                continue
+            got = shard.plan(prm, world)
+            assert got == shard.box_ranges(costs, world)
+            assert got[0][0] == 0 and sum(c for _, c in got) == nb and all(c >= 1 for _, c in got)
+            assert all(got[i][0] + got[i][1] == got[i + 1][0] for i in range(world - 1))
+    with pytest.raises(lib.ScolaError):
+        shard.plan(cases[0], 9)                  # more ranks than boxes
