@@ -403,8 +403,9 @@ int32_t scola_uses_tensor_cores(const scola_ctx *ctx);
  * Adjoint support.  With checkpointing enabled, scola_forward also stores the
  * displacements of every box particle at every force evaluation (the
  * per-step checkpoints: (nsteps + 1) x 3 x P floats) and the context keeps
- * the adjoint work arrays.  Batched form, 2LPT frame, no study mode and one
- * batch only (UNSUPPORTED otherwise).  Synchronises the stream.
+ * the adjoint work arrays.  Batched form, FDA order 2, a common a_f, no study mode
+ * and one batch only (UNSUPPORTED otherwise); 2LPT or Zel'dovich frame, modified or
+ * standard KDK factors.  Synchronises the stream.
  */
 scola_status scola_set_checkpointing(scola_ctx *ctx, int32_t enable);
 

@@ -213,8 +213,8 @@ def lpt_vjp(delta, L, lam_phi1, lam_psi1, lam_psi2):
 # ----------------------------------------------------------------------------- full run
 def loss_and_grad(w, cfg, delta_target):
     """Lval(w) and dLval/dw for the final-density loss of one sCOLA run."""
-    if getattr(cfg, "lpt_order", 2) != 2 or getattr(cfg, "fda_order", 2) != 2:
-        raise NotImplementedError("the adjoint follows the 2LPT frame and FDA order 2 only")
+    if getattr(cfg, "fda_order", 2) != 2 or getattr(cfg, "a_final", None) is not None:
+        raise NotImplementedError("the adjoint follows FDA order 2 and a common final scale factor only")
     w = np.asarray(w, dtype=np.float64)
     fields = scola.initial_fields(w, cfg)
     sched = scola.schedule(cfg)
@@ -281,6 +281,8 @@ def loss_and_grad(w, cfg, delta_target):
         np.add.at(lam_psi2, bx["ids"], lp2)
         lam_phi1 += bc_shell_T(lam_shell, cfg.L, cfg.Np, g.origin, g.dg, g.Ng)
     N = cfg.Np
+    if getattr(cfg, "lpt_order", 2) == 1:
+        lam_psi2[:] = 0.0          # Zel'dovich frame: Psi2 = 0 does not depend on the noise
     lam_delta = lpt_vjp(fields.delta, cfg.L, lam_phi1, lam_psi1.T.reshape(3, N, N, N),
                         lam_psi2.T.reshape(3, N, N, N))
     lam_w = ics.initial_density(lam_delta, cfg.L, cfg.Om, cfg.h, cfg.ns, cfg.sigma8)

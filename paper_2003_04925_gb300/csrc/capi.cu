@@ -1516,10 +1516,6 @@ scola_status scola_set_checkpointing(scola_ctx *c, int32_t enable) {
         set_error("the adjoint is built for FDA order 2 only");
         return SCOLA_ERR_UNSUPPORTED;
     }
-    if (on && c->prm.lpt_order != 2) {
-        set_error("the adjoint is built for the 2LPT frame only");
-        return SCOLA_ERR_UNSUPPORTED;
-    }
     if (on == c->checkpointing) return SCOLA_OK;
     CK(c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize());
     if (c->evolve_exec) {
@@ -1577,20 +1573,24 @@ scola_status scola_backward(scola_ctx *c, const float *lam_delta, float *lam_w) 
     }
     CK(launch_adj_init_scatter(*c, c->adj, c->lamPsi1, c->lamPsi2));
     CK(launch_adj_shell_to_phi1(*c, c->lam_shell, c->lam_phi1));
-    // full-box 2LPT and colouring adjoints (symmetric Fourier operators)
+    // full-box 2LPT and colouring adjoints (symmetric Fourier operators); in the Zel'dovich
+    // frame Psi2 = 0 does not depend on the noise and the second-order chain is absent
+    const bool second = c->prm.lpt_order == 2;
     CK(launch_neg_div(*c, c->lamPsi1, 1, c->lam_phi1));
-    CK(launch_neg_div(*c, c->lamPsi2, 0, c->lam_phi2));
-    CF(cufftExecR2C(c->plan_r2c, c->lam_phi2, c->ct));
-    CK(launch_inv_laplacian(*c, c->ct, c->ct, (float)(1.0 / (double)N3)));
-    CF(cufftExecC2R(c->plan_c2r, c->ct, c->g[0]));                // lam_S
     const int pairs[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
-    for (int q = 0; q < 6; ++q) {
-        CK(launch_second_derivative(*c, c->cp, c->ct, pairs[q][0], pairs[q][1]));
-        CF(cufftExecC2R(c->plan_c2r, c->ct, c->d2 + (size_t)q * N3));
+    if (second) {
+        CK(launch_neg_div(*c, c->lamPsi2, 0, c->lam_phi2));
+        CF(cufftExecR2C(c->plan_r2c, c->lam_phi2, c->ct));
+        CK(launch_inv_laplacian(*c, c->ct, c->ct, (float)(1.0 / (double)N3)));
+        CF(cufftExecC2R(c->plan_c2r, c->ct, c->g[0]));                // lam_S
+        for (int q = 0; q < 6; ++q) {
+            CK(launch_second_derivative(*c, c->cp, c->ct, pairs[q][0], pairs[q][1]));
+            CF(cufftExecC2R(c->plan_c2r, c->ct, c->d2 + (size_t)q * N3));
+        }
+        CK(launch_adj_source(*c, c->g[0], c->d2, c->lam_d2));
     }
-    CK(launch_adj_source(*c, c->g[0], c->d2, c->lam_d2));
     CF(cufftExecR2C(c->plan_r2c, c->lam_phi1, c->ck));
-    for (int q = 0; q < 6; ++q) {
+    for (int q = 0; second && q < 6; ++q) {
         CF(cufftExecR2C(c->plan_r2c, c->lam_d2 + (size_t)q * N3, c->ct));
         CK(launch_spec_d2_accumulate(*c, c->ct, c->ck, pairs[q][0], pairs[q][1]));
     }

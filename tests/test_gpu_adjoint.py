@@ -76,6 +76,28 @@ def test_backward_matches_fp64_oracle_adjoint(ratio, variant):
     assert max(rels) < 5e-3, rels
 
 
+@pytest.mark.parametrize("option", ["zeldovich", "standard_stepping"])
+def test_backward_variants_match_fp64_oracle_adjoint(option):
+    # The Zel'dovich frame (no second-order chain in the LPT adjoint) and the standard KDK
+    # factors (the same reverse sweep with other coefficients), tensor-core form.
+    over = {"zeldovich": dict(lpt_order=1), "standard_stepping": dict(time_stepping=1)}[option]
+    kw = dict(L=48.0, Np=16, Ntiles=2, Nbuf=2, mesh_ratio=1, nsteps=3, a_i=0.05, a_f=1.0, **over)
+    cfg = oracle_cfg(kw)
+    target = _target(kw, 22)
+    sim = _sim(kw, "tc")
+    rels = []
+    for seed in (21, 23, 24):
+        w = synth_inputs.white_noise(16, seed)
+        val, g = _gpu_loss_grad(sim, w, target)
+        _pkg().scola_device_status(sim.ctx)
+        val_o, g_o = adjoint.loss_and_grad(w.astype(np.float64), cfg, target)
+        assert abs(val / val_o - 1) < 1e-4
+        rels.append(np.linalg.norm(g - g_o) / np.linalg.norm(g_o))
+        print("gradient vs FP64 oracle: %s seed %d rel %.3e" % (option, seed, rels[-1]))
+    sim.close()
+    assert np.median(rels) < 1e-3 and max(rels) < 5e-3, rels
+
+
 def test_autograd_function_matches_backward():
     sc = _pkg()
     kw = dict(L=48.0, Np=16, Ntiles=2, Nbuf=2, mesh_ratio=1, nsteps=3, a_i=0.05, a_f=1.0)

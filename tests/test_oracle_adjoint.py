@@ -83,9 +83,11 @@ def test_lpt_vjp_finite_differences():
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("ratio", [1, 2])
-def test_whole_loss_gradient_finite_differences(ratio):
-    cfg = scola.ScolaConfig(L=48.0, Np=12, Ntiles=2, Nbuf=2, mesh_ratio=ratio, nsteps=2, a_i=0.05)
+@pytest.mark.parametrize("ratio,extra", [(1, {}), (2, {}), (1, {"lpt_order": 1}), (1, {"stepping": "standard"})])
+def test_whole_loss_gradient_finite_differences(ratio, extra):
+    # the default 2LPT frame with modified KDK factors at 1:1 and 2:1, and the Zel'dovich frame
+    # and the standard factors (the same reverse sweep with their own coefficients)
+    cfg = scola.ScolaConfig(L=48.0, Np=12, Ntiles=2, Nbuf=2, mesh_ratio=ratio, nsteps=2, a_i=0.05, **extra)
     w = synth_inputs.white_noise(12, 21).astype(np.float64)
     target = stats.cic_density_periodic(
         scola.run_scola(synth_inputs.white_noise(12, 22), cfg)["x"], cfg.L, cfg.Np, cfg.Np)
