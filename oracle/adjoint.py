@@ -213,8 +213,8 @@ def lpt_vjp(delta, L, lam_phi1, lam_psi1, lam_psi2):
 # ----------------------------------------------------------------------------- full run
 def loss_and_grad(w, cfg, delta_target):
     """Lval(w) and dLval/dw for the final-density loss of one sCOLA run."""
-    if getattr(cfg, "fda_order", 2) != 2 or getattr(cfg, "a_final", None) is not None:
-        raise NotImplementedError("the adjoint follows FDA order 2 and a common final scale factor only")
+    if getattr(cfg, "fda_order", 2) != 2:
+        raise NotImplementedError("the adjoint follows FDA order 2 only")
     w = np.asarray(w, dtype=np.float64)
     fields = scola.initial_fields(w, cfg)
     sched = scola.schedule(cfg)
@@ -224,22 +224,24 @@ def loss_and_grad(w, cfg, delta_target):
     boxes = []
     for b in range(cfg.nboxes):
         g = scola.box_geometry(cfg, b)
+        # per-tile final scale factors: the box's own KDK schedule (same a_i, same step count)
+        sb = scola.box_schedule(cfg, b) if getattr(cfg, "a_final", None) is not None else sched
         ids = tiling.box_global_ids(cfg.Np, cfg.Ntiles, g.t, g.Nbuf)
         psi1 = fields.psi1.reshape(3, -1)[:, ids].T
         psi2 = fields.psi2.reshape(3, -1)[:, ids].T
         qloc = (tiling.box_local_lattice(g.Nsc) + 0.5) * (cfg.L / cfg.Np)
         shell = boundary.bc_shell(fields.phi1, cfg.L, g.origin, g.dg, g.Ng)
-        s = -sched["D1_i"] * psi1 + sched["D2_i"] * psi2
+        s = -sb["D1_i"] * psi1 + sb["D2_i"] * psi2
         p = np.zeros_like(s)
         ss = []
         for k in range(n + 1):
             ss.append(s)
-            F = pm.box_force(qloc + s, g.dg, g.Ng, g.Nsc, sched["D1"][k] * shell)["F"]
-            D1, D2 = sched["D1"][k], sched["D2"][k]
-            p = p + sched["beta"][k] * (F - D1 * psi1 + (D2 - D1 * D1) * psi2)
+            F = pm.box_force(qloc + s, g.dg, g.Ng, g.Nsc, sb["D1"][k] * shell)["F"]
+            D1, D2 = sb["D1"][k], sb["D2"][k]
+            p = p + sb["beta"][k] * (F - D1 * psi1 + (D2 - D1 * D1) * psi2)
             if k < n:
-                s = s + sched["alpha"][k] * p - sched["dD1"][k] * psi1 + sched["dD2"][k] * psi2
-        boxes.append(dict(g=g, ids=ids, psi1=psi1, psi2=psi2, qloc=qloc, shell=shell, ss=ss, s=s))
+                s = s + sb["alpha"][k] * p - sb["dD1"][k] * psi1 + sb["dD2"][k] * psi2
+        boxes.append(dict(sb=sb, g=g, ids=ids, psi1=psi1, psi2=psi2, qloc=qloc, shell=shell, ss=ss, s=s))
     s_glob = np.zeros((Np3, 3))
     for bx in boxes:
         keep = tiling.tile_interior_mask(cfg.Np, cfg.Ntiles, bx["g"].Nbuf)
@@ -254,7 +256,7 @@ def loss_and_grad(w, cfg, delta_target):
     lam_psi2 = np.zeros((Np3, 3))
     lam_phi1 = np.zeros_like(fields.phi1)
     for bx in boxes:
-        g = bx["g"]
+        g, sb = bx["g"], bx["sb"]
         keep = tiling.tile_interior_mask(cfg.Np, cfg.Ntiles, g.Nbuf)
         lam_s = np.zeros_like(bx["s"])
         lam_s[keep] = lam_x[bx["ids"][keep]]
@@ -264,19 +266,19 @@ def loss_and_grad(w, cfg, delta_target):
         lam_shell = np.zeros((g.Ng + 4,) * 3)
         for k in range(n, -1, -1):
             if k < n:
-                lam_p = lam_p + sched["alpha"][k] * lam_s
-                lp1 = lp1 - sched["dD1"][k] * lam_s
-                lp2 = lp2 + sched["dD2"][k] * lam_s
-            b = sched["beta"][k]
-            D1, D2 = sched["D1"][k], sched["D2"][k]
+                lam_p = lam_p + sb["alpha"][k] * lam_s
+                lp1 = lp1 - sb["dD1"][k] * lam_s
+                lp2 = lp2 + sb["dD2"][k] * lam_s
+            b = sb["beta"][k]
+            D1, D2 = sb["D1"][k], sb["D2"][k]
             lam_F = b * lam_p
             lp1 = lp1 - b * D1 * lam_p
             lp2 = lp2 + b * (D2 - D1 * D1) * lam_p
             lx, lbc = box_force_vjp(bx["qloc"] + bx["ss"][k], g.dg, g.Ng, g.Nsc, D1 * bx["shell"], lam_F)
             lam_s = lam_s + lx
             lam_shell += D1 * lbc
-        lp1 = lp1 - sched["D1_i"] * lam_s
-        lp2 = lp2 + sched["D2_i"] * lam_s
+        lp1 = lp1 - sb["D1_i"] * lam_s
+        lp2 = lp2 + sb["D2_i"] * lam_s
         np.add.at(lam_psi1, bx["ids"], lp1)
         np.add.at(lam_psi2, bx["ids"], lp2)
         lam_phi1 += bc_shell_T(lam_shell, cfg.L, cfg.Np, g.origin, g.dg, g.Ng)

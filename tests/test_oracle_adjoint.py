@@ -83,15 +83,20 @@ def test_lpt_vjp_finite_differences():
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("ratio,extra", [(1, {}), (2, {}), (1, {"lpt_order": 1}), (1, {"stepping": "standard"})])
+@pytest.mark.parametrize("ratio,extra", [(1, {}), (2, {}), (1, {"lpt_order": 1}), (1, {"stepping": "standard"}),
+                                         (1, {"a_final": [1.0, 0.7, 0.5, 0.9, 0.8, 0.6, 0.95, 0.4]})])
 def test_whole_loss_gradient_finite_differences(ratio, extra):
-    # the default 2LPT frame with modified KDK factors at 1:1 and 2:1, and the Zel'dovich frame
-    # and the standard factors (the same reverse sweep with their own coefficients)
+    # the default 2LPT frame with modified KDK factors at 1:1 and 2:1, the Zel'dovich frame,
+    # the standard factors, and per-tile final scale factors (each box's reverse sweep with
+    # its own coefficients)
     cfg = scola.ScolaConfig(L=48.0, Np=12, Ntiles=2, Nbuf=2, mesh_ratio=ratio, nsteps=2, a_i=0.05, **extra)
     w = synth_inputs.white_noise(12, 21).astype(np.float64)
     target = stats.cic_density_periodic(
         scola.run_scola(synth_inputs.white_noise(12, 22), cfg)["x"], cfg.L, cfg.Np, cfg.Np)
     val, grad = adjoint.loss_and_grad(w, cfg, target)
+    # the adjoint's own forward sweep is the method's run (pinned on its own)
+    d_run = stats.cic_density_periodic(scola.run_scola(w, cfg)["x"], cfg.L, cfg.Np, cfg.Np)
+    assert abs(val - np.sum((d_run - target) ** 2)) < 1e-10 * val
     f = lambda ww: adjoint.loss_and_grad(ww, cfg, target)[0]
     for seed in (23, 24):
         d = synth_inputs.random_field(w.shape, seed)
