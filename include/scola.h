@@ -133,7 +133,7 @@ typedef enum scola_batch_mode {
  *                (light-cone scheduling, Sec. 5): tile t takes nsteps steps linear in a
  *                from a_i to a_final[t], and its particles leave scola_forward at that
  *                time (positions and momenta with L+ at a_final[t]).  All boxes still go
- *                through each launch together.  The adjoint needs a common a_f
+ *                through each launch together
  *   study_mode   bit flags of scola_study_mode (Sec. 4.3).  0 runs the method.  Otherwise
  *                scola_forward first runs the periodic full-box tCOLA of scola_tcola and
  *                keeps its density and potential at every force evaluation, then evolves
@@ -403,9 +403,9 @@ int32_t scola_uses_tensor_cores(const scola_ctx *ctx);
  * Adjoint support.  With checkpointing enabled, scola_forward also stores the
  * displacements of every box particle at every force evaluation (the
  * per-step checkpoints: (nsteps + 1) x 3 x P floats) and the context keeps
- * the adjoint work arrays.  Batched form, FDA order 2, a common a_f, no study mode
- * and one batch only (UNSUPPORTED otherwise); 2LPT or Zel'dovich frame, modified or
- * standard KDK factors.  Synchronises the stream.
+ * the adjoint work arrays.  Batched form, FDA order 2, no study mode and one batch
+ * only (UNSUPPORTED otherwise); 2LPT or Zel'dovich frame, modified or standard KDK
+ * factors, common or per-tile final scale factors.  Synchronises the stream.
  */
 scola_status scola_set_checkpointing(scola_ctx *ctx, int32_t enable);
 

@@ -932,6 +932,7 @@ scola_status fill_light_cone_tables(scola_ctx *c) {
             e[4] = kd.d1;
             e[5] = kd.d2;
             e[6] = (float)(1.0 / t.D1[k]);
+            e[7] = (float)t.beta[k];          // the adjoint's kick factor (its force is Phi itself)
         }
         const double pref = af * af * t.Hconf_f;
         coefL[2 * i] = (float)(-pref * t.dD1da_f);
@@ -1508,10 +1509,6 @@ scola_status scola_set_checkpointing(scola_ctx *c, int32_t enable) {
         set_error("the adjoint runs on the batched form only");
         return SCOLA_ERR_UNSUPPORTED;
     }
-    if (on && !c->a_final.empty()) {
-        set_error("the adjoint needs a common final scale factor (no a_final)");
-        return SCOLA_ERR_UNSUPPORTED;
-    }
     if (on && c->prm.fda_order != 2) {
         set_error("the adjoint is built for FDA order 2 only");
         return SCOLA_ERR_UNSUPPORTED;
@@ -1559,16 +1556,18 @@ scola_status scola_backward(scola_ctx *c, const float *lam_delta, float *lam_w) 
     // final density -> tile particles
     CK(launch_adj_final(*c, lam_delta, c->adj));
     const int n = (int)c->tt.alpha.size();
+    // with per-tile final scale factors every box takes its own factors of evaluation k from
+    // the coefficient table (k is passed on); otherwise the uniform scalars
     for (int k = n; k >= 0; --k) {
-        CK(launch_adj_kick_drift(*c, c->adj, kick_drift_coefficients(c->tt, k)));
+        CK(launch_adj_kick_drift(*c, c->adj, kick_drift_coefficients(c->tt, k), k));
         const float *sk = c->ckpt + (size_t)k * 3 * P;
-        CK(launch_deposit(*c, sk, P, (float)(1.0 / c->tt.D1[k])));
+        CK(launch_deposit(*c, sk, P, (float)(1.0 / c->tt.D1[k]), nullptr, false, k));
         CK(launch_poisson(*c));
         CK(cudaMemsetAsync(c->lamG, 0, fb * 3 * c->MP, c->stream));
-        CK(launch_adj_interp(*c, sk, c->adj, c->lamG, (float)c->tt.D1[k]));
+        CK(launch_adj_interp(*c, sk, c->adj, c->lamG, (float)c->tt.D1[k], k));
         CK(launch_adj_div(*c, c->lamG, c->lam_phi_pad, c->adj_in));
         CK(launch_poisson_buffers(*c, c->adj_in, c->work, c->work2, c->adj_out));
-        CK(launch_adj_shell(*c, c->lam_phi_pad, c->adj_out, (float)c->tt.D1[k], c->lam_shell));
+        CK(launch_adj_shell(*c, c->lam_phi_pad, c->adj_out, (float)c->tt.D1[k], c->lam_shell, k));
         CK(launch_adj_deposit(*c, sk, c->adj_out, c->adj));
     }
     CK(launch_adj_init_scatter(*c, c->adj, c->lamPsi1, c->lamPsi2));

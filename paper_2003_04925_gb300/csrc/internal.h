@@ -148,7 +148,7 @@ struct Ctx {
     bool deposit_split = false;                       // sorted form: 32-bit halves of the counts
     bool tuned = false;                               // the autotuner has picked the forms above
     // per-tile final scale factors: per box of the bound batch and force evaluation k, the
-    // FP32 coefficients [kF (forward, x D1), k1, k2, alpha, d1, d2, 1/D1, 0] at
+    // FP32 coefficients [kF (forward, x D1), k1, k2, alpha, d1, d2, 1/D1, beta (adjoint kF)] at
     // coef[(box (nsteps + 1) + k) 8], and the L+ factors [c1, c2] at coefL[2 box]; null
     // when every tile ends at a_f (the kernels then take the uniform scalars)
     float *coef = nullptr, *coefL = nullptr;
@@ -268,11 +268,12 @@ cudaError_t launch_true_pad(Ctx &c, const float *phi, float inv_D1);
 
 cudaError_t launch_adj_colour(Ctx &c, const cufftComplex *in, cufftComplex *out);
 cudaError_t launch_adj_final(Ctx &c, const float *lam_delta, float *adj);
-cudaError_t launch_adj_kick_drift(Ctx &c, float *adj, const KickDrift &kd);
-cudaError_t launch_adj_interp(Ctx &c, const float *s, float *adj, float *lamG, float D1);
+// k >= 0 with per-tile final scale factors: each box's factors of evaluation k (coef table)
+cudaError_t launch_adj_kick_drift(Ctx &c, float *adj, const KickDrift &kd, int k = -1);
+cudaError_t launch_adj_interp(Ctx &c, const float *s, float *adj, float *lamG, float D1, int k = -1);
 cudaError_t launch_adj_div(Ctx &c, const float *lamG, float *lam_phi_pad, float *interior_out);
 cudaError_t launch_adj_shell(Ctx &c, const float *lam_phi_pad, const float *lam_src_pad, float D1,
-                             float *lam_shell);
+                             float *lam_shell, int k = -1);
 cudaError_t launch_adj_deposit(Ctx &c, const float *s, const float *lam_src_pad, float *adj);
 cudaError_t launch_adj_init_scatter(Ctx &c, const float *adj, float *lamPsi1, float *lamPsi2);
 cudaError_t launch_adj_shell_to_phi1(Ctx &c, const float *lam_shell, float *lam_phi1);

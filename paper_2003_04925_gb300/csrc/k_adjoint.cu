@@ -90,9 +90,17 @@ k_adj_final(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
 
 __global__ void __launch_bounds__(kChunk)
 k_adj_kick_drift(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
-                 float *__restrict__ adj, long long P, KickDrift kd) {
+                 float *__restrict__ adj, long long P, KickDrift kd, const float *__restrict__ coef, int k, int nk) {
     const Chunk ch = chunks[blockIdx.x];
     const BoxDesc &B = boxes[ch.box];
+    if (const float *cf = box_coef(coef, ch.box, k, nk)) {     // this box's own time factors
+        kd.kF = cf[7];
+        kd.k1 = cf[1];
+        kd.k2 = cf[2];
+        kd.alpha = cf[3];
+        kd.d1 = cf[4];
+        kd.d2 = cf[5];
+    }
     const int local = ch.start + threadIdx.x;
     if (local >= B.Nsc * B.Nsc * B.Nsc) return;
     const long long gi = B.p_off + local;
@@ -119,9 +127,11 @@ k_adj_kick_drift(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ ch
 __global__ void __launch_bounds__(kChunk)
 k_adj_interp(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
              const float *__restrict__ s, long long P, const float *__restrict__ phi, float D1,
-             float *__restrict__ adj, float *__restrict__ lamG, long long MP) {
+             float *__restrict__ adj, float *__restrict__ lamG, long long MP, const float *__restrict__ coef,
+             int k, int nk) {
     const Chunk ch = chunks[blockIdx.x];
     const BoxDesc &B = boxes[ch.box];
+    if (const float *cf = box_coef(coef, ch.box, k, nk)) D1 = 1.0f / cf[6];
     const int Nsc = B.Nsc, Ng = B.Ng;
     const int local = ch.start + threadIdx.x;
     if (local >= Nsc * Nsc * Nsc) return;
@@ -197,9 +207,10 @@ k_adj_div(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
 __global__ void __launch_bounds__(kChunk)
 k_adj_shell(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
             const float *__restrict__ lam_phi_pad, const float *__restrict__ lam_src_pad, float D1,
-            float *__restrict__ lam_shell) {
+            float *__restrict__ lam_shell, const float *__restrict__ coef, int k, int nk) {
     const Chunk ch = chunks[blockIdx.x];
     const BoxDesc &B = boxes[ch.box];
+    if (const float *cf = box_coef(coef, ch.box, k, nk)) D1 = 1.0f / cf[6];
     const int Ng = B.Ng;
     const long long idx = (long long)ch.start + threadIdx.x;
     if (idx >= shell_count(Ng, 2)) return;
@@ -396,14 +407,16 @@ cudaError_t launch_adj_final(Ctx &c, const float *lam_delta, float *adj) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_adj_kick_drift(Ctx &c, float *adj, const KickDrift &kd) {
-    k_adj_kick_drift<<<c.n_pchunks, kChunk, 0, c.stream>>>(c.boxes, c.pchunks, adj, c.P, kd);
+cudaError_t launch_adj_kick_drift(Ctx &c, float *adj, const KickDrift &kd, int k) {
+    k_adj_kick_drift<<<c.n_pchunks, kChunk, 0, c.stream>>>(c.boxes, c.pchunks, adj, c.P, kd,
+                                                            k >= 0 ? c.coef : nullptr, k, c.coef_nk);
     ++c.launches;
     return cudaGetLastError();
 }
 
-cudaError_t launch_adj_interp(Ctx &c, const float *s, float *adj, float *lamG, float D1) {
-    k_adj_interp<<<c.n_pchunks, kChunk, 0, c.stream>>>(c.boxes, c.pchunks, s, c.P, c.phi, D1, adj, lamG, c.MP);
+cudaError_t launch_adj_interp(Ctx &c, const float *s, float *adj, float *lamG, float D1, int k) {
+    k_adj_interp<<<c.n_pchunks, kChunk, 0, c.stream>>>(c.boxes, c.pchunks, s, c.P, c.phi, D1, adj, lamG, c.MP,
+                                                        k >= 0 ? c.coef : nullptr, k, c.coef_nk);
     ++c.launches;
     return cudaGetLastError();
 }
@@ -416,9 +429,9 @@ cudaError_t launch_adj_div(Ctx &c, const float *lamG, float *lam_phi_pad, float 
 }
 
 cudaError_t launch_adj_shell(Ctx &c, const float *lam_phi_pad, const float *lam_src_pad, float D1,
-                             float *lam_shell) {
+                             float *lam_shell, int k) {
     k_adj_shell<<<c.n_shchunks, kChunk, 0, c.stream>>>(c.boxes, c.shchunks, lam_phi_pad, lam_src_pad, D1,
-                                                        lam_shell);
+                                                        lam_shell, k >= 0 ? c.coef : nullptr, k, c.coef_nk);
     ++c.launches;
     return cudaGetLastError();
 }

@@ -76,11 +76,13 @@ def test_backward_matches_fp64_oracle_adjoint(ratio, variant):
     assert max(rels) < 5e-3, rels
 
 
-@pytest.mark.parametrize("option", ["zeldovich", "standard_stepping"])
+@pytest.mark.parametrize("option", ["zeldovich", "standard_stepping", "light_cone"])
 def test_backward_variants_match_fp64_oracle_adjoint(option):
-    # The Zel'dovich frame (no second-order chain in the LPT adjoint) and the standard KDK
-    # factors (the same reverse sweep with other coefficients), tensor-core form.
-    over = {"zeldovich": dict(lpt_order=1), "standard_stepping": dict(time_stepping=1)}[option]
+    # The Zel'dovich frame (no second-order chain in the LPT adjoint), the standard KDK
+    # factors (the same reverse sweep with other coefficients) and per-tile final scale
+    # factors (every box's reverse sweep with its own coefficients), tensor-core form.
+    over = {"zeldovich": dict(lpt_order=1), "standard_stepping": dict(time_stepping=1),
+            "light_cone": dict(a_final=[1.0, 0.7, 0.5, 0.9, 0.8, 0.6, 0.95, 0.4])}[option]
     kw = dict(L=48.0, Np=16, Ntiles=2, Nbuf=2, mesh_ratio=1, nsteps=3, a_i=0.05, a_f=1.0, **over)
     cfg = oracle_cfg(kw)
     target = _target(kw, 22)
