@@ -27,13 +27,19 @@ gradient is assembled backwards through every step of ``scola.run_scola``:
          phi1 = Lap^-1 delta_i              (symmetric Fourier operators)
   A.1    delta_i = colour(w)                (real symmetric filter)
 
+Every stencil follows the run's FDA order (2, 4 or 6, Sec. 3.1): the order-n gradient at
+the CIC corners and in the LPT stage, the order-n boundary source and Laplacian symbol,
+n ghost layers.  Per-tile final scale factors give every box its own coefficients.
+
 Pins (tests/test_oracle_adjoint.py): dot-product identities <J v, u> = <v, J^T u>
 for each linear piece, and FP64 central finite differences of the whole loss
-along random directions.
+along random directions (orders 2, 4, 6; both LPT frames; both KDK factor sets;
+per-tile final scale factors), with the adjoint's own forward sweep checked against
+the method's run.
 """
 import numpy as np
 
-from . import boundary, ics, lpt, pm, scola, stats, tiling
+from . import boundary, fda, ics, lpt, pm, scola, stats, tiling
 
 
 # ----------------------------------------------------------------------------- CIC pieces
@@ -83,17 +89,31 @@ def box_density_vjp(xloc, dg, Ng, Nsc, lam_delta):
     return lam * inv_nbar / dg
 
 
-def interp_vjp(phi_pad, xloc, dg, lam_F):
-    """VJP of F = interpolate_gradient(phi_pad, x): returns (lam_x, lam_phi_pad)."""
-    Ng = phi_pad.shape[0] - 4
+def _shift_add(out, src, a, m, sign):
+    """out[c + m e_a] += sign * src[c] (m may be negative; entries shifted out are dropped)."""
+    n = src.shape[a]
+    dst_sl = [slice(None)] * 3
+    src_sl = [slice(None)] * 3
+    if m >= 0:
+        dst_sl[a], src_sl[a] = slice(m, n), slice(0, n - m)
+    else:
+        dst_sl[a], src_sl[a] = slice(0, n + m), slice(-m, n)
+    out[tuple(dst_sl)] += sign * src[tuple(src_sl)]
+
+
+def interp_vjp(phi_pad, xloc, dg, lam_F, order=2):
+    """VJP of F = interpolate_gradient(phi_pad, x) at FDA order n: returns (lam_x, lam_phi_pad)."""
+    P, ng = order, fda.n_ghost(order)
+    Ng = phi_pad.shape[0] - 2 * P
+    g = fda.gradient_coefficients(order)
     u_raw = pm.mesh_coordinate(xloc, dg)
-    u = np.clip(u_raw, -1.0, float(Ng))
+    u = np.clip(u_raw, -float(ng), float(Ng + ng - 1))
     free = (u == u_raw).astype(np.float64)               # d u / d u_raw (0 where clamped)
-    i0 = np.minimum(np.floor(u).astype(np.int64), Ng - 1)
+    i0 = np.minimum(np.floor(u).astype(np.int64), Ng + ng - 2)
     f = u - i0
-    P = phi_pad
+    Pp = phi_pad
     lam_x = np.zeros_like(u)
-    lam_G = np.zeros((3,) + P.shape)                     # adjoint of the gradient mesh
+    lam_G = np.zeros((3,) + Pp.shape)                    # adjoint of the gradient mesh
     for dx in (0, 1):
         for dy in (0, 1):
             for dz in (0, 1):
@@ -102,55 +122,58 @@ def interp_vjp(phi_pad, xloc, dg, lam_F):
                 g1 = [1.0 if d[a] else -1.0 for a in range(3)]
                 w = w1[0] * w1[1] * w1[2]
                 dw = np.stack([g1[0] * w1[1] * w1[2], w1[0] * g1[1] * w1[2], w1[0] * w1[1] * g1[2]], 1)
-                cx, cy, cz = i0[:, 0] + dx + 2, i0[:, 1] + dy + 2, i0[:, 2] + dz + 2
-                G = np.stack([(P[cx + 1, cy, cz] - P[cx - 1, cy, cz]),
-                              (P[cx, cy + 1, cz] - P[cx, cy - 1, cz]),
-                              (P[cx, cy, cz + 1] - P[cx, cy, cz - 1])], 1) / (2.0 * dg)
+                c = [i0[:, a] + d[a] + P for a in range(3)]
+                G = np.zeros_like(u)
+                for a in range(3):
+                    for m, gm in enumerate(g, start=1):
+                        cp, cm = list(c), list(c)
+                        cp[a], cm[a] = c[a] + m, c[a] - m
+                        G[:, a] += gm * (Pp[cp[0], cp[1], cp[2]] - Pp[cm[0], cm[1], cm[2]])
+                G /= dg
                 # direct term: d w / d u * (G . lam_F)
                 lam_x += dw * np.sum(G * lam_F, axis=1)[:, None]
                 for a in range(3):
-                    np.add.at(lam_G[a], (cx, cy, cz), w * lam_F[:, a])
+                    np.add.at(lam_G[a], (c[0], c[1], c[2]), w * lam_F[:, a])
     lam_x *= free / dg
-    # G_a(c) = (P(c + e_a) - P(c - e_a)) / (2 dg)  ->  lam_P(c +- e_a) += +- lam_G_a(c) / (2 dg)
-    lam_P = np.zeros_like(P)
+    # G_a(c) = sum_m g_m (P(c + m e_a) - P(c - m e_a)) / dg  ->  lam_P(c +- m e_a) += +- g_m lam_G_a(c) / dg
+    lam_P = np.zeros_like(Pp)
     for a in range(3):
-        g = lam_G[a] / (2.0 * dg)
-        sl_p = [slice(None)] * 3
-        sl_m = [slice(None)] * 3
-        src_p = [slice(None)] * 3
-        src_m = [slice(None)] * 3
-        sl_p[a], src_p[a] = slice(1, None), slice(None, -1)   # lam_P[c+1] += g[c]
-        sl_m[a], src_m[a] = slice(None, -1), slice(1, None)   # lam_P[c-1] -= g[c]
-        lam_P[tuple(sl_p)] += g[tuple(src_p)]
-        lam_P[tuple(sl_m)] -= g[tuple(src_m)]
+        for m, gm in enumerate(g, start=1):
+            _shift_add(lam_P, gm * lam_G[a] / dg, a, m, 1.0)
+            _shift_add(lam_P, gm * lam_G[a] / dg, a, -m, -1.0)
     return lam_x, lam_P
 
 
-def laplacian_on_interior_T(lam_int, dg):
-    """Adjoint of ``pm.laplacian_on_interior`` (padded -> interior)."""
+def laplacian_on_interior_T(lam_int, dg, order=2):
+    """Adjoint of ``pm.laplacian_on_interior`` (padded -> interior) at FDA order n."""
+    P = order
     Ng = lam_int.shape[0]
-    out = np.zeros((Ng + 4,) * 3)
-    c = slice(2, Ng + 2)
-    out[c, c, c] += -6.0 * lam_int
-    out[3:Ng + 3, c, c] += lam_int
-    out[1:Ng + 1, c, c] += lam_int
-    out[c, 3:Ng + 3, c] += lam_int
-    out[c, 1:Ng + 1, c] += lam_int
-    out[c, c, 3:Ng + 3] += lam_int
-    out[c, c, 1:Ng + 1] += lam_int
+    s = fda.second_derivative_coefficients(order)
+    out = np.zeros((Ng + 2 * P,) * 3)
+    c = slice(P, Ng + P)
+    out[c, c, c] += 3.0 * s[0] * lam_int
+    for m in range(1, len(s)):
+        hi, lo = slice(P + m, Ng + P + m), slice(P - m, Ng + P - m)
+        out[hi, c, c] += s[m] * lam_int
+        out[lo, c, c] += s[m] * lam_int
+        out[c, hi, c] += s[m] * lam_int
+        out[c, lo, c] += s[m] * lam_int
+        out[c, c, hi] += s[m] * lam_int
+        out[c, c, lo] += s[m] * lam_int
     return out / dg**2
 
 
-def box_force_vjp(xloc, dg, Ng, Nsc, phi_bc_padded, lam_F):
+def box_force_vjp(xloc, dg, Ng, Nsc, phi_bc_padded, lam_F, order=2):
     """VJP of ``pm.box_force`` (F only): returns (lam_x, lam_phi_bc_padded)."""
+    P = order
     delta, _ = pm.cic_deposit_box(xloc, dg, Ng, Nsc)
-    phi = pm.dirichlet_potential(delta, phi_bc_padded, dg)
-    lam_x, lam_P = interp_vjp(phi, xloc, dg, lam_F)
-    inside = boundary.interior_mask(Ng)
-    lam_int = lam_P[2:Ng + 2, 2:Ng + 2, 2:Ng + 2]
-    lam_src = pm.zero_bc_poisson(lam_int, dg)            # self-adjoint Dirichlet solve
+    phi = pm.dirichlet_potential(delta, phi_bc_padded, dg, order)
+    lam_x, lam_P = interp_vjp(phi, xloc, dg, lam_F, order)
+    inside = boundary.interior_mask(Ng, order)
+    lam_int = lam_P[P:Ng + P, P:Ng + P, P:Ng + P]
+    lam_src = pm.zero_bc_poisson(lam_int, dg, order)     # self-adjoint Dirichlet solve (S Lambda^-1 S)
     lam_bc = np.where(inside, 0.0, lam_P)                # ghost layers take Phi_BC directly
-    lam_bc -= np.where(inside, 0.0, laplacian_on_interior_T(lam_src, dg))
+    lam_bc -= np.where(inside, 0.0, laplacian_on_interior_T(lam_src, dg, order))
     lam_x += box_density_vjp(xloc, dg, Ng, Nsc, lam_src)
     return lam_x, lam_bc
 
@@ -171,40 +194,46 @@ def trilinear_periodic_T(vals, L, N, X):
     return out
 
 
-def bc_shell_T(lam_shell, L, N, origin, dg, Ng):
+def bc_shell_T(lam_shell, L, N, origin, dg, Ng, order=2):
     """Adjoint of ``boundary.bc_shell`` with respect to phi1."""
-    c = boundary.padded_cell_index(Ng).astype(np.float64)
+    c = boundary.padded_cell_index(Ng, order).astype(np.float64)
     cx, cy, cz = np.meshgrid(c, c, c, indexing="ij")
     X = np.stack([origin[0] + (cx.ravel() + 0.5) * dg, origin[1] + (cy.ravel() + 0.5) * dg,
                   origin[2] + (cz.ravel() + 0.5) * dg], axis=1)
-    vals = np.where(boundary.interior_mask(Ng), 0.0, lam_shell).ravel()
+    vals = np.where(boundary.interior_mask(Ng, order), 0.0, lam_shell).ravel()
     return trilinear_periodic_T(vals, L, N, X)
 
 
-def central_gradient_T(g, L):
+def central_gradient_T(g, L, order=2):
     """Adjoint of ``lpt.central_gradient``: the central difference is antisymmetric."""
     N = g.shape[1]
     d = L / N
-    return -sum((np.roll(g[a], -1, axis=a) - np.roll(g[a], 1, axis=a)) / (2.0 * d) for a in range(3))
+    cf = fda.gradient_coefficients(order)
+    return -sum(gm * (np.roll(g[a], -m, axis=a) - np.roll(g[a], m, axis=a)) / d
+                for a in range(3) for m, gm in enumerate(cf, start=1))
 
 
-def lpt_vjp(delta, L, lam_phi1, lam_psi1, lam_psi2):
+def lpt_vjp(delta, L, lam_phi1, lam_psi1, lam_psi2, order=2):
     """lam_delta_i from the adjoints of phi1, Psi1 and Psi2 (Eqs. 5-6, C.2)."""
     N = delta.shape[0]
     d = L / N
-    lam = lpt.laplacian_symbol(N, L)
-    inv = lambda fk: np.where(lam != 0, fk / np.where(lam != 0, lam, 1.0), 0.0)
+    lam = lpt.laplacian_symbol(N, L, order)
+
+    def inv(fk):
+        out = np.where(lam != 0, fk / np.where(lam != 0, lam, 1.0), 0.0)
+        out[0, 0, 0] = 0.0                   # the k = 0 mode is removed (by index)
+        return out
     kx, ky, kz = ics.fourier_wavenumbers(N, L)
-    D = [np.sin(kx * d) / d, np.sin(ky * d) / d, np.sin(kz * d) / d]
+    D = [fda.gradient_symbol(k, d, order) for k in (kx, ky, kz)]
     phi1_k = inv(np.fft.rfftn(delta))
     sec = lambda i, j, fk: np.fft.irfftn(-D[i] * D[j] * fk, s=delta.shape, axes=(0, 1, 2))
     xx, yy, zz = sec(0, 0, phi1_k), sec(1, 1, phi1_k), sec(2, 2, phi1_k)
     xy, xz, yz = sec(0, 1, phi1_k), sec(0, 2, phi1_k), sec(1, 2, phi1_k)
-    lam_phi2 = central_gradient_T(lam_psi2, L)
+    lam_phi2 = central_gradient_T(lam_psi2, L, order)
     lam_S = np.fft.irfftn(inv(np.fft.rfftn(lam_phi2)), s=delta.shape, axes=(0, 1, 2))
     parts = [((0, 0), lam_S * (yy + zz)), ((1, 1), lam_S * (xx + zz)), ((2, 2), lam_S * (xx + yy)),
              ((0, 1), -2.0 * lam_S * xy), ((0, 2), -2.0 * lam_S * xz), ((1, 2), -2.0 * lam_S * yz)]
-    lam_phi1_k = np.fft.rfftn(lam_phi1 + central_gradient_T(lam_psi1, L))
+    lam_phi1_k = np.fft.rfftn(lam_phi1 + central_gradient_T(lam_psi1, L, order))
     for (i, j), v in parts:
         lam_phi1_k = lam_phi1_k + (-D[i] * D[j]) * np.fft.rfftn(v)
     return np.fft.irfftn(inv(lam_phi1_k), s=delta.shape, axes=(0, 1, 2))
@@ -213,8 +242,7 @@ def lpt_vjp(delta, L, lam_phi1, lam_psi1, lam_psi2):
 # ----------------------------------------------------------------------------- full run
 def loss_and_grad(w, cfg, delta_target):
     """Lval(w) and dLval/dw for the final-density loss of one sCOLA run."""
-    if getattr(cfg, "fda_order", 2) != 2:
-        raise NotImplementedError("the adjoint follows FDA order 2 only")
+    order = getattr(cfg, "fda_order", 2)
     w = np.asarray(w, dtype=np.float64)
     fields = scola.initial_fields(w, cfg)
     sched = scola.schedule(cfg)
@@ -230,13 +258,13 @@ def loss_and_grad(w, cfg, delta_target):
         psi1 = fields.psi1.reshape(3, -1)[:, ids].T
         psi2 = fields.psi2.reshape(3, -1)[:, ids].T
         qloc = (tiling.box_local_lattice(g.Nsc) + 0.5) * (cfg.L / cfg.Np)
-        shell = boundary.bc_shell(fields.phi1, cfg.L, g.origin, g.dg, g.Ng)
+        shell = boundary.bc_shell(fields.phi1, cfg.L, g.origin, g.dg, g.Ng, order)
         s = -sb["D1_i"] * psi1 + sb["D2_i"] * psi2
         p = np.zeros_like(s)
         ss = []
         for k in range(n + 1):
             ss.append(s)
-            F = pm.box_force(qloc + s, g.dg, g.Ng, g.Nsc, sb["D1"][k] * shell)["F"]
+            F = pm.box_force(qloc + s, g.dg, g.Ng, g.Nsc, sb["D1"][k] * shell, order=order)["F"]
             D1, D2 = sb["D1"][k], sb["D2"][k]
             p = p + sb["beta"][k] * (F - D1 * psi1 + (D2 - D1 * D1) * psi2)
             if k < n:
@@ -263,7 +291,7 @@ def loss_and_grad(w, cfg, delta_target):
         lam_p = np.zeros_like(lam_s)
         lp1 = np.zeros_like(lam_s)
         lp2 = np.zeros_like(lam_s)
-        lam_shell = np.zeros((g.Ng + 4,) * 3)
+        lam_shell = np.zeros((g.Ng + 2 * order,) * 3)
         for k in range(n, -1, -1):
             if k < n:
                 lam_p = lam_p + sb["alpha"][k] * lam_s
@@ -274,18 +302,18 @@ def loss_and_grad(w, cfg, delta_target):
             lam_F = b * lam_p
             lp1 = lp1 - b * D1 * lam_p
             lp2 = lp2 + b * (D2 - D1 * D1) * lam_p
-            lx, lbc = box_force_vjp(bx["qloc"] + bx["ss"][k], g.dg, g.Ng, g.Nsc, D1 * bx["shell"], lam_F)
+            lx, lbc = box_force_vjp(bx["qloc"] + bx["ss"][k], g.dg, g.Ng, g.Nsc, D1 * bx["shell"], lam_F, order)
             lam_s = lam_s + lx
             lam_shell += D1 * lbc
         lp1 = lp1 - sb["D1_i"] * lam_s
         lp2 = lp2 + sb["D2_i"] * lam_s
         np.add.at(lam_psi1, bx["ids"], lp1)
         np.add.at(lam_psi2, bx["ids"], lp2)
-        lam_phi1 += bc_shell_T(lam_shell, cfg.L, cfg.Np, g.origin, g.dg, g.Ng)
+        lam_phi1 += bc_shell_T(lam_shell, cfg.L, cfg.Np, g.origin, g.dg, g.Ng, order)
     N = cfg.Np
     if getattr(cfg, "lpt_order", 2) == 1:
         lam_psi2[:] = 0.0          # Zel'dovich frame: Psi2 = 0 does not depend on the noise
     lam_delta = lpt_vjp(fields.delta, cfg.L, lam_phi1, lam_psi1.T.reshape(3, N, N, N),
-                        lam_psi2.T.reshape(3, N, N, N))
+                        lam_psi2.T.reshape(3, N, N, N), order)
     lam_w = ics.initial_density(lam_delta, cfg.L, cfg.Om, cfg.h, cfg.ns, cfg.sigma8)
     return value, lam_w
