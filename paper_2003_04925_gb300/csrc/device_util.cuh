@@ -189,6 +189,25 @@ __device__ __forceinline__ void shell_stencil(const BoxDesc &B, const int pc[3],
     }
 }
 
+// The same stencil with the offsets in FP64: r / den is exact to FP64 rounding (one division of
+// two exact integers), for the FP64 accumulation of the C.3 shell.
+__device__ __forceinline__ void shell_stencil_d(const BoxDesc &B, const int pc[3], int Ntile, int i0[3],
+                                                double f[3]) {
+    const int t[3] = {B.tx, B.ty, B.tz};
+    const int den = 2 * B.Ng;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int num = (2 * (pc[a] - B.gpad) + 1) * B.Nsc - B.Ng;
+        int q = num / den, r = num - q * den;
+        if (r < 0) {
+            r += den;
+            --q;
+        }
+        i0[a] = t[a] * Ntile - B.Nbuf + q;
+        f[a] = (double)r / (double)den;
+    }
+}
+
 __device__ __forceinline__ int wrap(int v, int n) {
     v %= n;
     return v < 0 ? v + n : v;

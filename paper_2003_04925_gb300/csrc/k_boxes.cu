@@ -6,9 +6,10 @@
 //             s = -D1(a_i) Psi1 + D2(a_i) Psi2, p_res = 0 (Eqs. 39, 55).
 //  shell      C.3: phi1 trilinearly interpolated (periodic, nodes at (i+1/2) d)
 //             to the centre of every padded PM cell outside the interior; the
-//             stencil comes from exact integer arithmetic (shell_stencil), the
-//             eight products are summed in FP32 in a fixed order (LEP scaling by
-//             D1(a_K) happens per force evaluation, Eq. 23).
+//             stencil comes from exact integer arithmetic (shell_stencil_d), the
+//             weights and the eight products are formed and summed in FP64 in a
+//             fixed order, and the sum is rounded once to FP32 (LEP scaling by
+//             D1(a_K) happens per force evaluation, Eq. 23).  Runs once per run.
 //  scatter    B.2 and L+: tile particles only; x = (q + s) mod L and
 //             p = p_res + a^2 calH (-dD1/da Psi1 + dD2/da Psi2) at a_f (Eq. 55).
 //  box_ids    the global id of every box particle (integer, for inspection).
@@ -62,26 +63,26 @@ k_shell(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
     int pc[3];
     shell_coord(idx, B.Ng, B.gpad, pc[0], pc[1], pc[2]);
     int i0[3];
-    float f[3];
-    shell_stencil(B, pc, Ntile, i0, f);
-    float sum = 0.0f;
+    double f[3];
+    shell_stencil_d(B, pc, Ntile, i0, f);
+    double sum = 0.0;
     const long long NN = (long long)N * N;
 #pragma unroll
     for (int dx = 0; dx < 2; ++dx) {
         const long long ix = wrap(i0[0] + dx, N);
-        const float wx = dx ? f[0] : 1.0f - f[0];
+        const double wx = dx ? f[0] : 1.0 - f[0];
 #pragma unroll
         for (int dy = 0; dy < 2; ++dy) {
             const long long iy = wrap(i0[1] + dy, N);
-            const float wxy = wx * (dy ? f[1] : 1.0f - f[1]);
+            const double wxy = wx * (dy ? f[1] : 1.0 - f[1]);
 #pragma unroll
             for (int dz = 0; dz < 2; ++dz) {
                 const long long iz = wrap(i0[2] + dz, N);
-                sum = fmaf(wxy * (dz ? f[2] : 1.0f - f[2]), phi1[ix * NN + iy * N + iz], sum);
+                sum = fma(wxy * (dz ? f[2] : 1.0 - f[2]), (double)phi1[ix * NN + iy * N + iz], sum);
             }
         }
     }
-    shell[B.sh_off + idx] = sum;
+    shell[B.sh_off + idx] = (float)sum;
 }
 
 __global__ void __launch_bounds__(kChunk)
