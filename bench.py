@@ -10,9 +10,14 @@ steps, per second.
   python bench.py [--gpus N --steps K --warmup W] [--workload batched_128]
   python bench.py --impl reference ...   # the FP64 CPU oracle on bounded samples
 
-Multi-GPU: every rank runs an independent replica of the workload (different
-seed); there is no collective on the data path (boxes never communicate), so
-value = sum over ranks of the work / max rank time ("weak" scaling).
+Multi-GPU: the run's boxes are split into cost-balanced contiguous ranges, one per
+rank (the library's shard plan); every rank builds the initial conditions itself and
+evolves its range, with no collective on the data path (boxes never communicate), so
+value = the work of all boxes / max rank time ("strong" scaling).
+
+The JSON line carries the per-tile comparison and the adjoint cost at its end; the
+per-kernel table, the study workload and the autotuner picks go to stderr and to
+gpurun_out/bench_details.json (or $SCOLA_BENCH_DETAILS).
 """
 import argparse
 import json
@@ -152,73 +157,123 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- oracle timing
-def oracle_sample_rate(name, budget_s, nboxes_cap=None):
-    """Oracle particle-steps/s on a bounded sample: ICs once (prorated), whole boxes evolved."""
-    import numpy as np
+# The FP64 oracle, as it stands, timed on the host cores: the boxes are independent (Sec. 3.2),
+# so one single-threaded process per core evolves whole boxes side by side.  The processes are
+# spawned (never forked from a process that holds a CUDA context), and each builds the
+# initial conditions once in its initializer, outside the timed region.
+_ORACLE = {}
+
+
+def _oracle_worker_init(name):
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
     import synth_inputs
     from oracle import scola as oscola
-    kw, W = workload_kwargs(name)
-    cfg = oscola.ScolaConfig(L=kw["L"], Np=kw["Np"], Ntiles=kw["Ntiles"],
-                             Nbuf=kw.get("buffers") or kw["Nbuf"], mesh_ratio=kw["mesh_ratio"],
-                             nsteps=kw["nsteps"], a_i=kw["a_i"], a_f=kw["a_f"])
+    cfg = oracle_config(name)
+    W = synth_inputs.WORKLOADS[name]
     w = synth_inputs.white_noise(cfg.Np, W["seed"])
+    _ORACLE.update(cfg=cfg, fields=oscola.initial_fields(w, cfg), sched=oscola.schedule(cfg))
+
+
+def _oracle_worker_box(b):
+    from oracle import scola as oscola
+    c = _ORACLE
     t0 = time.perf_counter()
-    fields = oscola.initial_fields(w, cfg)
-    sched = oscola.schedule(cfg)
-    t_ics = time.perf_counter() - t0
-    done, t_boxes, work = 0, 0.0, 0
-    while True:
-        b = (done * 37) % cfg.nboxes
-        t1 = time.perf_counter()
-        r = oscola.evolve_box(cfg, b, fields, sched)
-        t_boxes += time.perf_counter() - t1
-        work += r["geometry"].Nsc ** 3 * cfg.nsteps
-        done += 1
-        if t_boxes >= budget_s or (nboxes_cap and done >= nboxes_cap):
-            break
-    seconds = t_boxes + t_ics * done / cfg.nboxes
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    return {"value": work / seconds, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "%d of %d sCOLA boxes evolved over all %d steps (%.1f s) + 1/%d of the "
-                      "full-box IC/2LPT time per box (numpy FP64, BLAS threads up to %d)"
-                      % (done, cfg.nboxes, cfg.nsteps, t_boxes, cfg.nboxes, cores)}
+    r = oscola.evolve_box(c["cfg"], b, c["fields"], c["sched"])
+    return r["geometry"].Nsc ** 3 * c["cfg"].nsteps, time.perf_counter() - t0
+
+
+def _oracle_ics_seconds(name):
+    import synth_inputs
+    from oracle import scola as oscola
+    cfg = oracle_config(name)
+    w = synth_inputs.white_noise(cfg.Np, synth_inputs.WORKLOADS[name]["seed"])
+    t0 = time.perf_counter()
+    oscola.initial_fields(w, cfg)
+    return time.perf_counter() - t0
+
+
+def oracle_config(name):
+    from oracle import scola as oscola
+    kw, _ = workload_kwargs(name)
+    return oscola.ScolaConfig(L=kw["L"], Np=kw["Np"], Ntiles=kw["Ntiles"], Nbuf=kw.get("buffers") or kw["Nbuf"],
+                              mesh_ratio=kw["mesh_ratio"], nsteps=kw["nsteps"], a_i=kw["a_i"], a_f=kw["a_f"])
+
+
+def host_cores():
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+
+
+class OraclePool:
+    """One spawned single-threaded oracle process per host core (at most 16), each holding the
+    workload's initial conditions.  run(k) evolves k whole boxes side by side (box ids
+    rotating through the tiling) and returns (particle-steps, wall seconds)."""
+
+    def __init__(self, name, workers=None):
+        import multiprocessing as mp
+        from concurrent.futures import ProcessPoolExecutor
+        self.name = name
+        self.cores = workers or min(16, host_cores())
+        self.nboxes = oracle_config(name).nboxes
+        self.ex = ProcessPoolExecutor(max_workers=self.cores, mp_context=mp.get_context("spawn"),
+                                      initializer=_oracle_worker_init, initargs=(name,))
+        self.next = 0
+        self._start = [self.ex.submit(int, i) for i in range(self.cores)]   # spawn the workers now
+
+    def run(self, k):
+        ids = [((self.next + i) * 37) % self.nboxes for i in range(k)]
+        self.next += k
+        t0 = time.perf_counter()
+        res = list(self.ex.map(_oracle_worker_box, ids))
+        return sum(r[0] for r in res), time.perf_counter() - t0
+
+    def close(self):
+        self.ex.shutdown()
+
+
+def oracle_sample_rate(name, pool=None):
+    """Oracle particle-steps/s on a bounded sample: one box per core evolved over all COLA
+    steps, side by side, plus the IC/2LPT time prorated per box."""
+    own = pool is None
+    pool = pool or OraclePool(name)
+    pool.run(pool.cores)                                  # warm-up batch
+    work, sec = pool.run(pool.cores)
+    t_ics = _oracle_ics_seconds(name)
+    if own:
+        pool.close()
+    seconds = sec + t_ics * pool.cores / pool.nboxes
+    return {"value": work / seconds, "unit": UNIT, "cores": pool.cores, "kind": "oracle",
+            "sample": "%d of %d sCOLA boxes evolved over all steps side by side, one single-threaded numpy "
+                      "FP64 process per core (%.1f s wall), + %d/%d of the full-box IC/2LPT time"
+                      % (pool.cores, pool.nboxes, sec, pool.cores, pool.nboxes)}
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return
     kw, W = workload_kwargs(args.workload)
-    import synth_inputs
-    from oracle import scola as oscola
-    cfg = oscola.ScolaConfig(L=kw["L"], Np=kw["Np"], Ntiles=kw["Ntiles"],
-                             Nbuf=kw.get("buffers") or kw["Nbuf"], mesh_ratio=kw["mesh_ratio"],
-                             nsteps=kw["nsteps"], a_i=kw["a_i"], a_f=kw["a_f"])
-    w = synth_inputs.white_noise(cfg.Np, W["seed"])
-    t0 = time.perf_counter()
-    fields = oscola.initial_fields(w, cfg)
-    sched = oscola.schedule(cfg)
-    t_ics = time.perf_counter() - t0
-    # each step: one sCOLA box (rotating through the boxes) over all COLA steps, plus the
-    # per-box share of the IC stage; shrink to fewer boxes never (a box is the unit)
-    for i in range(args.warmup):
-        oscola.evolve_box(cfg, (i * 37) % cfg.nboxes, fields, sched)
+    pool = OraclePool(args.workload)
+    t_ics = _oracle_ics_seconds(args.workload)
+    # each step: one box per core, side by side, over all COLA steps, plus those boxes'
+    # share of the IC stage
+    for _ in range(args.warmup):
+        pool.run(pool.cores)
     t_total, work = 0.0, 0
-    for i in range(args.steps):
-        b = ((args.warmup + i) * 37) % cfg.nboxes
-        t1 = time.perf_counter()
-        r = oscola.evolve_box(cfg, b, fields, sched)
-        t_total += time.perf_counter() - t1 + t_ics / cfg.nboxes
-        work += r["geometry"].Nsc ** 3 * cfg.nsteps
+    for _ in range(args.steps):
+        wk, sec = pool.run(pool.cores)
+        t_total += sec + t_ics * pool.cores / pool.nboxes
+        work += wk
+    pool.close()
     value = work / t_total
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": config_block(args.workload, kw, W, {"step": "one sCOLA box over all COLA "
-                                   "steps + 1/nboxes of the IC/2LPT stage"}),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": "%d boxes of %d, numpy FP64" % (args.steps, cfg.nboxes)},
+            "config": config_block(args.workload, kw, W, {"step": "%d sCOLA boxes (one per host core) over all "
+                                   "COLA steps + their share of the IC/2LPT stage" % pool.cores}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": pool.cores, "kind": "oracle",
+                             "sample": "%d steps of %d of %d boxes, one single-threaded numpy FP64 process per "
+                                       "core" % (args.steps, pool.cores, pool.nboxes)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -243,7 +298,7 @@ def adjoint_cost(sc, torch, dst, steps):
     for _ in range(2):
         x, _ = sim.forward(w)
         d = sim.final_density(x)
-        sim.backward(2.0 * (d - target))
+        sim.backward_density(2.0 * (d - target))
         plain.forward(w)
     torch.cuda.synchronize()
     t_plain = t_fwd = t_bwd = 0.0
@@ -255,7 +310,7 @@ def adjoint_cost(sc, torch, dst, steps):
         d = sim.final_density(x)
         lam = 2.0 * (d - target)
         ev[2].record(stream)
-        sim.backward(lam)
+        sim.backward_density(lam)
         ev[3].record(stream)
         torch.cuda.synchronize()
         t_plain += ev[0].elapsed_time(ev[1])
@@ -265,8 +320,10 @@ def adjoint_cost(sc, torch, dst, steps):
     plain.close()
     sim.close()
     t_plain, t_fwd, t_bwd = t_plain / steps, t_fwd / steps, t_bwd / steps
-    return {"workload": "adjoint_128", "ms_forward": t_plain, "ms_forward_checkpointed": t_fwd,
-            "ms_backward": t_bwd, "adjoint_over_forward": t_bwd / t_plain,
+    # a gradient costs the checkpointed forward run (with the loss) plus the backward sweep
+    return {"workload": "adjoint_128", "ms_forward": round(t_plain, 4), "ms_forward_checkpointed": round(t_fwd, 4),
+            "ms_backward": round(t_bwd, 4), "backward_over_forward": round(t_bwd / t_plain, 4),
+            "gradient_over_forward": round((t_fwd + t_bwd) / t_plain, 4),
             "loss": "sum over the 128^3 CIC mesh of (delta - delta_target)^2, target from seed 2"}
 
 
@@ -408,6 +465,34 @@ def measured_traffic(workload, dst):
     return out
 
 
+def per_tile_cost(sc, torch, kw, w, x, p, ms_batched, steps, world):
+    """The plain per-tile form (one box per launch, boxes in turn) on the same input, with the
+    tensor-core solve the batched form uses and with the FP32 CUDA-core solve (the plain
+    per-tile FP32 GPU path); both give results bit-identical to their batched forms."""
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {}
+    work = particle_steps_per_run(kw)
+    for tag, dst in (("tc", kw["dst_variant"]), ("fp32", sc.SCOLA_DST_SIMT)):
+        pt = sc.Scola(**dict(kw, batch_mode=sc.SCOLA_BATCH_PER_TILE, dst_variant=dst))
+        xp, pp = torch.empty_like(x), torch.empty_like(p)
+        pt.forward(w, xp, pp)
+        torch.cuda.synchronize()
+        same = bool(torch.equal(xp, x) and torch.equal(pp, p)) if dst == kw["dst_variant"] else None
+        e0.record(stream)
+        for _ in range(steps):
+            pt.forward(w, xp, pp)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        pt.close()
+        out[tag] = {"value": world * work / (ms * 1e-3), "ms_per_step": round(ms, 3),
+                    "batched_speedup": round(ms / ms_batched, 3)}
+        if same is not None:
+            out[tag]["bit_identical_to_batched"] = same
+    return out
+
+
 def run_gpu(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -416,6 +501,9 @@ def run_gpu(args, rank, world, local_rank):
     import paper_2003_04925_gb300 as sc
     import synth_inputs
 
+    # the oracle's host processes start first (spawned, single-threaded); they build their
+    # initial conditions while the GPU work below runs
+    pool = OraclePool(args.workload) if rank == 0 and not args.no_cpu_baseline else None
     torch.cuda.set_device(local_rank)
     dist = None
     if world > 1:
@@ -426,9 +514,14 @@ def run_gpu(args, rank, world, local_rank):
                          "simt": sc.SCOLA_DST_SIMT}[args.dst]
     if args.batch_boxes:
         kw["batch_boxes"] = args.batch_boxes
+    if world > 1:
+        # strong scaling: one run, its boxes split into cost-balanced contiguous ranges, one per
+        # rank (boxes never communicate: no collective on the data path)
+        from paper_2003_04925_gb300 import shard
+        kw["box_first"], kw["box_count"] = (int(v) for v in shard.plan(sc.make_params(**kw), world)[rank])
     sim = sc.Scola(**kw)
     stream = torch.cuda.current_stream()
-    w_np = synth_inputs.white_noise(kw["Np"], W["seed"] + rank)
+    w_np = synth_inputs.white_noise(kw["Np"], W["seed"])
     w = torch.from_numpy(w_np).cuda()
     n = kw["Np"] ** 3
     x = torch.empty(n, 3, device="cuda")
@@ -466,6 +559,13 @@ def run_gpu(args, rank, world, local_rank):
         if dist is not None:
             dist.barrier()
 
+    def max_over_ranks(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
     clocks = ClockSampler(local_rank)
     barrier()
     torch.cuda.synchronize()
@@ -478,14 +578,11 @@ def run_gpu(args, rank, world, local_rank):
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps)
     launches = sim.stats()["kernel_launches"]
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    work = particle_steps_per_run(kw)
-    value = world * work / (ms * 1e-3)
+    full_kw = {k: v for k, v in kw.items() if k not in ("box_first", "box_count")}
+    work = particle_steps_per_run(full_kw)          # every box of the run, over all ranks
+    value = work / (ms * 1e-3)
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timing
     w_h = torch.from_numpy(w_np).pin_memory()
@@ -497,32 +594,21 @@ def run_gpu(args, rank, world, local_rank):
     t0 = time.perf_counter()
     for _ in range(args.steps):
         sim.forward_host(w_h, x_h, p_h)
-    t_e2e = (time.perf_counter() - t0) / args.steps
-    if dist is not None:
-        t = torch.tensor([t_e2e], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t.item())
-    e2e = {"value": world * work / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 4 * n,
-           "d2h_bytes_per_step": 2 * 12 * n}
+    t_e2e = max_over_ranks((time.perf_counter() - t0) / args.steps)
+    e2e = {"value": work / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 4 * n * world,
+           "d2h_bytes_per_step": 2 * 12 * n * world}
 
-    # the plain per-tile form (one box per launch, boxes in turn) on the same input
-    pt = sc.Scola(**dict(kw, batch_mode=sc.SCOLA_BATCH_PER_TILE))
-    xp, pp = torch.empty_like(x), torch.empty_like(p)
-    pt.forward(w, xp, pp)
-    torch.cuda.synchronize()
-    same = bool(torch.equal(xp, x) and torch.equal(pp, p))
-    k_pt = max(1, args.steps // 2)
-    e0.record(stream)
-    for _ in range(k_pt):
-        pt.forward(w, xp, pp)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms_pt = e0.elapsed_time(e1) / k_pt
-    pt.close()
-    per_tile = {"value": world * work / (ms_pt * 1e-3), "ms_per_step": ms_pt, "steps": k_pt,
-                "bit_identical_to_batched": same,
-                "speedup_batched_over_per_tile": ms_pt / ms}
-
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        peak_src = "measured"
+    except (OSError, ValueError):
+        peaks = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}
+        peak_src = "fallback"
+    details = {}
+    per_tile = adj = None
+    roofline = None
+    if world == 1:
+        per_tile = per_tile_cost(sc, torch, kw, w, x, p, ms, max(1, args.steps // 2), world)
     # per-kernel device time from events recorded between the kernels of the graph
     sc.scola_set_profiling(sim.ctx, True)
     for _ in range(2):
@@ -530,57 +616,59 @@ def run_gpu(args, rank, world, local_rank):
     torch.cuda.synchronize()
     kt = sc.scola_kernel_times(sim.ctx)
     sc.scola_set_profiling(sim.ctx, False)
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-        peak_src = "measured"
-    except (OSError, ValueError):
-        peaks = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}
-        peak_src = "fallback"
     dom, rows = kernel_roofline(kt, kw, clk, peaks, args.dst != "simt")
     sc.scola_device_status(sim.ctx)
     d = rows[dom]
     # ncu DRAM bytes per evaluation, keyed by class (dst_i: the i-th pass)
     traffic = measured_traffic(args.workload, args.dst)
     cls = {k: ("dst_%s" % k.split("_")[1] if k.startswith("dst_") else k) for k in rows}
-    roofline = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"],
-                "unit": d["unit"], "frac": d["frac"], "traffic": traffic.get(cls[dom]),
-                "traffic_source": "profiles/traffic_%s.json (ncu, DRAM read + write per force evaluation; "
-                                  "null where the kernel changed since the capture)" % args.workload,
+    roofline = {"kernel": dom, "bound": d["bound"], "achieved": round(d["achieved"], 2), "peak": d["peak"],
+                "unit": d["unit"], "frac": round(d["frac"], 4), "traffic": traffic.get(cls[dom]),
                 "peak_source": peak_src if d["bound"] == "hbm" else
-                "FP32 FMA: 152 SMs x 128 lanes x 2 flop x median SM clock under load",
-                "kernels": {k: {"ms_per_launch": round(v["ms"], 5), "share": round(v["share"], 4),
-                                "frac": round(v["frac"], 4), "bound": v["bound"],
-                                "traffic": traffic.get(cls[k])}
-                            for k, v in rows.items()}}
-
-    adj = adjoint_cost(sc, torch, args.dst, max(2, min(args.steps, 5)))
-    study = study_cost(sc, torch, {k: v for k, v in kw.items()}, W, max(2, min(args.steps, 5)), peaks)
+                "FP32 FMA: 152 SMs x 128 lanes x 2 flop x median SM clock under load"}
+    details["kernels"] = {k: {"ms_per_launch": round(v["ms"], 5), "share": round(v["share"], 4),
+                              "achieved": round(v["achieved"], 2), "unit": v["unit"],
+                              "frac": round(v["frac"], 4), "bound": v["bound"],
+                              "traffic": traffic.get(cls[k])} for k, v in rows.items()}
+    details["traffic_source"] = ("profiles/traffic_%s.json (ncu, DRAM read + write per force evaluation; "
+                                 "null where the kernel changed since the capture)" % args.workload)
+    if world == 1:
+        adj = adjoint_cost(sc, torch, args.dst, max(2, min(args.steps, 5)))
+        details["study"] = study_cost(sc, torch, {k: v for k, v in kw.items()}, W, max(2, min(args.steps, 5)),
+                                      peaks)
+    details["deposit_autotune"] = deposit_choice(sc, sim.stats())
+    details["dst_autotune"] = dst_tune
+    details["stats"] = {k: v for k, v in sim.stats().items() if k in ("ms_lpt", "ms_evolve", "r", "p", "batches")}
 
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
-        cpu = oracle_sample_rate(args.workload, budget_s=15.0)
+    if pool is not None:
+        cpu = oracle_sample_rate(args.workload, pool)
+        pool.close()
     if rank == 0:
-        nsc, ng = box_sizes(kw)
+        nsc, ng = box_sizes(full_kw)
         ws_bytes = 4 * (12 * sum(k**3 for k in nsc)) + 8 * sum(g**3 for g in ng) \
             + 4 * 2 * sum(g**3 for g in ng) + 4 * sum((g + 4) ** 3 for g in ng)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
                 "dtype": "f32", "data": "synthetic",
-                "config": config_block(args.workload, kw, W, {
+                "config": config_block(args.workload, full_kw, W, {
                     "step": "one full forward run (ICs + 2LPT + all boxes x all COLA steps + untiling)",
                     "particle_steps_per_step": work,
                     "l2": "working set %.2f GB > 129 MB L2, no flush" % (ws_bytes / 1e9),
-                    "parallelism": "replicas x%d" % world, "batching": "all boxes per launch, CUDA graph",
-                    "dst": {"tc": "dense sine-matrix pencils on tcgen05 tensor cores, 3xTF32",
-                            "tc4": "dense sine-matrix pencils on tcgen05 tensor cores, 4xTF32",
-                            "simt": "dense sine-matrix pencils, FP32 CUDA cores"}[args.dst]}),
-                "e2e": e2e, "per_tile": per_tile, "adjoint": adj, "study": study,
-                "gpu_launches": int(launches * args.steps),
-                "clocks": clk,
-                "roofline": roofline, "cpu_baseline": cpu,
-                "stats": {k: v for k, v in sim.stats().items() if k in ("ms_lpt", "ms_evolve", "r", "p")},
-                "deposit_autotune": deposit_choice(sc, sim.stats()), "dst_autotune": dst_tune}
+                    "parallelism": "boxes split over %d GPU(s)" % world,
+                    "dst": {"tc": "tcgen05 3xTF32", "tc4": "tcgen05 4xTF32", "simt": "FP32 CUDA cores"}[args.dst]}),
+                "gpu_launches": int(launches * args.steps), "clocks": clk,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e}
+        if per_tile is not None:
+            line["per_tile"] = per_tile
+        if adj is not None:
+            line["adjoint"] = adj
+        dpath = os.environ.get("SCOLA_BENCH_DETAILS", os.path.join(ROOT, "gpurun_out", "bench_details.json"))
+        if os.path.isdir(os.path.dirname(dpath)):
+            with open(dpath, "w") as fh:
+                json.dump(details, fh, indent=1)
+        print(json.dumps(details), file=sys.stderr, flush=True)
         print(json.dumps(line), flush=True)
     sim.close()
     if dist is not None:

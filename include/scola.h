@@ -410,21 +410,50 @@ int32_t scola_uses_tensor_cores(const scola_ctx *ctx);
 scola_status scola_set_checkpointing(scola_ctx *ctx, int32_t enable);
 
 /*
- * Gradient of a loss of the final density with respect to the white noise,
- * for the last scola_forward run on this context (made with checkpointing on).
- *   lam_delta_dev  device, Np^3 FP32: dLoss/d delta_final, where delta_final
- *                  is the periodic CIC density of scola_final_density (Sec. 4.1)
- *                  of that run's positions
- *   lam_w_dev      device, Np^3 FP32, receives dLoss/dw
- * Hand-written vector-Jacobian products of every step, in reverse: the
- * density, the untiling, the KDK sequence with the recomputed mesh force at
- * each checkpoint (interpolation weights, gradient mesh, the self-adjoint
- * Dirichlet solve, the boundary source and ghost layers, deposit weights,
- * App. B-C), L-, the boundary shell (C.3), 2LPT (Eqs. 5-6) and the colouring
- * (A.1).  Shared accumulations use FP32 atomics, so results can differ in the
- * last bits between calls.  Errors: STATE without a checkpointed forward run.
+ * Vector-Jacobian product of the whole forward run: the gradient, with respect to the white
+ * noise, of a loss of the final particle positions and momenta of the last scola_forward run
+ * on this context (made with checkpointing on).  The outputs of that run are x = (q + s) mod L
+ * (Sec. 2.1, Eq. 1, B.2) and p = p_res + a_f^2 calH(a_f)(-dD1/da Psi1 + dD2/da Psi2) (L+,
+ * Eq. 55) of every particle, so the sweep starts from lam_s = dL/dx, lam_p_res = dL/dp and the
+ * L+ transpose on each tile particle (buffer particles leave no output).
+ *   lam_x_dev  device, Np^3 x 3 FP32: dLoss/dx in the layout of scola_forward's x, or NULL (zero)
+ *   lam_p_dev  device, Np^3 x 3 FP32: dLoss/dp in the layout of scola_forward's p, or NULL (zero)
+ *   lam_w_dev  device, Np^3 FP32, receives dLoss/dw
+ * Hand-written vector-Jacobian products of every step, in reverse: the untiling and L+, the
+ * KDK sequence with the recomputed mesh force at each checkpoint (interpolation weights,
+ * gradient mesh, the self-adjoint Dirichlet solve, the boundary source and ghost layers,
+ * deposit weights, App. B-C), L-, the boundary shell (C.3), 2LPT (Eqs. 5-6) and the
+ * colouring (A.1).  Shared accumulations use FP32 atomics, so results can differ in the last
+ * bits between calls.  A position loss must be smooth across the periodic wrap of x (for
+ * example a loss of a periodic field sampled at x, as the final density is).
+ * Errors: INVALID_ARG (lam_w NULL, or both cotangents NULL); STATE without a checkpointed
+ * forward run, or after a scola_lpt_fields, scola_setup_boxes or scola_tcola call that
+ * replaced its state.
  */
-scola_status scola_backward(scola_ctx *ctx, const float *lam_delta_dev, float *lam_w_dev);
+scola_status scola_backward(scola_ctx *ctx, const float *lam_x_dev, const float *lam_p_dev, float *lam_w_dev);
+
+/*
+ * Adjoint of the final density (Sec. 4.1): lam_x = (d delta_final / dx)^T lam_delta for the
+ * periodic CIC density of scola_final_density, at the given positions.  Composed with
+ * scola_backward it differentiates a loss of the final density.  Needs no forward run.
+ *   x_dev          device, Np^3 x 3 FP32 positions in [0, L)
+ *   lam_delta_dev  device, Np^3 FP32: dLoss/d delta_final
+ *   lam_x_dev      device, Np^3 x 3 FP32, receives dLoss/dx
+ * Errors: INVALID_ARG (NULL), CUDA.
+ */
+scola_status scola_density_adjoint(scola_ctx *ctx, const float *x_dev, const float *lam_delta_dev,
+                                   float *lam_x_dev);
+
+/*
+ * Gradient of a loss of the final density with respect to the white noise for the last
+ * checkpointed scola_forward run: scola_density_adjoint at that run's positions followed by
+ * scola_backward, in one call (the positions are taken from the library's particle state,
+ * so no x buffer is needed; the result is the same).
+ *   lam_delta_dev  device, Np^3 FP32: dLoss/d delta_final (periodic CIC of scola_final_density)
+ *   lam_w_dev      device, Np^3 FP32, receives dLoss/dw
+ * Errors: as scola_backward.
+ */
+scola_status scola_backward_density(scola_ctx *ctx, const float *lam_delta_dev, float *lam_w_dev);
 
 /*
  * Box density without any allocation.  The paper has no counterpart: this is

@@ -2,12 +2,16 @@
 
 Test infrastructure (see ``oracle/__init__``).
 
-Loss:  Lval = sum_c (delta_f(c) - delta_t(c))^2  over the periodic N^3 CIC density of
-the final positions (Sec. 4.1), as a function of the white noise w.  The
-gradient is assembled backwards through every step of ``scola.run_scola``:
+Entry points: ``final_state_vjp`` turns dL/dx and dL/dp of the final positions and
+momenta of a run into dL/dw (w the white noise); ``loss_and_grad`` composes it with the
+periodic CIC adjoint for the loss Lval = sum_c (delta_f(c) - delta_t(c))^2 over the
+periodic N^3 CIC density of the final positions (Sec. 4.1).  The gradient is assembled
+backwards through every step of ``scola.run_scola``:
 
   delta_f = CIC(x)                      -> lam_x = dCIC/dx^T lam_delta        (weight gradients)
   x = (q + s_n) mod L  (tile particles) -> lam_s(n) = lam_x
+  p = p_res + a^2 calH (-dD1/da Psi1 + dD2/da Psi2)  (L+, Eq. 55)
+                                        -> lam_p_res = lam_p, lam_Psi1, lam_Psi2
   KDK in reverse (App. B, Eqs. 53-54), per box, with the displacements s_k of
   every force evaluation recomputed forward and kept (checkpoints):
       drift  s_k+1 = s_k + alpha p + d1 Psi1 + d2 Psi2
@@ -39,7 +43,7 @@ the method's run.
 """
 import numpy as np
 
-from . import boundary, fda, ics, lpt, pm, scola, stats, tiling
+from . import boundary, cosmology, fda, ics, lpt, pm, scola, stats, tiling
 
 
 # ----------------------------------------------------------------------------- CIC pieces
@@ -240,15 +244,16 @@ def lpt_vjp(delta, L, lam_phi1, lam_psi1, lam_psi2, order=2):
 
 
 # ----------------------------------------------------------------------------- full run
-def loss_and_grad(w, cfg, delta_target):
-    """Lval(w) and dLval/dw for the final-density loss of one sCOLA run."""
+def forward_with_checkpoints(w, cfg):
+    """The method's run from white noise w, keeping what the reverse sweep needs: the
+    initial fields, every box's displacements at each force evaluation (checkpoints), and
+    the final global positions x = (q + s) mod L and momenta p (L+, Eq. 55)."""
     order = getattr(cfg, "fda_order", 2)
     w = np.asarray(w, dtype=np.float64)
     fields = scola.initial_fields(w, cfg)
     sched = scola.schedule(cfg)
     n = len(sched["alpha"])
     Np3 = cfg.Np**3
-    # forward, keeping every box's displacements at each force evaluation
     boxes = []
     for b in range(cfg.nboxes):
         g = scola.box_geometry(cfg, b)
@@ -269,39 +274,57 @@ def loss_and_grad(w, cfg, delta_target):
             p = p + sb["beta"][k] * (F - D1 * psi1 + (D2 - D1 * D1) * psi2)
             if k < n:
                 s = s + sb["alpha"][k] * p - sb["dD1"][k] * psi1 + sb["dD2"][k] * psi2
-        boxes.append(dict(sb=sb, g=g, ids=ids, psi1=psi1, psi2=psi2, qloc=qloc, shell=shell, ss=ss, s=s))
+        a_f = scola.box_final_a(cfg, b)
+        p_fin = p + scola.lpt_momentum(a_f, sb["dD1da_f"], sb["dD2da_f"], psi1, psi2, cfg)
+        boxes.append(dict(sb=sb, g=g, ids=ids, psi1=psi1, psi2=psi2, qloc=qloc, shell=shell, ss=ss, s=s,
+                          p=p_fin, a_f=a_f))
     s_glob = np.zeros((Np3, 3))
+    p_glob = np.zeros((Np3, 3))
     for bx in boxes:
         keep = tiling.tile_interior_mask(cfg.Np, cfg.Ntiles, bx["g"].Nbuf)
         s_glob[bx["ids"][keep]] = bx["s"][keep]
+        p_glob[bx["ids"][keep]] = bx["p"][keep]
     x = np.mod(scola.lattice_positions(cfg.Np, cfg.L) + s_glob, cfg.L)
-    delta_f = stats.cic_density_periodic(x, cfg.L, cfg.Np, cfg.Np)
-    resid = delta_f - delta_target
-    value = float(np.sum(resid**2))
-    lam_x = periodic_density_vjp(x, cfg.L, cfg.Np, cfg.Np, 2.0 * resid)
+    return dict(fields=fields, boxes=boxes, n=n, order=order, x=x, p=p_glob)
 
+
+def final_state_vjp(state, cfg, lam_x, lam_p=None):
+    """dL/dw from dL/dx and dL/dp of the final global arrays of ``forward_with_checkpoints``.
+
+    x = (q + s) mod L (Sec. 2.1, Eq. 1) gives lam_s = lam_x for every tile particle; the
+    momentum p = p_res + a_f^2 calH(a_f) (-dD1/da Psi1 + dD2/da Psi2) (L+, Eq. 55) gives
+    lam_p_res = lam_p and lam_Psi1 = -c lam_p dD1/da, lam_Psi2 = c lam_p dD2/da with
+    c = a_f^2 calH(a_f).  Buffer particles of a box leave no output, so they start at zero.
+    Then the KDK sequence in reverse, L-, the shell, 2LPT and the colouring."""
+    order, n, fields = state["order"], state["n"], state["fields"]
+    Np3 = cfg.Np**3
+    lam_x = np.asarray(lam_x, dtype=np.float64)
+    lam_p = np.zeros((Np3, 3)) if lam_p is None else np.asarray(lam_p, dtype=np.float64)
     lam_psi1 = np.zeros((Np3, 3))
     lam_psi2 = np.zeros((Np3, 3))
     lam_phi1 = np.zeros_like(fields.phi1)
-    for bx in boxes:
+    for bx in state["boxes"]:
         g, sb = bx["g"], bx["sb"]
         keep = tiling.tile_interior_mask(cfg.Np, cfg.Ntiles, g.Nbuf)
         lam_s = np.zeros_like(bx["s"])
         lam_s[keep] = lam_x[bx["ids"][keep]]
-        lam_p = np.zeros_like(lam_s)
-        lp1 = np.zeros_like(lam_s)
-        lp2 = np.zeros_like(lam_s)
+        lam_p_res = np.zeros_like(lam_s)
+        lam_p_res[keep] = lam_p[bx["ids"][keep]]
+        c = bx["a_f"] ** 2 * cosmology.conformal_hubble(bx["a_f"], cfg.Om, cfg.OL)
+        lp1 = -c * sb["dD1da_f"] * lam_p_res
+        lp2 = c * sb["dD2da_f"] * lam_p_res
+        lam_pk = lam_p_res
         lam_shell = np.zeros((g.Ng + 2 * order,) * 3)
         for k in range(n, -1, -1):
             if k < n:
-                lam_p = lam_p + sb["alpha"][k] * lam_s
+                lam_pk = lam_pk + sb["alpha"][k] * lam_s
                 lp1 = lp1 - sb["dD1"][k] * lam_s
                 lp2 = lp2 + sb["dD2"][k] * lam_s
             b = sb["beta"][k]
             D1, D2 = sb["D1"][k], sb["D2"][k]
-            lam_F = b * lam_p
-            lp1 = lp1 - b * D1 * lam_p
-            lp2 = lp2 + b * (D2 - D1 * D1) * lam_p
+            lam_F = b * lam_pk
+            lp1 = lp1 - b * D1 * lam_pk
+            lp2 = lp2 + b * (D2 - D1 * D1) * lam_pk
             lx, lbc = box_force_vjp(bx["qloc"] + bx["ss"][k], g.dg, g.Ng, g.Nsc, D1 * bx["shell"], lam_F, order)
             lam_s = lam_s + lx
             lam_shell += D1 * lbc
@@ -315,5 +338,16 @@ def loss_and_grad(w, cfg, delta_target):
         lam_psi2[:] = 0.0          # Zel'dovich frame: Psi2 = 0 does not depend on the noise
     lam_delta = lpt_vjp(fields.delta, cfg.L, lam_phi1, lam_psi1.T.reshape(3, N, N, N),
                         lam_psi2.T.reshape(3, N, N, N), order)
-    lam_w = ics.initial_density(lam_delta, cfg.L, cfg.Om, cfg.h, cfg.ns, cfg.sigma8)
-    return value, lam_w
+    return ics.initial_density(lam_delta, cfg.L, cfg.Om, cfg.h, cfg.ns, cfg.sigma8)
+
+
+def loss_and_grad(w, cfg, delta_target):
+    """Lval(w) and dLval/dw for the final-density loss of one sCOLA run: the periodic CIC
+    adjoint of the final density (Sec. 4.1) gives lam_x, then ``final_state_vjp``."""
+    state = forward_with_checkpoints(w, cfg)
+    x = state["x"]
+    delta_f = stats.cic_density_periodic(x, cfg.L, cfg.Np, cfg.Np)
+    resid = delta_f - delta_target
+    value = float(np.sum(resid**2))
+    lam_x = periodic_density_vjp(x, cfg.L, cfg.Np, cfg.Np, 2.0 * resid)
+    return value, final_state_vjp(state, cfg, lam_x)

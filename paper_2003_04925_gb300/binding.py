@@ -94,7 +94,9 @@ _sig = {
     "scola_device_status": (c_int32, [c_void_p]),
     "scola_uses_tensor_cores": (c_int32, [c_void_p]),
     "scola_set_checkpointing": (c_int32, [c_void_p, c_int32]),
-    "scola_backward": (c_int32, [c_void_p, c_void_p, c_void_p]),
+    "scola_backward": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "scola_backward_density": (c_int32, [c_void_p, c_void_p, c_void_p]),
+    "scola_density_adjoint": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "scola_box_density_noalloc": (c_int32, [c_void_p, c_int32, c_int32, c_double, c_void_p, c_void_p]),
     "scola_box_offsets": (c_int32, [c_void_p, _P(c_int64), _P(c_int64), c_int32]),
     "scola_selftest_conversions": (c_int32, [c_int64, ctypes.c_uint64, _P(c_int64)]),
@@ -319,8 +321,16 @@ def scola_set_checkpointing(ctx, enable):
     _check(_lib.scola_set_checkpointing(ctx, 1 if enable else 0), "scola_set_checkpointing")
 
 
-def scola_backward(ctx, lam_delta, lam_w):
-    _check(_lib.scola_backward(ctx, _ptr(lam_delta), _ptr(lam_w)), "scola_backward")
+def scola_backward(ctx, lam_x, lam_p, lam_w):
+    _check(_lib.scola_backward(ctx, _ptr(lam_x), _ptr(lam_p), _ptr(lam_w)), "scola_backward")
+
+
+def scola_backward_density(ctx, lam_delta, lam_w):
+    _check(_lib.scola_backward_density(ctx, _ptr(lam_delta), _ptr(lam_w)), "scola_backward_density")
+
+
+def scola_density_adjoint(ctx, x, lam_delta, lam_x):
+    _check(_lib.scola_density_adjoint(ctx, _ptr(x), _ptr(lam_delta), _ptr(lam_x)), "scola_density_adjoint")
 
 
 def scola_box_density_noalloc(s, nsc, ng, dq, delta, stream=0):

@@ -1367,6 +1367,7 @@ scola_status scola_box_offsets(const scola_ctx *c, int64_t *m_off, int64_t *pp_o
 scola_status scola_lpt_fields(scola_ctx *c, const float *w, float *delta, float *phi1, float *phi2,
                               float *psi1, float *psi2) {
     if (!c || !w) return invalid("NULL context or white noise");
+    c->have_forward = false;            // the adjoint's LPT spectra are replaced
     CS(run_lpt(c, w, delta));
     const size_t n = sizeof(float) * (size_t)c->N3;
     if (phi1) CK(cudaMemcpyAsync(phi1, c->phi1, n, cudaMemcpyDeviceToDevice, c->stream));
@@ -1385,6 +1386,7 @@ scola_status scola_setup_boxes(scola_ctx *c) {
     }
     CS(autotune_deposit(c));
     CS(autotune_dst(c));
+    c->have_forward = false;            // the particle state of the last forward run is replaced
     CK(launch_box_init(*c));
     CK(launch_shell(*c));
     CK(launch_pad(*c, 1.0f));
@@ -1489,6 +1491,7 @@ scola_status scola_tcola(scola_ctx *c, const float *w, float *x, float *p) {
         return SCOLA_ERR_UNSUPPORTED;
     }
     const long long before = c->launches;
+    c->have_forward = false;            // the adjoint's LPT spectra are replaced
     CS(run_lpt(c, w, nullptr));
     c->tc_timed = false;
     CS(run_tcola(c, false));
@@ -1540,12 +1543,23 @@ scola_status scola_set_checkpointing(scola_ctx *c, int32_t enable) {
     return SCOLA_OK;
 }
 
-scola_status scola_backward(scola_ctx *c, const float *lam_delta, float *lam_w) {
-    if (!c || !lam_delta || !lam_w) return invalid("NULL argument");
+}  // extern "C"
+
+namespace {
+
+// The adjoint entry points need the checkpoints of a forward run made with checkpointing on,
+// and no later call that replaced the LPT fields or the box state.
+scola_status backward_ready(const scola_ctx *c) {
     if (!c->checkpointing || !c->have_forward) {
-        set_error("scola_backward needs checkpointing enabled before the forward run it differentiates");
+        set_error("the adjoint needs checkpointing enabled before the forward run it differentiates, "
+                  "and no scola_lpt_fields, scola_setup_boxes or scola_tcola call after that run");
         return SCOLA_ERR_STATE;
     }
+    return SCOLA_OK;
+}
+
+// Clears the backward accumulators; the caller then sets the tile particles' initial state.
+scola_status backward_clear(scola_ctx *c) {
     const long long P = c->P, N3 = c->N3;
     const size_t fb = sizeof(float);
     CK(cudaMemsetAsync(c->adj, 0, fb * 15 * P, c->stream));
@@ -1553,8 +1567,15 @@ scola_status scola_backward(scola_ctx *c, const float *lam_delta, float *lam_w) 
     CK(cudaMemsetAsync(c->lamPsi1, 0, fb * 3 * N3, c->stream));
     CK(cudaMemsetAsync(c->lamPsi2, 0, fb * 3 * N3, c->stream));
     CK(cudaMemsetAsync(c->lam_phi1, 0, fb * N3, c->stream));
-    // final density -> tile particles
-    CK(launch_adj_final(*c, lam_delta, c->adj));
+    return SCOLA_OK;
+}
+
+// The reverse sweep from the tile particles' adjoint state in c->adj to dLoss/dw: the KDK
+// sequence in reverse with the recomputed mesh force at each checkpoint, L-, the shell, 2LPT
+// and the colouring.
+scola_status reverse_sweep(scola_ctx *c, float *lam_w) {
+    const long long P = c->P, N3 = c->N3;
+    const size_t fb = sizeof(float);
     const int n = (int)c->tt.alpha.size();
     // with per-tile final scale factors every box takes its own factors of evaluation k from
     // the coefficient table (k is passed on); otherwise the uniform scalars
@@ -1595,6 +1616,33 @@ scola_status scola_backward(scola_ctx *c, const float *lam_delta, float *lam_w) 
     }
     CK(launch_adj_colour(*c, c->ck, c->ct));
     CF(cufftExecC2R(c->plan_c2r, c->ct, lam_w));
+    return SCOLA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+scola_status scola_backward(scola_ctx *c, const float *lam_x, const float *lam_p, float *lam_w) {
+    if (!c || !lam_w || (!lam_x && !lam_p)) return invalid("NULL argument (lam_w, or both lam_x and lam_p)");
+    CS(backward_ready(c));
+    CS(backward_clear(c));
+    CK(launch_adj_final_xp(*c, lam_x, lam_p, c->adj));
+    return reverse_sweep(c, lam_w);
+}
+
+scola_status scola_backward_density(scola_ctx *c, const float *lam_delta, float *lam_w) {
+    if (!c || !lam_delta || !lam_w) return invalid("NULL argument");
+    CS(backward_ready(c));
+    CS(backward_clear(c));
+    // final density -> tile particles
+    CK(launch_adj_final(*c, lam_delta, c->adj));
+    return reverse_sweep(c, lam_w);
+}
+
+scola_status scola_density_adjoint(scola_ctx *c, const float *x, const float *lam_delta, float *lam_x) {
+    if (!c || !x || !lam_delta || !lam_x) return invalid("NULL argument");
+    CK(launch_density_vjp(*c, x, lam_delta, lam_x));
     return SCOLA_OK;
 }
 

@@ -268,6 +268,10 @@ cudaError_t launch_true_pad(Ctx &c, const float *phi, float inv_D1);
 
 cudaError_t launch_adj_colour(Ctx &c, const cufftComplex *in, cufftComplex *out);
 cudaError_t launch_adj_final(Ctx &c, const float *lam_delta, float *adj);
+// tile particles' initial adjoint state from the cotangents of the global x and p (either null)
+cudaError_t launch_adj_final_xp(Ctx &c, const float *lam_x, const float *lam_p, float *adj);
+// the periodic CIC adjoint of the final density over the global positions
+cudaError_t launch_density_vjp(Ctx &c, const float *x, const float *lam_delta, float *lam_x);
 // k >= 0 with per-tile final scale factors: each box's factors of evaluation k (coef table)
 cudaError_t launch_adj_kick_drift(Ctx &c, float *adj, const KickDrift &kd, int k = -1);
 cudaError_t launch_adj_interp(Ctx &c, const float *s, float *adj, float *lamG, float D1, int k = -1);

@@ -1,5 +1,12 @@
-// Adjoint (vector-Jacobian products) of the sCOLA forward run, for the gradient of a
-// loss of the final density with respect to the white noise.
+// Adjoint (vector-Jacobian products) of the sCOLA forward run: the gradient of a loss of
+// the final positions and momenta (or of the final density) with respect to the white noise.
+//
+// Start of the reverse sweep, tile particles only (buffer particles leave no output):
+//   k_adj_final_xp  x = (q + s) mod L and p = p_res + c1 Psi1 + c2 Psi2 (L+, Eq. 55) give
+//                   lam_s = lam_x, lam_p = lam_p, lam_Psi1 = c1 lam_p, lam_Psi2 = c2 lam_p
+//   k_adj_final     lam_s = the periodic CIC adjoint of a final-density cotangent, from the
+//                   particle state (the density-loss entry point)
+//   k_density_vjp   the same periodic CIC adjoint over the global arrays: lam_x from x
 //
 // Per box particle the backward state is 5 rows of 3 x P floats (adj arena):
 //   lam_s (0..2), lam_p (3..5), lam_Psi1 (6..8), lam_Psi2 (9..11), lam_F (12..14).
@@ -86,6 +93,71 @@ k_adj_final(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
             }
 #pragma unroll
     for (int a = 0; a < 3; ++a) adj[a * P + gi] = lam[a] * inv_d;
+}
+
+// Final tile particles from the cotangents of the global outputs x and p (either may be
+// null = zero): the transposes of B.2's copy and of L+ (Eq. 55).
+__global__ void __launch_bounds__(kChunk)
+k_adj_final_xp(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks, long long P, int Np,
+               int Ntile, const float *__restrict__ lam_x, const float *__restrict__ lam_p, float c1, float c2,
+               const float *__restrict__ coefL, float *__restrict__ adj) {
+    const Chunk ch = chunks[blockIdx.x];
+    const BoxDesc &B = boxes[ch.box];
+    if (coefL) {                       // L+ at this tile's own final scale factor
+        c1 = coefL[2 * ch.box];
+        c2 = coefL[2 * ch.box + 1];
+    }
+    const int lt = ch.start + threadIdx.x;
+    if (lt >= Ntile * Ntile * Ntile) return;
+    int ti, tj, tk;
+    decode_local(lt, Ntile, ti, tj, tk);
+    const int Nsc = B.Nsc;
+    const long long gi = B.p_off + ((long long)(ti + B.Nbuf) * Nsc + (tj + B.Nbuf)) * Nsc + (tk + B.Nbuf);
+    const long long gid = ((long long)(B.tx * Ntile + ti) * Np + (B.ty * Ntile + tj)) * Np + (B.tz * Ntile + tk);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float lp = lam_p ? lam_p[gid * 3 + a] : 0.0f;
+        adj[a * P + gi] = lam_x ? lam_x[gid * 3 + a] : 0.0f;
+        adj[(3 + a) * P + gi] = lp;
+        adj[(6 + a) * P + gi] = c1 * lp;
+        adj[(9 + a) * P + gi] = c2 * lp;
+    }
+}
+
+// lam_x = d(periodic CIC density on the Np^3 grid)/dx^T lam_delta for every particle
+// (Sec. 4.1), from the global positions; the same arithmetic as k_adj_final.
+__global__ void k_density_vjp(const float *__restrict__ x, long long n, int Np, float inv_d,
+                              const float *__restrict__ lam_delta, float *__restrict__ lam_x) {
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+         idx += (long long)gridDim.x * blockDim.x) {
+        int i0[3];
+        float f[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float u = x[idx * 3 + a] * inv_d - 0.5f;
+            const float fl = floorf(u);
+            i0[a] = (int)fl;
+            f[a] = u - fl;
+        }
+        const long long NN = (long long)Np * Np;
+        float lam[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int dx = 0; dx < 2; ++dx)
+#pragma unroll
+            for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+                for (int dz = 0; dz < 2; ++dz) {
+                    const float wx = dx ? f[0] : 1.f - f[0], wy = dy ? f[1] : 1.f - f[1],
+                                wz = dz ? f[2] : 1.f - f[2];
+                    const float v = lam_delta[wrap(i0[0] + dx, Np) * NN + (long long)wrap(i0[1] + dy, Np) * Np +
+                                              wrap(i0[2] + dz, Np)];
+                    lam[0] += (dx ? 1.f : -1.f) * wy * wz * v;
+                    lam[1] += wx * (dy ? 1.f : -1.f) * wz * v;
+                    lam[2] += wx * wy * (dz ? 1.f : -1.f) * v;
+                }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) lam_x[idx * 3 + a] = lam[a] * inv_d;
+    }
 }
 
 __global__ void __launch_bounds__(kChunk)
@@ -403,6 +475,24 @@ cudaError_t launch_adj_final(Ctx &c, const float *lam_delta, float *adj) {
     const int Ntile = c.Np / c.Ntiles;
     k_adj_final<<<c.n_tchunks, kChunk, 0, c.stream>>>(c.boxes, c.tchunks, c.part, c.P, c.Np, Ntile,
                                                        (float)c.dq, (float)c.L, lam_delta, adj);
+    ++c.launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_final_xp(Ctx &c, const float *lam_x, const float *lam_p, float *adj) {
+    const int Ntile = c.Np / c.Ntiles;
+    const double af = c.prm.a_f;
+    const double pref = af * af * c.tt.Hconf_f;
+    k_adj_final_xp<<<c.n_tchunks, kChunk, 0, c.stream>>>(c.boxes, c.tchunks, c.P, c.Np, Ntile, lam_x, lam_p,
+                                                          (float)(-pref * c.tt.dD1da_f),
+                                                          (float)(pref * c.tt.dD2da_f), c.coefL, adj);
+    ++c.launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_density_vjp(Ctx &c, const float *x, const float *lam_delta, float *lam_x) {
+    k_density_vjp<<<grid_for(c.N3, 256), 256, 0, c.stream>>>(x, c.N3, c.Np, (float)((double)c.Np / c.L), lam_delta,
+                                                             lam_x);
     ++c.launches;
     return cudaGetLastError();
 }

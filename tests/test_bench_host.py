@@ -60,3 +60,15 @@ def test_stale_traffic_figures_are_nulled(tmp_path, monkeypatch):
     src.write_text("kernel source v2")
     assert bench.measured_traffic("w", "tc") == {"kick_drift": None, "deposit": None}
     assert bench.measured_traffic("missing", "tc") == {}
+
+
+def test_oracle_pool_times_whole_boxes_side_by_side():
+    # the CPU baseline: spawned single-threaded oracle processes, one box each per batch
+    pool = bench.OraclePool("plain_32", workers=2)
+    try:
+        work, sec = pool.run(2)
+        assert work == 2 * 24**3 * 10 and sec > 0
+        r = bench.oracle_sample_rate("plain_32", pool)
+        assert r["cores"] == 2 and r["value"] > 0 and r["kind"] == "oracle"
+    finally:
+        pool.close()

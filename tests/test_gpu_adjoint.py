@@ -43,7 +43,7 @@ def _gpu_loss_grad(sim, w_np, target):
     d = sim.final_density(x)
     t = torch.from_numpy(target.astype(np.float32)).cuda()
     lam = 2.0 * (d - t)
-    g = sim.backward(lam)
+    g = sim.backward_density(lam)
     torch.cuda.synchronize()
     dd = d.cpu().numpy().astype(np.float64)
     return float(np.sum((dd - target) ** 2)), g.cpu().numpy().astype(np.float64)
@@ -98,6 +98,100 @@ def test_backward_variants_match_fp64_oracle_adjoint(option):
         print("gradient vs FP64 oracle: %s seed %d rel %.3e" % (option, seed, rels[-1]))
     sim.close()
     assert np.median(rels) < 1e-3 and max(rels) < 5e-3, rels
+
+
+@pytest.mark.parametrize("variant", ["simt", "tc"])
+def test_backward_from_positions_and_momenta_matches_fp64_oracle(variant):
+    # The VJP of the whole run from dL/dx and dL/dp (Sec. 2.1 x = q + Psi, Eq. 55 L+) for the
+    # loss L = sum u.x + v.p with random weights, against the FP64 oracle's final_state_vjp
+    # (pinned by FP64 central differences).  Same kink argument and bounds as the density
+    # loss above; the momentum part is checked on its own too.
+    sc = _pkg()
+    kw = dict(L=48.0, Np=16, Ntiles=2, Nbuf=2, mesh_ratio=1, nsteps=3, a_i=0.05, a_f=1.0)
+    cfg = oracle_cfg(kw)
+    sim = _sim(kw, variant)
+    n = 16**3
+    u = synth_inputs.random_field((n, 3), 41)
+    v = synth_inputs.random_field((n, 3), 42)
+    ut = torch.from_numpy(u.astype(np.float32)).cuda()
+    vt = torch.from_numpy(v.astype(np.float32)).cuda()
+    rels, rels_p = [], []
+    for seed in (21, 23, 24):
+        w = synth_inputs.white_noise(16, seed)
+        sim.forward(torch.from_numpy(w).cuda())
+        g = sim.backward(ut, vt).cpu().numpy().astype(np.float64)
+        gp = sim.backward(None, vt).cpu().numpy().astype(np.float64)
+        torch.cuda.synchronize()
+        sc.scola_device_status(sim.ctx)
+        st = adjoint.forward_with_checkpoints(w.astype(np.float64), cfg)
+        g_o = adjoint.final_state_vjp(st, cfg, u, v)
+        gp_o = adjoint.final_state_vjp(st, cfg, np.zeros_like(u), v)
+        rels.append(np.linalg.norm(g - g_o) / np.linalg.norm(g_o))
+        rels_p.append(np.linalg.norm(gp - gp_o) / np.linalg.norm(gp_o))
+        print("x,p VJP vs FP64 oracle: %s seed %d rel %.3e (p only %.3e)" % (variant, seed, rels[-1], rels_p[-1]))
+    sim.close()
+    assert np.median(rels) < 1e-3 and max(rels) < 5e-3, rels
+    assert np.median(rels_p) < 1e-3 and max(rels_p) < 5e-3, rels_p
+
+
+def test_density_loss_is_the_composition_of_the_two_adjoints():
+    # scola_backward_density = scola_density_adjoint at the run's positions, then
+    # scola_backward from lam_x (FP32 atomics: equal up to the order of the additions).
+    kw = dict(L=48.0, Np=16, Ntiles=2, Nbuf=2, mesh_ratio=2, nsteps=3, a_i=0.05, a_f=1.0)
+    sim = _sim(kw, "tc")
+    target = torch.from_numpy(_target(kw, 22).astype(np.float32)).cuda()
+    x, _ = sim.forward(torch.from_numpy(synth_inputs.white_noise(16, 21)).cuda())
+    lam = 2.0 * (sim.final_density(x) - target)
+    g1 = sim.backward_density(lam)
+    g2 = sim.backward(sim.density_adjoint(x, lam))
+    torch.cuda.synchronize()
+    g1, g2 = g1.cpu().numpy(), g2.cpu().numpy()
+    np.testing.assert_allclose(g2, g1, rtol=1e-4, atol=1e-5 * np.abs(g1).max())
+    sim.close()
+
+
+def test_autograd_state_function_matches_backward():
+    sc = _pkg()
+    kw = dict(L=48.0, Np=16, Ntiles=2, Nbuf=2, mesh_ratio=1, nsteps=3, a_i=0.05, a_f=1.0)
+    sim = _sim(kw, "tc")
+    n = 16**3
+    u = torch.from_numpy(synth_inputs.random_field((n, 3), 41).astype(np.float32)).cuda()
+    v = torch.from_numpy(synth_inputs.random_field((n, 3), 42).astype(np.float32)).cuda()
+    w = torch.from_numpy(synth_inputs.white_noise(16, 21)).cuda().requires_grad_(True)
+    x, p = sc.ScolaState.apply(w, sim)
+    ((x * u).sum() + (p * v).sum()).backward()
+    sim.forward(w.detach())
+    g = sim.backward(u, v)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(w.grad.cpu().numpy(), g.cpu().numpy(), rtol=1e-4,
+                               atol=1e-6 * g.abs().max().item())
+    sim.close()
+
+
+def test_gradient_of_a_replaced_run_is_refused():
+    # A second forward pass on the same context between a differentiable pass and its
+    # backward replaces the checkpoints: the autograd functions raise instead of returning
+    # the other run's gradient, and the C entry points report STATE once the LPT fields or
+    # the box state have been replaced.
+    sc = _pkg()
+    kw = dict(L=48.0, Np=16, Ntiles=2, Nbuf=2, mesh_ratio=1, nsteps=3, a_i=0.05, a_f=1.0)
+    sim = _sim(kw, "simt")
+    w1 = torch.from_numpy(synth_inputs.white_noise(16, 21)).cuda().requires_grad_(True)
+    w2 = torch.from_numpy(synth_inputs.white_noise(16, 23)).cuda()
+    loss = (sc.ScolaDensity.apply(w1, sim) ** 2).sum()
+    sim.forward(w2)
+    with pytest.raises(RuntimeError, match="ran again"):
+        loss.backward()
+    x, p = sc.ScolaState.apply(w1, sim)
+    sim.forward(w2)
+    with pytest.raises(RuntimeError, match="ran again"):
+        (x.sum() + p.sum()).backward()
+    sim.forward(w2)
+    sim.lpt_fields(w2)
+    with pytest.raises(sc.ScolaError) as e:
+        sim.backward(torch.zeros(16**3, 3, device="cuda"))
+    assert e.value.status == 5          # SCOLA_ERR_STATE
+    sim.close()
 
 
 def test_autograd_function_matches_backward():

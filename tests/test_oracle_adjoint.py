@@ -111,3 +111,35 @@ def test_whole_loss_gradient_finite_differences(ratio, extra):
         d = synth_inputs.random_field(w.shape, seed)
         fd = _fd(f, w, d, 1e-6)
         assert abs(fd - np.sum(grad * d)) < 1e-5 * (abs(fd) + 1e-12), (fd, np.sum(grad * d))
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("extra", [{}, {"lpt_order": 1}, {"a_final": [1.0, 0.7, 0.5, 0.9, 0.8, 0.6, 0.95, 0.4]}])
+def test_final_state_vjp_finite_differences(extra):
+    # The VJP from the final positions and momenta (Sec. 2.1 x = q + Psi, Eq. 55 L+) to the
+    # white noise: a loss linear in x and p with random weights u, v against FP64 central
+    # differences.  x differences are taken modulo L so that no particle wraps across the
+    # periodic boundary between the two runs.  The forward sweep kept by the adjoint is the
+    # method's run itself, and lam_p = 0 reproduces the x-only chain of loss_and_grad.
+    cfg = scola.ScolaConfig(L=48.0, Np=12, Ntiles=2, Nbuf=2, mesh_ratio=1, nsteps=2, a_i=0.05, **extra)
+    w = synth_inputs.white_noise(12, 21).astype(np.float64)
+    st = adjoint.forward_with_checkpoints(w, cfg)
+    run = scola.run_scola(w, cfg)
+    assert np.array_equal(st["x"], run["x"]) and np.abs(st["p"] - run["p"]).max() < 1e-12 * np.abs(run["p"]).max()
+    u = synth_inputs.random_field((cfg.Np**3, 3), 31)
+    v = synth_inputs.random_field((cfg.Np**3, 3), 32)
+    grad = adjoint.final_state_vjp(st, cfg, u, v)
+    grad_x = adjoint.final_state_vjp(st, cfg, u)
+    grad_p = adjoint.final_state_vjp(st, cfg, np.zeros_like(u), v)
+    np.testing.assert_allclose(grad, grad_x + grad_p, rtol=1e-12, atol=1e-14 * np.abs(grad).max())
+    for seed in (33, 34):
+        d = synth_inputs.random_field(w.shape, seed)
+        eps = 1e-6
+        rp, rm = scola.run_scola(w + eps * d, cfg), scola.run_scola(w - eps * d, cfg)
+        dx = rp["x"] - rm["x"]
+        dx -= cfg.L * np.round(dx / cfg.L)
+        fd = (np.sum(u * dx) + np.sum(v * (rp["p"] - rm["p"]))) / (2 * eps)
+        assert abs(fd - np.sum(grad * d)) < 1e-5 * abs(fd), (fd, np.sum(grad * d))
+        # the momentum part alone (it reaches the noise through p_res and the L+ term)
+        fdp = np.sum(v * (rp["p"] - rm["p"])) / (2 * eps)
+        assert abs(fdp - np.sum(grad_p * d)) < 1e-5 * abs(fdp), (fdp, np.sum(grad_p * d))
