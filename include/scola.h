@@ -386,13 +386,30 @@ scola_status scola_tcola_kernel_times(const scola_ctx *ctx, double *ms_per_launc
 
 /*
  * Synchronises the stream and reports whether a kernel gave up on a bounded
- * wait since the context was created: SCOLA_OK, or SCOLA_ERR_TIMEOUT (results
- * of the affected launch are invalid; the context stays usable), or
- * SCOLA_ERR_CUDA when the sorted deposit's fill pass found more particles for a
- * key than its count pass (nothing is written past the slot range; the
- * densities of that launch are invalid).
+ * wait since the context was created or since the last call that reported one:
+ * SCOLA_OK, or SCOLA_ERR_TIMEOUT (results of the affected launch are invalid;
+ * the context stays usable), or SCOLA_ERR_CUDA when the sorted deposit's fill
+ * pass found more particles for a key than its count pass (nothing is written
+ * past the slot range; the densities of that launch are invalid).  A reported
+ * condition is cleared.
  */
 scola_status scola_device_status(scola_ctx *ctx);
+
+/*
+ * Failure-detection self-test (the paper has no counterpart).  Runs one tensor-core DST
+ * pass over the context's scratch meshes in which the thread that issues the tensor-core
+ * instructions first waits, for wait_seconds, on a barrier that nothing arrives on.  The
+ * wait expires, the CTA raises the device error flag, its other roles leave their loops at
+ * their next bounded wait, the tensor copies already issued drain (those waits keep their
+ * normal 2 s limit), tensor memory is freed and the kernel returns: nothing faults or hangs.
+ * Synchronous.  Returns SCOLA_ERR_TIMEOUT when the wait expired as designed (the flag is
+ * then cleared, see scola_device_status); the context stays usable and its next forward
+ * run is unaffected (the pass wrote only scratch meshes).
+ *   wait_seconds  0 < wait_seconds <= 2
+ * Errors: INVALID_ARG, UNSUPPORTED (no tensor-core DST, or more than one batch), STATE (no
+ * forward run or box set-up yet), CUDA.
+ */
+scola_status scola_selftest_wait_timeout(scola_ctx *ctx, double wait_seconds);
 
 /* 1 when the context's Poisson solve runs on the tensor cores, else 0 (under
  * SCOLA_DST_AUTO: the autotuner's pick once the first scola_forward or

@@ -15,7 +15,7 @@ from .binding import (  # noqa: F401
     scola_backward, scola_backward_density, scola_box_density_noalloc, scola_box_mass, scola_box_offsets, scola_box_particle_count, scola_box_particle_ids,
     scola_create, scola_density_adjoint, scola_destroy, scola_device_status, scola_final_density, scola_forward,
     scola_forward_host, scola_generate_white_noise, scola_get_stats, scola_kernel_times, scola_last_error, scola_lpt_fields,
-    scola_mesh_cell_count, scola_padded_cell_count, scola_pm_force, scola_power_spectrum, scola_selftest_conversions,
+    scola_mesh_cell_count, scola_padded_cell_count, scola_pm_force, scola_power_spectrum, scola_selftest_conversions, scola_selftest_wait_timeout,
     scola_set_checkpointing, scola_set_profiling, scola_shard_ranges, scola_setup_boxes, scola_status_string,
     scola_tcola, scola_tcola_kernel_times, TCOLA_STAGES, scola_tiling_info, scola_time_table, scola_uses_tensor_cores,
 )

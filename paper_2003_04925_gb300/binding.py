@@ -96,6 +96,7 @@ _sig = {
     "scola_set_checkpointing": (c_int32, [c_void_p, c_int32]),
     "scola_backward": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "scola_backward_density": (c_int32, [c_void_p, c_void_p, c_void_p]),
+    "scola_selftest_wait_timeout": (c_int32, [c_void_p, c_double]),
     "scola_density_adjoint": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "scola_box_density_noalloc": (c_int32, [c_void_p, c_int32, c_int32, c_double, c_void_p, c_void_p]),
     "scola_box_offsets": (c_int32, [c_void_p, _P(c_int64), _P(c_int64), c_int32]),
@@ -323,6 +324,10 @@ def scola_set_checkpointing(ctx, enable):
 
 def scola_backward(ctx, lam_x, lam_p, lam_w):
     _check(_lib.scola_backward(ctx, _ptr(lam_x), _ptr(lam_p), _ptr(lam_w)), "scola_backward")
+
+
+def scola_selftest_wait_timeout(ctx, wait_seconds):
+    _check(_lib.scola_selftest_wait_timeout(ctx, float(wait_seconds)), "scola_selftest_wait_timeout")
 
 
 def scola_backward_density(ctx, lam_delta, lam_w):

@@ -81,7 +81,10 @@ struct scola_ctx : public Ctx {
 
 namespace {
 
-constexpr int kMaxNg = 192;  // the DST passes hold a (Ng x 32 ceil(Ng/32)) sine matrix in shared memory
+// the FP32 DST passes hold a (Ng x 32 ceil(Ng/32)) sine matrix and a column tile in shared
+// memory (at most 227 KB: Ng <= 222); the tensor-core passes take Ng <= 256
+constexpr int kMaxNgSimt = 222;
+constexpr int kMaxNg = 256;
 
 scola_status invalid(const std::string &m) {
     set_error(m);
@@ -143,13 +146,14 @@ scola_status validate(const scola_params *p, std::vector<int32_t> &bufs, std::ve
         if (nsc > p->Np) return invalid("Np,sCOLA must not exceed Np (a box may not overlap itself)");
         const int ng = p->Ng ? p->Ng : p->mesh_ratio * nsc;
         if (ng < nsc) return invalid("Ng must be >= Np,sCOLA (Sec. 3.3, C.3)");
-        if (for_kernels && ng > kMaxNg) {
-            set_error("Ng > 192 is not built");
+        const bool tc_form = p->dst_variant == SCOLA_DST_TC_3XTF32 || p->dst_variant == SCOLA_DST_TC_4XTF32 ||
+                             p->dst_variant == SCOLA_DST_AUTO;
+        if (for_kernels && (ng > kMaxNg || (!tc_form && ng > kMaxNgSimt))) {
+            set_error("Ng > 256 is not built (Ng > 222 only with a tensor-core DST form)");
             return SCOLA_ERR_UNSUPPORTED;
         }
-        if (for_kernels && (p->dst_variant == SCOLA_DST_TC_3XTF32 || p->dst_variant == SCOLA_DST_TC_4XTF32) &&
-            !tc_supported(ng)) {
-            set_error("the tensor-core DST needs Ng % 4 == 0 and Ng <= 128, or Ng % 32 == 0 and Ng <= 256");
+        if (for_kernels && tc_form && !tc_supported(ng)) {
+            set_error("the tensor-core DST needs 2 <= Ng <= 256");
             return SCOLA_ERR_UNSUPPORTED;
         }
         geo[b] = {nsc, ng, bufs[b]};
@@ -609,8 +613,10 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &all_geo) {
     for (auto &kv : c->tbl_of) all_tc = all_tc && tc_supported(kv.first);
     // AUTO: both forms are set up where every Ng allows the tensor-core form, and the
     // autotuner keeps the faster (autotune_dst); the FP32 form otherwise
-    c->dst_auto = p.dst_variant == SCOLA_DST_AUTO && all_tc;
-    c->use_tc = (p.dst_variant == SCOLA_DST_TC_3XTF32) || (p.dst_variant == SCOLA_DST_TC_4XTF32) || c->dst_auto;
+    // (a mesh larger than the FP32 form takes leaves the tensor-core form alone)
+    c->dst_auto = p.dst_variant == SCOLA_DST_AUTO && all_tc && c->max_ng <= kMaxNgSimt;
+    c->use_tc = (p.dst_variant == SCOLA_DST_TC_3XTF32) || (p.dst_variant == SCOLA_DST_TC_4XTF32) ||
+                (p.dst_variant == SCOLA_DST_AUTO && all_tc);
     c->tc_lo_lo = p.dst_variant == SCOLA_DST_TC_4XTF32;
     if (c->use_tc) {
         for (auto &kv : c->tbl_of) {
@@ -622,18 +628,22 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &all_geo) {
             G.tiles = nullptr;
             G.ntiles = 0;
             // direct: S_nk for n, k < Ng; folded: the even-row (output 2n) and then the
-            // odd-row (output 2n + 1) halves S_{2n+p, k} for n, k < Ng / 2
+            // odd-row (output 2n + 1) halves S_{2n+p, k} for n, k < ceil(Ng / 2) (even) or
+            // floor(Ng / 2) (odd).  For odd Ng the even outputs' column k = (Ng - 1) / 2 (the
+            // middle element, which the kernel pairs with itself: x_mid + x_mid) is halved
             const int Kp = 32 * G.nkc;
             const bool fold = tc_folded(G.Ng);
-            const int Nk = fold ? G.Ng / 2 : G.Ng;
-            for (int par = 0; par < (fold ? 2 : 1); ++par)
+            for (int par = 0; par < (fold ? 2 : 1); ++par) {
+                const int Nk = fold ? (par ? G.Ng / 2 : (G.Ng + 1) / 2) : G.Ng;
                 for (int n = 0; n < G.Npad; ++n)
                     for (int k = 0; k < Kp; ++k) {
                         const int row = fold ? 2 * n + par : n;
+                        const double half = (fold && par == 0 && (G.Ng & 1) && k == G.Ng / 2) ? 0.5 : 1.0;
                         arena.push_back(n < Nk && k < Nk
-                                            ? (float)std::sin(M_PI * (double)(row + 1) * (k + 1) / (G.Ng + 1))
+                                            ? (float)(half * std::sin(M_PI * (double)(row + 1) * (k + 1) / (G.Ng + 1)))
                                             : 0.0f);
                     }
+            }
             c->tc_groups.push_back(G);
         }
     }
@@ -768,7 +778,7 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &all_geo) {
     }
     CS(bind_batch(c, 0, true));
 
-    CK(init_pm_kernels(*c));
+    if (!c->use_tc || c->dst_auto) CK(init_pm_kernels(*c));     // the FP32 DST passes
     CK(init_deposit_kernels());
     for (int i = 0; i < 4; ++i) CK(cudaEventCreate(&c->ev[i]));
     for (int i = 0; i < 2; ++i) CK(cudaEventCreate(&c->tc_ev[i]));
@@ -1730,6 +1740,7 @@ scola_status scola_device_status(scola_ctx *c) {
     CK(c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize());
     int flag = 0;
     CK(cudaMemcpy(&flag, c->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) CK(cudaMemset(c->dev_err, 0, sizeof(int)));     // reported once
     if (flag & 1) {
         set_error("a kernel's bounded wait expired; its results are invalid");
         return SCOLA_ERR_TIMEOUT;
@@ -1740,6 +1751,25 @@ scola_status scola_device_status(scola_ctx *c) {
         return SCOLA_ERR_CUDA;
     }
     return SCOLA_OK;
+}
+
+scola_status scola_selftest_wait_timeout(scola_ctx *c, double wait_seconds) {
+    if (!c || !(wait_seconds > 0.0) || wait_seconds > 2.0) return invalid("NULL context or wait outside (0, 2] s");
+    CS(need_one_batch(c));
+    if (!c->use_tc) {
+        set_error("the context does not use the tensor-core DST");
+        return SCOLA_ERR_UNSUPPORTED;
+    }
+    if (!c->setup_done) {
+        set_error("scola_selftest_wait_timeout needs a forward run or scola_setup_boxes first");
+        return SCOLA_ERR_STATE;
+    }
+    CS(scola_device_status(c));                                // nothing pending before the test
+    c->tc_stall_ns = (unsigned long long)(wait_seconds * 1e9);
+    const cudaError_t e = launch_poisson_tc_pass(*c, 0);       // work2 -> work: scratch meshes only
+    c->tc_stall_ns = 0;
+    CK(e);
+    return scola_device_status(c);
 }
 
 int32_t scola_uses_tensor_cores(const scola_ctx *c) { return c && c->use_tc ? 1 : 0; }

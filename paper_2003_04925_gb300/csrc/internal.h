@@ -134,6 +134,7 @@ struct Ctx {
     bool use_tc = false;                              // tensor-core (3xTF32) DST passes
     bool dst_auto = false, dst_tuned = false;         // SCOLA_DST_AUTO: the autotuner picks use_tc
     bool tc_lo_lo = false;                            // four-product TF32 form
+    unsigned long long tc_stall_ns = 0;               // > 0 only inside scola_selftest_wait_timeout
     std::vector<TcGroup> tc_groups;
     Chunk *tc_tiles = nullptr;
     std::vector<int> tc_tile_beg, tc_tile_end;        // each box's tile range in tc_tiles
@@ -227,6 +228,7 @@ cudaError_t init_deposit_kernels();
 int tc_plan_stages(int Ng, int &Npad, int &nkc);
 bool tc_supported(int Ng);
 bool tc_folded(int Ng);          // Ng > 128: the mirror-symmetric half-size form
+bool tc_ragged(int Ng);          // rows not 16-byte pitched for TMA: plain loads and stores
 cudaError_t init_tc_kernels();
 cudaError_t launch_poisson_tc(Ctx &c);
 cudaError_t launch_poisson_tc_pass(Ctx &c, int pass);

@@ -24,11 +24,20 @@
 // s_lo x_lo as well in the four-product form.  A single TF32 product gives position
 // errors of ~0.1 PM cell over a run, the three-term form stays near the FP32 level.
 //
-// Meshes with Ng > 128 (Ng % 32 == 0) use the mirror symmetry of the sine matrix,
+// Any Ng up to 256.  Meshes whose rows are 16-byte pitched (Ng % 4 == 0; folded: Ng % 32 == 0)
+// reach the stages by TMA.  Other meshes (the paper's own geometry, Ng = Np,sCOLA + 1, Sec. 4
+// Table 1) take the "ragged" path: the converter warps read each chunk from global memory with
+// plain coalesced loads (rows beyond the box and columns beyond Ng read as zero) and write the
+// split straight into the stage, and the epilogue stores element by element.
+//
+// Meshes with Ng > 128 use the mirror symmetry of the sine matrix,
 // S_{k, Ng-1-n} = (-1)^k S_kn: the even outputs are the half-size product of the even rows
 // of S with u_n = x_n + x_{Ng-1-n}, the odd outputs that of the odd rows with
-// v_n = x_n - x_{Ng-1-n} (n < Ng/2).  Each work item is one parity of one tile: the CTA
-// holds that parity's Ng/2 x Ng/2 matrix (its M rows and K both Ng/2 <= 128), loads
+// v_n = x_n - x_{Ng-1-n} (n < Ng/2).  For odd Ng the middle element pairs with itself: u
+// takes 2 x_mid there, so the even-parity matrix holds half of that column, and the odd
+// outputs do not see it (their sine vanishes there).  Each work item is one parity of one
+// tile: the CTA holds that parity's matrix (ceil(Ng/2) rows and columns for the even outputs,
+// floor(Ng/2) for the odd ones, at most 128), loads
 // every 16-column chunk of the rows together with its mirror chunk, and its converters
 // form u or v and split it into hi and lo parts in place of the two loaded chunks.  Half
 // the products of the direct form, and the two
@@ -52,6 +61,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <cstring>
 #include <map>
 #include <mutex>
 #include <utility>
@@ -101,6 +111,9 @@ struct TcArgs {
     float *out;
     int *err;
     int lo_lo;                   // 1: also accumulate a_lo s_lo (four TF32 products)
+    int ragged;                  // 1: rows not 16-byte pitched; plain loads and stores (no TMA)
+    unsigned long long stall_ns; // failure-detection self-test: > 0 makes the MMA thread first wait
+                                 // this long on a barrier nothing arrives on, then abort
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -265,7 +278,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(const __grid_constant__ 
     // folded: this CTA's parity (the grid is even, so item b + k grid keeps the parity of b),
     // and the contraction length and matrix rows Nk = Ng / 2
     const int parity = FOLD ? (int)(blockIdx.x & 1) : 0;
-    const int Nk = FOLD ? Ng / 2 : Ng;
+    const int Nk = FOLD ? (parity ? Ng / 2 : (Ng + 1) / 2) : Ng;
     const int nkb = (Nk + kKB - 1) / kKB;                 // data chunks per tile
     const uint32_t sch = (uint32_t)((Nk + 7) / 8) * 1024; // one sine chunk (hi or lo), Nk rows
     // The M = 128 operand reads 128 rows from each sine chunk; rows >= Ng come from what
@@ -357,12 +370,57 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(const __grid_constant__ 
         const float sgn = parity ? -1.0f : 1.0f;
         for (long long h = 0; h < nchunks && !*abort_flag; ++h) {
             const int s = (int)(h % NST);
+            unsigned char *xh = stages + (size_t)s * kStageBytes;
+            unsigned char *xl = stages + (size_t)s * kStageBytes + kHalfBytes;
+            if (A.ragged) {
+                // the stage is free once the MMA has consumed the chunk before in it; then
+                // element (r, k) of the chunk (row r of the tile, column 16 cc + k) is read
+                // by thread idx % 256 of idx = 16 r + k (a half warp reads 64 contiguous
+                // bytes), split and stored in both halves (folded: x + sgn x_mirror first)
+                if (!mbar_wait(&empty[s], (uint32_t)(((h / NST) & 1) ^ 1), abort_flag)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                const TileInfo ti = tile_at(h / nkb);
+                const int cc = (int)(h % nkb);
+                const float *src = A.in + ti.m_off + (long long)ti.row0 * Ng;
+                const int nrows = (int)min((long long)kTN, Ng2 - ti.row0);
+                if (cc == 0 && pt == 0 && h / nkb + 1 < my_tiles) {
+                    // the next tile's rows are one contiguous block: start bringing it into L2
+                    const TileInfo tn = tile_at(h / nkb + 1);
+                    const long long rows = min((long long)kTN, Ng2 - tn.row0);
+                    const uint32_t bytes = (uint32_t)(rows * Ng * sizeof(float)) & ~15u;
+                    if (bytes) prefetch_l2(A.in + tn.m_off + (long long)tn.row0 * Ng, bytes);
+                }
+                float v[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int idx = pt + kProducers * i;
+                    const int r = idx >> 4, col = cc * kKB + (idx & 15);
+                    float x = 0.0f;
+                    if (r < nrows) {
+                        const float *row = src + (long long)r * Ng;
+                        if (col < Ng) x = row[col];
+                        if (FOLD && Ng - 1 - col >= 0) x = fmaf(sgn, row[Ng - 1 - col], x);
+                    }
+                    v[i] = x;
+                }
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int idx = pt + kProducers * i;
+                    const uint32_t off = sw64_offset(idx >> 4, idx & 15);
+                    const float hi = tf32_rn(v[i]);
+                    *(float *)(xh + off) = hi;
+                    *(float *)(xl + off) = tf32_rn(v[i] - hi);
+                }
+                fence_proxy_async();
+                mbar_arrive(&full[s]);
+                continue;
+            }
             if (!mbar_wait(&loaded[s], (uint32_t)((h / NST) & 1), abort_flag)) {
                 *abort_flag = 1;
                 break;
             }
-            unsigned char *xh = stages + (size_t)s * kStageBytes;
-            unsigned char *xl = stages + (size_t)s * kStageBytes + kHalfBytes;
             if (FOLD) {
                 // half 0 holds columns n of the chunk, half 1 the mirror chunk (column 15 - k
                 // there pairs with column k here); the row becomes w = x + sgn x_mirror, split
@@ -404,8 +462,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(const __grid_constant__ 
     } else if (warp == 17) {
         // ---------------------------------------------------------------- tensor copies
         // lane 0 loads chunk g into stage g % NST as soon as the MMA has released it; on an
-        // abort it waits (bounded) for the copies it issued before the CTA may exit
-        if (lane == 0) {
+        // abort it waits (bounded) for the copies it issued before the CTA may exit.  Idle on
+        // the ragged path (the converters load the chunks themselves)
+        if (lane == 0 && !A.ragged) {
             long long g = 0;
             for (; g < nchunks && !*abort_flag; ++g) {
                 const int s = (int)(g % NST);
@@ -436,6 +495,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(const __grid_constant__ 
         }
     } else if (warp == 16) {
         // ---------------------------------------------------------------- MMA issuer
+        if (lane == 0 && A.stall_ns) {
+            // self-test of the failure path: the drain barrier receives nothing before the
+            // tear-down, so this bounded wait expires and the CTA aborts like any timeout
+            const unsigned long long t0 = now_ns();
+            while (!mbar_try_wait(drain, 0) && now_ns() - t0 < A.stall_ns) {
+            }
+            *abort_flag = 1;
+        }
         if (lane == 0) {
             const uint32_t idesc = idesc_tf32(kTM, kTN);
             const uint32_t shi = smem_u32(S_hi), slo = smem_u32(S_lo), st0 = smem_u32(stages);
@@ -530,7 +597,33 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(const __grid_constant__ 
                 // eight lanes cover 32 consecutive rows (128 bytes) of one column
                 const int ru = lane & 7, cg = lane >> 3;
                 const long long R = (long long)ti.row0 + half * 128 + rnd * 32 + 4 * ru;
-                if (R < Ng2) {
+                if (A.ragged && R < Ng2) {
+                    // element by element: rows R .. R + 3 may cross a row of the mesh or the
+                    // end of the box, and nothing is 16-byte aligned
+#pragma unroll 1
+                    for (int c = 0; c < 8; ++c) {
+                        const int nl = cg * 8 + c;
+                        if (nl >= ncol) break;
+                        const int nout = FOLD ? 2 * (n0 + nl) + parity : n0 + nl;
+                        const float4 x4 = reinterpret_cast<const float4 *>(buf + nl * 32)[ru ^ (nl & 7)];
+                        const float xv[4] = {x4.x, x4.y, x4.z, x4.w};
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const long long row = R + e;
+                            if (row >= Ng2) break;
+                            const int rhi = (int)(row / Ng), rlo = (int)(row - (long long)rhi * Ng);
+                            if (PASS == P_XI) {
+                                const int G = ti.pad;
+                                const long long S = Ng + 2 * G;
+                                A.out[ti.pp_off + ((long long)(nout + G) * S + (rhi + G)) * S + (rlo + G)] = xv[e] * scale;
+                            } else {
+                                float y = xv[e];
+                                if (PASS == P_XF) y = __fdividef(y, lam[nout] + lam[rhi] + lam[rlo]);
+                                A.out[ti.m_off + (long long)nout * Ng2 + row] = y;
+                            }
+                        }
+                    }
+                } else if (R < Ng2) {
                     const int rhi = (int)(R / Ng), rlo = (int)(R - (long long)(R / Ng) * Ng);
                     float4 lr;
                     if (PASS == P_XF)
@@ -630,8 +723,12 @@ cudaError_t input_map(Ctx &c, const float *buf, int Ng, CUtensorMap *out) {
 template <int PASS>
 cudaError_t run_tc_pass(Ctx &c, const TcGroup &G, const float *in, float *out) {
     TcArgs a;
-    cudaError_t me = input_map(c, in, G.Ng, &a.in_map);
-    if (me != cudaSuccess) return me;
+    std::memset(&a, 0, sizeof(a));
+    a.ragged = tc_ragged(G.Ng) ? 1 : 0;
+    if (!a.ragged) {
+        cudaError_t me = input_map(c, in, G.Ng, &a.in_map);
+        if (me != cudaSuccess) return me;
+    }
     const bool fold = tc_folded(G.Ng);
     a.boxes = c.boxes;
     a.tiles = G.tiles;
@@ -646,7 +743,8 @@ cudaError_t run_tc_pass(Ctx &c, const TcGroup &G, const float *in, float *out) {
     a.out = out;
     a.err = c.dev_err;
     a.lo_lo = c.tc_lo_lo ? 1 : 0;
-    const size_t smem = tc_smem_bytes(fold ? G.Ng / 2 : G.Ng, G.Ng, G.nkc, G.nstage);
+    a.stall_ns = c.tc_stall_ns;
+    const size_t smem = tc_smem_bytes(fold ? (G.Ng + 1) / 2 : G.Ng, G.Ng, G.nkc, G.nstage);
     if (fold) {
         // an even grid keeps each CTA on one parity (item b + k grid has the parity of b)
         const int grid = std::max(2, std::min(a.ntiles, c.num_sms) & ~1);
@@ -663,9 +761,11 @@ cudaError_t run_tc_pass(Ctx &c, const TcGroup &G, const float *in, float *out) {
 
 bool tc_folded(int Ng) { return Ng > kTM; }
 
+bool tc_ragged(int Ng) { return tc_folded(Ng) ? Ng % 32 != 0 : Ng % 4 != 0; }
+
 int tc_plan_stages(int Ng, int &Npad, int &nkc) {
     // as many data stages (up to 4) as fit next to the resident sine matrix, at least 2
-    const int Nk = tc_folded(Ng) ? Ng / 2 : Ng;
+    const int Nk = tc_folded(Ng) ? (Ng + 1) / 2 : Ng;
     Npad = ((Nk + 15) / 16) * 16;
     nkc = (Nk + kKA - 1) / kKA;
     for (int nst = 4; nst >= 2; --nst)
@@ -675,10 +775,8 @@ int tc_plan_stages(int Ng, int &Npad, int &nkc) {
 
 bool tc_supported(int Ng) {
     int Npad, nkc;
-    // direct form: Ng <= 128 (one M = 128 operand), rows of 16-byte units; folded form:
-    // Ng / 2 <= 128 and a multiple of 16 (whole 16-column chunks and their mirrors)
-    const bool shape = tc_folded(Ng) ? (Ng <= 2 * kTM && Ng % 32 == 0) : (Ng >= 4 && Ng % 4 == 0);
-    return shape && tc_plan_stages(Ng, Npad, nkc) >= 2;
+    // direct form: Ng <= 128 (one M = 128 operand); folded form: ceil(Ng / 2) <= 128
+    return Ng >= 2 && Ng <= 2 * kTM && tc_plan_stages(Ng, Npad, nkc) >= 2;
 }
 
 template <int PASS>

@@ -420,6 +420,9 @@ cudaError_t init_pm_kernels(Ctx &c) {
         case 4: e = set_attrs_R<4>(); c.dst_ctas_per_sm = ctas_per_sm_R<4>(c.max_ng); break;
         case 5: e = set_attrs_R<5>(); c.dst_ctas_per_sm = ctas_per_sm_R<5>(c.max_ng); break;
         case 6: e = set_attrs_R<6>(); c.dst_ctas_per_sm = ctas_per_sm_R<6>(c.max_ng); break;
+        case 7:
+            if (dst_smem_bytes(7, c.max_ng) > 227 * 1024) return cudaErrorInvalidValue;
+            e = set_attrs_R<7>(); c.dst_ctas_per_sm = ctas_per_sm_R<7>(c.max_ng); break;
         default: return cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return e;
@@ -436,6 +439,7 @@ cudaError_t launch_poisson_buffers(Ctx &c, const float *in, float *w1, float *w2
         case 4: return poisson_R<4>(c, in, w1, w2, out_pad);
         case 5: return poisson_R<5>(c, in, w1, w2, out_pad);
         case 6: return poisson_R<6>(c, in, w1, w2, out_pad);
+        case 7: return poisson_R<7>(c, in, w1, w2, out_pad);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -461,6 +465,7 @@ cudaError_t launch_poisson_pass(Ctx &c, int pass) {
         SCOLA_PASS_CASES(4)
         SCOLA_PASS_CASES(5)
         SCOLA_PASS_CASES(6)
+        SCOLA_PASS_CASES(7)
 #undef SCOLA_PASS_CASES
         default: return cudaErrorInvalidValue;
     }
