@@ -123,8 +123,8 @@ typedef enum scola_batch_mode {
  *                host-copy buffers of scola_forward_host) plus 1 GiB; the batch count
  *                is then raised to a divisor of the box count where batches stay at
  *                least half full.  A context with more than one batch runs
- *                scola_forward, scola_forward_host, scola_final_density and the
- *                host-only calls; the per-stage, inspection and adjoint calls need
+ *                scola_forward, scola_forward_host, scola_final_density, the adjoint
+ *                calls and the host-only calls; the per-stage and inspection calls need
  *                one batch (they return UNSUPPORTED otherwise)
  *   time_stepping one of scola_time_stepping
  *   a_final      optional per-tile final scale factors (host array of Ntiles^3, box-id
@@ -417,14 +417,34 @@ scola_status scola_selftest_wait_timeout(scola_ctx *ctx, double wait_seconds);
 int32_t scola_uses_tensor_cores(const scola_ctx *ctx);
 
 /*
- * Adjoint support.  With checkpointing enabled, scola_forward also stores the
- * displacements of every box particle at every force evaluation (the
- * per-step checkpoints: (nsteps + 1) x 3 x P floats) and the context keeps
- * the adjoint work arrays.  Batched form, FDA order 2, no study mode and one batch
- * only (UNSUPPORTED otherwise); 2LPT or Zel'dovich frame, modified or standard KDK
- * factors, common or per-tile final scale factors.  Synchronises the stream.
+ * Adjoint support.  With checkpointing enabled, scola_forward also stores checkpoints of
+ * every box particle's state (see scola_set_checkpoint_interval) and the context keeps the
+ * adjoint work arrays.  Batched form, FDA order 2, no study mode (UNSUPPORTED otherwise);
+ * 2LPT or Zel'dovich frame, modified or standard KDK factors, common or per-tile final scale
+ * factors, one or several streamed batches.  Synchronises the stream.
  */
 scola_status scola_set_checkpointing(scola_ctx *ctx, int32_t enable);
+
+/*
+ * How often the forward run checkpoints the particle state for the adjoint (the paper has no
+ * counterpart; it keeps long differentiated runs within device memory).  With n force
+ * evaluations (nsteps + 1) and P box particles per batch:
+ *   every = 1   every evaluation keeps the displacements: 3 n P floats, no recomputation;
+ *   every = m   every m-th evaluation keeps displacements and momenta, 6 ceil(n / m) P floats,
+ *               plus 3 m P for one replayed segment and 6 P for the final state: the reverse
+ *               sweep replays each segment of m evaluations forward from its checkpoint (the
+ *               same deterministic kernels, so the same trajectory and the same gradient) at
+ *               the cost of one more forward pass;
+ *   every = 0   the m that needs the fewest floats (about sqrt(2 n)).
+ * With several streamed batches the backward pass replays each batch's evolution from C.1
+ * to rebuild its checkpoints (one more forward pass).  The default is 1.  Changing the
+ * interval drops any stored checkpoints (the next backward needs a new forward run).
+ * Synchronises the stream.  Errors: INVALID_ARG (NULL, every < 0), OOM, CUDA.
+ */
+scola_status scola_set_checkpoint_interval(scola_ctx *ctx, int32_t every);
+
+/* The checkpoint interval in use (1 by default). */
+int32_t scola_checkpoint_interval(const scola_ctx *ctx);
 
 /*
  * Vector-Jacobian product of the whole forward run: the gradient, with respect to the white

@@ -97,6 +97,8 @@ _sig = {
     "scola_backward": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "scola_backward_density": (c_int32, [c_void_p, c_void_p, c_void_p]),
     "scola_selftest_wait_timeout": (c_int32, [c_void_p, c_double]),
+    "scola_set_checkpoint_interval": (c_int32, [c_void_p, c_int32]),
+    "scola_checkpoint_interval": (c_int32, [c_void_p]),
     "scola_density_adjoint": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "scola_box_density_noalloc": (c_int32, [c_void_p, c_int32, c_int32, c_double, c_void_p, c_void_p]),
     "scola_box_offsets": (c_int32, [c_void_p, _P(c_int64), _P(c_int64), c_int32]),
@@ -324,6 +326,14 @@ def scola_set_checkpointing(ctx, enable):
 
 def scola_backward(ctx, lam_x, lam_p, lam_w):
     _check(_lib.scola_backward(ctx, _ptr(lam_x), _ptr(lam_p), _ptr(lam_w)), "scola_backward")
+
+
+def scola_set_checkpoint_interval(ctx, every):
+    _check(_lib.scola_set_checkpoint_interval(ctx, int(every)), "scola_set_checkpoint_interval")
+
+
+def scola_checkpoint_interval(ctx):
+    return _lib.scola_checkpoint_interval(ctx)
 
 
 def scola_selftest_wait_timeout(ctx, wait_seconds):

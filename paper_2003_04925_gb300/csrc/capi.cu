@@ -759,6 +759,10 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &all_geo) {
     CS(dev_alloc(&c->ppchunks, L_ppch));
     CS(dev_alloc(&c->sbricks, L_sbr));
     if (c->use_tc) CS(dev_alloc(&c->tc_tiles, L_tct));
+    c->cap_P = P;
+    c->cap_M = M;
+    c->cap_MP = MP;
+    c->cap_SH = SH;
     CS(dev_alloc(&c->part, 12 * P));
     CS(dev_alloc(&c->kcount, NK));
     CS(dev_alloc(&c->koffs, NK));
@@ -1142,9 +1146,11 @@ scola_status enqueue_evolution(scola_ctx *c) {
     // read them)
     const bool fused = c->deposit_form == 0 && !(c->prm.study_mode & SCOLA_STUDY_TRUE_DENSITY);
     for (int k = 0; k <= n; ++k) {
-        if (c->checkpointing)
-            CK(cudaMemcpyAsync(c->ckpt + (size_t)k * 3 * c->P, c->part, sizeof(float) * 3 * (size_t)c->P,
-                               cudaMemcpyDeviceToDevice, c->stream));
+        if (c->checkpointing && k % c->ckpt_every == 0) {
+            const size_t rows = c->ckpt_every == 1 ? 3 : 6;          // s, or s and p_res
+            CK(cudaMemcpyAsync(c->ckpt + (size_t)(k / c->ckpt_every) * rows * c->P, c->part,
+                               sizeof(float) * rows * (size_t)c->P, cudaMemcpyDeviceToDevice, c->stream));
+        }
         CK(mark());
         scola_status st;
         const bool sourced = study_inputs(c, k, st);
@@ -1196,7 +1202,18 @@ scola_status ensure_graph(scola_ctx *c) {
     return SCOLA_OK;
 }
 
-// The per-stage, inspection and adjoint entry points address one set of box arenas.
+// Checkpoint storage for the context's interval (see Ctx::ckpt_every), sized for the largest
+// batch.
+scola_status alloc_checkpoints(scola_ctx *c) {
+    const long long P = c->cap_P;
+    const int n1 = c->prm.nsteps + 1, m = c->ckpt_every;
+    if (!c->ckpt) CS(dev_alloc(&c->ckpt, m == 1 ? 3LL * n1 * P : 6LL * ((n1 - 1) / m + 1) * P));
+    if (m > 1 && !c->seg) CS(dev_alloc(&c->seg, 3LL * m * P));
+    if (m > 1 && !c->fin) CS(dev_alloc(&c->fin, 6 * P));
+    return SCOLA_OK;
+}
+
+// The per-stage and inspection entry points address one set of box arenas.
 scola_status need_one_batch(const scola_ctx *c) {
     if (c->batch_first.size() == 2) return SCOLA_OK;
     set_error("this call needs a context whose boxes form one batch (set batch_boxes to the box count)");
@@ -1337,7 +1354,7 @@ void scola_destroy(scola_ctx *c) {
         cufftDestroy(c->tc_c2r);
     }
     void *ptrs[] = {c->boxes, c->all_boxes, c->all_coef, c->all_coefL, c->coef, c->coefL, c->tables, c->table_arena, c->pchunks, c->tchunks, c->shchunks,
-                    c->zitems, c->citems, c->mchunks, c->ppchunks, c->tc_tiles, c->dev_err, c->ckpt,
+                    c->zitems, c->citems, c->mchunks, c->ppchunks, c->tc_tiles, c->dev_err, c->ckpt, c->seg, c->fin,
                     c->adj, c->lamG, c->lam_phi_pad, c->adj_in, c->adj_out, c->lam_shell, c->lamPsi1,
                     c->lamPsi2, c->lam_phi1, c->lam_phi2, c->d2, c->lam_d2, c->part, c->dep_acc, c->kcount,
                     c->koffs, c->kcursor, c->sentries, c->sbricks,
@@ -1512,7 +1529,6 @@ scola_status scola_tcola(scola_ctx *c, const float *w, float *x, float *p) {
 
 scola_status scola_set_checkpointing(scola_ctx *c, int32_t enable) {
     if (!c) return invalid("NULL context");
-    CS(need_one_batch(c));
     const bool on = enable != 0;
     if (on && c->prm.study_mode) {
         set_error("the adjoint is not built for the study modes");
@@ -1534,15 +1550,15 @@ scola_status scola_set_checkpointing(scola_ctx *c, int32_t enable) {
     }
     c->checkpointing = on;
     c->have_forward = false;
-    if (on && !c->ckpt) {
-        const long long P = c->P, N3 = c->N3;
-        CS(dev_alloc(&c->ckpt, (long long)(c->prm.nsteps + 1) * 3 * P));
+    if (on) CS(alloc_checkpoints(c));
+    if (on && !c->adj) {
+        const long long P = c->cap_P, N3 = c->N3;
         CS(dev_alloc(&c->adj, 15 * P));
-        CS(dev_alloc(&c->lamG, 3 * c->MP));
-        CS(dev_alloc(&c->lam_phi_pad, c->MP));
-        CS(dev_alloc(&c->adj_in, c->M));
-        CS(dev_alloc(&c->adj_out, c->MP));
-        CS(dev_alloc(&c->lam_shell, c->SH));
+        CS(dev_alloc(&c->lamG, 3 * c->cap_MP));
+        CS(dev_alloc(&c->lam_phi_pad, c->cap_MP));
+        CS(dev_alloc(&c->adj_in, c->cap_M));
+        CS(dev_alloc(&c->adj_out, c->cap_MP));
+        CS(dev_alloc(&c->lam_shell, c->cap_SH));
         CS(dev_alloc(&c->lamPsi1, 3 * N3));
         CS(dev_alloc(&c->lamPsi2, 3 * N3));
         CS(dev_alloc(&c->lam_phi1, N3));
@@ -1552,6 +1568,40 @@ scola_status scola_set_checkpointing(scola_ctx *c, int32_t enable) {
     }
     return SCOLA_OK;
 }
+
+scola_status scola_set_checkpoint_interval(scola_ctx *c, int32_t every) {
+    if (!c || every < 0) return invalid("NULL context or negative interval");
+    const int n1 = c->prm.nsteps + 1;                       // force evaluations
+    int m = every;
+    if (m == 0) {                                           // fewest floats: slots x 6 + m x 3 (+ 6)
+        long long best = -1;
+        for (int q = 1; q <= n1; ++q) {
+            const long long fl = q == 1 ? 3LL * n1 : 6LL * ((n1 - 1) / q + 1) + 3LL * q + 6;
+            if (best < 0 || fl < best) {
+                best = fl;
+                m = q;
+            }
+        }
+    }
+    m = std::min(m, n1);
+    if (m == c->ckpt_every) return SCOLA_OK;
+    CK(c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize());
+    if (c->evolve_exec) {                                   // the copies in the graph depend on m
+        CK(cudaGraphExecDestroy(c->evolve_exec));
+        c->evolve_exec = nullptr;
+    }
+    c->ckpt_every = m;
+    c->have_forward = false;
+    for (float **q : {&c->ckpt, &c->seg, &c->fin})
+        if (*q) {
+            CK(cudaFree(*q));
+            *q = nullptr;
+        }
+    if (c->checkpointing) CS(alloc_checkpoints(c));
+    return SCOLA_OK;
+}
+
+int32_t scola_checkpoint_interval(const scola_ctx *c) { return c ? c->ckpt_every : 0; }
 
 }  // extern "C"
 
@@ -1568,43 +1618,84 @@ scola_status backward_ready(const scola_ctx *c) {
     return SCOLA_OK;
 }
 
-// Clears the backward accumulators; the caller then sets the tile particles' initial state.
-scola_status backward_clear(scola_ctx *c) {
-    const long long P = c->P, N3 = c->N3;
+// Clears the full-box accumulators of the backward pass (once per call).
+scola_status backward_clear_global(scola_ctx *c) {
+    const long long N3 = c->N3;
     const size_t fb = sizeof(float);
-    CK(cudaMemsetAsync(c->adj, 0, fb * 15 * P, c->stream));
-    CK(cudaMemsetAsync(c->lam_shell, 0, fb * c->SH, c->stream));
     CK(cudaMemsetAsync(c->lamPsi1, 0, fb * 3 * N3, c->stream));
     CK(cudaMemsetAsync(c->lamPsi2, 0, fb * 3 * N3, c->stream));
     CK(cudaMemsetAsync(c->lam_phi1, 0, fb * N3, c->stream));
     return SCOLA_OK;
 }
 
-// The reverse sweep from the tile particles' adjoint state in c->adj to dLoss/dw: the KDK
-// sequence in reverse with the recomputed mesh force at each checkpoint, L-, the shell, 2LPT
-// and the colouring.
-scola_status reverse_sweep(scola_ctx *c, float *lam_w) {
-    const long long P = c->P, N3 = c->N3;
+// Clears the bound batch's backward state; the caller then sets its tile particles' state.
+scola_status backward_clear_batch(scola_ctx *c) {
+    const size_t fb = sizeof(float);
+    CK(cudaMemsetAsync(c->adj, 0, fb * 15 * c->P, c->stream));
+    CK(cudaMemsetAsync(c->lam_shell, 0, fb * c->SH, c->stream));
+    return SCOLA_OK;
+}
+
+// One force evaluation k of the reverse KDK sweep of the bound batch, with sk the box
+// particles' displacements at k: the kick and drift transposes, then the mesh force
+// recomputed at sk and its transpose (interpolation, gradient, Dirichlet solve, boundary
+// terms, deposit).  With per-tile final scale factors every box takes its own factors of
+// evaluation k from the coefficient table (k is passed on); otherwise the uniform scalars.
+scola_status reverse_step(scola_ctx *c, int k, const float *sk) {
+    const long long P = c->P;
+    CK(launch_adj_kick_drift(*c, c->adj, kick_drift_coefficients(c->tt, k), k));
+    CK(launch_deposit(*c, sk, P, (float)(1.0 / c->tt.D1[k]), nullptr, false, k));
+    CK(launch_poisson(*c));
+    CK(cudaMemsetAsync(c->lamG, 0, sizeof(float) * 3 * c->MP, c->stream));
+    CK(launch_adj_interp(*c, sk, c->adj, c->lamG, (float)c->tt.D1[k], k));
+    CK(launch_adj_div(*c, c->lamG, c->lam_phi_pad, c->adj_in));
+    CK(launch_poisson_buffers(*c, c->adj_in, c->work, c->work2, c->adj_out));
+    CK(launch_adj_shell(*c, c->lam_phi_pad, c->adj_out, (float)c->tt.D1[k], c->lam_shell, k));
+    CK(launch_adj_deposit(*c, sk, c->adj_out, c->adj));
+    return SCOLA_OK;
+}
+
+// The reverse sweep of the bound batch from its tile particles' adjoint state in c->adj,
+// accumulated into the full-box lam_Psi1, lam_Psi2 (L-) and lam_phi1 (the C.3 shell).
+// Checkpoints every m-th evaluation (m > 1) hold s and p_res: each segment
+// [j m, min(n, j m + m - 1)] is replayed forward from its slot (the same deterministic
+// kernels, so the same displacements as the run) into seg, then swept in reverse; the
+// particle arena's final state is saved before and restored after.
+scola_status reverse_batch(scola_ctx *c) {
+    const long long P = c->P;
     const size_t fb = sizeof(float);
     const int n = (int)c->tt.alpha.size();
-    // with per-tile final scale factors every box takes its own factors of evaluation k from
-    // the coefficient table (k is passed on); otherwise the uniform scalars
-    for (int k = n; k >= 0; --k) {
-        CK(launch_adj_kick_drift(*c, c->adj, kick_drift_coefficients(c->tt, k), k));
-        const float *sk = c->ckpt + (size_t)k * 3 * P;
-        CK(launch_deposit(*c, sk, P, (float)(1.0 / c->tt.D1[k]), nullptr, false, k));
-        CK(launch_poisson(*c));
-        CK(cudaMemsetAsync(c->lamG, 0, fb * 3 * c->MP, c->stream));
-        CK(launch_adj_interp(*c, sk, c->adj, c->lamG, (float)c->tt.D1[k], k));
-        CK(launch_adj_div(*c, c->lamG, c->lam_phi_pad, c->adj_in));
-        CK(launch_poisson_buffers(*c, c->adj_in, c->work, c->work2, c->adj_out));
-        CK(launch_adj_shell(*c, c->lam_phi_pad, c->adj_out, (float)c->tt.D1[k], c->lam_shell, k));
-        CK(launch_adj_deposit(*c, sk, c->adj_out, c->adj));
+    const int m = c->ckpt_every;
+    if (m == 1) {
+        for (int k = n; k >= 0; --k) CS(reverse_step(c, k, c->ckpt + (size_t)k * 3 * P));
+    } else {
+        CK(cudaMemcpyAsync(c->fin, c->part, fb * 6 * P, cudaMemcpyDeviceToDevice, c->stream));
+        for (int j = n / m; j >= 0; --j) {
+            const int k0 = j * m, k1 = std::min(n, k0 + m - 1);
+            CK(cudaMemcpyAsync(c->part, c->ckpt + (size_t)j * 6 * P, fb * 6 * P, cudaMemcpyDeviceToDevice,
+                               c->stream));
+            for (int k = k0; k <= k1; ++k) {
+                CK(cudaMemcpyAsync(c->seg + (size_t)(k - k0) * 3 * P, c->part, fb * 3 * P, cudaMemcpyDeviceToDevice,
+                                   c->stream));
+                if (k == k1) break;
+                CK(launch_deposit(*c, c->part, P, (float)(1.0 / c->tt.D1[k]), nullptr, false, k));
+                CK(launch_poisson(*c));
+                CK(launch_kick_drift(*c, forward_kick(c->tt, k), false, k));
+            }
+            for (int k = k1; k >= k0; --k) CS(reverse_step(c, k, c->seg + (size_t)(k - k0) * 3 * P));
+        }
+        CK(cudaMemcpyAsync(c->part, c->fin, fb * 6 * P, cudaMemcpyDeviceToDevice, c->stream));
     }
     CK(launch_adj_init_scatter(*c, c->adj, c->lamPsi1, c->lamPsi2));
     CK(launch_adj_shell_to_phi1(*c, c->lam_shell, c->lam_phi1));
-    // full-box 2LPT and colouring adjoints (symmetric Fourier operators); in the Zel'dovich
-    // frame Psi2 = 0 does not depend on the noise and the second-order chain is absent
+    return SCOLA_OK;
+}
+
+// The full-box 2LPT and colouring adjoints (symmetric Fourier operators) from the
+// accumulated lam_Psi1, lam_Psi2, lam_phi1 to dLoss/dw; in the Zel'dovich frame Psi2 = 0
+// does not depend on the noise and the second-order chain is absent.
+scola_status lpt_adjoint(scola_ctx *c, float *lam_w) {
+    const long long N3 = c->N3;
     const bool second = c->prm.lpt_order == 2;
     CK(launch_neg_div(*c, c->lamPsi1, 1, c->lam_phi1));
     const int pairs[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
@@ -1629,6 +1720,28 @@ scola_status reverse_sweep(scola_ctx *c, float *lam_w) {
     return SCOLA_OK;
 }
 
+// The whole backward pass.  One batch: its checkpoints are those of the forward run.  Several
+// streamed batches: each batch is bound in turn and its evolution replayed from C.1 with the
+// checkpointing graph (deterministic: the run's own trajectory, and its checkpoints), its
+// tile particles take their initial adjoint state (init), and its reverse sweep accumulates
+// into the full-box arrays; the LPT and colouring adjoints run once at the end.
+template <typename Init>
+scola_status backward_all(scola_ctx *c, float *lam_w, Init init) {
+    CS(backward_clear_global(c));
+    const int nbatch = (int)c->batch_first.size() - 1;
+    for (int b = 0; b < nbatch; ++b) {
+        if (nbatch > 1) {
+            CS(bind_batch(c, b));
+            CS(ensure_graph(c));
+            CK(cudaGraphLaunch(c->evolve_exec, c->stream));
+        }
+        CS(backward_clear_batch(c));
+        CK(init());
+        CS(reverse_batch(c));
+    }
+    return lpt_adjoint(c, lam_w);
+}
+
 }  // namespace
 
 extern "C" {
@@ -1636,18 +1749,14 @@ extern "C" {
 scola_status scola_backward(scola_ctx *c, const float *lam_x, const float *lam_p, float *lam_w) {
     if (!c || !lam_w || (!lam_x && !lam_p)) return invalid("NULL argument (lam_w, or both lam_x and lam_p)");
     CS(backward_ready(c));
-    CS(backward_clear(c));
-    CK(launch_adj_final_xp(*c, lam_x, lam_p, c->adj));
-    return reverse_sweep(c, lam_w);
+    return backward_all(c, lam_w, [&]() { return launch_adj_final_xp(*c, lam_x, lam_p, c->adj); });
 }
 
 scola_status scola_backward_density(scola_ctx *c, const float *lam_delta, float *lam_w) {
     if (!c || !lam_delta || !lam_w) return invalid("NULL argument");
     CS(backward_ready(c));
-    CS(backward_clear(c));
-    // final density -> tile particles
-    CK(launch_adj_final(*c, lam_delta, c->adj));
-    return reverse_sweep(c, lam_w);
+    // final density -> tile particles (from the batch's final particle state)
+    return backward_all(c, lam_w, [&]() { return launch_adj_final(*c, lam_delta, c->adj); });
 }
 
 scola_status scola_density_adjoint(scola_ctx *c, const float *x, const float *lam_delta, float *lam_x) {

@@ -183,7 +183,14 @@ struct Ctx {
 
     // adjoint (scola_set_checkpointing / scola_backward)
     bool checkpointing = false, have_forward = false;
-    float *ckpt = nullptr;                            // (nsteps+1) x 3 x P displacements
+    // checkpoints: every ckpt_every-th force evaluation k keeps the displacements (ckpt_every
+    // = 1: 3 x P floats per slot, every evaluation) or the displacements and momenta
+    // (ckpt_every > 1: 6 x P per slot; the reverse sweep replays each segment of ckpt_every
+    // evaluations from its slot into seg and restores the final state from fin)
+    int ckpt_every = 1;
+    float *ckpt = nullptr;
+    float *seg = nullptr, *fin = nullptr;
+    long long cap_P = 0, cap_M = 0, cap_MP = 0, cap_SH = 0;   // the largest batch's arena sizes
     float *adj = nullptr;                             // 15 x P backward particle state
     float *lamG = nullptr, *lam_phi_pad = nullptr, *adj_in = nullptr, *adj_out = nullptr;
     float *lam_shell = nullptr, *lamPsi1 = nullptr, *lamPsi2 = nullptr;

@@ -116,7 +116,11 @@ class Scola:
     def stats(self):
         return B.scola_get_stats(self.ctx)
 
-    def enable_checkpointing(self, on=True):
+    def enable_checkpointing(self, on=True, every=None):
+        """Checkpoints for the adjoint; every: the checkpoint interval (1: every force
+        evaluation, m: every m-th with segment replay, 0: the fewest floats)."""
+        if every is not None:
+            B.scola_set_checkpoint_interval(self.ctx, every)
         B.scola_set_checkpointing(self.ctx, on)
 
     def backward(self, lam_x=None, lam_p=None):

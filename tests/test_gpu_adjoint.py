@@ -194,6 +194,44 @@ def test_gradient_of_a_replaced_run_is_refused():
     sim.close()
 
 
+@pytest.mark.parametrize("every,batch_boxes", [(3, 0), (0, 0), (1, 2), (2, 2)])
+def test_interval_checkpoints_and_streamed_batches_give_the_same_gradient(every, batch_boxes):
+    # Checkpoints every m-th force evaluation with segment replay, and streamed batches whose
+    # evolution the backward pass replays batch by batch: the replays are the run's own
+    # deterministic trajectory, so the gradient equals the every-evaluation, one-batch
+    # gradient up to the order of the FP32 atomic additions of the adjoint.  7 steps (8 force
+    # evaluations) make uneven segments; batch_boxes = 2 gives 4 batches of the 8 boxes.
+    kw = dict(L=48.0, Np=16, Ntiles=2, Nbuf=2, mesh_ratio=1, nsteps=7, a_i=0.05, a_f=1.0)
+    target = torch.from_numpy(_target(dict(kw, nsteps=3), 22).astype(np.float32)).cuda()
+    w = torch.from_numpy(synth_inputs.white_noise(16, 21)).cuda()
+    n = 16**3
+    u = torch.from_numpy(synth_inputs.random_field((n, 3), 41).astype(np.float32)).cuda()
+    ref = _sim(kw, "tc")
+    x, _ = ref.forward(w)
+    lam = 2.0 * (ref.final_density(x) - target)
+    g_ref = ref.backward_density(lam).cpu().numpy()
+    gx_ref = ref.backward(u).cpu().numpy()
+    ref.close()
+    sc = _pkg()
+    sim = sc.Scola(**dict(lib_kwargs(kw), dst_variant=sc.SCOLA_DST_TC_3XTF32, batch_boxes=batch_boxes))
+    sim.enable_checkpointing(True, every=every)
+    assert sim.stats()["batches"] == (4 if batch_boxes else 1)
+    m = sc.scola_checkpoint_interval(sim.ctx)
+    assert m == (every if every else m) and m >= 1
+    x2, _ = sim.forward(w)
+    assert torch.equal(x, x2)
+    g = sim.backward_density(lam).cpu().numpy()
+    g_again = sim.backward_density(lam).cpu().numpy()      # the final state survives the replay
+    gx = sim.backward(u).cpu().numpy()
+    torch.cuda.synchronize()
+    sc.scola_device_status(sim.ctx)
+    sim.close()
+    for a, b in ((g, g_ref), (g_again, g_ref), (gx, gx_ref)):
+        rel = np.linalg.norm(a - b) / np.linalg.norm(b)
+        print("every=%d batches=%d interval %d: rel diff %.2e" % (every, 4 if batch_boxes else 1, m, rel))
+        assert rel < 1e-5, rel
+
+
 def test_autograd_function_matches_backward():
     sc = _pkg()
     kw = dict(L=48.0, Np=16, Ntiles=2, Nbuf=2, mesh_ratio=1, nsteps=3, a_i=0.05, a_f=1.0)
