@@ -98,20 +98,30 @@ struct TileInfo {
 };
 constexpr int kTileCache = 96;
 
-struct TcArgs {
+// One Ng group of a launch: the boxes sharing Ng, their tiles, tables and tensor map, and
+// the CTAs [cta0, cta0 + nctas) that process them.  Every CTA holds the sine matrix of its
+// own group only, so boxes of uneven mesh sizes share one launch per pass.
+struct TcGroupArgs {
     CUtensorMap in_map;          // the input as rows of Ng floats (64-byte swizzle boxes 16 x 256)
-    const BoxDesc *boxes;
     const Chunk *tiles;          // (box, tile-in-box)
-    int ntiles;                  // work items: tiles, or 2 x tiles (one per parity) when folded
-    int Ng, Npad, nkc, nstage;   // uniform Ng for the launch; nkc sine chunks; nstage data stages
     const float *S;              // FP32 sine matrix, Npad x (nkc*32), zero padded (folded: the
                                  // even-row and then the odd-row half matrices)
     const float *lam;            // Dirichlet eigenvalues, Ng
+    int ntiles;                  // work items: tiles, or 2 x tiles (one per parity) when folded
+    int Ng, Npad, nkc, nstage;   // nkc sine chunks; nstage data stages
+    int ragged;                  // 1: rows not 16-byte pitched; plain loads and stores (no TMA)
+    int cta0, nctas;             // this group's CTAs (an even count when folded)
+};
+constexpr int kMaxTcGroups = 4;
+
+struct TcArgs {
+    TcGroupArgs grp[kMaxTcGroups];
+    int ngroups;
+    const BoxDesc *boxes;
     const float *in;
     float *out;
     int *err;
     int lo_lo;                   // 1: also accumulate a_lo s_lo (four TF32 products)
-    int ragged;                  // 1: rows not 16-byte pitched; plain loads and stores (no TMA)
     unsigned long long stall_ns; // failure-detection self-test: > 0 makes the MMA thread first wait
                                  // this long on a barrier nothing arrives on, then abort
 };
@@ -274,10 +284,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(const __grid_constant__ 
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-aligned (in the shared window) base for the swizzled operand tiles
     unsigned char *base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-    const int Ng = A.Ng, nka = A.nkc, NST = A.nstage;
-    // folded: this CTA's parity (the grid is even, so item b + k grid keeps the parity of b),
-    // and the contraction length and matrix rows Nk = Ng / 2
-    const int parity = FOLD ? (int)(blockIdx.x & 1) : 0;
+    // this CTA's group, and its index among the group's CTAs
+    int gi = 0;
+    while (gi + 1 < A.ngroups && (int)blockIdx.x >= A.grp[gi + 1].cta0) ++gi;
+    const TcGroupArgs &G = A.grp[gi];
+    const int bid = (int)blockIdx.x - G.cta0, nbid = G.nctas;
+    const int Ng = G.Ng, nka = G.nkc, NST = G.nstage;
+    // folded: this CTA's parity (the group's CTA count is even, so item b + k nbid keeps the
+    // parity of b), and the contraction length and matrix rows Nk = Ng / 2
+    const int parity = FOLD ? (bid & 1) : 0;
     const int Nk = FOLD ? (parity ? Ng / 2 : (Ng + 1) / 2) : Ng;
     const int nkb = (Nk + kKB - 1) / kKB;                 // data chunks per tile
     const uint32_t sch = (uint32_t)((Nk + 7) / 8) * 1024; // one sine chunk (hi or lo), Nk rows
@@ -304,7 +319,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(const __grid_constant__ 
 
     // ---- set-up: S (hi/lo split, swizzled), lambda, tile table, barriers, tensor memory
     const int Kp = nka * kKA;
-    const float *Sg = A.S + (FOLD ? (long long)parity * A.Npad * Kp : 0LL);
+    const float *Sg = G.S + (FOLD ? (long long)parity * G.Npad * Kp : 0LL);
     for (int q = tid; q < Nk * Kp; q += kThreads) {
         const int n = q / Kp, k = q % Kp;
         const float sv = Sg[q];
@@ -313,10 +328,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(const __grid_constant__ 
         *(float *)(S_hi + off) = hi;
         *(float *)(S_lo + off) = tf32_rn(sv - hi);
     }
-    for (int q = tid; q < Ng; q += kThreads) lam[q] = A.lam[q];
-    const long long my_tiles = A.ntiles > (int)blockIdx.x ? (A.ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    for (int q = tid; q < Ng; q += kThreads) lam[q] = G.lam[q];
+    const long long my_tiles = G.ntiles > bid ? (G.ntiles - 1 - bid) / nbid + 1 : 0;
     auto load_tile = [&](long long k) {
-        const Chunk tl = A.tiles[((int)blockIdx.x + k * (int)gridDim.x) >> (FOLD ? 1 : 0)];
+        const Chunk tl = G.tiles[(bid + k * nbid) >> (FOLD ? 1 : 0)];
         TileInfo ti;
         ti.m_off = A.boxes[tl.box].m_off;
         ti.pp_off = A.boxes[tl.box].pp_off;
@@ -372,7 +387,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(const __grid_constant__ 
             const int s = (int)(h % NST);
             unsigned char *xh = stages + (size_t)s * kStageBytes;
             unsigned char *xl = stages + (size_t)s * kStageBytes + kHalfBytes;
-            if (A.ragged) {
+            if (G.ragged) {
                 // the stage is free once the MMA has consumed the chunk before in it; then
                 // element (r, k) of the chunk (row r of the tile, column 16 cc + k) is read
                 // by thread idx % 256 of idx = 16 r + k (a half warp reads 64 contiguous
@@ -464,7 +479,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(const __grid_constant__ 
         // lane 0 loads chunk g into stage g % NST as soon as the MMA has released it; on an
         // abort it waits (bounded) for the copies it issued before the CTA may exit.  Idle on
         // the ragged path (the converters load the chunks themselves)
-        if (lane == 0 && !A.ragged) {
+        if (lane == 0 && !G.ragged) {
             long long g = 0;
             for (; g < nchunks && !*abort_flag; ++g) {
                 const int s = (int)(g % NST);
@@ -481,9 +496,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(const __grid_constant__ 
                 }
                 const int cc = (int)(g % nkb), y = (int)(ti.m_off / Ng + ti.row0);
                 mbar_arrive_expect_tx(&loaded[s], FOLD ? 2 * kHalfBytes : kHalfBytes);
-                tma_load_2d(smem_u32(stages + (size_t)s * kStageBytes), &A.in_map, cc * kKB, y, &loaded[s]);
+                tma_load_2d(smem_u32(stages + (size_t)s * kStageBytes), &G.in_map, cc * kKB, y, &loaded[s]);
                 if (FOLD)   // the mirror chunk: columns Ng - 16 (cc + 1) .. Ng - 16 cc - 1
-                    tma_load_2d(smem_u32(stages + (size_t)s * kStageBytes + kHalfBytes), &A.in_map,
+                    tma_load_2d(smem_u32(stages + (size_t)s * kStageBytes + kHalfBytes), &G.in_map,
                                 Ng - (cc + 1) * kKB, y, &loaded[s]);
             }
             if (*abort_flag) {
@@ -597,7 +612,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(const __grid_constant__ 
                 // eight lanes cover 32 consecutive rows (128 bytes) of one column
                 const int ru = lane & 7, cg = lane >> 3;
                 const long long R = (long long)ti.row0 + half * 128 + rnd * 32 + 4 * ru;
-                if (A.ragged && R < Ng2) {
+                if (G.ragged && R < Ng2) {
                     // element by element: rows R .. R + 3 may cross a row of the mesh or the
                     // end of the box, and nothing is 16-byte aligned
 #pragma unroll 1
@@ -720,39 +735,71 @@ cudaError_t input_map(Ctx &c, const float *buf, int Ng, CUtensorMap *out) {
     return cudaSuccess;
 }
 
+// One launch of pass PASS over up to kMaxTcGroups Ng groups of the same form (all direct or
+// all folded).  The persistent grid (one CTA per SM) is split among the groups in proportion
+// to their work (items x Ng, the contraction length), each group getting at least one CTA
+// (two when folded, one per parity) and no more CTAs than items.
 template <int PASS>
-cudaError_t run_tc_pass(Ctx &c, const TcGroup &G, const float *in, float *out) {
+cudaError_t run_tc_pass(Ctx &c, const std::vector<TcGroup> &groups, const float *in, float *out) {
     TcArgs a;
     std::memset(&a, 0, sizeof(a));
-    a.ragged = tc_ragged(G.Ng) ? 1 : 0;
-    if (!a.ragged) {
-        cudaError_t me = input_map(c, in, G.Ng, &a.in_map);
-        if (me != cudaSuccess) return me;
+    const int ng = (int)groups.size();
+    if (ng < 1 || ng > kMaxTcGroups) return cudaErrorInvalidValue;
+    const bool fold = tc_folded(groups[0].Ng);
+    const int step = fold ? 2 : 1;
+    double total = 0;
+    std::vector<double> work(ng);
+    std::vector<int> items(ng), ctas(ng);
+    for (int g = 0; g < ng; ++g) {
+        items[g] = fold ? 2 * groups[g].ntiles : groups[g].ntiles;
+        work[g] = (double)items[g] * groups[g].Ng;
+        total += work[g];
     }
-    const bool fold = tc_folded(G.Ng);
+    int sum = 0;
+    for (int g = 0; g < ng; ++g) {
+        int n = (int)(c.num_sms * work[g] / std::max(total, 1.0)) / step * step;
+        n = std::max(step, std::min(n, (items[g] + step - 1) / step * step));
+        ctas[g] = n;
+        sum += n;
+    }
+    while (sum > std::max(c.num_sms, step * ng)) {            // trim the largest share
+        int g = (int)(std::max_element(ctas.begin(), ctas.end()) - ctas.begin());
+        if (ctas[g] <= step) break;
+        ctas[g] -= step;
+        sum -= step;
+    }
+    size_t smem = 0;
+    int cta0 = 0;
+    for (int g = 0; g < ng; ++g) {
+        const TcGroup &G = groups[g];
+        TcGroupArgs &A = a.grp[g];
+        A.ragged = tc_ragged(G.Ng) ? 1 : 0;
+        if (!A.ragged) {
+            cudaError_t me = input_map(c, in, G.Ng, &A.in_map);
+            if (me != cudaSuccess) return me;
+        }
+        A.tiles = G.tiles;
+        A.ntiles = items[g];
+        A.Ng = G.Ng;
+        A.Npad = G.Npad;
+        A.nkc = G.nkc;
+        A.nstage = G.nstage;
+        A.S = c.table_arena + G.s_off;
+        A.lam = c.table_arena + G.lam_off;
+        A.cta0 = cta0;
+        A.nctas = ctas[g];
+        cta0 += ctas[g];
+        smem = std::max(smem, tc_smem_bytes(fold ? (G.Ng + 1) / 2 : G.Ng, G.Ng, G.nkc, G.nstage));
+    }
+    a.ngroups = ng;
     a.boxes = c.boxes;
-    a.tiles = G.tiles;
-    a.ntiles = fold ? 2 * G.ntiles : G.ntiles;     // folded: one item per parity of each tile
-    a.Ng = G.Ng;
-    a.Npad = G.Npad;
-    a.nkc = G.nkc;
-    a.nstage = G.nstage;
-    a.S = c.table_arena + G.s_off;
-    a.lam = c.table_arena + G.lam_off;
     a.in = in;
     a.out = out;
     a.err = c.dev_err;
     a.lo_lo = c.tc_lo_lo ? 1 : 0;
     a.stall_ns = c.tc_stall_ns;
-    const size_t smem = tc_smem_bytes(fold ? (G.Ng + 1) / 2 : G.Ng, G.Ng, G.nkc, G.nstage);
-    if (fold) {
-        // an even grid keeps each CTA on one parity (item b + k grid has the parity of b)
-        const int grid = std::max(2, std::min(a.ntiles, c.num_sms) & ~1);
-        k_dst_tc<PASS, true><<<grid, kThreads, smem, c.stream>>>(a);
-    } else {
-        const int grid = std::max(1, std::min(a.ntiles, c.num_sms));
-        k_dst_tc<PASS, false><<<grid, kThreads, smem, c.stream>>>(a);
-    }
+    if (fold) k_dst_tc<PASS, true><<<cta0, kThreads, smem, c.stream>>>(a);
+    else k_dst_tc<PASS, false><<<cta0, kThreads, smem, c.stream>>>(a);
     ++c.launches;
     return cudaGetLastError();
 }
@@ -815,17 +862,36 @@ std::vector<TcGroup> active_groups(const Ctx &c) {
     return one;
 }
 
+// The active groups split into launches: direct and folded forms apart, at most kMaxTcGroups
+// groups each (every workload here makes one launch per pass).
+std::vector<std::vector<TcGroup>> tc_launches(const Ctx &c) {
+    std::vector<std::vector<TcGroup>> out;
+    for (int f = 0; f < 2; ++f) {
+        std::vector<TcGroup> cur;
+        for (const TcGroup &G : active_groups(c)) {
+            if ((int)tc_folded(G.Ng) != f) continue;
+            cur.push_back(G);
+            if ((int)cur.size() == kMaxTcGroups) {
+                out.push_back(cur);
+                cur.clear();
+            }
+        }
+        if (!cur.empty()) out.push_back(cur);
+    }
+    return out;
+}
+
 cudaError_t launch_poisson_tc_pass(Ctx &c, int pass) {
     // buffers: source (work2) -> work -> work2 -> work -> work2 -> work -> phi
     cudaError_t e = cudaSuccess;
-    for (const TcGroup &G : active_groups(c)) {
+    for (const auto &L : tc_launches(c)) {
         switch (pass) {
-            case 0: e = run_tc_pass<P_F>(c, G, c.work2, c.work); break;
-            case 1: e = run_tc_pass<P_F>(c, G, c.work, c.work2); break;
-            case 2: e = run_tc_pass<P_XF>(c, G, c.work2, c.work); break;
-            case 3: e = run_tc_pass<P_ZI>(c, G, c.work, c.work2); break;
-            case 4: e = run_tc_pass<P_YI>(c, G, c.work2, c.work); break;
-            case 5: e = run_tc_pass<P_XI>(c, G, c.work, c.phi); break;
+            case 0: e = run_tc_pass<P_F>(c, L, c.work2, c.work); break;
+            case 1: e = run_tc_pass<P_F>(c, L, c.work, c.work2); break;
+            case 2: e = run_tc_pass<P_XF>(c, L, c.work2, c.work); break;
+            case 3: e = run_tc_pass<P_ZI>(c, L, c.work, c.work2); break;
+            case 4: e = run_tc_pass<P_YI>(c, L, c.work2, c.work); break;
+            case 5: e = run_tc_pass<P_XI>(c, L, c.work, c.phi); break;
             default: return cudaErrorInvalidValue;
         }
         if (e != cudaSuccess) return e;
@@ -844,13 +910,13 @@ cudaError_t launch_poisson_tc(Ctx &c) {
 
 cudaError_t launch_poisson_tc_buffers(Ctx &c, const float *in, float *w1, float *w2, float *out_pad) {
     cudaError_t e = cudaSuccess;
-    for (const TcGroup &G : active_groups(c)) {
-        e = run_tc_pass<P_F>(c, G, in, w1);
-        if (e == cudaSuccess) e = run_tc_pass<P_F>(c, G, w1, w2);
-        if (e == cudaSuccess) e = run_tc_pass<P_XF>(c, G, w2, w1);
-        if (e == cudaSuccess) e = run_tc_pass<P_ZI>(c, G, w1, w2);
-        if (e == cudaSuccess) e = run_tc_pass<P_YI>(c, G, w2, w1);
-        if (e == cudaSuccess) e = run_tc_pass<P_XI>(c, G, w1, out_pad);
+    for (const auto &L : tc_launches(c)) {
+        e = run_tc_pass<P_F>(c, L, in, w1);
+        if (e == cudaSuccess) e = run_tc_pass<P_F>(c, L, w1, w2);
+        if (e == cudaSuccess) e = run_tc_pass<P_XF>(c, L, w2, w1);
+        if (e == cudaSuccess) e = run_tc_pass<P_ZI>(c, L, w1, w2);
+        if (e == cudaSuccess) e = run_tc_pass<P_YI>(c, L, w2, w1);
+        if (e == cudaSuccess) e = run_tc_pass<P_XI>(c, L, w1, out_pad);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
