@@ -45,10 +45,10 @@ def parse():
     ap.add_argument("--impl", default="scola", choices=["scola", "reference"])
     ap.add_argument("--workload", default="batched_128")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--dst", default="auto", choices=["auto", "tc", "tc4", "simt"],
-                    help="Poisson-solve form: the library's autotuner (auto, default: the faster of "
-                         "3xTF32 tensor cores and FP32 CUDA cores), tensor-core 3xTF32 (tc), 4xTF32 (tc4) "
-                         "or FP32 CUDA cores (simt)")
+    ap.add_argument("--dst", default="auto", choices=["auto", "tc", "tc4", "tc3", "simt"],
+                    help="Poisson-solve form: the library's autotuner (auto, default: the fastest of the "
+                         "tensor-core forms and FP32 CUDA cores), tensor-core 3xTF32 in six passes (tc), "
+                         "4xTF32 (tc4), 3xTF32 in three passes (tc3) or FP32 CUDA cores (simt)")
     ap.add_argument("--forward-only", action="store_true",
                     help="only W + K forward runs of the batched form (for ncu launch lists)")
     ap.add_argument("--batch-boxes", type=int, default=0,
@@ -284,8 +284,7 @@ def adjoint_cost(sc, torch, dst, steps):
     import numpy as np
     import synth_inputs
     kw, W = workload_kwargs("adjoint_128")
-    kw["dst_variant"] = {"tc": sc.SCOLA_DST_TC_3XTF32, "tc4": sc.SCOLA_DST_TC_4XTF32,
-                         "simt": sc.SCOLA_DST_SIMT}[dst]
+    kw["dst_variant"] = dst_code(sc, dst)
     plain = sc.Scola(**kw)
     sim = sc.Scola(**kw)
     sim.enable_checkpointing(True)
@@ -391,13 +390,13 @@ def study_cost(sc, torch, kw, W, steps, peaks):
 
 
 # ----------------------------------------------------------------------------- roofline
-def kernel_roofline(kt, kw, clocks, peaks, tc):
+def kernel_roofline(kt, kw, clocks, peaks, form):
     """Algorithmic bytes or flops per launch of each kernel class and the dominant one.
 
     FP32 form: the five DST passes are dense products on CUDA cores (ALU bound,
     2 Ng flops per cell per transform; pass 3 does two transforms).  Tensor-core
-    form: six passes, each streaming its mesh once (HBM bound: 4 B read + 4 B
-    written per cell).  Deposit: the positions once (12 B per particle) and the
+    forms: six passes (or three), each streaming its mesh once (HBM bound: 4 B read
+    + 4 B written per cell).  Deposit: the positions once (12 B per particle) and the
     Poisson source written once (4 B per cell).
     """
     nsc, ng = box_sizes(kw)
@@ -407,7 +406,13 @@ def kernel_roofline(kt, kw, clocks, peaks, tc):
     dense = sum(2.0 * g * g**3 for g in ng)          # flops of one dense DST-I along one axis
     work = {"deposit": ("hbm", 12.0 * P + 4.0 * M),
             "kick_drift": ("hbm", 72.0 * P + 4.0 * MP)}
-    if tc:
+    if form == "tc3":
+        # three mesh passes: z forward, the plane pass (y, x forward, division, x, y inverse),
+        # z inverse; each streams the mesh once
+        names = ["dst_1_z_fwd", "dst_2_plane", "dst_3_z_inv", None, None, None]
+        for nm in names[:3]:
+            work[nm] = ("hbm", 8.0 * M)
+    elif form in ("tc", "tc4"):
         names = ["dst_1_z_fwd", "dst_2_y_fwd", "dst_3_x_fwd_div", "dst_4_z_inv", "dst_5_y_inv",
                  "dst_6_x_inv"]
         for i, nm in enumerate(names):
@@ -510,8 +515,7 @@ def run_gpu(args, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     kw, W = workload_kwargs(args.workload)
-    kw["dst_variant"] = {"auto": sc.SCOLA_DST_AUTO, "tc": sc.SCOLA_DST_TC_3XTF32, "tc4": sc.SCOLA_DST_TC_4XTF32,
-                         "simt": sc.SCOLA_DST_SIMT}[args.dst]
+    kw["dst_variant"] = dst_code(sc, args.dst)
     if args.batch_boxes:
         kw["batch_boxes"] = args.batch_boxes
     if world > 1:
@@ -542,8 +546,9 @@ def run_gpu(args, rank, world, local_rank):
     dst_tune = dst_choice(sc, sim.stats())
     if args.dst == "auto":
         # the form the autotuner kept; every later context of this run asks for it
-        args.dst = "tc" if sc.scola_uses_tensor_cores(sim.ctx) else "simt"
-        kw["dst_variant"] = {"tc": sc.SCOLA_DST_TC_3XTF32, "simt": sc.SCOLA_DST_SIMT}[args.dst]
+        args.dst = {sc.SCOLA_DST_TC_3XTF32: "tc", sc.SCOLA_DST_TC_4XTF32: "tc4", sc.SCOLA_DST_TC_3PASS: "tc3",
+                    sc.SCOLA_DST_SIMT: "simt"}[sim.stats()["dst_form"]]
+        kw["dst_variant"] = dst_code(sc, args.dst)
     if args.forward_only:
         t0 = time.perf_counter()
         for _ in range(args.steps):
@@ -616,7 +621,7 @@ def run_gpu(args, rank, world, local_rank):
     torch.cuda.synchronize()
     kt = sc.scola_kernel_times(sim.ctx)
     sc.scola_set_profiling(sim.ctx, False)
-    dom, rows = kernel_roofline(kt, kw, clk, peaks, args.dst != "simt")
+    dom, rows = kernel_roofline(kt, kw, clk, peaks, args.dst)
     sc.scola_device_status(sim.ctx)
     d = rows[dom]
     # ncu DRAM bytes per evaluation, keyed by class (dst_i: the i-th pass)
@@ -657,7 +662,8 @@ def run_gpu(args, rank, world, local_rank):
                     "particle_steps_per_step": work,
                     "l2": "working set %.2f GB > 129 MB L2, no flush" % (ws_bytes / 1e9),
                     "parallelism": "boxes split over %d GPU(s)" % world,
-                    "dst": {"tc": "tcgen05 3xTF32", "tc4": "tcgen05 4xTF32", "simt": "FP32 CUDA cores"}[args.dst]}),
+                    "dst": {"tc": "tcgen05 3xTF32, six passes", "tc4": "tcgen05 4xTF32, six passes",
+                            "tc3": "tcgen05 3xTF32, three passes", "simt": "FP32 CUDA cores"}[args.dst]}),
                 "gpu_launches": int(launches * args.steps), "clocks": clk,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e}
         if per_tile is not None:
@@ -690,12 +696,17 @@ def deposit_choice(sc, st):
 def dst_choice(sc, st):
     """The Poisson-solve form in use and, under the autotuner, the candidates it timed (ms per
     solve of all boxes; both forms meet the accuracy bound)."""
-    names = {sc.SCOLA_DST_TC_3XTF32: "tensor cores, 3xTF32", sc.SCOLA_DST_TC_4XTF32: "tensor cores, 4xTF32",
-             sc.SCOLA_DST_SIMT: "FP32 CUDA cores"}
+    names = {sc.SCOLA_DST_TC_3XTF32: "tensor cores, 3xTF32, six passes", sc.SCOLA_DST_TC_4XTF32: "tensor cores, 4xTF32",
+             sc.SCOLA_DST_TC_3PASS: "tensor cores, 3xTF32, three passes", sc.SCOLA_DST_SIMT: "FP32 CUDA cores"}
     cand = st["ms_dst_candidates"]
+    order = ("tensor cores, 3xTF32, six passes", "FP32 CUDA cores", "tensor cores, 3xTF32, three passes")
     return {"kept": names.get(st["dst_form"], "not chosen"),
-            "candidates_ms": {n: round(t, 4) for n, t in zip(("tensor cores, 3xTF32", "FP32 CUDA cores"), cand)
-                              if t > 0}}
+            "candidates_ms": {n: round(t, 4) for n, t in zip(order, cand) if t > 0}}
+
+
+def dst_code(sc, name):
+    return {"auto": sc.SCOLA_DST_AUTO, "tc": sc.SCOLA_DST_TC_3XTF32, "tc4": sc.SCOLA_DST_TC_4XTF32,
+            "tc3": sc.SCOLA_DST_TC_3PASS, "simt": sc.SCOLA_DST_SIMT}[name]
 
 
 def main():

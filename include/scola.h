@@ -54,9 +54,14 @@ typedef enum scola_dst_variant {
     SCOLA_DST_SIMT = 0,          /* dense sine-matrix pencils on FP32 CUDA cores */
     SCOLA_DST_TC_3XTF32 = 1,     /* the same products on tcgen05 tensor cores, 3xTF32 split */
     SCOLA_DST_TC_4XTF32 = 3,     /* as 1, plus the lo x lo product (four TF32 products) */
-    SCOLA_DST_AUTO = 2           /* the faster of the 3xTF32 tensor-core and the FP32 forms, timed
-                                    once on the context's boxes before the first evolution (the
-                                    FP32 form alone where some Ng excludes the tensor cores) */
+    SCOLA_DST_TC_3PASS = 4,      /* the 3xTF32 products in three mesh passes instead of six: z
+                                    forward; every z-frequency plane transformed along y and x,
+                                    divided and transformed back in shared memory; z inverse.
+                                    Every Ng <= 96 with Ng % 4 == 0 (UNSUPPORTED otherwise) */
+    SCOLA_DST_AUTO = 2           /* the fastest of the tensor-core forms (six passes, and three
+                                    where every Ng allows it) and the FP32 form, timed once on
+                                    the context's boxes before the first evolution (the FP32 form
+                                    alone where some Ng excludes the tensor cores) */
 } scola_dst_variant;
 
 typedef enum scola_deposit_form {
@@ -206,8 +211,9 @@ typedef struct scola_stats {
     int32_t dst_form;             /* the Poisson-solve form in use (scola_dst_variant) once chosen:
                                      the requested one, or the autotuner's pick under AUTO
                                      (0 until the first scola_forward / scola_setup_boxes) */
-    double ms_dst_candidates[2];  /* AUTO: autotuner timings of one Poisson solve, tensor-core
-                                     and FP32 forms; 0 = not timed */
+    double ms_dst_candidates[3];  /* AUTO: autotuner timings of one Poisson solve: tensor cores
+                                     in six passes, FP32, tensor cores in three passes; 0 = not
+                                     timed */
 } scola_stats;
 
 /*

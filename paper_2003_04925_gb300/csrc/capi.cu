@@ -104,7 +104,8 @@ scola_status validate(const scola_params *p, std::vector<int32_t> &bufs, std::ve
         return SCOLA_ERR_UNSUPPORTED;
     }
     if (p->dst_variant != SCOLA_DST_SIMT && p->dst_variant != SCOLA_DST_TC_3XTF32 &&
-        p->dst_variant != SCOLA_DST_TC_4XTF32 && p->dst_variant != SCOLA_DST_AUTO)
+        p->dst_variant != SCOLA_DST_TC_4XTF32 && p->dst_variant != SCOLA_DST_TC_3PASS &&
+        p->dst_variant != SCOLA_DST_AUTO)
         return invalid("unknown dst_variant");
     if (p->batch_mode != SCOLA_BATCH_ALL && p->batch_mode != SCOLA_BATCH_PER_TILE)
         return invalid("unknown batch_mode");
@@ -147,7 +148,7 @@ scola_status validate(const scola_params *p, std::vector<int32_t> &bufs, std::ve
         const int ng = p->Ng ? p->Ng : p->mesh_ratio * nsc;
         if (ng < nsc) return invalid("Ng must be >= Np,sCOLA (Sec. 3.3, C.3)");
         const bool tc_form = p->dst_variant == SCOLA_DST_TC_3XTF32 || p->dst_variant == SCOLA_DST_TC_4XTF32 ||
-                             p->dst_variant == SCOLA_DST_AUTO;
+                             p->dst_variant == SCOLA_DST_TC_3PASS || p->dst_variant == SCOLA_DST_AUTO;
         if (for_kernels && (ng > kMaxNg || (!tc_form && ng > kMaxNgSimt))) {
             set_error("Ng > 256 is not built (Ng > 222 only with a tensor-core DST form)");
             return SCOLA_ERR_UNSUPPORTED;
@@ -206,6 +207,10 @@ struct BatchPlan {
     std::vector<int> pbeg, shbeg, zbeg, cbeg, mbeg, sbbeg, tile_beg, tile_end, dep_groups;
     std::vector<long long> group_first;                // per tensor-core group: first tile, count
     std::vector<int> group_ntiles;
+    std::vector<Chunk> planes;                         // three-pass solve: (box, plane) per group
+    std::vector<long long> group_plane_first;
+    std::vector<int> group_nplanes, plane_beg;
+    long long n_planes = 0;
     long long P = 0, M = 0, MP = 0, SH = 0, NK = 0, dep_cells = 0;
 };
 
@@ -247,10 +252,13 @@ void plan_batch(const scola_ctx *c, const std::vector<BoxGeom> &tiling_geo, int 
         B.ty = (gb / p.Ntiles) % p.Ntiles;
         B.tz = gb % p.Ntiles;
         // interior meshes start at multiples of lcm(64, Ng): aligned, and a whole number of
-        // Ng-float rows from the buffer start (the tensor-core passes address them as rows)
+        // Ng-float rows from the buffer start (the tensor-core passes address them as rows);
+        // where the three-pass solve may run, a whole number of Ng^2-float planes (its z
+        // inverse addresses the mesh as planes)
         {
+            const long long unit = c->tc3_ok ? (long long)g.ng * g.ng : g.ng;
             long long q = 64;
-            while (q % g.ng) q += 64;
+            while (q % unit) q += 64;
             M = (M + q - 1) / q * q;
         }
         B.p_off = P;
@@ -338,6 +346,21 @@ void plan_batch(const scola_ctx *c, const std::vector<BoxGeom> &tiling_geo, int 
         }
         bp.group_ntiles.push_back((int)(bp.n_tct - bp.group_first.back()));
     }
+    // plane items of the three-pass solve: per Ng group, every plane of each box
+    bp.plane_beg.assign(count, 0);
+    if (c->tc3_ok)
+        for (const TcGroup &G : c->tc_groups) {
+            bp.group_plane_first.push_back(bp.n_planes);
+            for (int b = 0; b < count; ++b) {
+                if (bp.geo[b].ng != G.Ng) continue;
+                bp.plane_beg[b] = (int)bp.n_planes;
+                for (int n = 0; n < G.Ng; ++n) {
+                    if (lists) bp.planes.push_back({b, n});
+                    ++bp.n_planes;
+                }
+            }
+            bp.group_nplanes.push_back((int)(bp.n_planes - bp.group_plane_first.back()));
+        }
     bp.P = P;
     bp.M = M;
     bp.MP = MP;
@@ -419,6 +442,7 @@ scola_status bind_batch(scola_ctx *c, int k, bool force = false) {
     CS(put(c->ppchunks, bp.ppch));
     CS(put(c->sbricks, bp.sbr));
     if (c->use_tc) CS(put(c->tc_tiles, bp.tct));
+    if (c->tc3_ok) CS(put(c->tc_planes, bp.planes));
     c->nboxes = count;
     c->boxes_h = bp.boxes;
     c->n_pchunks = (int)bp.n_pch;
@@ -441,7 +465,10 @@ scola_status bind_batch(scola_ctx *c, int k, bool force = false) {
     for (size_t g = 0; g < c->tc_groups.size(); ++g) {
         c->tc_groups[g].tiles = c->tc_tiles + bp.group_first[g];
         c->tc_groups[g].ntiles = bp.group_ntiles[g];
+        c->tc_groups[g].planes = c->tc3_ok ? c->tc_planes + bp.group_plane_first[g] : nullptr;
+        c->tc_groups[g].nplanes = c->tc3_ok ? bp.group_nplanes[g] : 0;
     }
+    c->tc_plane_beg = bp.plane_beg;
     c->P = bp.P;
     c->M = bp.M;
     c->MP = bp.MP;
@@ -616,13 +643,25 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &all_geo) {
     // (a mesh larger than the FP32 form takes leaves the tensor-core form alone)
     c->dst_auto = p.dst_variant == SCOLA_DST_AUTO && all_tc && c->max_ng <= kMaxNgSimt;
     c->use_tc = (p.dst_variant == SCOLA_DST_TC_3XTF32) || (p.dst_variant == SCOLA_DST_TC_4XTF32) ||
-                (p.dst_variant == SCOLA_DST_AUTO && all_tc);
+                (p.dst_variant == SCOLA_DST_TC_3PASS) || (p.dst_variant == SCOLA_DST_AUTO && all_tc);
     c->tc_lo_lo = p.dst_variant == SCOLA_DST_TC_4XTF32;
+    // the three-pass solve (plane pass, k_dst_plane.cu) where every Ng allows it
+    bool all_plane = true;
+    for (auto &kv : c->tbl_of) all_plane = all_plane && plane_supported(kv.first);
+    c->tc3_ok = c->use_tc && all_plane && (p.dst_variant == SCOLA_DST_TC_3PASS || p.dst_variant == SCOLA_DST_AUTO);
+    if (p.dst_variant == SCOLA_DST_TC_3PASS && !c->tc3_ok) {
+        set_error("the three-pass tensor-core solve needs every Ng <= 96 with Ng % 4 == 0");
+        return SCOLA_ERR_UNSUPPORTED;
+    }
+    c->tc3 = p.dst_variant == SCOLA_DST_TC_3PASS;
     if (c->use_tc) {
         for (auto &kv : c->tbl_of) {
             TcGroup G;
             G.Ng = kv.first;
             G.nstage = tc_plan_stages(G.Ng, G.Npad, G.nkc);
+            G.nstage_zm = tc_plan_stages(G.Ng, G.Npad, G.nkc, true);
+            G.planes = nullptr;
+            G.nplanes = 0;
             G.lam_off = c->tables_h[kv.second].lam_off;
             G.s_off = (long long)arena.size();
             G.tiles = nullptr;
@@ -718,7 +757,8 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &all_geo) {
 
     // every batch's layout (box descriptors kept; list lengths and arena sizes maxed)
     long long P = 0, M = 0, MP = 0, SH = 0, NK = 0, dep = 0;
-    long long L_pch = 0, L_tch = 0, L_shch = 0, L_zit = 0, L_cit = 0, L_mch = 0, L_ppch = 0, L_sbr = 0, L_tct = 0;
+    long long L_pch = 0, L_tch = 0, L_shch = 0, L_zit = 0, L_cit = 0, L_mch = 0, L_ppch = 0, L_sbr = 0, L_tct = 0,
+              L_pl = 0;
     int max_count = 0;
     for (int k = 0; k < nbatch; ++k) {
         BatchPlan bp;
@@ -740,6 +780,7 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &all_geo) {
         L_ppch = std::max(L_ppch, bp.n_ppch);
         L_sbr = std::max(L_sbr, bp.n_sbr);
         L_tct = std::max(L_tct, bp.n_tct);
+        L_pl = std::max(L_pl, bp.n_planes);
         max_count = std::max(max_count, n);
         c->P_all += bp.P;
         for (const BoxGeom &g : bp.geo) c->M_all += (long long)g.ng * g.ng * g.ng;
@@ -759,6 +800,7 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &all_geo) {
     CS(dev_alloc(&c->ppchunks, L_ppch));
     CS(dev_alloc(&c->sbricks, L_sbr));
     if (c->use_tc) CS(dev_alloc(&c->tc_tiles, L_tct));
+    if (c->tc3_ok) CS(dev_alloc(&c->tc_planes, L_pl));
     c->cap_P = P;
     c->cap_M = M;
     c->cap_MP = MP;
@@ -1068,22 +1110,27 @@ scola_status autotune_deposit(scola_ctx *c) {
 scola_status autotune_dst(scola_ctx *c) {
     if (c->dst_tuned) return SCOLA_OK;
     if (!c->dst_auto) {
-        c->stats.dst_form = c->use_tc ? (c->tc_lo_lo ? SCOLA_DST_TC_4XTF32 : SCOLA_DST_TC_3XTF32) : SCOLA_DST_SIMT;
+        c->stats.dst_form = c->use_tc ? (c->tc3 ? SCOLA_DST_TC_3PASS : c->tc_lo_lo ? SCOLA_DST_TC_4XTF32
+                                                                                    : SCOLA_DST_TC_3XTF32)
+                                      : SCOLA_DST_SIMT;
         c->dst_tuned = true;
         return SCOLA_OK;
     }
+    // candidates: tensor cores in six passes, FP32 CUDA cores, tensor cores in three passes
     const long long launches = c->launches;
-    float t[2] = {-1.0f, -1.0f};
+    float t[3] = {-1.0f, -1.0f, -1.0f};
     {
         std::unique_ptr<BoxView> view;
         if (c->prm.batch_mode == SCOLA_BATCH_PER_TILE) view.reset(new BoxView(c, 0));
-        for (int q = 0; q < 2; ++q) {
-            c->use_tc = q == 0;
+        for (int q = 0; q < 3; ++q) {
+            if (q == 2 && !c->tc3_ok) continue;
+            c->use_tc = q != 1;
+            c->tc3 = q == 2;
+            static const char *names[3] = {"tensor-core form: ", "FP32 form: ", "three-pass tensor-core form: "};
             cudaError_t e = launch_poisson(*c);
             if (e == cudaSuccess) e = c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize();
             if (e != cudaSuccess) {
-                set_error(std::string("Poisson-solve autotuner, ") + (q == 0 ? "tensor-core form: " : "FP32 form: ") +
-                          cudaGetErrorString(e));
+                set_error(std::string("Poisson-solve autotuner, ") + names[q] + cudaGetErrorString(e));
                 return SCOLA_ERR_CUDA;
             }
             for (int rep = 0; rep < 3; ++rep) {
@@ -1097,10 +1144,12 @@ scola_status autotune_dst(scola_ctx *c) {
             }
         }
     }
-    c->use_tc = t[0] <= t[1];
-    c->stats.ms_dst_candidates[0] = t[0];
-    c->stats.ms_dst_candidates[1] = t[1];
-    c->stats.dst_form = c->use_tc ? SCOLA_DST_TC_3XTF32 : SCOLA_DST_SIMT;
+    int best = t[0] <= t[1] ? 0 : 1;
+    if (t[2] >= 0.0f && t[2] < t[best]) best = 2;
+    c->use_tc = best != 1;
+    c->tc3 = best == 2;
+    for (int q = 0; q < 3; ++q) c->stats.ms_dst_candidates[q] = t[q] < 0.0f ? 0.0 : t[q];
+    c->stats.dst_form = best == 0 ? SCOLA_DST_TC_3XTF32 : best == 1 ? SCOLA_DST_SIMT : SCOLA_DST_TC_3PASS;
     c->launches = launches;
     c->dst_tuned = true;
     return SCOLA_OK;
@@ -1354,7 +1403,7 @@ void scola_destroy(scola_ctx *c) {
         cufftDestroy(c->tc_c2r);
     }
     void *ptrs[] = {c->boxes, c->all_boxes, c->all_coef, c->all_coefL, c->coef, c->coefL, c->tables, c->table_arena, c->pchunks, c->tchunks, c->shchunks,
-                    c->zitems, c->citems, c->mchunks, c->ppchunks, c->tc_tiles, c->dev_err, c->ckpt, c->seg, c->fin,
+                    c->zitems, c->citems, c->mchunks, c->ppchunks, c->tc_tiles, c->tc_planes, c->dev_err, c->ckpt, c->seg, c->fin,
                     c->adj, c->lamG, c->lam_phi_pad, c->adj_in, c->adj_out, c->lam_shell, c->lamPsi1,
                     c->lamPsi2, c->lam_phi1, c->lam_phi2, c->d2, c->lam_d2, c->part, c->dep_acc, c->kcount,
                     c->koffs, c->kcursor, c->sentries, c->sbricks,

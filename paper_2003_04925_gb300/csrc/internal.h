@@ -61,8 +61,11 @@ struct DstTable {                 // offsets into the device table arena (floats
 
 struct TcGroup {                  // one tensor-core DST launch group: boxes sharing Ng
     int Ng, Npad, nkc, nstage;
+    int nstage_zm;                // stages of the plane-major z inverse (three-pass solve)
     Chunk *tiles;                 // device (box, kTcTileRows-row tile of the box)
     int ntiles;
+    Chunk *planes;                // device (box, plane n) items of the plane pass (three-pass solve)
+    int nplanes;
     long long s_off;              // FP32 sine matrix Npad x (32 nkc) in table_arena
     long long lam_off;            // eigenvalues in table_arena
 };
@@ -138,6 +141,10 @@ struct Ctx {
     std::vector<TcGroup> tc_groups;
     Chunk *tc_tiles = nullptr;
     std::vector<int> tc_tile_beg, tc_tile_end;        // each box's tile range in tc_tiles
+    bool tc3 = false;                                 // the three-pass tensor-core solve
+    bool tc3_ok = false;                              // every Ng allows it (plane_supported)
+    Chunk *tc_planes = nullptr;                       // plane items of every group
+    std::vector<int> tc_plane_beg;                    // each box's first plane item
     int view_box = -1;                                // >= 0: launches restricted to this box
     int *dev_err = nullptr;                           // set by kernels whose bounded waits expired
     float *part = nullptr;
@@ -232,7 +239,10 @@ cudaError_t launch_deposit_sorted(Ctx &c, const float *s, long long stride, floa
 cudaError_t clear_key_counts(Ctx &c);
 cudaError_t init_pm_kernels(Ctx &c);
 cudaError_t init_deposit_kernels();
-int tc_plan_stages(int Ng, int &Npad, int &nkc);
+int tc_plan_stages(int Ng, int &Npad, int &nkc, bool zm = false);
+bool plane_supported(int Ng);    // the three-pass solve: Ng <= 96, Ng % 4 == 0
+cudaError_t init_plane_kernel();
+cudaError_t launch_plane_pass(Ctx &c, const std::vector<TcGroup> &groups, const float *in, float *out);
 bool tc_supported(int Ng);
 bool tc_folded(int Ng);          // Ng > 128: the mirror-symmetric half-size form
 bool tc_ragged(int Ng);          // rows not 16-byte pitched for TMA: plain loads and stores

@@ -1,0 +1,402 @@
+// Dirichlet Poisson solve in three mesh passes on the tensor cores: the plane pass
+// (App. C, Eqs. 63-71).
+//
+// The solve of a box mesh with Ng <= 96 and Ng % 4 == 0 runs as
+//   pass 1  z+     the one-axis pass of k_dst_tc.cu:   src[i][j][k] -> W1[n][i][j]
+//   pass 2  plane  this kernel: every z-frequency plane n of W1, held in shared memory, is
+//                  transformed along y and x, divided by lambda_l + lambda_m + lambda_n, and
+//                  transformed back along x and y                -> W2[n][i'][j']
+//   pass 3  z-     the one-axis pass reading W2 plane by plane (k_dst_tc.cu, P_ZM), writing
+//                  the padded potential in its natural [i][j][k] layout
+// so the mesh crosses device memory three times per solve instead of six.
+//
+// Each step is D = S X^T with the sine matrix S (S_kn = sin(pi (k+1)(n+1)/(Ng+1))) as the
+// M = 128 operand, resident in shared memory, and the plane's Ng rows as the N operand,
+// split into TF32 hi and lo parts (3xTF32, or four products with lo x lo).  TMEM lane u of
+// D holds output index u of every row, so one epilogue thread per lane owns one row of the
+// next step's operand: it reads its lane, splits it and writes it straight into the K-major
+// operand in shared memory, and the next step contracts the other axis:
+//   step 1  rows i,   K = j   ->  lanes m  (y frequency), columns i
+//   step 2  rows m,   K = i   ->  lanes l  (x frequency), columns m   (then / lambda sum)
+//   step 3  rows l,   K = m   ->  lanes j' (y),           columns l
+//   step 4  rows j',  K = l   ->  lanes i' (x),           columns j'  -> row i' of W2[n]
+// An N = 96 TF32 MMA takes ~56 cycles against 128 at N = 256 (the pipe's rate per column,
+// bounded by the operand reads from shared memory), so the plane steps keep the tensor
+// pipe at ~85 % of its rate.  Two planes are in flight per CTA (two operand buffers, two
+// accumulators): while the epilogue turns one plane's accumulator into its next operand,
+// the tensor cores run the other plane's step.
+//
+// One persistent CTA per SM, 10 warps:
+//   warps 0-7  split each loaded plane into hi/lo; the epilogues of the four steps
+//   warp 8     TMEM allocation; lane 0 issues tcgen05.mma and tcgen05.commit
+//   warp 9     lane 0 issues the tensor copies of each plane (Ng/16 boxes of 16 x Npad)
+// The CTAs of a launch are split among the Ng groups of the boxes (as in k_dst_tc.cu).
+// Every wait is bounded (about 2 s); on expiry the CTA raises the error flag, stops
+// issuing, waits (bounded) for its issued copies and MMAs, frees TMEM and returns.
+#include <cuda.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "device_util.cuh"
+#include "tc_util.cuh"
+
+namespace scola {
+
+namespace {
+
+using namespace tc;
+
+constexpr int kPlThreads = 320;
+constexpr int kPlGroups = 4;
+
+struct PlaneGroupArgs {
+    CUtensorMap in_map;          // W1 as rows of Ng floats: boxes of 16 x Npad, 64-byte swizzle
+    const Chunk *items;          // (box, plane n)
+    const float *S;              // sine matrix rows, Ng x (32 nka) (the one-axis passes' table)
+    const float *lam;            // Dirichlet eigenvalues, Ng
+    int nitems, Ng, Npad, nka, nkb;
+    int cta0, nctas;
+};
+
+struct PlaneArgs {
+    PlaneGroupArgs grp[kPlGroups];
+    int ngroups;
+    const BoxDesc *boxes;
+    float *out;
+    int *err;
+    int lo_lo;
+};
+
+__global__ void __launch_bounds__(kPlThreads, 1) k_dst_plane(const __grid_constant__ PlaneArgs A) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    int gi = 0;
+    while (gi + 1 < A.ngroups && (int)blockIdx.x >= A.grp[gi + 1].cta0) ++gi;
+    const PlaneGroupArgs &G = A.grp[gi];
+    const int bid = (int)blockIdx.x - G.cta0, nbid = G.nctas;
+    const int Ng = G.Ng, Npad = G.Npad, nka = G.nka, nkb = G.nkb;
+    const uint32_t sch = (uint32_t)((Ng + 7) / 8) * 1024;      // one sine chunk (32 K), hi or lo
+    const uint32_t bhalf = (uint32_t)nkb * Npad * 64;          // one operand, hi or lo
+    // The M = 128 operand reads 128 rows from each sine chunk; rows >= Ng come from what
+    // follows and only feed TMEM lanes that the epilogue discards.
+    unsigned char *S_hi = base;
+    unsigned char *S_lo = base + nka * sch;
+    unsigned char *bufs = base + 2 * nka * sch;                // buffer e: hi, then lo
+    uint64_t *bars = (uint64_t *)(bufs + 4 * (size_t)bhalf);
+    uint64_t *loaded = bars;          // the plane's tensor copies have landed
+    uint64_t *opready = bars + 2;     // the next step's operand is written (256 arrivals)
+    uint64_t *accfull = bars + 4;     // the step's MMAs are complete
+    uint64_t *bufempty = bars + 6;    // step 4 is complete: the buffer may take the next plane
+    uint64_t *drain = bars + 8;
+    uint32_t *tmem_slot = (uint32_t *)(bars + 9);
+    volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+    float *lam = (float *)(tmem_slot + 4);
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+
+    // ---- set-up: S (hi/lo split, swizzled), eigenvalues, barriers, tensor memory
+    const int Kp = nka * 32;
+    for (int q = tid; q < Ng * Kp; q += kPlThreads) {
+        const int n = q / Kp, k = q % Kp;
+        const float sv = G.S[q];
+        const float hi = tf32_rn(sv);
+        const uint32_t off = (uint32_t)(k / 32) * sch + sw128_offset(n, k % 32);
+        *(float *)(S_hi + off) = hi;
+        *(float *)(S_lo + off) = tf32_rn(sv - hi);
+    }
+    for (int q = tid; q < Ng; q += kPlThreads) lam[q] = G.lam[q];
+    for (int q = tid; q < (int)(bhalf / 4); q += kPlThreads) {     // clean operand padding
+        reinterpret_cast<float4 *>(bufs)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const long long my_items = G.nitems > bid ? (G.nitems - 1 - bid) / nbid + 1 : 0;
+    if (tid == 0) {
+        for (int e = 0; e < 2; ++e) {
+            mbar_init(&loaded[e], 1);
+            mbar_init(&opready[e], 256);
+            mbar_init(&accfull[e], 1);
+            mbar_init(&bufempty[e], 1);
+        }
+        mbar_init(drain, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 8) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(256));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const long long Ng2 = (long long)Ng * Ng;
+    const long long npairs = (my_items + 1) / 2;
+
+    if (warp == 9) {
+        // ---------------------------------------------------------------- tensor copies
+        // plane p goes to buffer p % 2 once step 4 of plane p - 2 has finished with it; on an
+        // abort, wait (bounded) for the copies already issued before the CTA may exit
+        if (lane == 0) {
+            long long p = 0;
+            for (; p < my_items && !*abort_flag; ++p) {
+                const int e = (int)(p & 1);
+                const long long j = p >> 1;
+                if (j > 0 && !mbar_wait(&bufempty[e], (uint32_t)((j - 1) & 1), abort_flag)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                const Chunk it = G.items[bid + p * nbid];
+                const long long m_off = A.boxes[it.box].m_off;
+                const int y = (int)(m_off / Ng + (long long)it.start * Ng);     // row (n, i = 0)
+                unsigned char *hi = bufs + (size_t)e * 2 * bhalf;
+                mbar_arrive_expect_tx(&loaded[e], bhalf);
+                for (int c = 0; c < nkb; ++c)
+                    tma_load_2d(smem_u32(hi + (size_t)c * Npad * 64), &G.in_map, c * 16, y, &loaded[e]);
+            }
+            if (*abort_flag) {
+                const unsigned long long t0 = now_ns();
+                for (long long q = p - 2 > 0 ? p - 2 : 0; q < p; ++q)
+                    while (!mbar_try_wait(&loaded[q & 1], (uint32_t)((q >> 1) & 1)) && now_ns() - t0 < kWaitNs) {
+                    }
+            }
+        }
+    } else if (warp == 8) {
+        // ---------------------------------------------------------------- MMA issuer
+        // order: for each pair of planes, steps 1..4, each step for both planes
+        if (lane == 0) {
+            const uint32_t idesc = idesc_tf32(128, Npad);
+            const uint32_t shi = smem_u32(S_hi), slo = smem_u32(S_lo);
+            bool ok = true;
+            for (long long q = 0; q < npairs && ok && !*abort_flag; ++q)
+                for (int s = 1; s <= 4 && ok; ++s)
+                    for (int e = 0; e < 2; ++e) {
+                        if (2 * q + e >= my_items) break;
+                        if (!mbar_wait(&opready[e], (uint32_t)((s - 1) & 1), abort_flag)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t d = tmem + (uint32_t)(e * 128);
+                        const uint32_t bh = smem_u32(bufs + (size_t)e * 2 * bhalf), bl = bh + bhalf;
+                        for (int kg = 0; kg < Ng; kg += 8) {
+                            const uint32_t ao = (uint32_t)(kg / 32) * sch + (uint32_t)((kg % 32) / 8) * 32;
+                            const uint32_t bo = (uint32_t)(kg / 16) * Npad * 64 + (uint32_t)((kg % 16) / 8) * 32;
+                            const uint64_t ahi = sw128_desc(shi + ao), alo = sw128_desc(slo + ao);
+                            const uint64_t bhi = sw64_desc(bh + bo), blo = sw64_desc(bl + bo);
+                            mma_tf32(d, ahi, bhi, idesc, kg > 0 ? 1u : 0u);
+                            mma_tf32(d, ahi, blo, idesc, 1);
+                            mma_tf32(d, alo, bhi, idesc, 1);
+                            if (A.lo_lo) mma_tf32(d, alo, blo, idesc, 1);
+                        }
+                        mma_commit(&accfull[e]);
+                        if (s == 4) mma_commit(&bufempty[e]);
+                    }
+            if (!ok) *abort_flag = 1;
+        }
+    } else {
+        // ---------------------------------------------------------------- warps 0-7
+        // warp w reads TMEM lanes 32 (w & 3) + lane (the output index of its row) and the
+        // 16-column chunks c = (w >> 2), (w >> 2) + 2, ... of the accumulator
+        const int lq = warp & 3, hsel = warp >> 2;
+        const int row = lq * 32 + lane;
+        bool ok = true;
+        for (long long q = 0; q < npairs && ok && !*abort_flag; ++q) {
+            // split the pair's loaded planes in place: hi over the copy, lo into the other half;
+            // rows >= Ng (the next plane's rows brought by the box) are cleared
+            for (int e = 0; e < 2; ++e) {
+                if (2 * q + e >= my_items) break;
+                if (!mbar_wait(&loaded[e], (uint32_t)(q & 1), abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                unsigned char *hi = bufs + (size_t)e * 2 * bhalf, *lo = hi + bhalf;
+                const int units = nkb * Npad * 4;
+                for (int u = tid; u < units; u += 256) {
+                    const int c = u / (Npad * 4), rem = u % (Npad * 4);
+                    const int r = rem >> 2, qq = rem & 3;
+                    const uint32_t off = (uint32_t)c * Npad * 64 + sw64_offset(r, 4 * qq);
+                    float4 v = *reinterpret_cast<const float4 *>(hi + off);
+                    if (r >= Ng) v = make_float4(0.f, 0.f, 0.f, 0.f);
+                    const float4 h = make_float4(tf32_rn(v.x), tf32_rn(v.y), tf32_rn(v.z), tf32_rn(v.w));
+                    *reinterpret_cast<float4 *>(hi + off) = h;
+                    *reinterpret_cast<float4 *>(lo + off) =
+                        make_float4(tf32_rn(v.x - h.x), tf32_rn(v.y - h.y), tf32_rn(v.z - h.z), tf32_rn(v.w - h.w));
+                }
+                fence_proxy_async();
+                mbar_arrive(&opready[e]);
+            }
+            for (int s = 1; s <= 4 && ok; ++s)
+                for (int e = 0; e < 2; ++e) {
+                    const long long p = 2 * q + e;
+                    if (p >= my_items) break;
+                    if (!mbar_wait(&accfull[e], (uint32_t)((s - 1) & 1), abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const Chunk it = G.items[bid + p * nbid];
+                    const int n = it.start;
+                    unsigned char *hi = bufs + (size_t)e * 2 * bhalf, *lo = hi + bhalf;
+                    const uint32_t tb = tmem + (uint32_t)(e * 128) + ((uint32_t)(lq * 32) << 16);
+                    const long long m_off = s == 4 ? A.boxes[it.box].m_off : 0;
+                    for (int c = hsel; c < nkb; c += 2) {
+                        float v[16];
+                        tmem_ld16_issue(tb + (uint32_t)(c * 16), v);
+                        tmem_ld_wait();
+                        tmem_regs_ready(v);
+                        if (s < 4) {
+                            // this lane's row of the next operand, columns 16 c .. 16 c + 15
+                            if (row < Npad) {
+#pragma unroll
+                                for (int qq = 0; qq < 4; ++qq) {
+                                    float x[4];
+#pragma unroll
+                                    for (int t = 0; t < 4; ++t) {
+                                        const int col = c * 16 + 4 * qq + t;
+                                        float y = (row < Ng && col < Ng) ? v[4 * qq + t] : 0.0f;
+                                        if (s == 2 && row < Ng && col < Ng)
+                                            y = __fdividef(y, lam[row] + lam[col] + lam[n]);
+                                        x[t] = y;
+                                    }
+                                    const float4 h = make_float4(tf32_rn(x[0]), tf32_rn(x[1]), tf32_rn(x[2]), tf32_rn(x[3]));
+                                    const uint32_t off = (uint32_t)c * Npad * 64 + sw64_offset(row, 4 * qq);
+                                    *reinterpret_cast<float4 *>(hi + off) = h;
+                                    *reinterpret_cast<float4 *>(lo + off) = make_float4(
+                                        tf32_rn(x[0] - h.x), tf32_rn(x[1] - h.y), tf32_rn(x[2] - h.z), tf32_rn(x[3] - h.w));
+                                }
+                            }
+                        } else if (row < Ng) {
+                            // row i' of W2[n]: columns j' = 16 c .. (Ng % 4 == 0: whole float4s)
+                            float *dst = A.out + m_off + (long long)n * Ng2 + (long long)row * Ng;
+#pragma unroll
+                            for (int qq = 0; qq < 4; ++qq) {
+                                const int col = c * 16 + 4 * qq;
+                                if (col < Ng)
+                                    *reinterpret_cast<float4 *>(dst + col) =
+                                        make_float4(v[4 * qq], v[4 * qq + 1], v[4 * qq + 2], v[4 * qq + 3]);
+                            }
+                        }
+                    }
+                    if (s < 4) fence_proxy_async();
+                    tc_fence_before();
+                    if (s < 4) mbar_arrive(&opready[e]);
+                }
+        }
+        if (!ok) *abort_flag = 1;
+    }
+
+    // ---- tear-down: every role has left its loop; drain, then free tensor memory
+    if (warp == 8 && lane == 0 && *abort_flag) {
+        mma_commit(drain);
+        const unsigned long long t0 = now_ns();
+        while (!mbar_try_wait(drain, 0) && now_ns() - t0 < kWaitNs) {
+        }
+    }
+    if (*abort_flag && tid == 0) atomicOr(A.err, 1);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 8) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
+}
+
+size_t plane_smem_bytes(int Ng, int Npad, int nka, int nkb) {
+    const size_t sch = (size_t)((Ng + 7) / 8) * 1024;
+    return 1024 + 2 * (size_t)nka * sch + 4 * (size_t)nkb * Npad * 64 + 9 * 8 + 16 + (size_t)Ng * 4 + 64;
+}
+
+constexpr size_t kPlSmemBudget = 227 * 1024;
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// W1 as a 2D tensor of rows of Ng floats, boxes of 16 x Npad with the 64-byte swizzle of
+// the MMA's K-major operand.
+cudaError_t plane_map(Ctx &c, const float *buf, int Ng, int Npad, CUtensorMap *out) {
+    static EncodeTiledFn encode = nullptr;
+    if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return e != cudaSuccess ? e : cudaErrorNotSupported;
+        encode = (EncodeTiledFn)fn;
+    }
+    const cuuint64_t dims[2] = {(cuuint64_t)Ng, (cuuint64_t)(c.M / Ng)};
+    const cuuint64_t strides[1] = {(cuuint64_t)Ng * sizeof(float)};
+    const cuuint32_t box[2] = {16u, (cuuint32_t)Npad};
+    const cuuint32_t estr[2] = {1, 1};
+    if (encode(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(buf), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorInvalidValue;
+    return cudaSuccess;
+}
+
+}  // namespace
+
+bool plane_supported(int Ng) {
+    if (Ng < 8 || Ng > 96 || Ng % 4 != 0) return false;
+    const int Npad = (Ng + 15) / 16 * 16, nka = (Ng + 31) / 32, nkb = (Ng + 15) / 16;
+    return plane_smem_bytes(Ng, Npad, nka, nkb) <= kPlSmemBudget;
+}
+
+cudaError_t init_plane_kernel() {
+    return cudaFuncSetAttribute(k_dst_plane, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPlSmemBudget);
+}
+
+// The plane pass over the given Ng groups (at most kPlGroups per launch): items are (box,
+// plane) pairs of every box of each group; the persistent grid is split among the groups in
+// proportion to their work (planes x Ng^2).
+cudaError_t launch_plane_pass(Ctx &c, const std::vector<TcGroup> &groups, const float *in, float *out) {
+    for (size_t g0 = 0; g0 < groups.size(); g0 += kPlGroups) {
+        const int ng = (int)std::min(groups.size() - g0, (size_t)kPlGroups);
+        PlaneArgs a;
+        std::memset(&a, 0, sizeof(a));
+        double total = 0;
+        std::vector<double> work(ng);
+        for (int g = 0; g < ng; ++g) {
+            const TcGroup &G = groups[g0 + g];
+            work[g] = (double)G.nplanes * G.Ng * G.Ng;
+            total += work[g];
+        }
+        int cta0 = 0;
+        size_t smem = 0;
+        for (int g = 0; g < ng; ++g) {
+            const TcGroup &G = groups[g0 + g];
+            PlaneGroupArgs &P = a.grp[g];
+            P.Ng = G.Ng;
+            P.Npad = (G.Ng + 15) / 16 * 16;
+            P.nka = G.nkc;
+            P.nkb = (G.Ng + 15) / 16;
+            cudaError_t e = plane_map(c, in, P.Ng, P.Npad, &P.in_map);
+            if (e != cudaSuccess) return e;
+            P.items = G.planes;
+            P.nitems = G.nplanes;
+            P.S = c.table_arena + G.s_off;
+            P.lam = c.table_arena + G.lam_off;
+            int n = (int)(c.num_sms * work[g] / std::max(total, 1.0));
+            n = std::max(1, std::min(n, std::max(1, G.nplanes)));
+            if (g == ng - 1) n = std::max(1, std::min(std::max(1, c.num_sms - cta0), std::max(1, G.nplanes)));
+            P.cta0 = cta0;
+            P.nctas = n;
+            cta0 += n;
+            smem = std::max(smem, plane_smem_bytes(P.Ng, P.Npad, P.nka, P.nkb));
+        }
+        a.ngroups = ng;
+        a.boxes = c.boxes;
+        a.out = out;
+        a.err = c.dev_err;
+        a.lo_lo = c.tc_lo_lo ? 1 : 0;
+        k_dst_plane<<<cta0, kPlThreads, smem, c.stream>>>(a);
+        ++c.launches;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace scola

@@ -89,7 +89,16 @@ constexpr int kTmemCols = 2 * kTN;   // double-buffered accumulator
 // Per epilogue warp: a 32 x 33 float block for transposing 32 columns x 32 rows.
 constexpr int kXposeBytes = 32 * 33 * 4;
 
-enum TcPass { P_F = 1, P_XF = 2, P_ZI = 3, P_YI = 4, P_XI = 5 };   // P_F: z+ and y+
+enum TcPass { P_F = 1, P_XF = 2, P_ZI = 3, P_YI = 4, P_XI = 5, P_ZM = 6 };   // P_F: z+ and y+
+// P_ZM: the z inverse of the three-pass solve (k_dst_plane.cu), reading W2[n][i][j] plane by
+// plane: a tile is 256 consecutive cells q = (i, j) of the planes, its K chunk 16 planes n;
+// the tensor copy brings the [16 n][256 q] box unswizzled, the converters transpose it into
+// the K-major operand while splitting it, and the epilogue writes the padded potential in
+// its natural layout, one TMEM lane (output k) per consecutive float, so 32 lanes store 128
+// contiguous bytes.
+
+// Stage bytes of a pass: hi and lo halves (and the untransposed copy for P_ZM).
+__host__ __device__ constexpr int stage_bytes(int pass) { return (pass == P_ZM ? 3 : 2) * kHalfBytes; }
 
 // Per-CTA cache of the tiles a CTA processes (the first kTileCache of them): the box
 // offsets and the first row, so that the producer and the epilogue need no dependent
@@ -149,9 +158,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(const __grid_constant__ 
     // follows (the next chunk, or the stages) and only feed TMEM lanes that are never read.
     unsigned char *S_hi = base;
     unsigned char *S_lo = base + nka * sch;
+    constexpr int SB = stage_bytes(PASS);
     unsigned char *stages = base + 2 * nka * sch;
-    float *xpose = (float *)(stages + (size_t)NST * kStageBytes);     // 8 x kXposeBytes
-    uint64_t *bars = (uint64_t *)((unsigned char *)xpose + 8 * kXposeBytes);
+    float *xpose = (float *)(stages + (size_t)NST * SB);              // 8 x kXposeBytes (not P_ZM)
+    uint64_t *bars = (uint64_t *)((unsigned char *)xpose + (PASS == P_ZM ? 0 : 8 * kXposeBytes));
     uint64_t *full = bars;                 // converted (MMA may read the stage)
     uint64_t *empty = bars + NST;          // consumed (the stage may be reloaded)
     uint64_t *loaded = bars + 2 * NST;     // the tensor copy into the stage has landed
@@ -234,8 +244,31 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(const __grid_constant__ 
         const float sgn = parity ? -1.0f : 1.0f;
         for (long long h = 0; h < nchunks && !*abort_flag; ++h) {
             const int s = (int)(h % NST);
-            unsigned char *xh = stages + (size_t)s * kStageBytes;
-            unsigned char *xl = stages + (size_t)s * kStageBytes + kHalfBytes;
+            unsigned char *xh = stages + (size_t)s * SB;
+            unsigned char *xl = stages + (size_t)s * SB + kHalfBytes;
+            if (PASS == P_ZM) {
+                // transpose the [16 n][256 q] copy into the K-major operand: thread pt owns
+                // row (cell) pt; consecutive threads read consecutive floats of each n row
+                if (!mbar_wait(&loaded[s], (uint32_t)((h / NST) & 1), abort_flag)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                const float *raw = reinterpret_cast<const float *>(stages + (size_t)s * SB + 2 * kHalfBytes);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    float x[4];
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) x[t] = raw[(4 * u + t) * kTN + pt];
+                    const float4 hv = make_float4(tf32_rn(x[0]), tf32_rn(x[1]), tf32_rn(x[2]), tf32_rn(x[3]));
+                    const uint32_t off = sw64_offset(pt, 4 * u);
+                    *reinterpret_cast<float4 *>(xh + off) = hv;
+                    *reinterpret_cast<float4 *>(xl + off) = make_float4(
+                        tf32_rn(x[0] - hv.x), tf32_rn(x[1] - hv.y), tf32_rn(x[2] - hv.z), tf32_rn(x[3] - hv.w));
+                }
+                fence_proxy_async();
+                mbar_arrive(&full[s]);
+                continue;
+            }
             if (G.ragged) {
                 // the stage is free once the MMA has consumed the chunk before in it; then
                 // element (r, k) of the chunk (row r of the tile, column 16 cc + k) is read
@@ -337,6 +370,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(const __grid_constant__ 
                     break;
                 }
                 const TileInfo ti = tile_at(g / nkb);
+                if (PASS == P_ZM) {
+                    // planes 16 cc .. 16 cc + 15 of the box, cells row0 .. row0 + 255
+                    const int cc = (int)(g % nkb), y = (int)(ti.m_off / Ng2 + cc * kKB);
+                    mbar_arrive_expect_tx(&loaded[s], kHalfBytes);
+                    tma_load_2d(smem_u32(stages + (size_t)s * SB + 2 * kHalfBytes), &G.in_map, ti.row0, y, &loaded[s]);
+                    continue;
+                }
                 if (g % nkb == 0 && g / nkb + 1 < my_tiles) {
                     // the next tile's rows are one contiguous block: start bringing it into L2
                     const TileInfo tn = tile_at(g / nkb + 1);
@@ -345,9 +385,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(const __grid_constant__ 
                 }
                 const int cc = (int)(g % nkb), y = (int)(ti.m_off / Ng + ti.row0);
                 mbar_arrive_expect_tx(&loaded[s], FOLD ? 2 * kHalfBytes : kHalfBytes);
-                tma_load_2d(smem_u32(stages + (size_t)s * kStageBytes), &G.in_map, cc * kKB, y, &loaded[s]);
+                tma_load_2d(smem_u32(stages + (size_t)s * SB), &G.in_map, cc * kKB, y, &loaded[s]);
                 if (FOLD)   // the mirror chunk: columns Ng - 16 (cc + 1) .. Ng - 16 cc - 1
-                    tma_load_2d(smem_u32(stages + (size_t)s * kStageBytes + kHalfBytes), &G.in_map,
+                    tma_load_2d(smem_u32(stages + (size_t)s * SB + kHalfBytes), &G.in_map,
                                 Ng - (cc + 1) * kKB, y, &loaded[s]);
             }
             if (*abort_flag) {
@@ -388,7 +428,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(const __grid_constant__ 
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t xh = st0 + (uint32_t)s * kStageBytes, xl = xh + kHalfBytes;
+                    const uint32_t xh = st0 + (uint32_t)s * SB, xl = xh + kHalfBytes;
 #pragma unroll
                     for (int kk = 0; kk < kKB / 8; ++kk) {
                         const int kg = c * kKB + kk * 8;
@@ -420,7 +460,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(const __grid_constant__ 
         const int quarter = warp & 3, half = warp >> 2;
         const int n0 = quarter * 32;
         const int ncol = Nk - n0 < 32 ? Nk - n0 : 32;        // valid columns of this warp (may be <= 0)
-        const float scale = (PASS == P_XI) ? 8.0f / ((float)(Ng + 1) * (Ng + 1) * (Ng + 1)) : 1.0f;
+        const float scale = (PASS == P_XI || PASS == P_ZM) ? 8.0f / ((float)(Ng + 1) * (Ng + 1) * (Ng + 1)) : 1.0f;
         // (the padded row length S depends on the box's ghost width: taken per tile below)
         float *buf = xpose + warp * (kXposeBytes / 4);
         uint32_t t = 0;
@@ -433,6 +473,39 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(const __grid_constant__ 
             tc_fence_after();
             const TileInfo ti = tile_at(it);
             const uint32_t tbase = tmem + (uint32_t)(a * kTN + half * 128) + ((uint32_t)n0 << 16);
+            if (PASS == P_ZM) {
+                // lane = output k of this warp's quarter, columns = cells q of its half tile:
+                // padded Phi[i + gp][j + gp][k + gp], 32 lanes -> 32 consecutive floats
+                const int gp = ti.pad;
+                const long long S = Ng + 2 * gp;
+#pragma unroll 1
+                for (int g16 = 0; g16 < 8; ++g16) {
+                    float v[16];
+                    if (ncol > 0) {
+                        tmem_ld16_issue(tbase + (uint32_t)(g16 * 16), v);
+                        tmem_ld_wait();
+                        tmem_regs_ready(v);
+                    }
+                    if (g16 == 7) {
+                        tc_fence_before();
+                        mbar_arrive(&tempty[a]);
+                    }
+                    if (ncol > 0 && lane < ncol) {
+                        const long long q0 = (long long)ti.row0 + half * 128 + g16 * 16;
+                        float *dst = A.out + ti.pp_off + gp;
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const long long q = q0 + j;
+                            if (q < Ng2) {
+                                const long long i = q / Ng, jj = q - i * Ng;
+                                dst[((i + gp) * S + (jj + gp)) * S + n0 + lane] = v[j] * scale;
+                            }
+                        }
+                    }
+                    __syncwarp();
+                }
+                continue;
+            }
 #pragma unroll 1
             for (int rnd = 0; rnd < 4; ++rnd) {
                 float v0[16], v1[16];
@@ -537,9 +610,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(const __grid_constant__ 
 }
 
 // Dynamic shared memory of a launch: Nk matrix rows (Ng, or Ng / 2 folded), Ng eigenvalues.
-size_t tc_smem_bytes(int Nk, int Ng, int nkc, int nstage) {
+size_t tc_smem_bytes(int Nk, int Ng, int nkc, int nstage, bool zm = false) {
     const size_t sch = (size_t)((Nk + 7) / 8) * 1024;
-    return 1024 + 2 * (size_t)nkc * sch + (size_t)nstage * kStageBytes + 8 * kXposeBytes + (3 * nstage + 5) * 8 + 16 +
+    return 1024 + 2 * (size_t)nkc * sch + (size_t)nstage * stage_bytes(zm ? P_ZM : P_F) + (zm ? 0 : 8 * kXposeBytes) +
+           (3 * nstage + 5) * 8 + 16 +
            (size_t)Ng * 4 + 16 + kTileCache * sizeof(TileInfo) + 64;
 }
 
@@ -552,9 +626,10 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-cudaError_t input_map(Ctx &c, const float *buf, int Ng, CUtensorMap *out) {
+cudaError_t input_map(Ctx &c, const float *buf, int Ng, CUtensorMap *out, bool plane_major = false) {
     static std::mutex mu;
     static std::map<std::pair<std::pair<const void *, long long>, int>, CUtensorMap> cache;
+    if (plane_major) Ng = -Ng;                       // (its own cache entries)
     static EncodeTiledFn encode = nullptr;
     std::lock_guard<std::mutex> lock(mu);
     const auto key = std::make_pair(std::make_pair((const void *)buf, c.M), Ng);
@@ -571,14 +646,27 @@ cudaError_t input_map(Ctx &c, const float *buf, int Ng, CUtensorMap *out) {
         encode = (EncodeTiledFn)fn;
     }
     CUtensorMap m;
-    const cuuint64_t dims[2] = {(cuuint64_t)Ng, (cuuint64_t)(c.M / Ng)};
-    const cuuint64_t strides[1] = {(cuuint64_t)Ng * sizeof(float)};
-    const cuuint32_t box[2] = {(cuuint32_t)kKB, (cuuint32_t)kTN};
     const cuuint32_t estr[2] = {1, 1};
-    if (encode(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(buf), dims, strides, box, estr,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-        return cudaErrorInvalidValue;
+    if (plane_major) {
+        // rows of Ng^2 floats (one plane of a box mesh, box offsets multiples of Ng^2), boxes of
+        // 256 cells x 16 planes, unswizzled (the converters transpose them)
+        const long long n2 = (long long)Ng * Ng;
+        const cuuint64_t dims[2] = {(cuuint64_t)n2, (cuuint64_t)(c.M / n2)};
+        const cuuint64_t strides[1] = {(cuuint64_t)n2 * sizeof(float)};
+        const cuuint32_t box[2] = {(cuuint32_t)kTN, (cuuint32_t)kKB};
+        if (encode(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(buf), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    } else {
+        const cuuint64_t dims[2] = {(cuuint64_t)Ng, (cuuint64_t)(c.M / Ng)};
+        const cuuint64_t strides[1] = {(cuuint64_t)Ng * sizeof(float)};
+        const cuuint32_t box[2] = {(cuuint32_t)kKB, (cuuint32_t)kTN};
+        if (encode(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(buf), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
     cache[key] = m;
     *out = m;
     return cudaSuccess;
@@ -622,9 +710,9 @@ cudaError_t run_tc_pass(Ctx &c, const std::vector<TcGroup> &groups, const float 
     for (int g = 0; g < ng; ++g) {
         const TcGroup &G = groups[g];
         TcGroupArgs &A = a.grp[g];
-        A.ragged = tc_ragged(G.Ng) ? 1 : 0;
+        A.ragged = (PASS != P_ZM && tc_ragged(G.Ng)) ? 1 : 0;
         if (!A.ragged) {
-            cudaError_t me = input_map(c, in, G.Ng, &A.in_map);
+            cudaError_t me = input_map(c, in, G.Ng, &A.in_map, PASS == P_ZM);
             if (me != cudaSuccess) return me;
         }
         A.tiles = G.tiles;
@@ -632,13 +720,13 @@ cudaError_t run_tc_pass(Ctx &c, const std::vector<TcGroup> &groups, const float 
         A.Ng = G.Ng;
         A.Npad = G.Npad;
         A.nkc = G.nkc;
-        A.nstage = G.nstage;
+        A.nstage = PASS == P_ZM ? G.nstage_zm : G.nstage;
         A.S = c.table_arena + G.s_off;
         A.lam = c.table_arena + G.lam_off;
         A.cta0 = cta0;
         A.nctas = ctas[g];
         cta0 += ctas[g];
-        smem = std::max(smem, tc_smem_bytes(fold ? (G.Ng + 1) / 2 : G.Ng, G.Ng, G.nkc, G.nstage));
+        smem = std::max(smem, tc_smem_bytes(fold ? (G.Ng + 1) / 2 : G.Ng, G.Ng, G.nkc, A.nstage, PASS == P_ZM));
     }
     a.ngroups = ng;
     a.boxes = c.boxes;
@@ -659,20 +747,20 @@ bool tc_folded(int Ng) { return Ng > kTM; }
 
 bool tc_ragged(int Ng) { return tc_folded(Ng) ? Ng % 32 != 0 : Ng % 4 != 0; }
 
-int tc_plan_stages(int Ng, int &Npad, int &nkc) {
+int tc_plan_stages(int Ng, int &Npad, int &nkc, bool zm) {
     // as many data stages (up to 4) as fit next to the resident sine matrix, at least 2
     const int Nk = tc_folded(Ng) ? (Ng + 1) / 2 : Ng;
     Npad = ((Nk + 15) / 16) * 16;
     nkc = (Nk + kKA - 1) / kKA;
     for (int nst = 4; nst >= 2; --nst)
-        if (tc_smem_bytes(Nk, Ng, nkc, nst) <= kSmemBudget) return nst;
+        if (tc_smem_bytes(Nk, Ng, nkc, nst, zm) <= kSmemBudget) return nst;
     return 0;
 }
 
 bool tc_supported(int Ng) {
     int Npad, nkc;
     // direct form: Ng <= 128 (one M = 128 operand); folded form: ceil(Ng / 2) <= 128
-    return Ng >= 2 && Ng <= 2 * kTM && tc_plan_stages(Ng, Npad, nkc) >= 2;
+    return Ng >= 2 && Ng <= 2 * kTM && tc_plan_stages(Ng, Npad, nkc, false) >= 2;
 }
 
 template <int PASS>
@@ -689,6 +777,8 @@ cudaError_t init_tc_kernels() {
     if ((e = set_tc_attr<P_XF>())) return e;
     if ((e = set_tc_attr<P_ZI>())) return e;
     if ((e = set_tc_attr<P_YI>())) return e;
+    if ((e = set_tc_attr<P_ZM>())) return e;
+    if ((e = init_plane_kernel())) return e;
     return set_tc_attr<P_XI>();
 }
 
@@ -706,6 +796,10 @@ std::vector<TcGroup> active_groups(const Ctx &c) {
         TcGroup V = G;
         V.tiles = c.tc_tiles + c.tc_tile_beg[c.view_box];
         V.ntiles = c.tc_tile_end[c.view_box] - c.tc_tile_beg[c.view_box];
+        if (c.tc_planes) {
+            V.planes = c.tc_planes + c.tc_plane_beg[c.view_box];
+            V.nplanes = G.Ng;
+        }
         one.push_back(V);
     }
     return one;
@@ -731,6 +825,18 @@ std::vector<std::vector<TcGroup>> tc_launches(const Ctx &c) {
 }
 
 cudaError_t launch_poisson_tc_pass(Ctx &c, int pass) {
+    if (c.tc3) {
+        // three passes: source (work2) -> work (z+) -> work2 (plane) -> phi (z-)
+        if (pass >= 3) return cudaSuccess;
+        cudaError_t e = cudaSuccess;
+        for (const auto &L : tc_launches(c)) {
+            if (pass == 0) e = run_tc_pass<P_F>(c, L, c.work2, c.work);
+            else if (pass == 1) e = launch_plane_pass(c, L, c.work, c.work2);
+            else e = run_tc_pass<P_ZM>(c, L, c.work2, c.phi);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
     // buffers: source (work2) -> work -> work2 -> work -> work2 -> work -> phi
     cudaError_t e = cudaSuccess;
     for (const auto &L : tc_launches(c)) {
@@ -759,6 +865,15 @@ cudaError_t launch_poisson_tc(Ctx &c) {
 
 cudaError_t launch_poisson_tc_buffers(Ctx &c, const float *in, float *w1, float *w2, float *out_pad) {
     cudaError_t e = cudaSuccess;
+    if (c.tc3) {
+        for (const auto &L : tc_launches(c)) {
+            e = run_tc_pass<P_F>(c, L, in, w1);
+            if (e == cudaSuccess) e = launch_plane_pass(c, L, w1, w2);
+            if (e == cudaSuccess) e = run_tc_pass<P_ZM>(c, L, w2, out_pad);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
     for (const auto &L : tc_launches(c)) {
         e = run_tc_pass<P_F>(c, L, in, w1);
         if (e == cudaSuccess) e = run_tc_pass<P_F>(c, L, w1, w2);

@@ -27,7 +27,7 @@ def test_roofline_rows_use_the_algorithmic_bytes():
     kt = {"deposit": 0.25, "kick_drift": 0.24}
     kt.update({"dst_%d" % i: 0.1 for i in range(1, 7)})
     peaks = {"hbm_gbs": 6789.0, "sm_max_mhz": 2070.0}
-    dom, rows = bench.kernel_roofline(kt, kw, {"sm_mhz": 2070.0}, peaks, True)
+    dom, rows = bench.kernel_roofline(kt, kw, {"sm_mhz": 2070.0}, peaks, "tc")
     assert dom == "deposit"
     assert rows["deposit"]["achieved"] == pytest.approx((12.0 * P + 4.0 * M) / 0.25e-3 / 1e9)
     assert rows["kick_drift"]["achieved"] == pytest.approx((72.0 * P + 4.0 * MP) / 0.24e-3 / 1e9)
@@ -37,7 +37,7 @@ def test_roofline_rows_use_the_algorithmic_bytes():
     assert sum(r["share"] for r in rows.values()) == pytest.approx(1.0)
     # FP32 form: five passes on the CUDA cores, bound by FMA throughput
     kt["dst_6"] = 0.0
-    dom, rows = bench.kernel_roofline(kt, kw, {"sm_mhz": 2000.0}, peaks, False)
+    dom, rows = bench.kernel_roofline(kt, kw, {"sm_mhz": 2000.0}, peaks, "simt")
     alu = 152 * 128 * 2 * 2000e6 / 1e12
     assert rows["dst_3_x_solve"]["bound"] == "alu"
     assert rows["dst_3_x_solve"]["achieved"] == pytest.approx(2 * 64 * 2.0 * 96 * 96**3 / 0.1e-3 / 1e12)
@@ -72,3 +72,15 @@ def test_oracle_pool_times_whole_boxes_side_by_side():
         assert r["cores"] == 2 and r["value"] > 0 and r["kind"] == "oracle"
     finally:
         pool.close()
+
+
+def test_roofline_rows_of_the_three_pass_solve():
+    # three mesh passes, each streaming the mesh once; passes 4-6 do not exist
+    kw, _ = bench.workload_kwargs("batched_128")
+    M = 64 * 96**3
+    kt = {"deposit": 0.25, "kick_drift": 0.24, "dst_1": 0.1, "dst_2": 0.15, "dst_3": 0.1,
+          "dst_4": 0.0, "dst_5": 0.0, "dst_6": 0.0}
+    dom, rows = bench.kernel_roofline(kt, kw, {"sm_mhz": 2070.0}, {"hbm_gbs": 6691.8}, "tc3")
+    assert set(k for k in rows if k.startswith("dst")) == {"dst_1_z_fwd", "dst_2_plane", "dst_3_z_inv"}
+    assert rows["dst_2_plane"]["achieved"] == pytest.approx(8.0 * M / 0.15e-3 / 1e9)
+    assert dom == "deposit"

@@ -63,12 +63,22 @@ CASES_PM = {
 
 
 def _sim(kw, variant="simt"):
-    code = {"simt": sc.SCOLA_DST_SIMT, "tc": sc.SCOLA_DST_TC_3XTF32, "tc4": sc.SCOLA_DST_TC_4XTF32}[variant]
+    code = {"simt": sc.SCOLA_DST_SIMT, "tc": sc.SCOLA_DST_TC_3XTF32, "tc4": sc.SCOLA_DST_TC_4XTF32,
+            "tc3": sc.SCOLA_DST_TC_3PASS}[variant]
     return sc.Scola(**dict(lib_kwargs(kw), dst_variant=code))
 
 
+def _mesh_sizes(kw):
+    ntile = kw["Np"] // kw["Ntiles"]
+    bufs = kw.get("buffers") or [kw["Nbuf"]] * kw["Ntiles"] ** 3
+    return {kw.get("Ng") or kw["mesh_ratio"] * (ntile + 2 * b) for b in bufs}
+
+
 def _skip_unsupported(kw, variant):
-    """Every mesh of these cases runs on both forms (the tensor-core DST takes Ng <= 256)."""
+    """Every mesh of these cases runs on the six-pass and FP32 forms (Ng <= 256); the
+    three-pass solve takes Ng <= 96 with Ng % 4 == 0."""
+    if variant == "tc3" and any(g > 96 or g % 4 for g in _mesh_sizes(kw)):
+        pytest.skip("the three-pass tensor-core solve needs Ng <= 96 and Ng % 4 == 0")
 
 
 def _to_dev(a):
@@ -102,7 +112,7 @@ def test_box_particle_ids_are_bit_exact(name):
     sim.close()
 
 
-@pytest.mark.parametrize("variant", ["simt", "tc"])
+@pytest.mark.parametrize("variant", ["simt", "tc", "tc3"])
 @pytest.mark.parametrize("name", list(CASES_PM))
 def test_pm_force_matches_oracle(name, variant):
     # One force evaluation (deposit, Dirichlet DST-I solve, gradient, interpolation) on
@@ -216,7 +226,7 @@ def _pk_rel_err(delta_a, delta_b, L, N):
     return np.abs(pa[ok] / pb[ok] - 1).max()
 
 
-@pytest.mark.parametrize("variant", ["simt", "tc", "tc4"])
+@pytest.mark.parametrize("variant", ["simt", "tc", "tc4", "tc3"])
 @pytest.mark.parametrize("name", ["plain_32", "uneven", "table1_like", "fold_160", "fold_odd", "fda4",
                                   "fda6_ratio2"])
 def test_forward_matches_oracle(name, variant):
@@ -263,7 +273,7 @@ def test_forward_is_deterministic_and_host_variant_agrees():
     sim.close()
 
 
-@pytest.mark.parametrize("variant", ["simt", "tc"])
+@pytest.mark.parametrize("variant", ["simt", "tc", "tc3"])
 @pytest.mark.parametrize("name", ["plain_32", "uneven"])
 def test_per_tile_form_matches_batched_form(name, variant):
     # One box per launch (the plain per-tile form) gives bit-identical results: every kernel
@@ -437,7 +447,7 @@ def test_state_and_argument_errors():
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("variant", ["simt", "tc"])
+@pytest.mark.parametrize("variant", ["simt", "tc", "tc3"])
 def test_batched_128_sampled_boxes_match_oracle(variant):
     # Full-size batched workload in the benchmark's launch configuration; the oracle
     # evolves two sampled boxes (boxes are independent, so each is exact on its own).
@@ -463,7 +473,7 @@ _UNEVEN_CACHE = {}
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("variant", ["simt", "tc", "tc4"])
+@pytest.mark.parametrize("variant", ["simt", "tc", "tc4", "tc3"])
 def test_uneven_256_sampled_boxes_match_oracle(variant):
     # The uneven-buffer workload (256^3 particles, 4^3 tiles, buffers drawn from {4, 8, 16},
     # 1:1 meshes of 72, 80 and 96 cells in one launch), in the benchmark's launch form; the
