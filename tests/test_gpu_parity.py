@@ -123,7 +123,7 @@ def test_pm_force_matches_oracle(name, variant):
     cfg = oracle_cfg(kw)
     w, f, sched = oracle_fields(kw)
     sim = _sim(kw, variant)
-    assert sc.scola_uses_tensor_cores(sim.ctx) == (variant == "tc")
+    assert sc.scola_uses_tensor_cores(sim.ctx) == variant.startswith("tc")
     sim.lpt_fields(_to_dev(w))
     sim.setup_boxes()
     D1 = 0.73
