@@ -81,7 +81,8 @@ __global__ void __launch_bounds__(kPlThreads, 1) k_dst_plane(const __grid_consta
     const uint32_t sch = (uint32_t)((Ng + 7) / 8) * 1024;      // one sine chunk (32 K), hi or lo
     const uint32_t bhalf = (uint32_t)nkb * Npad * 64;          // one operand, hi or lo
     // The M = 128 operand reads 128 rows from each sine chunk; rows >= Ng come from what
-    // follows and only feed TMEM lanes that the epilogue discards.
+    // follows (the allocation always extends 16 KB past the last chunk's start, see
+    // plane_smem_bytes) and only feed TMEM lanes that the epilogue discards.
     unsigned char *S_hi = base;
     unsigned char *S_lo = base + nka * sch;
     unsigned char *bufs = base + 2 * nka * sch;                // buffer e: hi, then lo
@@ -305,7 +306,11 @@ __global__ void __launch_bounds__(kPlThreads, 1) k_dst_plane(const __grid_consta
 
 size_t plane_smem_bytes(int Ng, int Npad, int nka, int nkb) {
     const size_t sch = (size_t)((Ng + 7) / 8) * 1024;
-    return 1024 + 2 * (size_t)nka * sch + 4 * (size_t)nkb * Npad * 64 + 9 * 8 + 16 + (size_t)Ng * 4 + 64;
+    const size_t layout = 2 * (size_t)nka * sch + 4 * (size_t)nkb * Npad * 64 + 9 * 8 + 16 + (size_t)Ng * 4 + 64;
+    // the M = 128 operand reads 128 rows (16 KB) from the start of every sine chunk, up to
+    // the last lo chunk: for small Ng that reaches past the layout, so the allocation covers it
+    const size_t reach = (2 * (size_t)nka - 1) * sch + 128 * 128;
+    return 1024 + (layout > reach ? layout : reach);
 }
 
 constexpr size_t kPlSmemBudget = 227 * 1024;
