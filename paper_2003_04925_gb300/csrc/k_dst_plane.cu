@@ -27,7 +27,8 @@
 // the tensor cores run the other plane's step.
 //
 // One persistent CTA per SM, 10 warps:
-//   warps 0-7  split each loaded plane into hi/lo; the epilogues of the four steps
+//   warps 0-3  split the planes of buffer 0 into hi/lo; the epilogues of their four steps
+//   warps 4-7  the same for buffer 1, so the two planes' epilogues overlap
 //   warp 8     TMEM allocation; lane 0 issues tcgen05.mma and tcgen05.commit
 //   warp 9     lane 0 issues the tensor copies of each plane (Ng/16 boxes of 16 x Npad)
 // The CTAs of a launch are split among the Ng groups of the boxes (as in k_dst_tc.cu).
@@ -88,7 +89,7 @@ __global__ void __launch_bounds__(kPlThreads, 1) k_dst_plane(const __grid_consta
     unsigned char *bufs = base + 2 * nka * sch;                // buffer e: hi, then lo
     uint64_t *bars = (uint64_t *)(bufs + 4 * (size_t)bhalf);
     uint64_t *loaded = bars;          // the plane's tensor copies have landed
-    uint64_t *opready = bars + 2;     // the next step's operand is written (256 arrivals)
+    uint64_t *opready = bars + 2;     // the next step's operand is written (128 arrivals)
     uint64_t *accfull = bars + 4;     // the step's MMAs are complete
     uint64_t *bufempty = bars + 6;    // step 4 is complete: the buffer may take the next plane
     uint64_t *drain = bars + 8;
@@ -116,7 +117,7 @@ __global__ void __launch_bounds__(kPlThreads, 1) k_dst_plane(const __grid_consta
     if (tid == 0) {
         for (int e = 0; e < 2; ++e) {
             mbar_init(&loaded[e], 1);
-            mbar_init(&opready[e], 256);
+            mbar_init(&opready[e], 128);
             mbar_init(&accfull[e], 1);
             mbar_init(&bufempty[e], 1);
         }
@@ -176,7 +177,7 @@ __global__ void __launch_bounds__(kPlThreads, 1) k_dst_plane(const __grid_consta
                 for (int s = 1; s <= 4 && ok; ++s)
                     for (int e = 0; e < 2; ++e) {
                         if (2 * q + e >= my_items) break;
-                        if (!mbar_wait(&opready[e], (uint32_t)((s - 1) & 1), abort_flag)) {
+                        if (!mbar_spin(&opready[e], (uint32_t)((s - 1) & 1), abort_flag)) {
                             ok = false;
                             break;
                         }
@@ -200,92 +201,88 @@ __global__ void __launch_bounds__(kPlThreads, 1) k_dst_plane(const __grid_consta
         }
     } else {
         // ---------------------------------------------------------------- warps 0-7
-        // warp w reads TMEM lanes 32 (w & 3) + lane (the output index of its row) and the
-        // 16-column chunks c = (w >> 2), (w >> 2) + 2, ... of the accumulator
-        const int lq = warp & 3, hsel = warp >> 2;
+        // warp group e = warp / 4 serves buffer e (planes p = 2 q + e); warp w reads TMEM
+        // lanes 32 (w & 3) + lane, the output index of its row, over all column chunks
+        const int e = warp >> 2, lq = warp & 3;
+        const int gt = tid & 127;                       // thread within the group
         const int row = lq * 32 + lane;
+        unsigned char *hi = bufs + (size_t)e * 2 * bhalf, *lo = hi + bhalf;
+        const uint32_t tb = tmem + (uint32_t)(e * 128) + ((uint32_t)(lq * 32) << 16);
         bool ok = true;
         for (long long q = 0; q < npairs && ok && !*abort_flag; ++q) {
-            // split the pair's loaded planes in place: hi over the copy, lo into the other half;
-            // rows >= Ng (the next plane's rows brought by the box) are cleared
-            for (int e = 0; e < 2; ++e) {
-                if (2 * q + e >= my_items) break;
-                if (!mbar_wait(&loaded[e], (uint32_t)(q & 1), abort_flag)) {
+            const long long p = 2 * q + e;
+            if (p >= my_items) break;
+            const Chunk it = G.items[bid + p * nbid];
+            const int n = it.start;
+            const long long m_off = A.boxes[it.box].m_off;
+            // split the loaded plane in place: hi over the copy, lo into the other half; rows
+            // >= Ng (the next plane's rows brought by the box) are cleared
+            if (!mbar_spin(&loaded[e], (uint32_t)(q & 1), abort_flag)) {
+                ok = false;
+                break;
+            }
+            const int units = nkb * Npad * 4;
+            for (int u = gt; u < units; u += 128) {
+                const int c = u / (Npad * 4), rem = u % (Npad * 4);
+                const int r = rem >> 2, qq = rem & 3;
+                const uint32_t off = (uint32_t)c * Npad * 64 + sw64_offset(r, 4 * qq);
+                float4 v = *reinterpret_cast<const float4 *>(hi + off);
+                if (r >= Ng) v = make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 h = make_float4(tf32_rn(v.x), tf32_rn(v.y), tf32_rn(v.z), tf32_rn(v.w));
+                *reinterpret_cast<float4 *>(hi + off) = h;
+                *reinterpret_cast<float4 *>(lo + off) =
+                    make_float4(tf32_rn(v.x - h.x), tf32_rn(v.y - h.y), tf32_rn(v.z - h.z), tf32_rn(v.w - h.w));
+            }
+            fence_proxy_async();
+            mbar_arrive(&opready[e]);
+            const float lam_row = row < Ng ? lam[row] : 0.0f, lam_n = lam[n];
+            for (int s = 1; s <= 4; ++s) {
+                if (!mbar_spin(&accfull[e], (uint32_t)((s - 1) & 1), abort_flag)) {
                     ok = false;
                     break;
                 }
-                unsigned char *hi = bufs + (size_t)e * 2 * bhalf, *lo = hi + bhalf;
-                const int units = nkb * Npad * 4;
-                for (int u = tid; u < units; u += 256) {
-                    const int c = u / (Npad * 4), rem = u % (Npad * 4);
-                    const int r = rem >> 2, qq = rem & 3;
-                    const uint32_t off = (uint32_t)c * Npad * 64 + sw64_offset(r, 4 * qq);
-                    float4 v = *reinterpret_cast<const float4 *>(hi + off);
-                    if (r >= Ng) v = make_float4(0.f, 0.f, 0.f, 0.f);
-                    const float4 h = make_float4(tf32_rn(v.x), tf32_rn(v.y), tf32_rn(v.z), tf32_rn(v.w));
-                    *reinterpret_cast<float4 *>(hi + off) = h;
-                    *reinterpret_cast<float4 *>(lo + off) =
-                        make_float4(tf32_rn(v.x - h.x), tf32_rn(v.y - h.y), tf32_rn(v.z - h.z), tf32_rn(v.w - h.w));
-                }
-                fence_proxy_async();
-                mbar_arrive(&opready[e]);
-            }
-            for (int s = 1; s <= 4 && ok; ++s)
-                for (int e = 0; e < 2; ++e) {
-                    const long long p = 2 * q + e;
-                    if (p >= my_items) break;
-                    if (!mbar_wait(&accfull[e], (uint32_t)((s - 1) & 1), abort_flag)) {
-                        ok = false;
-                        break;
-                    }
-                    tc_fence_after();
-                    const Chunk it = G.items[bid + p * nbid];
-                    const int n = it.start;
-                    unsigned char *hi = bufs + (size_t)e * 2 * bhalf, *lo = hi + bhalf;
-                    const uint32_t tb = tmem + (uint32_t)(e * 128) + ((uint32_t)(lq * 32) << 16);
-                    const long long m_off = s == 4 ? A.boxes[it.box].m_off : 0;
-                    for (int c = hsel; c < nkb; c += 2) {
-                        float v[16];
-                        tmem_ld16_issue(tb + (uint32_t)(c * 16), v);
-                        tmem_ld_wait();
-                        tmem_regs_ready(v);
-                        if (s < 4) {
-                            // this lane's row of the next operand, columns 16 c .. 16 c + 15
-                            if (row < Npad) {
-#pragma unroll
-                                for (int qq = 0; qq < 4; ++qq) {
-                                    float x[4];
-#pragma unroll
-                                    for (int t = 0; t < 4; ++t) {
-                                        const int col = c * 16 + 4 * qq + t;
-                                        float y = (row < Ng && col < Ng) ? v[4 * qq + t] : 0.0f;
-                                        if (s == 2 && row < Ng && col < Ng)
-                                            y = __fdividef(y, lam[row] + lam[col] + lam[n]);
-                                        x[t] = y;
-                                    }
-                                    const float4 h = make_float4(tf32_rn(x[0]), tf32_rn(x[1]), tf32_rn(x[2]), tf32_rn(x[3]));
-                                    const uint32_t off = (uint32_t)c * Npad * 64 + sw64_offset(row, 4 * qq);
-                                    *reinterpret_cast<float4 *>(hi + off) = h;
-                                    *reinterpret_cast<float4 *>(lo + off) = make_float4(
-                                        tf32_rn(x[0] - h.x), tf32_rn(x[1] - h.y), tf32_rn(x[2] - h.z), tf32_rn(x[3] - h.w));
-                                }
-                            }
-                        } else if (row < Ng) {
-                            // row i' of W2[n]: columns j' = 16 c .. (Ng % 4 == 0: whole float4s)
-                            float *dst = A.out + m_off + (long long)n * Ng2 + (long long)row * Ng;
+                tc_fence_after();
+                for (int c = 0; c < nkb; ++c) {
+                    float v[16];
+                    tmem_ld16_issue(tb + (uint32_t)(c * 16), v);
+                    tmem_ld_wait();
+                    tmem_regs_ready(v);
+                    if (s < 4) {
+                        // this lane's row of the next operand, columns 16 c .. 16 c + 15
+                        if (row < Npad) {
 #pragma unroll
                             for (int qq = 0; qq < 4; ++qq) {
-                                const int col = c * 16 + 4 * qq;
-                                if (col < Ng)
-                                    *reinterpret_cast<float4 *>(dst + col) =
-                                        make_float4(v[4 * qq], v[4 * qq + 1], v[4 * qq + 2], v[4 * qq + 3]);
+                                float x[4];
+#pragma unroll
+                                for (int t = 0; t < 4; ++t) {
+                                    const int col = c * 16 + 4 * qq + t;
+                                    float y = (row < Ng && col < Ng) ? v[4 * qq + t] : 0.0f;
+                                    if (s == 2 && row < Ng && col < Ng) y = __fdividef(y, lam_row + lam[col] + lam_n);
+                                    x[t] = y;
+                                }
+                                const float4 h = make_float4(tf32_rn(x[0]), tf32_rn(x[1]), tf32_rn(x[2]), tf32_rn(x[3]));
+                                const uint32_t off = (uint32_t)c * Npad * 64 + sw64_offset(row, 4 * qq);
+                                *reinterpret_cast<float4 *>(hi + off) = h;
+                                *reinterpret_cast<float4 *>(lo + off) = make_float4(
+                                    tf32_rn(x[0] - h.x), tf32_rn(x[1] - h.y), tf32_rn(x[2] - h.z), tf32_rn(x[3] - h.w));
                             }
                         }
+                    } else if (row < Ng) {
+                        // row i' of W2[n]: columns j' = 16 c .. (Ng % 4 == 0: whole float4s)
+                        float *dst = A.out + m_off + (long long)n * Ng2 + (long long)row * Ng;
+#pragma unroll
+                        for (int qq = 0; qq < 4; ++qq) {
+                            const int col = c * 16 + 4 * qq;
+                            if (col < Ng)
+                                *reinterpret_cast<float4 *>(dst + col) =
+                                    make_float4(v[4 * qq], v[4 * qq + 1], v[4 * qq + 2], v[4 * qq + 3]);
+                        }
                     }
-                    if (s < 4) fence_proxy_async();
-                    tc_fence_before();
-                    if (s < 4) mbar_arrive(&opready[e]);
                 }
+                if (s < 4) fence_proxy_async();
+                tc_fence_before();
+                if (s < 4) mbar_arrive(&opready[e]);
+            }
         }
         if (!ok) *abort_flag = 1;
     }

@@ -491,14 +491,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(const __grid_constant__ 
                         mbar_arrive(&tempty[a]);
                     }
                     if (ncol > 0 && lane < ncol) {
-                        const long long q0 = (long long)ti.row0 + half * 128 + g16 * 16;
-                        float *dst = A.out + ti.pp_off + gp;
+                        // cell q = i Ng + jj (q < Ng^2 < 2^31): one division per 16 cells, then
+                        // step along the row
+                        const int q0 = ti.row0 + half * 128 + g16 * 16;
+                        int i = q0 / Ng, jj = q0 - i * Ng;
+                        float *dst = A.out + ti.pp_off + gp + n0 + lane;
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
-                            const long long q = q0 + j;
-                            if (q < Ng2) {
-                                const long long i = q / Ng, jj = q - i * Ng;
-                                dst[((i + gp) * S + (jj + gp)) * S + n0 + lane] = v[j] * scale;
+                            if (q0 + j < Ng2)
+                                dst[((long long)(i + gp) * S + (jj + gp)) * S] = v[j] * scale;
+                            if (++jj == Ng) {
+                                jj = 0;
+                                ++i;
                             }
                         }
                     }
