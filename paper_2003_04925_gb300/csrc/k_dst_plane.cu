@@ -30,7 +30,10 @@
 //   warps 0-3  split the planes of buffer 0 into hi/lo; the epilogues of their four steps
 //   warps 4-7  the same for buffer 1, so the two planes' epilogues overlap
 //   warp 8     TMEM allocation; lane 0 issues tcgen05.mma and tcgen05.commit
-//   warp 9     lane 0 issues the tensor copies of each plane (Ng/16 boxes of 16 x Npad)
+//   warp 9     lane 0 issues the tensor copies of each plane (Ng/32 boxes of 32 x Npad)
+// The operands are K-major with the 128-byte swizzle (chunks of 32 columns), as the sine
+// matrix: an epilogue thread reads all its accumulator columns with the TMEM loads in flight
+// together and writes its row of the next operand in 16-byte units.
 // The CTAs of a launch are split among the Ng groups of the boxes (as in k_dst_tc.cu).
 // Every wait is bounded (about 2 s); on expiry the CTA raises the error flag, stops
 // issuing, waits (bounded) for its issued copies and MMAs, frees TMEM and returns.
@@ -54,11 +57,11 @@ constexpr int kPlThreads = 320;
 constexpr int kPlGroups = 4;
 
 struct PlaneGroupArgs {
-    CUtensorMap in_map;          // W1 as rows of Ng floats: boxes of 16 x Npad, 64-byte swizzle
+    CUtensorMap in_map;          // W1 as rows of Ng floats: boxes of 32 x Npad, 128-byte swizzle
     const Chunk *items;          // (box, plane n)
     const float *S;              // sine matrix rows, Ng x (32 nka) (the one-axis passes' table)
     const float *lam;            // Dirichlet eigenvalues, Ng
-    int nitems, Ng, Npad, nka, nkb;
+    int nitems, Ng, Npad, nka;   // nka: 32-column chunks of the sine matrix and of the operands
     int cta0, nctas;
 };
 
@@ -71,6 +74,54 @@ struct PlaneArgs {
     int lo_lo;
 };
 
+// One epilogue thread's row after step STEP of a plane (v: its accumulator lane, 16 x nc16
+// columns).  Steps 1-3: the row of the next operand (K-major, 128-byte swizzle, hi and lo
+// TF32 parts), zero outside the Ng x Ng block; step 2 first divides by the eigenvalue sum
+// (row: x frequency l, column: y frequency m, plane: z frequency n).  Step 4: row i' of the
+// output plane, written to global memory.
+template <int STEP>
+__device__ __forceinline__ void plane_rows(const float (&v)[6][16], int nc16, int row, int Ng, int Npad, uint32_t och,
+                                           unsigned char *hi, unsigned char *lo, const float *lam, float lam_row,
+                                           float lam_n, float *dst) {
+    if (STEP == 4) {
+        if (row >= Ng) return;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            if (c >= nc16) break;
+#pragma unroll
+            for (int qq = 0; qq < 4; ++qq) {
+                const int col = c * 16 + 4 * qq;
+                if (col < Ng)
+                    *reinterpret_cast<float4 *>(dst + col) =
+                        make_float4(v[c][4 * qq], v[c][4 * qq + 1], v[c][4 * qq + 2], v[c][4 * qq + 3]);
+            }
+        }
+        return;
+    }
+    if (row >= Npad) return;
+    const bool rv = row < Ng;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        if (c >= nc16) break;
+#pragma unroll
+        for (int qq = 0; qq < 4; ++qq) {
+            const int col0 = c * 16 + 4 * qq;
+            float x[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                float y = v[c][4 * qq + t];
+                if (STEP == 2) y = __fdividef(y, lam_row + lam[col0 + t] + lam_n);
+                x[t] = (rv && col0 + t < Ng) ? y : 0.0f;
+            }
+            const float4 h = make_float4(tf32_rn(x[0]), tf32_rn(x[1]), tf32_rn(x[2]), tf32_rn(x[3]));
+            const uint32_t off = (uint32_t)(col0 >> 5) * och + sw128_offset(row, col0 & 31);
+            *reinterpret_cast<float4 *>(hi + off) = h;
+            *reinterpret_cast<float4 *>(lo + off) =
+                make_float4(tf32_rn(x[0] - h.x), tf32_rn(x[1] - h.y), tf32_rn(x[2] - h.z), tf32_rn(x[3] - h.w));
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kPlThreads, 1) k_dst_plane(const __grid_constant__ PlaneArgs A) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
@@ -78,9 +129,10 @@ __global__ void __launch_bounds__(kPlThreads, 1) k_dst_plane(const __grid_consta
     while (gi + 1 < A.ngroups && (int)blockIdx.x >= A.grp[gi + 1].cta0) ++gi;
     const PlaneGroupArgs &G = A.grp[gi];
     const int bid = (int)blockIdx.x - G.cta0, nbid = G.nctas;
-    const int Ng = G.Ng, Npad = G.Npad, nka = G.nka, nkb = G.nkb;
+    const int Ng = G.Ng, Npad = G.Npad, nka = G.nka;
     const uint32_t sch = (uint32_t)((Ng + 7) / 8) * 1024;      // one sine chunk (32 K), hi or lo
-    const uint32_t bhalf = (uint32_t)nkb * Npad * 64;          // one operand, hi or lo
+    const uint32_t och = (uint32_t)Npad * 128;                 // one operand chunk (32 K)
+    const uint32_t bhalf = (uint32_t)nka * och;                // one operand, hi or lo
     // The M = 128 operand reads 128 rows from each sine chunk; rows >= Ng come from what
     // follows (the allocation always extends 16 KB past the last chunk's start, see
     // plane_smem_bytes) and only feed TMEM lanes that the epilogue discards.
@@ -109,7 +161,7 @@ __global__ void __launch_bounds__(kPlThreads, 1) k_dst_plane(const __grid_consta
         *(float *)(S_hi + off) = hi;
         *(float *)(S_lo + off) = tf32_rn(sv - hi);
     }
-    for (int q = tid; q < Ng; q += kPlThreads) lam[q] = G.lam[q];
+    for (int q = tid; q < 128; q += kPlThreads) lam[q] = q < Ng ? G.lam[q] : 0.0f;
     for (int q = tid; q < (int)(bhalf / 4); q += kPlThreads) {     // clean operand padding
         reinterpret_cast<float4 *>(bufs)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
@@ -156,8 +208,8 @@ __global__ void __launch_bounds__(kPlThreads, 1) k_dst_plane(const __grid_consta
                 const int y = (int)(m_off / Ng + (long long)it.start * Ng);     // row (n, i = 0)
                 unsigned char *hi = bufs + (size_t)e * 2 * bhalf;
                 mbar_arrive_expect_tx(&loaded[e], bhalf);
-                for (int c = 0; c < nkb; ++c)
-                    tma_load_2d(smem_u32(hi + (size_t)c * Npad * 64), &G.in_map, c * 16, y, &loaded[e]);
+                for (int c = 0; c < nka; ++c)
+                    tma_load_2d(smem_u32(hi + (size_t)c * och), &G.in_map, c * 32, y, &loaded[e]);
             }
             if (*abort_flag) {
                 const unsigned long long t0 = now_ns();
@@ -186,9 +238,9 @@ __global__ void __launch_bounds__(kPlThreads, 1) k_dst_plane(const __grid_consta
                         const uint32_t bh = smem_u32(bufs + (size_t)e * 2 * bhalf), bl = bh + bhalf;
                         for (int kg = 0; kg < Ng; kg += 8) {
                             const uint32_t ao = (uint32_t)(kg / 32) * sch + (uint32_t)((kg % 32) / 8) * 32;
-                            const uint32_t bo = (uint32_t)(kg / 16) * Npad * 64 + (uint32_t)((kg % 16) / 8) * 32;
+                            const uint32_t bo = (uint32_t)(kg / 32) * och + (uint32_t)((kg % 32) / 8) * 32;
                             const uint64_t ahi = sw128_desc(shi + ao), alo = sw128_desc(slo + ao);
-                            const uint64_t bhi = sw64_desc(bh + bo), blo = sw64_desc(bl + bo);
+                            const uint64_t bhi = sw128_desc(bh + bo), blo = sw128_desc(bl + bo);
                             mma_tf32(d, ahi, bhi, idesc, kg > 0 ? 1u : 0u);
                             mma_tf32(d, ahi, blo, idesc, 1);
                             mma_tf32(d, alo, bhi, idesc, 1);
@@ -208,6 +260,7 @@ __global__ void __launch_bounds__(kPlThreads, 1) k_dst_plane(const __grid_consta
         const int row = lq * 32 + lane;
         unsigned char *hi = bufs + (size_t)e * 2 * bhalf, *lo = hi + bhalf;
         const uint32_t tb = tmem + (uint32_t)(e * 128) + ((uint32_t)(lq * 32) << 16);
+        const int nc16 = Npad / 16;                     // 16-column accumulator chunks (<= 6)
         bool ok = true;
         for (long long q = 0; q < npairs && ok && !*abort_flag; ++q) {
             const long long p = 2 * q + e;
@@ -216,69 +269,56 @@ __global__ void __launch_bounds__(kPlThreads, 1) k_dst_plane(const __grid_consta
             const int n = it.start;
             const long long m_off = A.boxes[it.box].m_off;
             // split the loaded plane in place: hi over the copy, lo into the other half; rows
-            // >= Ng (the next plane's rows brought by the box) are cleared
+            // >= Ng (the next plane's rows brought by the box) are cleared.  Four 16-byte units
+            // per thread in flight at a time
             if (!mbar_spin(&loaded[e], (uint32_t)(q & 1), abort_flag)) {
                 ok = false;
                 break;
             }
-            const int units = nkb * Npad * 4;
-            for (int u = gt; u < units; u += 128) {
-                const int c = u / (Npad * 4), rem = u % (Npad * 4);
-                const int r = rem >> 2, qq = rem & 3;
-                const uint32_t off = (uint32_t)c * Npad * 64 + sw64_offset(r, 4 * qq);
-                float4 v = *reinterpret_cast<const float4 *>(hi + off);
-                if (r >= Ng) v = make_float4(0.f, 0.f, 0.f, 0.f);
-                const float4 h = make_float4(tf32_rn(v.x), tf32_rn(v.y), tf32_rn(v.z), tf32_rn(v.w));
-                *reinterpret_cast<float4 *>(hi + off) = h;
-                *reinterpret_cast<float4 *>(lo + off) =
-                    make_float4(tf32_rn(v.x - h.x), tf32_rn(v.y - h.y), tf32_rn(v.z - h.z), tf32_rn(v.w - h.w));
+            const int units = nka * Npad * 8;
+            for (int u0 = gt; u0 < units; u0 += 4 * 128) {
+                float4 v[4];
+                uint32_t off[4];
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const int u = u0 + 128 * b;
+                    const int c = u / (Npad * 8), rem = u - c * (Npad * 8);
+                    const int r = rem >> 3, qq = rem & 7;
+                    off[b] = (uint32_t)c * och + sw128_offset(r, 4 * qq);
+                    v[b] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (u < units && r < Ng) v[b] = *reinterpret_cast<const float4 *>(hi + off[b]);
+                }
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    if (u0 + 128 * b >= units) break;
+                    const float4 h = make_float4(tf32_rn(v[b].x), tf32_rn(v[b].y), tf32_rn(v[b].z), tf32_rn(v[b].w));
+                    *reinterpret_cast<float4 *>(hi + off[b]) = h;
+                    *reinterpret_cast<float4 *>(lo + off[b]) = make_float4(
+                        tf32_rn(v[b].x - h.x), tf32_rn(v[b].y - h.y), tf32_rn(v[b].z - h.z), tf32_rn(v[b].w - h.w));
+                }
             }
             fence_proxy_async();
             mbar_arrive(&opready[e]);
             const float lam_row = row < Ng ? lam[row] : 0.0f, lam_n = lam[n];
+            float *dst = A.out + m_off + (long long)n * Ng2 + (long long)row * Ng;
             for (int s = 1; s <= 4; ++s) {
                 if (!mbar_spin(&accfull[e], (uint32_t)((s - 1) & 1), abort_flag)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                for (int c = 0; c < nkb; ++c) {
-                    float v[16];
-                    tmem_ld16_issue(tb + (uint32_t)(c * 16), v);
-                    tmem_ld_wait();
-                    tmem_regs_ready(v);
-                    if (s < 4) {
-                        // this lane's row of the next operand, columns 16 c .. 16 c + 15
-                        if (row < Npad) {
+                // every column of this lane in flight at once, then one wait
+                float v[6][16];
 #pragma unroll
-                            for (int qq = 0; qq < 4; ++qq) {
-                                float x[4];
+                for (int c = 0; c < 6; ++c)
+                    if (c < nc16) tmem_ld16_issue(tb + (uint32_t)(c * 16), v[c]);
+                tmem_ld_wait();
 #pragma unroll
-                                for (int t = 0; t < 4; ++t) {
-                                    const int col = c * 16 + 4 * qq + t;
-                                    float y = (row < Ng && col < Ng) ? v[4 * qq + t] : 0.0f;
-                                    if (s == 2 && row < Ng && col < Ng) y = __fdividef(y, lam_row + lam[col] + lam_n);
-                                    x[t] = y;
-                                }
-                                const float4 h = make_float4(tf32_rn(x[0]), tf32_rn(x[1]), tf32_rn(x[2]), tf32_rn(x[3]));
-                                const uint32_t off = (uint32_t)c * Npad * 64 + sw64_offset(row, 4 * qq);
-                                *reinterpret_cast<float4 *>(hi + off) = h;
-                                *reinterpret_cast<float4 *>(lo + off) = make_float4(
-                                    tf32_rn(x[0] - h.x), tf32_rn(x[1] - h.y), tf32_rn(x[2] - h.z), tf32_rn(x[3] - h.w));
-                            }
-                        }
-                    } else if (row < Ng) {
-                        // row i' of W2[n]: columns j' = 16 c .. (Ng % 4 == 0: whole float4s)
-                        float *dst = A.out + m_off + (long long)n * Ng2 + (long long)row * Ng;
-#pragma unroll
-                        for (int qq = 0; qq < 4; ++qq) {
-                            const int col = c * 16 + 4 * qq;
-                            if (col < Ng)
-                                *reinterpret_cast<float4 *>(dst + col) =
-                                    make_float4(v[4 * qq], v[4 * qq + 1], v[4 * qq + 2], v[4 * qq + 3]);
-                        }
-                    }
-                }
+                for (int c = 0; c < 6; ++c) tmem_regs_ready(v[c]);
+                if (s == 1) plane_rows<1>(v, nc16, row, Ng, Npad, och, hi, lo, lam, lam_row, lam_n, dst);
+                else if (s == 2) plane_rows<2>(v, nc16, row, Ng, Npad, och, hi, lo, lam, lam_row, lam_n, dst);
+                else if (s == 3) plane_rows<3>(v, nc16, row, Ng, Npad, och, hi, lo, lam, lam_row, lam_n, dst);
+                else plane_rows<4>(v, nc16, row, Ng, Npad, och, hi, lo, lam, lam_row, lam_n, dst);
                 if (s < 4) fence_proxy_async();
                 tc_fence_before();
                 if (s < 4) mbar_arrive(&opready[e]);
@@ -301,9 +341,9 @@ __global__ void __launch_bounds__(kPlThreads, 1) k_dst_plane(const __grid_consta
     if (warp == 8) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
 }
 
-size_t plane_smem_bytes(int Ng, int Npad, int nka, int nkb) {
+size_t plane_smem_bytes(int Ng, int Npad, int nka) {
     const size_t sch = (size_t)((Ng + 7) / 8) * 1024;
-    const size_t layout = 2 * (size_t)nka * sch + 4 * (size_t)nkb * Npad * 64 + 9 * 8 + 16 + (size_t)Ng * 4 + 64;
+    const size_t layout = 2 * (size_t)nka * sch + 4 * (size_t)nka * Npad * 128 + 9 * 8 + 16 + 128 * 4 + 64;
     // the M = 128 operand reads 128 rows (16 KB) from the start of every sine chunk, up to
     // the last lo chunk: for small Ng that reaches past the layout, so the allocation covers it
     const size_t reach = (2 * (size_t)nka - 1) * sch + 128 * 128;
@@ -316,7 +356,7 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-// W1 as a 2D tensor of rows of Ng floats, boxes of 16 x Npad with the 64-byte swizzle of
+// W1 as a 2D tensor of rows of Ng floats, boxes of 32 x Npad with the 128-byte swizzle of
 // the MMA's K-major operand.
 cudaError_t plane_map(Ctx &c, const float *buf, int Ng, int Npad, CUtensorMap *out) {
     static EncodeTiledFn encode = nullptr;
@@ -329,10 +369,10 @@ cudaError_t plane_map(Ctx &c, const float *buf, int Ng, int Npad, CUtensorMap *o
     }
     const cuuint64_t dims[2] = {(cuuint64_t)Ng, (cuuint64_t)(c.M / Ng)};
     const cuuint64_t strides[1] = {(cuuint64_t)Ng * sizeof(float)};
-    const cuuint32_t box[2] = {16u, (cuuint32_t)Npad};
+    const cuuint32_t box[2] = {32u, (cuuint32_t)Npad};
     const cuuint32_t estr[2] = {1, 1};
     if (encode(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(buf), dims, strides, box, estr,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
     return cudaSuccess;
@@ -342,8 +382,8 @@ cudaError_t plane_map(Ctx &c, const float *buf, int Ng, int Npad, CUtensorMap *o
 
 bool plane_supported(int Ng) {
     if (Ng < 8 || Ng > 96 || Ng % 4 != 0) return false;
-    const int Npad = (Ng + 15) / 16 * 16, nka = (Ng + 31) / 32, nkb = (Ng + 15) / 16;
-    return plane_smem_bytes(Ng, Npad, nka, nkb) <= kPlSmemBudget;
+    const int Npad = (Ng + 15) / 16 * 16, nka = (Ng + 31) / 32;
+    return plane_smem_bytes(Ng, Npad, nka) <= kPlSmemBudget;
 }
 
 cudaError_t init_plane_kernel() {
@@ -373,7 +413,6 @@ cudaError_t launch_plane_pass(Ctx &c, const std::vector<TcGroup> &groups, const 
             P.Ng = G.Ng;
             P.Npad = (G.Ng + 15) / 16 * 16;
             P.nka = G.nkc;
-            P.nkb = (G.Ng + 15) / 16;
             cudaError_t e = plane_map(c, in, P.Ng, P.Npad, &P.in_map);
             if (e != cudaSuccess) return e;
             P.items = G.planes;
@@ -386,7 +425,7 @@ cudaError_t launch_plane_pass(Ctx &c, const std::vector<TcGroup> &groups, const 
             P.cta0 = cta0;
             P.nctas = n;
             cta0 += n;
-            smem = std::max(smem, plane_smem_bytes(P.Ng, P.Npad, P.nka, P.nkb));
+            smem = std::max(smem, plane_smem_bytes(P.Ng, P.Npad, P.nka));
         }
         a.ngroups = ng;
         a.boxes = c.boxes;
