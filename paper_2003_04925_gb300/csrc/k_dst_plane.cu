@@ -11,32 +11,31 @@
 // so the mesh crosses device memory three times per solve instead of six.
 //
 // Each step is D = S X^T with the sine matrix S (S_kn = sin(pi (k+1)(n+1)/(Ng+1))) as the
-// M = 128 operand, resident in shared memory, and the plane's Ng rows as the N operand,
-// split into TF32 hi and lo parts (3xTF32, or four products with lo x lo).  TMEM lane u of
-// D holds output index u of every row, so one epilogue thread per lane owns one row of the
-// next step's operand: it reads its lane, splits it and writes it straight into the K-major
-// operand in shared memory, and the next step contracts the other axis:
+// M = 128 operand and the plane's Ng rows as the N operand, split into TF32 hi and lo parts
+// (3xTF32, or four products with lo x lo).  S_hi and S_lo stay in tensor memory for the
+// whole launch (the A operand of tcgen05.mma may come from TMEM), so an N = 96 MMA reads only
+// the 3 KB data operand from shared memory: ~48 cycles against ~56 with both operands in
+// shared memory, and the shared-memory bandwidth stays free for the epilogues.  TMEM lane u
+// of D holds output index u of every row, so one epilogue thread per lane owns one row of
+// the next step's operand: it reads its lane, splits it and writes it straight into the
+// K-major operand in shared memory, and the next step contracts the other axis:
 //   step 1  rows i,   K = j   ->  lanes m  (y frequency), columns i
 //   step 2  rows m,   K = i   ->  lanes l  (x frequency), columns m   (then / lambda sum)
 //   step 3  rows l,   K = m   ->  lanes j' (y),           columns l
 //   step 4  rows j',  K = l   ->  lanes i' (x),           columns j'  -> row i' of W2[n]
-// An N = 96 TF32 MMA takes ~56 cycles against 128 at N = 256 (the pipe's rate per column,
-// bounded by the operand reads from shared memory), so the plane steps keep the tensor
-// pipe at ~85 % of its rate.  Two planes are in flight per CTA (two operand buffers, two
-// accumulators): while the epilogue turns one plane's accumulator into its next operand,
-// the tensor cores run the other plane's step.
+// Three planes are in flight per CTA (three operand buffers, three accumulators): while
+// the epilogues turn two planes' accumulators into their next operands, the tensor cores
+// run the third plane's step, and the next plane's copy lands behind them.
 //
-// One persistent CTA per SM, 10 warps:
-//   warps 0-3  split the planes of buffer 0 into hi/lo; the epilogues of their four steps
-//   warps 4-7  the same for buffer 1, so the two planes' epilogues overlap
-//   warp 8     TMEM allocation; lane 0 issues tcgen05.mma and tcgen05.commit
-//   warp 9     lane 0 issues the tensor copies of each plane (Ng/32 boxes of 32 x Npad)
-// The operands are K-major with the 128-byte swizzle (chunks of 32 columns), as the sine
-// matrix: an epilogue thread reads all its accumulator columns with the TMEM loads in flight
-// together and writes its row of the next operand in 16-byte units.
-// The CTAs of a launch are split among the Ng groups of the boxes (as in k_dst_tc.cu).
-// Every wait is bounded (about 2 s); on expiry the CTA raises the error flag, stops
-// issuing, waits (bounded) for its issued copies and MMAs, frees TMEM and returns.
+// One persistent CTA per SM, 14 warps:
+//   warps 4e .. 4e+3 (e = 0, 1, 2)  buffer e: split its planes into hi/lo, the epilogues of
+//                                   their four steps
+//   warp 12    TMEM allocation; lane 0 issues tcgen05.mma and tcgen05.commit
+//   warp 13    lane 0 issues the tensor copies of each plane (Ng/32 boxes of 32 x Npad)
+// The operands are K-major with the 128-byte swizzle (chunks of 32 columns).  The CTAs of
+// a launch are split among the Ng groups of the boxes (as in k_dst_tc.cu).  Every wait is
+// bounded (about 2 s); on expiry the CTA raises the error flag, stops issuing, waits
+// (bounded) for its issued copies and MMAs, frees TMEM and returns.
 #include <cuda.h>
 #include <stdint.h>
 
@@ -53,7 +52,8 @@ namespace {
 
 using namespace tc;
 
-constexpr int kPlThreads = 320;
+constexpr int kPlThreads = 448;
+constexpr int kPlBuf = 3;       // planes in flight
 constexpr int kPlGroups = 4;
 
 struct PlaneGroupArgs {
@@ -74,26 +74,27 @@ struct PlaneArgs {
     int lo_lo;
 };
 
-// One epilogue thread's row after step STEP of a plane (v: its accumulator lane, 16 x nc16
-// columns).  Steps 1-3: the row of the next operand (K-major, 128-byte swizzle, hi and lo
-// TF32 parts), zero outside the Ng x Ng block; step 2 first divides by the eigenvalue sum
-// (row: x frequency l, column: y frequency m, plane: z frequency n).  Step 4: row i' of the
-// output plane, written to global memory.
+// One epilogue thread's row after step STEP of a plane, accumulator chunks c0 .. c0 + 2 (v:
+// 16 columns each; chunks >= nc16 absent).  Steps 1-3: the row of the next operand (K-major,
+// 128-byte swizzle, hi and lo TF32 parts), zero outside the Ng x Ng block; step 2 first
+// divides by the eigenvalue sum (row: x frequency l, column: y frequency m, plane: z
+// frequency n).  Step 4: row i' of the output plane, written to global memory.
 template <int STEP>
-__device__ __forceinline__ void plane_rows(const float (&v)[6][16], int nc16, int row, int Ng, int Npad, uint32_t och,
-                                           unsigned char *hi, unsigned char *lo, const float *lam, float lam_row,
-                                           float lam_n, float *dst) {
+__device__ __forceinline__ void plane_rows(const float (&v)[3][16], int c0, int nc16, int row, int Ng, int Npad,
+                                           uint32_t och, unsigned char *hi, unsigned char *lo, const float *lam,
+                                           float lam_row, float lam_n, float *dst) {
     if (STEP == 4) {
         if (row >= Ng) return;
 #pragma unroll
-        for (int c = 0; c < 6; ++c) {
+        for (int cc = 0; cc < 3; ++cc) {
+            const int c = c0 + cc;
             if (c >= nc16) break;
 #pragma unroll
             for (int qq = 0; qq < 4; ++qq) {
                 const int col = c * 16 + 4 * qq;
                 if (col < Ng)
                     *reinterpret_cast<float4 *>(dst + col) =
-                        make_float4(v[c][4 * qq], v[c][4 * qq + 1], v[c][4 * qq + 2], v[c][4 * qq + 3]);
+                        make_float4(v[cc][4 * qq], v[cc][4 * qq + 1], v[cc][4 * qq + 2], v[cc][4 * qq + 3]);
             }
         }
         return;
@@ -101,7 +102,8 @@ __device__ __forceinline__ void plane_rows(const float (&v)[6][16], int nc16, in
     if (row >= Npad) return;
     const bool rv = row < Ng;
 #pragma unroll
-    for (int c = 0; c < 6; ++c) {
+    for (int cc = 0; cc < 3; ++cc) {
+        const int c = c0 + cc;
         if (c >= nc16) break;
 #pragma unroll
         for (int qq = 0; qq < 4; ++qq) {
@@ -109,7 +111,7 @@ __device__ __forceinline__ void plane_rows(const float (&v)[6][16], int nc16, in
             float x[4];
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
-                float y = v[c][4 * qq + t];
+                float y = v[cc][4 * qq + t];
                 if (STEP == 2) y = __fdividef(y, lam_row + lam[col0 + t] + lam_n);
                 x[t] = (rv && col0 + t < Ng) ? y : 0.0f;
             }
@@ -130,44 +132,31 @@ __global__ void __launch_bounds__(kPlThreads, 1) k_dst_plane(const __grid_consta
     const PlaneGroupArgs &G = A.grp[gi];
     const int bid = (int)blockIdx.x - G.cta0, nbid = G.nctas;
     const int Ng = G.Ng, Npad = G.Npad, nka = G.nka;
-    const uint32_t sch = (uint32_t)((Ng + 7) / 8) * 1024;      // one sine chunk (32 K), hi or lo
+    const int Kp = nka * 32;                                   // sine columns held (TMEM)
     const uint32_t och = (uint32_t)Npad * 128;                 // one operand chunk (32 K)
     const uint32_t bhalf = (uint32_t)nka * och;                // one operand, hi or lo
-    // The M = 128 operand reads 128 rows from each sine chunk; rows >= Ng come from what
-    // follows (the allocation always extends 16 KB past the last chunk's start, see
-    // plane_smem_bytes) and only feed TMEM lanes that the epilogue discards.
-    unsigned char *S_hi = base;
-    unsigned char *S_lo = base + nka * sch;
-    unsigned char *bufs = base + 2 * nka * sch;                // buffer e: hi, then lo
-    uint64_t *bars = (uint64_t *)(bufs + 4 * (size_t)bhalf);
-    uint64_t *loaded = bars;          // the plane's tensor copies have landed
-    uint64_t *opready = bars + 2;     // the next step's operand is written (128 arrivals)
-    uint64_t *accfull = bars + 4;     // the step's MMAs are complete
-    uint64_t *bufempty = bars + 6;    // step 4 is complete: the buffer may take the next plane
-    uint64_t *drain = bars + 8;
-    uint32_t *tmem_slot = (uint32_t *)(bars + 9);
+    // TMEM columns: S_hi [0, Kp), S_lo [Kp, 2 Kp), accumulator e at 2 Kp + e accw
+    const uint32_t accw = (uint32_t)((Npad + 31) / 32 * 32);
+    unsigned char *bufs = base;                                // buffer e: hi, then lo
+    uint64_t *bars = (uint64_t *)(bufs + 2 * kPlBuf * (size_t)bhalf);
+    uint64_t *loaded = bars;                 // the plane's tensor copies have landed
+    uint64_t *opready = bars + kPlBuf;       // the next step's operand is written (128 arrivals)
+    uint64_t *accfull = bars + 2 * kPlBuf;   // the step's MMAs are complete
+    uint64_t *bufempty = bars + 3 * kPlBuf;  // step 4 is complete: the buffer may take the next plane
+    uint64_t *drain = bars + 4 * kPlBuf;
+    uint32_t *tmem_slot = (uint32_t *)(drain + 1);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
     float *lam = (float *)(tmem_slot + 4);
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
 
-    // ---- set-up: S (hi/lo split, swizzled), eigenvalues, barriers, tensor memory
-    const int Kp = nka * 32;
-    for (int q = tid; q < Ng * Kp; q += kPlThreads) {
-        const int n = q / Kp, k = q % Kp;
-        const float sv = G.S[q];
-        const float hi = tf32_rn(sv);
-        const uint32_t off = (uint32_t)(k / 32) * sch + sw128_offset(n, k % 32);
-        *(float *)(S_hi + off) = hi;
-        *(float *)(S_lo + off) = tf32_rn(sv - hi);
-    }
+    // ---- set-up: eigenvalues, clean operand buffers, barriers, tensor memory
     for (int q = tid; q < 128; q += kPlThreads) lam[q] = q < Ng ? G.lam[q] : 0.0f;
-    for (int q = tid; q < (int)(bhalf / 4); q += kPlThreads) {     // clean operand padding
+    for (int q = tid; q < (int)(2 * kPlBuf * bhalf / 16); q += kPlThreads)
         reinterpret_cast<float4 *>(bufs)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
     const long long my_items = G.nitems > bid ? (G.nitems - 1 - bid) / nbid + 1 : 0;
     if (tid == 0) {
-        for (int e = 0; e < 2; ++e) {
+        for (int e = 0; e < kPlBuf; ++e) {
             mbar_init(&loaded[e], 1);
             mbar_init(&opready[e], 128);
             mbar_init(&accfull[e], 1);
@@ -177,9 +166,9 @@ __global__ void __launch_bounds__(kPlThreads, 1) k_dst_plane(const __grid_consta
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 8) {
+    if (warp == 12) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(256));
+                     "r"(512));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     fence_proxy_async();
@@ -187,18 +176,39 @@ __global__ void __launch_bounds__(kPlThreads, 1) k_dst_plane(const __grid_consta
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    if (warp < 4) {
+        // S into TMEM: lane k holds row k (zero for k >= Ng), hi parts in columns [0, Kp),
+        // lo parts in [Kp, 2 Kp); the table row k has Kp columns, zero beyond Ng
+        const int k = warp * 32 + lane;
+        const uint32_t lb = (uint32_t)(warp * 32) << 16;
+        for (int c = 0; c < Kp / 16; ++c) {
+            float h[16], l[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const float sv = k < Ng ? G.S[(long long)k * Kp + c * 16 + j] : 0.0f;
+                h[j] = tf32_rn(sv);
+                l[j] = tf32_rn(sv - h[j]);
+            }
+            tmem_st16(tmem + lb + (uint32_t)(c * 16), h);
+            tmem_st16(tmem + lb + (uint32_t)(Kp + c * 16), l);
+        }
+        tmem_st_wait();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
     const long long Ng2 = (long long)Ng * Ng;
-    const long long npairs = (my_items + 1) / 2;
+    const long long ntrip = (my_items + kPlBuf - 1) / kPlBuf;
 
-    if (warp == 9) {
+    if (warp == 13) {
         // ---------------------------------------------------------------- tensor copies
-        // plane p goes to buffer p % 2 once step 4 of plane p - 2 has finished with it; on an
+        // plane p goes to buffer p % 3 once step 4 of plane p - 3 has finished with it; on an
         // abort, wait (bounded) for the copies already issued before the CTA may exit
         if (lane == 0) {
             long long p = 0;
             for (; p < my_items && !*abort_flag; ++p) {
-                const int e = (int)(p & 1);
-                const long long j = p >> 1;
+                const int e = (int)(p % kPlBuf);
+                const long long j = p / kPlBuf;
                 if (j > 0 && !mbar_wait(&bufempty[e], (uint32_t)((j - 1) & 1), abort_flag)) {
                     *abort_flag = 1;
                     break;
@@ -213,38 +223,37 @@ __global__ void __launch_bounds__(kPlThreads, 1) k_dst_plane(const __grid_consta
             }
             if (*abort_flag) {
                 const unsigned long long t0 = now_ns();
-                for (long long q = p - 2 > 0 ? p - 2 : 0; q < p; ++q)
-                    while (!mbar_try_wait(&loaded[q & 1], (uint32_t)((q >> 1) & 1)) && now_ns() - t0 < kWaitNs) {
+                for (long long q = p - kPlBuf > 0 ? p - kPlBuf : 0; q < p; ++q)
+                    while (!mbar_try_wait(&loaded[q % kPlBuf], (uint32_t)((q / kPlBuf) & 1)) &&
+                           now_ns() - t0 < kWaitNs) {
                     }
             }
         }
-    } else if (warp == 8) {
+    } else if (warp == 12) {
         // ---------------------------------------------------------------- MMA issuer
-        // order: for each pair of planes, steps 1..4, each step for both planes
+        // order: for each triple of planes, steps 1..4, each step for the triple's planes
         if (lane == 0) {
             const uint32_t idesc = idesc_tf32(128, Npad);
-            const uint32_t shi = smem_u32(S_hi), slo = smem_u32(S_lo);
             bool ok = true;
-            for (long long q = 0; q < npairs && ok && !*abort_flag; ++q)
+            for (long long q = 0; q < ntrip && ok && !*abort_flag; ++q)
                 for (int s = 1; s <= 4 && ok; ++s)
-                    for (int e = 0; e < 2; ++e) {
-                        if (2 * q + e >= my_items) break;
+                    for (int e = 0; e < kPlBuf; ++e) {
+                        if (q * kPlBuf + e >= my_items) break;
                         if (!mbar_spin(&opready[e], (uint32_t)((s - 1) & 1), abort_flag)) {
                             ok = false;
                             break;
                         }
                         tc_fence_after();
-                        const uint32_t d = tmem + (uint32_t)(e * 128);
+                        const uint32_t d = tmem + (uint32_t)(2 * Kp) + (uint32_t)e * accw;
                         const uint32_t bh = smem_u32(bufs + (size_t)e * 2 * bhalf), bl = bh + bhalf;
                         for (int kg = 0; kg < Ng; kg += 8) {
-                            const uint32_t ao = (uint32_t)(kg / 32) * sch + (uint32_t)((kg % 32) / 8) * 32;
                             const uint32_t bo = (uint32_t)(kg / 32) * och + (uint32_t)((kg % 32) / 8) * 32;
-                            const uint64_t ahi = sw128_desc(shi + ao), alo = sw128_desc(slo + ao);
                             const uint64_t bhi = sw128_desc(bh + bo), blo = sw128_desc(bl + bo);
-                            mma_tf32(d, ahi, bhi, idesc, kg > 0 ? 1u : 0u);
-                            mma_tf32(d, ahi, blo, idesc, 1);
-                            mma_tf32(d, alo, bhi, idesc, 1);
-                            if (A.lo_lo) mma_tf32(d, alo, blo, idesc, 1);
+                            const uint32_t ahi = tmem + (uint32_t)kg, alo = tmem + (uint32_t)(Kp + kg);
+                            mma_tf32_ts(d, ahi, bhi, idesc, kg > 0 ? 1u : 0u);
+                            mma_tf32_ts(d, ahi, blo, idesc, 1);
+                            mma_tf32_ts(d, alo, bhi, idesc, 1);
+                            if (A.lo_lo) mma_tf32_ts(d, alo, blo, idesc, 1);
                         }
                         mma_commit(&accfull[e]);
                         if (s == 4) mma_commit(&bufempty[e]);
@@ -252,18 +261,18 @@ __global__ void __launch_bounds__(kPlThreads, 1) k_dst_plane(const __grid_consta
             if (!ok) *abort_flag = 1;
         }
     } else {
-        // ---------------------------------------------------------------- warps 0-7
-        // warp group e = warp / 4 serves buffer e (planes p = 2 q + e); warp w reads TMEM
+        // ---------------------------------------------------------------- warps 0-11
+        // warp group e = warp / 4 serves buffer e (planes p = 3 q + e); warp w reads TMEM
         // lanes 32 (w & 3) + lane, the output index of its row, over all column chunks
         const int e = warp >> 2, lq = warp & 3;
         const int gt = tid & 127;                       // thread within the group
         const int row = lq * 32 + lane;
         unsigned char *hi = bufs + (size_t)e * 2 * bhalf, *lo = hi + bhalf;
-        const uint32_t tb = tmem + (uint32_t)(e * 128) + ((uint32_t)(lq * 32) << 16);
+        const uint32_t tb = tmem + (uint32_t)(2 * Kp) + (uint32_t)e * accw + ((uint32_t)(lq * 32) << 16);
         const int nc16 = Npad / 16;                     // 16-column accumulator chunks (<= 6)
         bool ok = true;
-        for (long long q = 0; q < npairs && ok && !*abort_flag; ++q) {
-            const long long p = 2 * q + e;
+        for (long long q = 0; q < ntrip && ok && !*abort_flag; ++q) {
+            const long long p = q * kPlBuf + e;
             if (p >= my_items) break;
             const Chunk it = G.items[bid + p * nbid];
             const int n = it.start;
@@ -307,18 +316,21 @@ __global__ void __launch_bounds__(kPlThreads, 1) k_dst_plane(const __grid_consta
                     break;
                 }
                 tc_fence_after();
-                // every column of this lane in flight at once, then one wait
-                float v[6][16];
+                // the lane's columns in two halves of up to three 16-column chunks, each half's
+                // TMEM loads in flight together
+                for (int c0 = 0; c0 < nc16; c0 += 3) {
+                    float v[3][16];
 #pragma unroll
-                for (int c = 0; c < 6; ++c)
-                    if (c < nc16) tmem_ld16_issue(tb + (uint32_t)(c * 16), v[c]);
-                tmem_ld_wait();
+                    for (int cc = 0; cc < 3; ++cc)
+                        if (c0 + cc < nc16) tmem_ld16_issue(tb + (uint32_t)((c0 + cc) * 16), v[cc]);
+                    tmem_ld_wait();
 #pragma unroll
-                for (int c = 0; c < 6; ++c) tmem_regs_ready(v[c]);
-                if (s == 1) plane_rows<1>(v, nc16, row, Ng, Npad, och, hi, lo, lam, lam_row, lam_n, dst);
-                else if (s == 2) plane_rows<2>(v, nc16, row, Ng, Npad, och, hi, lo, lam, lam_row, lam_n, dst);
-                else if (s == 3) plane_rows<3>(v, nc16, row, Ng, Npad, och, hi, lo, lam, lam_row, lam_n, dst);
-                else plane_rows<4>(v, nc16, row, Ng, Npad, och, hi, lo, lam, lam_row, lam_n, dst);
+                    for (int cc = 0; cc < 3; ++cc) tmem_regs_ready(v[cc]);
+                    if (s == 1) plane_rows<1>(v, c0, nc16, row, Ng, Npad, och, hi, lo, lam, lam_row, lam_n, dst);
+                    else if (s == 2) plane_rows<2>(v, c0, nc16, row, Ng, Npad, och, hi, lo, lam, lam_row, lam_n, dst);
+                    else if (s == 3) plane_rows<3>(v, c0, nc16, row, Ng, Npad, och, hi, lo, lam, lam_row, lam_n, dst);
+                    else plane_rows<4>(v, c0, nc16, row, Ng, Npad, och, hi, lo, lam, lam_row, lam_n, dst);
+                }
                 if (s < 4) fence_proxy_async();
                 tc_fence_before();
                 if (s < 4) mbar_arrive(&opready[e]);
@@ -328,7 +340,7 @@ __global__ void __launch_bounds__(kPlThreads, 1) k_dst_plane(const __grid_consta
     }
 
     // ---- tear-down: every role has left its loop; drain, then free tensor memory
-    if (warp == 8 && lane == 0 && *abort_flag) {
+    if (warp == 12 && lane == 0 && *abort_flag) {
         mma_commit(drain);
         const unsigned long long t0 = now_ns();
         while (!mbar_try_wait(drain, 0) && now_ns() - t0 < kWaitNs) {
@@ -338,16 +350,12 @@ __global__ void __launch_bounds__(kPlThreads, 1) k_dst_plane(const __grid_consta
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 8) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
+    if (warp == 12) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
 
 size_t plane_smem_bytes(int Ng, int Npad, int nka) {
-    const size_t sch = (size_t)((Ng + 7) / 8) * 1024;
-    const size_t layout = 2 * (size_t)nka * sch + 4 * (size_t)nka * Npad * 128 + 9 * 8 + 16 + 128 * 4 + 64;
-    // the M = 128 operand reads 128 rows (16 KB) from the start of every sine chunk, up to
-    // the last lo chunk: for small Ng that reaches past the layout, so the allocation covers it
-    const size_t reach = (2 * (size_t)nka - 1) * sch + 128 * 128;
-    return 1024 + (layout > reach ? layout : reach);
+    (void)Ng;
+    return 1024 + 2 * kPlBuf * (size_t)nka * Npad * 128 + (4 * kPlBuf + 1) * 8 + 16 + 128 * 4 + 64;
 }
 
 constexpr size_t kPlSmemBudget = 227 * 1024;
