@@ -234,6 +234,7 @@ __global__ void __launch_bounds__(kPlThreads, 1) k_dst_plane(const __grid_consta
         // order: for each triple of planes, steps 1..4, each step for the triple's planes
         if (lane == 0) {
             const uint32_t idesc = idesc_tf32(128, Npad);
+            const bool lo_lo = A.lo_lo != 0;
             bool ok = true;
             for (long long q = 0; q < ntrip && ok && !*abort_flag; ++q)
                 for (int s = 1; s <= 4 && ok; ++s)
@@ -245,15 +246,33 @@ __global__ void __launch_bounds__(kPlThreads, 1) k_dst_plane(const __grid_consta
                         }
                         tc_fence_after();
                         const uint32_t d = tmem + (uint32_t)(2 * Kp) + (uint32_t)e * accw;
-                        const uint32_t bh = smem_u32(bufs + (size_t)e * 2 * bhalf), bl = bh + bhalf;
-                        for (int kg = 0; kg < Ng; kg += 8) {
-                            const uint32_t bo = (uint32_t)(kg / 32) * och + (uint32_t)((kg % 32) / 8) * 32;
-                            const uint64_t bhi = sw128_desc(bh + bo), blo = sw128_desc(bl + bo);
-                            const uint32_t ahi = tmem + (uint32_t)kg, alo = tmem + (uint32_t)(Kp + kg);
-                            mma_tf32_ts(d, ahi, bhi, idesc, kg > 0 ? 1u : 0u);
-                            mma_tf32_ts(d, ahi, blo, idesc, 1);
-                            mma_tf32_ts(d, alo, bhi, idesc, 1);
-                            if (A.lo_lo) mma_tf32_ts(d, alo, blo, idesc, 1);
+                        // descriptors advance by (byte offset >> 4) in their address field
+                        // (shared addresses < 2^18: no carry out of the field)
+                        const uint64_t bh0 = sw128_desc(smem_u32(bufs + (size_t)e * 2 * bhalf));
+                        const uint64_t bl0 = bh0 + (bhalf >> 4);
+                        for (int kc = 0; kc < nka; ++kc) {
+                            const uint64_t bhc = bh0 + ((uint64_t)kc * (och >> 4)), blc = bl0 + ((uint64_t)kc * (och >> 4));
+                            const uint32_t ahc = tmem + (uint32_t)(kc * 32), alc = ahc + (uint32_t)Kp;
+                            if (lo_lo) {
+#pragma unroll
+                                for (int kk = 0; kk < 4; ++kk) {
+                                    if (kc * 32 + kk * 8 >= Ng) break;
+                                    const uint64_t bhi = bhc + (uint64_t)(kk * 2), blo = blc + (uint64_t)(kk * 2);
+                                    mma_tf32_ts(d, ahc + kk * 8, bhi, idesc, (kc | kk) ? 1u : 0u);
+                                    mma_tf32_ts(d, ahc + kk * 8, blo, idesc, 1);
+                                    mma_tf32_ts(d, alc + kk * 8, bhi, idesc, 1);
+                                    mma_tf32_ts(d, alc + kk * 8, blo, idesc, 1);
+                                }
+                            } else {
+#pragma unroll
+                                for (int kk = 0; kk < 4; ++kk) {
+                                    if (kc * 32 + kk * 8 >= Ng) break;
+                                    const uint64_t bhi = bhc + (uint64_t)(kk * 2), blo = blc + (uint64_t)(kk * 2);
+                                    mma_tf32_ts(d, ahc + kk * 8, bhi, idesc, (kc | kk) ? 1u : 0u);
+                                    mma_tf32_ts(d, ahc + kk * 8, blo, idesc, 1);
+                                    mma_tf32_ts(d, alc + kk * 8, bhi, idesc, 1);
+                                }
+                            }
                         }
                         mma_commit(&accfull[e]);
                         if (s == 4) mma_commit(&bufempty[e]);
