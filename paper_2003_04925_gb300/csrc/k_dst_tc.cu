@@ -475,36 +475,41 @@ __global__ void __launch_bounds__(kThreads, 1) k_dst_tc(const __grid_constant__ 
             const uint32_t tbase = tmem + (uint32_t)(a * kTN + half * 128) + ((uint32_t)n0 << 16);
             if (PASS == P_ZM) {
                 // lane = output k of this warp's quarter, columns = cells q of its half tile:
-                // padded Phi[i + gp][j + gp][k + gp], 32 lanes -> 32 consecutive floats
+                // padded Phi[i + gp][j + gp][k + gp], 32 lanes -> 32 consecutive floats.  Two
+                // batches of 64 columns, each with its TMEM loads in flight together; the
+                // padded offset steps by one row (S) per cell, by 2 gp rows more per mesh row
                 const int gp = ti.pad;
-                const long long S = Ng + 2 * gp;
+                const int S = Ng + 2 * gp;                  // padded box < 2^31 floats
 #pragma unroll 1
-                for (int g16 = 0; g16 < 8; ++g16) {
-                    float v[16];
+                for (int b64 = 0; b64 < 2; ++b64) {
+                    float v[4][16];
                     if (ncol > 0) {
-                        tmem_ld16_issue(tbase + (uint32_t)(g16 * 16), v);
+#pragma unroll
+                        for (int cc = 0; cc < 4; ++cc) tmem_ld16_issue(tbase + (uint32_t)(b64 * 64 + cc * 16), v[cc]);
                         tmem_ld_wait();
-                        tmem_regs_ready(v);
+#pragma unroll
+                        for (int cc = 0; cc < 4; ++cc) tmem_regs_ready(v[cc]);
                     }
-                    if (g16 == 7) {
+                    if (b64 == 1) {
                         tc_fence_before();
                         mbar_arrive(&tempty[a]);
                     }
                     if (ncol > 0 && lane < ncol) {
-                        // cell q = i Ng + jj (q < Ng^2 < 2^31): one division per 16 cells, then
-                        // step along the row
-                        const int q0 = ti.row0 + half * 128 + g16 * 16;
-                        int i = q0 / Ng, jj = q0 - i * Ng;
+                        const int q0 = ti.row0 + half * 128 + b64 * 64;
+                        int jj = q0 % Ng;
+                        int off = ((q0 / Ng + gp) * S + (jj + gp)) * S;
                         float *dst = A.out + ti.pp_off + gp + n0 + lane;
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            if (q0 + j < Ng2)
-                                dst[((long long)(i + gp) * S + (jj + gp)) * S] = v[j] * scale;
-                            if (++jj == Ng) {
-                                jj = 0;
-                                ++i;
+                        for (int cc = 0; cc < 4; ++cc)
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) {
+                                if (q0 + cc * 16 + j < Ng2) dst[off] = v[cc][j] * scale;
+                                off += S;
+                                if (++jj == Ng) {
+                                    jj = 0;
+                                    off += 2 * gp * S;
+                                }
                             }
-                        }
                     }
                     __syncwarp();
                 }
