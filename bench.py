@@ -55,6 +55,9 @@ def parse():
                     help="boxes per streamed batch (0: the library's choice)")
     ap.add_argument("--tcola-only", action="store_true",
                     help="only W + K periodic tCOLA runs of the workload's particles (for ncu captures)")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="the batched throughput, e2e and roofline only: no per-tile form, adjoint or study "
+                         "legs (for the large workloads)")
     return ap.parse_args()
 
 
@@ -612,7 +615,7 @@ def run_gpu(args, rank, world, local_rank):
     details = {}
     per_tile = adj = None
     roofline = None
-    if world == 1:
+    if world == 1 and not args.headline_only:
         per_tile = per_tile_cost(sc, torch, kw, w, x, p, ms, max(1, args.steps // 2), world)
     # per-kernel device time from events recorded between the kernels of the graph
     sc.scola_set_profiling(sim.ctx, True)
@@ -637,7 +640,7 @@ def run_gpu(args, rank, world, local_rank):
                               "traffic": traffic.get(cls[k])} for k, v in rows.items()}
     details["traffic_source"] = ("profiles/traffic_%s.json (ncu, DRAM read + write per force evaluation; "
                                  "null where the kernel changed since the capture)" % args.workload)
-    if world == 1:
+    if world == 1 and not args.headline_only:
         adj = adjoint_cost(sc, torch, args.dst, max(2, min(args.steps, 5)))
         details["study"] = study_cost(sc, torch, {k: v for k, v in kw.items()}, W, max(2, min(args.steps, 5)),
                                       peaks)

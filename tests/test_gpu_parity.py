@@ -367,11 +367,17 @@ def test_dst_autotuner_keeps_one_form(name):
     xa, pa = auto.forward(w)
     torch.cuda.synchronize()
     st = auto.stats()
-    assert st["dst_form"] in (sc.SCOLA_DST_TC_3XTF32, sc.SCOLA_DST_SIMT)
-    assert all(t > 0 for t in st["ms_dst_candidates"])
-    assert (st["dst_form"] == sc.SCOLA_DST_TC_3XTF32) == (st["ms_dst_candidates"][0] <= st["ms_dst_candidates"][1])
-    print("dst autotuner %s: tensor cores %.4f ms, FP32 %.4f ms per solve" % ((name,) + tuple(st["ms_dst_candidates"])))
-    assert sc.scola_uses_tensor_cores(auto.ctx) == (1 if st["dst_form"] == sc.SCOLA_DST_TC_3XTF32 else 0)
+    # candidates: six-pass tensor cores, FP32, three-pass tensor cores (timed where every Ng
+    # allows it: Ng <= 96, Ng % 4 == 0); the kept form is the fastest timed one
+    forms = (sc.SCOLA_DST_TC_3XTF32, sc.SCOLA_DST_SIMT, sc.SCOLA_DST_TC_3PASS)
+    cand = st["ms_dst_candidates"]
+    three = all(g <= 96 and g % 4 == 0 for g in _mesh_sizes(kw))
+    assert cand[0] > 0 and cand[1] > 0 and (cand[2] > 0) == three, cand
+    timed = [(t, f) for t, f in zip(cand, forms) if t > 0]
+    assert st["dst_form"] == min(timed)[1], (st["dst_form"], cand)
+    print("dst autotuner %s: six-pass tensor cores %.4f ms, FP32 %.4f ms, three-pass %.4f ms per solve"
+          % ((name,) + tuple(cand)))
+    assert sc.scola_uses_tensor_cores(auto.ctx) == (0 if st["dst_form"] == sc.SCOLA_DST_SIMT else 1)
     auto.close()
     fixed = sc.Scola(**dict(lib_kwargs(kw), dst_variant=st["dst_form"]))
     xf, pf = fixed.forward(w)
