@@ -393,7 +393,7 @@ def study_cost(sc, torch, kw, W, steps, peaks):
 
 
 # ----------------------------------------------------------------------------- roofline
-def kernel_roofline(kt, kw, clocks, peaks, form):
+def kernel_roofline(kt, kw, clocks, peaks, form, box_frac=1.0):
     """Algorithmic bytes or flops per launch of each kernel class and the dominant one.
 
     FP32 form: the five DST passes are dense products on CUDA cores (ALU bound,
@@ -403,10 +403,11 @@ def kernel_roofline(kt, kw, clocks, peaks, form):
     Poisson source written once (4 B per cell).
     """
     nsc, ng = box_sizes(kw)
-    P = sum(n**3 for n in nsc)
-    M = sum(g**3 for g in ng)
-    MP = sum((g + 4) ** 3 for g in ng)
-    dense = sum(2.0 * g * g**3 for g in ng)          # flops of one dense DST-I along one axis
+    # box_frac: the share of the boxes one launch processes (streamed batches: one batch)
+    P = box_frac * sum(n**3 for n in nsc)
+    M = box_frac * sum(g**3 for g in ng)
+    MP = box_frac * sum((g + 4) ** 3 for g in ng)
+    dense = box_frac * sum(2.0 * g * g**3 for g in ng)   # flops of one dense DST-I along one axis
     work = {"deposit": ("hbm", 12.0 * P + 4.0 * M),
             "kick_drift": ("hbm", 72.0 * P + 4.0 * MP)}
     if form == "tc3":
@@ -624,7 +625,9 @@ def run_gpu(args, rank, world, local_rank):
     torch.cuda.synchronize()
     kt = sc.scola_kernel_times(sim.ctx)
     sc.scola_set_profiling(sim.ctx, False)
-    dom, rows = kernel_roofline(kt, kw, clk, peaks, args.dst)
+    st = sim.stats()
+    box_frac = st["batch_boxes"] / st["nboxes"] if st["batches"] > 1 else 1.0
+    dom, rows = kernel_roofline(kt, kw, clk, peaks, args.dst, box_frac)
     sc.scola_device_status(sim.ctx)
     d = rows[dom]
     # ncu DRAM bytes per evaluation, keyed by class (dst_i: the i-th pass)
