@@ -45,10 +45,11 @@ def parse():
     ap.add_argument("--impl", default="scola", choices=["scola", "reference"])
     ap.add_argument("--workload", default="batched_128")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--dst", default="auto", choices=["auto", "tc", "tc4", "tc3", "simt"],
+    ap.add_argument("--dst", default="auto", choices=["auto", "tc", "tc4", "tc3", "simt", "radix"],
                     help="Poisson-solve form: the library's autotuner (auto, default: the fastest of the "
                          "tensor-core forms and FP32 CUDA cores), tensor-core 3xTF32 in six passes (tc), "
-                         "4xTF32 (tc4), 3xTF32 in three passes (tc3) or FP32 CUDA cores (simt)")
+                         "4xTF32 (tc4), 3xTF32 in three passes (tc3), dense FP32 CUDA cores (simt) or radix "
+                         "(Bluestein) FP32 transforms (radix)")
     ap.add_argument("--forward-only", action="store_true",
                     help="only W + K forward runs of the batched form (for ncu launch lists)")
     ap.add_argument("--batch-boxes", type=int, default=0,
@@ -398,8 +399,8 @@ def kernel_roofline(kt, kw, clocks, peaks, form, box_frac=1.0):
 
     FP32 form: the five DST passes are dense products on CUDA cores (ALU bound,
     2 Ng flops per cell per transform; pass 3 does two transforms).  Tensor-core
-    forms: six passes (or three), each streaming its mesh once (HBM bound: 4 B read
-    + 4 B written per cell).  Deposit: the positions once (12 B per particle) and the
+    and radix forms: six passes (or three), each streaming its mesh once (HBM bound:
+    4 B read + 4 B written per cell).  Deposit: the positions once (12 B per particle) and the
     Poisson source written once (4 B per cell).
     """
     nsc, ng = box_sizes(kw)
@@ -416,7 +417,9 @@ def kernel_roofline(kt, kw, clocks, peaks, form, box_frac=1.0):
         names = ["dst_1_z_fwd", "dst_2_plane", "dst_3_z_inv", None, None, None]
         for nm in names[:3]:
             work[nm] = ("hbm", 8.0 * M)
-    elif form in ("tc", "tc4"):
+    elif form in ("tc", "tc4", "radix"):
+        # six one-axis passes (tensor-core products, or radix transforms on CUDA cores), each
+        # streaming its mesh once
         names = ["dst_1_z_fwd", "dst_2_y_fwd", "dst_3_x_fwd_div", "dst_4_z_inv", "dst_5_y_inv",
                  "dst_6_x_inv"]
         for i, nm in enumerate(names):
@@ -551,7 +554,7 @@ def run_gpu(args, rank, world, local_rank):
     if args.dst == "auto":
         # the form the autotuner kept; every later context of this run asks for it
         args.dst = {sc.SCOLA_DST_TC_3XTF32: "tc", sc.SCOLA_DST_TC_4XTF32: "tc4", sc.SCOLA_DST_TC_3PASS: "tc3",
-                    sc.SCOLA_DST_SIMT: "simt"}[sim.stats()["dst_form"]]
+                    sc.SCOLA_DST_SIMT: "simt", sc.SCOLA_DST_RADIX: "radix"}[sim.stats()["dst_form"]]
         kw["dst_variant"] = dst_code(sc, args.dst)
     if args.forward_only:
         t0 = time.perf_counter()
@@ -669,7 +672,8 @@ def run_gpu(args, rank, world, local_rank):
                     "l2": "working set %.2f GB > 129 MB L2, no flush" % (ws_bytes / 1e9),
                     "parallelism": "boxes split over %d GPU(s)" % world,
                     "dst": {"tc": "tcgen05 3xTF32, six passes", "tc4": "tcgen05 4xTF32, six passes",
-                            "tc3": "tcgen05 3xTF32, three passes", "simt": "FP32 CUDA cores"}[args.dst]}),
+                            "tc3": "tcgen05 3xTF32, three passes", "simt": "FP32 CUDA cores",
+                            "radix": "FP32 CUDA cores, radix (Bluestein) transforms"}[args.dst]}),
                 "gpu_launches": int(launches * args.steps), "clocks": clk,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e}
         if per_tile is not None:
@@ -703,16 +707,19 @@ def dst_choice(sc, st):
     """The Poisson-solve form in use and, under the autotuner, the candidates it timed (ms per
     solve of all boxes; both forms meet the accuracy bound)."""
     names = {sc.SCOLA_DST_TC_3XTF32: "tensor cores, 3xTF32, six passes", sc.SCOLA_DST_TC_4XTF32: "tensor cores, 4xTF32",
-             sc.SCOLA_DST_TC_3PASS: "tensor cores, 3xTF32, three passes", sc.SCOLA_DST_SIMT: "FP32 CUDA cores"}
+             sc.SCOLA_DST_TC_3PASS: "tensor cores, 3xTF32, three passes", sc.SCOLA_DST_SIMT: "FP32 CUDA cores",
+             sc.SCOLA_DST_RADIX: "FP32 CUDA cores, radix (Bluestein) transforms"}
     cand = st["ms_dst_candidates"]
-    order = ("tensor cores, 3xTF32, six passes", "FP32 CUDA cores", "tensor cores, 3xTF32, three passes")
+    order = ("tensor cores, 3xTF32, six passes", "FP32 CUDA cores", "tensor cores, 3xTF32, three passes",
+             "FP32 CUDA cores, radix (Bluestein) transforms")
     return {"kept": names.get(st["dst_form"], "not chosen"),
             "candidates_ms": {n: round(t, 4) for n, t in zip(order, cand) if t > 0}}
 
 
 def dst_code(sc, name):
     return {"auto": sc.SCOLA_DST_AUTO, "tc": sc.SCOLA_DST_TC_3XTF32, "tc4": sc.SCOLA_DST_TC_4XTF32,
-            "tc3": sc.SCOLA_DST_TC_3PASS, "simt": sc.SCOLA_DST_SIMT}[name]
+            "tc3": sc.SCOLA_DST_TC_3PASS, "simt": sc.SCOLA_DST_SIMT,
+            "radix": sc.SCOLA_DST_RADIX}[name]
 
 
 def main():

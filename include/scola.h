@@ -58,10 +58,16 @@ typedef enum scola_dst_variant {
                                     forward; every z-frequency plane transformed along y and x,
                                     divided and transformed back in shared memory; z inverse.
                                     Every Ng <= 96 with Ng % 4 == 0 (UNSUPPORTED otherwise) */
+    SCOLA_DST_RADIX = 5,         /* fast sine transforms on FP32 CUDA cores, O(Ng log Ng) per
+                                    pencil: each DST-I of length Ng from a real DFT of length
+                                    Ng + 1 (two pencils per complex transform), done by
+                                    Bluestein's chirp convolution with radix-2 FFTs of a power-of-two
+                                    length in shared memory; every 1 <= Ng <= 256 */
     SCOLA_DST_AUTO = 2           /* the fastest of the tensor-core forms (six passes, and three
-                                    where every Ng allows it) and the FP32 form, timed once on
-                                    the context's boxes before the first evolution (the FP32 form
-                                    alone where some Ng excludes the tensor cores) */
+                                    where every Ng allows it), the dense FP32 form and the radix
+                                    form, timed once on the context's boxes before the first
+                                    evolution (where Ng > 222 excludes the dense FP32 form: the
+                                    six-pass tensor-core form alone) */
 } scola_dst_variant;
 
 typedef enum scola_deposit_form {
@@ -211,9 +217,9 @@ typedef struct scola_stats {
     int32_t dst_form;             /* the Poisson-solve form in use (scola_dst_variant) once chosen:
                                      the requested one, or the autotuner's pick under AUTO
                                      (0 until the first scola_forward / scola_setup_boxes) */
-    double ms_dst_candidates[3];  /* AUTO: autotuner timings of one Poisson solve: tensor cores
-                                     in six passes, FP32, tensor cores in three passes; 0 = not
-                                     timed */
+    double ms_dst_candidates[4];  /* AUTO: autotuner timings of one Poisson solve: tensor cores
+                                     in six passes, dense FP32, tensor cores in three passes,
+                                     radix FP32; 0 = not timed */
 } scola_stats;
 
 /*

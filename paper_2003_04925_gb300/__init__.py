@@ -11,7 +11,7 @@ from .binding import (  # noqa: F401
     EXPORTED, KERNEL_CLASSES, SCOLA_BATCH_ALL, SCOLA_BATCH_PER_TILE, SCOLA_DEPOSIT_ATOMIC,
     SCOLA_DEPOSIT_AUTO, SCOLA_DEPOSIT_SORTED, SCOLA_STEPPING_MODIFIED, SCOLA_STEPPING_STANDARD, SCOLA_DST_AUTO, SCOLA_DST_SIMT,
     SCOLA_STUDY_NONE, SCOLA_STUDY_TRUE_DENSITY, SCOLA_STUDY_TRUE_POTENTIAL,
-    SCOLA_DST_TC_3XTF32, SCOLA_DST_TC_4XTF32, SCOLA_DST_TC_3PASS, ScolaError, ScolaParams, make_params,
+    SCOLA_DST_TC_3XTF32, SCOLA_DST_TC_4XTF32, SCOLA_DST_TC_3PASS, SCOLA_DST_RADIX, ScolaError, ScolaParams, make_params,
     scola_backward, scola_backward_density, scola_checkpoint_interval, scola_box_density_noalloc, scola_box_mass, scola_box_offsets, scola_box_particle_count, scola_box_particle_ids,
     scola_create, scola_density_adjoint, scola_destroy, scola_device_status, scola_final_density, scola_forward,
     scola_forward_host, scola_generate_white_noise, scola_get_stats, scola_kernel_times, scola_last_error, scola_lpt_fields,

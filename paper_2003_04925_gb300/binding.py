@@ -19,6 +19,7 @@ SCOLA_DST_SIMT = 0
 SCOLA_DST_TC_3XTF32 = 1
 SCOLA_DST_TC_4XTF32 = 3
 SCOLA_DST_TC_3PASS = 4
+SCOLA_DST_RADIX = 5
 SCOLA_DST_AUTO = 2
 SCOLA_BATCH_ALL = 0
 SCOLA_BATCH_PER_TILE = 1
@@ -58,7 +59,7 @@ class ScolaStats(ctypes.Structure):
         ("ms_lpt", c_double), ("ms_evolve", c_double), ("kernel_launches", c_int64),
         ("deposit_form", c_int32), ("deposit_threads", c_int32), ("deposit_split", c_int32),
         ("ms_deposit_candidates", c_double * 4), ("batches", c_int32), ("batch_boxes", c_int32),
-        ("ms_tcola", c_double), ("dst_form", c_int32), ("ms_dst_candidates", c_double * 3),
+        ("ms_tcola", c_double), ("dst_form", c_int32), ("ms_dst_candidates", c_double * 4),
     ]
 
 

@@ -105,7 +105,7 @@ scola_status validate(const scola_params *p, std::vector<int32_t> &bufs, std::ve
     }
     if (p->dst_variant != SCOLA_DST_SIMT && p->dst_variant != SCOLA_DST_TC_3XTF32 &&
         p->dst_variant != SCOLA_DST_TC_4XTF32 && p->dst_variant != SCOLA_DST_TC_3PASS &&
-        p->dst_variant != SCOLA_DST_AUTO)
+        p->dst_variant != SCOLA_DST_RADIX && p->dst_variant != SCOLA_DST_AUTO)
         return invalid("unknown dst_variant");
     if (p->batch_mode != SCOLA_BATCH_ALL && p->batch_mode != SCOLA_BATCH_PER_TILE)
         return invalid("unknown batch_mode");
@@ -149,8 +149,13 @@ scola_status validate(const scola_params *p, std::vector<int32_t> &bufs, std::ve
         if (ng < nsc) return invalid("Ng must be >= Np,sCOLA (Sec. 3.3, C.3)");
         const bool tc_form = p->dst_variant == SCOLA_DST_TC_3XTF32 || p->dst_variant == SCOLA_DST_TC_4XTF32 ||
                              p->dst_variant == SCOLA_DST_TC_3PASS || p->dst_variant == SCOLA_DST_AUTO;
-        if (for_kernels && (ng > kMaxNg || (!tc_form && ng > kMaxNgSimt))) {
-            set_error("Ng > 256 is not built (Ng > 222 only with a tensor-core DST form)");
+        const bool rx_form = p->dst_variant == SCOLA_DST_RADIX;
+        if (for_kernels && (ng > kMaxNg || (!tc_form && !rx_form && ng > kMaxNgSimt))) {
+            set_error("Ng > 256 is not built (Ng > 222 only with a tensor-core or radix DST form)");
+            return SCOLA_ERR_UNSUPPORTED;
+        }
+        if (for_kernels && rx_form && !rx_supported(ng)) {
+            set_error("the radix DST needs 1 <= Ng <= 256");
             return SCOLA_ERR_UNSUPPORTED;
         }
         if (for_kernels && tc_form && !tc_supported(ng)) {
@@ -211,6 +216,10 @@ struct BatchPlan {
     std::vector<long long> group_plane_first;
     std::vector<int> group_nplanes, plane_beg;
     long long n_planes = 0;
+    std::vector<Chunk> rxt;                            // radix DST: (box, tile) per group
+    long long n_rxt = 0;
+    std::vector<long long> rx_group_first;
+    std::vector<int> rx_group_ntiles, rx_tile_beg, rx_tile_end;
     long long P = 0, M = 0, MP = 0, SH = 0, NK = 0, dep_cells = 0;
 };
 
@@ -361,6 +370,23 @@ void plan_batch(const scola_ctx *c, const std::vector<BoxGeom> &tiling_geo, int 
             }
             bp.group_nplanes.push_back((int)(bp.n_planes - bp.group_plane_first.back()));
         }
+    // radix DST tiles: per Ng group, each box's tiles of 2 R rows
+    bp.rx_tile_beg.assign(count, 0);
+    bp.rx_tile_end.assign(count, 0);
+    for (const RxGroup &G : c->rx_groups) {
+        bp.rx_group_first.push_back(bp.n_rxt);
+        for (int b = 0; b < count; ++b) {
+            if (bp.geo[b].ng != G.Ng) continue;
+            const long long rows = (long long)G.Ng * G.Ng;
+            bp.rx_tile_beg[b] = (int)bp.n_rxt;
+            for (long long t = 0; t * 2 * G.R < rows; ++t) {
+                if (lists) bp.rxt.push_back({b, (int)t});
+                ++bp.n_rxt;
+            }
+            bp.rx_tile_end[b] = (int)bp.n_rxt;
+        }
+        bp.rx_group_ntiles.push_back((int)(bp.n_rxt - bp.rx_group_first.back()));
+    }
     bp.P = P;
     bp.M = M;
     bp.MP = MP;
@@ -443,6 +469,7 @@ scola_status bind_batch(scola_ctx *c, int k, bool force = false) {
     CS(put(c->sbricks, bp.sbr));
     if (c->use_tc) CS(put(c->tc_tiles, bp.tct));
     if (c->tc3_ok) CS(put(c->tc_planes, bp.planes));
+    if (c->rx_ok) CS(put(c->rx_tiles, bp.rxt));
     c->nboxes = count;
     c->boxes_h = bp.boxes;
     c->n_pchunks = (int)bp.n_pch;
@@ -469,6 +496,12 @@ scola_status bind_batch(scola_ctx *c, int k, bool force = false) {
         c->tc_groups[g].nplanes = c->tc3_ok ? bp.group_nplanes[g] : 0;
     }
     c->tc_plane_beg = bp.plane_beg;
+    for (size_t g = 0; g < c->rx_groups.size(); ++g) {
+        c->rx_groups[g].tiles = c->rx_tiles + bp.rx_group_first[g];
+        c->rx_groups[g].ntiles = bp.rx_group_ntiles[g];
+    }
+    c->rx_tile_beg = bp.rx_tile_beg;
+    c->rx_tile_end = bp.rx_tile_end;
     c->P = bp.P;
     c->M = bp.M;
     c->MP = bp.MP;
@@ -654,6 +687,21 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &all_geo) {
         return SCOLA_ERR_UNSUPPORTED;
     }
     c->tc3 = p.dst_variant == SCOLA_DST_TC_3PASS;
+    // the radix form: requested, or one more autotuner candidate where every Ng allows it
+    bool all_rx = true;
+    for (auto &kv : c->tbl_of) all_rx = all_rx && rx_supported(kv.first);
+    c->rx = p.dst_variant == SCOLA_DST_RADIX;
+    c->rx_ok = c->rx || (c->dst_auto && all_rx);
+    if (c->rx_ok)
+        for (auto &kv : c->tbl_of) {
+            RxGroup G;
+            G.Ng = kv.first;
+            G.tiles = nullptr;
+            G.ntiles = 0;
+            G.lam_off = c->tables_h[kv.second].lam_off;
+            rx_tables(G, arena);
+            c->rx_groups.push_back(G);
+        }
     if (c->use_tc) {
         for (auto &kv : c->tbl_of) {
             TcGroup G;
@@ -696,6 +744,7 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &all_geo) {
     CS(upload(&c->tables, c->tables_h));
     CS(upload(&c->table_arena, arena));
     if (c->use_tc) CK(init_tc_kernels());
+    if (c->rx_ok) CK(init_rx_kernels());
     CS(dev_alloc(&c->dev_err, 1));
     CK(cudaMemset(c->dev_err, 0, sizeof(int)));
 
@@ -758,7 +807,7 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &all_geo) {
     // every batch's layout (box descriptors kept; list lengths and arena sizes maxed)
     long long P = 0, M = 0, MP = 0, SH = 0, NK = 0, dep = 0;
     long long L_pch = 0, L_tch = 0, L_shch = 0, L_zit = 0, L_cit = 0, L_mch = 0, L_ppch = 0, L_sbr = 0, L_tct = 0,
-              L_pl = 0;
+              L_pl = 0, L_rx = 0;
     int max_count = 0;
     for (int k = 0; k < nbatch; ++k) {
         BatchPlan bp;
@@ -781,6 +830,7 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &all_geo) {
         L_sbr = std::max(L_sbr, bp.n_sbr);
         L_tct = std::max(L_tct, bp.n_tct);
         L_pl = std::max(L_pl, bp.n_planes);
+        L_rx = std::max(L_rx, bp.n_rxt);
         max_count = std::max(max_count, n);
         c->P_all += bp.P;
         for (const BoxGeom &g : bp.geo) c->M_all += (long long)g.ng * g.ng * g.ng;
@@ -801,6 +851,7 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &all_geo) {
     CS(dev_alloc(&c->sbricks, L_sbr));
     if (c->use_tc) CS(dev_alloc(&c->tc_tiles, L_tct));
     if (c->tc3_ok) CS(dev_alloc(&c->tc_planes, L_pl));
+    if (c->rx_ok) CS(dev_alloc(&c->rx_tiles, L_rx));
     c->cap_P = P;
     c->cap_M = M;
     c->cap_MP = MP;
@@ -824,7 +875,7 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &all_geo) {
     }
     CS(bind_batch(c, 0, true));
 
-    if (!c->use_tc || c->dst_auto) CK(init_pm_kernels(*c));     // the FP32 DST passes
+    if ((!c->use_tc && !c->rx) || c->dst_auto) CK(init_pm_kernels(*c));     // the FP32 DST passes
     CK(init_deposit_kernels());
     for (int i = 0; i < 4; ++i) CK(cudaEventCreate(&c->ev[i]));
     for (int i = 0; i < 2; ++i) CK(cudaEventCreate(&c->tc_ev[i]));
@@ -1102,31 +1153,40 @@ scola_status autotune_deposit(scola_ctx *c) {
 }
 
 // Poisson-solve autotuner (SCOLA_DST_AUTO where every Ng allows the tensor-core form).  The
-// 3xTF32 tensor-core passes and the FP32 CUDA-core passes both meet the accuracy bound; each
-// solves the context's current source (the boxes of the first batch, or box 0 in the
-// per-tile form) three times after a warm-up, timed with CUDA events, and the faster is kept
-// for the life of the context and its captured graph.  Runs once, after autotune_deposit
-// (whose last candidate leaves a valid source in the mesh).
+// candidates all meet the accuracy bound: the 3xTF32 tensor-core passes (six passes, and
+// three where every Ng allows the plane pass), the dense FP32 CUDA-core passes and the radix
+// (Bluestein) FP32 passes.  Each solves the context's current source (the boxes of the first
+// batch, or box 0 in the per-tile form) three times after a warm-up, timed with CUDA events,
+// and the fastest is kept for the life of the context and its captured graph.  Runs once,
+// after autotune_deposit (whose last candidate leaves a valid source in the mesh).
 scola_status autotune_dst(scola_ctx *c) {
     if (c->dst_tuned) return SCOLA_OK;
     if (!c->dst_auto) {
-        c->stats.dst_form = c->use_tc ? (c->tc3 ? SCOLA_DST_TC_3PASS : c->tc_lo_lo ? SCOLA_DST_TC_4XTF32
-                                                                                    : SCOLA_DST_TC_3XTF32)
-                                      : SCOLA_DST_SIMT;
+        c->stats.dst_form = c->rx ? SCOLA_DST_RADIX
+                            : c->use_tc ? (c->tc3 ? SCOLA_DST_TC_3PASS : c->tc_lo_lo ? SCOLA_DST_TC_4XTF32
+                                                                                      : SCOLA_DST_TC_3XTF32)
+                                        : SCOLA_DST_SIMT;
         c->dst_tuned = true;
         return SCOLA_OK;
     }
-    // candidates: tensor cores in six passes, FP32 CUDA cores, tensor cores in three passes
+    // candidates: tensor cores in six passes, FP32 CUDA cores, tensor cores in three passes,
+    // radix FP32
+    static const int forms[4] = {SCOLA_DST_TC_3XTF32, SCOLA_DST_SIMT, SCOLA_DST_TC_3PASS, SCOLA_DST_RADIX};
+    static const char *names[4] = {"tensor-core form: ", "FP32 form: ", "three-pass tensor-core form: ",
+                                   "radix form: "};
+    auto select = [&](int q) {
+        c->use_tc = q == 0 || q == 2;
+        c->tc3 = q == 2;
+        c->rx = q == 3;
+    };
     const long long launches = c->launches;
-    float t[3] = {-1.0f, -1.0f, -1.0f};
+    float t[4] = {-1.0f, -1.0f, -1.0f, -1.0f};
     {
         std::unique_ptr<BoxView> view;
         if (c->prm.batch_mode == SCOLA_BATCH_PER_TILE) view.reset(new BoxView(c, 0));
-        for (int q = 0; q < 3; ++q) {
-            if (q == 2 && !c->tc3_ok) continue;
-            c->use_tc = q != 1;
-            c->tc3 = q == 2;
-            static const char *names[3] = {"tensor-core form: ", "FP32 form: ", "three-pass tensor-core form: "};
+        for (int q = 0; q < 4; ++q) {
+            if ((q == 2 && !c->tc3_ok) || (q == 3 && !c->rx_ok)) continue;
+            select(q);
             cudaError_t e = launch_poisson(*c);
             if (e == cudaSuccess) e = c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize();
             if (e != cudaSuccess) {
@@ -1144,12 +1204,12 @@ scola_status autotune_dst(scola_ctx *c) {
             }
         }
     }
-    int best = t[0] <= t[1] ? 0 : 1;
-    if (t[2] >= 0.0f && t[2] < t[best]) best = 2;
-    c->use_tc = best != 1;
-    c->tc3 = best == 2;
-    for (int q = 0; q < 3; ++q) c->stats.ms_dst_candidates[q] = t[q] < 0.0f ? 0.0 : t[q];
-    c->stats.dst_form = best == 0 ? SCOLA_DST_TC_3XTF32 : best == 1 ? SCOLA_DST_SIMT : SCOLA_DST_TC_3PASS;
+    int best = 0;
+    for (int q = 1; q < 4; ++q)
+        if (t[q] >= 0.0f && (t[best] < 0.0f || t[q] < t[best])) best = q;
+    select(best);
+    for (int q = 0; q < 4; ++q) c->stats.ms_dst_candidates[q] = t[q] < 0.0f ? 0.0 : t[q];
+    c->stats.dst_form = forms[best];
     c->launches = launches;
     c->dst_tuned = true;
     return SCOLA_OK;
@@ -1403,7 +1463,7 @@ void scola_destroy(scola_ctx *c) {
         cufftDestroy(c->tc_c2r);
     }
     void *ptrs[] = {c->boxes, c->all_boxes, c->all_coef, c->all_coefL, c->coef, c->coefL, c->tables, c->table_arena, c->pchunks, c->tchunks, c->shchunks,
-                    c->zitems, c->citems, c->mchunks, c->ppchunks, c->tc_tiles, c->tc_planes, c->dev_err, c->ckpt, c->seg, c->fin,
+                    c->zitems, c->citems, c->mchunks, c->ppchunks, c->tc_tiles, c->tc_planes, c->rx_tiles, c->dev_err, c->ckpt, c->seg, c->fin,
                     c->adj, c->lamG, c->lam_phi_pad, c->adj_in, c->adj_out, c->lam_shell, c->lamPsi1,
                     c->lamPsi2, c->lam_phi1, c->lam_phi2, c->d2, c->lam_d2, c->part, c->dep_acc, c->kcount,
                     c->koffs, c->kcursor, c->sentries, c->sbricks,

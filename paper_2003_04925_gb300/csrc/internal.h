@@ -70,6 +70,13 @@ struct TcGroup {                  // one tensor-core DST launch group: boxes sha
     long long lam_off;            // eigenvalues in table_arena
 };
 
+struct RxGroup {                  // one radix DST launch group: boxes sharing Ng
+    int Ng, P, L, logL, R;        // DFT length P = Ng + 1, Bluestein length L, pencil pairs per tile
+    Chunk *tiles;                 // device (box, tile of 2 R rows of the box)
+    int ntiles;
+    long long w_off, bk_off, tw_off, sn_off, lam_off;   // tables in table_arena
+};
+
 struct KickDrift {                // FP32 copies of FP64 host coefficients for one force time
     float kF, k1, k2;             // p += kF F + k1 psi1 + k2 psi2
     float alpha, d1, d2;          // s += alpha p + d1 psi1 + d2 psi2
@@ -145,6 +152,11 @@ struct Ctx {
     bool tc3_ok = false;                              // every Ng allows it (plane_supported)
     Chunk *tc_planes = nullptr;                       // plane items of every group
     std::vector<int> tc_plane_beg;                    // each box's first plane item
+    bool rx = false;                                  // the radix (Bluestein) DST passes
+    bool rx_ok = false;                               // set up (SCOLA_DST_RADIX, or an AUTO candidate)
+    std::vector<RxGroup> rx_groups;
+    Chunk *rx_tiles = nullptr;
+    std::vector<int> rx_tile_beg, rx_tile_end;        // each box's tile range in rx_tiles
     int view_box = -1;                                // >= 0: launches restricted to this box
     int *dev_err = nullptr;                           // set by kernels whose bounded waits expired
     float *part = nullptr;
@@ -243,6 +255,13 @@ int tc_plan_stages(int Ng, int &Npad, int &nkc, bool zm = false);
 bool plane_supported(int Ng);    // the three-pass solve: Ng <= 96, Ng % 4 == 0
 cudaError_t init_plane_kernel();
 cudaError_t launch_plane_pass(Ctx &c, const std::vector<TcGroup> &groups, const float *in, float *out);
+// radix DST (k_dst_radix.cu): plan of one Ng, its host tables appended to the arena
+void rx_plan(int Ng, int &P, int &L, int &logL, int &R);
+bool rx_supported(int Ng);
+void rx_tables(RxGroup &G, std::vector<float> &arena);
+cudaError_t init_rx_kernels();
+cudaError_t launch_poisson_rx_pass(Ctx &c, int pass);
+cudaError_t launch_poisson_rx_buffers(Ctx &c, const float *in, float *w1, float *w2, float *out_pad);
 bool tc_supported(int Ng);
 bool tc_folded(int Ng);          // Ng > 128: the mirror-symmetric half-size form
 bool tc_ragged(int Ng);          // rows not 16-byte pitched for TMA: plain loads and stores

@@ -431,6 +431,7 @@ cudaError_t init_pm_kernels(Ctx &c) {
 }
 
 cudaError_t launch_poisson_buffers(Ctx &c, const float *in, float *w1, float *w2, float *out_pad) {
+    if (c.rx) return launch_poisson_rx_buffers(c, in, w1, w2, out_pad);
     if (c.use_tc) return launch_poisson_tc_buffers(c, in, w1, w2, out_pad);
     switch (c.max_R) {
         case 1: return poisson_R<1>(c, in, w1, w2, out_pad);
@@ -449,7 +450,8 @@ cudaError_t launch_poisson(Ctx &c) { return launch_poisson_buffers(c, c.work2, c
 
 cudaError_t launch_poisson_pass(Ctx &c, int pass) {
     // the passes of launch_poisson, one at a time (for per-kernel timing); the FP32
-    // form has five passes, the tensor-core form six
+    // form has five passes, the tensor-core and radix forms six
+    if (c.rx) return launch_poisson_rx_pass(c, pass);
     if (c.use_tc) return launch_poisson_tc_pass(c, pass);
     if (pass == 5) return cudaSuccess;
     switch (c.max_R * 8 + pass) {

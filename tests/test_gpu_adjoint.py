@@ -26,7 +26,7 @@ def _pkg():
 def _sim(kw, variant):
     sc = _pkg()
     code = {"simt": sc.SCOLA_DST_SIMT, "tc": sc.SCOLA_DST_TC_3XTF32, "tc4": sc.SCOLA_DST_TC_4XTF32,
-            "tc3": sc.SCOLA_DST_TC_3PASS}[variant]
+            "tc3": sc.SCOLA_DST_TC_3PASS, "radix": sc.SCOLA_DST_RADIX}[variant]
     sim = sc.Scola(**dict(lib_kwargs(kw), dst_variant=code))
     sim.enable_checkpointing(True)
     return sim
@@ -50,7 +50,7 @@ def _gpu_loss_grad(sim, w_np, target):
     return float(np.sum((dd - target) ** 2)), g.cpu().numpy().astype(np.float64)
 
 
-@pytest.mark.parametrize("variant", ["simt", "tc", "tc4", "tc3"])
+@pytest.mark.parametrize("variant", ["simt", "tc", "tc4", "tc3", "radix"])
 @pytest.mark.parametrize("ratio", [1, 2])
 def test_backward_matches_fp64_oracle_adjoint(ratio, variant):
     # The loss is piecewise smooth: CIC weights are piecewise linear in position, so a

@@ -64,7 +64,7 @@ CASES_PM = {
 
 def _sim(kw, variant="simt"):
     code = {"simt": sc.SCOLA_DST_SIMT, "tc": sc.SCOLA_DST_TC_3XTF32, "tc4": sc.SCOLA_DST_TC_4XTF32,
-            "tc3": sc.SCOLA_DST_TC_3PASS}[variant]
+            "tc3": sc.SCOLA_DST_TC_3PASS, "radix": sc.SCOLA_DST_RADIX}[variant]
     return sc.Scola(**dict(lib_kwargs(kw), dst_variant=code))
 
 
@@ -112,7 +112,7 @@ def test_box_particle_ids_are_bit_exact(name):
     sim.close()
 
 
-@pytest.mark.parametrize("variant", ["simt", "tc", "tc3"])
+@pytest.mark.parametrize("variant", ["simt", "tc", "tc3", "radix"])
 @pytest.mark.parametrize("name", list(CASES_PM))
 def test_pm_force_matches_oracle(name, variant):
     # One force evaluation (deposit, Dirichlet DST-I solve, gradient, interpolation) on
@@ -126,6 +126,8 @@ def test_pm_force_matches_oracle(name, variant):
     assert sc.scola_uses_tensor_cores(sim.ctx) == variant.startswith("tc")
     sim.lpt_fields(_to_dev(w))
     sim.setup_boxes()
+    if variant == "radix":
+        assert sim.stats()["dst_form"] == sc.SCOLA_DST_RADIX
     D1 = 0.73
     s_all, refs = [], []
     for b in range(cfg.nboxes):
@@ -226,7 +228,7 @@ def _pk_rel_err(delta_a, delta_b, L, N):
     return np.abs(pa[ok] / pb[ok] - 1).max()
 
 
-@pytest.mark.parametrize("variant", ["simt", "tc", "tc4", "tc3"])
+@pytest.mark.parametrize("variant", ["simt", "tc", "tc4", "tc3", "radix"])
 @pytest.mark.parametrize("name", ["plain_32", "uneven", "table1_like", "fold_160", "fold_odd", "fda4",
                                   "fda6_ratio2"])
 def test_forward_matches_oracle(name, variant):
@@ -273,7 +275,7 @@ def test_forward_is_deterministic_and_host_variant_agrees():
     sim.close()
 
 
-@pytest.mark.parametrize("variant", ["simt", "tc", "tc3"])
+@pytest.mark.parametrize("variant", ["simt", "tc", "tc3", "radix"])
 @pytest.mark.parametrize("name", ["plain_32", "uneven"])
 def test_per_tile_form_matches_batched_form(name, variant):
     # One box per launch (the plain per-tile form) gives bit-identical results: every kernel
@@ -358,26 +360,27 @@ def test_box_ranges_merge_to_the_full_run(variant):
 
 @pytest.mark.parametrize("name", ["plain_32", "table1_like", "fold_odd", "table1_1gpc"])
 def test_dst_autotuner_keeps_one_form(name):
-    # SCOLA_DST_AUTO times the tensor-core and the FP32 Poisson solves on the context's own
-    # boxes and keeps the faster; the run then equals, bit for bit, a context that asks for
-    # that form.  Every Ng <= 222 allows both forms, so both are timed.
+    # SCOLA_DST_AUTO times the tensor-core, the dense FP32 and the radix FP32 Poisson solves on
+    # the context's own boxes and keeps the fastest; the run then equals, bit for bit, a
+    # context that asks for that form.  Every Ng <= 222 allows these three, so all are timed.
     kw = CASES_PM[name]
     w = _to_dev(synth_inputs.white_noise(kw["Np"], 6))
     auto = sc.Scola(**dict(lib_kwargs(kw), dst_variant=sc.SCOLA_DST_AUTO))
     xa, pa = auto.forward(w)
     torch.cuda.synchronize()
     st = auto.stats()
-    # candidates: six-pass tensor cores, FP32, three-pass tensor cores (timed where every Ng
-    # allows it: Ng <= 96, Ng % 4 == 0); the kept form is the fastest timed one
-    forms = (sc.SCOLA_DST_TC_3XTF32, sc.SCOLA_DST_SIMT, sc.SCOLA_DST_TC_3PASS)
+    # candidates: six-pass tensor cores, dense FP32, three-pass tensor cores (timed where every
+    # Ng allows it: Ng <= 96, Ng % 4 == 0), radix FP32; the kept form is the fastest timed one
+    forms = (sc.SCOLA_DST_TC_3XTF32, sc.SCOLA_DST_SIMT, sc.SCOLA_DST_TC_3PASS, sc.SCOLA_DST_RADIX)
     cand = st["ms_dst_candidates"]
     three = all(g <= 96 and g % 4 == 0 for g in _mesh_sizes(kw))
-    assert cand[0] > 0 and cand[1] > 0 and (cand[2] > 0) == three, cand
+    assert cand[0] > 0 and cand[1] > 0 and (cand[2] > 0) == three and cand[3] > 0, cand
     timed = [(t, f) for t, f in zip(cand, forms) if t > 0]
     assert st["dst_form"] == min(timed)[1], (st["dst_form"], cand)
-    print("dst autotuner %s: six-pass tensor cores %.4f ms, FP32 %.4f ms, three-pass %.4f ms per solve"
-          % ((name,) + tuple(cand)))
-    assert sc.scola_uses_tensor_cores(auto.ctx) == (0 if st["dst_form"] == sc.SCOLA_DST_SIMT else 1)
+    print("dst autotuner %s: six-pass tensor cores %.4f ms, dense FP32 %.4f ms, three-pass %.4f ms, "
+          "radix %.4f ms per solve" % ((name,) + tuple(cand)))
+    cuda_cores = (sc.SCOLA_DST_SIMT, sc.SCOLA_DST_RADIX)
+    assert sc.scola_uses_tensor_cores(auto.ctx) == (0 if st["dst_form"] in cuda_cores else 1)
     auto.close()
     fixed = sc.Scola(**dict(lib_kwargs(kw), dst_variant=st["dst_form"]))
     xf, pf = fixed.forward(w)
@@ -453,7 +456,7 @@ def test_state_and_argument_errors():
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("variant", ["simt", "tc", "tc3"])
+@pytest.mark.parametrize("variant", ["simt", "tc", "tc3", "radix"])
 def test_batched_128_sampled_boxes_match_oracle(variant):
     # Full-size batched workload in the benchmark's launch configuration; the oracle
     # evolves two sampled boxes (boxes are independent, so each is exact on its own).
@@ -479,7 +482,7 @@ _UNEVEN_CACHE = {}
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("variant", ["simt", "tc", "tc4", "tc3"])
+@pytest.mark.parametrize("variant", ["simt", "tc", "tc4", "tc3", "radix"])
 def test_uneven_256_sampled_boxes_match_oracle(variant):
     # The uneven-buffer workload (256^3 particles, 4^3 tiles, buffers drawn from {4, 8, 16},
     # 1:1 meshes of 72, 80 and 96 cells in one launch), in the benchmark's launch form; the
