@@ -15,9 +15,10 @@
 //   Z_k = conj(w_k) sum_n (z_n conj(w_n)) w_{k-n},
 // a circular convolution of length L (a power of two >= 2P - 1) done as
 // IFFT_L(FFT_L(z conj w) * FFT_L(b)), b_m = w_|m| for |m| < P (wrapped), FFT_L(b) tabulated
-// on the host in FP64.  Each FFT_L is a radix-2 Stockham transform in shared memory
-// (log2 L stages, natural order in and out, twiddles from a table); R pencil pairs per CTA,
-// R L = 4096 complex values per buffer.  FP32 throughout.
+// on the host in FP64 (its product fused into the first stage of the inverse).  Each FFT_L
+// is a Stockham transform in shared memory with radix-16 butterflies in registers
+// (fft_util.cuh); R pencil pairs per CTA, R L = 4096 complex values per buffer.  FP32
+// throughout.
 //
 // The six passes, their layouts and epilogues are those of the one-axis tensor-core passes:
 // each reads rows whose transform axis is contiguous and writes its result transposed,
@@ -33,13 +34,15 @@
 #include <vector>
 
 #include "device_util.cuh"
+#include "fft_util.cuh"
 
 namespace scola {
 
 namespace {
 
 constexpr int kRxThreads = 256;
-constexpr int kRxSpan = 4096;       // complex values per shared-memory buffer (R pairs x L)
+constexpr int kRxSpan = 4096;       // complex values per transform batch (R pairs x L)
+constexpr int kRxBuf = fft::padded(kRxSpan);   // per shared-memory buffer (padded rows)
 constexpr int kMaxRxGroups = 4;     // Ng groups per launch (more: further launches)
 
 enum RxPass { RX_F = 1, RX_XF = 2, RX_ZI = 3, RX_YI = 4, RX_XI = 5 };
@@ -50,7 +53,7 @@ struct RxGroupArgs {
     int Ng, P, L, logL, R;
     const float2 *w;                // w_n, n < P
     const float2 *Bk;               // FFT_L(b)
-    const float2 *tw;               // exp(-2 pi i j / L), j < L / 2
+    const float2 *tw;               // exp(-2 pi i j / L), j < L
     const float *sn;                // sin(pi n / P), n < P
     const float *lam;               // Dirichlet eigenvalues, Ng
 };
@@ -63,46 +66,15 @@ struct RxArgs {
     float *out;
 };
 
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {   // a conj(b)
-    return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
-}
-
-// Radix-2 Stockham FFT of length L = 2^logL (sign -1: forward, +1: inverse, unnormalised) of
-// the R rows of src (row-major, R x L), ping-ponging with dst; returns the buffer holding the
-// result.  Stage m (1, 2, .. L/2) combines x[j] and x[j + L/2] with the twiddle of j mod m into
-// positions 2 (j - j mod m) + j mod m and that + m.
-__device__ float2 *stockham(float2 *src, float2 *dst, int R, int logL, const float2 *tw, int sign) {
-    const int half = 1 << (logL - 1);
-    for (int s = 0; s < logL; ++s) {
-        const int m = 1 << s;
-        for (int q = threadIdx.x; q < R * half; q += kRxThreads) {
-            const int r = q >> (logL - 1), j = q & (half - 1);
-            const float2 *x = src + (r << logL);
-            float2 *y = dst + (r << logL);
-            const int k = j & (m - 1), g = j - k;
-            float2 t = tw[k << (logL - 1 - s)];
-            if (sign > 0) t.y = -t.y;
-            const float2 a = x[j], b = cmul(x[j + half], t);
-            y[2 * g + k] = make_float2(a.x + b.x, a.y + b.y);
-            y[2 * g + k + m] = make_float2(a.x - b.x, a.y - b.y);
-        }
-        __syncthreads();
-        float2 *tmp = src;
-        src = dst;
-        dst = tmp;
-    }
-    return src;
-}
+using fft::cmul;
+using fft::cmulc;
 
 size_t rx_smem_bytes(int Ng, int P, int L) {
-    return sizeof(float2) * ((size_t)2 * kRxSpan + L / 2 + L + P) + sizeof(float) * ((size_t)P + Ng) + 16;
+    return sizeof(float2) * ((size_t)2 * kRxBuf + L + L + P) + sizeof(float) * ((size_t)P + Ng) + 16;
 }
 
 template <int PASS>
-__global__ void __launch_bounds__(kRxThreads) k_dst_radix(const RxArgs A) {
+__global__ void __launch_bounds__(kRxThreads, 3) k_dst_radix(const RxArgs A) {
     int gi = 0;
     while (gi + 1 < A.ngroups && (int)blockIdx.x >= A.g[gi].cta_end) ++gi;
     const RxGroupArgs &G = A.g[gi];
@@ -111,14 +83,15 @@ __global__ void __launch_bounds__(kRxThreads) k_dst_radix(const RxArgs A) {
     const int Ng = G.Ng, P = G.P, L = G.L, logL = G.logL, R = G.R;
     const int rows = 2 * R;                                // pencils per tile (a power of two)
     const int Ngs = Ng | 1;                                // odd row stride of the result rows
+    const int Ls = fft::padded(L);                         // padded row stride of the transforms
     float2 *buf0 = reinterpret_cast<float2 *>(smem);
-    float2 *buf1 = buf0 + kRxSpan;
-    float2 *tw = buf1 + kRxSpan;                           // L / 2
-    float2 *Bk = tw + L / 2;                               // L
+    float2 *buf1 = buf0 + kRxBuf;
+    float2 *tw = buf1 + kRxBuf;                            // L
+    float2 *Bk = tw + L;                                   // L
     float2 *w = Bk + L;                                    // P
     float *sn = reinterpret_cast<float *>(w + P);          // P
     float *lam = sn + P;                                   // Ng
-    for (int q = threadIdx.x; q < L / 2; q += kRxThreads) tw[q] = G.tw[q];
+    for (int q = threadIdx.x; q < L; q += kRxThreads) tw[q] = G.tw[q];
     for (int q = threadIdx.x; q < L; q += kRxThreads) Bk[q] = G.Bk[q];
     for (int q = threadIdx.x; q < P; q += kRxThreads) {
         w[q] = G.w[q];
@@ -142,9 +115,9 @@ __global__ void __launch_bounds__(kRxThreads) k_dst_radix(const RxArgs A) {
         const float *src = A.in + B.m_off + row0 * Ng;
         for (int q = threadIdx.x; q < rows * Ng; q += kRxThreads) xs[q] = q < nrow * Ng ? src[q] : 0.0f;
         __syncthreads();
-        // a_n = (y'_n + i y''_n) conj(w_n), n < P; zero to L
-        for (int q = threadIdx.x; q < R * L; q += kRxThreads) {
-            const int pr = q >> logL, n = q & (L - 1);
+        // forward transform of a_n = (y'_n + i y''_n) conj(w_n) (n < P; zero to L), formed from
+        // the staged rows as the first stage loads them
+        auto chirped = [&](int pr, int n) {
             float2 v = make_float2(0.f, 0.f);
             if (n >= 1 && n < P) {
                 const float *x1 = xs + (2 * pr) * Ng, *x2 = x1 + Ng;
@@ -154,21 +127,22 @@ __global__ void __launch_bounds__(kRxThreads) k_dst_radix(const RxArgs A) {
                 const float y2 = s * (a2 + b2) + 0.5f * (a2 - b2);
                 v = cmulc(make_float2(y1, y2), w[n]);
             }
-            buf0[q] = v;
-        }
-        __syncthreads();
-        float2 *f = stockham(buf0, buf1, R, logL, tw, -1);
-        for (int q = threadIdx.x; q < R * L; q += kRxThreads) f[q] = cmul(f[q], Bk[q & (L - 1)]);
-        __syncthreads();
-        f = stockham(f, f == buf0 ? buf1 : buf0, R, logL, tw, +1);
+            return v;
+        };
+        float2 *f = fft::transform<-1>(chirped, buf0, buf1, R, logL, tw);
+        // inverse transform of its product with FFT_L(b)
+        float2 *g = f == buf0 ? buf1 : buf0;
+        const float2 *fc = f;
+        auto product = [&](int pr, int n) { return cmul(fc[pr * Ls + fft::pad(n)], Bk[n]); };
+        f = fft::transform<+1>(product, g, f, R, logL, tw);
         // unpack the pairs: even outputs S_{2k} = -Im Y_k; odd increments R_k (R_0 / 2) placed
         // at the odd outputs' columns, summed below
         float *S = reinterpret_cast<float *>(f == buf0 ? buf1 : buf0);
         for (int q = threadIdx.x; q < R * (H + 1); q += kRxThreads) {
             const int pr = q / (H + 1), k = q - pr * (H + 1);
-            const float2 *fr = f + (pr << logL);
+            const float2 *fr = f + pr * Ls;
             const int km = k == 0 ? 0 : P - k;
-            float2 Zk = cmulc(fr[k], w[k]), Zm = cmulc(fr[km], w[km]);
+            float2 Zk = cmulc(fr[fft::pad(k)], w[k]), Zm = cmulc(fr[fft::pad(km)], w[km]);
             Zk.x *= invL; Zk.y *= invL; Zm.x *= invL; Zm.y *= invL;
             const float re1 = 0.5f * (Zk.x + Zm.x), im1 = 0.5f * (Zk.y - Zm.y);
             const float re2 = 0.5f * (Zk.y + Zm.y), im2 = -0.5f * (Zk.x - Zm.x);
@@ -206,12 +180,13 @@ __global__ void __launch_bounds__(kRxThreads) k_dst_radix(const RxArgs A) {
         }
         __syncthreads();
         // out[k][row] (consecutive threads: consecutive rows)
+        const int logrows = __ffs(rows) - 1;
         for (int q = threadIdx.x; q < Ng * rows; q += kRxThreads) {
-            const int kk = q / rows, r = q & (rows - 1);
+            const int kk = q >> logrows, r = q & (rows - 1);
             if (r >= nrow) continue;
-            const long long row = row0 + r;
+            const int row = (int)row0 + r;                  // < Ng^2 <= 2^16
             float v = S[r * Ngs + kk];
-            const int rhi = (int)(row / Ng), rlo = (int)(row - (long long)rhi * Ng);
+            const int rhi = row / Ng, rlo = row - rhi * Ng;
             if (PASS == RX_XI) {
                 const int Gp = B.gpad;
                 const long long Sd = Ng + 2 * Gp;
@@ -370,7 +345,7 @@ void rx_tables(RxGroup &G, std::vector<float> &arena) {
         arena.push_back((float)im);
     }
     G.tw_off = even();
-    for (int j = 0; j < L / 2; ++j) {
+    for (int j = 0; j < L; ++j) {
         arena.push_back((float)cs[j]);
         arena.push_back((float)-sn[j]);
     }
