@@ -521,6 +521,11 @@ scola_status tcola_alloc(scola_ctx *c) {
         set_error("the periodic tCOLA grid needs mesh_ratio >= 1");
         return SCOLA_ERR_UNSUPPORTED;
     }
+    if (!tc_fft_supported(c->tc_ng)) {
+        set_error("the periodic tCOLA grid needs 2 <= mesh_ratio Np <= 1024");
+        return SCOLA_ERR_UNSUPPORTED;
+    }
+    CK(init_tc_fft_kernels());
     const int N = c->tc_ng;
     const long long nk = (long long)N * N * (N / 2 + 1), nrec = (long long)(c->prm.nsteps + 1) * c->tc_n3;
     CS(dev_alloc(&c->tc_acc, c->tc_n3));
@@ -528,17 +533,9 @@ scola_status tcola_alloc(scola_ctx *c) {
     CS(dev_alloc(&c->tc_delta, c->tc_n3));
     CS(dev_alloc(&c->tc_phi, c->tc_n3));
     CS(dev_alloc(&c->tc_dk, nk));
+    CS(dev_alloc(&c->tc_dk2, nk));
     if (c->prm.study_mode & SCOLA_STUDY_TRUE_DENSITY) CS(dev_alloc(&c->rec_delta, nrec));
     if (c->prm.study_mode & SCOLA_STUDY_TRUE_POTENTIAL) CS(dev_alloc(&c->rec_phi, nrec));
-    CF(cufftPlan3d(&c->tc_r2c, N, N, N, CUFFT_R2C));
-    if (cufftPlan3d(&c->tc_c2r, N, N, N, CUFFT_C2R) != CUFFT_SUCCESS) {
-        cufftDestroy(c->tc_r2c);
-        set_error("cufftPlan3d failed for the periodic tCOLA grid");
-        return SCOLA_ERR_CUDA;
-    }
-    c->tc_plans = true;
-    CF(cufftSetStream(c->tc_r2c, c->stream));
-    CF(cufftSetStream(c->tc_c2r, c->stream));
     CS(dev_alloc(&c->tc_part, 6 * c->N3));
     return SCOLA_OK;
 }
@@ -609,7 +606,7 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &all_geo) {
     // LPT-grid sine tables: sin(pi n/N) and sin(2 pi n/N)/d with n the wrapped wavenumber
     c->sin_half_off = (long long)arena.size();
     for (int i = 0; i < p.Np; ++i) {
-        const int n = i < p.Np / 2 ? i : i - p.Np;
+        const int n = 2 * i < p.Np ? i : i - p.Np;
         arena.push_back((float)std::sin(M_PI * n / p.Np));
     }
     // colouring amplitude sqrt(P(k) / d^3) / N^3 per integer |n|^2 = nx^2 + ny^2 + nz^2 of the
@@ -627,7 +624,7 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &all_geo) {
     }
     c->sin_full_off = (long long)arena.size();
     for (int i = 0; i < p.Np; ++i) {
-        const int n = i < p.Np / 2 ? i : i - p.Np;
+        const int n = 2 * i < p.Np ? i : i - p.Np;
         arena.push_back((float)(std::sin(2.0 * M_PI * n / p.Np) / c->dq));
     }
     // FDA order 4/6 on the LPT grid: per grid index, the 1D second-derivative symbol
@@ -641,7 +638,7 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &all_geo) {
         // (written as 2 sum_m s_m (cos(m k d) - 1), since s0 = -2 sum_m s_m: exactly 0 at k = 0)
         c->lap1_off = (long long)arena.size();
         for (int i = 0; i < p.Np; ++i) {
-            const int n = i < p.Np / 2 ? i : i - p.Np;
+            const int n = 2 * i < p.Np ? i : i - p.Np;
             const double kd = 2.0 * M_PI * n / p.Np;
             double v = 0.0;
             for (int m = 1; m <= ngh; ++m) v += 2.0 * sc[m] * (std::cos(m * kd) - 1.0);
@@ -649,7 +646,7 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &all_geo) {
         }
         c->grad1_off = (long long)arena.size();
         for (int i = 0; i < p.Np; ++i) {
-            const int n = i < p.Np / 2 ? i : i - p.Np;
+            const int n = 2 * i < p.Np ? i : i - p.Np;
             const double kd = 2.0 * M_PI * n / p.Np;
             double v = 0.0;
             for (int m = 1; m <= ngh; ++m) v += gc[m - 1] * std::sin(m * kd);
@@ -664,9 +661,12 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &all_geo) {
         const double dgf = p.L / c->tc_ng;
         c->tc_lap_off = (long long)arena.size();
         for (int i = 0; i < c->tc_ng; ++i) {
-            const int n = i < c->tc_ng / 2 ? i : i - c->tc_ng;
+            const int n = 2 * i < c->tc_ng ? i : i - c->tc_ng;
             arena.push_back((float)(2.0 * (std::cos(2.0 * M_PI * n / c->tc_ng) - 1.0) / (dgf * dgf)));
         }
+        // and the tables of its FFTs (twiddles; the Bluestein chirp where tc_ng is not a power of two)
+        if (tc_fft_supported(c->tc_ng))
+            tc_fft_tables(c->tc_ng, arena, c->tc_fft_tw_off, c->tc_fft_w_off, c->tc_fft_bk_off);
     }
     // tensor-core DST groups (one per distinct Ng): the FP32 sine matrix
     bool all_tc = true;
@@ -982,9 +982,7 @@ scola_status run_tcola(scola_ctx *c, bool record) {
         CK(mark(k, 1));
         CK(launch_tc_density(*c, delta));
         CK(mark(k, 2));
-        CF(cufftExecR2C(c->tc_r2c, delta, c->tc_dk));
-        CK(launch_tc_green(*c));
-        CF(cufftExecC2R(c->tc_c2r, c->tc_dk, phi));
+        CK(launch_tc_poisson(*c, delta, phi));
         CK(mark(k, 3));
         CK(launch_tc_kick_drift(*c, phi, kick_drift_coefficients(c->tt, k)));
         CK(mark(k, 4));
@@ -1458,10 +1456,6 @@ void scola_destroy(scola_ctx *c) {
         cufftDestroy(c->plan_r2c);
         cufftDestroy(c->plan_c2r);
     }
-    if (c->tc_plans) {
-        cufftDestroy(c->tc_r2c);
-        cufftDestroy(c->tc_c2r);
-    }
     void *ptrs[] = {c->boxes, c->all_boxes, c->all_coef, c->all_coefL, c->coef, c->coefL, c->tables, c->table_arena, c->pchunks, c->tchunks, c->shchunks,
                     c->zitems, c->citems, c->mchunks, c->ppchunks, c->tc_tiles, c->tc_planes, c->rx_tiles, c->dev_err, c->ckpt, c->seg, c->fin,
                     c->adj, c->lamG, c->lam_phi_pad, c->adj_in, c->adj_out, c->lam_shell, c->lamPsi1,
@@ -1470,7 +1464,7 @@ void scola_destroy(scola_ctx *c) {
                     c->work, c->work2, c->phi,
                     c->shell, c->ck, c->cp, c->ct, c->g[0], c->g[1], c->g[2], c->g[3], c->phi1,
                     c->phi2, c->psi1, c->psi2, c->dens_acc, c->w_h2d, c->x_h2d, c->p_h2d,
-                    c->tc_part, c->tc_acc, c->tc_delta, c->tc_phi, c->tc_dk, c->rec_delta, c->rec_phi};
+                    c->tc_part, c->tc_acc, c->tc_delta, c->tc_phi, c->tc_dk, c->tc_dk2, c->rec_delta, c->rec_phi};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     for (auto &e : c->ev)

@@ -9,7 +9,8 @@
 // DFTs split into radix-4 and radix-2 butterflies with their twiddles as constants.
 //
 // Rows sit in shared memory with one pad slot per 16 complex values (index i -> i + i / 16),
-// which keeps the stride-16 accesses of the first stage free of bank conflicts.
+// which keeps the stride-16 accesses of the first stage free of bank conflicts, and an odd
+// row stride (row_stride), which keeps reads across rows (a transposed epilogue) free of them.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -19,6 +20,9 @@ namespace fft {
 
 __device__ __forceinline__ int pad(int i) { return i + (i >> 4); }
 __host__ __device__ constexpr int padded(int L) { return L + L / 16; }
+__host__ __device__ constexpr int row_stride(int L) { return padded(L) | 1; }
+// shared-memory complex values for R rows of length L (R L <= span, R <= max_rows)
+__host__ __device__ constexpr int rows_buffer(int span, int max_rows) { return padded(span) + max_rows; }
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -117,7 +121,7 @@ template <int Q, int SIGN, class Load>
 __device__ __forceinline__ void stage(Load load, float2 *dst, int rows, int logL, int m, const float2 *tw) {
     constexpr int logQ = Q == 2 ? 1 : Q == 4 ? 2 : Q == 8 ? 3 : 4;
     const int L = 1 << logL, nb = L >> logQ, lognb = logL - logQ;
-    const int Ls = padded(L);
+    const int Ls = row_stride(L);
     const int step = L / (m * Q);
     for (int q = threadIdx.x; q < rows * nb; q += blockDim.x) {
         const int r = q >> lognb, j = q & (nb - 1);
@@ -141,13 +145,19 @@ __device__ __forceinline__ void stage(Load load, float2 *dst, int rows, int logL
     }
 }
 
+struct NoHook {
+    __device__ void operator()() const {}
+};
+
 // The whole transform of `rows` rows (SIGN -1 forward, +1 inverse, unnormalised).  The first
 // stage reads through first(r, n) and writes dst; later stages ping-pong between dst and spare
 // (first may read spare, never dst).  Returns the buffer holding the result; synchronises the
-// block after every stage.  logL >= 1.
-template <int SIGN, class Load>
-__device__ float2 *transform(Load first, float2 *dst, float2 *spare, int rows, int logL, const float2 *tw) {
-    const int Ls = padded(1 << logL);
+// block after every stage and calls after_first() once the first stage's barrier has passed
+// (whatever first read is free from then on).  logL >= 1.
+template <int SIGN, class Load, class Hook = NoHook>
+__device__ float2 *transform(Load first, float2 *dst, float2 *spare, int rows, int logL, const float2 *tw,
+                             Hook after_first = Hook()) {
+    const int Ls = row_stride(1 << logL);
     auto from = [&](const float2 *src) {
         return [src, Ls](int r, int n) { return src[r * Ls + pad(n)]; };
     };
@@ -158,6 +168,7 @@ __device__ float2 *transform(Load first, float2 *dst, float2 *spare, int rows, i
         if (!started) stage<16, SIGN>(first, a, rows, logL, m, tw);
         else stage<16, SIGN>(from(b), a, rows, logL, m, tw);
         __syncthreads();
+        if (!started) after_first();
         started = true;
         float2 *t = a;
         a = b;
@@ -176,6 +187,7 @@ __device__ float2 *transform(Load first, float2 *dst, float2 *spare, int rows, i
             if (left == 3) stage<8, SIGN>(from(b), a, rows, logL, m, tw);
         }
         __syncthreads();
+        if (!started) after_first();
         float2 *t = a;
         a = b;
         b = t;

@@ -195,9 +195,8 @@ struct Ctx {
     long long tc_n3 = 0, tc_lap_off = 0;              // tc_lap_off: 1D FDA-2 symbol per index in table_arena
     float *tc_part = nullptr, *tc_delta = nullptr, *tc_phi = nullptr;
     unsigned long long *tc_acc = nullptr;
-    cufftComplex *tc_dk = nullptr;
-    cufftHandle tc_r2c = 0, tc_c2r = 0;
-    bool tc_plans = false;
+    cufftComplex *tc_dk = nullptr, *tc_dk2 = nullptr;   // half-spectrum work grids (N^2 (N/2 + 1))
+    long long tc_fft_tw_off = 0, tc_fft_w_off = 0, tc_fft_bk_off = 0;   // FFT tables in table_arena
     float *rec_delta = nullptr, *rec_phi = nullptr;
 
     // adjoint (scola_set_checkpointing / scola_backward)
@@ -292,11 +291,16 @@ cudaError_t launch_spectrum(Ctx &c, const cufftComplex *dk, const int *bin_of_n2
 constexpr int kMaxSpectrumBins = 2048;
 
 // periodic tCOLA (k_tcola.cu): particle init, deposit into the counts, density (clears the
-// counts), Green's function on tc_dk, kick-drift reading the potential phi, final x and p
+// counts), kick-drift reading the potential phi, final x and p
 cudaError_t launch_tc_init(Ctx &c);
 cudaError_t launch_tc_deposit(Ctx &c);
 cudaError_t launch_tc_density(Ctx &c, float *delta);
-cudaError_t launch_tc_green(Ctx &c);
+// the periodic Poisson solve delta -> Phi on the tCOLA grid (k_tcola_fft.cu, five passes)
+void tc_fft_plan(int N, int &L, int &logL, int &R, bool &blue);
+bool tc_fft_supported(int N);
+void tc_fft_tables(int N, std::vector<float> &arena, long long &tw_off, long long &w_off, long long &bk_off);
+cudaError_t init_tc_fft_kernels();
+cudaError_t launch_tc_poisson(Ctx &c, const float *delta, float *phi);
 cudaError_t launch_tc_kick_drift(Ctx &c, const float *phi, const KickDrift &kd);
 cudaError_t launch_tc_final(Ctx &c, float *x, float *p);
 // study inputs of the bound batch's boxes: the Poisson source from a full-grid delta

@@ -42,7 +42,6 @@ namespace {
 
 constexpr int kRxThreads = 256;
 constexpr int kRxSpan = 4096;       // complex values per transform batch (R pairs x L)
-constexpr int kRxBuf = fft::padded(kRxSpan);   // per shared-memory buffer (padded rows)
 constexpr int kMaxRxGroups = 4;     // Ng groups per launch (more: further launches)
 
 enum RxPass { RX_F = 1, RX_XF = 2, RX_ZI = 3, RX_YI = 4, RX_XI = 5 };
@@ -69,8 +68,11 @@ struct RxArgs {
 using fft::cmul;
 using fft::cmulc;
 
+// shared-memory buffer of the R rows of one transform batch (padded rows, odd stride)
+int rx_buf(int L) { return (kRxSpan / L) * fft::row_stride(L); }
+
 size_t rx_smem_bytes(int Ng, int P, int L) {
-    return sizeof(float2) * ((size_t)2 * kRxBuf + L + L + P) + sizeof(float) * ((size_t)P + Ng) + 16;
+    return sizeof(float2) * ((size_t)2 * rx_buf(L) + L + L + P) + sizeof(float) * ((size_t)P + Ng) + 16;
 }
 
 template <int PASS>
@@ -83,10 +85,10 @@ __global__ void __launch_bounds__(kRxThreads, 3) k_dst_radix(const RxArgs A) {
     const int Ng = G.Ng, P = G.P, L = G.L, logL = G.logL, R = G.R;
     const int rows = 2 * R;                                // pencils per tile (a power of two)
     const int Ngs = Ng | 1;                                // odd row stride of the result rows
-    const int Ls = fft::padded(L);                         // padded row stride of the transforms
+    const int Ls = fft::row_stride(L);                     // padded row stride of the transforms
     float2 *buf0 = reinterpret_cast<float2 *>(smem);
-    float2 *buf1 = buf0 + kRxBuf;
-    float2 *tw = buf1 + kRxBuf;                            // L
+    float2 *buf1 = buf0 + R * Ls;
+    float2 *tw = buf1 + R * Ls;                            // L
     float2 *Bk = tw + L;                                   // L
     float2 *w = Bk + L;                                    // P
     float *sn = reinterpret_cast<float *>(w + P);          // P

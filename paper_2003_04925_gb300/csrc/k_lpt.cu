@@ -19,7 +19,8 @@ namespace scola {
 
 namespace {
 
-__device__ __forceinline__ int wavenumber(int i, int N) { return i < N / 2 ? i : i - N; }
+// the wrapped wavenumber of DFT index i: 0 .. (N - 1) / 2, then negative (-N / 2 first for even N)
+__device__ __forceinline__ int wavenumber(int i, int N) { return 2 * i < N ? i : i - N; }
 
 // White noise (step A.1) from Philox4x32-10 (Salmon et al. 2011): counter block g = (g mod
 // 2^32, g div 2^32, 0, 0) under the key (seed mod 2^32, seed div 2^32); ten rounds that

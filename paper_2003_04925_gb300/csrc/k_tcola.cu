@@ -9,8 +9,9 @@
 //   deposit     periodic CIC, 2^-32 fixed-point 64-bit atomics (the sums do not depend on
 //               the order of the additions: deterministic)
 //   density     delta = (Ngf / Np)^3 n - 1; the counts are cleared as they are read
-//   green       Phi_k = delta_k / (Lambda(k) Ngf^3) on the cuFFT half spectrum, Lambda the
-//               FDA-2 Laplacian symbol sum_a (2 / dg^2)(cos(k_a dg) - 1), k = 0 removed
+//   poisson     Phi_k = delta_k / (Lambda(k) Ngf^3), Lambda the FDA-2 Laplacian symbol
+//               sum_a (2 / dg^2)(cos(k_a dg) - 1), k = 0 removed (k_tcola_fft.cu: five passes
+//               of shared-memory FFTs)
 //   kick_drift  FDA-2 central gradient at the 8 CIC corners (periodic wrap), CIC-weighted,
 //               then the kick (Eqs. 48, 54) and the drift (Eq. 53)
 //   final       x = (q + s) mod L, p = p_res + L+ at a_f (Eq. 55)
@@ -94,28 +95,6 @@ __global__ void k_tc_density(unsigned long long *__restrict__ acc, long long n, 
          i += (long long)gridDim.x * blockDim.x) {
         delta[i] = fixed_to_float(acc[i]) * sc - 1.0f;
         acc[i] = 0ull;
-    }
-}
-
-__global__ void k_tc_green(cufftComplex *__restrict__ dk, int Ngf, const float *__restrict__ lap1, float inv_n3) {
-    const int Nz = Ngf / 2 + 1;
-    const long long n = (long long)Ngf * Ngf * Nz;
-    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
-         idx += (long long)gridDim.x * blockDim.x) {
-        const int kz = (int)(idx % Nz);
-        const long long t = idx / Nz;
-        const int ky = (int)(t % Ngf), kx = (int)(t / Ngf);
-        cufftComplex v = dk[idx];
-        if (idx == 0) {
-            v.x = 0.0f;
-            v.y = 0.0f;
-        } else {
-            const float lam = lap1[kx] + lap1[ky] + lap1[kz];
-            const float g = inv_n3 / lam;
-            v.x *= g;
-            v.y *= g;
-        }
-        dk[idx] = v;
     }
 }
 
@@ -268,14 +247,6 @@ cudaError_t launch_tc_density(Ctx &c, float *delta) {
     const int ratio = c.tc_ng / c.Np;
     const float sc = (float)((double)ratio * ratio * ratio / kFix);
     k_tc_density<<<grid_of(c.tc_n3, 256), 256, 0, c.stream>>>(c.tc_acc, c.tc_n3, sc, delta);
-    ++c.launches;
-    return cudaGetLastError();
-}
-
-cudaError_t launch_tc_green(Ctx &c) {
-    const long long n = (long long)c.tc_ng * c.tc_ng * (c.tc_ng / 2 + 1);
-    k_tc_green<<<grid_of(n, 256), 256, 0, c.stream>>>(c.tc_dk, c.tc_ng, c.table_arena + c.tc_lap_off,
-                                                      (float)(1.0 / (double)c.tc_n3));
     ++c.launches;
     return cudaGetLastError();
 }

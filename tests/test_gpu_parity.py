@@ -59,6 +59,9 @@ CASES_PM = {
     # one box of the paper's 1 Gpc/h geometry (Sec. 4 Table 1: Np,sCOLA = 188, Ng = 189, the
     # 1000/1024 Mpc/h particle spacing) on its own
     "table1_1gpc": dict(L=188 * 1000.0 / 1024, Np=188, Ntiles=1, Nbuf=0, Ng=189, nsteps=1, a_i=0.05, a_f=1.0),
+    # an odd number of particles per side: the initial conditions' top positive wavenumber
+    # (N - 1) / 2 has no negative twin
+    "odd_np": dict(SMALL, Np=25, Ntiles=1, Nbuf=0, nsteps=4),
 }
 
 
@@ -85,7 +88,7 @@ def _to_dev(a):
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
 
 
-@pytest.mark.parametrize("name", ["plain_32", "single_box", "fda4", "fda6_ratio2"])
+@pytest.mark.parametrize("name", ["plain_32", "single_box", "fda4", "fda6_ratio2", "odd_np"])
 def test_lpt_fields_match_oracle(name):
     kw = CASES_PM[name]
     w, f, _ = oracle_fields(kw)

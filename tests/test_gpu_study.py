@@ -49,9 +49,17 @@ def _errors(x, p, xr, pr, L, dg):
     return rms, prel
 
 
-@pytest.mark.parametrize("ratio", [1, 2])
-def test_tcola_matches_oracle(ratio):
-    kw = dict(SMALL, mesh_ratio=ratio)
+# tCOLA grids of N = mesh_ratio Np = 32 and 64 (power-of-two transforms), 48 (even, Bluestein)
+# and 25 (odd, Bluestein)
+TCOLA_GRIDS = {"32": dict(SMALL, mesh_ratio=1), "64": dict(SMALL, mesh_ratio=2),
+               "48": dict(SMALL, Np=24, Ntiles=1, Nbuf=0, mesh_ratio=2),
+               "25": dict(SMALL, Np=25, Ntiles=1, Nbuf=0, mesh_ratio=1)}
+
+
+@pytest.mark.parametrize("grid", list(TCOLA_GRIDS))
+def test_tcola_matches_oracle(grid):
+    kw = TCOLA_GRIDS[grid]
+    ratio = kw["mesh_ratio"]
     cfg = oracle_cfg(kw)
     w = synth_inputs.white_noise(cfg.Np, 1)
     sim = _sim(kw)
@@ -69,7 +77,7 @@ def test_tcola_matches_oracle(ratio):
     xr = np.mod(oscola.lattice_positions(cfg.Np, cfg.L) + ref["s"], cfg.L)
     dg = cfg.L / (ratio * cfg.Np)
     rms, prel = _errors(_np(x1), _np(p1), xr, ref["p"], cfg.L, dg)
-    print("tcola ratio %d: position RMS %.3e PM cells, momentum RMS %.3e relative" % (ratio, rms, prel))
+    print("tcola grid %s: position RMS %.3e PM cells, momentum RMS %.3e relative" % (grid, rms, prel))
     assert rms <= 1e-3, rms
     assert prel <= 1e-3, prel
 
