@@ -13,7 +13,8 @@
  * 3.4, Eq. 23, App. A-C), and writes the tile particles back to global
  * arrays (B.2).  Every step of this path runs in the library's own CUDA
  * kernels except the full-box Fourier transforms of the initial-condition
- * stage, which call cuFFT (the paper's code calls FFTW there, Sec. 3.1).
+ * stage and of its adjoint, which call cuFFT once per run (the paper's code
+ * calls FFTW there, Sec. 3.1).
  *
  * Conventions used by every entry point:
  *   - units: Mpc/h, time in 1/H0 with H0 = 1, time variable the scale factor a;
@@ -391,8 +392,8 @@ scola_status scola_kernel_times(const scola_ctx *ctx, double *ms_per_launch, int
  * Average device time per force evaluation [ms] of the stages of the last periodic tCOLA
  * run (scola_tcola, or the study-mode records of scola_forward) made in profiling mode.
  * ms_per_launch (host, n >= 4 doubles) receives: periodic CIC deposit, density (counts ->
- * delta, clearing the counts), Poisson solve (cuFFT R2C, Green's function, cuFFT C2R),
- * interpolate + kick + drift.  Errors: STATE when no tCOLA run was profiled.
+ * delta, clearing the counts), Poisson solve (five passes of shared-memory FFTs with the
+ * Green's function in the z pass), interpolate + kick + drift.  Errors: STATE when no tCOLA run was profiled.
  */
 scola_status scola_tcola_kernel_times(const scola_ctx *ctx, double *ms_per_launch, int32_t n);
 
@@ -431,9 +432,10 @@ int32_t scola_uses_tensor_cores(const scola_ctx *ctx);
 /*
  * Adjoint support.  With checkpointing enabled, scola_forward also stores checkpoints of
  * every box particle's state (see scola_set_checkpoint_interval) and the context keeps the
- * adjoint work arrays.  Batched form, FDA order 2, no study mode (UNSUPPORTED otherwise);
- * 2LPT or Zel'dovich frame, modified or standard KDK factors, common or per-tile final scale
- * factors, one or several streamed batches.  Synchronises the stream.
+ * adjoint work arrays.  Batched form, no study mode (UNSUPPORTED otherwise); FDA order 2, 4
+ * or 6, 2LPT or Zel'dovich frame, modified or standard KDK factors, common or per-tile final
+ * scale factors, one or several streamed batches, any Poisson-solve form.  Synchronises the
+ * stream.
  */
 scola_status scola_set_checkpointing(scola_ctx *ctx, int32_t enable);
 
@@ -605,8 +607,10 @@ scola_status scola_generate_white_noise(scola_ctx *ctx, uint64_t seed, float *w_
  *   w_dev  device, Np^3 white noise (as scola_forward)
  *   x_dev  device, Np^3 x 3 final positions in [0, L), global-id order
  *   p_dev  device, Np^3 x 3 final momenta (L+ applied), global-id order
- * Every particle is written.  FP32 fields and particles; cuFFT transforms.
- * Errors: INVALID_ARG (NULL), UNSUPPORTED (fda_order != 2), OOM, CUDA.
+ * Every particle is written.  FP32 fields and particles; the library's own shared-memory
+ * FFTs (power-of-two grids directly, others by Bluestein's chirp transform).
+ * Errors: INVALID_ARG (NULL), UNSUPPORTED (fda_order != 2, or mesh_ratio Np outside
+ * 2 .. 1024), OOM, CUDA.
  */
 scola_status scola_tcola(scola_ctx *ctx, const float *w_dev, float *x_dev, float *p_dev);
 

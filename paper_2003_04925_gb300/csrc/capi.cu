@@ -1641,10 +1641,6 @@ scola_status scola_set_checkpointing(scola_ctx *c, int32_t enable) {
         set_error("the adjoint runs on the batched form only");
         return SCOLA_ERR_UNSUPPORTED;
     }
-    if (on && c->prm.fda_order != 2) {
-        set_error("the adjoint is built for FDA order 2 only");
-        return SCOLA_ERR_UNSUPPORTED;
-    }
     if (on == c->checkpointing) return SCOLA_OK;
     CK(c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize());
     if (c->evolve_exec) {

@@ -24,9 +24,9 @@
 // full-box arrays, and the shells' adjoint scattered to phi1 (trilinear transpose).
 // The 2LPT and colouring adjoints (Fourier, symmetric operators) are in capi.cu.
 // Accumulations shared between particles use FP32 atomics (sum order varies).
+// FDA order n = 2, 4, 6 (Sec. 3.1): padded grids of G = n ghost layers per side, gradients of
+// n / 2 central-difference terms; each transpose follows the forward kernel of the same order.
 #include "device_util.cuh"
-
-// (The adjoint is built for FDA order 2: padded grids of Ng + 4 cells, 2 ghost layers.)
 
 namespace scola {
 
@@ -196,6 +196,7 @@ k_adj_kick_drift(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ ch
     }
 }
 
+template <int ORDER>
 __global__ void __launch_bounds__(kChunk)
 k_adj_interp(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
              const float *__restrict__ s, long long P, const float *__restrict__ phi, float D1,
@@ -204,7 +205,7 @@ k_adj_interp(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks
     const Chunk ch = chunks[blockIdx.x];
     const BoxDesc &B = boxes[ch.box];
     if (const float *cf = box_coef(coef, ch.box, k, nk)) D1 = 1.0f / cf[6];
-    const int Nsc = B.Nsc, Ng = B.Ng;
+    const int Nsc = B.Nsc, Ng = B.Ng, G = B.gpad, ng = Fda<ORDER>::ng;
     const int local = ch.start + threadIdx.x;
     if (local >= Nsc * Nsc * Nsc) return;
     const long long gi = B.p_off + local;
@@ -214,11 +215,13 @@ k_adj_interp(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks
     const float lF[3] = {adj[12 * P + gi], adj[13 * P + gi], adj[14 * P + gi]};
     int i0[3];
     float f[3], fr[3];
-    corner_setup(B, b, sv, -1.0f, (float)Ng, Ng - 1, i0, f, fr);
-    const long long S1 = Ng + 4, S2 = S1 * S1;
-    const long long base = B.pp_off + ((long long)(i0[0] + 2) * S1 + (i0[1] + 2)) * S1 + (i0[2] + 2);
+    // the forward clamp: mesh coordinate in [-ng, Ng + ng - 1], lower corner <= Ng + ng - 2
+    corner_setup(B, b, sv, -(float)ng, (float)(Ng + ng - 1), Ng + ng - 2, i0, f, fr);
+    const long long S1 = Ng + 2 * G, S2 = S1 * S1;
+    const long long st[3] = {S2, S1, 1};
+    const long long base = B.pp_off + ((long long)(i0[0] + G) * S1 + (i0[1] + G)) * S1 + (i0[2] + G);
     const float *Pp = phi + base;
-    const float h = 0.5f * B.inv_dg * D1;     // the stored potential is Phi / D1
+    const float h = B.inv_dg * D1;            // the stored potential is Phi / D1
     float dir[3] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int dx = 0; dx < 2; ++dx)
@@ -227,10 +230,14 @@ k_adj_interp(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks
 #pragma unroll
             for (int dz = 0; dz < 2; ++dz) {
                 const long long o = dx * S2 + dy * S1 + dz;
-                const float G0 = (Pp[o + S2] - Pp[o - S2]) * h;
-                const float G1 = (Pp[o + S1] - Pp[o - S1]) * h;
-                const float G2 = (Pp[o + 1] - Pp[o - 1]) * h;
-                const float gl = G0 * lF[0] + G1 * lF[1] + G2 * lF[2];
+                float gl = 0.0f;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    float g = 0.0f;
+#pragma unroll
+                    for (int m = 1; m <= ng; ++m) g = fmaf(Fda<ORDER>::g(m), Pp[o + m * st[a]] - Pp[o - m * st[a]], g);
+                    gl = fmaf(g * h, lF[a], gl);
+                }
                 const float wx = dx ? f[0] : 1.f - f[0], wy = dy ? f[1] : 1.f - f[1],
                             wz = dz ? f[2] : 1.f - f[2];
                 dir[0] += (dx ? 1.f : -1.f) * wy * wz * gl;
@@ -245,14 +252,16 @@ k_adj_interp(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks
     for (int a = 0; a < 3; ++a) adj[a * P + gi] += dir[a] * fr[a] * B.inv_dg;
 }
 
-// lam_Phi(c) = sum_a (lam_G_a(c - e_a) - lam_G_a(c + e_a)) / (2 dg) over the padded grid.
+// lam_Phi(c) = sum_a sum_m g_m (lam_G_a(c - m e_a) - lam_G_a(c + m e_a)) / dg over the padded grid
+// (the transpose of the order-n central gradient).
+template <int ORDER>
 __global__ void __launch_bounds__(kChunk)
 k_adj_div(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
           const float *__restrict__ lamG, long long MP, float *__restrict__ lam_phi_pad,
           float *__restrict__ interior_out) {
     const Chunk ch = chunks[blockIdx.x];
     const BoxDesc &B = boxes[ch.box];
-    const int Ng = B.Ng, S = Ng + 4;
+    const int Ng = B.Ng, G = B.gpad, S = Ng + 2 * G;
     const long long n = (long long)S * S * S;
     const long long idx = (long long)ch.start + threadIdx.x;
     if (idx >= n) return;
@@ -263,19 +272,27 @@ k_adj_div(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
     float v = 0.0f;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const float *G = lamG + a * MP;
-        if (p[a] > 0) v += G[here - strides[a]];
-        if (p[a] < S - 1) v -= G[here + strides[a]];
+        const float *Ga = lamG + a * MP;
+#pragma unroll
+        for (int m = 1; m <= Fda<ORDER>::ng; ++m) {
+            float d = 0.0f;
+            if (p[a] - m >= 0) d += Ga[here - m * strides[a]];
+            if (p[a] + m < S) d -= Ga[here + m * strides[a]];
+            v = fmaf(Fda<ORDER>::g(m), d, v);
+        }
     }
-    v *= 0.5f * B.inv_dg;
-    const bool inside = p[0] >= 2 && p[0] < Ng + 2 && p[1] >= 2 && p[1] < Ng + 2 && p[2] >= 2 && p[2] < Ng + 2;
+    v *= B.inv_dg;
+    const bool inside = p[0] >= G && p[0] < Ng + G && p[1] >= G && p[1] < Ng + G && p[2] >= G && p[2] < Ng + G;
     if (inside)
-        interior_out[B.m_off + ((long long)(p[0] - 2) * Ng + (p[1] - 2)) * Ng + (p[2] - 2)] = v;
+        interior_out[B.m_off + ((long long)(p[0] - G) * Ng + (p[1] - G)) * Ng + (p[2] - G)] = v;
     else
         lam_phi_pad[here] = v;
 }
 
-// lam_shell += D1 (lam_Phi_ghost - transpose of the boundary source of Eq. 62).
+// lam_shell += D1 (lam_Phi_ghost - transpose of the boundary source of Eq. 62).  A ghost
+// cell m' layers beyond a face, whose other two coordinates are interior, enters the order-n
+// Laplacian of the interior cells m - m' from the face (m = m' .. n / 2) with weight s_m.
+template <int ORDER>
 __global__ void __launch_bounds__(kChunk)
 k_adj_shell(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
             const float *__restrict__ lam_phi_pad, const float *__restrict__ lam_src_pad, float D1,
@@ -283,12 +300,12 @@ k_adj_shell(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
     const Chunk ch = chunks[blockIdx.x];
     const BoxDesc &B = boxes[ch.box];
     if (const float *cf = box_coef(coef, ch.box, k, nk)) D1 = 1.0f / cf[6];
-    const int Ng = B.Ng;
+    const int Ng = B.Ng, G = B.gpad;
     const long long idx = (long long)ch.start + threadIdx.x;
-    if (idx >= shell_count(Ng, 2)) return;
+    if (idx >= shell_count(Ng, G)) return;
     int p[3];
-    shell_coord(idx, Ng, 2, p[0], p[1], p[2]);
-    const long long S = Ng + 4;
+    shell_coord(idx, Ng, G, p[0], p[1], p[2]);
+    const long long S = Ng + 2 * G;
     const long long strides[3] = {S * S, S, 1};
     const long long here = B.pp_off + ((long long)p[0] * S + p[1]) * S + p[2];
     float v = lam_phi_pad[here];
@@ -296,10 +313,14 @@ k_adj_shell(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const int o1 = (a + 1) % 3, o2 = (a + 2) % 3;
-        const bool others = p[o1] >= 2 && p[o1] < Ng + 2 && p[o2] >= 2 && p[o2] < Ng + 2;
+        const bool others = p[o1] >= G && p[o1] < Ng + G && p[o2] >= G && p[o2] < Ng + G;
         if (!others) continue;
-        if (p[a] == 1) v -= lam_src_pad[here + strides[a]] * c2;
-        if (p[a] == Ng + 2) v -= lam_src_pad[here - strides[a]] * c2;
+        const int below = G - p[a], above = p[a] - (Ng + G - 1);      // m' on either side
+#pragma unroll
+        for (int m = 1; m <= Fda<ORDER>::ng; ++m) {
+            if (below >= 1 && m >= below) v -= Fda<ORDER>::s(m) * lam_src_pad[here + m * strides[a]] * c2;
+            if (above >= 1 && m >= above) v -= Fda<ORDER>::s(m) * lam_src_pad[here - m * strides[a]] * c2;
+        }
     }
     lam_shell[B.sh_off + idx] += D1 * v;
 }
@@ -320,7 +341,8 @@ k_adj_deposit(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunk
     int i0[3];
     float f[3], fr[3];
     corner_setup(B, b, sv, -2.0f, (float)Ng + 1.0f, Ng + 1, i0, f, fr);
-    const long long S = Ng + 4;
+    const int G = B.gpad;
+    const long long S = Ng + 2 * G;
     float lam[3] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int dx = 0; dx < 2; ++dx) {
@@ -334,7 +356,7 @@ k_adj_deposit(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunk
             for (int dz = 0; dz < 2; ++dz) {
                 const int cz = i0[2] + dz;
                 if ((unsigned)cz >= (unsigned)Ng) continue;
-                const float v = lam_src_pad[B.pp_off + ((long long)(cx + 2) * S + (cy + 2)) * S + (cz + 2)];
+                const float v = lam_src_pad[B.pp_off + ((long long)(cx + G) * S + (cy + G)) * S + (cz + G)];
                 const float wx = dx ? f[0] : 1.f - f[0], wy = dy ? f[1] : 1.f - f[1],
                             wz = dz ? f[2] : 1.f - f[2];
                 lam[0] += (dx ? 1.f : -1.f) * wy * wz * v;
@@ -381,11 +403,11 @@ k_adj_shell_to_phi1(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__
     const Chunk ch = chunks[blockIdx.x];
     const BoxDesc &B = boxes[ch.box];
     const long long idx = (long long)ch.start + threadIdx.x;
-    if (idx >= shell_count(B.Ng, 2)) return;
+    if (idx >= shell_count(B.Ng, B.gpad)) return;
     const float lv = lam_shell[B.sh_off + idx];
     if (lv == 0.0f) return;
     int pc[3];
-    shell_coord(idx, B.Ng, 2, pc[0], pc[1], pc[2]);
+    shell_coord(idx, B.Ng, B.gpad, pc[0], pc[1], pc[2]);
     int i0[3];
     float f[3];
     shell_stencil(B, pc, Ntile, i0, f);
@@ -403,26 +425,25 @@ k_adj_shell_to_phi1(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__
             }
 }
 
-// out = -sum_a central_difference_a(g_a) (+ out when accumulate): transpose of the gradient.
-__global__ void k_neg_div(const float *__restrict__ g, int N, float inv_2d, int accumulate,
-                          float *__restrict__ out) {
-    const long long N3 = (long long)N * N * N;
+// out = -sum_a D_a(g_a) (+ out when accumulate): the transpose of the periodic order-n central
+// gradient D_a f(c) = (1/d) sum_m g_m (f(c + m e_a) - f(c - m e_a)).
+template <int ORDER>
+__global__ void k_neg_div(const float *__restrict__ g, int N, float inv_d, int accumulate, float *__restrict__ out) {
+    const long long N3 = (long long)N * N * N, NN = (long long)N * N;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < N3;
          idx += (long long)gridDim.x * blockDim.x) {
-        const int k = (int)(idx % N);
-        const long long t = idx / N;
-        const int j = (int)(t % N);
-        const int i = (int)(t / N);
-        const long long NN = (long long)N * N;
-        const int ip = i + 1 == N ? 0 : i + 1, im = i == 0 ? N - 1 : i - 1;
-        const int jp = j + 1 == N ? 0 : j + 1, jm = j == 0 ? N - 1 : j - 1;
-        const int kp = k + 1 == N ? 0 : k + 1, km = k == 0 ? N - 1 : k - 1;
-        const long long row = (long long)i * NN + (long long)j * N;
-        const float v = (g[(long long)ip * NN + (long long)j * N + k] - g[(long long)im * NN + (long long)j * N + k]) +
-                        (g[N3 + (long long)i * NN + (long long)jp * N + k] -
-                         g[N3 + (long long)i * NN + (long long)jm * N + k]) +
-                        (g[2 * N3 + row + kp] - g[2 * N3 + row + km]);
-        out[idx] = (accumulate ? out[idx] : 0.0f) - v * inv_2d;
+        const int c[3] = {(int)(idx / NN), (int)((idx / N) % N), (int)(idx % N)};
+        const long long st[3] = {NN, N, 1};
+        float v = 0.0f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float *ga = g + a * N3;
+            const long long rest = idx - c[a] * st[a];
+#pragma unroll
+            for (int m = 1; m <= Fda<ORDER>::ng; ++m)
+                v = fmaf(Fda<ORDER>::g(m), ga[rest + wrap(c[a] + m, N) * st[a]] - ga[rest + wrap(c[a] - m, N) * st[a]], v);
+        }
+        out[idx] = (accumulate ? out[idx] : 0.0f) - v * inv_d;
     }
 }
 
@@ -504,24 +525,31 @@ cudaError_t launch_adj_kick_drift(Ctx &c, float *adj, const KickDrift &kd, int k
     return cudaGetLastError();
 }
 
+// the kernel template of the context's FDA order
+#define SCOLA_BY_ORDER(KERNEL, GRID, ...)                                                    \
+    switch (c.prm.fda_order) {                                                               \
+        case 4: KERNEL<4><<<GRID, kChunk, 0, c.stream>>>(__VA_ARGS__); break;                \
+        case 6: KERNEL<6><<<GRID, kChunk, 0, c.stream>>>(__VA_ARGS__); break;                \
+        default: KERNEL<2><<<GRID, kChunk, 0, c.stream>>>(__VA_ARGS__);                      \
+    }
+
 cudaError_t launch_adj_interp(Ctx &c, const float *s, float *adj, float *lamG, float D1, int k) {
-    k_adj_interp<<<c.n_pchunks, kChunk, 0, c.stream>>>(c.boxes, c.pchunks, s, c.P, c.phi, D1, adj, lamG, c.MP,
-                                                        k >= 0 ? c.coef : nullptr, k, c.coef_nk);
+    SCOLA_BY_ORDER(k_adj_interp, c.n_pchunks, c.boxes, c.pchunks, s, c.P, c.phi, D1, adj, lamG, c.MP,
+                   k >= 0 ? c.coef : nullptr, k, c.coef_nk)
     ++c.launches;
     return cudaGetLastError();
 }
 
 cudaError_t launch_adj_div(Ctx &c, const float *lamG, float *lam_phi_pad, float *interior_out) {
-    k_adj_div<<<c.n_ppchunks, kChunk, 0, c.stream>>>(c.boxes, c.ppchunks, lamG, c.MP, lam_phi_pad,
-                                                      interior_out);
+    SCOLA_BY_ORDER(k_adj_div, c.n_ppchunks, c.boxes, c.ppchunks, lamG, c.MP, lam_phi_pad, interior_out)
     ++c.launches;
     return cudaGetLastError();
 }
 
 cudaError_t launch_adj_shell(Ctx &c, const float *lam_phi_pad, const float *lam_src_pad, float D1,
                              float *lam_shell, int k) {
-    k_adj_shell<<<c.n_shchunks, kChunk, 0, c.stream>>>(c.boxes, c.shchunks, lam_phi_pad, lam_src_pad, D1,
-                                                        lam_shell, k >= 0 ? c.coef : nullptr, k, c.coef_nk);
+    SCOLA_BY_ORDER(k_adj_shell, c.n_shchunks, c.boxes, c.shchunks, lam_phi_pad, lam_src_pad, D1, lam_shell,
+                   k >= 0 ? c.coef : nullptr, k, c.coef_nk)
     ++c.launches;
     return cudaGetLastError();
 }
@@ -549,8 +577,13 @@ cudaError_t launch_adj_shell_to_phi1(Ctx &c, const float *lam_shell, float *lam_
 }
 
 cudaError_t launch_neg_div(Ctx &c, const float *g, int accumulate, float *out) {
-    const double d = c.L / c.Np;
-    k_neg_div<<<grid_for(c.N3, 256), 256, 0, c.stream>>>(g, c.Np, (float)(0.5 / d), accumulate, out);
+    const float inv_d = (float)(c.Np / c.L);
+    const int grid = grid_for(c.N3, 256);
+    switch (c.prm.fda_order) {
+        case 4: k_neg_div<4><<<grid, 256, 0, c.stream>>>(g, c.Np, inv_d, accumulate, out); break;
+        case 6: k_neg_div<6><<<grid, 256, 0, c.stream>>>(g, c.Np, inv_d, accumulate, out); break;
+        default: k_neg_div<2><<<grid, 256, 0, c.stream>>>(g, c.Np, inv_d, accumulate, out);
+    }
     ++c.launches;
     return cudaGetLastError();
 }
@@ -564,8 +597,9 @@ cudaError_t launch_adj_source(Ctx &c, const float *lamS, const float *d2, float 
 cudaError_t launch_spec_d2_accumulate(Ctx &c, const cufftComplex *in, cufftComplex *acc, int i, int j) {
     const int N = c.Np;
     const long long n = (long long)N * N * (N / 2 + 1);
-    k_spec_d2_accumulate<<<grid_for(n, 256), 256, 0, c.stream>>>(in, acc, N, c.table_arena + c.sin_full_off,
-                                                                  i, j);
+    // the gradient symbol of the context's FDA order (as the forward second derivatives)
+    k_spec_d2_accumulate<<<grid_for(n, 256), 256, 0, c.stream>>>(
+        in, acc, N, c.table_arena + (c.prm.fda_order != 2 ? c.grad1_off : c.sin_full_off), i, j);
     ++c.launches;
     return cudaGetLastError();
 }

@@ -99,9 +99,10 @@ __global__ void k_colour(cufftComplex *ck, int N, const float *__restrict__ amp)
     }
 }
 
-// Adjoint of colouring after the inverse Laplacian: out = in * amp(k) / Lambda(k), k = 0 -> 0.
+// Adjoint of colouring after the inverse Laplacian: out = in * amp(k) / Lambda(k), k = 0 -> 0;
+// Lambda the FDA-2 symbol from s_half, or (lap1 not null) the order-n symbol sum of lap1.
 __global__ void k_adj_colour(const cufftComplex *in, cufftComplex *out, int N, const float *__restrict__ amp,
-                             const float *s_half, float inv_d2) {
+                             const float *s_half, float inv_d2, const float *__restrict__ lap1) {
     const int Nz = N / 2 + 1;
     const long long n = (long long)N * N * Nz;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
@@ -115,7 +116,7 @@ __global__ void k_adj_colour(const cufftComplex *in, cufftComplex *out, int N, c
         float m = 0.0f;
         if (n2 > 0) {
             const float sx = s_half[kx], sy = s_half[ky], sz = s_half[kz];
-            const float lam = -4.0f * inv_d2 * (sx * sx + sy * sy + sz * sz);
+            const float lam = lap1 ? lap1[kx] + lap1[ky] + lap1[kz] : -4.0f * inv_d2 * (sx * sx + sy * sy + sz * sz);
             m = amp[n2] / lam;
         }
         cufftComplex v = in[idx];
@@ -273,9 +274,9 @@ cudaError_t launch_adj_colour(Ctx &c, const cufftComplex *in, cufftComplex *out)
     const int N = c.Np;
     const long long n = (long long)N * N * (N / 2 + 1);
     const double d = c.L / N;
-    k_adj_colour<<<grid_for(n, 256), 256, 0, c.stream>>>(in, out, N, c.table_arena + c.amp_off,
-                                                          c.table_arena + c.sin_half_off,
-                                                          (float)(1.0 / (d * d)));
+    k_adj_colour<<<grid_for(n, 256), 256, 0, c.stream>>>(
+        in, out, N, c.table_arena + c.amp_off, c.table_arena + c.sin_half_off, (float)(1.0 / (d * d)),
+        c.prm.fda_order != 2 ? c.table_arena + c.lap1_off : nullptr);
     ++c.launches;
     return cudaGetLastError();
 }
