@@ -695,10 +695,12 @@ def deposit_choice(sc, st):
     """The deposit form the context's autotuner kept and the candidates it timed (ms per
     deposit of all boxes; every form gives the same density bit for bit)."""
     names = ("sorted bricks, 256 threads", "sorted bricks, 512 threads",
-             "sorted bricks, 256 threads, 32-bit halves", "L2 fixed-point atomics")
+             "sorted bricks, 256 threads, 32-bit halves", "sorted bricks, 256 threads, 16-bit halves",
+             "L2 fixed-point atomics")
+    halves = {0: "", 1: ", 32-bit halves", 2: ", 16-bit halves"}
     form = {sc.SCOLA_DEPOSIT_SORTED: "sorted bricks, %d threads%s" % (st["deposit_threads"],
-                                                                    ", 32-bit halves" if st["deposit_split"] else ""),
-            sc.SCOLA_DEPOSIT_ATOMIC: names[3]}.get(st["deposit_form"], "not tuned")
+                                                                    halves.get(st["deposit_split"], "")),
+            sc.SCOLA_DEPOSIT_ATOMIC: names[4]}.get(st["deposit_form"], "not tuned")
     return {"kept": form, "candidates_ms": {n: round(t, 4) for n, t in zip(names, st["ms_deposit_candidates"])
                                             if t > 0}}
 

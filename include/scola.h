@@ -206,8 +206,10 @@ typedef struct scola_stats {
     int32_t deposit_form;         /* the form in use: SCOLA_DEPOSIT_SORTED or _ATOMIC (0 before
                                      the first scola_forward / scola_setup_boxes) */
     int32_t deposit_threads;      /* threads per brick CTA of the sorted form, else 0 */
-    int32_t deposit_split;        /* 1: the sorted form keeps 32-bit halves of the counts */
-    double ms_deposit_candidates[4]; /* autotuner timings of one deposit (all boxes of the first
+    int32_t deposit_split;        /* the sorted form's counters: 0 64-bit, 1 32-bit halves with a
+                                     carry, 2 16-bit halves with reductions (exact while a brick
+                                     holds at most 65535 entries; busier bricks use 1) */
+    double ms_deposit_candidates[5]; /* autotuner timings of one deposit (all boxes of the first
                                      batch, or its box 0 in the per-tile form): sorted/256,
                                      sorted/512, sorted/256 with 32-bit halves, atomic;
                                      0 = not timed */

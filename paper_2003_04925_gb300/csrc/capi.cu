@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "device_util.cuh"
+#include "fft_util.cuh"
 
 namespace scola {
 namespace {
@@ -298,6 +299,7 @@ void plan_batch(const scola_ctx *c, const std::vector<BoxGeom> &tiling_geo, int 
         B.q2u = (float)((double)g.ng / g.nsc);
         B.nbar_inv = (float)std::pow((double)g.ng / g.nsc, 3);
         B.dg_d = dg;
+        B.inv_2ng_d = 1.0 / (2.0 * g.ng);
         const int t3[3] = {B.tx, B.ty, B.tz};
         for (int a = 0; a < 3; ++a) B.origin_d[a] = ((double)t3[a] * ntile - g.nbuf) * c->dq;
         bp.boxes.push_back(B);
@@ -668,6 +670,10 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &all_geo) {
         if (tc_fft_supported(c->tc_ng))
             tc_fft_tables(c->tc_ng, arena, c->tc_fft_tw_off, c->tc_fft_w_off, c->tc_fft_bk_off);
     }
+    // the shared-memory FFTs' second-stage twiddles (radix DST, tCOLA Poisson solve)
+    if (arena.size() & 1) arena.push_back(0.0f);
+    c->fft_w256_off = (long long)arena.size();
+    fft::append_w256(arena);
     // tensor-core DST groups (one per distinct Ng): the FP32 sine matrix
     bool all_tc = true;
     for (auto &kv : c->tbl_of) all_tc = all_tc && tc_supported(kv.first);
@@ -1091,13 +1097,12 @@ struct BoxView {
 scola_status autotune_deposit(scola_ctx *c) {
     if (c->tuned) return SCOLA_OK;
     struct Cand {
-        int form, threads;
-        bool split;
+        int form, threads, split;
     };
-    const Cand all[4] = {{0, 256, false}, {0, 512, false}, {0, 256, true}, {1, 512, false}};
-    int lo = 0, hi = 4;
-    if (c->prm.deposit_form == SCOLA_DEPOSIT_SORTED) hi = 3;
-    if (c->prm.deposit_form == SCOLA_DEPOSIT_ATOMIC) lo = 3;
+    const Cand all[5] = {{0, 256, 0}, {0, 512, 0}, {0, 256, 1}, {0, 256, 2}, {1, 512, 0}};
+    int lo = 0, hi = 5;
+    if (c->prm.deposit_form == SCOLA_DEPOSIT_SORTED) hi = 4;
+    if (c->prm.deposit_form == SCOLA_DEPOSIT_ATOMIC) lo = 4;
     const long long launches = c->launches;
     float best = -1.0f;
     int pick = lo;
@@ -1114,7 +1119,9 @@ scola_status autotune_deposit(scola_ctx *c) {
             c->deposit_split = all[q].split;
             const std::string which = std::string("deposit autotuner, ") +
                                       (all[q].form == 0 ? "sorted form, " + std::to_string(all[q].threads) + " threads" +
-                                                              (all[q].split ? ", 32-bit halves" : "")
+                                                              (all[q].split == 1   ? ", 32-bit halves"
+                                                               : all[q].split == 2 ? ", 16-bit halves"
+                                                                                   : "")
                                                         : std::string("atomic form"));
             cudaError_t e = launch_deposit(*c, c->part, c->P, inv_D1);      // warm-up
             if (e == cudaSuccess) e = c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize();
@@ -1144,7 +1151,7 @@ scola_status autotune_deposit(scola_ctx *c) {
     c->deposit_split = all[pick].split;
     c->stats.deposit_form = all[pick].form == 0 ? SCOLA_DEPOSIT_SORTED : SCOLA_DEPOSIT_ATOMIC;
     c->stats.deposit_threads = all[pick].form == 0 ? all[pick].threads : 0;
-    c->stats.deposit_split = all[pick].split ? 1 : 0;
+    c->stats.deposit_split = all[pick].split;
     c->launches = launches;
     c->tuned = true;
     return SCOLA_OK;

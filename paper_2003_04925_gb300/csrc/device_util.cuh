@@ -16,35 +16,38 @@ __host__ __device__ inline long long shell_count(int Ng, int P) {
 
 // Padded coordinates (0..Ng+2P-1 per axis) of shell cell `idx`.  Enumeration: the 2P
 // full i-planes {0..P-1, Ng+P..Ng+2P-1}; then, for interior i, the 2P full j-rows; then,
-// for interior i and j, the 2P k-cells.
-__device__ inline void shell_coord(long long idx, int Ng, int P, int &pi, int &pj, int &pk) {
+// for interior i and j, the 2P k-cells.  (32-bit arithmetic: a shell of Ng <= 256, P <= 6
+// has fewer than 2^22 cells.)
+__device__ inline void shell_coord(long long idx64, int Ng, int P, int &pi, int &pj, int &pk) {
+    int idx = (int)idx64;
     const int S = Ng + 2 * P;
-    const long long plane = (long long)S * S;
-    const long long A = 2LL * P * plane;
+    const int plane = S * S;
+    const int A = 2 * P * plane;
     if (idx < A) {
-        const int q = (int)(idx / plane);
-        const long long r = idx - q * plane;
+        const int q = idx / plane;
+        const int r = idx - q * plane;
         pi = q < P ? q : Ng + q;
-        pj = (int)(r / S);
-        pk = (int)(r - (long long)pj * S);
+        pj = r / S;
+        pk = r - pj * S;
         return;
     }
     idx -= A;
-    const long long rowblk = 2LL * P * S;
-    const long long B = (long long)Ng * rowblk;
+    const int rowblk = 2 * P * S;
+    const int B = Ng * rowblk;
     if (idx < B) {
-        pi = P + (int)(idx / rowblk);
-        const int r = (int)(idx % rowblk);
+        pi = P + idx / rowblk;
+        const int r = idx - (pi - P) * rowblk;
         const int q = r / S;
         pj = q < P ? q : Ng + q;
         pk = r - q * S;
         return;
     }
     idx -= B;
-    pi = P + (int)(idx / (2LL * P * Ng));
-    const int r = (int)(idx % (2LL * P * Ng));
+    const int line = 2 * P * Ng;
+    pi = P + idx / line;
+    const int r = idx - (pi - P) * line;
     pj = P + r / (2 * P);
-    const int q = r % (2 * P);
+    const int q = r - (pj - P) * (2 * P);
     pk = q < P ? q : Ng + q;
 }
 
@@ -189,8 +192,9 @@ __device__ __forceinline__ void shell_stencil(const BoxDesc &B, const int pc[3],
     }
 }
 
-// The same stencil with the offsets in FP64: r / den is exact to FP64 rounding (one division of
-// two exact integers), for the FP64 accumulation of the C.3 shell.
+// The same stencil with the offsets in FP64, for the FP64 accumulation of the C.3 shell: the
+// exact integer r times the box's FP64 reciprocal of den (two FP64 roundings, far below the
+// FP32 rounding of the result; FP64 division is slow on this GPU).
 __device__ __forceinline__ void shell_stencil_d(const BoxDesc &B, const int pc[3], int Ntile, int i0[3],
                                                 double f[3]) {
     const int t[3] = {B.tx, B.ty, B.tz};
@@ -204,7 +208,7 @@ __device__ __forceinline__ void shell_stencil_d(const BoxDesc &B, const int pc[3
             --q;
         }
         i0[a] = t[a] * Ntile - B.Nbuf + q;
-        f[a] = (double)r / (double)den;
+        f[a] = (double)r * B.inv_2ng_d;
     }
 }
 

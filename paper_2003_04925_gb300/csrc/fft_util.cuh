@@ -15,6 +15,9 @@
 
 #include <cuda_runtime.h>
 
+#include <cmath>
+#include <vector>
+
 namespace scola {
 namespace fft {
 
@@ -114,11 +117,32 @@ __device__ __forceinline__ void dft(float2 *v) {
     if constexpr (Q == 16) dft16<SIGN>(v);
 }
 
+// Twiddles of a radix-16 stage after sub-transforms of length 16 (the same for every L):
+// w256[16 i + k] = exp(-2 pi i i k / 256), i, k < 16; thread k reads w256[16 i + k], a
+// contiguous run, where tw[i k L / 256] would be a stride-i (bank-conflicted) one.
+constexpr int kW256 = 256;
+
+// Whether a transform of length 2^logL reads tw at all: a radix-16 stage after sub-transforms
+// of 256, or a last radix-2/4/8 stage after a radix-16 one (the first stage has no twiddles,
+// the second radix-16 stage reads w256).
+__host__ __device__ constexpr bool needs_tw(int logL) { return logL / 4 >= 3 || (logL % 4 != 0 && logL / 4 >= 1); }
+
+// The w256 table (host, FP64 then rounded): 512 floats, re/im interleaved.
+inline void append_w256(std::vector<float> &arena) {
+    for (int i = 0; i < 16; ++i)
+        for (int k = 0; k < 16; ++k) {
+            const double a = -2.0 * 3.14159265358979323846 * (double)(i * k) / 256.0;
+            arena.push_back((float)std::cos(a));
+            arena.push_back((float)std::sin(a));
+        }
+}
+
 // One Stockham stage of radix Q over `rows` rows of length L = 2^logL, after sub-transforms
 // of length m: input element n of row r comes from load(r, n), output goes to the padded row
-// r of dst (row stride padded(L)).  tw[e] = exp(-2 pi i e / L), e < L.
+// r of dst (row stride padded(L)).  tw[e] = exp(-2 pi i e / L), e < L; w256 as above.
 template <int Q, int SIGN, class Load>
-__device__ __forceinline__ void stage(Load load, float2 *dst, int rows, int logL, int m, const float2 *tw) {
+__device__ __forceinline__ void stage(Load load, float2 *dst, int rows, int logL, int m, const float2 *tw,
+                                      const float2 *w256) {
     constexpr int logQ = Q == 2 ? 1 : Q == 4 ? 2 : Q == 8 ? 3 : 4;
     const int L = 1 << logL, nb = L >> logQ, lognb = logL - logQ;
     const int Ls = row_stride(L);
@@ -131,9 +155,10 @@ __device__ __forceinline__ void stage(Load load, float2 *dst, int rows, int logL
 #pragma unroll
         for (int i = 0; i < Q; ++i) v[i] = load(r, j + i * nb);
         if (m > 1) {
+            const bool w16 = Q == 16 && m == 16;
 #pragma unroll
             for (int i = 1; i < Q; ++i) {
-                float2 t = tw[i * k * step];
+                float2 t = w16 ? w256[16 * i + k] : tw[i * k * step];
                 if (SIGN > 0) t.y = -t.y;
                 v[i] = cmul(v[i], t);
             }
@@ -156,7 +181,7 @@ struct NoHook {
 // (whatever first read is free from then on).  logL >= 1.
 template <int SIGN, class Load, class Hook = NoHook>
 __device__ float2 *transform(Load first, float2 *dst, float2 *spare, int rows, int logL, const float2 *tw,
-                             Hook after_first = Hook()) {
+                             const float2 *w256, Hook after_first = Hook()) {
     const int Ls = row_stride(1 << logL);
     auto from = [&](const float2 *src) {
         return [src, Ls](int r, int n) { return src[r * Ls + pad(n)]; };
@@ -165,8 +190,8 @@ __device__ float2 *transform(Load first, float2 *dst, float2 *spare, int rows, i
     float2 *a = dst, *b = spare;      // a: the next stage's output
     bool started = false;
     while (left >= 4) {
-        if (!started) stage<16, SIGN>(first, a, rows, logL, m, tw);
-        else stage<16, SIGN>(from(b), a, rows, logL, m, tw);
+        if (!started) stage<16, SIGN>(first, a, rows, logL, m, tw, w256);
+        else stage<16, SIGN>(from(b), a, rows, logL, m, tw, w256);
         __syncthreads();
         if (!started) after_first();
         started = true;
@@ -178,13 +203,13 @@ __device__ float2 *transform(Load first, float2 *dst, float2 *spare, int rows, i
     }
     if (left > 0) {
         if (!started) {
-            if (left == 1) stage<2, SIGN>(first, a, rows, logL, m, tw);
-            if (left == 2) stage<4, SIGN>(first, a, rows, logL, m, tw);
-            if (left == 3) stage<8, SIGN>(first, a, rows, logL, m, tw);
+            if (left == 1) stage<2, SIGN>(first, a, rows, logL, m, tw, w256);
+            if (left == 2) stage<4, SIGN>(first, a, rows, logL, m, tw, w256);
+            if (left == 3) stage<8, SIGN>(first, a, rows, logL, m, tw, w256);
         } else {
-            if (left == 1) stage<2, SIGN>(from(b), a, rows, logL, m, tw);
-            if (left == 2) stage<4, SIGN>(from(b), a, rows, logL, m, tw);
-            if (left == 3) stage<8, SIGN>(from(b), a, rows, logL, m, tw);
+            if (left == 1) stage<2, SIGN>(from(b), a, rows, logL, m, tw, w256);
+            if (left == 2) stage<4, SIGN>(from(b), a, rows, logL, m, tw, w256);
+            if (left == 3) stage<8, SIGN>(from(b), a, rows, logL, m, tw, w256);
         }
         __syncthreads();
         if (!started) after_first();

@@ -45,6 +45,7 @@ struct BoxDesc {
     int gpad;                     // ghost layers per side of the padded potential: 2 N_ghost = FDA order
     int fda;                      // FDA order 2, 4, 6
     double dg_d, origin_d[3];     // FP64 box geometry (cell size, origin of the box frame)
+    double inv_2ng_d;             // 1 / (2 Ng) in FP64 (the C.3 shell stencil's offsets)
 };
 
 struct Chunk {                    // one CTA of a particle- or cell-parallel kernel
@@ -165,7 +166,8 @@ struct Ctx {
     // entries (one per box particle at most); the real bricks (box, brick in box)
     int deposit_form = 0;                             // 0: sorted bricks, 1: L2 fixed-point atomics
     int deposit_threads = 512;                        // threads per brick CTA of the sorted form
-    bool deposit_split = false;                       // sorted form: 32-bit halves of the counts
+    int deposit_split = 0;                            // sorted form's counters: 64-bit, 32-bit halves
+                                                      // with a carry (1), 16-bit halves reduced (2)
     bool tuned = false;                               // the autotuner has picked the forms above
     // per-tile final scale factors: per box of the bound batch and force evaluation k, the
     // FP32 coefficients [kF (forward, x D1), k1, k2, alpha, d1, d2, 1/D1, beta (adjoint kF)] at
@@ -197,6 +199,7 @@ struct Ctx {
     unsigned long long *tc_acc = nullptr;
     cufftComplex *tc_dk = nullptr, *tc_dk2 = nullptr;   // half-spectrum work grids (N^2 (N/2 + 1))
     long long tc_fft_tw_off = 0, tc_fft_w_off = 0, tc_fft_bk_off = 0;   // FFT tables in table_arena
+    long long fft_w256_off = 0;                       // the radix-16 second-stage twiddles (fft_util.cuh)
     float *rec_delta = nullptr, *rec_phi = nullptr;
 
     // adjoint (scola_set_checkpointing / scola_backward)

@@ -65,21 +65,25 @@ k_shell(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
     int i0[3];
     double f[3];
     shell_stencil_d(B, pc, Ntile, i0, f);
+    // the two periodic node indices per axis (one modulo each)
+    int ix[3][2];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        ix[a][0] = wrap(i0[a], N);
+        ix[a][1] = ix[a][0] + 1 == N ? 0 : ix[a][0] + 1;
+    }
     double sum = 0.0;
     const long long NN = (long long)N * N;
 #pragma unroll
     for (int dx = 0; dx < 2; ++dx) {
-        const long long ix = wrap(i0[0] + dx, N);
         const double wx = dx ? f[0] : 1.0 - f[0];
 #pragma unroll
         for (int dy = 0; dy < 2; ++dy) {
-            const long long iy = wrap(i0[1] + dy, N);
             const double wxy = wx * (dy ? f[1] : 1.0 - f[1]);
+            const float *row = phi1 + ix[0][dx] * NN + (long long)ix[1][dy] * N;
 #pragma unroll
-            for (int dz = 0; dz < 2; ++dz) {
-                const long long iz = wrap(i0[2] + dz, N);
-                sum = fma(wxy * (dz ? f[2] : 1.0 - f[2]), (double)phi1[ix * NN + iy * N + iz], sum);
-            }
+            for (int dz = 0; dz < 2; ++dz)
+                sum = fma(wxy * (dz ? f[2] : 1.0 - f[2]), (double)row[ix[2][dz]], sum);
         }
     }
     shell[B.sh_off + idx] = (float)sum;

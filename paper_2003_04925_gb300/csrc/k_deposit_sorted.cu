@@ -166,10 +166,22 @@ __device__ __forceinline__ void add_split(unsigned *lo, unsigned *hi, int c, uns
     if (old > 0xffffffffu - v) atomicAdd(hi + c, 1u);
 }
 
+// Adds fixed-point weight f (at most 2^32) as its low 16 bits and the rest (at most 2^16) to two
+// 32-bit counters with reductions that return nothing: the count is hi 2^16 + lo, exact while
+// a cell receives at most 65535 weights (a brick with at most 65535 entries).
+__device__ __forceinline__ void add_red16(unsigned *lo, unsigned *hi, int c, unsigned long long f) {
+    atomicAdd(lo + c, (unsigned)(f & 0xffffu));
+    atomicAdd(hi + c, (unsigned)(f >> 16));
+}
+
+// Counter modes of the brick pass: 64-bit atomics; 32-bit halves with a carry; 16-bit halves
+// with reductions (bricks with more than 65535 entries take the carry form).
+enum { kAcc64 = 0, kAccHalves = 1, kAccRed16 = 2 };
+
 // Adds the CIC weights of one entry (fractions v.xyz, packed lower cell v.w) that fall in the
 // brick [x0, x0 + 16) x [y0, ..) x [z0, ..) to its counters.  kFull: the brick lies inside
 // the mesh, so only the brick bounds need checking.
-template <bool kSplit, bool kFull>
+template <int kMode, bool kFull>
 __device__ __forceinline__ void deposit_entry(unsigned long long *acc, const float4 v, int x0, int y0, int z0,
                                               int Ng) {
     const int pk = __float_as_int(v.w);
@@ -190,9 +202,12 @@ __device__ __forceinline__ void deposit_entry(unsigned long long *acc, const flo
                 if ((unsigned)cz >= (unsigned)kBrick || (!kFull && z0 + cz >= Ng)) continue;
                 const unsigned long long f = weight_to_fixed(wxy * (ez ? v.z : 1.0f - v.z));
                 const int cell = (cx * kBrick + cy) * kBrick + cz;
-                if (kSplit) {
+                if (kMode == kAccHalves) {
                     unsigned *lo = reinterpret_cast<unsigned *>(acc);
                     add_split(lo, lo + kBrickCells, cell, f);
+                } else if (kMode == kAccRed16) {
+                    unsigned *lo = reinterpret_cast<unsigned *>(acc);
+                    add_red16(lo, lo + kBrickCells, cell, f);
                 } else {
                     atomicAdd(&acc[cell], f);
                 }
@@ -202,8 +217,8 @@ __device__ __forceinline__ void deposit_entry(unsigned long long *acc, const flo
 }
 
 // One CTA of T threads per real brick (item.start = brick index in the box, nb^3 of them).
-// kSplit: the counts as 32-bit low and high halves (32-bit atomics), else 64-bit atomics.
-template <int kBrickThreads, bool kSplit>
+// kMode: the counter form (kAcc64, kAccHalves, kAccRed16).
+template <int kBrickThreads, int kMode>
 __global__ void __launch_bounds__(kBrickThreads, kBrickThreads == 256 ? 6 : 3)
 k_sort_brick(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ items, const int *__restrict__ cnt,
              const int *__restrict__ offs, const float4 *__restrict__ entries, const float *__restrict__ phi_pad,
@@ -246,17 +261,24 @@ k_sort_brick(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ items,
     const int own = seg_start[8], total = seg_start[kSegments];
     const float4 *own_list = list + seg_o[0];
     const bool full = x0 + kBrick <= Ng && y0 + kBrick <= Ng && z0 + kBrick <= Ng;
+    // the 16-bit form needs at most 65535 weights per cell: bricks with more entries (uniform
+    // per CTA) take the carry form in the same counters
+    const bool red16 = kMode == kAccRed16 && total <= 65535;
+    auto deposit = [&](const float4 &v) {
+        if (kMode == kAccRed16 && !red16) {
+            if (full) deposit_entry<kAccHalves, true>(acc, v, x0, y0, z0, Ng);
+            else deposit_entry<kAccHalves, false>(acc, v, x0, y0, z0, Ng);
+        } else {
+            if (full) deposit_entry<kMode, true>(acc, v, x0, y0, z0, Ng);
+            else deposit_entry<kMode, false>(acc, v, x0, y0, z0, Ng);
+        }
+    };
     for (int e = tid; e < own; e += 2 * kBrickThreads) {
         const bool two = e + kBrickThreads < own;
         const float4 v0 = own_list[e];
         const float4 v1 = two ? own_list[e + kBrickThreads] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        if (full) {
-            deposit_entry<kSplit, true>(acc, v0, x0, y0, z0, Ng);
-            if (two) deposit_entry<kSplit, true>(acc, v1, x0, y0, z0, Ng);
-        } else {
-            deposit_entry<kSplit, false>(acc, v0, x0, y0, z0, Ng);
-            if (two) deposit_entry<kSplit, false>(acc, v1, x0, y0, z0, Ng);
-        }
+        deposit(v0);
+        if (two) deposit(v1);
     }
     for (int e = own + tid; e < total; e += kBrickThreads) {
         int lo = 8, hi = kSegments;              // seg_start[lo] <= e < seg_start[hi]
@@ -265,9 +287,7 @@ k_sort_brick(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ items,
             if (seg_start[mid] <= e) lo = mid;
             else hi = mid;
         }
-        const float4 v = list[seg_o[lo] + e - seg_start[lo]];
-        if (full) deposit_entry<kSplit, true>(acc, v, x0, y0, z0, Ng);
-        else deposit_entry<kSplit, false>(acc, v, x0, y0, z0, Ng);
+        deposit(list[seg_o[lo] + e - seg_start[lo]]);
     }
     __syncthreads();
     // cells: item q -> (x, y) row of the brick, 4 consecutive z cells
@@ -279,12 +299,13 @@ k_sort_brick(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ items,
         const int i = x0 + lx, j = y0 + ly, k = z0 + lz;
         if (i >= Ng || j >= Ng || k >= Ng) continue;
         ulonglong2 a01, a23;
-        if (kSplit) {
+        if (kMode != kAcc64) {
             const unsigned *lo = reinterpret_cast<const unsigned *>(acc) + (lx * kBrick + ly) * kBrick + lz;
             const uint4 l = *reinterpret_cast<const uint4 *>(lo);
             const uint4 h = *reinterpret_cast<const uint4 *>(lo + kBrickCells);
-            a01 = make_ulonglong2(((unsigned long long)h.x << 32) | l.x, ((unsigned long long)h.y << 32) | l.y);
-            a23 = make_ulonglong2(((unsigned long long)h.z << 32) | l.z, ((unsigned long long)h.w << 32) | l.w);
+            const int sh = red16 ? 16 : 32;
+            a01 = make_ulonglong2(((unsigned long long)h.x << sh) + l.x, ((unsigned long long)h.y << sh) + l.y);
+            a23 = make_ulonglong2(((unsigned long long)h.z << sh) + l.z, ((unsigned long long)h.w << sh) + l.w);
         } else {
             const ulonglong2 *a = reinterpret_cast<const ulonglong2 *>(acc + (lx * kBrick + ly) * kBrick + lz);
             a01 = a[0];
@@ -317,8 +338,9 @@ k_sort_brick(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ items,
 
 // Shared memory is the brick kernel's occupancy limit: ask for the largest carveout.
 cudaError_t init_deposit_kernels() {
-    const void *fns[] = {(const void *)k_sort_brick<256, false>, (const void *)k_sort_brick<512, false>,
-                         (const void *)k_sort_brick<256, true>, (const void *)k_sort_brick<512, true>};
+    const void *fns[] = {(const void *)k_sort_brick<256, kAcc64>, (const void *)k_sort_brick<512, kAcc64>,
+                         (const void *)k_sort_brick<256, kAccHalves>, (const void *)k_sort_brick<512, kAccHalves>,
+                         (const void *)k_sort_brick<256, kAccRed16>};
     for (const void *f : fns) {
         cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
                                              cudaSharedmemCarveoutMaxShared);
@@ -360,15 +382,16 @@ cudaError_t launch_deposit_sorted(Ctx &c, const float *s, long long stride, floa
     k_sort_bin<true><<<(c.n_pchunks + 1) / 2, kChunk, 0, c.stream>>>(c.boxes, c.pchunks, c.n_pchunks, s, stride,
                                                                      c.kcursor, c.sentries, c.kcount, c.koffs, c.dev_err);
     if ((e = cudaGetLastError()) != cudaSuccess) return step_error("sorted deposit: fill launch", e);
-#define SCOLA_BRICK(T, SPLIT)                                                                             \
-    k_sort_brick<T, SPLIT><<<c.n_sbricks, T, 0, c.stream>>>(c.boxes, c.sbricks, c.kcount, c.koffs, c.sentries, \
-                                                            c.phi, inv_D1, coef, kstep, c.coef_nk, c.work2, delta_out)
-    if (c.deposit_threads == 256) {
-        if (c.deposit_split) SCOLA_BRICK(256, true);
-        else SCOLA_BRICK(256, false);
+#define SCOLA_BRICK(T, MODE)                                                                              \
+    k_sort_brick<T, MODE><<<c.n_sbricks, T, 0, c.stream>>>(c.boxes, c.sbricks, c.kcount, c.koffs, c.sentries, \
+                                                           c.phi, inv_D1, coef, kstep, c.coef_nk, c.work2, delta_out)
+    if (c.deposit_split == kAccRed16) SCOLA_BRICK(256, kAccRed16);
+    else if (c.deposit_threads == 256) {
+        if (c.deposit_split == kAccHalves) SCOLA_BRICK(256, kAccHalves);
+        else SCOLA_BRICK(256, kAcc64);
     } else {
-        if (c.deposit_split) SCOLA_BRICK(512, true);
-        else SCOLA_BRICK(512, false);
+        if (c.deposit_split == kAccHalves) SCOLA_BRICK(512, kAccHalves);
+        else SCOLA_BRICK(512, kAcc64);
     }
 #undef SCOLA_BRICK
     if ((e = cudaGetLastError()) != cudaSuccess) return step_error("sorted deposit: brick launch", e);

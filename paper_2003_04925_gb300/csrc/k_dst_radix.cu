@@ -53,6 +53,7 @@ struct RxGroupArgs {
     const float2 *w;                // w_n, n < P
     const float2 *Bk;               // FFT_L(b)
     const float2 *tw;               // exp(-2 pi i j / L), j < L
+    const float2 *w256;             // the radix-16 second-stage twiddles
     const float *sn;                // sin(pi n / P), n < P
     const float *lam;               // Dirichlet eigenvalues, Ng
 };
@@ -71,8 +72,12 @@ using fft::cmulc;
 // shared-memory buffer of the R rows of one transform batch (padded rows, odd stride)
 int rx_buf(int L) { return (kRxSpan / L) * fft::row_stride(L); }
 
+// twiddles held in shared memory: L where a stage reads them, else none
+int rx_tw(int L) { return fft::needs_tw(31 - __builtin_clz((unsigned)L)) ? L : 0; }
+
 size_t rx_smem_bytes(int Ng, int P, int L) {
-    return sizeof(float2) * ((size_t)2 * rx_buf(L) + L + L + P) + sizeof(float) * ((size_t)P + Ng) + 16;
+    return sizeof(float2) * ((size_t)2 * rx_buf(L) + fft::kW256 + rx_tw(L) + L + P) + sizeof(float) * ((size_t)P + Ng) +
+           16;
 }
 
 template <int PASS>
@@ -86,14 +91,17 @@ __global__ void __launch_bounds__(kRxThreads, 3) k_dst_radix(const RxArgs A) {
     const int rows = 2 * R;                                // pencils per tile (a power of two)
     const int Ngs = Ng | 1;                                // odd row stride of the result rows
     const int Ls = fft::row_stride(L);                     // padded row stride of the transforms
+    const int ntw = fft::needs_tw(logL) ? L : 0;
     float2 *buf0 = reinterpret_cast<float2 *>(smem);
     float2 *buf1 = buf0 + R * Ls;
-    float2 *tw = buf1 + R * Ls;                            // L
-    float2 *Bk = tw + L;                                   // L
+    float2 *w256 = buf1 + R * Ls;                          // 256
+    float2 *tw = w256 + fft::kW256;                        // L where read, else none
+    float2 *Bk = tw + ntw;                                 // L
     float2 *w = Bk + L;                                    // P
     float *sn = reinterpret_cast<float *>(w + P);          // P
     float *lam = sn + P;                                   // Ng
-    for (int q = threadIdx.x; q < L; q += kRxThreads) tw[q] = G.tw[q];
+    for (int q = threadIdx.x; q < ntw; q += kRxThreads) tw[q] = G.tw[q];
+    for (int q = threadIdx.x; q < fft::kW256; q += kRxThreads) w256[q] = G.w256[q];
     for (int q = threadIdx.x; q < L; q += kRxThreads) Bk[q] = G.Bk[q];
     for (int q = threadIdx.x; q < P; q += kRxThreads) {
         w[q] = G.w[q];
@@ -131,12 +139,12 @@ __global__ void __launch_bounds__(kRxThreads, 3) k_dst_radix(const RxArgs A) {
             }
             return v;
         };
-        float2 *f = fft::transform<-1>(chirped, buf0, buf1, R, logL, tw);
+        float2 *f = fft::transform<-1>(chirped, buf0, buf1, R, logL, tw, w256);
         // inverse transform of its product with FFT_L(b)
         float2 *g = f == buf0 ? buf1 : buf0;
         const float2 *fc = f;
         auto product = [&](int pr, int n) { return cmul(fc[pr * Ls + fft::pad(n)], Bk[n]); };
-        f = fft::transform<+1>(product, g, f, R, logL, tw);
+        f = fft::transform<+1>(product, g, f, R, logL, tw, w256);
         // unpack the pairs: even outputs S_{2k} = -Im Y_k; odd increments R_k (R_0 / 2) placed
         // at the odd outputs' columns, summed below
         float *S = reinterpret_cast<float *>(f == buf0 ? buf1 : buf0);
@@ -269,6 +277,7 @@ cudaError_t run_rx_pass(Ctx &c, const float *in, float *out) {
             q.w = reinterpret_cast<const float2 *>(c.table_arena + G.w_off);
             q.Bk = reinterpret_cast<const float2 *>(c.table_arena + G.bk_off);
             q.tw = reinterpret_cast<const float2 *>(c.table_arena + G.tw_off);
+            q.w256 = reinterpret_cast<const float2 *>(c.table_arena + c.fft_w256_off);
             q.sn = c.table_arena + G.sn_off;
             q.lam = c.table_arena + G.lam_off;
             beg += n;

@@ -48,6 +48,7 @@ struct FtArgs {
     int *err;                 // bit 1 set if a staged copy's bounded wait expired
     float invL, inv_n3;
     const float2 *tw;         // exp(-2 pi i e / L), e < L
+    const float2 *w256;       // the radix-16 second-stage twiddles
     const float2 *w;          // Bluestein chirp w_n, n < N
     const float2 *Bk;         // Bluestein: DFT_L of the chirp kernel
     const float *lap;         // 1D FDA-2 symbol per index, N
@@ -64,14 +65,14 @@ using fft::cmulc;
 struct Rows {
     int N, L, logL, R, Ls, blue;
     float invL;
-    const float2 *tw, *w, *Bk;
+    const float2 *tw, *w, *Bk, *w256;
 };
 
 // DFT of R rows of length N (SIGN -1 forward, +1 inverse, unnormalised), x_n = load(r, n);
 // load may read `spare`, never `dst`.  Returns the buffer to read with row_get.
 template <int SIGN, class Load, class Hook = fft::NoHook>
 __device__ float2 *row_dft(const Rows &F, Load load, float2 *dst, float2 *spare, Hook after_first = Hook()) {
-    if (!F.blue) return fft::transform<SIGN>(load, dst, spare, F.R, F.logL, F.tw, after_first);
+    if (!F.blue) return fft::transform<SIGN>(load, dst, spare, F.R, F.logL, F.tw, F.w256, after_first);
     const float2 *w = F.w;
     const int N = F.N;
     auto chirped = [&](int r, int n) {
@@ -80,12 +81,12 @@ __device__ float2 *row_dft(const Rows &F, Load load, float2 *dst, float2 *spare,
         if (SIGN > 0) x.y = -x.y;
         return cmulc(x, w[n]);
     };
-    float2 *f = fft::transform<-1>(chirped, dst, spare, F.R, F.logL, F.tw, after_first);
+    float2 *f = fft::transform<-1>(chirped, dst, spare, F.R, F.logL, F.tw, F.w256, after_first);
     float2 *g = f == dst ? spare : dst;
     const float2 *fc = f, *Bk = F.Bk;
     const int Ls = F.Ls;
     auto product = [&](int r, int n) { return cmul(fc[r * Ls + fft::pad(n)], Bk[n]); };
-    return fft::transform<+1>(product, g, f, F.R, F.logL, F.tw);
+    return fft::transform<+1>(product, g, f, F.R, F.logL, F.tw, F.w256);
 }
 
 // Element k of row r of the DFT that row_dft left in res.
@@ -101,7 +102,7 @@ __device__ __forceinline__ float2 row_get(const Rows &F, const float2 *res, int 
 }
 
 size_t ft_smem_bytes(int N, int L) {
-    return 16 + kFtStage + sizeof(float2) * ((size_t)2 * kFtBuf + 2 * L + N) + sizeof(float) * N;
+    return 16 + kFtStage + sizeof(float2) * ((size_t)2 * kFtBuf + fft::kW256 + 2 * L + N) + sizeof(float) * N;
 }
 
 // Issue (warp 0) the bulk copies of tile t's input rows into st; their byte count arrives on bar.
@@ -159,10 +160,12 @@ __global__ void __launch_bounds__(kFtThreads, 2) k_tc_fft(const FtArgs A) {
     const float2 *stc = reinterpret_cast<const float2 *>(st);
     float2 *b0 = reinterpret_cast<float2 *>(st + kFtStage);
     float2 *b1 = b0 + kFtBuf;
-    float2 *tw = b1 + kFtBuf;        // L
+    float2 *w256 = b1 + kFtBuf;      // 256
+    float2 *tw = w256 + fft::kW256;  // L
     float2 *Bk = tw + L;             // L (Bluestein)
     float2 *w = Bk + L;              // N (Bluestein)
     float *lap = reinterpret_cast<float *>(w + N);
+    for (int q = threadIdx.x; q < fft::kW256; q += kFtThreads) w256[q] = A.w256[q];
     for (int q = threadIdx.x; q < L; q += kFtThreads) {
         tw[q] = A.tw[q];
         if (A.blue) Bk[q] = A.Bk[q];
@@ -183,6 +186,7 @@ __global__ void __launch_bounds__(kFtThreads, 2) k_tc_fft(const FtArgs A) {
     F.tw = tw;
     F.w = w;
     F.Bk = Bk;
+    F.w256 = w256;
     const int N2 = N * N, logR = __ffs(R) - 1;
     if (BULK) {
         if (threadIdx.x == 0) {
@@ -470,6 +474,7 @@ cudaError_t launch_tc_poisson(Ctx &c, const float *delta, float *phi) {
     a.invL = 1.0f / (float)a.L;
     a.inv_n3 = (float)(1.0 / (double)c.tc_n3);
     a.tw = reinterpret_cast<const float2 *>(c.table_arena + c.tc_fft_tw_off);
+    a.w256 = reinterpret_cast<const float2 *>(c.table_arena + c.fft_w256_off);
     a.w = reinterpret_cast<const float2 *>(c.table_arena + c.tc_fft_w_off);
     a.Bk = reinterpret_cast<const float2 *>(c.table_arena + c.tc_fft_bk_off);
     a.lap = c.table_arena + c.tc_lap_off;
