@@ -9,8 +9,8 @@
 // DFTs split into radix-4 and radix-2 butterflies with their twiddles as constants.
 //
 // Rows sit in shared memory with one pad slot per 16 complex values (index i -> i + i / 16),
-// which keeps the stride-16 accesses of the first stage free of bank conflicts, and an odd
-// row stride (row_stride), which keeps reads across rows (a transposed epilogue) free of them.
+// which keeps the stride-16 accesses of the first stage free of bank conflicts, at an odd row
+// stride (row_stride).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -23,9 +23,11 @@ namespace fft {
 
 __device__ __forceinline__ int pad(int i) { return i + (i >> 4); }
 __host__ __device__ constexpr int padded(int L) { return L + L / 16; }
-__host__ __device__ constexpr int row_stride(int L) { return padded(L) | 1; }
-// shared-memory complex values for R rows of length L (R L <= span, R <= max_rows)
-__host__ __device__ constexpr int rows_buffer(int span, int max_rows) { return padded(span) + max_rows; }
+// Row stride (complex values) of the rows of one transform batch: padded(L), made odd (a
+// stride that is a multiple of the bank count would put a column of consecutive rows in one
+// bank; strides tuned per access pattern measured no faster).  R, the rows per batch, is
+// kept in the signature for the callers' buffer sizing.
+__host__ __device__ constexpr int row_stride(int L, int R) { return (void)R, padded(L) | 1; }
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -145,7 +147,7 @@ __device__ __forceinline__ void stage(Load load, float2 *dst, int rows, int logL
                                       const float2 *w256) {
     constexpr int logQ = Q == 2 ? 1 : Q == 4 ? 2 : Q == 8 ? 3 : 4;
     const int L = 1 << logL, nb = L >> logQ, lognb = logL - logQ;
-    const int Ls = row_stride(L);
+    const int Ls = row_stride(L, rows);
     const int step = L / (m * Q);
     for (int q = threadIdx.x; q < rows * nb; q += blockDim.x) {
         const int r = q >> lognb, j = q & (nb - 1);
@@ -182,7 +184,7 @@ struct NoHook {
 template <int SIGN, class Load, class Hook = NoHook>
 __device__ float2 *transform(Load first, float2 *dst, float2 *spare, int rows, int logL, const float2 *tw,
                              const float2 *w256, Hook after_first = Hook()) {
-    const int Ls = row_stride(1 << logL);
+    const int Ls = row_stride(1 << logL, rows);
     auto from = [&](const float2 *src) {
         return [src, Ls](int r, int n) { return src[r * Ls + pad(n)]; };
     };

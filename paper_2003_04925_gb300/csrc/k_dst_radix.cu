@@ -70,7 +70,7 @@ using fft::cmul;
 using fft::cmulc;
 
 // shared-memory buffer of the R rows of one transform batch (padded rows, odd stride)
-int rx_buf(int L) { return (kRxSpan / L) * fft::row_stride(L); }
+int rx_buf(int L) { return (kRxSpan / L) * fft::row_stride(L, kRxSpan / L); }
 
 // twiddles held in shared memory: L where a stage reads them, else none
 int rx_tw(int L) { return fft::needs_tw(31 - __builtin_clz((unsigned)L)) ? L : 0; }
@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(kRxThreads, 3) k_dst_radix(const RxArgs A) {
     const int Ng = G.Ng, P = G.P, L = G.L, logL = G.logL, R = G.R;
     const int rows = 2 * R;                                // pencils per tile (a power of two)
     const int Ngs = Ng | 1;                                // odd row stride of the result rows
-    const int Ls = fft::row_stride(L);                     // padded row stride of the transforms
+    const int Ls = fft::row_stride(L, R);                  // padded row stride of the transforms
     const int ntw = fft::needs_tw(logL) ? L : 0;
     float2 *buf0 = reinterpret_cast<float2 *>(smem);
     float2 *buf1 = buf0 + R * Ls;

@@ -38,7 +38,6 @@ namespace {
 constexpr int kFtThreads = 256;
 constexpr int kFtSpan = 2048;                    // complex values per transform batch (R rows x L)
 constexpr int kFtMaxRows = 256;                  // R cap (tiny grids)
-constexpr int kFtBuf = fft::rows_buffer(kFtSpan, kFtMaxRows);
 constexpr int kFtStage = 20480;                  // staging bytes: the largest tile input (R <= 256)
 
 enum FtPass { FT_X_FWD = 1, FT_Y_FWD = 2, FT_Z_SOLVE = 3, FT_Y_INV = 4, FT_X_INV = 5 };
@@ -101,8 +100,12 @@ __device__ __forceinline__ float2 row_get(const Rows &F, const float2 *res, int 
     return X;
 }
 
+// rows per tile and the complex values of one shared-memory buffer of them
+int ft_rows(int L) { return std::min(kFtSpan / L, kFtMaxRows); }
+int ft_buf(int L) { return ft_rows(L) * fft::row_stride(L, ft_rows(L)); }
+
 size_t ft_smem_bytes(int N, int L) {
-    return 16 + kFtStage + sizeof(float2) * ((size_t)2 * kFtBuf + fft::kW256 + 2 * L + N) + sizeof(float) * N;
+    return 16 + kFtStage + sizeof(float2) * ((size_t)2 * ft_buf(L) + fft::kW256 + 2 * L + N) + sizeof(float) * N;
 }
 
 // Issue (warp 0) the bulk copies of tile t's input rows into st; their byte count arrives on bar.
@@ -158,9 +161,10 @@ __global__ void __launch_bounds__(kFtThreads, 2) k_tc_fft(const FtArgs A) {
     unsigned char *st = smem + 16;
     const float *stf = reinterpret_cast<const float *>(st);
     const float2 *stc = reinterpret_cast<const float2 *>(st);
+    const int Ls = fft::row_stride(L, R);
     float2 *b0 = reinterpret_cast<float2 *>(st + kFtStage);
-    float2 *b1 = b0 + kFtBuf;
-    float2 *w256 = b1 + kFtBuf;      // 256
+    float2 *b1 = b0 + R * Ls;
+    float2 *w256 = b1 + R * Ls;      // 256
     float2 *tw = w256 + fft::kW256;  // L
     float2 *Bk = tw + L;             // L (Bluestein)
     float2 *w = Bk + L;              // N (Bluestein)
@@ -180,7 +184,7 @@ __global__ void __launch_bounds__(kFtThreads, 2) k_tc_fft(const FtArgs A) {
     F.L = L;
     F.logL = A.logL;
     F.R = R;
-    F.Ls = fft::row_stride(L);
+    F.Ls = Ls;
     F.blue = A.blue;
     F.invL = A.invL;
     F.tw = tw;
@@ -385,7 +389,7 @@ void tc_fft_plan(int N, int &L, int &logL, int &R, bool &blue) {
         L <<= 1;
         ++logL;
     }
-    R = std::min(kFtSpan / L, kFtMaxRows);
+    R = ft_rows(L);
 }
 
 bool tc_fft_supported(int N) {
