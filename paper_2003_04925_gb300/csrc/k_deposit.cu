@@ -19,6 +19,11 @@ namespace scola {
 
 namespace {
 
+// Consecutive lanes hold Lagrangian neighbours along z (k fastest).  Where a lane's lower
+// CIC corner is its left neighbour's lower corner moved one cell up in z (the common case on
+// meshes of one cell per particle spacing), the neighbour's four upper-z weights fall on this
+// lane's four lower-z cells: the lane adds them to its own (integer sums: the same totals)
+// and the neighbour skips those atomics.
 __global__ void __launch_bounds__(kChunk)
 k_deposit(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks, const float *__restrict__ s,
           long long stride, unsigned long long *__restrict__ acc, long long acc_base) {
@@ -26,37 +31,61 @@ k_deposit(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks, c
     const BoxDesc &B = boxes[ch.box];
     const int Nsc = B.Nsc, Ng = B.Ng;
     const int local = ch.start + threadIdx.x;
-    if (local >= Nsc * Nsc * Nsc) return;
-    const long long gi = B.p_off + local;
-    int b[3];
-    decode_local(local, Nsc, b[0], b[1], b[2]);
-    int i0[3];
-    float f[3];
+    const bool valid = local < Nsc * Nsc * Nsc;       // (every lane takes part in the shuffles)
+    int i0[3] = {-1000, -1000, -1000};
+    float f[3] = {0.f, 0.f, 0.f};
+    if (valid) {
+        const long long gi = B.p_off + local;
+        int b[3];
+        decode_local(local, Nsc, b[0], b[1], b[2]);
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        float u = fmaf(__ldg(s + a * stride + gi), B.inv_dg, fmaf((float)b[a], B.q2u, 0.5f * B.q2u - 0.5f));
-        u = fminf(fmaxf(u, -2.0f), (float)Ng + 1.0f);
-        const float fl = floorf(u);
-        i0[a] = (int)fl;
-        f[a] = u - fl;
+        for (int a = 0; a < 3; ++a) {
+            float u = fmaf(__ldg(s + a * stride + gi), B.inv_dg, fmaf((float)b[a], B.q2u, 0.5f * B.q2u - 0.5f));
+            u = fminf(fmaxf(u, -2.0f), (float)Ng + 1.0f);
+            const float fl = floorf(u);
+            i0[a] = (int)fl;
+            f[a] = u - fl;
+        }
     }
+    // fixed-point weights of the eight corners
+    unsigned long long w[2][2][2];
+#pragma unroll
+    for (int dx = 0; dx < 2; ++dx) {
+        const float wx = dx ? f[0] : 1.0f - f[0];
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy) {
+            const float wxy = wx * (dy ? f[1] : 1.0f - f[1]);
+#pragma unroll
+            for (int dz = 0; dz < 2; ++dz) w[dx][dy][dz] = valid ? weight_to_fixed(wxy * (dz ? f[2] : 1.0f - f[2])) : 0ull;
+        }
+    }
+    const int lane = threadIdx.x & 31;
+    const int px = __shfl_up_sync(0xffffffffu, i0[0], 1), py = __shfl_up_sync(0xffffffffu, i0[1], 1),
+              pz = __shfl_up_sync(0xffffffffu, i0[2], 1);
+    const bool take = valid && lane > 0 && px == i0[0] && py == i0[1] && pz + 1 == i0[2];
+    const bool give = __shfl_down_sync(0xffffffffu, take ? 1 : 0, 1) && lane < 31;
+#pragma unroll
+    for (int dx = 0; dx < 2; ++dx)
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy) {
+            const unsigned long long up = __shfl_up_sync(0xffffffffu, w[dx][dy][1], 1);
+            if (take) w[dx][dy][0] += up;
+        }
+    if (!valid) return;
     unsigned long long *base = acc + (B.m_off - acc_base);
 #pragma unroll
     for (int dx = 0; dx < 2; ++dx) {
         const int cx = i0[0] + dx;
         if ((unsigned)cx >= (unsigned)Ng) continue;
-        const float wx = dx ? f[0] : 1.0f - f[0];
 #pragma unroll
         for (int dy = 0; dy < 2; ++dy) {
             const int cy = i0[1] + dy;
             if ((unsigned)cy >= (unsigned)Ng) continue;
-            const float wxy = wx * (dy ? f[1] : 1.0f - f[1]);
 #pragma unroll
             for (int dz = 0; dz < 2; ++dz) {
                 const int cz = i0[2] + dz;
-                if ((unsigned)cz >= (unsigned)Ng) continue;
-                const float w = wxy * (dz ? f[2] : 1.0f - f[2]);
-                atomicAdd(base + ((long long)cx * Ng + cy) * Ng + cz, weight_to_fixed(w));
+                if ((unsigned)cz >= (unsigned)Ng || (dz == 1 && give)) continue;
+                atomicAdd(base + ((long long)cx * Ng + cy) * Ng + cz, w[dx][dy][dz]);
             }
         }
     }
