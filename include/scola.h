@@ -53,7 +53,9 @@ typedef enum scola_status {
 
 typedef enum scola_dst_variant {
     SCOLA_DST_SIMT = 0,          /* dense sine-matrix pencils on FP32 CUDA cores */
-    SCOLA_DST_TC_3XTF32 = 1,     /* the same products on tcgen05 tensor cores, 3xTF32 split */
+    SCOLA_DST_TC_3XTF32 = 1,     /* the same products on tcgen05 tensor cores, 3xTF32 split;
+                                    every 2 <= Ng <= 240 (the sine matrix resident in shared
+                                    memory, folded by its mirror symmetry for Ng > 128) */
     SCOLA_DST_TC_4XTF32 = 3,     /* as 1, plus the lo x lo product (four TF32 products) */
     SCOLA_DST_TC_3PASS = 4,      /* the 3xTF32 products in three mesh passes instead of six: z
                                     forward; every z-frequency plane transformed along y and x,
@@ -62,13 +64,14 @@ typedef enum scola_dst_variant {
     SCOLA_DST_RADIX = 5,         /* fast sine transforms on FP32 CUDA cores, O(Ng log Ng) per
                                     pencil: each DST-I of length Ng from a real DFT of length
                                     Ng + 1 (two pencils per complex transform), done by
-                                    Bluestein's chirp convolution with radix-2 FFTs of a power-of-two
+                                    Bluestein's chirp convolution with radix-16 FFTs of a power-of-two
                                     length in shared memory; every 1 <= Ng <= 256 */
     SCOLA_DST_AUTO = 2           /* the fastest of the tensor-core forms (six passes, and three
                                     where every Ng allows it), the dense FP32 form and the radix
                                     form, timed once on the context's boxes before the first
                                     evolution (where Ng > 222 excludes the dense FP32 form: the
-                                    six-pass tensor-core form alone) */
+                                    six-pass tensor-core form alone; where Ng > 240 excludes the
+                                    tensor cores: the radix form) */
 } scola_dst_variant;
 
 typedef enum scola_deposit_form {

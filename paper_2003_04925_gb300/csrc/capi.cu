@@ -149,18 +149,20 @@ scola_status validate(const scola_params *p, std::vector<int32_t> &bufs, std::ve
         const int ng = p->Ng ? p->Ng : p->mesh_ratio * nsc;
         if (ng < nsc) return invalid("Ng must be >= Np,sCOLA (Sec. 3.3, C.3)");
         const bool tc_form = p->dst_variant == SCOLA_DST_TC_3XTF32 || p->dst_variant == SCOLA_DST_TC_4XTF32 ||
-                             p->dst_variant == SCOLA_DST_TC_3PASS || p->dst_variant == SCOLA_DST_AUTO;
+                             p->dst_variant == SCOLA_DST_TC_3PASS;
         const bool rx_form = p->dst_variant == SCOLA_DST_RADIX;
-        if (for_kernels && (ng > kMaxNg || (!tc_form && !rx_form && ng > kMaxNgSimt))) {
-            set_error("Ng > 256 is not built (Ng > 222 only with a tensor-core or radix DST form)");
+        const bool auto_form = p->dst_variant == SCOLA_DST_AUTO;
+        if (for_kernels && (ng > kMaxNg || (!tc_form && !rx_form && !auto_form && ng > kMaxNgSimt))) {
+            set_error("Ng > 256 is not built (Ng > 222 only with a tensor-core, radix or automatic DST form)");
             return SCOLA_ERR_UNSUPPORTED;
         }
-        if (for_kernels && rx_form && !rx_supported(ng)) {
+        if (for_kernels && (rx_form || auto_form) && !rx_supported(ng) && !tc_supported(ng)) {
             set_error("the radix DST needs 1 <= Ng <= 256");
             return SCOLA_ERR_UNSUPPORTED;
         }
         if (for_kernels && tc_form && !tc_supported(ng)) {
-            set_error("the tensor-core DST needs 2 <= Ng <= 256");
+            set_error("the tensor-core DST needs 2 <= Ng <= 240 (its sine matrix and two data stages in 227 KB of "
+                      "shared memory)");
             return SCOLA_ERR_UNSUPPORTED;
         }
         geo[b] = {nsc, ng, bufs[b]};
@@ -677,9 +679,10 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &all_geo) {
     // tensor-core DST groups (one per distinct Ng): the FP32 sine matrix
     bool all_tc = true;
     for (auto &kv : c->tbl_of) all_tc = all_tc && tc_supported(kv.first);
-    // AUTO: both forms are set up where every Ng allows the tensor-core form, and the
-    // autotuner keeps the faster (autotune_dst); the FP32 form otherwise
-    // (a mesh larger than the FP32 form takes leaves the tensor-core form alone)
+    // AUTO: the forms are set up where every Ng allows the tensor-core form, and the
+    // autotuner keeps the fastest (autotune_dst); a mesh larger than the FP32 form takes
+    // leaves the tensor-core form alone, one larger than the tensor-core form takes the radix
+    // form
     c->dst_auto = p.dst_variant == SCOLA_DST_AUTO && all_tc && c->max_ng <= kMaxNgSimt;
     c->use_tc = (p.dst_variant == SCOLA_DST_TC_3XTF32) || (p.dst_variant == SCOLA_DST_TC_4XTF32) ||
                 (p.dst_variant == SCOLA_DST_TC_3PASS) || (p.dst_variant == SCOLA_DST_AUTO && all_tc);
@@ -696,7 +699,8 @@ scola_status build(scola_ctx *c, const std::vector<BoxGeom> &all_geo) {
     // the radix form: requested, or one more autotuner candidate where every Ng allows it
     bool all_rx = true;
     for (auto &kv : c->tbl_of) all_rx = all_rx && rx_supported(kv.first);
-    c->rx = p.dst_variant == SCOLA_DST_RADIX;
+    // (AUTO where some Ng exceeds the tensor-core form's 240: the radix form, which takes 256)
+    c->rx = p.dst_variant == SCOLA_DST_RADIX || (p.dst_variant == SCOLA_DST_AUTO && !all_tc && all_rx);
     c->rx_ok = c->rx || (c->dst_auto && all_rx);
     if (c->rx_ok)
         for (auto &kv : c->tbl_of) {

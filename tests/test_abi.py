@@ -84,6 +84,22 @@ def test_validation_errors_without_gpu(lib):
         lib.scola_tiling_info(ok)
 
 
+def test_mesh_size_limits_are_refused_before_any_device_work(lib):
+    # scola_create validates the problem (with the kernels' mesh limits) before touching the
+    # device: the largest meshes each Poisson form takes, and one past them
+    one_box = dict(L=100.0, Ntiles=1, Nbuf=0, mesh_ratio=1)
+    cases = [(dict(one_box, Np=222, Ng=223, dst_variant=lib.SCOLA_DST_SIMT), 2),     # dense FP32: Ng <= 222
+             (dict(one_box, Np=241, Ng=241, dst_variant=lib.SCOLA_DST_TC_3XTF32), 2),   # tensor cores: <= 240
+             (dict(one_box, Np=256, Ng=257, dst_variant=lib.SCOLA_DST_TC_3XTF32), 2),
+             (dict(one_box, Np=256, Ng=257, dst_variant=lib.SCOLA_DST_RADIX), 2),
+             (dict(one_box, Np=256, Ng=257, dst_variant=lib.SCOLA_DST_AUTO), 2),
+             (dict(one_box, Np=32, Ng=20), 1)]                                       # Ng < Np,sCOLA
+    for kw, status in cases:
+        with pytest.raises(lib.ScolaError) as e:
+            lib.scola_create(lib.make_params(**kw))
+        assert e.value.status == status, kw
+
+
 def test_struct_layout_matches_header(lib, tmp_path):
     """Field offsets and sizes of the ctypes structures equal those a C compiler gives the
     header's structures."""

@@ -67,7 +67,7 @@ CASES_PM = {
 
 def _sim(kw, variant="simt"):
     code = {"simt": sc.SCOLA_DST_SIMT, "tc": sc.SCOLA_DST_TC_3XTF32, "tc4": sc.SCOLA_DST_TC_4XTF32,
-            "tc3": sc.SCOLA_DST_TC_3PASS, "radix": sc.SCOLA_DST_RADIX}[variant]
+            "tc3": sc.SCOLA_DST_TC_3PASS, "radix": sc.SCOLA_DST_RADIX, "auto": sc.SCOLA_DST_AUTO}[variant]
     return sc.Scola(**dict(lib_kwargs(kw), dst_variant=code))
 
 
@@ -123,13 +123,28 @@ def test_pm_force_matches_oracle(name, variant):
     # (mass drop in the deposit, clamping in the interpolation).
     kw = CASES_PM[name]
     _skip_unsupported(kw, variant)
+    _check_pm_force(kw, variant, name == "plain_32")
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("variant", ["tc", "radix", "auto"])
+def test_largest_mesh_force_matches_oracle(variant):
+    # The largest meshes: Ng = 240 for the tensor-core (folded) form, 256 for the radix form
+    # and for the autotuner, which takes the radix form there (the dense FP32 form stops at
+    # 222): one box at 2:1, with the same checks
+    np_ = 120 if variant == "tc" else 128
+    kw = dict(L=float(np_), Np=np_, Ntiles=1, Nbuf=0, mesh_ratio=2, nsteps=1, a_i=0.05, a_f=1.0)
+    _check_pm_force(kw, variant, False)
+
+
+def _check_pm_force(kw, variant, expect_drop):
     cfg = oracle_cfg(kw)
     w, f, sched = oracle_fields(kw)
     sim = _sim(kw, variant)
     assert sc.scola_uses_tensor_cores(sim.ctx) == variant.startswith("tc")
     sim.lpt_fields(_to_dev(w))
     sim.setup_boxes()
-    if variant == "radix":
+    if variant == "radix" or (variant == "auto" and max(_mesh_sizes(kw)) > 240):
         assert sim.stats()["dst_form"] == sc.SCOLA_DST_RADIX
     D1 = 0.73
     s_all, refs = [], []
@@ -173,7 +188,7 @@ def test_pm_force_matches_oracle(name, variant):
     for b, (g, r) in enumerate(refs):
         assert abs(dep[b] - r["deposited"]) <= 1e-6 * g.Nsc**3, (b, dep[b], r["deposited"])
         assert abs(int(esc[b]) - int(r["clamped"].sum())) <= 1, (b, esc[b], r["clamped"].sum())
-    if name == "plain_32":
+    if expect_drop:
         assert any(r["deposited"] < g.Nsc**3 - 1.0 for g, r in refs) and esc.sum() > 0
     sc.scola_device_status(sim.ctx)
     sim.close()
