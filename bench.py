@@ -479,13 +479,14 @@ def measured_traffic(workload, dst):
 
 def per_tile_cost(sc, torch, kw, w, x, p, ms_batched, steps, world):
     """The plain per-tile form (one box per launch, boxes in turn) on the same input, with the
-    tensor-core solve the batched form uses and with the FP32 CUDA-core solve (the plain
-    per-tile FP32 GPU path); both give results bit-identical to their batched forms."""
+    Poisson form the batched run uses, with the dense FP32 CUDA-core solve (the plain per-tile
+    FP32 GPU path) and with the radix FP32 solve; each gives results bit-identical to its
+    batched form (checked for the batched run's own form)."""
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     out = {}
     work = particle_steps_per_run(kw)
-    for tag, dst in (("tc", kw["dst_variant"]), ("fp32", sc.SCOLA_DST_SIMT)):
+    for tag, dst in (("tc", kw["dst_variant"]), ("fp32", sc.SCOLA_DST_SIMT), ("radix", sc.SCOLA_DST_RADIX)):
         pt = sc.Scola(**dict(kw, batch_mode=sc.SCOLA_BATCH_PER_TILE, dst_variant=dst))
         xp, pp = torch.empty_like(x), torch.empty_like(p)
         pt.forward(w, xp, pp)

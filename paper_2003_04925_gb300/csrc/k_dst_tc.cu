@@ -80,7 +80,6 @@ constexpr int kTN = kTcTileRows;     // MMA N: data rows per tile (256)
 constexpr int kKA = 32;              // K per sine-matrix chunk (one 128-byte swizzle row of FP32)
 constexpr int kKB = 16;              // K per data chunk (one 64-byte swizzle row of FP32)
 constexpr int kHalfBytes = kTN * 64; // one data chunk, hi or lo (16 KB)
-constexpr int kStageBytes = 2 * kHalfBytes;
 constexpr int kThreads = 576;        // 8 epilogue, 8 converter, 1 MMA, 1 TMA warps
 constexpr int kProducers = 256;      // converter threads; each splits kHalfBytes / 16 / kProducers units per chunk
 constexpr int kUnits = kHalfBytes / 16 / kProducers;
