@@ -226,6 +226,11 @@ typedef struct scola_stats {
     double ms_dst_candidates[4];  /* AUTO: autotuner timings of one Poisson solve: tensor cores
                                      in six passes, dense FP32, tensor cores in three passes,
                                      radix FP32; 0 = not timed */
+    int32_t adjoint_potentials_kept; /* 1: with checkpoints at every force evaluation the
+                                     forward run also keeps each evaluation's padded potential
+                                     (they fit half of the free device memory), and the
+                                     backward pass restores it instead of recomputing the
+                                     deposit and the Poisson solve */
 } scola_stats;
 
 /*

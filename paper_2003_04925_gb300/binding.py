@@ -59,7 +59,7 @@ class ScolaStats(ctypes.Structure):
         ("ms_lpt", c_double), ("ms_evolve", c_double), ("kernel_launches", c_int64),
         ("deposit_form", c_int32), ("deposit_threads", c_int32), ("deposit_split", c_int32),
         ("ms_deposit_candidates", c_double * 5), ("batches", c_int32), ("batch_boxes", c_int32),
-        ("ms_tcola", c_double), ("dst_form", c_int32), ("ms_dst_candidates", c_double * 4),
+        ("ms_tcola", c_double), ("dst_form", c_int32), ("ms_dst_candidates", c_double * 4), ("adjoint_potentials_kept", c_int32),
     ]
 
 

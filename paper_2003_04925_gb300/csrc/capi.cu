@@ -1284,6 +1284,9 @@ scola_status enqueue_evolution(scola_ctx *c) {
         } else {
             CK(launch_poisson(*c));
         }
+        if (c->checkpointing && c->ckpt_phi && c->ckpt_every == 1)
+            CK(cudaMemcpyAsync(c->ckpt_phi + (size_t)k * c->MP, c->phi, sizeof(float) * (size_t)c->MP,
+                               cudaMemcpyDeviceToDevice, c->stream));
         CK(launch_kick_drift(*c, forward_kick(c->tt, k), fused, k));
         CK(mark());
     }
@@ -1328,6 +1331,13 @@ scola_status alloc_checkpoints(scola_ctx *c) {
     if (!c->ckpt) CS(dev_alloc(&c->ckpt, m == 1 ? 3LL * n1 * P : 6LL * ((n1 - 1) / m + 1) * P));
     if (m > 1 && !c->seg) CS(dev_alloc(&c->seg, 3LL * m * P));
     if (m > 1 && !c->fin) CS(dev_alloc(&c->fin, 6 * P));
+    if (m == 1 && !c->ckpt_phi) {
+        size_t free_b = 0, total_b = 0;
+        CK(cudaMemGetInfo(&free_b, &total_b));
+        const size_t need = sizeof(float) * (size_t)n1 * (size_t)c->cap_MP;
+        if (need <= free_b / 2) CS(dev_alloc(&c->ckpt_phi, (long long)n1 * c->cap_MP));
+    }
+    c->stats.adjoint_potentials_kept = c->ckpt_phi ? 1 : 0;
     return SCOLA_OK;
 }
 
@@ -1468,7 +1478,7 @@ void scola_destroy(scola_ctx *c) {
         cufftDestroy(c->plan_c2r);
     }
     void *ptrs[] = {c->boxes, c->all_boxes, c->all_coef, c->all_coefL, c->coef, c->coefL, c->tables, c->table_arena, c->pchunks, c->tchunks, c->shchunks,
-                    c->zitems, c->citems, c->mchunks, c->ppchunks, c->tc_tiles, c->tc_planes, c->rx_tiles, c->dev_err, c->ckpt, c->seg, c->fin,
+                    c->zitems, c->citems, c->mchunks, c->ppchunks, c->tc_tiles, c->tc_planes, c->rx_tiles, c->dev_err, c->ckpt, c->ckpt_phi, c->seg, c->fin,
                     c->adj, c->lamG, c->lam_phi_pad, c->adj_in, c->adj_out, c->lam_shell, c->lamPsi1,
                     c->lamPsi2, c->lam_phi1, c->lam_phi2, c->d2, c->lam_d2, c->part, c->dep_acc, c->kcount,
                     c->koffs, c->kcursor, c->sentries, c->sbricks,
@@ -1702,11 +1712,12 @@ scola_status scola_set_checkpoint_interval(scola_ctx *c, int32_t every) {
     }
     c->ckpt_every = m;
     c->have_forward = false;
-    for (float **q : {&c->ckpt, &c->seg, &c->fin})
+    for (float **q : {&c->ckpt, &c->seg, &c->fin, &c->ckpt_phi})
         if (*q) {
             CK(cudaFree(*q));
             *q = nullptr;
         }
+    c->stats.adjoint_potentials_kept = 0;
     if (c->checkpointing) CS(alloc_checkpoints(c));
     return SCOLA_OK;
 }
@@ -1754,8 +1765,13 @@ scola_status backward_clear_batch(scola_ctx *c) {
 scola_status reverse_step(scola_ctx *c, int k, const float *sk) {
     const long long P = c->P;
     CK(launch_adj_kick_drift(*c, c->adj, kick_drift_coefficients(c->tt, k), k));
-    CK(launch_deposit(*c, sk, P, (float)(1.0 / c->tt.D1[k]), nullptr, false, k));
-    CK(launch_poisson(*c));
+    if (c->ckpt_phi && c->ckpt_every == 1) {       // the potential the forward run kept
+        CK(cudaMemcpyAsync(c->phi, c->ckpt_phi + (size_t)k * c->MP, sizeof(float) * (size_t)c->MP,
+                           cudaMemcpyDeviceToDevice, c->stream));
+    } else {
+        CK(launch_deposit(*c, sk, P, (float)(1.0 / c->tt.D1[k]), nullptr, false, k));
+        CK(launch_poisson(*c));
+    }
     CK(cudaMemsetAsync(c->lamG, 0, sizeof(float) * 3 * c->MP, c->stream));
     CK(launch_adj_interp(*c, sk, c->adj, c->lamG, (float)c->tt.D1[k], k));
     CK(launch_adj_div(*c, c->lamG, c->lam_phi_pad, c->adj_in));

@@ -210,6 +210,10 @@ struct Ctx {
     // evaluations from its slot into seg and restores the final state from fin)
     int ckpt_every = 1;
     float *ckpt = nullptr;
+    // with every-evaluation checkpoints, also each evaluation's padded potential (cap_MP floats
+    // per slot) where the slots fit half of the free device memory: the reverse sweep restores
+    // it instead of recomputing the deposit and the Poisson solve
+    float *ckpt_phi = nullptr;
     float *seg = nullptr, *fin = nullptr;
     long long cap_P = 0, cap_M = 0, cap_MP = 0, cap_SH = 0;   // the largest batch's arena sizes
     float *adj = nullptr;                             // 15 x P backward particle state

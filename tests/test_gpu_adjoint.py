@@ -212,6 +212,7 @@ def test_interval_checkpoints_and_streamed_batches_give_the_same_gradient(every,
     n = 16**3
     u = torch.from_numpy(synth_inputs.random_field((n, 3), 41).astype(np.float32)).cuda()
     ref = _sim(kw, "tc")
+    assert ref.stats()["adjoint_potentials_kept"] == 1      # restored, not recomputed
     x, _ = ref.forward(w)
     lam = 2.0 * (ref.final_density(x) - target)
     g_ref = ref.backward_density(lam).cpu().numpy()
@@ -223,6 +224,7 @@ def test_interval_checkpoints_and_streamed_batches_give_the_same_gradient(every,
     assert sim.stats()["batches"] == (4 if batch_boxes else 1)
     m = sc.scola_checkpoint_interval(sim.ctx)
     assert m == (every if every else m) and m >= 1
+    assert sim.stats()["adjoint_potentials_kept"] == (1 if m == 1 else 0)   # m > 1: recomputed
     x2, _ = sim.forward(w)
     assert torch.equal(x, x2)
     g = sim.backward_density(lam).cpu().numpy()
