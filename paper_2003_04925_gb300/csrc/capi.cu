@@ -1674,7 +1674,7 @@ scola_status scola_set_checkpointing(scola_ctx *c, int32_t enable) {
     if (on && !c->adj) {
         const long long P = c->cap_P, N3 = c->N3;
         CS(dev_alloc(&c->adj, 15 * P));
-        CS(dev_alloc(&c->lamG, 3 * c->cap_MP));
+        CS(dev_alloc(&c->lamG, 4 * c->cap_MP));       // interleaved (x, y, z, unused) per padded cell
         CS(dev_alloc(&c->lam_phi_pad, c->cap_MP));
         CS(dev_alloc(&c->adj_in, c->cap_M));
         CS(dev_alloc(&c->adj_out, c->cap_MP));
@@ -1772,7 +1772,7 @@ scola_status reverse_step(scola_ctx *c, int k, const float *sk) {
         CK(launch_deposit(*c, sk, P, (float)(1.0 / c->tt.D1[k]), nullptr, false, k));
         CK(launch_poisson(*c));
     }
-    CK(cudaMemsetAsync(c->lamG, 0, sizeof(float) * 3 * c->MP, c->stream));
+    CK(cudaMemsetAsync(c->lamG, 0, sizeof(float) * 4 * c->MP, c->stream));
     CK(launch_adj_interp(*c, sk, c->adj, c->lamG, (float)c->tt.D1[k], k));
     CK(launch_adj_div(*c, c->lamG, c->lam_phi_pad, c->adj_in));
     CK(launch_poisson_buffers(*c, c->adj_in, c->work, c->work2, c->adj_out));

@@ -15,7 +15,7 @@
 //   kick   p += kF F + k1 Psi1 + k2 Psi2      -> lam_F = kF lam_p,   lam_Psi += k lam_p
 //   force  F(s_k): recomputed mesh potential at the checkpointed s_k, then
 //     k_adj_interp   lam_s += (d weights / ds) (G . lam_F)   (direct term, clamp aware)
-//                    lam_G += weights * lam_F                (3 channels, padded grid)
+//                    lam_G += weights * lam_F   (3 channels interleaved per padded cell)
 //     k_adj_div      lam_Phi = -div lam_G (transpose of the central difference);
 //                    interior part -> Dirichlet solve (self-adjoint), ghosts kept
 //     k_adj_shell    lam_shell += D1(a_k) (lam_Phi_ghost - boundary-source transpose)
@@ -244,16 +244,15 @@ k_adj_interp(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks
                 dir[1] += wx * (dy ? 1.f : -1.f) * wz * gl;
                 dir[2] += wx * wy * (dz ? 1.f : -1.f) * gl;
                 const float w = wx * wy * wz;
-                atomicAdd(lamG + base + o, w * lF[0]);
-                atomicAdd(lamG + MP + base + o, w * lF[1]);
-                atomicAdd(lamG + 2 * MP + base + o, w * lF[2]);
+                // lam_G interleaved per padded cell (x, y, z, unused): one 16-byte vector atomic
+                atomicAdd(reinterpret_cast<float4 *>(lamG) + base + o, make_float4(w * lF[0], w * lF[1], w * lF[2], 0.f));
             }
 #pragma unroll
     for (int a = 0; a < 3; ++a) adj[a * P + gi] += dir[a] * fr[a] * B.inv_dg;
 }
 
 // lam_Phi(c) = sum_a sum_m g_m (lam_G_a(c - m e_a) - lam_G_a(c + m e_a)) / dg over the padded grid
-// (the transpose of the order-n central gradient).
+// (the transpose of the order-n central gradient); lam_G interleaved, one float4 per cell.
 template <int ORDER>
 __global__ void __launch_bounds__(kChunk)
 k_adj_div(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
@@ -270,14 +269,14 @@ k_adj_div(const BoxDesc *__restrict__ boxes, const Chunk *__restrict__ chunks,
     const long long strides[3] = {(long long)S * S, S, 1};
     const long long here = B.pp_off + idx;
     float v = 0.0f;
+    const float *G4 = lamG;          // 4 floats per padded cell
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const float *Ga = lamG + a * MP;
 #pragma unroll
         for (int m = 1; m <= Fda<ORDER>::ng; ++m) {
             float d = 0.0f;
-            if (p[a] - m >= 0) d += Ga[here - m * strides[a]];
-            if (p[a] + m < S) d -= Ga[here + m * strides[a]];
+            if (p[a] - m >= 0) d += G4[4 * (here - m * strides[a]) + a];
+            if (p[a] + m < S) d -= G4[4 * (here + m * strides[a]) + a];
             v = fmaf(Fda<ORDER>::g(m), d, v);
         }
     }
