@@ -16,8 +16,8 @@ evolves its range, with no collective on the data path (boxes never communicate)
 value = the work of all boxes / max rank time ("strong" scaling).
 
 The JSON line carries the per-tile comparison and the adjoint cost at its end; the
-per-kernel table, the study workload and the autotuner picks go to stderr and to
-gpurun_out/bench_details.json (or $SCOLA_BENCH_DETAILS).
+per-kernel table, the study workload and the autotuner picks go to stderr and to the file
+$SCOLA_BENCH_DETAILS (default: scola_bench_details.json in the system's temporary directory).
 """
 import argparse
 import json
@@ -681,7 +681,7 @@ def run_gpu(args, rank, world, local_rank):
             line["per_tile"] = per_tile
         if adj is not None:
             line["adjoint"] = adj
-        dpath = os.environ.get("SCOLA_BENCH_DETAILS", os.path.join(ROOT, "gpurun_out", "bench_details.json"))
+        dpath = os.environ.get("SCOLA_BENCH_DETAILS", os.path.join(tempfile.gettempdir(), "scola_bench_details.json"))
         if os.path.isdir(os.path.dirname(dpath)):
             with open(dpath, "w") as fh:
                 json.dump(details, fh, indent=1)

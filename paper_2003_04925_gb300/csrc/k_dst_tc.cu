@@ -629,7 +629,7 @@ constexpr size_t kSmemBudget = 227 * 1024;
 
 // The input buffer as a 2D tensor of rows of Ng floats (box m_off are multiples of Ng), for
 // 16 x 256 tensor copies with the 64-byte swizzle of the MMA stages; encoded once per
-// (buffer, Ng) through the driver entry point.
+// (buffer, Ng) through the CUDA driver API's entry point (cuTensorMapEncodeTiled).
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
