@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--dst", default="auto", choices=["auto", "tc", "tc4", "tc3", "simt", "radix"],
                     help="Poisson-solve form: the library's autotuner (auto, default: the fastest of the "
                          "tensor-core forms and FP32 CUDA cores), tensor-core 3xTF32 in six passes (tc), "
-                         "4xTF32 (tc4), 3xTF32 in three passes (tc3), dense FP32 CUDA cores (simt) or radix "
+                         "4xTF32 (tc4), three passes (tc3: 3xTF32 z passes, 3xFP16 plane pass), dense FP32 CUDA cores (simt) or radix "
                          "(Bluestein) FP32 transforms (radix)")
     ap.add_argument("--forward-only", action="store_true",
                     help="only W + K forward runs of the batched form (for ncu launch lists)")
@@ -673,7 +673,7 @@ def run_gpu(args, rank, world, local_rank):
                     "l2": "working set %.2f GB > 129 MB L2, no flush" % (ws_bytes / 1e9),
                     "parallelism": "boxes split over %d GPU(s)" % world,
                     "dst": {"tc": "tcgen05 3xTF32, six passes", "tc4": "tcgen05 4xTF32, six passes",
-                            "tc3": "tcgen05 3xTF32, three passes", "simt": "FP32 CUDA cores",
+                            "tc3": "tcgen05 three passes (3xTF32 z, 3xFP16 planes)", "simt": "FP32 CUDA cores",
                             "radix": "FP32 CUDA cores, radix (Bluestein) transforms"}[args.dst]}),
                 "gpu_launches": int(launches * args.steps), "clocks": clk,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e}
@@ -710,10 +710,10 @@ def dst_choice(sc, st):
     """The Poisson-solve form in use and, under the autotuner, the candidates it timed (ms per
     solve of all boxes; both forms meet the accuracy bound)."""
     names = {sc.SCOLA_DST_TC_3XTF32: "tensor cores, 3xTF32, six passes", sc.SCOLA_DST_TC_4XTF32: "tensor cores, 4xTF32",
-             sc.SCOLA_DST_TC_3PASS: "tensor cores, 3xTF32, three passes", sc.SCOLA_DST_SIMT: "FP32 CUDA cores",
+             sc.SCOLA_DST_TC_3PASS: "tensor cores, three passes (3xTF32 z, 3xFP16 planes)", sc.SCOLA_DST_SIMT: "FP32 CUDA cores",
              sc.SCOLA_DST_RADIX: "FP32 CUDA cores, radix (Bluestein) transforms"}
     cand = st["ms_dst_candidates"]
-    order = ("tensor cores, 3xTF32, six passes", "FP32 CUDA cores", "tensor cores, 3xTF32, three passes",
+    order = ("tensor cores, 3xTF32, six passes", "FP32 CUDA cores", "tensor cores, three passes (3xTF32 z, 3xFP16 planes)",
              "FP32 CUDA cores, radix (Bluestein) transforms")
     return {"kept": names.get(st["dst_form"], "not chosen"),
             "candidates_ms": {n: round(t, 4) for n, t in zip(order, cand) if t > 0}}

@@ -57,9 +57,11 @@ typedef enum scola_dst_variant {
                                     every 2 <= Ng <= 240 (the sine matrix resident in shared
                                     memory, folded by its mirror symmetry for Ng > 128) */
     SCOLA_DST_TC_4XTF32 = 3,     /* as 1, plus the lo x lo product (four TF32 products) */
-    SCOLA_DST_TC_3PASS = 4,      /* the 3xTF32 products in three mesh passes instead of six: z
-                                    forward; every z-frequency plane transformed along y and x,
-                                    divided and transformed back in shared memory; z inverse.
+    SCOLA_DST_TC_3PASS = 4,      /* the products in three mesh passes instead of six: z forward
+                                    (3xTF32); every z-frequency plane transformed along y and x,
+                                    divided and transformed back in shared memory (3xFP16, each
+                                    pencil scaled by a power of two into FP16's range: the same
+                                    ~22 bits as 3xTF32 at twice its rate); z inverse (3xTF32).
                                     Every Ng <= 96 with Ng % 4 == 0 (UNSUPPORTED otherwise) */
     SCOLA_DST_RADIX = 5,         /* fast sine transforms on FP32 CUDA cores, O(Ng log Ng) per
                                     pencil: each DST-I of length Ng from a real DFT of length

@@ -11,32 +11,42 @@
 // so the mesh crosses device memory three times per solve instead of six.
 //
 // Each step is D = S X^T with the sine matrix S (S_kn = sin(pi (k+1)(n+1)/(Ng+1))) as the
-// M = 128 operand and the plane's Ng rows as the N operand, split into TF32 hi and lo parts
-// (3xTF32, or four products with lo x lo).  S_hi and S_lo stay in tensor memory for the
-// whole launch (the A operand of tcgen05.mma may come from TMEM), so an N = 96 MMA reads only
-// the 3 KB data operand from shared memory: ~48 cycles against ~56 with both operands in
-// shared memory, and the shared-memory bandwidth stays free for the epilogues.  TMEM lane u
-// of D holds output index u of every row, so one epilogue thread per lane owns one row of
-// the next step's operand: it reads its lane, splits it and writes it straight into the
-// K-major operand in shared memory, and the next step contracts the other axis:
+// M = 128 operand and the plane's Ng rows as the N operand, both split into FP16 hi and lo
+// parts: S_hi X_hi + S_hi X_lo + S_lo X_hi (or four products with lo x lo) on
+// tcgen05.mma kind::f16, which runs at twice the TF32 rate and reads half the operand
+// bytes.  FP16 has TF32's 11-bit significand but a narrow exponent range, so every operand
+// row (one pencil) is multiplied by a power of two 2^s that puts its largest magnitude in
+// [2^14, 2^15) before the split, and S by 2^14: hi + lo then keep ~22 bits of the pencil
+// relative to its largest element, as 3xTF32 does, smaller elements keep their absolute
+// error at that level, and no part overflows.  Column n of D carries the factor
+// 2^(14 + s_n) of pencil n; the epilogue that reads D multiplies it out (exactly) before it
+// scales its own row.  S_hi and S_lo stay in tensor memory for the whole launch (the A
+// operand of tcgen05.mma may come from TMEM), so the MMAs read only the data operand from
+// shared memory.  TMEM lane u of D holds output index u of every row, so one epilogue thread
+// per lane owns one row of the next step's operand: it reads its lane, scales and splits it
+// and writes it straight into the K-major operand in shared memory, and the next step
+// contracts the other axis:
 //   step 1  rows i,   K = j   ->  lanes m  (y frequency), columns i
 //   step 2  rows m,   K = i   ->  lanes l  (x frequency), columns m   (then / lambda sum)
 //   step 3  rows l,   K = m   ->  lanes j' (y),           columns l
 //   step 4  rows j',  K = l   ->  lanes i' (x),           columns j'  -> row i' of W2[n]
 // Three planes are in flight per CTA (three operand buffers, three accumulators): while
 // the epilogues turn two planes' accumulators into their next operands, the tensor cores
-// run the third plane's step, and the next plane's copy lands behind them.
+// run the third plane's step.  The FP32 planes land in two staging buffers by tensor copy;
+// the group that takes a plane scales and splits it row by row into its operand buffer.
 //
-// One persistent CTA per SM, 14 warps:
-//   warps 4e .. 4e+3 (e = 0, 1, 2)  buffer e: split its planes into hi/lo, the epilogues of
-//                                   their four steps
-//   warp 12    TMEM allocation; lane 0 issues tcgen05.mma and tcgen05.commit
-//   warp 13    lane 0 issues the tensor copies of each plane (Ng/32 boxes of 32 x Npad)
-// The operands are K-major with the 128-byte swizzle (chunks of 32 columns).  The CTAs of
-// a launch are split among the Ng groups of the boxes (as in k_dst_tc.cu).  Every wait is
-// bounded (about 2 s); on expiry the CTA raises the error flag, stops issuing, waits
-// (bounded) for its issued copies and MMAs, frees TMEM and returns.
+// One persistent CTA per SM, 11 warps (at most 168 registers a thread):
+//   warps 4e .. 4e+2 (e = 0, 1, 2)  buffer e: split its planes into hi/lo, the epilogues of
+//                                   their four steps (TMEM lanes 0 .. 95: Npad <= 96)
+//   warp 7     TMEM allocation; lane 0 issues tcgen05.mma and tcgen05.commit
+//   warp 3     lane 0 issues the tensor copies of each plane (Ng/32 boxes of 32 x Npad)
+// The operands are K-major with the 128-byte swizzle (chunks of 64 FP16 columns; the
+// staging buffers in chunks of 32 FP32 columns).  The CTAs of a launch are split among the
+// Ng groups of the boxes (as in k_dst_tc.cu).  Every wait is bounded (about 2 s); on expiry
+// the CTA raises the error flag, stops issuing, waits (bounded) for its issued copies and
+// MMAs, frees TMEM and returns.
 #include <cuda.h>
+#include <cuda_fp16.h>
 #include <stdint.h>
 
 #include <algorithm>
@@ -52,16 +62,21 @@ namespace {
 
 using namespace tc;
 
-constexpr int kPlThreads = 448;
+constexpr int kPlThreads = 352;
+constexpr int kPlRows = 96;    // threads of an epilogue group: one per operand row
 constexpr int kPlBuf = 3;       // planes in flight
+constexpr int kPlStage = 2;     // FP32 staging buffers for the tensor copies
 constexpr int kPlGroups = 4;
+constexpr int kPlMaxN = 96;     // largest Ng of the plane pass
+constexpr int kSExp = 14;       // S is held as S 2^14
+constexpr int kSCols = 64;      // TMEM columns of S_hi (two FP16 elements per column)
 
 struct PlaneGroupArgs {
     CUtensorMap in_map;          // W1 as rows of Ng floats: boxes of 32 x Npad, 128-byte swizzle
     const Chunk *items;          // (box, plane n)
     const float *S;              // sine matrix rows, Ng x (32 nka) (the one-axis passes' table)
     const float *lam;            // Dirichlet eigenvalues, Ng
-    int nitems, Ng, Npad, nka;   // nka: 32-column chunks of the sine matrix and of the operands
+    int nitems, Ng, Npad, nka;   // nka: 32-column chunks of the FP32 rows and of the sine table
     int cta0, nctas;
 };
 
@@ -74,54 +89,61 @@ struct PlaneArgs {
     int lo_lo;
 };
 
-// One epilogue thread's row after step STEP of a plane, accumulator chunks c0 .. c0 + 2 (v:
-// 16 columns each; chunks >= nc16 absent).  Steps 1-3: the row of the next operand (K-major,
-// 128-byte swizzle, hi and lo TF32 parts), zero outside the Ng x Ng block; step 2 first
-// divides by the eigenvalue sum (row: x frequency l, column: y frequency m, plane: z
-// frequency n).  Step 4: row i' of the output plane, written to global memory.
-template <int STEP>
-__device__ __forceinline__ void plane_rows(const float (&v)[3][16], int c0, int nc16, int row, int Ng, int Npad,
-                                           uint32_t och, unsigned char *hi, unsigned char *lo, const float *lam,
-                                           float lam_row, float lam_n, float *dst) {
-    if (STEP == 4) {
-        if (row >= Ng) return;
+// 2^s as a float, |s| <= 126.
+__device__ __forceinline__ float pow2f(int s) { return __uint_as_float((uint32_t)(127 + s) << 23); }
+
+// The exponent s that puts a row's largest magnitude m in [2^14, 2^15): 0 for a zero or
+// non-finite row, at most 100 (rows below 2^-86 keep their absolute error far below 2^-40).
+__device__ __forceinline__ int row_exp(float m) {
+    if (!(m > 0.0f) || !(m <= 3.0e38f)) return 0;
+    const int E = (int)((__float_as_uint(m) >> 23) & 0xFFu) - 127;
+    return min(kSExp - E, 100);
+}
+
+__device__ __forceinline__ uint32_t h2_bits(__half2 h) {
+    uint32_t u;
+    memcpy(&u, &h, 4);
+    return u;
+}
+
+// Row `row` of a K-major FP16 operand pair (128-byte swizzle, 64-column chunks och bytes
+// apart): x[k] sc split into hi and lo, in units of 8 columns up to nu.
+__device__ __forceinline__ void put_row(const float (&x)[kPlMaxN / 16][16], float sc, int row, int nu, uint32_t och,
+                                        unsigned char *hi, unsigned char *lo) {
 #pragma unroll
-        for (int cc = 0; cc < 3; ++cc) {
-            const int c = c0 + cc;
-            if (c >= nc16) break;
+    for (int u = 0; u < kPlMaxN / 8; ++u) {
+        if (u >= nu) break;
+        uint32_t h[4], l[4];
 #pragma unroll
-            for (int qq = 0; qq < 4; ++qq) {
-                const int col = c * 16 + 4 * qq;
-                if (col < Ng)
-                    *reinterpret_cast<float4 *>(dst + col) =
-                        make_float4(v[cc][4 * qq], v[cc][4 * qq + 1], v[cc][4 * qq + 2], v[cc][4 * qq + 3]);
-            }
+        for (int t = 0; t < 4; ++t) {
+            const float a = x[u >> 1][8 * (u & 1) + 2 * t] * sc, b = x[u >> 1][8 * (u & 1) + 2 * t + 1] * sc;
+            const __half2 hh = __floats2half2_rn(a, b);
+            const float2 hf = __half22float2(hh);
+            h[t] = h2_bits(hh);
+            l[t] = h2_bits(__floats2half2_rn(a - hf.x, b - hf.y));
         }
-        return;
+        const uint32_t off = (uint32_t)(u >> 3) * och + (uint32_t)((row >> 3) * 1024 + (row & 7) * 128) +
+                             ((uint32_t)((u & 7) ^ (row & 7)) << 4);
+        *reinterpret_cast<uint4 *>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<uint4 *>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
     }
-    if (row >= Npad) return;
-    const bool rv = row < Ng;
+}
+
+// Largest magnitude of a row: 16 independent partial maxima, then a tree (a short
+// dependency chain instead of one of 96 steps).
+__device__ __forceinline__ float row_max(const float (&x)[kPlMaxN / 16][16]) {
+    float m[16];
 #pragma unroll
-    for (int cc = 0; cc < 3; ++cc) {
-        const int c = c0 + cc;
-        if (c >= nc16) break;
+    for (int j = 0; j < 16; ++j) m[j] = fabsf(x[0][j]);
 #pragma unroll
-        for (int qq = 0; qq < 4; ++qq) {
-            const int col0 = c * 16 + 4 * qq;
-            float x[4];
+    for (int c = 1; c < kPlMaxN / 16; ++c)
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                float y = v[cc][4 * qq + t];
-                if (STEP == 2) y = __fdividef(y, lam_row + lam[col0 + t] + lam_n);
-                x[t] = (rv && col0 + t < Ng) ? y : 0.0f;
-            }
-            const float4 h = make_float4(tf32_rn(x[0]), tf32_rn(x[1]), tf32_rn(x[2]), tf32_rn(x[3]));
-            const uint32_t off = (uint32_t)(col0 >> 5) * och + sw128_offset(row, col0 & 31);
-            *reinterpret_cast<float4 *>(hi + off) = h;
-            *reinterpret_cast<float4 *>(lo + off) =
-                make_float4(tf32_rn(x[0] - h.x), tf32_rn(x[1] - h.y), tf32_rn(x[2] - h.z), tf32_rn(x[3] - h.w));
-        }
-    }
+        for (int j = 0; j < 16; ++j) m[j] = fmaxf(m[j], fabsf(x[c][j]));
+#pragma unroll
+    for (int w = 8; w > 0; w >>= 1)
+#pragma unroll
+        for (int j = 0; j < w; ++j) m[j] = fmaxf(m[j], m[j + w]);
+    return m[0];
 }
 
 __global__ void __launch_bounds__(kPlThreads, 1) k_dst_plane(const __grid_constant__ PlaneArgs A) {
@@ -132,41 +154,50 @@ __global__ void __launch_bounds__(kPlThreads, 1) k_dst_plane(const __grid_consta
     const PlaneGroupArgs &G = A.grp[gi];
     const int bid = (int)blockIdx.x - G.cta0, nbid = G.nctas;
     const int Ng = G.Ng, Npad = G.Npad, nka = G.nka;
-    const int Kp = nka * 32;                                   // sine columns held (TMEM)
-    const uint32_t och = (uint32_t)Npad * 128;                 // one operand chunk (32 K)
-    const uint32_t bhalf = (uint32_t)nka * och;                // one operand, hi or lo
-    // TMEM columns: S_hi [0, Kp), S_lo [Kp, 2 Kp), accumulator e at 2 Kp + e accw
+    const int Kp = nka * 32;                                   // columns of the sine table rows
+    const int nk16 = (Ng + 15) / 16;                           // K steps of the MMAs
+    const uint32_t och = (uint32_t)Npad * 128;                 // one 128-byte-wide chunk of rows
+    const uint32_t bhalf = (uint32_t)((nk16 + 3) / 4) * och;   // one FP16 operand, hi or lo
+    const uint32_t bstage = (uint32_t)nka * och;               // one FP32 staging buffer
+    // TMEM columns: S_hi [0, 64), S_lo [64, 128), accumulator e at 128 + e accw
     const uint32_t accw = (uint32_t)((Npad + 31) / 32 * 32);
-    unsigned char *bufs = base;                                // buffer e: hi, then lo
-    uint64_t *bars = (uint64_t *)(bufs + 2 * kPlBuf * (size_t)bhalf);
-    uint64_t *loaded = bars;                 // the plane's tensor copies have landed
-    uint64_t *opready = bars + kPlBuf;       // the next step's operand is written (128 arrivals)
-    uint64_t *accfull = bars + 2 * kPlBuf;   // the step's MMAs are complete
-    uint64_t *bufempty = bars + 3 * kPlBuf;  // step 4 is complete: the buffer may take the next plane
-    uint64_t *drain = bars + 4 * kPlBuf;
+    unsigned char *ops = base;                                 // buffer e: hi, then lo
+    unsigned char *stage = ops + 2 * kPlBuf * (size_t)bhalf;   // staging buffer b
+    uint64_t *bars = (uint64_t *)(stage + kPlStage * (size_t)bstage);
+    // loaded[e]: the copies of group e's next plane have landed.  The barrier belongs to the
+    // consuming group, not to the staging buffer, so that its phases follow the group's own
+    // planes (a buffer's planes alternate between groups, and a parity wait must never be
+    // two phases ahead of the barrier)
+    uint64_t *loaded = bars;
+    uint64_t *stfree = bars + kPlBuf;                  // staging b: its plane is split (96 arrivals)
+    uint64_t *opready = stfree + kPlStage;             // the next step's operand is written (96 arrivals)
+    uint64_t *accfull = opready + kPlBuf;              // the step's MMAs are complete
+    uint64_t *drain = accfull + kPlBuf;
     uint32_t *tmem_slot = (uint32_t *)(drain + 1);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
     float *lam = (float *)(tmem_slot + 4);
+    float *uns = lam + 128;                            // [buffer][slot][column]: 2^-(14 + s) of row
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
 
     // ---- set-up: eigenvalues, clean operand buffers, barriers, tensor memory
     for (int q = tid; q < 128; q += kPlThreads) lam[q] = q < Ng ? G.lam[q] : 0.0f;
+    for (int q = tid; q < kPlBuf * 2 * 128; q += kPlThreads) uns[q] = 0.0f;
     for (int q = tid; q < (int)(2 * kPlBuf * bhalf / 16); q += kPlThreads)
-        reinterpret_cast<float4 *>(bufs)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        reinterpret_cast<float4 *>(ops)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
     const long long my_items = G.nitems > bid ? (G.nitems - 1 - bid) / nbid + 1 : 0;
     if (tid == 0) {
+        for (int b = 0; b < kPlStage; ++b) mbar_init(&stfree[b], kPlRows);
         for (int e = 0; e < kPlBuf; ++e) {
             mbar_init(&loaded[e], 1);
-            mbar_init(&opready[e], 128);
+            mbar_init(&opready[e], kPlRows);
             mbar_init(&accfull[e], 1);
-            mbar_init(&bufempty[e], 1);
         }
         mbar_init(drain, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 12) {
+    if (warp == 7) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                      "r"(512));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -177,20 +208,27 @@ __global__ void __launch_bounds__(kPlThreads, 1) k_dst_plane(const __grid_consta
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     if (warp < 4) {
-        // S into TMEM: lane k holds row k (zero for k >= Ng), hi parts in columns [0, Kp),
-        // lo parts in [Kp, 2 Kp); the table row k has Kp columns, zero beyond Ng
+        // S 2^14 into TMEM: lane k holds row k (zero for k >= Ng), two FP16 elements per
+        // column (element 2c in the low half of column c), hi parts in columns [0, 64), lo
+        // parts in [64, 128); the table row k has Kp columns, zero beyond Ng.  Warp w writes
+        // lanes 32 w .. 32 w + 31
         const int k = warp * 32 + lane;
         const uint32_t lb = (uint32_t)(warp * 32) << 16;
-        for (int c = 0; c < Kp / 16; ++c) {
+        const float ss = pow2f(kSExp);
+        for (int g = 0; g < kSCols / 16; ++g) {
             float h[16], l[16];
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-                const float sv = k < Ng ? G.S[(long long)k * Kp + c * 16 + j] : 0.0f;
-                h[j] = tf32_rn(sv);
-                l[j] = tf32_rn(sv - h[j]);
+                const int c0 = 32 * g + 2 * j;
+                const float a = (k < Ng && c0 < Kp) ? G.S[(long long)k * Kp + c0] * ss : 0.0f;
+                const float b = (k < Ng && c0 + 1 < Kp) ? G.S[(long long)k * Kp + c0 + 1] * ss : 0.0f;
+                const __half2 hh = __floats2half2_rn(a, b);
+                const float2 hf = __half22float2(hh);
+                h[j] = __uint_as_float(h2_bits(hh));
+                l[j] = __uint_as_float(h2_bits(__floats2half2_rn(a - hf.x, b - hf.y)));
             }
-            tmem_st16(tmem + lb + (uint32_t)(c * 16), h);
-            tmem_st16(tmem + lb + (uint32_t)(Kp + c * 16), l);
+            tmem_st16(tmem + lb + (uint32_t)(g * 16), h);
+            tmem_st16(tmem + lb + (uint32_t)(kSCols + g * 16), l);
         }
         tmem_st_wait();
     }
@@ -200,40 +238,42 @@ __global__ void __launch_bounds__(kPlThreads, 1) k_dst_plane(const __grid_consta
     const long long Ng2 = (long long)Ng * Ng;
     const long long ntrip = (my_items + kPlBuf - 1) / kPlBuf;
 
-    if (warp == 13) {
+    if (warp == 3) {
         // ---------------------------------------------------------------- tensor copies
-        // plane p goes to buffer p % 3 once step 4 of plane p - 3 has finished with it; on an
-        // abort, wait (bounded) for the copies already issued before the CTA may exit
+        // plane p goes to staging buffer p % 2 once plane p - 2 has been split out of it, and
+        // completes on loaded[p % 3]; the copies are issued in plane order, so group p % 3 has
+        // taken its plane p - 3 before plane p can land.  On an abort, wait (bounded) for the
+        // copies already issued before the CTA may exit
         if (lane == 0) {
             long long p = 0;
             for (; p < my_items && !*abort_flag; ++p) {
-                const int e = (int)(p % kPlBuf);
-                const long long j = p / kPlBuf;
-                if (j > 0 && !mbar_wait(&bufempty[e], (uint32_t)((j - 1) & 1), abort_flag)) {
+                const int b = (int)(p % kPlStage);
+                const long long j = p / kPlStage;
+                if (j > 0 && !mbar_wait(&stfree[b], (uint32_t)((j - 1) & 1), abort_flag)) {
                     *abort_flag = 1;
                     break;
                 }
                 const Chunk it = G.items[bid + p * nbid];
                 const long long m_off = A.boxes[it.box].m_off;
                 const int y = (int)(m_off / Ng + (long long)it.start * Ng);     // row (n, i = 0)
-                unsigned char *hi = bufs + (size_t)e * 2 * bhalf;
-                mbar_arrive_expect_tx(&loaded[e], bhalf);
-                for (int c = 0; c < nka; ++c)
-                    tma_load_2d(smem_u32(hi + (size_t)c * och), &G.in_map, c * 32, y, &loaded[e]);
+                unsigned char *st = stage + (size_t)b * bstage;
+                uint64_t *bar = &loaded[p % kPlBuf];
+                mbar_arrive_expect_tx(bar, bstage);
+                for (int c = 0; c < nka; ++c) tma_load_2d(smem_u32(st + (size_t)c * och), &G.in_map, c * 32, y, bar);
             }
             if (*abort_flag) {
                 const unsigned long long t0 = now_ns();
-                for (long long q = p - kPlBuf > 0 ? p - kPlBuf : 0; q < p; ++q)
+                for (long long q = p - kPlStage > 0 ? p - kPlStage : 0; q < p; ++q)
                     while (!mbar_try_wait(&loaded[q % kPlBuf], (uint32_t)((q / kPlBuf) & 1)) &&
                            now_ns() - t0 < kWaitNs) {
                     }
             }
         }
-    } else if (warp == 12) {
+    } else if (warp == 7) {
         // ---------------------------------------------------------------- MMA issuer
         // order: for each triple of planes, steps 1..4, each step for the triple's planes
         if (lane == 0) {
-            const uint32_t idesc = idesc_tf32(128, Npad);
+            const uint32_t idesc = idesc_f16(128, Npad);
             const bool lo_lo = A.lo_lo != 0;
             bool ok = true;
             for (long long q = 0; q < ntrip && ok && !*abort_flag; ++q)
@@ -245,50 +285,37 @@ __global__ void __launch_bounds__(kPlThreads, 1) k_dst_plane(const __grid_consta
                             break;
                         }
                         tc_fence_after();
-                        const uint32_t d = tmem + (uint32_t)(2 * Kp) + (uint32_t)e * accw;
+                        const uint32_t d = tmem + (uint32_t)(2 * kSCols) + (uint32_t)e * accw;
                         // descriptors advance by (byte offset >> 4) in their address field
-                        // (shared addresses < 2^18: no carry out of the field)
-                        const uint64_t bh0 = sw128_desc(smem_u32(bufs + (size_t)e * 2 * bhalf));
+                        // (shared addresses < 2^18: no carry out of the field); a K step of 16
+                        // FP16 columns is 32 bytes of the swizzled row, 8 TMEM columns of S
+                        const uint64_t bh0 = sw128_desc(smem_u32(ops + (size_t)e * 2 * bhalf));
                         const uint64_t bl0 = bh0 + (bhalf >> 4);
-                        for (int kc = 0; kc < nka; ++kc) {
-                            const uint64_t bhc = bh0 + ((uint64_t)kc * (och >> 4)), blc = bl0 + ((uint64_t)kc * (och >> 4));
-                            const uint32_t ahc = tmem + (uint32_t)(kc * 32), alc = ahc + (uint32_t)Kp;
-                            if (lo_lo) {
-#pragma unroll
-                                for (int kk = 0; kk < 4; ++kk) {
-                                    if (kc * 32 + kk * 8 >= Ng) break;
-                                    const uint64_t bhi = bhc + (uint64_t)(kk * 2), blo = blc + (uint64_t)(kk * 2);
-                                    mma_tf32_ts(d, ahc + kk * 8, bhi, idesc, (kc | kk) ? 1u : 0u);
-                                    mma_tf32_ts(d, ahc + kk * 8, blo, idesc, 1);
-                                    mma_tf32_ts(d, alc + kk * 8, bhi, idesc, 1);
-                                    mma_tf32_ts(d, alc + kk * 8, blo, idesc, 1);
-                                }
-                            } else {
-#pragma unroll
-                                for (int kk = 0; kk < 4; ++kk) {
-                                    if (kc * 32 + kk * 8 >= Ng) break;
-                                    const uint64_t bhi = bhc + (uint64_t)(kk * 2), blo = blc + (uint64_t)(kk * 2);
-                                    mma_tf32_ts(d, ahc + kk * 8, bhi, idesc, (kc | kk) ? 1u : 0u);
-                                    mma_tf32_ts(d, ahc + kk * 8, blo, idesc, 1);
-                                    mma_tf32_ts(d, alc + kk * 8, bhi, idesc, 1);
-                                }
-                            }
+                        for (int t = 0; t < nk16; ++t) {
+                            const uint64_t off = (uint64_t)(t >> 2) * (och >> 4) + (uint64_t)((t & 3) * 2);
+                            const uint32_t ah = tmem + (uint32_t)(t * 8), al = ah + (uint32_t)kSCols;
+                            mma_f16_ts(d, ah, bh0 + off, idesc, t ? 1u : 0u);
+                            mma_f16_ts(d, ah, bl0 + off, idesc, 1);
+                            mma_f16_ts(d, al, bh0 + off, idesc, 1);
+                            if (lo_lo) mma_f16_ts(d, al, bl0 + off, idesc, 1);
                         }
                         mma_commit(&accfull[e]);
-                        if (s == 4) mma_commit(&bufempty[e]);
                     }
             if (!ok) *abort_flag = 1;
         }
     } else {
-        // ---------------------------------------------------------------- warps 0-11
+        // ---------------------------------------------------------------- warps 4e .. 4e+2
         // warp group e = warp / 4 serves buffer e (planes p = 3 q + e); warp w reads TMEM
-        // lanes 32 (w & 3) + lane, the output index of its row, over all column chunks
+        // lanes 32 (w & 3) + lane, the output index of its row, over all column chunks.  Each
+        // scheduler runs one warp of every group, so the groups wait with suspending waits
+        // that leave the issue slots to the group at work
         const int e = warp >> 2, lq = warp & 3;
-        const int gt = tid & 127;                       // thread within the group
         const int row = lq * 32 + lane;
-        unsigned char *hi = bufs + (size_t)e * 2 * bhalf, *lo = hi + bhalf;
-        const uint32_t tb = tmem + (uint32_t)(2 * Kp) + (uint32_t)e * accw + ((uint32_t)(lq * 32) << 16);
+        unsigned char *hi = ops + (size_t)e * 2 * bhalf, *lo = hi + bhalf;
+        float *un = uns + e * 2 * 128;
+        const uint32_t tb = tmem + (uint32_t)(2 * kSCols) + (uint32_t)e * accw + ((uint32_t)(lq * 32) << 16);
         const int nc16 = Npad / 16;                     // 16-column accumulator chunks (<= 6)
+        const int nu = 2 * nk16;                        // 8-column operand units written per row
         bool ok = true;
         for (long long q = 0; q < ntrip && ok && !*abort_flag; ++q) {
             const long long p = q * kPlBuf + e;
@@ -296,70 +323,111 @@ __global__ void __launch_bounds__(kPlThreads, 1) k_dst_plane(const __grid_consta
             const Chunk it = G.items[bid + p * nbid];
             const int n = it.start;
             const long long m_off = A.boxes[it.box].m_off;
-            // split the loaded plane in place: hi over the copy, lo into the other half; rows
-            // >= Ng (the next plane's rows brought by the box) are cleared.  Four 16-byte units
-            // per thread in flight at a time
-            if (!mbar_spin(&loaded[e], (uint32_t)(q & 1), abort_flag)) {
+            const int b = (int)(p % kPlStage);
+            if (!mbar_wait(&loaded[e], (uint32_t)(q & 1), abort_flag)) {
                 ok = false;
                 break;
             }
-            const int units = nka * Npad * 8;
-            for (int u0 = gt; u0 < units; u0 += 4 * 128) {
-                float4 v[4];
-                uint32_t off[4];
+            float x[kPlMaxN / 16][16];
+            {
+                // the thread's row of the FP32 plane (rows >= Ng: the next plane's rows brought by
+                // the copy, cleared; columns >= Ng: zero, filled by the copy beyond the tensor's
+                // rows of Ng floats), then the staging buffer is released
+                const unsigned char *st = stage + (size_t)b * bstage;
 #pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    const int u = u0 + 128 * b;
-                    const int c = u / (Npad * 8), rem = u - c * (Npad * 8);
-                    const int r = rem >> 3, qq = rem & 7;
-                    off[b] = (uint32_t)c * och + sw128_offset(r, 4 * qq);
-                    v[b] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (u < units && r < Ng) v[b] = *reinterpret_cast<const float4 *>(hi + off[b]);
-                }
+                for (int c = 0; c < kPlMaxN / 32; ++c)
 #pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    if (u0 + 128 * b >= units) break;
-                    const float4 h = make_float4(tf32_rn(v[b].x), tf32_rn(v[b].y), tf32_rn(v[b].z), tf32_rn(v[b].w));
-                    *reinterpret_cast<float4 *>(hi + off[b]) = h;
-                    *reinterpret_cast<float4 *>(lo + off[b]) = make_float4(
-                        tf32_rn(v[b].x - h.x), tf32_rn(v[b].y - h.y), tf32_rn(v[b].z - h.z), tf32_rn(v[b].w - h.w));
-                }
+                    for (int qq = 0; qq < 8; ++qq) {
+                        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (c < nka && row < Ng)
+                            v = *reinterpret_cast<const float4 *>(st + (uint32_t)c * och + sw128_offset(row, 4 * qq));
+                        const int k = 32 * c + 4 * qq;
+                        x[k >> 4][(k & 15)] = v.x;
+                        x[k >> 4][(k & 15) + 1] = v.y;
+                        x[k >> 4][(k & 15) + 2] = v.z;
+                        x[k >> 4][(k & 15) + 3] = v.w;
+                    }
+                mbar_arrive(&stfree[b]);
+                const int s0 = row_exp(row_max(x));
+                if (row < Npad) put_row(x, pow2f(s0), row, nu, och, hi, lo);
+                un[row] = pow2f(-(kSExp + s0));
             }
             fence_proxy_async();
             mbar_arrive(&opready[e]);
             const float lam_row = row < Ng ? lam[row] : 0.0f, lam_n = lam[n];
             float *dst = A.out + m_off + (long long)n * Ng2 + (long long)row * Ng;
             for (int s = 1; s <= 4; ++s) {
-                if (!mbar_spin(&accfull[e], (uint32_t)((s - 1) & 1), abort_flag)) {
+                if (!mbar_wait(&accfull[e], (uint32_t)((s - 1) & 1), abort_flag)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                // the lane's columns in two halves of up to three 16-column chunks, each half's
-                // TMEM loads in flight together
-                for (int c0 = 0; c0 < nc16; c0 += 3) {
-                    float v[3][16];
 #pragma unroll
-                    for (int cc = 0; cc < 3; ++cc)
-                        if (c0 + cc < nc16) tmem_ld16_issue(tb + (uint32_t)((c0 + cc) * 16), v[cc]);
-                    tmem_ld_wait();
+                for (int c = 0; c < kPlMaxN / 16; ++c)
+                    if (c < nc16) tmem_ld16_issue(tb + (uint32_t)(c * 16), x[c]);
+                tmem_ld_wait();
 #pragma unroll
-                    for (int cc = 0; cc < 3; ++cc) tmem_regs_ready(v[cc]);
-                    if (s == 1) plane_rows<1>(v, c0, nc16, row, Ng, Npad, och, hi, lo, lam, lam_row, lam_n, dst);
-                    else if (s == 2) plane_rows<2>(v, c0, nc16, row, Ng, Npad, och, hi, lo, lam, lam_row, lam_n, dst);
-                    else if (s == 3) plane_rows<3>(v, c0, nc16, row, Ng, Npad, och, hi, lo, lam, lam_row, lam_n, dst);
-                    else plane_rows<4>(v, c0, nc16, row, Ng, Npad, och, hi, lo, lam, lam_row, lam_n, dst);
+                for (int c = 0; c < kPlMaxN / 16; ++c) {
+                    tmem_regs_ready(x[c]);
+                    if (c >= nc16)
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) x[c][j] = 0.0f;
                 }
-                if (s < 4) fence_proxy_async();
-                tc_fence_before();
-                if (s < 4) mbar_arrive(&opready[e]);
+                // column k of D carries 2^(14 + s_k) of the row it came from (slot (s - 1) & 1);
+                // step 2 divides by the eigenvalue sum (row: x frequency l, column: y frequency
+                // m, plane: z frequency n).  D is exactly zero outside the Ng x Ng block (rows:
+                // S is zero beyond Ng; columns: so are the operand rows), and so is y there
+                // (lambda is zero-padded and lambda_n > 0); chunks >= nc16 are not loaded: zero
+                const float4 *u_in = reinterpret_cast<const float4 *>(un + ((s - 1) & 1) * 128);
+                const float4 *lam4 = reinterpret_cast<const float4 *>(lam);
+#pragma unroll
+                for (int c = 0; c < kPlMaxN / 16; ++c)
+#pragma unroll
+                    for (int jq = 0; jq < 4; ++jq) {
+                        const float4 u4 = u_in[4 * c + jq];
+                        const float uu[4] = {u4.x, u4.y, u4.z, u4.w};
+                        float ll[4] = {0.f, 0.f, 0.f, 0.f};
+                        if (s == 2) {
+                            const float4 l4 = lam4[4 * c + jq];
+                            ll[0] = l4.x, ll[1] = l4.y, ll[2] = l4.z, ll[3] = l4.w;
+                        }
+#pragma unroll
+                        for (int t = 0; t < 4; ++t) {
+                            const int j = 4 * jq + t;
+                            float y = x[c][j] * uu[t];
+                            if (s == 2) y = __fdividef(y, lam_row + ll[t] + lam_n);
+                            x[c][j] = y;
+                        }
+                    }
+                if (s == 4) {
+                    // row i' of the output plane
+                    if (row < Ng) {
+#pragma unroll
+                        for (int c = 0; c < kPlMaxN / 16; ++c)
+#pragma unroll
+                            for (int qq = 0; qq < 4; ++qq) {
+                                const int col = 16 * c + 4 * qq;
+                                if (col < Ng)
+                                    *reinterpret_cast<float4 *>(dst + col) = make_float4(
+                                        x[c][4 * qq], x[c][4 * qq + 1], x[c][4 * qq + 2], x[c][4 * qq + 3]);
+                            }
+                    }
+                    tc_fence_before();
+                } else {
+                    const int sr = row_exp(row_max(x));
+                    if (row < Npad) put_row(x, pow2f(sr), row, nu, och, hi, lo);
+                    un[(s & 1) * 128 + row] = pow2f(-(kSExp + sr));
+                    fence_proxy_async();
+                    tc_fence_before();
+                    mbar_arrive(&opready[e]);
+                }
             }
         }
         if (!ok) *abort_flag = 1;
     }
 
     // ---- tear-down: every role has left its loop; drain, then free tensor memory
-    if (warp == 12 && lane == 0 && *abort_flag) {
+    if (warp == 7 && lane == 0 && *abort_flag) {
         mma_commit(drain);
         const unsigned long long t0 = now_ns();
         while (!mbar_try_wait(drain, 0) && now_ns() - t0 < kWaitNs) {
@@ -369,12 +437,13 @@ __global__ void __launch_bounds__(kPlThreads, 1) k_dst_plane(const __grid_consta
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 12) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+    if (warp == 7) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
 
 size_t plane_smem_bytes(int Ng, int Npad, int nka) {
-    (void)Ng;
-    return 1024 + 2 * kPlBuf * (size_t)nka * Npad * 128 + (4 * kPlBuf + 1) * 8 + 16 + 128 * 4 + 64;
+    const size_t nk64 = (size_t)(Ng + 63) / 64;
+    return 1024 + 2 * kPlBuf * nk64 * Npad * 128 + kPlStage * (size_t)nka * Npad * 128 +
+           (kPlStage + 3 * kPlBuf + 1) * 8 + 16 + 128 * 4 + kPlBuf * 2 * 128 * 4 + 64;
 }
 
 constexpr size_t kPlSmemBudget = 227 * 1024;
@@ -383,8 +452,8 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-// W1 as a 2D tensor of rows of Ng floats, boxes of 32 x Npad with the 128-byte swizzle of
-// the MMA's K-major operand.
+// W1 as a 2D tensor of rows of Ng floats, boxes of 32 x Npad with the 128-byte swizzle (the
+// staging layout the splitting threads read).
 cudaError_t plane_map(Ctx &c, const float *buf, int Ng, int Npad, CUtensorMap *out) {
     static EncodeTiledFn encode = nullptr;
     if (!encode) {

@@ -1,7 +1,7 @@
 // Device helpers of the tensor-core kernels (sm_103a): mbarriers with bounded waits, TMA
-// tensor copies, tcgen05 MMA and tensor-memory access, shared-memory matrix descriptors and
-// the TF32 hi/lo split.  The layouts follow the PTX ISA's tcgen05 shared-memory descriptor
-// and instruction descriptor formats.
+// tensor copies, tcgen05 MMA (kind::tf32 and kind::f16) and tensor-memory access,
+// shared-memory matrix descriptors and the TF32 hi/lo split.  The layouts follow the PTX
+// ISA's tcgen05 shared-memory descriptor and instruction descriptor formats.
 #pragma once
 
 #include <cuda.h>
@@ -181,6 +181,23 @@ __device__ __forceinline__ void mma_tf32_ts(uint32_t d_tmem, uint32_t a_tmem, ui
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+// Instruction descriptor: D F32, A and B F16, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// D (+)= A B^T with A (M x 16, one row per TMEM lane, two K elements per column, the lower
+// index in the low half) read from tensor memory and B from shared memory: kind::f16, A and
+// B F16, D F32.
+__device__ __forceinline__ void mma_f16_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
+                                           uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
         "r"(a_tmem), "l"(b), "r"(idesc), "r"(accumulate));
 }
 
