@@ -30,6 +30,8 @@
 //   step 2  rows m,   K = i   ->  lanes l  (x frequency), columns m   (then / lambda sum)
 //   step 3  rows l,   K = m   ->  lanes j' (y),           columns l
 //   step 4  rows j',  K = l   ->  lanes i' (x),           columns j'  -> row i' of W2[n]
+// The output plane is written row by row into the group's operand buffer (free once the
+// step-4 MMAs are complete; the staging layout) and leaves by tensor store.
 // Three planes are in flight per CTA (three operand buffers, three accumulators): while
 // the epilogues turn two planes' accumulators into their next operands, the tensor cores
 // run the third plane's step.  The FP32 planes land in two staging buffers by tensor copy;
@@ -73,6 +75,7 @@ constexpr int kSCols = 64;      // TMEM columns of S_hi (two FP16 elements per c
 
 struct PlaneGroupArgs {
     CUtensorMap in_map;          // W1 as rows of Ng floats: boxes of 32 x Npad, 128-byte swizzle
+    CUtensorMap out_map;         // W2 as rows of Ng floats: boxes of 32 x Ng, 128-byte swizzle
     const Chunk *items;          // (box, plane n)
     const float *S;              // sine matrix rows, Ng x (32 nka) (the one-axis passes' table)
     const float *lam;            // Dirichlet eigenvalues, Ng
@@ -84,7 +87,6 @@ struct PlaneArgs {
     PlaneGroupArgs grp[kPlGroups];
     int ngroups;
     const BoxDesc *boxes;
-    float *out;
     int *err;
     int lo_lo;
 };
@@ -172,7 +174,9 @@ __global__ void __launch_bounds__(kPlThreads, 1) k_dst_plane(const __grid_consta
     uint64_t *stfree = bars + kPlBuf;                  // staging b: its plane is split (96 arrivals)
     uint64_t *opready = stfree + kPlStage;             // the next step's operand is written (96 arrivals)
     uint64_t *accfull = opready + kPlBuf;              // the step's MMAs are complete
-    uint64_t *drain = accfull + kPlBuf;
+    uint64_t *outw = accfull + kPlBuf;                 // the output plane is in shared memory (96 arrivals)
+    uint64_t *outfree = outw + kPlBuf;                 // its tensor store has read it
+    uint64_t *drain = outfree + kPlBuf;
     uint32_t *tmem_slot = (uint32_t *)(drain + 1);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
     float *lam = (float *)(tmem_slot + 4);
@@ -192,6 +196,8 @@ __global__ void __launch_bounds__(kPlThreads, 1) k_dst_plane(const __grid_consta
             mbar_init(&loaded[e], 1);
             mbar_init(&opready[e], kPlRows);
             mbar_init(&accfull[e], 1);
+            mbar_init(&outw[e], kPlRows);
+            mbar_init(&outfree[e], 1);
         }
         mbar_init(drain, 1);
         *abort_flag = 0;
@@ -235,7 +241,6 @@ __global__ void __launch_bounds__(kPlThreads, 1) k_dst_plane(const __grid_consta
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const long long Ng2 = (long long)Ng * Ng;
     const long long ntrip = (my_items + kPlBuf - 1) / kPlBuf;
 
     if (warp == 3) {
@@ -348,6 +353,18 @@ __global__ void __launch_bounds__(kPlThreads, 1) k_dst_plane(const __grid_consta
                         x[k >> 4][(k & 15) + 3] = v.w;
                     }
                 mbar_arrive(&stfree[b]);
+                // the operand buffer holds the previous plane's output until its tensor store
+                // has read it (issued by the group's thread 0, which signals here)
+                if (q > 0) {
+                    if (row == 0) {
+                        bulk_wait_read();
+                        mbar_arrive(&outfree[e]);
+                    }
+                    if (!mbar_wait(&outfree[e], (uint32_t)((q - 1) & 1), abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                }
                 const int s0 = row_exp(row_max(x));
                 if (row < Npad) put_row(x, pow2f(s0), row, nu, och, hi, lo);
                 un[row] = pow2f(-(kSExp + s0));
@@ -355,7 +372,6 @@ __global__ void __launch_bounds__(kPlThreads, 1) k_dst_plane(const __grid_consta
             fence_proxy_async();
             mbar_arrive(&opready[e]);
             const float lam_row = row < Ng ? lam[row] : 0.0f, lam_n = lam[n];
-            float *dst = A.out + m_off + (long long)n * Ng2 + (long long)row * Ng;
             for (int s = 1; s <= 4; ++s) {
                 if (!mbar_wait(&accfull[e], (uint32_t)((s - 1) & 1), abort_flag)) {
                     ok = false;
@@ -400,19 +416,33 @@ __global__ void __launch_bounds__(kPlThreads, 1) k_dst_plane(const __grid_consta
                         }
                     }
                 if (s == 4) {
-                    // row i' of the output plane
+                    // row i' of the output plane into the operand buffer (32-column chunks,
+                    // 128-byte swizzle, as the copies bring the planes in); thread 0 of the
+                    // group stores the plane once every row is written
                     if (row < Ng) {
 #pragma unroll
-                        for (int c = 0; c < kPlMaxN / 16; ++c)
+                        for (int c = 0; c < kPlMaxN / 32; ++c)
 #pragma unroll
-                            for (int qq = 0; qq < 4; ++qq) {
-                                const int col = 16 * c + 4 * qq;
-                                if (col < Ng)
-                                    *reinterpret_cast<float4 *>(dst + col) = make_float4(
-                                        x[c][4 * qq], x[c][4 * qq + 1], x[c][4 * qq + 2], x[c][4 * qq + 3]);
+                            for (int qq = 0; qq < 8; ++qq) {
+                                const int k = 32 * c + 4 * qq;
+                                if (c < nka)
+                                    *reinterpret_cast<float4 *>(hi + (uint32_t)c * och + sw128_offset(row, 4 * qq)) =
+                                        make_float4(x[k >> 4][k & 15], x[k >> 4][(k & 15) + 1], x[k >> 4][(k & 15) + 2],
+                                                    x[k >> 4][(k & 15) + 3]);
                             }
                     }
+                    fence_proxy_async();
                     tc_fence_before();
+                    mbar_arrive(&outw[e]);
+                    if (row == 0) {
+                        if (!mbar_wait(&outw[e], (uint32_t)(q & 1), abort_flag)) {
+                            ok = false;
+                            break;
+                        }
+                        const int y = (int)(m_off / Ng + (long long)n * Ng);     // row (n, i' = 0)
+                        for (int c = 0; c < nka; ++c) tma_store_2d(&G.out_map, c * 32, y, smem_u32(hi + (size_t)c * och));
+                        bulk_commit();
+                    }
                 } else {
                     const int sr = row_exp(row_max(x));
                     if (row < Npad) put_row(x, pow2f(sr), row, nu, och, hi, lo);
@@ -423,6 +453,8 @@ __global__ void __launch_bounds__(kPlThreads, 1) k_dst_plane(const __grid_consta
                 }
             }
         }
+        // thread 0's tensor stores complete before the CTA exits
+        if (row == 0) bulk_wait_all();
         if (!ok) *abort_flag = 1;
     }
 
@@ -443,7 +475,7 @@ __global__ void __launch_bounds__(kPlThreads, 1) k_dst_plane(const __grid_consta
 size_t plane_smem_bytes(int Ng, int Npad, int nka) {
     const size_t nk64 = (size_t)(Ng + 63) / 64;
     return 1024 + 2 * kPlBuf * nk64 * Npad * 128 + kPlStage * (size_t)nka * Npad * 128 +
-           (kPlStage + 3 * kPlBuf + 1) * 8 + 16 + 128 * 4 + kPlBuf * 2 * 128 * 4 + 64;
+           (kPlStage + 5 * kPlBuf + 1) * 8 + 16 + 128 * 4 + kPlBuf * 2 * 128 * 4 + 64;
 }
 
 constexpr size_t kPlSmemBudget = 227 * 1024;
@@ -452,9 +484,10 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-// W1 as a 2D tensor of rows of Ng floats, boxes of 32 x Npad with the 128-byte swizzle (the
-// staging layout the splitting threads read).
-cudaError_t plane_map(Ctx &c, const float *buf, int Ng, int Npad, CUtensorMap *out) {
+// A plane-major mesh buffer as a 2D tensor of rows of Ng floats, boxes of 32 x `rows` with
+// the 128-byte swizzle: W1 with rows = Npad (the staging layout the splitting threads read),
+// W2 with rows = Ng (the output planes).
+cudaError_t plane_map(Ctx &c, const float *buf, int Ng, int rows, CUtensorMap *out) {
     static EncodeTiledFn encode = nullptr;
     if (!encode) {
         void *fn = nullptr;
@@ -465,7 +498,7 @@ cudaError_t plane_map(Ctx &c, const float *buf, int Ng, int Npad, CUtensorMap *o
     }
     const cuuint64_t dims[2] = {(cuuint64_t)Ng, (cuuint64_t)(c.M / Ng)};
     const cuuint64_t strides[1] = {(cuuint64_t)Ng * sizeof(float)};
-    const cuuint32_t box[2] = {32u, (cuuint32_t)Npad};
+    const cuuint32_t box[2] = {32u, (cuuint32_t)rows};
     const cuuint32_t estr[2] = {1, 1};
     if (encode(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(buf), dims, strides, box, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -510,6 +543,7 @@ cudaError_t launch_plane_pass(Ctx &c, const std::vector<TcGroup> &groups, const 
             P.Npad = (G.Ng + 15) / 16 * 16;
             P.nka = G.nkc;
             cudaError_t e = plane_map(c, in, P.Ng, P.Npad, &P.in_map);
+            if (e == cudaSuccess) e = plane_map(c, out, P.Ng, P.Ng, &P.out_map);
             if (e != cudaSuccess) return e;
             P.items = G.planes;
             P.nitems = G.nplanes;
@@ -525,7 +559,6 @@ cudaError_t launch_plane_pass(Ctx &c, const std::vector<TcGroup> &groups, const 
         }
         a.ngroups = ng;
         a.boxes = c.boxes;
-        a.out = out;
         a.err = c.dev_err;
         a.lo_lo = c.tc_lo_lo ? 1 : 0;
         k_dst_plane<<<cta0, kPlThreads, smem, c.stream>>>(a);
