@@ -224,6 +224,12 @@ class OraclePool:
         self.next = 0
         self._start = [self.ex.submit(int, i) for i in range(self.cores)]   # spawn the workers now
 
+    def wait_ready(self):
+        """Block until every worker has built its initial conditions (so that no oracle work
+        competes with a timed region for the host cores)."""
+        for f in self._start:
+            f.result()
+
     def run(self, k):
         ids = [((self.next + i) * 37) % self.nboxes for i in range(k)]
         self.next += k
@@ -515,7 +521,8 @@ def run_gpu(args, rank, world, local_rank):
     import synth_inputs
 
     # the oracle's host processes start first (spawned, single-threaded); they build their
-    # initial conditions while the GPU work below runs
+    # initial conditions while the GPU context, the inputs and the autotuners are set up, and
+    # are idle before the first timed region (wait_ready below)
     pool = OraclePool(args.workload) if rank == 0 and not args.no_cpu_baseline else None
     torch.cuda.set_device(local_rank)
     dist = None
@@ -580,6 +587,8 @@ def run_gpu(args, rank, world, local_rank):
         return float(t.item())
 
     clocks = ClockSampler(local_rank)
+    if pool is not None:
+        pool.wait_ready()
     barrier()
     torch.cuda.synchronize()
     clocks.start()
