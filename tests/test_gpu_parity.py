@@ -137,7 +137,20 @@ def test_largest_mesh_force_matches_oracle(variant):
     _check_pm_force(kw, variant, False)
 
 
-def _check_pm_force(kw, variant, expect_drop):
+@pytest.mark.parametrize("variant", ["simt", "tc", "tc3", "radix"])
+@pytest.mark.parametrize("d1_exp", [-60, 60])
+def test_pm_force_far_outside_fp16_range(variant, d1_exp):
+    # The solve's source is delta / D1 minus the boundary term of the unscaled shell (Eq. 23
+    # scales the shell by D1), and the returned potential is D1 times the solution: D1 = 2^-60
+    # makes the source ~2^60 times the density, D1 = 2^60 leaves a source of O(1) whose
+    # potential is returned ~2^60 large.  Both are far outside FP16's range (the three-pass
+    # form's plane pass multiplies FP16 hi/lo parts, each pencil scaled by a power of two
+    # first); every form must keep the relative accuracy it has at D1 = 0.73 against the
+    # FP64 oracle, which is exact at any D1.
+    _check_pm_force(CASES_PM["ratio2"], variant, False, D1=2.0**d1_exp)
+
+
+def _check_pm_force(kw, variant, expect_drop, D1=0.73):
     cfg = oracle_cfg(kw)
     w, f, sched = oracle_fields(kw)
     sim = _sim(kw, variant)
@@ -146,7 +159,6 @@ def _check_pm_force(kw, variant, expect_drop):
     sim.setup_boxes()
     if variant == "radix" or (variant == "auto" and max(_mesh_sizes(kw)) > 240):
         assert sim.stats()["dst_form"] == sc.SCOLA_DST_RADIX
-    D1 = 0.73
     s_all, refs = [], []
     for b in range(cfg.nboxes):
         g, ids, s0 = box_initial_displacements(cfg, f, sched, b)
