@@ -62,6 +62,11 @@ CASES_PM = {
     # an odd number of particles per side: the initial conditions' top positive wavenumber
     # (N - 1) / 2 has no negative twin
     "odd_np": dict(SMALL, Np=25, Ntiles=1, Nbuf=0, nsteps=4),
+    # the three-pass solve's extremes: one 16-column K step (Ng = 12, padded to 16 rows), and
+    # a full-width plane (Ng = 92: three 32-column copies, six K steps, padded to 96 rows
+    # that bring the next plane's first rows along)
+    "tiny_mesh": dict(L=40.0, Np=8, Ntiles=1, Nbuf=0, Ng=12, nsteps=2, a_i=0.05, a_f=1.0),
+    "ng92": dict(L=92.0, Np=46, Ntiles=1, Nbuf=0, Ng=92, nsteps=2, a_i=0.05, a_f=1.0),
 }
 
 
