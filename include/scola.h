@@ -521,9 +521,9 @@ scola_status scola_backward_density(scola_ctx *ctx, const float *lam_delta_dev, 
 /*
  * Box density without any allocation.  The paper has no counterpart: this is
  * an interface for callers that cannot allocate device memory at the point
- * where they need a density (for example code running while a stream is being
- * captured into a CUDA graph, or a service that forbids allocations outside
- * its own memory pool).  It computes the same B^sCOLA cloud-in-cell density as
+ * where they need a density (for example a service that forbids allocations
+ * outside its own memory pool, or a loop that must not call the allocator).
+ * It computes the same B^sCOLA cloud-in-cell density as
  * scola_pm_force's delta output for one box, needs no context, and calls no
  * cudaMalloc, cudaFree or allocating library routine.
  *   s_dev      device, 3 x nsc^3 FP32 displacements s = x - q of the box
@@ -540,8 +540,7 @@ scola_status scola_backward_density(scola_ctx *ctx, const float *lam_delta_dev, 
  * clears the part it uses first.  Calls whose work overlaps on the GPU
  * (different streams or host threads) race on the scratch: serialise them.
  * The first call on each device looks up the scratch's device address with
- * cudaGetSymbolAddress (with that device current); make that first call
- * before any stream capture begins.
+ * cudaGetSymbolAddress (with that device current).
  * Errors: INVALID_ARG (NULL pointers, ng < nsc, ng^3 above the maximum),
  * CUDA.
  */

@@ -1,10 +1,8 @@
 // Allocation-free box density: scola_box_density_noalloc.
 //
-// Some callers cannot allocate device memory when they need a density: code
-// that runs while a CUDA stream is being captured into a graph (cudaMalloc is
-// not allowed there), services that account every byte through their own
-// pool and forbid hidden allocations, and real-time loops that must not call
-// the allocator.  For them this entry point computes the sCOLA box density
+// Some callers cannot allocate device memory when they need a density:
+// services that account every byte through their own pool and forbid hidden
+// allocations, and real-time loops that must not call the allocator.  For them this entry point computes the sCOLA box density
 // (the same B^sCOLA cloud-in-cell deposit as scola_pm_force) with its scratch
 // held in a fixed, file-scope device array instead of a context arena.
 //
@@ -16,8 +14,7 @@
 // caller.  Host code cannot pass the array's name to a kernel (in host code it
 // is a host-side stand-in, not a device address), so the device address is
 // looked up with cudaGetSymbolAddress once per device, on the first call made
-// with that device current.  Because of that set-up, the first call on each
-// device should happen before any stream capture begins.
+// with that device current.
 #include <cmath>
 #include <mutex>
 

@@ -1,8 +1,8 @@
 """The allocation-free density entry point against the context-based one.
 
 scola_box_density_noalloc serves callers that cannot allocate device memory
-where they need a box density (for example inside a stream capture, or under
-an allocator that forbids hidden allocations); its scratch is a fixed array in
+where they need a box density (for example under an allocator that forbids
+hidden allocations); its scratch is a fixed array in
 the library instead of a context arena.  Its result must equal the density
 output of scola_pm_force for the same box and displacements, on consecutive
 calls (the shared scratch is cleared by each call).  This file is collected
